@@ -1,0 +1,1334 @@
+// ASMG oracle: TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, single-threaded FP64 restatement of the auxiliary-space
+// multigrid preconditioned CG of Grasedyck, Wang and Xu ("A Nearly Optimal
+// Multigrid Method for General Unstructured Grids").  Only the test suite,
+// the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+// shares no code, header or table with the CUDA library and imports nothing
+// from it.  Compile with -O2 -ffp-contract=off (no FMA contraction) so that
+// the cluster-tree quantisation rounds exactly like the device code.
+//
+// Each function names the passage of the paper it follows.  Where the paper
+// is silent or garbled, the reading taken is stated beside the code:
+//   R1  root box = vertex bounding box widened to a square at its min corner
+//   R2  quantised Morton keys with D = 31 (2D) / 21 (3D) bits per coordinate
+//   R3  closure = unique minimal edge-2:1-balanced refinement of the box tree
+//   R4  box triangulation: SW-NE diagonal, or a centre fan when an edge
+//       carries a hanging midpoint (the Fig. "closure2" templates)
+//   R5  Scott-Zhang support sigma_i = lowest-index element at node i;
+//       psi_i = (12 lambda_i - 3)/|sigma_i| (2D dual basis); exact clipping
+//   R6  finest auxiliary coefficient = area-weighted mean of the fine ones;
+//       coarser auxiliary operators are Galerkin (I^T A I)
+//   R7  smoother R_l = multicolour Gauss-Seidel on the set N~_l of new or
+//       changed nodes (local smoothing, eq. "decomposition"); "full" mode
+//       smooths every node of the level instead
+//   R8  Algorithm 1 with "+" corrections applied from zero as a preconditioner
+//   R9  flexible (Polak-Ribiere) beta in PCG, stop at ||r|| <= rtol ||b||
+//   R10 colouring = Jones-Plassmann with splitmix64 priorities, smallest
+//       free colour; the same definition is implemented independently on
+//       the device, so no colouring is ever passed from one side to the other
+//
+// 3D: fine assembly, mass matrix and the octree are dimension-generic; the
+// auxiliary hierarchy is built for d = 2 only.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+typedef __int128 i128;
+
+struct CSR {
+  int64_t nr = 0, nc = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  double get(int64_t i, int32_t j) const {
+    for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p)
+      if (col[p] == j) return val[p];
+    return 0.0;
+  }
+};
+
+// Build a CSR matrix from per-row (column, value) lists: sort each row by
+// column and add duplicates.
+CSR csr_from_rows(int64_t nr, int64_t nc, std::vector<std::vector<std::pair<int32_t, double>>>& rows) {
+  CSR M;
+  M.nr = nr;
+  M.nc = nc;
+  M.ptr.assign(nr + 1, 0);
+  for (int64_t i = 0; i < nr; ++i) {
+    auto& r = rows[i];
+    std::stable_sort(r.begin(), r.end(),
+                     [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) { return a.first < b.first; });
+    int64_t cnt = 0;
+    for (size_t k = 0; k < r.size(); ++k)
+      if (k == 0 || r[k].first != r[k - 1].first) ++cnt;
+    M.ptr[i + 1] = M.ptr[i] + cnt;
+  }
+  M.col.resize(M.ptr[nr]);
+  M.val.resize(M.ptr[nr]);
+  for (int64_t i = 0; i < nr; ++i) {
+    auto& r = rows[i];
+    int64_t p = M.ptr[i] - 1;
+    for (size_t k = 0; k < r.size(); ++k) {
+      if (k == 0 || r[k].first != r[k - 1].first) {
+        ++p;
+        M.col[p] = r[k].first;
+        M.val[p] = 0.0;
+      }
+      M.val[p] += r[k].second;
+    }
+    std::vector<std::pair<int32_t, double>>().swap(r);
+  }
+  return M;
+}
+
+void spmv(const CSR& A, const double* x, double* y) {
+  for (int64_t i = 0; i < A.nr; ++i) {
+    double s = 0.0;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) s += A.val[p] * x[A.col[p]];
+    y[i] = s;
+  }
+}
+
+CSR transpose(const CSR& A) {
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(A.nc);
+  for (int64_t i = 0; i < A.nr; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) rows[A.col[p]].push_back({(int32_t)i, A.val[p]});
+  return csr_from_rows(A.nc, A.nr, rows);
+}
+
+// C = A * B (plain row-by-row sparse product).
+CSR matmul(const CSR& A, const CSR& B) {
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(A.nr);
+  for (int64_t i = 0; i < A.nr; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+      for (int64_t q = B.ptr[A.col[p]]; q < B.ptr[A.col[p] + 1]; ++q)
+        rows[i].push_back({B.col[q], A.val[p] * B.val[q]});
+  return csr_from_rows(A.nr, B.nc, rows);
+}
+
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+  double s = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) s += a[i] * b[i];
+  return s;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014; Vigna's published constants): a
+// counter-based 64-bit mixer used for colouring priorities.
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+struct Params {
+  int n_min = 3, nu_pre = 2, nu_post = 2, coarse_max = 512, smoothing = 0, max_iter = 500, colouring = 0, stage = 2;
+};
+
+struct Seg {
+  uint64_t prefix;
+  int64_t begin, end;
+  int split;
+};
+
+struct Level {
+  std::vector<uint64_t> key;                 // free nodes, ascending lattice Morton key
+  std::vector<uint64_t> allkey;              // all nodes incl. boundary, ascending
+  std::vector<std::array<uint64_t, 3>> tri;  // level triangles (lattice Morton keys, CCW)
+  CSR A;                                     // level operator on free nodes
+  CSR I;                                     // nodal interpolation from level l-1
+  std::vector<int32_t> smooth;               // smoothing set sorted by (colour, index)
+  std::vector<int32_t> colour;               // colour per free node, -1 outside the set
+  std::vector<int32_t> cstart;               // colour class starts in `smooth`
+};
+
+struct Oracle {
+  int dim = 2;
+  int64_t nv = 0, ne = 0;
+  std::vector<double> X;
+  std::vector<int32_t> E;
+  std::vector<uint8_t> bflag;
+  std::vector<double> coeff;
+  Params prm;
+  std::string err;
+
+  // fine problem (Sec. 2)
+  std::vector<int32_t> free_of_vertex, vertex_of_free;
+  CSR A;
+  std::vector<int32_t> fine_colour, fine_smooth, fine_cstart;
+
+  // cluster tree (Sec. 3.1)
+  int D = 31;
+  double amin[3] = {0, 0, 0}, L = 0;
+  std::vector<uint64_t> keys;   // per element, in element order
+  std::vector<int32_t> perm;    // elements sorted by key (stable)
+  std::vector<std::vector<Seg>> tree;
+
+  // closed box tree (Sec. 3.2): per depth, packed box coordinates -> split
+  std::vector<std::unordered_map<uint64_t, uint8_t>> boxes;
+  int J = 0;  // finest auxiliary level (depth)
+  int c = 0;  // coarsest level used by the V-cycle
+  std::vector<Level> lv;
+  std::vector<double> finest_coef;  // per triangle of level J
+  CSR P, Pfull;                     // Scott-Zhang transfer (free / all aux columns)
+  std::vector<double> chol;         // dense Cholesky factor of A_c (row-major lower)
+  int64_t nc_dense = 0;
+};
+
+// --------------------------------------------------------------------------
+// Sec. 2: P1 stiffness a_ij = int a grad phi_i . grad phi_j and mass matrix.
+// --------------------------------------------------------------------------
+
+// Barycentric gradients G (rows) and measure of a simplex.
+void simplex_geometry(const Oracle& o, int64_t e, double G[4][3], double& vol) {
+  const int d = o.dim;
+  const int32_t* v = &o.E[e * (d + 1)];
+  const double* p0 = &o.X[(int64_t)v[0] * d];
+  if (d == 2) {
+    const double* p1 = &o.X[(int64_t)v[1] * 2];
+    const double* p2 = &o.X[(int64_t)v[2] * 2];
+    double x10 = p1[0] - p0[0], y10 = p1[1] - p0[1], x20 = p2[0] - p0[0], y20 = p2[1] - p0[1];
+    double det = x10 * y20 - x20 * y10;
+    vol = 0.5 * det;
+    G[1][0] = y20 / det;
+    G[1][1] = -x20 / det;
+    G[2][0] = -y10 / det;
+    G[2][1] = x10 / det;
+    G[0][0] = -(G[1][0] + G[2][0]);
+    G[0][1] = -(G[1][1] + G[2][1]);
+  } else {
+    double Jm[3][3];
+    for (int k = 1; k <= 3; ++k)
+      for (int r = 0; r < 3; ++r) Jm[r][k - 1] = o.X[(int64_t)v[k] * 3 + r] - p0[r];
+    double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
+                 Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
+                 Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+    vol = det / 6.0;
+    // rows of J^{-1} are the gradients of lambda_1..lambda_3
+    double inv[3][3];
+    inv[0][0] = (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) / det;
+    inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
+    inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
+    inv[1][0] = (Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2]) / det;
+    inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
+    inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
+    inv[2][0] = (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]) / det;
+    inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
+    inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) G[k + 1][r] = inv[k][r];
+    for (int r = 0; r < 3; ++r) G[0][r] = -(G[1][r] + G[2][r] + G[3][r]);
+  }
+}
+
+void assemble_fine(Oracle& o) {
+  const int d = o.dim, nvert = d + 1;
+  o.free_of_vertex.assign(o.nv, -1);
+  o.vertex_of_free.clear();
+  for (int64_t v = 0; v < o.nv; ++v)
+    if (o.bflag[v] != 1) {
+      o.free_of_vertex[v] = (int32_t)o.vertex_of_free.size();
+      o.vertex_of_free.push_back((int32_t)v);
+    }
+  int64_t n = o.vertex_of_free.size();
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
+  for (int64_t e = 0; e < o.ne; ++e) {
+    double G[4][3], vol;
+    simplex_geometry(o, e, G, vol);
+    double a = o.coeff.empty() ? 1.0 : o.coeff[e];
+    const int32_t* v = &o.E[e * nvert];
+    for (int i = 0; i < nvert; ++i) {
+      int32_t fi = o.free_of_vertex[v[i]];
+      if (fi < 0) continue;
+      for (int j = 0; j < nvert; ++j) {
+        int32_t fj = o.free_of_vertex[v[j]];
+        if (fj < 0) continue;
+        double g = 0.0;
+        for (int r = 0; r < d; ++r) g += G[i][r] * G[j][r];
+        rows[fi].push_back({fj, a * vol * g});
+      }
+    }
+  }
+  o.A = csr_from_rows(n, n, rows);
+}
+
+// b = M f_h restricted to free rows; M_e = |tau| (1 + delta_ij) / ((d+1)(d+2)).
+void mass_apply(const Oracle& o, const double* f, double* b) {
+  const int d = o.dim, nvert = d + 1;
+  const double den = (d == 2) ? 12.0 : 20.0;
+  std::vector<double> full(o.nv, 0.0);
+  for (int64_t e = 0; e < o.ne; ++e) {
+    double G[4][3], vol;
+    simplex_geometry(o, e, G, vol);
+    const int32_t* v = &o.E[e * nvert];
+    for (int i = 0; i < nvert; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < nvert; ++j) s += (i == j ? 2.0 : 1.0) * f[v[j]];
+      full[v[i]] += vol / den * s;
+    }
+  }
+  for (size_t k = 0; k < o.vertex_of_free.size(); ++k) b[k] = full[o.vertex_of_free[k]];
+}
+
+// --------------------------------------------------------------------------
+// Sec. 3.1: box tree over element barycenters (R1, R2).
+// --------------------------------------------------------------------------
+
+uint64_t interleave(const uint64_t* q, int dim, int bits) {
+  uint64_t key = 0;
+  for (int j = 0; j < bits; ++j)
+    for (int k = 0; k < dim; ++k)
+      if ((q[k] >> j) & 1ULL) key |= 1ULL << (dim * j + k);
+  return key;
+}
+
+void deinterleave(uint64_t key, int dim, int bits, uint64_t* q) {
+  for (int k = 0; k < dim; ++k) q[k] = 0;
+  for (int j = 0; j < bits; ++j)
+    for (int k = 0; k < dim; ++k)
+      if ((key >> (dim * j + k)) & 1ULL) q[k] |= 1ULL << j;
+}
+
+uint64_t pack_box(const uint64_t* q, int dim) {
+  return dim == 2 ? (q[0] | (q[1] << 32)) : (q[0] | (q[1] << 21) | (q[2] << 42));
+}
+
+void unpack_box(uint64_t p, int dim, uint64_t* q) {
+  if (dim == 2) {
+    q[0] = p & 0xffffffffULL;
+    q[1] = p >> 32;
+  } else {
+    q[0] = p & 0x1fffffULL;
+    q[1] = (p >> 21) & 0x1fffffULL;
+    q[2] = p >> 42;
+  }
+}
+
+void build_tree(Oracle& o) {
+  const int d = o.dim, nvert = d + 1;
+  o.D = (d == 2) ? 31 : 21;
+  double mx[3];
+  for (int k = 0; k < d; ++k) {
+    o.amin[k] = INFINITY;
+    mx[k] = -INFINITY;
+  }
+  for (int64_t v = 0; v < o.nv; ++v)
+    for (int k = 0; k < d; ++k) {
+      o.amin[k] = std::min(o.amin[k], o.X[v * d + k]);
+      mx[k] = std::max(mx[k], o.X[v * d + k]);
+    }
+  o.L = 0.0;
+  for (int k = 0; k < d; ++k) o.L = std::max(o.L, mx[k] - o.amin[k]);
+  // Quantisation: q = floor((sum_v p_v - (d+1) a) * 2^D / ((d+1) L)), clamped.
+  const double S = std::ldexp(1.0, o.D) / (double)(d + 1) / o.L;
+  double Ak[3];
+  for (int k = 0; k < d; ++k) Ak[k] = (double)(d + 1) * o.amin[k];
+  const uint64_t qmax = (1ULL << o.D) - 1;
+  o.keys.resize(o.ne);
+  for (int64_t e = 0; e < o.ne; ++e) {
+    uint64_t q[3];
+    for (int k = 0; k < d; ++k) {
+      double s = o.X[(int64_t)o.E[e * nvert] * d + k];
+      for (int j = 1; j < nvert; ++j) s = s + o.X[(int64_t)o.E[e * nvert + j] * d + k];
+      double t = (s - Ak[k]) * S;
+      double f = std::floor(t);
+      if (!(f > 0.0)) f = 0.0;
+      q[k] = (f >= (double)qmax) ? qmax : (uint64_t)f;
+    }
+    o.keys[e] = interleave(q, d, o.D);
+  }
+  o.perm.resize(o.ne);
+  for (int64_t e = 0; e < o.ne; ++e) o.perm[e] = (int32_t)e;
+  std::stable_sort(o.perm.begin(), o.perm.end(), [&](int32_t a, int32_t b) { return o.keys[a] < o.keys[b]; });
+  // Level-by-level subdivision; a node with more than n_min barycenters is
+  // split into all 2^d children, including empty ones (Sec. 3.1).
+  o.tree.clear();
+  o.tree.push_back({Seg{0, 0, o.ne, 0}});
+  for (int lvl = 0;; ++lvl) {
+    std::vector<Seg> next;
+    for (auto& s : o.tree[lvl]) {
+      if (s.end - s.begin <= o.prm.n_min || lvl >= o.D) continue;
+      s.split = 1;
+      const int shift = d * (o.D - lvl - 1);
+      int64_t p = s.begin;
+      for (uint64_t ch = 0; ch < (1ULL << d); ++ch) {
+        int64_t b = p;
+        while (p < s.end && ((o.keys[o.perm[p]] >> shift) & ((1ULL << d) - 1)) == ch) ++p;
+        next.push_back(Seg{(s.prefix << d) | ch, b, p, 0});
+      }
+    }
+    if (next.empty()) break;
+    o.tree.push_back(next);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Sec. 3.2: closure (R3).  A leaf must be split when an edge-adjacent leaf
+// (face- or edge-adjacent in 3D) is two or more levels finer.
+// --------------------------------------------------------------------------
+
+bool box_exists(const Oracle& o, int depth, const uint64_t* q, uint8_t* split) {
+  if (depth >= (int)o.boxes.size()) return false;
+  auto it = o.boxes[depth].find(pack_box(q, o.dim));
+  if (it == o.boxes[depth].end()) return false;
+  if (split) *split = it->second;
+  return true;
+}
+
+// The neighbour offsets whose shared boundary with a box can carry hanging
+// nodes: edges in 2D; faces and edges in 3D.
+std::vector<std::array<int, 3>> neighbour_offsets(int dim) {
+  std::vector<std::array<int, 3>> offs;
+  for (int z = (dim == 3 ? -1 : 0); z <= (dim == 3 ? 1 : 0); ++z)
+    for (int y = -1; y <= 1; ++y)
+      for (int x = -1; x <= 1; ++x) {
+        int nz = (x != 0) + (y != 0) + (z != 0);
+        if (nz >= 1 && nz <= dim - 1) offs.push_back({x, y, z});
+      }
+  return offs;
+}
+
+bool must_split(const Oracle& o, int depth, const uint64_t* q, const std::vector<std::array<int, 3>>& offs) {
+  const int d = o.dim;
+  const int64_t nb = 1LL << depth;
+  for (auto& off : offs) {
+    uint64_t n[3];
+    bool inside = true;
+    for (int k = 0; k < d; ++k) {
+      int64_t v = (int64_t)q[k] + off[k];
+      if (v < 0 || v >= nb) inside = false;
+      n[k] = (uint64_t)v;
+    }
+    if (!inside) continue;
+    uint8_t sp = 0;
+    if (!box_exists(o, depth, n, &sp) || !sp) continue;
+    for (int ch = 0; ch < (1 << d); ++ch) {
+      bool touches = true;
+      uint64_t cq[3];
+      for (int k = 0; k < d; ++k) {
+        int bit = (ch >> k) & 1;
+        if (off[k] == 1 && bit != 0) touches = false;
+        if (off[k] == -1 && bit != 1) touches = false;
+        cq[k] = 2 * n[k] + bit;
+      }
+      if (!touches) continue;
+      uint8_t csp = 0;
+      if (box_exists(o, depth + 1, cq, &csp) && csp) return true;
+    }
+  }
+  return false;
+}
+
+void build_closure(Oracle& o) {
+  const int d = o.dim;
+  o.boxes.assign(o.tree.size(), {});
+  for (size_t lvl = 0; lvl < o.tree.size(); ++lvl)
+    for (auto& s : o.tree[lvl]) {
+      uint64_t q[3];
+      deinterleave(s.prefix, d, (int)lvl, q);
+      o.boxes[lvl][pack_box(q, d)] = (uint8_t)s.split;
+    }
+  auto offs = neighbour_offsets(d);
+  for (;;) {
+    std::vector<std::pair<int, uint64_t>> todo;
+    for (size_t lvl = 0; lvl < o.boxes.size(); ++lvl)
+      for (auto& kv : o.boxes[lvl]) {
+        if (kv.second) continue;
+        uint64_t q[3];
+        unpack_box(kv.first, d, q);
+        if (must_split(o, (int)lvl, q, offs)) todo.push_back({(int)lvl, kv.first});
+      }
+    if (todo.empty()) break;
+    for (auto& t : todo) {
+      o.boxes[t.first][t.second] = 1;
+      if ((int)o.boxes.size() <= t.first + 1) o.boxes.resize(t.first + 2);
+      uint64_t q[3];
+      unpack_box(t.second, d, q);
+      for (int ch = 0; ch < (1 << d); ++ch) {
+        uint64_t cq[3];
+        for (int k = 0; k < d; ++k) cq[k] = 2 * q[k] + ((ch >> k) & 1);
+        o.boxes[t.first + 1][pack_box(cq, d)] = 0;
+      }
+    }
+  }
+  while (!o.boxes.empty() && o.boxes.back().empty()) o.boxes.pop_back();
+  o.J = (int)o.boxes.size() - 1;
+}
+
+// --------------------------------------------------------------------------
+// Sec. 3.3: conforming nested auxiliary triangulations sigma^(l) (R4), 2D.
+// Lattice coordinates are integers on the 2^D grid of the root box.
+// --------------------------------------------------------------------------
+
+uint64_t node_key2(uint64_t x, uint64_t y) {
+  uint64_t q[2] = {x, y};
+  return interleave(q, 2, 32);
+}
+
+void node_xy(uint64_t key, uint64_t& x, uint64_t& y) {
+  uint64_t q[2];
+  deinterleave(key, 2, 32, q);
+  x = q[0];
+  y = q[1];
+}
+
+// Triangles of box (depth, ix, iy) as seen at level `lvl`: the SW-NE diagonal
+// split, or a fan about the centre when a same-depth edge neighbour is split
+// (then the shared edge carries a hanging midpoint).
+void box_triangles(const Oracle& o, int depth, uint64_t ix, uint64_t iy, int lvl,
+                   std::vector<std::array<uint64_t, 3>>& out) {
+  const uint64_t s = 1ULL << (o.D - depth);
+  const uint64_t x0 = ix * s, y0 = iy * s;
+  bool hang[4] = {false, false, false, false};  // S, E, N, W
+  if (depth < lvl) {
+    const int dx[4] = {0, 1, 0, -1}, dy[4] = {-1, 0, 1, 0};
+    const int64_t nb = 1LL << depth;
+    for (int e = 0; e < 4; ++e) {
+      int64_t nx = (int64_t)ix + dx[e], ny = (int64_t)iy + dy[e];
+      if (nx < 0 || ny < 0 || nx >= nb || ny >= nb) continue;
+      uint64_t q[2] = {(uint64_t)nx, (uint64_t)ny};
+      uint8_t sp = 0;
+      if (box_exists(o, depth, q, &sp) && sp) hang[e] = true;
+    }
+  }
+  uint64_t SW = node_key2(x0, y0), SE = node_key2(x0 + s, y0), NE = node_key2(x0 + s, y0 + s),
+           NW = node_key2(x0, y0 + s);
+  if (!(hang[0] || hang[1] || hang[2] || hang[3])) {
+    out.push_back({SW, SE, NE});
+    out.push_back({SW, NE, NW});
+    return;
+  }
+  const uint64_t h = s / 2;
+  uint64_t C = node_key2(x0 + h, y0 + h);
+  std::vector<uint64_t> ring;
+  ring.push_back(SW);
+  if (hang[0]) ring.push_back(node_key2(x0 + h, y0));
+  ring.push_back(SE);
+  if (hang[1]) ring.push_back(node_key2(x0 + s, y0 + h));
+  ring.push_back(NE);
+  if (hang[2]) ring.push_back(node_key2(x0 + h, y0 + s));
+  ring.push_back(NW);
+  if (hang[3]) ring.push_back(node_key2(x0, y0 + h));
+  for (size_t i = 0; i < ring.size(); ++i) out.push_back({ring[i], ring[(i + 1) % ring.size()], C});
+}
+
+bool on_boundary(const Oracle& o, uint64_t key) {
+  uint64_t x, y;
+  node_xy(key, x, y);
+  const uint64_t top = 1ULL << o.D;
+  return x == 0 || y == 0 || x == top || y == top;
+}
+
+void level_triangles(const Oracle& o, int lvl, std::vector<std::array<uint64_t, 3>>& tri) {
+  tri.clear();
+  for (int depth = 0; depth <= lvl && depth < (int)o.boxes.size(); ++depth) {
+    // deterministic order: sort the boxes of this depth by packed coordinate
+    std::vector<std::pair<uint64_t, uint8_t>> bx(o.boxes[depth].begin(), o.boxes[depth].end());
+    std::sort(bx.begin(), bx.end());
+    for (auto& kv : bx) {
+      if (depth < lvl && kv.second) continue;  // interior box of the truncated tree
+      uint64_t q[2];
+      unpack_box(kv.first, 2, q);
+      box_triangles(o, depth, q[0], q[1], lvl, tri);
+    }
+  }
+}
+
+int32_t find_index(const std::vector<uint64_t>& sorted, uint64_t k) {
+  auto it = std::lower_bound(sorted.begin(), sorted.end(), k);
+  if (it == sorted.end() || *it != k) return -1;
+  return (int32_t)(it - sorted.begin());
+}
+
+void physical(const Oracle& o, uint64_t key, double* p) {
+  uint64_t x, y;
+  node_xy(key, x, y);
+  p[0] = o.amin[0] + std::ldexp((double)x, -o.D) * o.L;
+  p[1] = o.amin[1] + std::ldexp((double)y, -o.D) * o.L;
+}
+
+// P1 stiffness of a triangle given in physical coordinates.
+void tri_stiffness(const double* p0, const double* p1, const double* p2, double K[3][3]) {
+  double x10 = p1[0] - p0[0], y10 = p1[1] - p0[1], x20 = p2[0] - p0[0], y20 = p2[1] - p0[1];
+  double det = x10 * y20 - x20 * y10;
+  double G[3][2];
+  G[1][0] = y20 / det;
+  G[1][1] = -x20 / det;
+  G[2][0] = -y10 / det;
+  G[2][1] = x10 / det;
+  G[0][0] = -(G[1][0] + G[2][0]);
+  G[0][1] = -(G[1][1] + G[2][1]);
+  double area = 0.5 * det;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K[i][j] = area * (G[i][0] * G[j][0] + G[i][1] * G[j][1]);
+}
+
+// --------------------------------------------------------------------------
+// Clipping and exact integration (R5, R6).
+// --------------------------------------------------------------------------
+
+struct Pt {
+  double x, y;
+};
+
+// Sutherland-Hodgman clipping of a convex polygon by a CCW triangle.
+std::vector<Pt> clip(const std::vector<Pt>& poly0, const Pt* K) {
+  std::vector<Pt> poly = poly0;
+  for (int e = 0; e < 3 && !poly.empty(); ++e) {
+    Pt a = K[e], b = K[(e + 1) % 3];
+    std::vector<Pt> out;
+    size_t n = poly.size();
+    for (size_t i = 0; i < n; ++i) {
+      Pt P = poly[i], Q = poly[(i + 1) % n];
+      double dP = (b.x - a.x) * (P.y - a.y) - (b.y - a.y) * (P.x - a.x);
+      double dQ = (b.x - a.x) * (Q.y - a.y) - (b.y - a.y) * (Q.x - a.x);
+      bool inP = dP >= 0.0, inQ = dQ >= 0.0;
+      if (inP) out.push_back(P);
+      if (inP != inQ) {
+        double t = dP / (dP - dQ);
+        out.push_back(Pt{P.x + t * (Q.x - P.x), P.y + t * (Q.y - P.y)});
+      }
+    }
+    poly.swap(out);
+  }
+  return poly;
+}
+
+// barycentric coordinates of x in triangle T
+void bary(const Pt* T, Pt x, double* lam) {
+  double det = (T[1].x - T[0].x) * (T[2].y - T[0].y) - (T[2].x - T[0].x) * (T[1].y - T[0].y);
+  lam[1] = ((x.x - T[0].x) * (T[2].y - T[0].y) - (T[2].x - T[0].x) * (x.y - T[0].y)) / det;
+  lam[2] = ((T[1].x - T[0].x) * (x.y - T[0].y) - (x.x - T[0].x) * (T[1].y - T[0].y)) / det;
+  lam[0] = 1.0 - lam[1] - lam[2];
+}
+
+double poly_area(const std::vector<Pt>& p) {
+  double a = 0.0;
+  for (size_t i = 1; i + 1 < p.size(); ++i)
+    a += 0.5 * ((p[i].x - p[0].x) * (p[i + 1].y - p[0].y) - (p[i + 1].x - p[0].x) * (p[i].y - p[0].y));
+  return a;
+}
+
+// Leaf boxes of the closed tree whose closed extent meets [lo, hi].
+void leaves_overlapping(const Oracle& o, double lox, double loy, double hix, double hiy,
+                        std::vector<std::array<uint64_t, 3>>& out) {
+  std::vector<std::array<uint64_t, 3>> stack;  // (depth, ix, iy)
+  stack.push_back({0, 0, 0});
+  while (!stack.empty()) {
+    auto b = stack.back();
+    stack.pop_back();
+    int depth = (int)b[0];
+    double w = std::ldexp(o.L, -depth);
+    double x0 = o.amin[0] + (double)b[1] * w, y0 = o.amin[1] + (double)b[2] * w;
+    if (x0 > hix || y0 > hiy || x0 + w < lox || y0 + w < loy) continue;
+    uint64_t q[2] = {b[1], b[2]};
+    uint8_t sp = 0;
+    if (!box_exists(o, depth, q, &sp)) continue;
+    if (!sp) {
+      out.push_back(b);
+      continue;
+    }
+    for (int ch = 0; ch < 4; ++ch) stack.push_back({(uint64_t)depth + 1, 2 * b[1] + (ch & 1), 2 * b[2] + (ch >> 1)});
+  }
+}
+
+void build_aux(Oracle& o) {
+  const int J = o.J;
+  o.lv.assign(J + 1, Level());
+  for (int l = 0; l <= J; ++l) {
+    Level& L = o.lv[l];
+    level_triangles(o, l, L.tri);
+    for (auto& t : L.tri)
+      for (int k = 0; k < 3; ++k) L.allkey.push_back(t[k]);
+    std::sort(L.allkey.begin(), L.allkey.end());
+    L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
+    for (auto k : L.allkey)
+      if (!on_boundary(o, k)) L.key.push_back(k);
+  }
+  // coarsest level used: the finest level with at most coarse_max free nodes
+  o.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if ((int64_t)o.lv[l].key.size() <= o.prm.coarse_max) o.c = l;
+
+  // Finest auxiliary coefficient (R6) by exact clipping of every fine element
+  // against the level-J triangles of the leaf boxes it meets.
+  Level& LJ = o.lv[J];
+  std::map<std::array<uint64_t, 3>, int64_t> tri_index;
+  for (size_t t = 0; t < LJ.tri.size(); ++t) tri_index[LJ.tri[t]] = (int64_t)t;
+  std::vector<double> num(LJ.tri.size(), 0.0);
+  std::vector<std::array<uint64_t, 3>> leaves, ktri;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    Pt T[3];
+    for (int k = 0; k < 3; ++k) T[k] = Pt{o.X[(int64_t)o.E[3 * e + k] * 2], o.X[(int64_t)o.E[3 * e + k] * 2 + 1]};
+    double lox = std::min({T[0].x, T[1].x, T[2].x}), hix = std::max({T[0].x, T[1].x, T[2].x});
+    double loy = std::min({T[0].y, T[1].y, T[2].y}), hiy = std::max({T[0].y, T[1].y, T[2].y});
+    leaves.clear();
+    leaves_overlapping(o, lox, loy, hix, hiy, leaves);
+    double a = o.coeff.empty() ? 1.0 : o.coeff[e];
+    std::vector<Pt> poly(T, T + 3);
+    for (auto& b : leaves) {
+      ktri.clear();
+      box_triangles(o, (int)b[0], b[1], b[2], J, ktri);
+      for (auto& kt : ktri) {
+        Pt K[3];
+        for (int k = 0; k < 3; ++k) {
+          double p[2];
+          physical(o, kt[k], p);
+          K[k] = Pt{p[0], p[1]};
+        }
+        auto cp = clip(poly, K);
+        if (cp.size() < 3) continue;
+        num[tri_index.at(kt)] += a * poly_area(cp);
+      }
+    }
+  }
+  o.finest_coef.resize(LJ.tri.size());
+  for (size_t t = 0; t < LJ.tri.size(); ++t) {
+    double p0[2], p1[2], p2[2];
+    physical(o, LJ.tri[t][0], p0);
+    physical(o, LJ.tri[t][1], p1);
+    physical(o, LJ.tri[t][2], p2);
+    double area = 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]));
+    o.finest_coef[t] = num[t] / area;
+  }
+
+  // A_J: P1 stiffness of T_J with the averaged coefficient (Sec. 4.1: the
+  // auxiliary operator comes from the bilinear form).
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(LJ.key.size());
+    for (size_t t = 0; t < LJ.tri.size(); ++t) {
+      double p[3][2];
+      int32_t id[3];
+      for (int k = 0; k < 3; ++k) {
+        physical(o, LJ.tri[t][k], p[k]);
+        id[k] = find_index(LJ.key, LJ.tri[t][k]);
+      }
+      double K[3][3];
+      tri_stiffness(p[0], p[1], p[2], K);
+      for (int i = 0; i < 3; ++i)
+        if (id[i] >= 0)
+          for (int j = 0; j < 3; ++j)
+            if (id[j] >= 0) rows[id[i]].push_back({id[j], o.finest_coef[t] * K[i][j]});
+    }
+    LJ.A = csr_from_rows(LJ.key.size(), LJ.key.size(), rows);
+  }
+
+  // Interpolation I_l: nodal interpolation of the level l-1 P1 function at
+  // the level-l nodes (nested spaces, Sec. 3.3).
+  for (int l = std::max(1, o.c + 1); l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    Level& Lc = o.lv[l - 1];
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(Lf.key.size());
+    for (size_t k = 0; k < Lf.key.size(); ++k) {
+      int32_t j = find_index(Lc.key, Lf.key[k]);
+      if (j >= 0) {
+        rows[k].push_back({j, 1.0});
+        continue;
+      }
+      uint64_t x, y;
+      node_xy(Lf.key[k], x, y);
+      // descend the truncated tree to the level-(l-1) leaf box containing the node
+      int depth = 0;
+      uint64_t bx = 0, by = 0;
+      for (;;) {
+        uint64_t q[2] = {bx, by};
+        uint8_t sp = 0;
+        box_exists(o, depth, q, &sp);
+        if (depth == l - 1 || !sp) break;
+        uint64_t half = 1ULL << (o.D - depth - 1);
+        uint64_t cx = (x - bx * (2 * half)) >= half ? 1 : 0;
+        uint64_t cy = (y - by * (2 * half)) >= half ? 1 : 0;
+        // points on the far edge of the root box stay in the last child
+        if (x == (bx + 1) * 2 * half) cx = 1;
+        if (y == (by + 1) * 2 * half) cy = 1;
+        bx = 2 * bx + cx;
+        by = 2 * by + cy;
+        ++depth;
+      }
+      std::vector<std::array<uint64_t, 3>> ktri;
+      box_triangles(o, depth, bx, by, l - 1, ktri);
+      bool found = false;
+      for (auto& kt : ktri) {
+        i128 P[3][2];
+        for (int v = 0; v < 3; ++v) {
+          uint64_t vx, vy;
+          node_xy(kt[v], vx, vy);
+          P[v][0] = (i128)vx;
+          P[v][1] = (i128)vy;
+        }
+        i128 det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+        i128 n1 = ((i128)x - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * ((i128)y - P[0][1]);
+        i128 n2 = (P[1][0] - P[0][0]) * ((i128)y - P[0][1]) - ((i128)x - P[0][0]) * (P[1][1] - P[0][1]);
+        i128 n0 = det - n1 - n2;
+        if (n0 < 0 || n1 < 0 || n2 < 0) continue;
+        i128 nn[3] = {n0, n1, n2};
+        for (int v = 0; v < 3; ++v) {
+          if (nn[v] == 0) continue;
+          int32_t jj = find_index(Lc.key, kt[v]);
+          if (jj < 0) continue;  // Dirichlet vertex: value 0
+          rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
+        }
+        found = true;
+        break;
+      }
+      if (!found) {
+        o.err = "oracle: interpolation point not located";
+        return;
+      }
+    }
+    Lf.I = csr_from_rows(Lf.key.size(), Lc.key.size(), rows);
+  }
+
+  // Galerkin coarse operators A_{l-1} = I_l^T A_l I_l (Sec. 2.3: A_i is the
+  // restriction of A to V_i).
+  for (int l = J; l > o.c; --l) {
+    CSR It = transpose(o.lv[l].I);
+    CSR AI = matmul(o.lv[l].A, o.lv[l].I);
+    o.lv[l - 1].A = matmul(It, AI);
+  }
+
+  // Smoothing sets (R7): free vertices of level-l triangles that are not
+  // level-(l-1) triangles, i.e. new nodes and nodes whose hat changed.
+  for (int l = o.c + 1; l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    std::vector<int32_t> set;
+    if (o.prm.smoothing == 1) {
+      for (size_t k = 0; k < Lf.key.size(); ++k) set.push_back((int32_t)k);
+    } else {
+      std::set<std::array<uint64_t, 3>> prev;
+      for (auto t : o.lv[l - 1].tri) {
+        std::sort(t.begin(), t.end());
+        prev.insert(t);
+      }
+      std::vector<uint8_t> mark(Lf.key.size(), 0);
+      for (auto t : Lf.tri) {
+        auto ts = t;
+        std::sort(ts.begin(), ts.end());
+        if (prev.count(ts)) continue;
+        for (int v = 0; v < 3; ++v) {
+          int32_t id = find_index(Lf.key, t[v]);
+          if (id >= 0) mark[id] = 1;
+        }
+      }
+      for (size_t k = 0; k < Lf.key.size(); ++k)
+        if (mark[k]) set.push_back((int32_t)k);
+    }
+    Lf.smooth = set;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Scott-Zhang transfer (Sec. 4.1, R5): P_ik = int_{sigma_i} psi_i phi^J_k.
+// --------------------------------------------------------------------------
+
+void build_transfer(Oracle& o) {
+  const Level& LJ = o.lv[o.J];
+  const int64_t n = o.vertex_of_free.size();
+  std::vector<int32_t> sigma(o.nv, -1);
+  for (int64_t e = 0; e < o.ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      int32_t v = o.E[3 * e + k];
+      if (sigma[v] < 0) sigma[v] = (int32_t)e;  // elements visited in index order
+    }
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(n), rows_full(n);
+  std::vector<std::array<uint64_t, 3>> leaves, ktri;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t v = o.vertex_of_free[i];
+    int32_t e = sigma[v];
+    Pt T[3];
+    int loc = -1;
+    for (int k = 0; k < 3; ++k) {
+      int32_t vk = o.E[3 * (int64_t)e + k];
+      T[k] = Pt{o.X[(int64_t)vk * 2], o.X[(int64_t)vk * 2 + 1]};
+      if (vk == v) loc = k;
+    }
+    double area = 0.5 * ((T[1].x - T[0].x) * (T[2].y - T[0].y) - (T[2].x - T[0].x) * (T[1].y - T[0].y));
+    double lox = std::min({T[0].x, T[1].x, T[2].x}), hix = std::max({T[0].x, T[1].x, T[2].x});
+    double loy = std::min({T[0].y, T[1].y, T[2].y}), hiy = std::max({T[0].y, T[1].y, T[2].y});
+    leaves.clear();
+    leaves_overlapping(o, lox, loy, hix, hiy, leaves);
+    std::vector<Pt> poly(T, T + 3);
+    for (auto& b : leaves) {
+      ktri.clear();
+      box_triangles(o, (int)b[0], b[1], b[2], o.J, ktri);
+      for (auto& kt : ktri) {
+        Pt K[3];
+        for (int k = 0; k < 3; ++k) {
+          double p[2];
+          physical(o, kt[k], p);
+          K[k] = Pt{p[0], p[1]};
+        }
+        auto cp = clip(poly, K);
+        if (cp.size() < 3) continue;
+        for (size_t s = 1; s + 1 < cp.size(); ++s) {
+          Pt q[3] = {cp[0], cp[s], cp[s + 1]};
+          double ta = 0.5 * ((q[1].x - q[0].x) * (q[2].y - q[0].y) - (q[2].x - q[0].x) * (q[1].y - q[0].y));
+          // edge-midpoint rule: exact for the quadratic psi_i * phi_k
+          double acc[3] = {0, 0, 0};
+          for (int m = 0; m < 3; ++m) {
+            Pt mid{0.5 * (q[m].x + q[(m + 1) % 3].x), 0.5 * (q[m].y + q[(m + 1) % 3].y)};
+            double ls[3], lk[3];
+            bary(T, mid, ls);
+            bary(K, mid, lk);
+            double psi = (12.0 * ls[loc] - 3.0) / area;
+            for (int k = 0; k < 3; ++k) acc[k] += psi * lk[k];
+          }
+          for (int k = 0; k < 3; ++k) {
+            double val = ta * acc[k] / 3.0;
+            int32_t jf = find_index(LJ.allkey, kt[k]);
+            rows_full[i].push_back({jf, val});
+            int32_t jj = find_index(LJ.key, kt[k]);
+            if (jj >= 0) rows[i].push_back({jj, val});
+          }
+        }
+      }
+    }
+  }
+  o.P = csr_from_rows(n, LJ.key.size(), rows);
+  o.Pfull = csr_from_rows(n, LJ.allkey.size(), rows_full);
+}
+
+// --------------------------------------------------------------------------
+// Colouring (R10): Jones-Plassmann with splitmix64 priorities.
+// --------------------------------------------------------------------------
+
+void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<uint64_t>& prio_key,
+               std::vector<int32_t>& colour, int mode) {
+  colour.assign(A.nr, -1);
+  std::vector<uint8_t> in(A.nr, 0);
+  for (auto v : set) in[v] = 1;
+  if (mode == 1) {  // one colour per node, in index order: lexicographic GS
+    std::vector<int32_t> s = set;
+    std::sort(s.begin(), s.end());
+    for (size_t k = 0; k < s.size(); ++k) colour[s[k]] = (int32_t)k;
+    return;
+  }
+  auto prio = [&](int32_t v) { return std::make_pair(splitmix64(prio_key[v]), prio_key[v]); };
+  std::vector<int32_t> todo = set;
+  while (!todo.empty()) {
+    std::vector<int32_t> winners, rest;
+    for (auto v : todo) {
+      bool win = true;
+      auto pv = prio(v);
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        int32_t w = A.col[p];
+        if (w == v || !in[w] || colour[w] >= 0) continue;
+        if (prio(w) > pv) {
+          win = false;
+          break;
+        }
+      }
+      (win ? winners : rest).push_back(v);
+    }
+    for (auto v : winners) {
+      std::vector<uint8_t> used;
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        int32_t w = A.col[p];
+        if (w == v || !in[w] || colour[w] < 0) continue;
+        if ((size_t)colour[w] >= used.size()) used.resize(colour[w] + 1, 0);
+        used[colour[w]] = 1;
+      }
+      int32_t cc = 0;
+      while ((size_t)cc < used.size() && used[cc]) ++cc;
+      colour[v] = cc;
+    }
+    todo.swap(rest);
+  }
+}
+
+void order_by_colour(const std::vector<int32_t>& set, const std::vector<int32_t>& colour,
+                     std::vector<int32_t>& smooth, std::vector<int32_t>& cstart) {
+  smooth = set;
+  std::stable_sort(smooth.begin(), smooth.end(), [&](int32_t a, int32_t b) {
+    return colour[a] != colour[b] ? colour[a] < colour[b] : a < b;
+  });
+  cstart.clear();
+  for (size_t k = 0; k < smooth.size(); ++k)
+    if (k == 0 || colour[smooth[k]] != colour[smooth[k - 1]]) cstart.push_back((int32_t)k);
+  cstart.push_back((int32_t)smooth.size());
+}
+
+void build_colourings(Oracle& o) {
+  std::vector<int32_t> all(o.A.nr);
+  std::vector<uint64_t> pk(o.A.nr);
+  for (int64_t i = 0; i < o.A.nr; ++i) {
+    all[i] = (int32_t)i;
+    pk[i] = (uint64_t)o.vertex_of_free[i];
+  }
+  jp_colour(o.A, all, pk, o.fine_colour, o.prm.colouring);
+  order_by_colour(all, o.fine_colour, o.fine_smooth, o.fine_cstart);
+  for (int l = o.c + 1; l <= o.J; ++l) {
+    Level& L = o.lv[l];
+    jp_colour(L.A, L.smooth, L.key, L.colour, o.prm.colouring);
+    std::vector<int32_t> set = L.smooth;
+    order_by_colour(set, L.colour, L.smooth, L.cstart);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Coarsest level: B_0 = A_0^{-1} by dense Cholesky (Algorithm 2).
+// --------------------------------------------------------------------------
+
+bool cholesky(std::vector<double>& M, int64_t n) {
+  for (int64_t j = 0; j < n; ++j) {
+    double s = M[j * n + j];
+    for (int64_t k = 0; k < j; ++k) s -= M[j * n + k] * M[j * n + k];
+    if (!(s > 0.0)) return false;
+    double d = std::sqrt(s);
+    M[j * n + j] = d;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = M[i * n + j];
+      for (int64_t k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
+      M[i * n + j] = t / d;
+    }
+    for (int64_t i = 0; i < j; ++i) M[i * n + j] = 0.0;
+  }
+  return true;
+}
+
+void chol_solve(const std::vector<double>& Lm, int64_t n, const double* b, double* x) {
+  std::vector<double> y(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int64_t k = 0; k < i; ++k) s -= Lm[i * n + k] * y[k];
+    y[i] = s / Lm[i * n + i];
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int64_t k = i + 1; k < n; ++k) s -= Lm[k * n + i] * x[k];
+    x[i] = s / Lm[i * n + i];
+  }
+}
+
+void build_coarse(Oracle& o) {
+  const CSR& Ac = o.lv[o.c].A;
+  int64_t n = Ac.nr;
+  o.nc_dense = n;
+  o.chol.assign(n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = Ac.ptr[i]; p < Ac.ptr[i + 1]; ++p) o.chol[i * n + Ac.col[p]] = Ac.val[p];
+  if (!cholesky(o.chol, n)) o.err = "oracle: coarse matrix not positive definite";
+}
+
+// --------------------------------------------------------------------------
+// Smoother, V-cycle (Algorithm 2) and the multiplicative preconditioner
+// (Algorithm 1, R8).
+// --------------------------------------------------------------------------
+
+// One Gauss-Seidel sweep over `smooth` in colour order (forward) or reverse
+// colour order (backward): u_i += (f_i - (A u)_i) / a_ii.  Nodes of one
+// colour are not coupled, so their order inside the class is immaterial.
+void gs_sweep(const CSR& A, const std::vector<int32_t>& smooth, const std::vector<int32_t>& cstart,
+              const double* f, double* u, bool forward) {
+  int ncol = (int)cstart.size() - 1;
+  for (int cc = 0; cc < ncol; ++cc) {
+    int col = forward ? cc : ncol - 1 - cc;
+    for (int32_t k = cstart[col]; k < cstart[col + 1]; ++k) {
+      int32_t i = smooth[k];
+      double s = f[i], dia = 0.0;
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        s -= A.val[p] * u[A.col[p]];
+        if (A.col[p] == i) dia = A.val[p];
+      }
+      u[i] += s / dia;
+    }
+  }
+}
+
+void vcycle(const Oracle& o, int l, const std::vector<double>& f, std::vector<double>& u) {
+  const Level& L = o.lv[l];
+  u.assign(L.key.size(), 0.0);
+  if (l == o.c) {
+    if (o.nc_dense > 0) chol_solve(o.chol, o.nc_dense, f.data(), u.data());
+    return;
+  }
+  for (int s = 0; s < o.prm.nu_pre; ++s) gs_sweep(L.A, L.smooth, L.cstart, f.data(), u.data(), true);
+  std::vector<double> Au(L.key.size()), r(L.key.size());
+  spmv(L.A, u.data(), Au.data());
+  for (size_t i = 0; i < r.size(); ++i) r[i] = f[i] - Au[i];
+  const CSR& I = L.I;
+  std::vector<double> fc(o.lv[l - 1].key.size(), 0.0);
+  for (int64_t i = 0; i < I.nr; ++i)
+    for (int64_t p = I.ptr[i]; p < I.ptr[i + 1]; ++p) fc[I.col[p]] += I.val[p] * r[i];
+  std::vector<double> ec;
+  vcycle(o, l - 1, fc, ec);
+  for (int64_t i = 0; i < I.nr; ++i)
+    for (int64_t p = I.ptr[i]; p < I.ptr[i + 1]; ++p) u[i] += I.val[p] * ec[I.col[p]];
+  for (int s = 0; s < o.prm.nu_post; ++s) gs_sweep(L.A, L.smooth, L.cstart, f.data(), u.data(), false);
+}
+
+void precond(const Oracle& o, const double* r, double* z) {
+  const int64_t n = o.A.nr;
+  std::vector<double> u(n, 0.0), Au(n), rho(n);
+  // (1) u1 = S r : one forward multicolour sweep from zero
+  gs_sweep(o.A, o.fine_smooth, o.fine_cstart, r, u.data(), true);
+  // (2) u2 = u1 + P Btilde P^T (r - A u1)
+  spmv(o.A, u.data(), Au.data());
+  for (int64_t i = 0; i < n; ++i) rho[i] = r[i] - Au[i];
+  const int64_t nJ = o.lv[o.J].key.size();
+  if (nJ > 0) {
+    std::vector<double> fJ(nJ, 0.0), eJ;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = o.P.ptr[i]; p < o.P.ptr[i + 1]; ++p) fJ[o.P.col[p]] += o.P.val[p] * rho[i];
+    vcycle(o, o.J, fJ, eJ);
+    for (int64_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int64_t p = o.P.ptr[i]; p < o.P.ptr[i + 1]; ++p) s += o.P.val[p] * eJ[o.P.col[p]];
+      u[i] += s;
+    }
+  }
+  // (3) u3 = u2 + S^T (r - A u2) : one backward multicolour sweep
+  gs_sweep(o.A, o.fine_smooth, o.fine_cstart, r, u.data(), false);
+  for (int64_t i = 0; i < n; ++i) z[i] = u[i];
+}
+
+// PCG with the flexible beta (R9); returns 0 converged, 1 not converged,
+// -4 breakdown.
+int pcg(const Oracle& o, const double* b, double* u, double rtol, int* iters, double* hist) {
+  const int64_t n = o.A.nr;
+  std::vector<double> bb(b, b + n), x(u, u + n), r(n), z(n), p(n), q(n), rold(n);
+  spmv(o.A, x.data(), q.data());
+  for (int64_t i = 0; i < n; ++i) r[i] = bb[i] - q[i];
+  double nb = std::sqrt(dot(bb, bb));
+  double nr = std::sqrt(dot(r, r));
+  hist[0] = nr;
+  *iters = 0;
+  if (nr <= rtol * nb) {
+    for (int64_t i = 0; i < n; ++i) u[i] = x[i];
+    return 0;
+  }
+  precond(o, r.data(), z.data());
+  p = z;
+  double rz = dot(r, z);
+  int status = 1;
+  for (int k = 0; k < o.prm.max_iter; ++k) {
+    spmv(o.A, p.data(), q.data());
+    double pq = dot(p, q);
+    if (!(pq > 0.0) || !(rz > 0.0)) {
+      status = -4;
+      break;
+    }
+    double alpha = rz / pq;
+    rold = r;
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    nr = std::sqrt(dot(r, r));
+    hist[k + 1] = nr;
+    *iters = k + 1;
+    if (nr <= rtol * nb) {
+      status = 0;
+      break;
+    }
+    precond(o, r.data(), z.data());
+    double num = 0.0;
+    for (int64_t i = 0; i < n; ++i) num += z[i] * (r[i] - rold[i]);
+    double beta = num / rz;
+    rz = dot(r, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+  }
+  for (int64_t i = 0; i < n; ++i) u[i] = x[i];
+  return status;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C interface (ctypes)
+// ==========================================================================
+
+extern "C" {
+
+void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t* E, const uint8_t* bflag,
+                 const double* coeff, const int32_t* params, char* err, int errlen) {
+  Oracle* o = new Oracle();
+  o->dim = dim;
+  o->nv = nv;
+  o->ne = ne;
+  o->X.assign(X, X + nv * dim);
+  o->E.assign(E, E + ne * (dim + 1));
+  o->bflag.assign(bflag, bflag + nv);
+  if (coeff) o->coeff.assign(coeff, coeff + ne);
+  if (params) {
+    o->prm.n_min = params[0];
+    o->prm.nu_pre = params[1];
+    o->prm.nu_post = params[2];
+    o->prm.coarse_max = params[3];
+    o->prm.smoothing = params[4];
+    o->prm.max_iter = params[5];
+    o->prm.colouring = params[6];
+    o->prm.stage = params[7];
+  }
+  assemble_fine(*o);
+  build_tree(*o);
+  if (o->prm.stage >= 1) build_closure(*o);
+  if (o->prm.stage >= 2) {
+    if (dim != 2) {
+      o->err = "oracle: auxiliary hierarchy is built for 2D meshes only";
+    } else {
+      build_aux(*o);
+      if (o->err.empty()) build_transfer(*o);
+      if (o->err.empty()) build_colourings(*o);
+      if (o->err.empty()) build_coarse(*o);
+    }
+  }
+  if (!o->err.empty()) {
+    if (err) snprintf(err, errlen, "%s", o->err.c_str());
+    delete o;
+    return nullptr;
+  }
+  return o;
+}
+
+void orc_destroy(void* h) { delete (Oracle*)h; }
+
+// Integer information.  `what`: nfree, J, c, D, ntree_levels, nseg(l),
+// nlevel(l) [free nodes], nall(l), ntri(l), nnzA(l) [l=-1: fine A], nI(l),
+// nsmooth(l), ncolours(l) [l=-1 fine], nP, nPfull, nbox(l).
+int64_t orc_info(void* h, const char* what, int l) {
+  Oracle& o = *(Oracle*)h;
+  std::string w(what);
+  if (w == "nfree") return o.A.nr;
+  if (w == "J") return o.J;
+  if (w == "c") return o.c;
+  if (w == "D") return o.D;
+  if (w == "ntree_levels") return (int64_t)o.tree.size();
+  if (w == "nseg") return (int64_t)o.tree.at(l).size();
+  if (w == "nbox_levels") return (int64_t)o.boxes.size();
+  if (w == "nbox") return (int64_t)o.boxes.at(l).size();
+  if (w == "nlevel") return (int64_t)o.lv.at(l).key.size();
+  if (w == "nall") return (int64_t)o.lv.at(l).allkey.size();
+  if (w == "ntri") return (int64_t)o.lv.at(l).tri.size();
+  if (w == "nnzA") return l < 0 ? (int64_t)o.A.col.size() : (int64_t)o.lv.at(l).A.col.size();
+  if (w == "nI") return (int64_t)o.lv.at(l).I.col.size();
+  if (w == "nsmooth") return l < 0 ? (int64_t)o.fine_smooth.size() : (int64_t)o.lv.at(l).smooth.size();
+  if (w == "ncolours") return l < 0 ? (int64_t)o.fine_cstart.size() - 1 : (int64_t)o.lv.at(l).cstart.size() - 1;
+  if (w == "nP") return (int64_t)o.P.col.size();
+  if (w == "nPfull") return (int64_t)o.Pfull.col.size();
+  return -1;
+}
+
+static void put_csr(const CSR& M, void* out, int part) {
+  if (part == 0) memcpy(out, M.ptr.data(), M.ptr.size() * 8);
+  if (part == 1) memcpy(out, M.col.data(), M.col.size() * 4);
+  if (part == 2) memcpy(out, M.val.data(), M.val.size() * 8);
+}
+
+// Array export; the caller sizes `out` from orc_info.
+int orc_get(void* h, const char* what, int l, void* out) {
+  Oracle& o = *(Oracle*)h;
+  std::string w(what);
+  if (w == "keys") { memcpy(out, o.keys.data(), o.keys.size() * 8); return 0; }
+  if (w == "perm") { memcpy(out, o.perm.data(), o.perm.size() * 4); return 0; }
+  if (w == "root") { double* d = (double*)out; d[0] = o.amin[0]; d[1] = o.amin[1]; d[2] = o.dim == 3 ? o.amin[2] : 0; d[3] = o.L; return 0; }
+  if (w == "seg") {  // int64 [nseg, 4]: prefix, begin, end, split
+    int64_t* d = (int64_t*)out;
+    for (size_t k = 0; k < o.tree.at(l).size(); ++k) {
+      auto& s = o.tree[l][k];
+      d[4 * k] = (int64_t)s.prefix; d[4 * k + 1] = s.begin; d[4 * k + 2] = s.end; d[4 * k + 3] = s.split;
+    }
+    return 0;
+  }
+  if (w == "box") {  // uint64 [nbox, 2]: packed coords, split; sorted
+    std::vector<std::pair<uint64_t, uint8_t>> bx(o.boxes.at(l).begin(), o.boxes.at(l).end());
+    std::sort(bx.begin(), bx.end());
+    uint64_t* d = (uint64_t*)out;
+    for (size_t k = 0; k < bx.size(); ++k) { d[2 * k] = bx[k].first; d[2 * k + 1] = bx[k].second; }
+    return 0;
+  }
+  if (w == "level_key") { memcpy(out, o.lv.at(l).key.data(), o.lv[l].key.size() * 8); return 0; }
+  if (w == "level_allkey") { memcpy(out, o.lv.at(l).allkey.data(), o.lv[l].allkey.size() * 8); return 0; }
+  if (w == "level_tri") { memcpy(out, o.lv.at(l).tri.data(), o.lv[l].tri.size() * 24); return 0; }
+  if (w == "finest_coef") { memcpy(out, o.finest_coef.data(), o.finest_coef.size() * 8); return 0; }
+  if (w == "smooth") {
+    if (l < 0) memcpy(out, o.fine_smooth.data(), o.fine_smooth.size() * 4);
+    else memcpy(out, o.lv.at(l).smooth.data(), o.lv[l].smooth.size() * 4);
+    return 0;
+  }
+  if (w == "cstart") {
+    if (l < 0) memcpy(out, o.fine_cstart.data(), o.fine_cstart.size() * 4);
+    else memcpy(out, o.lv.at(l).cstart.data(), o.lv[l].cstart.size() * 4);
+    return 0;
+  }
+  if (w == "colour") {
+    if (l < 0) memcpy(out, o.fine_colour.data(), o.fine_colour.size() * 4);
+    else memcpy(out, o.lv.at(l).colour.data(), o.lv[l].colour.size() * 4);
+    return 0;
+  }
+  if (w == "vertex_of_free") { memcpy(out, o.vertex_of_free.data(), o.vertex_of_free.size() * 4); return 0; }
+  const CSR* M = nullptr;
+  std::string base;
+  if (w.rfind("A_", 0) == 0) { M = l < 0 ? &o.A : &o.lv.at(l).A; base = w.substr(2); }
+  else if (w.rfind("I_", 0) == 0) { M = &o.lv.at(l).I; base = w.substr(2); }
+  else if (w.rfind("Pfull_", 0) == 0) { M = &o.Pfull; base = w.substr(6); }
+  else if (w.rfind("P_", 0) == 0) { M = &o.P; base = w.substr(2); }
+  if (M) {
+    put_csr(*M, out, base == "ptr" ? 0 : base == "col" ? 1 : 2);
+    return 0;
+  }
+  return -1;
+}
+
+void orc_mass_apply(void* h, const double* f, double* b) { mass_apply(*(Oracle*)h, f, b); }
+
+void orc_spmv(void* h, int l, const double* x, double* y) {
+  Oracle& o = *(Oracle*)h;
+  spmv(l < 0 ? o.A : o.lv.at(l).A, x, y);
+}
+
+void orc_precond(void* h, const double* r, double* z) { precond(*(Oracle*)h, r, z); }
+
+void orc_vcycle(void* h, const double* f, double* e) {
+  Oracle& o = *(Oracle*)h;
+  std::vector<double> fv(f, f + o.lv[o.J].key.size()), ev;
+  vcycle(o, o.J, fv, ev);
+  std::copy(ev.begin(), ev.end(), e);
+}
+
+void orc_gs_sweep(void* h, const double* f, double* u, int forward) {
+  Oracle& o = *(Oracle*)h;
+  gs_sweep(o.A, o.fine_smooth, o.fine_cstart, f, u, forward != 0);
+}
+
+int orc_solve(void* h, const double* b, double* u, double rtol, int* iters, double* hist) {
+  return pcg(*(Oracle*)h, b, u, rtol, iters, hist);
+}
+
+// dL/da_e = -lambda_e^T K_e^(1) u_e, with u, lambda given on free nodes
+// (zero on Dirichlet vertices) and K_e^(1) the element stiffness for a = 1.
+void orc_elem_grad(void* h, const double* u, const double* lam, double* g) {
+  Oracle& o = *(Oracle*)h;
+  const int d = o.dim, nvert = d + 1;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    double G[4][3], vol;
+    simplex_geometry(o, e, G, vol);
+    double ue[4], le[4];
+    for (int k = 0; k < nvert; ++k) {
+      int32_t f = o.free_of_vertex[o.E[e * nvert + k]];
+      ue[k] = f >= 0 ? u[f] : 0.0;
+      le[k] = f >= 0 ? lam[f] : 0.0;
+    }
+    double s = 0.0;
+    for (int i = 0; i < nvert; ++i)
+      for (int j = 0; j < nvert; ++j) {
+        double gg = 0.0;
+        for (int r = 0; r < d; ++r) gg += G[i][r] * G[j][r];
+        s += le[i] * vol * gg * ue[j];
+      }
+    g[e] = -s;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,500 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these compares the oracle with itself: each check is a closed form,
+an invariant the paper states, a library routine for a special case, or a
+brute-force recomputation by a different characterisation.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle
+from oracle import lattice_xy
+
+D2 = 31
+TOP = 1 << D2
+
+
+def _grid(gen, n, **kw):
+    return gen.grid2d(n, kw.pop("seed", 1), **kw)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2: stiffness and mass
+# --------------------------------------------------------------------------
+
+def test_stiffness_is_five_point_laplacian_on_right_triangles(gen):
+    # Textbook identity: P1 on a uniform grid of SW-NE right triangles gives
+    # the 5-point stencil [4; -1 -1 -1 -1], independent of h.
+    n = 9
+    m = _grid(gen, n, jitter=0.0, random_diag=False)
+    o = oracle.Oracle(m, stage=0)
+    A = o.A().toarray()
+    m1 = n - 2
+    T = sp.diags([-1, 2, -1], [-1, 0, 1], shape=(m1, m1))
+    L5 = (sp.kron(sp.eye(m1), T) + sp.kron(T, sp.eye(m1))).toarray()
+    assert np.abs(A - L5).max() < 1e-13
+
+
+def test_stiffness_annihilates_linears_on_interior_rows(gen):
+    m = _grid(gen, 17, seed=3)
+    o = oracle.Oracle(m, stage=0)
+    A = o.A()
+    vf = o.vertex_of_free()
+    x, y = m.verts[vf, 0], m.verts[vf, 1]
+    # rows whose stencil touches no Dirichlet vertex
+    interior = np.ones(o.nfree, bool)
+    bnd = set(np.nonzero(m.bflag)[0].tolist())
+    for e in m.elems:
+        if any(int(v) in bnd for v in e):
+            for v in e:
+                if m.bflag[v] == 0:
+                    interior[np.searchsorted(vf, v)] = False
+    for g in (np.ones_like(x), x, y, 2.0 - 3.0 * x + 0.5 * y):
+        r = A @ g
+        assert np.abs(r[interior]).max() < 1e-11
+    As = A.toarray()
+    assert np.abs(As - As.T).max() < 1e-14
+    assert np.linalg.eigvalsh(As).min() > 0
+
+
+def test_mass_matrix_integrates_products_exactly(gen):
+    # With every vertex free, 1^T M 1 = |Omega|, 1^T M x = 1/2, y^T M x = 1/4.
+    m = _grid(gen, 9, seed=2)
+    m.bflag[:] = 0
+    o = oracle.Oracle(m, stage=0)
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    assert abs(o.mass_apply(np.ones(m.nv)).sum() - 1.0) < 1e-14
+    assert abs(o.mass_apply(x).sum() - 0.5) < 1e-14
+    assert abs(o.mass_apply(x) @ y - 0.25) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# Sec. 5 / C11: PCG solution
+# --------------------------------------------------------------------------
+
+def test_pcg_matches_dense_cholesky(gen):
+    m = _grid(gen, 12, seed=4)
+    f = gen.nodal_uniform(m, 7)
+    o = oracle.Oracle(m)
+    b = o.mass_apply(f)
+    u, st, it, hist = o.solve(b, rtol=1e-14)
+    ref = np.linalg.solve(o.A().toarray(), b)
+    assert st == 0
+    assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+    assert hist[-1] <= 1e-14 * np.linalg.norm(b)
+
+
+def _l2_error(m, vf, u_free):
+    u = np.zeros(m.nv)
+    u[vf] = u_free
+    err2 = 0.0
+    V = m.verts
+    for k in range(3):
+        a, b = m.elems[:, k], m.elems[:, (k + 1) % 3]
+        mid = 0.5 * (V[a] + V[b])
+        uh = 0.5 * (u[a] + u[b])
+        ue = np.sin(math.pi * mid[:, 0]) * np.sin(math.pi * mid[:, 1])
+        p0, p1, p2 = V[m.elems[:, 0]], V[m.elems[:, 1]], V[m.elems[:, 2]]
+        area = 0.5 * ((p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1]) - (p2[:, 0] - p0[:, 0]) * (p1[:, 1] - p0[:, 1]))
+        err2 += (area / 3.0 * (uh - ue) ** 2).sum()
+    return math.sqrt(err2)
+
+
+def test_manufactured_solution_converges_at_second_order(gen):
+    errs = []
+    for n in (17, 33, 65, 129):
+        m, f = gen.workload_small_poisson(seed=1, nside=n)
+        o = oracle.Oracle(m)
+        u, st, it, _ = o.solve(o.mass_apply(f), rtol=1e-12)
+        assert st == 0
+        errs.append(_l2_error(m, o.vertex_of_free(), u))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(3.3 < r < 4.8 for r in ratios), (errs, ratios)
+
+
+def test_iterations_grow_at_most_logarithmically(gen):
+    # Sec. 4: kappa(BA) <~ log N; Sec. 5: PCG steps flat in N (5 at 4 sizes).
+    its = []
+    for n in (17, 33, 65, 129, 257):
+        m = gen.grid2d(n, 1)
+        o = oracle.Oracle(m)
+        _, st, it, _ = o.solve(o.mass_apply(gen.nodal_uniform(m, 5)), rtol=1e-8)
+        assert st == 0
+        its.append(it)
+    assert its[-1] <= its[0] + 4, its
+    assert max(its) <= 12, its
+
+
+def test_standalone_asmg_rate(gen):
+    # Sec. 5 (Fig. rate_Dirichlet): ASMG as a stationary iteration reduces the
+    # residual by roughly 0.4 per step, level independently.
+    for n in (33, 65):
+        m = gen.grid2d(n, 2)
+        o = oracle.Oracle(m)
+        A = o.A()
+        b = o.mass_apply(gen.nodal_uniform(m, 3))
+        u = np.zeros(o.nfree)
+        rn = [np.linalg.norm(b)]
+        for _ in range(12):
+            u = u + o.precond(b - A @ u)
+            rn.append(np.linalg.norm(b - A @ u))
+        rate = (rn[-1] / rn[4]) ** (1.0 / 8.0)
+        assert rate < 0.5, rate
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.1: cluster tree
+# --------------------------------------------------------------------------
+
+def _check_tree(m, o, n_min=3):
+    levels = o.tree_levels()
+    perm = o.perm()
+    a0, a1, _, L = o.root()
+    bc = m.verts[m.elems].sum(1) / 3.0
+    assert np.array_equal(np.sort(perm), np.arange(m.ne))
+    keys = o.keys()
+    ks = keys[perm]
+    assert (np.diff(ks.astype(np.float64)) >= 0).all()
+    eq = ks[1:] == ks[:-1]
+    assert (perm[1:][eq] > perm[:-1][eq]).all()   # stable: ties by element index
+    for d, segs in enumerate(levels):
+        w = L / 2 ** d
+        for prefix, b, e, split in segs:
+            q = np.zeros(2, np.int64)
+            for j in range(d):
+                q[0] |= ((int(prefix) >> (2 * j)) & 1) << j
+                q[1] |= ((int(prefix) >> (2 * j + 1)) & 1) << j
+            lo = np.array([a0 + q[0] * w, a1 + q[1] * w])
+            pts = bc[perm[b:e]]
+            tol = 1e-12 * L
+            assert (pts >= lo - tol).all() and (pts <= lo + w + tol).all()
+            if split:
+                assert e - b > n_min
+            elif d < 31:
+                assert e - b <= n_min
+        if d + 1 < len(levels):
+            ch = levels[d + 1]
+            nsplit = int(segs[:, 3].sum())
+            assert ch.shape[0] == 4 * nsplit   # all four children, empty ones too
+    return levels
+
+
+def test_cluster_tree_membership_and_counts(gen):
+    for m in (gen.grid2d(17, 3), gen.grid2d(33, 4, graded=True)):
+        o = oracle.Oracle(m, stage=0)
+        _check_tree(m, o)
+
+
+def test_cluster_tree_depth_bound(gen):
+    # Lemma (Sec. 3.1): a split node at depth l satisfies h <= 2^-l sqrt(2) L,
+    # h the minimal barycenter distance, so the depth is <= log2(sqrt2 L/h)+1.
+    from scipy.spatial import cKDTree
+    m = gen.grid2d(33, 5, graded=True)
+    o = oracle.Oracle(m, stage=0)
+    bc = m.verts[m.elems].mean(1)
+    dist, _ = cKDTree(bc).query(bc, k=2)
+    h = dist[:, 1].min()
+    L = o.root()[3]
+    depth = len(o.tree_levels()) - 1
+    assert depth <= math.floor(math.log2(math.sqrt(2) * L / h)) + 1
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.2: closure
+# --------------------------------------------------------------------------
+
+def _unpack(p):
+    return int(p) & 0xFFFFFFFF, int(p) >> 32
+
+
+def _minimal_balanced_by_neighbour_rule(o):
+    """Different characterisation of the edge-2:1 balanced refinement: a tree
+    is balanced iff every split box has all four same-depth edge neighbours.
+    Close the cluster tree's split set under that rule with a worklist."""
+    split = set()
+    for d, segs in enumerate(o.tree_levels()):
+        for prefix, b, e, s in segs:
+            if s:
+                q = [0, 0]
+                for j in range(d):
+                    q[0] |= ((int(prefix) >> (2 * j)) & 1) << j
+                    q[1] |= ((int(prefix) >> (2 * j + 1)) & 1) << j
+                split.add((d, q[0], q[1]))
+    work = list(split)
+    while work:
+        d, x, y = work.pop()
+        # ancestors must be split
+        if d > 0 and (d - 1, x // 2, y // 2) not in split:
+            split.add((d - 1, x // 2, y // 2))
+            work.append((d - 1, x // 2, y // 2))
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            nx, ny = x + dx, y + dy
+            if not (0 <= nx < 2 ** d and 0 <= ny < 2 ** d) or d == 0:
+                continue
+            par = (d - 1, nx // 2, ny // 2)
+            if par not in split:
+                split.add(par)
+                work.append(par)
+    return split
+
+
+def test_closure_is_minimal_balanced_refinement(gen):
+    for m in (gen.grid2d(33, 6, graded=True), gen.grid2d(17, 7, graded=True)):
+        o = oracle.Oracle(m, stage=1)
+        got = set()
+        allboxes = set()
+        for d, arr in enumerate(o.boxes()):
+            for p, s in arr:
+                x, y = _unpack(p)
+                allboxes.add((d, x, y))
+                if s:
+                    got.add((d, x, y))
+        assert got == _minimal_balanced_by_neighbour_rule(o)
+        # every split box has its four children; every non-root box its parent
+        for d, x, y in got:
+            for c in range(4):
+                assert (d + 1, 2 * x + (c & 1), 2 * y + (c >> 1)) in allboxes
+        for d, x, y in allboxes:
+            if d:
+                assert (d - 1, x // 2, y // 2) in got
+
+
+def test_closure_leaves_are_edge_balanced_by_brute_force(gen):
+    m = gen.grid2d(17, 8, graded=True)
+    o = oracle.Oracle(m, stage=1)
+    leaves = []
+    for d, arr in enumerate(o.boxes()):
+        for p, s in arr:
+            if not s:
+                x, y = _unpack(p)
+                w = 1 << (D2 - d)
+                leaves.append((d, x * w, y * w, w))
+    for i, (d1, x1, y1, w1) in enumerate(leaves):
+        for d2, x2, y2, w2 in leaves[i + 1:]:
+            # shared edge of positive length?
+            ox = min(x1 + w1, x2 + w2) - max(x1, x2)
+            oy = min(y1 + w1, y2 + w2) - max(y1, y2)
+            if (ox == 0 and oy > 0) or (oy == 0 and ox > 0):
+                assert abs(d1 - d2) <= 1
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.3: auxiliary triangulations
+# --------------------------------------------------------------------------
+
+def _tri_xy(tri):
+    x, y = lattice_xy(tri.reshape(-1))
+    return x.reshape(-1, 3).astype(object), y.reshape(-1, 3).astype(object)
+
+
+def test_aux_triangulations_conforming_right_isosceles_nested(gen):
+    m = gen.grid2d(17, 9, graded=True)
+    o = oracle.Oracle(m)
+    prev = None
+    for l in range(o.J + 1):
+        tri = o.level_tri(l)
+        X, Y = _tri_xy(tri)
+        area2 = (X[:, 1] - X[:, 0]) * (Y[:, 2] - Y[:, 0]) - (X[:, 2] - X[:, 0]) * (Y[:, 1] - Y[:, 0])
+        assert all(a > 0 for a in area2)                      # CCW
+        assert sum(area2) == 2 * TOP * TOP                    # covers the root box
+        for t in range(tri.shape[0]):                          # right isosceles => min angle 45
+            sides = sorted((X[t, k] - X[t, (k + 1) % 3]) ** 2 + (Y[t, k] - Y[t, (k + 1) % 3]) ** 2 for k in range(3))
+            assert sides[0] == sides[1] and sides[2] == 2 * sides[0]
+        edges = {}
+        for t in range(tri.shape[0]):
+            for k in range(3):
+                e = tuple(sorted((int(tri[t, k]), int(tri[t, (k + 1) % 3]))))
+                edges[e] = edges.get(e, 0) + 1
+        for (a, b), cnt in edges.items():
+            (xa, xb), (ya, yb) = lattice_xy(np.array([a, b], np.uint64))
+            on_bnd = (xa == xb and xa in (0, TOP)) or (ya == yb and ya in (0, TOP))
+            assert cnt == (1 if on_bnd else 2)
+        if prev is not None:
+            # nested: each fine triangle lies in one coarse triangle
+            PX, PY = prev
+            for t in range(tri.shape[0]):
+                ok = False
+                for s in range(PX.shape[0]):
+                    inside = True
+                    for k in range(3):
+                        px, py = X[t, k], Y[t, k]
+                        for e in range(3):
+                            ax, ay, bx, by = PX[s, e], PY[s, e], PX[s, (e + 1) % 3], PY[s, (e + 1) % 3]
+                            if (bx - ax) * (py - ay) - (by - ay) * (px - ax) < 0:
+                                inside = False
+                    if inside:
+                        ok = True
+                        break
+                assert ok
+        prev = (X, Y)
+
+
+def test_interpolation_reproduces_linears(gen):
+    m = gen.grid2d(17, 10, graded=True)
+    o = oracle.Oracle(m, coarse_max=1)
+    for l in range(max(1, o.c + 1), o.J + 1):
+        I = o.I(l)
+        fx, fy = lattice_xy(o.level_keys(l))
+        cx, cy = lattice_xy(o.level_keys(l - 1))
+        fx, fy, cx, cy = (v.astype(np.float64) for v in (fx, fy, cx, cy))
+        rs = np.asarray(I.sum(1)).ravel()
+        full = np.abs(rs - 1.0) < 1e-15
+        assert np.allclose((I @ cx)[full], fx[full], rtol=0, atol=1e-6)
+        assert np.allclose((I @ cy)[full], fy[full], rtol=0, atol=1e-6)
+        assert (I.getnnz(1) <= 2).all()   # new nodes are midpoints of coarse edges
+
+
+def _rediscretise(o, l):
+    tri = o.level_tri(l)
+    keys = o.level_keys(l)
+    a0, a1, _, L = o.root()
+    X, Y = lattice_xy(tri.reshape(-1))
+    X = (a0 + np.ldexp(X.astype(np.float64), -D2) * L).reshape(-1, 3)
+    Y = (a1 + np.ldexp(Y.astype(np.float64), -D2) * L).reshape(-1, 3)
+    n = keys.size
+    rows, cols, vals = [], [], []
+    for t in range(tri.shape[0]):
+        det = (X[t, 1] - X[t, 0]) * (Y[t, 2] - Y[t, 0]) - (X[t, 2] - X[t, 0]) * (Y[t, 1] - Y[t, 0])
+        b = np.array([Y[t, 1] - Y[t, 2], Y[t, 2] - Y[t, 0], Y[t, 0] - Y[t, 1]])
+        c = np.array([X[t, 2] - X[t, 1], X[t, 0] - X[t, 2], X[t, 1] - X[t, 0]])
+        K = (np.outer(b, b) + np.outer(c, c)) / (2.0 * det)
+        idx = np.searchsorted(keys, tri[t])
+        for i in range(3):
+            for j in range(3):
+                if idx[i] < n and keys[idx[i]] == tri[t, i] and idx[j] < n and keys[idx[j]] == tri[t, j]:
+                    rows.append(idx[i]); cols.append(idx[j]); vals.append(K[i, j])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+def test_galerkin_equals_rediscretisation_for_constant_coefficient(gen):
+    m = gen.grid2d(17, 11, graded=True)
+    o = oracle.Oracle(m, coarse_max=1)
+    for l in range(o.c, o.J + 1):
+        G = o.A(l)
+        R = _rediscretise(o, l)
+        assert abs(G - R).max() <= 1e-12 * abs(R).max()
+
+
+def test_uniform_aux_levels_are_five_point(gen):
+    m, _ = gen.workload_small_poisson()
+    o = oracle.Oracle(m, coarse_max=1)
+    for l in range(1, o.J + 1):
+        n1 = 2 ** l - 1
+        assert o.info("nlevel", l) == n1 * n1
+        A = o.A(l).toarray()
+        # canonical (Morton) order -> row-major order
+        x, y = lattice_xy(o.level_keys(l))
+        step = TOP >> l
+        rm = (y // step - 1) * n1 + (x // step - 1)
+        Pm = np.zeros((n1 * n1, n1 * n1))
+        Pm[rm.astype(np.int64), np.arange(n1 * n1)] = 1
+        T = sp.diags([-1, 2, -1], [-1, 0, 1], shape=(n1, n1))
+        L5 = (sp.kron(sp.eye(n1), T) + sp.kron(T, sp.eye(n1))).toarray()
+        assert np.abs(Pm @ A @ Pm.T - L5).max() < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.1: Scott-Zhang transfer
+# --------------------------------------------------------------------------
+
+def test_scott_zhang_reproduces_linears(gen):
+    for m in (gen.grid2d(17, 12), gen.grid2d(17, 13, graded=True)):
+        o = oracle.Oracle(m)
+        Pf = o.P(full=True)
+        a0, a1, _, L = o.root()
+        x, y = lattice_xy(o.level_keys(o.J, all_nodes=True))
+        X = a0 + np.ldexp(x.astype(np.float64), -D2) * L
+        Y = a1 + np.ldexp(y.astype(np.float64), -D2) * L
+        vf = o.vertex_of_free()
+        for c0, gx, gy in ((1.0, 0.0, 0.0), (0.3, 1.5, -2.0)):
+            got = Pf @ (c0 + gx * X + gy * Y)
+            want = c0 + gx * m.verts[vf, 0] + gy * m.verts[vf, 1]
+            assert np.abs(got - want).max() < 1e-11
+
+
+def test_scott_zhang_is_identity_when_aux_grid_equals_fine_grid(gen):
+    # Unjittered SW-NE grid with 2^k cells per side: leaves are the cells, so
+    # T_J is the fine mesh and Pi is the identity (Sec. 4.1: Pi preserves
+    # piecewise linears).
+    m = gen.grid2d(17, 1, jitter=0.0, random_diag=False)
+    o = oracle.Oracle(m)
+    P = o.P().toarray()
+    vf = o.vertex_of_free()
+    x, y = lattice_xy(o.level_keys(o.J))
+    X = np.ldexp(x.astype(np.float64), -D2)
+    Y = np.ldexp(y.astype(np.float64), -D2)
+    # match fine free vertices to aux nodes by position
+    order = np.lexsort((X, Y))
+    fine_order = np.lexsort((m.verts[vf, 0], m.verts[vf, 1]))
+    Pm = P[np.ix_(fine_order, order)]
+    assert np.abs(Pm - np.eye(P.shape[0])).max() < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Algorithms 1 and 2: smoother, V-cycle, preconditioner
+# --------------------------------------------------------------------------
+
+def test_colourings_are_valid_and_smoothing_sets_contain_new_nodes(gen):
+    m = gen.grid2d(33, 14, graded=True)
+    o = oracle.Oracle(m)
+    A = o.A()
+    sm, cs, col = o.smoothing_set(-1)
+    r, c = A.nonzero()
+    off = r != c
+    assert (col[r[off]] != col[c[off]]).all()
+    for l in range(o.c + 1, o.J + 1):
+        Al = o.A(l)
+        sm, cs, col = o.smoothing_set(l)
+        r, c = Al.nonzero()
+        both = (col[r] >= 0) & (col[c] >= 0) & (r != c)
+        assert (col[r[both]] != col[c[both]]).all()
+        new = ~np.isin(o.level_keys(l), o.level_keys(l - 1))
+        assert np.isin(np.nonzero(new)[0], sm).all()
+
+
+def test_sequential_colouring_gives_lexicographic_gauss_seidel(gen):
+    # One colour per row in index order turns the sweep into (D - L)^{-1}.
+    m = gen.grid2d(12, 15)
+    o = oracle.Oracle(m, colouring=1)
+    A = o.A().tocsr()
+    r = np.random.default_rng(0).uniform(-1, 1, o.nfree)
+    u = o.gs_sweep(r, np.zeros(o.nfree), forward=True)
+    ref = spla.spsolve_triangular(sp.tril(A).tocsr(), r, lower=True)
+    assert np.abs(u - ref).max() < 1e-12 * np.abs(ref).max()
+    ub = o.gs_sweep(r, np.zeros(o.nfree), forward=False)
+    refb = spla.spsolve_triangular(sp.triu(A).tocsr(), r, lower=False)
+    assert np.abs(ub - refb).max() < 1e-12 * np.abs(refb).max()
+
+
+def test_single_aux_level_vcycle_is_exact_solve(gen):
+    m = gen.grid2d(17, 16, graded=True)
+    o = oracle.Oracle(m, coarse_max=10 ** 6)
+    assert o.c == o.J
+    AJ = o.A(o.J)
+    f = np.random.default_rng(1).uniform(-1, 1, AJ.shape[0])
+    e = o.vcycle(f)
+    assert np.abs(AJ @ e - f).max() < 1e-10 * np.abs(f).max()
+
+
+def test_preconditioner_is_symmetric_positive_definite(gen):
+    # Algorithm 1 applies S then S^T around a symmetric V-cycle (Alg. 2 with
+    # forward pre- and backward post-smoothing), so B_co is SPD.
+    for m in (gen.grid2d(12, 17), gen.grid2d(13, 18, graded=True)):
+        o = oracle.Oracle(m, coarse_max=20)
+        n = o.nfree
+        B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+        assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+        assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_vcycle_is_symmetric(gen):
+    m = gen.grid2d(17, 19, graded=True)
+    o = oracle.Oracle(m, coarse_max=10)
+    n = o.info("nlevel", o.J)
+    rng = np.random.default_rng(2)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    assert abs(o.vcycle(x) @ y - x @ o.vcycle(y)) <= 1e-12 * abs(x @ o.vcycle(x))
