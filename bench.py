@@ -1,0 +1,291 @@
+"""Benchmark: ASMG-preconditioned CG solve throughput on one GB300.
+
+metric  dofs/s to rel. residual 1e-8 = free dofs / (time of one amg_solve:
+        graph launch -> status back), setup excluded.
+workload (default) 2049^2 jittered random-diagonal grid mapped by x->x^2,
+        y->y^2 (4,190,209 free dofs, 8,388,608 triangles), coefficient 1,
+        nodal f ~ U[-1,1]; the mixed form (FP32 smoother/transfers/V-cycle,
+        FP64 CG) is the headline, the plain FP64 form is timed beside it.
+
+One "step" = one full solve from u0 = 0 to rtol 1e-8.  Inputs are resident in
+HBM before the timed region; the working set (matrices, vectors: several GB)
+is far larger than L2, so no flush is needed between steps.
+With torchrun (N > 1) every rank solves its own replica (the solve does not
+shard); value = all ranks' dofs / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dofs/s to rel. residual 1e-8"
+RTOL = 1e-8
+
+
+def _workload(name: str, seed: int):
+    from paper_1410_2153_gb300 import meshgen
+    if name == "graded2049":
+        return meshgen.workload_graded(seed=seed, nside=2049)
+    if name.startswith("graded"):
+        return meshgen.workload_graded(seed=seed, nside=int(name[6:]))
+    if name == "poisson65":
+        return meshgen.workload_small_poisson(seed=seed)
+    if name.startswith("jitter"):
+        m = meshgen.grid2d(int(name[6:]), seed)
+        return m, meshgen.nodal_uniform(m, seed + 1000)
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(nside: int = 257, seed: int = 1):
+    """The oracle as it stands (single thread) on a bounded sample of the same
+    workload family: the graded mesh at nside^2 vertices, same generator."""
+    import oracle
+    m, f = _workload(f"graded{nside}", seed)
+    o = oracle.Oracle(m)
+    b = o.mass_apply(f)
+    t = time.perf_counter()
+    u, st, it, _ = o.solve(b, rtol=RTOL)
+    dt = time.perf_counter() - t
+    return {"value": o.nfree / dt, "unit": "dofs/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle PCG solve of the graded {nside}x{nside} mesh ({o.nfree} dofs, {it} iterations, "
+                      f"{dt:.2f} s; setup excluded)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nside = 257
+    import oracle
+    m, f = _workload(f"graded{nside}", 1)
+    o = oracle.Oracle(m)
+    b = o.mass_apply(f)
+    for _ in range(args.warmup):
+        o.solve(b, rtol=RTOL)
+    t = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        _, st, it, _ = o.solve(b, rtol=RTOL)
+        its = it
+    dt = time.perf_counter() - t
+    val = o.nfree * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "dofs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"graded{nside}", "nfree": o.nfree, "iterations": its,
+                       "note": "CPU oracle, bounded sample of the graded workload family"},
+            "cpu_baseline": {"value": val, "unit": "dofs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"graded {nside}x{nside} mesh, {o.nfree} dofs"},
+            "e2e": {"value": val, "unit": "dofs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="asmg")
+    ap.add_argument("--workload", default="graded2049")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_1410_2153_gb300 import asmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes_stream = stream.cuda_stream
+
+    mesh, f = _workload(args.workload, 1 + rank)
+    t0 = time.perf_counter()
+    solvers = {}
+    for prec in ([asmg.ASMG_MIXED] if args.no_fp64 else [asmg.ASMG_MIXED, asmg.ASMG_FP64]):
+        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream)
+        solvers[prec] = s
+    t_setup = time.perf_counter() - t0
+    s = solvers[asmg.ASMG_MIXED]
+    n = s.info("nfree")
+    fd = torch.from_numpy(f).to(dev)
+    b = s.mass_apply(fd)
+    u = torch.zeros(mesh.nv, dtype=torch.float64, device=dev)
+    hist = np.zeros(s.params.max_iter + 1)
+
+    def solve_dev(sol):
+        u.zero_()
+        rc, it = asmg.amg_solve(sol.h, b, u, RTOL, hist, sp)
+        return rc, it
+
+    results = {}
+    for prec, sol in solvers.items():
+        for _ in range(args.warmup):
+            solve_dev(sol)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = ClockSampler(local) if prec == asmg.ASMG_MIXED else None
+        if clk:
+            clk.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its = []
+        for _ in range(args.steps):
+            rc, it = solve_dev(sol)
+            its.append(it)
+            assert rc == asmg.ASMG_OK, (rc, asmg.amg_last_error())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        clocks = clk.stop() if clk else None
+        t = torch.tensor([ms], device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        results[prec] = dict(ms=float(t.item()), its=its, clocks=clocks)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    bh = b.cpu().numpy()
+    uh = np.zeros(mesh.nv)
+    for _ in range(2):
+        uh[:] = 0
+        asmg.amg_solve(s.h, bh, uh, RTOL, hist, sp)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        uh[:] = 0
+        asmg.amg_solve(s.h, bh, uh, RTOL, hist, sp)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / args.steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    mix = results[asmg.ASMG_MIXED]
+    ms_step = mix["ms"] / args.steps
+    value = world * n / (ms_step / 1e3)
+    bytes_iter = s.info("bytes_iter")
+    it_mix = int(np.median(mix["its"]))
+    achieved = bytes_iter * it_mix / (ms_step / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": "dofs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: graded jittered random-diagonal grid, x->x^2, y->y^2",
+                   "nfree": n, "triangles": mesh.ne, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
+                   "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
+                   "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
+                   "l2": "working set (several GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * n / e2e_s, "unit": "dofs/s", "h2d_bytes_per_step": 8 * 2 * mesh.nv,
+                "d2h_bytes_per_step": 8 * mesh.nv + 8 * (it_mix + 1)},
+        "gpu_launches": int(s.info("launches_per_iter")) * it_mix * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "scope": f"whole solve: algorithmic bytes per iteration x iterations / solve time; "
+                              f"peak {peak_kind}"},
+        "clocks": mix["clocks"],
+    }
+    if asmg.ASMG_FP64 in results:
+        r64 = results[asmg.ASMG_FP64]
+        ms64 = r64["ms"] / args.steps
+        line["fp64"] = {"value": world * n / (ms64 / 1e3), "ms_per_step": ms64,
+                        "iterations": int(np.median(r64["its"]))}
+        line["mixed_vs_fp64_speedup"] = ms64 / ms_step
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for sol in solvers.values():
+        sol.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * asmg.h -- C ABI of the GB300 (sm_103a) auxiliary-space multigrid solver.
+ *
+ * The library solves the P1 finite-element system A u = b of the problem
+ * "find u with a(u, v) = <f, v> for all v" (Sec. 2, eq. bilinearform) by
+ * conjugate gradients preconditioned with the multiplicative auxiliary-space
+ * preconditioner of Algorithm 1: a Gauss-Seidel smoother on the given grid
+ * plus a geometric V-cycle (Algorithm 2) on the nested auxiliary grids built
+ * from the cluster tree of element barycenters (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - Return value: ASMG_OK (0) on success, > 0 for a warning, < 0 for an
+ *     error.  On error, amg_last_error() returns a message for the calling
+ *     thread; no output is partially written unless stated.
+ *   - Arrays may be host or device (CUDA) pointers unless stated; the
+ *     library detects which with cudaPointerGetAttributes and stages host
+ *     arrays through device memory.  Arrays are caller-owned and need only
+ *     stay valid for the duration of the call.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue their device work on it and synchronise it before returning.
+ *   - Indices are 0-based.  Vertex arrays are indexed by vertex number.
+ *   - The handle owns all device memory it allocates; amg_destroy frees it.
+ *     A handle may be used from one host thread at a time.
+ */
+#ifndef ASMG_H
+#define ASMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct asmg_s* asmg_handle;
+
+enum asmg_status {
+  ASMG_OK = 0,
+  ASMG_NOT_CONVERGED = 1,     /* max_iter reached; u holds the last iterate */
+  ASMG_ERR_INVALID_ARG = -1,  /* null pointer, bad size or bad parameter */
+  ASMG_ERR_BAD_MESH = -2,     /* index out of range, non-positive measure, bad flag or coefficient */
+  ASMG_ERR_UNSUPPORTED = -3,  /* Neumann flags, dim not supported, non-box domain */
+  ASMG_ERR_BREAKDOWN = -4,    /* <p, A p> <= 0 or NaN, or <r, z> <= 0 in PCG */
+  ASMG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
+  ASMG_ERR_OOM = -6,          /* device allocation failed */
+  ASMG_ERR_TIMEOUT = -7       /* a bounded device wait expired */
+};
+
+enum asmg_precision { ASMG_FP64 = 0, ASMG_MIXED = 1 };
+
+typedef struct {
+  int32_t n_min;           /* cluster size below which a box is not split; 3 (Sec. 3.1) */
+  int32_t nu_pre;          /* pre-smoothing sweeps per auxiliary level; 2 (Sec. 5.1) */
+  int32_t nu_post;         /* post-smoothing sweeps per auxiliary level; 2 */
+  int32_t coarse_max_dofs; /* the V-cycle stops at the finest level with at most this many dofs,
+                              solved exactly (B_0 = A_0^{-1}, Algorithm 2); 512 */
+  int32_t precision;       /* ASMG_FP64: everything in FP64.  ASMG_MIXED: smoother, transfers and
+                              V-cycle in FP32 inside the FP64 CG (coarse solve, dots and residual
+                              recurrence stay FP64) */
+  int32_t max_iter;        /* PCG iteration cap; 500 */
+  int32_t smoothing;       /* 0: smooth the new/changed nodes N~_l of each level (Sec. 4.2, eq.
+                              decomposition); 1: smooth every node of every level */
+  int32_t use_graph;       /* 1: run the PCG loop as one CUDA graph with a device-side WHILE node */
+} asmg_params;
+
+/* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */
+int asmg_default_params(asmg_params* p);
+
+/*
+ * Build the solver for one mesh (Sec. 2-4).
+ *   dim        2 (triangles).  Other values return ASMG_ERR_UNSUPPORTED.
+ *   nv, vertices   float64 [nv * dim], row-major coordinates.
+ *   ne, elements   int32 [ne * (dim + 1)], vertex indices of each simplex,
+ *                  positively oriented (counter-clockwise).
+ *   boundary   uint8 [nv]: 0 free vertex, 1 Dirichlet vertex (u = 0).  The
+ *              value 2 (Neumann) returns ASMG_ERR_UNSUPPORTED.
+ *   coeff      float64 [ne] per-element coefficient a_e > 0, or NULL for a = 1.
+ *   params     NULL for the defaults.
+ *   out        receives the handle (NULL on error).
+ * The domain must be the square (cube) spanned by the vertices' bounding box
+ * (the root box of Sec. 3.1); otherwise ASMG_ERR_UNSUPPORTED.  Inputs are
+ * validated before any other work (ASMG_ERR_BAD_MESH).  The call copies what
+ * it keeps: the caller may free every input afterwards.
+ */
+int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int32_t* elements,
+              const uint8_t* boundary, const double* coeff, const asmg_params* params, void* stream,
+              asmg_handle* out);
+
+/*
+ * PCG solve of A u = b (Sec. 5.2) with the preconditioner of Algorithm 1.
+ *   b            float64 [nv] assembled load vector; entries at Dirichlet
+ *                vertices are ignored (see amg_mass_apply).
+ *   u            float64 [nv]: in = initial guess, out = solution (0 at
+ *                Dirichlet vertices).
+ *   rtol         stop when ||r_k||_2 <= rtol * ||b||_2 (free entries).
+ *   iterations   host int: PCG steps taken.
+ *   res_history  host float64 [max_iter + 1] or NULL: ||r_k||_2, k = 0..iterations.
+ * Returns ASMG_OK, ASMG_NOT_CONVERGED (u = last iterate, history filled) or
+ * ASMG_ERR_BREAKDOWN.  Host or device b/u are accepted; a host call times the
+ * copies inside the solve.
+ */
+int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* iterations, double* res_history,
+              void* stream);
+
+/*
+ * b = M f_h: the consistent P1 mass matrix applied to nodal values f [nv]
+ * (float64), result b [nv] with 0 at Dirichlet vertices.  This is the load
+ * vector <f, phi_i> of eq. bilinearform for the interpolant f_h.
+ */
+int amg_mass_apply(asmg_handle h, const double* f_nodal, double* b, void* stream);
+
+/*
+ * z = B_co r: one application of the preconditioner of Algorithm 1 (smooth,
+ * auxiliary correction through the Scott-Zhang transfer of Sec. 4.1, smooth
+ * back), r and z float64 [nv] (Dirichlet entries ignored / set to 0).
+ */
+int amg_precond_apply(asmg_handle h, const double* r, double* z, void* stream);
+
+/*
+ * y = A x with the fine stiffness matrix a_ij = int a grad phi_i . grad phi_j
+ * (Sec. 2); x, y float64 [nv], Dirichlet entries ignored / set to 0.
+ */
+int amg_spmv(asmg_handle h, const double* x, double* y, void* stream);
+
+/*
+ * Sensitivity of L(u(a)) to the element coefficients: with u the solution and
+ * lambda the adjoint solution (A lambda = dL/du), both float64 [nv],
+ *   dL_dcoeff[e] = -lambda_e^T K_e^(1) u_e,
+ * K_e^(1) the element stiffness for a_e = 1 (not in the paper).
+ */
+int amg_element_grad(asmg_handle h, const double* u, const double* lambda, double* dL_dcoeff, void* stream);
+
+/*
+ * Replace the element coefficients (float64 [ne], > 0) and rebuild every
+ * operator that depends on them (fine A, auxiliary operators, coarse
+ * inverse).  The tree, the auxiliary grids, the transfer and the colourings
+ * depend on geometry only and are kept.
+ */
+int amg_update_coefficients(asmg_handle h, const double* coeff, void* stream);
+
+/* Integer facts about a handle (see enum asmg_info_what); *value receives it. */
+enum asmg_info_what {
+  ASMG_INFO_NFREE = 0,        /* free fine dofs n */
+  ASMG_INFO_J = 1,            /* finest auxiliary level (tree depth) */
+  ASMG_INFO_COARSE = 2,       /* coarsest level used by the V-cycle */
+  ASMG_INFO_NAUX = 3,         /* free nodes of auxiliary level `level` */
+  ASMG_INFO_NSMOOTH = 4,      /* smoothed nodes of level `level` (-1: fine grid) */
+  ASMG_INFO_NCOLOURS = 5,     /* colours of level `level` (-1: fine grid) */
+  ASMG_INFO_NTREE_LEVELS = 6, /* depths of the cluster tree */
+  ASMG_INFO_NSEG = 7,         /* cluster-tree nodes at depth `level` */
+  ASMG_INFO_NSPLIT = 8,       /* split boxes of the closed tree at depth `level` */
+  ASMG_INFO_NNZ_A = 9,        /* stored non-zeros of the fine matrix */
+  ASMG_INFO_NNZ_P = 10,       /* non-zeros of the transfer P */
+  ASMG_INFO_NROWS_E = 11,     /* residual rows of level `level` */
+  ASMG_INFO_BYTES_ITER = 12,  /* algorithmic bytes of one PCG iteration (current precision) */
+  ASMG_INFO_NNZ_LEVEL = 13    /* stored non-zeros of level `level` (smoothing + residual rows) */
+};
+int amg_info(asmg_handle h, int what, int level, int64_t* value);
+
+/*
+ * Copy internal setup data to a host buffer for testing (see enum
+ * asmg_export_what).  With host_buf = NULL only *count (elements of the
+ * stated type) is returned.
+ */
+enum asmg_export_what {
+  ASMG_EXPORT_KEYS = 0,        /* uint64 [ne] element Morton keys */
+  ASMG_EXPORT_PERM = 1,        /* int32 [ne] elements sorted by key (stable) */
+  ASMG_EXPORT_SEG = 2,         /* int64 [nseg(level) * 4]: prefix, begin, end, split */
+  ASMG_EXPORT_SPLIT = 3,       /* uint64 [nsplit(level)] Morton prefixes of split boxes, ascending */
+  ASMG_EXPORT_AUX_KEYS = 4,    /* uint64 [naux(J)] lattice Morton keys of the finest-level free nodes */
+  ASMG_EXPORT_FINE_COLOUR = 5, /* int32 [nfree] colour of each free dof (free dofs in vertex order) */
+  ASMG_EXPORT_SMOOTH = 6,      /* uint64 [nsmooth(level) * 2]: node key, colour */
+  ASMG_EXPORT_LEVEL_ROWS = 7,  /* (row key, col key, value) triplets of level `level`, as
+                                  uint64, uint64, float64 (count = triplets; buffer 24 bytes each) */
+  ASMG_EXPORT_P = 8,           /* (fine vertex, aux key, value) triplets of P, 24 bytes each */
+  ASMG_EXPORT_FINE_A = 9       /* (row vertex, col vertex, value) triplets of A, 24 bytes each */
+};
+int amg_export(asmg_handle h, int what, int level, void* host_buf, int64_t* count);
+
+/* Free the handle and all device memory it owns.  NULL is ignored. */
+void amg_destroy(asmg_handle h);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASMG_H */

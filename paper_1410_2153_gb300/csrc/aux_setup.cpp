@@ -1,0 +1,693 @@
+// Host part of the setup (first version): closure of the box tree
+// (Sec. 3.2), the nested conforming auxiliary triangulations (Sec. 3.3) with
+// the per-level data of the in-place V-cycle, the finest auxiliary
+// coefficient and the Scott-Zhang transfer (Sec. 4.1).
+//
+// Boxes are named by depth and Morton prefix of their integer position; the
+// closed tree is stored as one sorted array of split prefixes per depth.
+// Auxiliary nodes are integer points of the 2^D lattice of the root box,
+// named by their 64-bit Morton key; the free nodes of the finest level,
+// sorted by key, are the auxiliary unknowns (every coarser level's nodes
+// are among them because the grids are nested).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "internal.h"
+
+namespace asmg {
+
+namespace {
+
+inline uint64_t spread(uint64_t v) {
+  v &= 0xffffffffULL;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFULL;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFULL;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0FULL;
+  v = (v | (v << 2)) & 0x3333333333333333ULL;
+  v = (v | (v << 1)) & 0x5555555555555555ULL;
+  return v;
+}
+
+inline uint64_t compact(uint64_t v) {
+  v &= 0x5555555555555555ULL;
+  v = (v | (v >> 1)) & 0x3333333333333333ULL;
+  v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0FULL;
+  v = (v | (v >> 4)) & 0x00FF00FF00FF00FFULL;
+  v = (v | (v >> 8)) & 0x0000FFFF0000FFFFULL;
+  v = (v | (v >> 16)) & 0x00000000FFFFFFFFULL;
+  return v;
+}
+
+inline uint64_t mort(uint64_t x, uint64_t y) { return spread(x) | (spread(y) << 1); }
+
+struct BoxTree {
+  int D = 31;
+  std::vector<std::vector<uint64_t>> S;  // split prefixes per depth, sorted
+
+  bool split(int d, uint64_t p) const {
+    if (d < 0 || d >= (int)S.size()) return false;
+    return std::binary_search(S[d].begin(), S[d].end(), p);
+  }
+  bool exists(int d, uint64_t p) const { return d == 0 ? p == 0 : split(d - 1, p >> 2); }
+  // edge neighbour at the same depth (dir 0 S, 1 E, 2 N, 3 W)
+  bool nbr(int d, uint64_t p, int dir, uint64_t& q) const {
+    static const int dx[4] = {0, 1, 0, -1}, dy[4] = {-1, 0, 1, 0};
+    int64_t x = (int64_t)compact(p) + dx[dir], y = (int64_t)compact(p >> 1) + dy[dir];
+    int64_t nb = 1LL << d;
+    if (x < 0 || y < 0 || x >= nb || y >= nb) return false;
+    q = mort((uint64_t)x, (uint64_t)y);
+    return true;
+  }
+  // hanging midpoints of box (d, p) when it is shown at a level > d
+  void hanging(int d, uint64_t p, bool h[4]) const {
+    for (int e = 0; e < 4; ++e) {
+      uint64_t q;
+      h[e] = nbr(d, p, e, q) && split(d, q);
+    }
+  }
+};
+
+// Triangles of a box as lattice-key triples: SW-NE diagonal, or a fan about
+// the centre through the hanging midpoints (Fig. "closure2").
+void box_tris(const BoxTree& T, int d, uint64_t p, const bool h[4], std::vector<std::array<uint64_t, 3>>& out) {
+  const uint64_t s = 1ULL << (T.D - d);
+  const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s;
+  const uint64_t SW = mort(x0, y0), SE = mort(x0 + s, y0), NE = mort(x0 + s, y0 + s), NW = mort(x0, y0 + s);
+  if (!(h[0] || h[1] || h[2] || h[3])) {
+    out.push_back({SW, SE, NE});
+    out.push_back({SW, NE, NW});
+    return;
+  }
+  const uint64_t m = s >> 1, C = mort(x0 + m, y0 + m);
+  uint64_t ring[8];
+  int n = 0;
+  ring[n++] = SW;
+  if (h[0]) ring[n++] = mort(x0 + m, y0);
+  ring[n++] = SE;
+  if (h[1]) ring[n++] = mort(x0 + s, y0 + m);
+  ring[n++] = NE;
+  if (h[2]) ring[n++] = mort(x0 + m, y0 + s);
+  ring[n++] = NW;
+  if (h[3]) ring[n++] = mort(x0, y0 + m);
+  for (int i = 0; i < n; ++i) out.push_back({ring[i], ring[(i + 1) % n], C});
+}
+
+inline bool boundary_key(const BoxTree& T, uint64_t k) {
+  uint64_t x = compact(k), y = compact(k >> 1), top = 1ULL << T.D;
+  return x == 0 || y == 0 || x == top || y == top;
+}
+
+inline int32_t id_of(const std::vector<uint64_t>& keys, uint64_t k) {
+  auto it = std::lower_bound(keys.begin(), keys.end(), k);
+  return (it != keys.end() && *it == k) ? (int32_t)(it - keys.begin()) : -1;
+}
+
+void sort_unique(std::vector<uint64_t>& v) {
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+// Boxes at depth d (children of the split boxes at d-1), ascending prefix.
+std::vector<uint64_t> boxes_at(const BoxTree& T, int d) {
+  if (d == 0) return {0};
+  std::vector<uint64_t> b;
+  if (d - 1 >= (int)T.S.size()) return b;
+  b.reserve(T.S[d - 1].size() * 4);
+  for (uint64_t p : T.S[d - 1])
+    for (uint64_t c = 0; c < 4; ++c) b.push_back((p << 2) | c);
+  return b;
+}
+
+// ---------------------------------------------------------------- clipping
+struct V2 {
+  double x, y;
+};
+
+// Clip the convex polygon `in` (CCW) to the half-plane n.x <= c.
+int clip_half(const V2* in, int n, double nx, double ny, double c, V2* out) {
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const V2& a = in[i];
+    const V2& b = in[(i + 1) % n];
+    double fa = nx * a.x + ny * a.y - c, fb = nx * b.x + ny * b.y - c;
+    if (fa <= 0) out[m++] = a;
+    if ((fa <= 0) != (fb <= 0)) {
+      double t = fa / (fa - fb);
+      out[m++] = V2{a.x + t * (b.x - a.x), a.y + t * (b.y - a.y)};
+    }
+  }
+  return m;
+}
+
+// Clip polygon P (CCW, local coordinates) by triangle K (CCW).
+int clip_tri(const V2* P, int n, const V2* K, V2* out) {
+  V2 buf[2][16];
+  int m = n;
+  for (int i = 0; i < n; ++i) buf[0][i] = P[i];
+  int cur = 0;
+  for (int e = 0; e < 3 && m >= 3; ++e) {
+    const V2& a = K[e];
+    const V2& b = K[(e + 1) % 3];
+    // inside of a CCW edge a->b: cross(b - a, x - a) >= 0  <=>  n.x <= c
+    double nx = (b.y - a.y), ny = -(b.x - a.x);
+    double c = nx * a.x + ny * a.y;
+    m = clip_half(buf[cur], m, nx, ny, c, buf[1 - cur]);
+    cur = 1 - cur;
+  }
+  for (int i = 0; i < m; ++i) out[i] = buf[cur][i];
+  return m;
+}
+
+// Moments of a polygon by Green's theorem: [1, x, y, x^2, xy, y^2].
+void moments(const V2* p, int n, double M[6]) {
+  for (int k = 0; k < 6; ++k) M[k] = 0;
+  for (int i = 0; i < n; ++i) {
+    const V2& a = p[i];
+    const V2& b = p[(i + 1) % n];
+    double c = a.x * b.y - b.x * a.y;
+    M[0] += c;
+    M[1] += (a.x + b.x) * c;
+    M[2] += (a.y + b.y) * c;
+    M[3] += (a.x * a.x + a.x * b.x + b.x * b.x) * c;
+    M[4] += (a.x * b.y + 2 * a.x * a.y + 2 * b.x * b.y + b.x * a.y) * c;
+    M[5] += (a.y * a.y + a.y * b.y + b.y * b.y) * c;
+  }
+  M[0] /= 2;
+  M[1] /= 6;
+  M[2] /= 6;
+  M[3] /= 12;
+  M[4] /= 24;
+  M[5] /= 12;
+}
+
+// Affine coefficients (c0 + c1 x + c2 y) of the barycentric function of vertex j.
+void bary_affine(const V2* T, int j, double c[3]) {
+  const V2 &p = T[(j + 1) % 3], &q = T[(j + 2) % 3];
+  double twoA = (T[1].x - T[0].x) * (T[2].y - T[0].y) - (T[2].x - T[0].x) * (T[1].y - T[0].y);
+  c[0] = (p.x * q.y - q.x * p.y) / twoA;
+  c[1] = (p.y - q.y) / twoA;
+  c[2] = (q.x - p.x) / twoA;
+}
+
+// int (f0 + f1 x + f2 y)(g0 + g1 x + g2 y) from the moments
+inline double prod_int(const double f[3], const double g[3], const double M[6]) {
+  return f[0] * g[0] * M[0] + (f[0] * g[1] + f[1] * g[0]) * M[1] + (f[0] * g[2] + f[2] * g[0]) * M[2] +
+         f[1] * g[1] * M[3] + (f[1] * g[2] + f[2] * g[1]) * M[4] + f[2] * g[2] * M[5];
+}
+
+// Leaves of the closed tree meeting the closed lattice rectangle [lo, hi].
+void leaves_in(const BoxTree& T, int64_t lox, int64_t loy, int64_t hix, int64_t hiy,
+               std::vector<std::pair<int, uint64_t>>& out) {
+  std::pair<int, uint64_t> st[256];
+  int sp = 0;
+  st[sp++] = {0, 0};
+  while (sp) {
+    auto b = st[--sp];
+    int64_t s = 1LL << (T.D - b.first);
+    int64_t x0 = (int64_t)compact(b.second) * s, y0 = (int64_t)compact(b.second >> 1) * s;
+    if (x0 > hix || y0 > hiy || x0 + s < lox || y0 + s < loy) continue;
+    if (!T.split(b.first, b.second)) {
+      out.push_back(b);
+      continue;
+    }
+    for (uint64_t c = 0; c < 4; ++c) st[sp++] = {b.first + 1, (b.second << 2) | c};
+  }
+}
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 4096) nt = 1;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&, t] { f(t, nt, n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
+}  // namespace
+
+uint64_t lattice_key2(uint64_t x, uint64_t y) { return mort(x, y); }
+void lattice_xy2(uint64_t key, uint64_t& x, uint64_t& y) {
+  x = compact(key);
+  y = compact(key >> 1);
+}
+
+void lattice_point(const TreeResult& t, uint64_t key, double* p) {
+  p[0] = t.amin[0] + std::ldexp((double)compact(key), -t.D) * t.L;
+  p[1] = t.amin[1] + std::ldexp((double)compact(key >> 1), -t.D) * t.L;
+}
+
+void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
+                    const std::vector<int32_t>& free_of_vertex, AuxHost& out) {
+  BoxTree T;
+  T.D = tree.D;
+  T.S = tree.split;
+
+  // ---- Closure (Sec. 3.2, steps Mark/Close/Refine), finest level first:
+  // a split box needs all four same-depth edge neighbours, so the parent of
+  // every such neighbour is marked for refinement one level up.
+  for (int d = (int)T.S.size() - 1; d >= 1; --d) {
+    std::vector<uint64_t> add;
+    for (uint64_t p : T.S[d])
+      for (int e = 0; e < 4; ++e) {
+        uint64_t q;
+        if (T.nbr(d, p, e, q)) add.push_back(q >> 2);
+      }
+    std::vector<uint64_t>& up = T.S[d - 1];
+    up.insert(up.end(), add.begin(), add.end());
+    sort_unique(up);
+  }
+  out.split = T.S;
+  const int J = (int)T.S.size();
+  out.J = J;
+  std::vector<std::vector<uint64_t>> BX(J + 1);  // boxes per depth, ascending prefix
+  for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
+
+  // ---- finest-level nodes (aux unknowns)
+  {
+    std::vector<uint64_t> keys;
+    std::vector<std::array<uint64_t, 3>> tri;
+    for (int d = 0; d <= J; ++d) {
+      for (uint64_t p : BX[d]) {
+        if (T.split(d, p)) continue;
+        bool h[4];
+        T.hanging(d, p, h);
+        tri.clear();
+        box_tris(T, d, p, h, tri);
+        for (auto& t : tri)
+          for (int k = 0; k < 3; ++k)
+            if (!boundary_key(T, t[k])) keys.push_back(t[k]);
+      }
+    }
+    sort_unique(keys);
+    out.aux_key = std::move(keys);
+  }
+  const std::vector<uint64_t>& AK = out.aux_key;
+
+  // ---- per level: changed boxes, new nodes and their parents, level sizes
+  struct LevelInfo {
+    std::vector<uint64_t> fanned;  // leaves at depth l-1 that gain hanging midpoints at level l
+  };
+  std::vector<LevelInfo> info(J + 1);
+  out.nlevel.assign(J + 1, 0);
+  std::vector<std::vector<std::array<uint64_t, 3>>> newnodes(J + 1);  // key, parent0, parent1
+  for (int l = 1; l <= J; ++l) {
+    const int d = l - 1;
+    const auto& bx = BX[d];
+    std::vector<std::array<uint64_t, 3>> nn;
+    auto add_box = [&](uint64_t p, bool split) {
+      const uint64_t s = 1ULL << (T.D - d), m = s >> 1;
+      const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s;
+      const uint64_t SW = mort(x0, y0), SE = mort(x0 + s, y0), NE = mort(x0 + s, y0 + s), NW = mort(x0, y0 + s);
+      nn.push_back({mort(x0 + m, y0 + m), SW, NE});  // centre: midpoint of the SW-NE diagonal
+      if (split) {
+        nn.push_back({mort(x0 + m, y0), SW, SE});
+        nn.push_back({mort(x0 + s, y0 + m), SE, NE});
+        nn.push_back({mort(x0 + m, y0 + s), NW, NE});
+        nn.push_back({mort(x0, y0 + m), SW, NW});
+      }
+    };
+    for (uint64_t p : bx) {
+      bool sp = T.split(d, p);
+      if (sp) {
+        add_box(p, true);
+      } else {
+        bool h[4];
+        T.hanging(d, p, h);
+        if (h[0] || h[1] || h[2] || h[3]) {
+          info[l].fanned.push_back(p);
+          add_box(p, false);
+        }
+      }
+    }
+    std::sort(nn.begin(), nn.end());
+    nn.erase(std::unique(nn.begin(), nn.end(), [](const std::array<uint64_t, 3>& a, const std::array<uint64_t, 3>& b) {
+               return a[0] == b[0];
+             }),
+             nn.end());
+    int64_t nfree = 0;
+    for (auto& v : nn)
+      if (!boundary_key(T, v[0])) ++nfree;
+    out.nlevel[l] = out.nlevel[l - 1] + nfree;
+    newnodes[l] = std::move(nn);
+  }
+  // coarsest level used: finest level with at most coarse_max_dofs free nodes
+  out.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  const int c = out.c;
+
+  // ---- finest auxiliary coefficient: area-weighted mean of the fine
+  // coefficients (exact clipping), accumulated per box half for coarser levels
+  const bool varcoef = !mesh.coeff.empty();
+  // integral of a over the lower-right (0) / upper-left (1) diagonal halves
+  // of every box, per depth, aligned with boxes_at(T, d)
+  std::vector<std::vector<std::array<double, 2>>> half(J + 1);
+  // integrals over the fan triangles of fanned leaves (key: sorted triangle)
+  std::vector<std::pair<std::array<uint64_t, 3>, double>> fanint;
+  auto tri_sorted = [](std::array<uint64_t, 3> t) {
+    std::sort(t.begin(), t.end());
+    return t;
+  };
+  if (varcoef) {
+    // finest triangles, indexed by leaf order
+    std::vector<std::array<uint64_t, 3>> ftri;
+    std::vector<std::vector<int64_t>> first(J + 1);
+    for (int d = 0; d <= J; ++d) {
+      const auto& bx = BX[d];
+      first[d].assign(bx.size(), -1);
+      for (size_t i = 0; i < bx.size(); ++i) {
+        if (T.split(d, bx[i])) continue;
+        bool h[4];
+        T.hanging(d, bx[i], h);
+        first[d][i] = (int64_t)ftri.size();
+        box_tris(T, d, bx[i], h, ftri);
+      }
+    }
+    // clip every fine element against the finest triangles it meets
+    std::vector<std::vector<std::pair<int64_t, double>>> contrib(64);
+    parallel_for(mesh.ne, [&](unsigned t, unsigned, int64_t b, int64_t e) {
+      auto& mine = contrib[t];
+      std::vector<std::pair<int, uint64_t>> lv;
+      std::vector<std::array<uint64_t, 3>> kt;
+      const double sc = std::ldexp(1.0, T.D) / tree.L;
+      for (int64_t el = b; el < e; ++el) {
+        V2 P[3];
+        double mnx = INFINITY, mny = INFINITY, mxx = -INFINITY, mxy = -INFINITY;
+        for (int k = 0; k < 3; ++k) {
+          int32_t v = mesh.E[3 * el + k];
+          P[k] = V2{mesh.X[2 * v], mesh.X[2 * v + 1]};
+          mnx = std::min(mnx, P[k].x); mxx = std::max(mxx, P[k].x);
+          mny = std::min(mny, P[k].y); mxy = std::max(mxy, P[k].y);
+        }
+        lv.clear();
+        leaves_in(T, (int64_t)std::floor((mnx - tree.amin[0]) * sc) - 2, (int64_t)std::floor((mny - tree.amin[1]) * sc) - 2,
+                  (int64_t)std::ceil((mxx - tree.amin[0]) * sc) + 2, (int64_t)std::ceil((mxy - tree.amin[1]) * sc) + 2, lv);
+        const V2 o = P[0];
+        V2 Pl[3];
+        for (int k = 0; k < 3; ++k) Pl[k] = V2{P[k].x - o.x, P[k].y - o.y};
+        for (auto& lf : lv) {
+          const auto& bx = BX[lf.first];
+          const size_t bi = std::lower_bound(bx.begin(), bx.end(), lf.second) - bx.begin();
+          const int64_t f0 = first[lf.first][bi];
+          bool h[4];
+          T.hanging(lf.first, lf.second, h);
+          kt.clear();
+          box_tris(T, lf.first, lf.second, h, kt);
+          for (size_t q = 0; q < kt.size(); ++q) {
+            V2 K[3];
+            for (int k = 0; k < 3; ++k) {
+              double p[2];
+              lattice_point(tree, kt[q][k], p);
+              K[k] = V2{p[0] - o.x, p[1] - o.y};
+            }
+            V2 poly[16];
+            int m = clip_tri(Pl, 3, K, poly);
+            if (m < 3) continue;
+            double M[6];
+            moments(poly, m, M);
+            if (!(M[0] > 0)) continue;
+            mine.push_back({f0 + (int64_t)q, M[0] * mesh.coeff[el]});
+          }
+        }
+      }
+    });
+    // reduce into finest-triangle integrals (fixed order: thread, then element)
+    std::vector<double> I(ftri.size(), 0.0);
+    for (auto& v : contrib)
+      for (auto& pr : v) I[pr.first] += pr.second;
+    // box-half integrals, bottom-up
+    for (int d = J; d >= 0; --d) {
+      const auto& bx = BX[d];
+      half[d].assign(bx.size(), {0.0, 0.0});
+      for (size_t i = 0; i < bx.size(); ++i) {
+        uint64_t p = bx[i];
+        if (!T.split(d, p)) {
+          bool h[4];
+          T.hanging(d, p, h);
+          std::vector<std::array<uint64_t, 3>> kt;
+          box_tris(T, d, p, h, kt);
+          const int64_t f0 = first[d][i];
+          if (!(h[0] || h[1] || h[2] || h[3])) {
+            half[d][i] = {I[f0], I[f0 + 1]};
+          } else {
+            // fan triangles on the S and E edges form the lower-right half
+            const uint64_t s = 1ULL << (T.D - d);
+            const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s;
+            for (size_t k = 0; k < kt.size(); ++k) {
+              uint64_t ax = compact(kt[k][0]), ay = compact(kt[k][0] >> 1);
+              uint64_t bxx = compact(kt[k][1]), by = compact(kt[k][1] >> 1);
+              bool lr = (ay == y0 && by == y0) || (ax == x0 + s && bxx == x0 + s);
+              half[d][i][lr ? 0 : 1] += I[f0 + k];
+              fanint.push_back({tri_sorted(kt[k]), I[f0 + k]});
+            }
+          }
+        } else {
+          const auto& ch = BX[d + 1];
+          size_t j = std::lower_bound(ch.begin(), ch.end(), p << 2) - ch.begin();
+          // children: 0 SW, 1 SE, 2 NW, 3 NE (bit 0 = x, bit 1 = y)
+          const auto& sw = half[d + 1][j];
+          const auto& se = half[d + 1][j + 1];
+          const auto& nw = half[d + 1][j + 2];
+          const auto& ne = half[d + 1][j + 3];
+          half[d][i][0] = sw[0] + se[0] + se[1] + ne[0];
+          half[d][i][1] = sw[1] + nw[0] + nw[1] + ne[1];
+        }
+      }
+    }
+    std::sort(fanint.begin(), fanint.end());
+  }
+  // coefficient of one triangle of box (d, p) at a level where the box shows
+  // as diagonal split (k = 0 lower-right, 1 upper-left) or as fan
+  auto tri_coef = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> double {
+    if (!varcoef) return 1.0;
+    double pa[2], pb[2], pc[2];
+    lattice_point(tree, t[0], pa);
+    lattice_point(tree, t[1], pb);
+    lattice_point(tree, t[2], pc);
+    double area = 0.5 * ((pb[0] - pa[0]) * (pc[1] - pa[1]) - (pc[0] - pa[0]) * (pb[1] - pa[1]));
+    double integral;
+    if (diag) {
+      const auto& bx = BX[d];
+      size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      integral = half[d][i][k];
+    } else {
+      auto key = tri_sorted(t);
+      auto it = std::lower_bound(fanint.begin(), fanint.end(), std::pair<std::array<uint64_t, 3>, double>(key, -HUGE_VAL));
+      integral = it->second;
+    }
+    return integral / area;
+  };
+
+  // emit the triangles of box (d, p) as shown at level l
+  auto emit_box = [&](int d, uint64_t p, int l, std::vector<int32_t>& ids, std::vector<uint64_t>& keys,
+                      std::vector<double>& coef) {
+    bool h[4] = {false, false, false, false};
+    if (d < l) T.hanging(d, p, h);
+    std::vector<std::array<uint64_t, 3>> kt;
+    box_tris(T, d, p, h, kt);
+    bool diag = !(h[0] || h[1] || h[2] || h[3]);
+    for (size_t k = 0; k < kt.size(); ++k) {
+      for (int v = 0; v < 3; ++v) {
+        keys.push_back(kt[k][v]);
+        ids.push_back(boundary_key(T, kt[k][v]) ? -1 : id_of(AK, kt[k][v]));
+      }
+      coef.push_back(tri_coef(d, p, diag, (int)k, kt[k]));
+    }
+  };
+
+  // ---- coarsest level: all triangles of sigma^(c)
+  {
+    std::vector<uint64_t> ck;
+    for (int d = 0; d <= c; ++d) {
+      for (uint64_t p : BX[d]) {
+        if (d < c && T.split(d, p)) continue;
+        emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef);
+      }
+    }
+    for (auto id : out.coarse_tri_id)
+      if (id >= 0) out.coarse_id.push_back(id);
+    std::sort(out.coarse_id.begin(), out.coarse_id.end());
+    out.coarse_id.erase(std::unique(out.coarse_id.begin(), out.coarse_id.end()), out.coarse_id.end());
+  }
+
+  // ---- levels c+1..J: smoothing sets, assembly triangles, new nodes
+  out.levels.clear();
+  for (int l = c + 1; l <= J; ++l) {
+    AuxLevelHost L;
+    L.level = l;
+    const int d = l - 1;
+    const uint64_t s = 1ULL << (T.D - d);
+    std::vector<uint64_t> changed = info[l].fanned;  // plus the split boxes
+    changed.insert(changed.end(), T.S[d].begin(), T.S[d].end());
+    sort_unique(changed);
+    // N~_l
+    std::vector<uint64_t> sm;
+    if (prm.smoothing == 1) {
+      // every node of the level
+      for (int dd = 0; dd <= l; ++dd) {
+        for (uint64_t p : BX[dd]) {
+          if (dd < l && T.split(dd, p)) continue;
+          bool h[4] = {false, false, false, false};
+          if (dd < l) T.hanging(dd, p, h);
+          std::vector<std::array<uint64_t, 3>> kt;
+          box_tris(T, dd, p, h, kt);
+          for (auto& t : kt)
+            for (int v = 0; v < 3; ++v)
+              if (!boundary_key(T, t[v])) sm.push_back(t[v]);
+        }
+      }
+    } else {
+      for (uint64_t p : changed) {
+        const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s, m = s >> 1;
+        bool sp = T.split(d, p);
+        for (int iy = 0; iy <= 2; ++iy)
+          for (int ix = 0; ix <= 2; ++ix) {
+            bool mid = (ix == 1) || (iy == 1);
+            if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
+            uint64_t k = mort(x0 + ix * m, y0 + iy * m);
+            if (!boundary_key(T, k)) sm.push_back(k);
+          }
+      }
+    }
+    sort_unique(sm);
+    for (uint64_t k : sm) L.smooth.push_back(id_of(AK, k));
+
+    // relevant boxes: changed boxes and the level-l leaves around them
+    std::vector<std::pair<int, uint64_t>> rel;
+    if (prm.smoothing == 1) {
+      for (int dd = 0; dd <= l; ++dd)
+        for (uint64_t p : BX[dd])
+          if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
+    } else {
+      for (uint64_t p : changed) {
+        if (T.split(d, p)) {
+          for (uint64_t ch = 0; ch < 4; ++ch) rel.push_back({d + 1, (p << 2) | ch});
+        } else {
+          rel.push_back({d, p});
+        }
+        const int64_t x = (int64_t)compact(p), y = (int64_t)compact(p >> 1), nb = 1LL << d;
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            if (!dx && !dy) continue;
+            if (x + dx < 0 || y + dy < 0 || x + dx >= nb || y + dy >= nb) continue;
+            int dd = d;
+            uint64_t q = mort((uint64_t)(x + dx), (uint64_t)(y + dy));
+            while (!T.exists(dd, q)) {
+              --dd;
+              q >>= 2;
+            }
+            if (dd == d && T.split(d, q)) {
+              for (uint64_t ch = 0; ch < 4; ++ch) rel.push_back({d + 1, (q << 2) | ch});
+            } else {
+              rel.push_back({dd, q});
+            }
+          }
+      }
+    }
+    std::sort(rel.begin(), rel.end());
+    rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+    for (auto& b : rel) emit_box(b.first, b.second, l, L.tri_id, L.tri_key, L.tri_coef);
+
+    // new nodes with their parents
+    for (auto& v : newnodes[l]) {
+      if (boundary_key(T, v[0])) continue;
+      L.new_id.push_back(id_of(AK, v[0]));
+      L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
+      L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
+    }
+    out.levels.push_back(std::move(L));
+  }
+
+  // ---- Scott-Zhang transfer (Sec. 4.1): P_ik = int_{sigma_i} psi_i phi_k,
+  // sigma_i the lowest-index element at node i, psi_i = (12 lambda_i - 3)/|sigma_i|
+  std::vector<int32_t> sigma(mesh.nv, -1);
+  for (int64_t e = mesh.ne - 1; e >= 0; --e)
+    for (int k = 0; k < 3; ++k) sigma[mesh.E[3 * e + k]] = (int32_t)e;
+  std::vector<int32_t> vert_of_free;
+  for (int64_t v = 0; v < mesh.nv; ++v)
+    if (free_of_vertex[v] >= 0) vert_of_free.push_back((int32_t)v);
+  const int64_t n = (int64_t)vert_of_free.size();
+  std::vector<Triplets> parts(64);
+  parallel_for(n, [&](unsigned t, unsigned, int64_t b, int64_t e) {
+    Triplets& mine = parts[t];
+    std::vector<std::pair<int, uint64_t>> lv;
+    std::vector<std::array<uint64_t, 3>> kt;
+    std::vector<std::pair<int32_t, double>> row;
+    const double sc = std::ldexp(1.0, T.D) / tree.L;
+    for (int64_t i = b; i < e; ++i) {
+      const int32_t v = vert_of_free[i];
+      const int32_t el = sigma[v];
+      V2 P[3];
+      int loc = 0;
+      for (int k = 0; k < 3; ++k) {
+        int32_t w = mesh.E[3 * (int64_t)el + k];
+        P[k] = V2{mesh.X[2 * w], mesh.X[2 * w + 1]};
+        if (w == v) loc = k;
+      }
+      const V2 o = P[0];
+      V2 Pl[3];
+      for (int k = 0; k < 3; ++k) Pl[k] = V2{P[k].x - o.x, P[k].y - o.y};
+      const double area = 0.5 * (Pl[1].x * Pl[2].y - Pl[2].x * Pl[1].y);
+      double lam[3], psi[3];
+      bary_affine(Pl, loc, lam);
+      psi[0] = (12.0 * lam[0] - 3.0) / area;
+      psi[1] = 12.0 * lam[1] / area;
+      psi[2] = 12.0 * lam[2] / area;
+      double mnx = std::min({P[0].x, P[1].x, P[2].x}), mxx = std::max({P[0].x, P[1].x, P[2].x});
+      double mny = std::min({P[0].y, P[1].y, P[2].y}), mxy = std::max({P[0].y, P[1].y, P[2].y});
+      lv.clear();
+      leaves_in(T, (int64_t)std::floor((mnx - tree.amin[0]) * sc) - 2, (int64_t)std::floor((mny - tree.amin[1]) * sc) - 2,
+                (int64_t)std::ceil((mxx - tree.amin[0]) * sc) + 2, (int64_t)std::ceil((mxy - tree.amin[1]) * sc) + 2, lv);
+      row.clear();
+      for (auto& lf : lv) {
+        bool h[4];
+        T.hanging(lf.first, lf.second, h);
+        kt.clear();
+        box_tris(T, lf.first, lf.second, h, kt);
+        for (auto& k3 : kt) {
+          V2 K[3];
+          for (int k = 0; k < 3; ++k) {
+            double p[2];
+            lattice_point(tree, k3[k], p);
+            K[k] = V2{p[0] - o.x, p[1] - o.y};
+          }
+          V2 poly[16];
+          int m = clip_tri(Pl, 3, K, poly);
+          if (m < 3) continue;
+          double M[6];
+          moments(poly, m, M);
+          if (!(M[0] > 0)) continue;
+          for (int k = 0; k < 3; ++k) {
+            if (boundary_key(T, k3[k])) continue;
+            double phi[3];
+            bary_affine(K, k, phi);
+            row.push_back({id_of(AK, k3[k]), prod_int(psi, phi, M)});
+          }
+        }
+      }
+      std::sort(row.begin(), row.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b2) {
+        return a.first < b2.first;
+      });
+      for (size_t k = 0; k < row.size();) {
+        size_t j = k;
+        double sum = 0.0;
+        while (j < row.size() && row[j].first == row[k].first) sum += row[j++].second;
+        mine.r.push_back((int32_t)i);
+        mine.c.push_back(row[k].first);
+        mine.v.push_back(sum);
+        k = j;
+      }
+    }
+  });
+  for (auto& p : parts) {
+    out.P.r.insert(out.P.r.end(), p.r.begin(), p.r.end());
+    out.P.c.insert(out.P.c.end(), p.c.begin(), p.c.end());
+    out.P.v.insert(out.P.v.end(), p.v.begin(), p.v.end());
+  }
+}
+
+}  // namespace asmg

@@ -1,0 +1,795 @@
+// C ABI entry points (include/asmg.h) and the setup pipeline.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <numeric>
+
+#include "handle.h"
+
+using namespace asmg;
+
+namespace {
+
+thread_local std::string g_err;
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+std::vector<T> to_host(const T* p, int64_t n, cudaStream_t s) {
+  std::vector<T> h((size_t)n);
+  if (n == 0) return h;
+  if (is_device(p)) {
+    ASMG_CUDA(cudaMemcpyAsync(h.data(), p, sizeof(T) * n, cudaMemcpyDeviceToHost, s));
+    ASMG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(h.data(), p, sizeof(T) * n);
+  }
+  return h;
+}
+
+void copy_in(double* dst, const double* src, int64_t n, cudaStream_t s) {
+  ASMG_CUDA(cudaMemcpyAsync(dst, src, 8 * n, is_device(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+void copy_out(double* dst, const double* src, int64_t n, cudaStream_t s) {
+  ASMG_CUDA(cudaMemcpyAsync(dst, src, 8 * n, is_device(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+int64_t pad32(int64_t n) { return (n + 31) / 32 * 32; }
+
+// rows of a host CSR selected and renumbered: out row k = A row sel[k] (or
+// empty when sel[k] < 0), columns mapped by cmap (dropped when < 0)
+HostCSR select_rows(const HostCSR& A, const std::vector<int64_t>& sel, const std::vector<int32_t>* cmap,
+                    const std::vector<uint8_t>* colkeep) {
+  HostCSR B;
+  B.nr = (int64_t)sel.size();
+  B.nc = A.nc;
+  B.ptr.assign(B.nr + 1, 0);
+  for (int64_t k = 0; k < B.nr; ++k) {
+    if (sel[k] >= 0)
+      for (int64_t p = A.ptr[sel[k]]; p < A.ptr[sel[k] + 1]; ++p) {
+        int32_t c = A.col[p];
+        if (colkeep && !(*colkeep)[c]) continue;
+        B.col.push_back(cmap ? (*cmap)[c] : c);
+        B.val.push_back(A.val[p]);
+      }
+    B.ptr[k + 1] = (int64_t)B.col.size();
+  }
+  return B;
+}
+
+template <class T>
+void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
+                     const std::vector<uint8_t>& inset, AuxLevelDev<T>& D, cudaStream_t s) {
+  D.level = L.level;
+  // smoothing rows ordered by (colour, id), colour blocks padded to 32
+  int ncol = 0;
+  for (int32_t id : L.smooth) ncol = std::max(ncol, colour[id] + 1);
+  D.ncolours = ncol;
+  std::vector<std::vector<int32_t>> byc(ncol);
+  for (int32_t id : L.smooth) byc[colour[id]].push_back(id);
+  std::vector<int64_t> sel;
+  D.cstart.assign(1, 0);
+  for (int c = 0; c < ncol; ++c) {
+    for (int32_t id : byc[c]) sel.push_back(id);
+    while (sel.size() % 32) sel.push_back(-1);
+    D.cstart.push_back((int64_t)sel.size());
+  }
+  D.nsm = (int64_t)sel.size();
+  D.nsm_real = (int64_t)L.smooth.size();
+  std::vector<int32_t> rows(sel.size());
+  std::vector<T> dinv(sel.size(), (T)0);
+  for (size_t k = 0; k < sel.size(); ++k) {
+    rows[k] = (int32_t)sel[k];
+    if (sel[k] >= 0) {
+      double dg = 0;
+      for (int64_t p = Arows.ptr[sel[k]]; p < Arows.ptr[sel[k] + 1]; ++p)
+        if (Arows.col[p] == sel[k]) dg = Arows.val[p];
+      if (!(dg > 0)) ASMG_FAIL(ASMG_ERR_CUDA, "auxiliary level %d: non-positive diagonal", L.level);
+      dinv[k] = (T)(1.0 / dg);
+    }
+  }
+  HostCSR SM = select_rows(Arows, sel, nullptr, nullptr);
+  sell_build<T>(D.SM, SM, 0, s);
+  D.sm_rows.upload(rows, s);
+  D.sm_dinv.upload(dinv, s);
+  // residual rows: every row with an entry in a smoothing column
+  std::vector<int64_t> rsel;
+  for (int64_t i = 0; i < Arows.nr; ++i) {
+    bool any = false;
+    for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1] && !any; ++p) any = inset[Arows.col[p]];
+    if (any) rsel.push_back(i);
+  }
+  while (rsel.size() % 32) rsel.push_back(-1);
+  D.nrs = (int64_t)rsel.size();
+  HostCSR RS = select_rows(Arows, rsel, nullptr, &inset);
+  sell_build<T>(D.RS, RS, 0, s);
+  std::vector<int32_t> rsrows(rsel.begin(), rsel.end());
+  D.rs_rows.upload(rsrows, s);
+  // prolongation and restriction of the new nodes
+  D.nnew = (int64_t)L.new_id.size();
+  D.nn_id.upload(L.new_id, s);
+  D.nn_p0.upload(L.new_p0, s);
+  D.nn_p1.upload(L.new_p1, s);
+  std::vector<std::pair<int32_t, int32_t>> pc;  // (parent, child)
+  for (size_t k = 0; k < L.new_id.size(); ++k) {
+    if (L.new_p0[k] >= 0) pc.push_back({L.new_p0[k], L.new_id[k]});
+    if (L.new_p1[k] >= 0) pc.push_back({L.new_p1[k], L.new_id[k]});
+  }
+  std::sort(pc.begin(), pc.end());
+  std::vector<int32_t> pid, pptr(1, 0), child;
+  for (size_t k = 0; k < pc.size(); ++k) {
+    if (k == 0 || pc[k].first != pc[k - 1].first) {
+      if (k) pptr.push_back((int32_t)child.size());
+      pid.push_back(pc[k].first);
+    }
+    child.push_back(pc[k].second);
+  }
+  if (!pid.empty()) pptr.push_back((int32_t)child.size());
+  D.npar = (int64_t)pid.size();
+  D.rp_id.upload(pid, s);
+  D.rp_ptr.upload(pptr, s);
+  D.rp_child.upload(child, s);
+  D.fs.alloc(std::max<int64_t>(D.nsm, 1));
+  D.us.alloc(std::max<int64_t>(D.nsm, 1));
+  D.fs.zero(s);
+  D.us.zero(s);
+}
+
+// triangles given by lattice keys -> device coordinates, ids, coefficients
+struct TriDev {
+  DBuf<double> xy, coef;
+  DBuf<int32_t> id;
+};
+
+void upload_tris(const asmg_s& h, const std::vector<uint64_t>& keys, const std::vector<int32_t>& ids,
+                 const std::vector<double>& coef, TriDev& T, cudaStream_t s) {
+  std::vector<double> xy(keys.size() * 2);
+  for (size_t k = 0; k < keys.size(); ++k) lattice_point(h.tree, keys[k], &xy[2 * k]);
+  T.xy.upload(xy, s);
+  T.id.upload(ids, s);
+  T.coef.upload(coef, s);
+}
+
+template <class T>
+void build_prec(asmg_s& h, Prec<T>& P, const HostCSR& Aperm, const std::vector<double>& dinv_perm, cudaStream_t s) {
+  if (std::is_same<T, float>::value) {
+    sell_build<T>(P.Af, Aperm, 0, s);
+    std::vector<T> d(dinv_perm.begin(), dinv_perm.end());
+    P.dinv_f.upload(d, s);
+  }
+  // transfer P (rows: permuted fine rows) and P^T (rows: aux nodes)
+  const Triplets& Tp = h.aux.P;
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(h.npad), trows(h.nJpad);
+    for (size_t k = 0; k < Tp.r.size(); ++k) {
+      int32_t pr = h.row_of_free[Tp.r[k]];
+      rows[pr].push_back({Tp.c[k], Tp.v[k]});
+      trows[Tp.c[k]].push_back({pr, Tp.v[k]});
+    }
+    auto to_csr = [](std::vector<std::vector<std::pair<int32_t, double>>>& rr, int64_t nc) {
+      HostCSR A;
+      A.nr = (int64_t)rr.size();
+      A.nc = nc;
+      A.ptr.assign(A.nr + 1, 0);
+      for (int64_t i = 0; i < A.nr; ++i) {
+        std::sort(rr[i].begin(), rr[i].end());
+        for (auto& e : rr[i]) {
+          A.col.push_back(e.first);
+          A.val.push_back(e.second);
+        }
+        A.ptr[i + 1] = (int64_t)A.col.size();
+      }
+      return A;
+    };
+    HostCSR Pc = to_csr(rows, h.nJpad), Ptc = to_csr(trows, h.npad);
+    sell_build<T>(P.P, Pc, 0, s);
+    sell_build<T>(P.PT, Ptc, 0, s);
+  }
+}
+
+void build_all(asmg_s& h, cudaStream_t s) {
+  double t0 = now();
+  MeshHost& m = h.mesh;
+  const int64_t nv = m.nv, ne = m.ne;
+  // ---- fine problem: free dofs, assembly, colouring, permutation
+  h.free_of_vertex.assign(nv, -1);
+  h.vertex_of_free.clear();
+  for (int64_t v = 0; v < nv; ++v)
+    if (m.bflag[v] == 0) {
+      h.free_of_vertex[v] = (int32_t)h.vertex_of_free.size();
+      h.vertex_of_free.push_back((int32_t)v);
+    }
+  h.n = (int64_t)h.vertex_of_free.size();
+  if (h.n == 0) ASMG_FAIL(ASMG_ERR_BAD_MESH, "no free vertices");
+  h.d_free_of_vertex.upload(h.free_of_vertex, s);
+  h.A_host = assemble_mesh(ne, h.dX.p, h.dE.p, h.d_free_of_vertex.p, h.dCoeff.p, h.n, s);
+  {
+    std::vector<uint8_t> all(h.n, 1);
+    std::vector<uint64_t> pk(h.vertex_of_free.begin(), h.vertex_of_free.end());
+    h.fine_colour = jp_colour_gpu(h.A_host, all, pk, s);
+  }
+  int ncol = 0;
+  for (auto c : h.fine_colour) ncol = std::max(ncol, c + 1);
+  std::vector<int64_t> sel;
+  h.fine_cstart.assign(1, 0);
+  {
+    std::vector<std::vector<int32_t>> byc(ncol);
+    for (int64_t i = 0; i < h.n; ++i) byc[h.fine_colour[i]].push_back((int32_t)i);
+    for (int c = 0; c < ncol; ++c) {
+      for (auto i : byc[c]) sel.push_back(i);
+      while (sel.size() % 32) sel.push_back(-1);
+      h.fine_cstart.push_back((int64_t)sel.size());
+    }
+  }
+  h.npad = (int64_t)sel.size();
+  h.row_of_free.assign(h.n, -1);
+  std::vector<int32_t> vrow(h.npad, -1), rowv(nv, -1);
+  for (int64_t k = 0; k < h.npad; ++k)
+    if (sel[k] >= 0) {
+      h.row_of_free[sel[k]] = (int32_t)k;
+      vrow[k] = h.vertex_of_free[sel[k]];
+      rowv[vrow[k]] = (int32_t)k;
+    }
+  h.d_vertex_of_row.upload(vrow, s);
+  h.d_row_of_vertex.upload(rowv, s);
+  HostCSR Aperm = select_rows(h.A_host, sel, &h.row_of_free, nullptr);
+  std::vector<double> dinv(h.npad, 0.0);
+  for (int64_t k = 0; k < h.npad; ++k)
+    for (int64_t p = Aperm.ptr[k]; p < Aperm.ptr[k + 1]; ++p)
+      if (Aperm.col[p] == k) dinv[k] = 1.0 / Aperm.val[p];
+  sell_build<double>(h.A64, Aperm, 0, s);
+  h.dinv64.upload(dinv, s);
+  h.stats.t_fine = now() - t0;
+
+  // ---- auxiliary hierarchy (host), transfer
+  double t1 = now();
+  h.aux = AuxHost();
+  build_aux_host(m, h.tree, h.prm, h.free_of_vertex, h.aux);
+  h.stats.t_aux = now() - t1;
+  double t2 = now();
+  h.nJ = (int64_t)h.aux.aux_key.size();
+  h.nJpad = pad32(h.nJ);
+
+  // ---- auxiliary levels: device assembly, colouring, SELL
+  h.level_smooth_keys.clear();
+  h.level_smooth_colour.clear();
+  h.level_rows.clear();
+  h.p64.lev.clear();
+  h.p32.lev.clear();
+  for (const AuxLevelHost& L : h.aux.levels) {
+    std::vector<uint8_t> inset(h.nJ, 0);
+    for (int32_t id : L.smooth) inset[id] = 1;
+    TriDev T;
+    upload_tris(h, L.tri_key, L.tri_id, L.tri_coef, T, s);
+    DBuf<uint8_t> dkeep;
+    dkeep.upload(inset, s);
+    HostCSR Arows = assemble_triangles((int64_t)L.tri_coef.size(), T.xy.p, T.id.p, T.coef.p, dkeep.p, h.nJ, s);
+    std::vector<int32_t> colour = jp_colour_gpu(Arows, inset, h.aux.aux_key, s);
+    // export copies
+    std::vector<uint64_t> sk;
+    std::vector<int32_t> sc;
+    for (int32_t id : L.smooth) {
+      sk.push_back(h.aux.aux_key[id]);
+      sc.push_back(colour[id]);
+    }
+    h.level_smooth_keys.push_back(sk);
+    h.level_smooth_colour.push_back(sc);
+    Triplets tr;
+    for (int64_t i = 0; i < Arows.nr; ++i)
+      for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1]; ++p) {
+        tr.r.push_back((int32_t)i);
+        tr.c.push_back(Arows.col[p]);
+        tr.v.push_back(Arows.val[p]);
+      }
+    h.level_rows.push_back(std::move(tr));
+    if (h.prm.precision == ASMG_MIXED) {
+      h.p32.lev.emplace_back();
+      build_level_dev<float>(h, L, Arows, colour, inset, h.p32.lev.back(), s);
+    } else {
+      h.p64.lev.emplace_back();
+      build_level_dev<double>(h, L, Arows, colour, inset, h.p64.lev.back(), s);
+    }
+  }
+  // ---- coarsest level: explicit inverse of A_c (B_0 = A_0^{-1})
+  h.nc = (int64_t)h.aux.coarse_id.size();
+  if (h.nc > 0) {
+    std::vector<int32_t> loc(h.aux.coarse_tri_id.size());
+    for (size_t k = 0; k < loc.size(); ++k) {
+      int32_t id = h.aux.coarse_tri_id[k];
+      loc[k] = id < 0 ? -1
+                      : (int32_t)(std::lower_bound(h.aux.coarse_id.begin(), h.aux.coarse_id.end(), id) -
+                                  h.aux.coarse_id.begin());
+    }
+    TriDev T;
+    upload_tris(h, h.aux.coarse_tri_key, loc, h.aux.coarse_tri_coef, T, s);
+    HostCSR Ac = assemble_triangles((int64_t)h.aux.coarse_tri_coef.size(), T.xy.p, T.id.p, T.coef.p, nullptr, h.nc, s);
+    const int64_t n = h.nc;
+    std::vector<double> M(n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = Ac.ptr[i]; p < Ac.ptr[i + 1]; ++p) M[i * n + Ac.col[p]] = Ac.val[p];
+    // Cholesky M = L L^T (lower, in place)
+    for (int64_t j = 0; j < n; ++j) {
+      double d = M[j * n + j];
+      for (int64_t k = 0; k < j; ++k) d -= M[j * n + k] * M[j * n + k];
+      if (!(d > 0)) ASMG_FAIL(ASMG_ERR_CUDA, "coarsest auxiliary matrix is not positive definite");
+      d = std::sqrt(d);
+      M[j * n + j] = d;
+      for (int64_t i = j + 1; i < n; ++i) {
+        double t = M[i * n + j];
+        for (int64_t k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
+        M[i * n + j] = t / d;
+      }
+    }
+    // inverse column by column: solve L L^T x = e_c
+    std::vector<double> inv(n * n), y(n);
+    for (int64_t c = 0; c < n; ++c) {
+      for (int64_t i = 0; i < n; ++i) {
+        double t = (i == c) ? 1.0 : 0.0;
+        for (int64_t k = 0; k < i; ++k) t -= M[i * n + k] * y[k];
+        y[i] = t / M[i * n + i];
+      }
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double t = y[i];
+        for (int64_t k = i + 1; k < n; ++k) t -= M[k * n + i] * inv[k * n + c];
+        inv[i * n + c] = t / M[i * n + i];
+      }
+    }
+    h.d_cinv.upload(inv, s);
+    h.d_cid.upload(h.aux.coarse_id, s);
+  }
+  // ---- transfer and fine smoother copy
+  if (h.prm.precision == ASMG_MIXED)
+    build_prec<float>(h, h.p32, Aperm, dinv, s);
+  else
+    build_prec<double>(h, h.p64, Aperm, dinv, s);
+  setup_solve(h, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  h.stats.t_levels = now() - t2;
+  if (h.gexec) {
+    cudaGraphExecDestroy(h.gexec);
+    h.gexec = nullptr;
+  }
+  if (h.graph) {
+    cudaGraphDestroy(h.graph);
+    h.graph = nullptr;
+  }
+}
+
+// algorithmic bytes of one PCG iteration (compulsory traffic, real non-zeros)
+template <class T>
+int64_t iteration_bytes(const asmg_s& h, const Prec<T>& P) {
+  const int64_t s = sizeof(T), n = h.n, nJ = h.nJ;
+  const int64_t nnzA = h.A64.nnz_real;
+  int64_t b = 0;
+  b += nnzA * 12 + 16 * n;                  // q = A p, <p, q>
+  b += 48 * n;                              // x += a p, r -= a q, ||r||
+  b += (s + 16) * n;                        // <z, r>, <z, q>
+  b += (s + 16) * n;                        // p = z + beta p
+  b += 2 * (nnzA * (s + 4) + 8 * n + 2 * s * n);  // two fine sweeps
+  if (nJ > 0) {
+    b += nnzA * (s + 4) + 8 * n + 2 * s * n;  // fine residual
+    b += (P.PT.nnz_real) * (s + 4) + s * n + 2 * s * nJ;  // P^T
+    b += (P.P.nnz_real) * (s + 4) + s * nJ + 2 * s * n;   // P
+    for (auto& L : P.lev) {
+      const int64_t m = L.nsm_real;
+      b += (h.prm.nu_pre + h.prm.nu_post) * (L.SM.nnz_real * (s + 4) + m * (4 + 3 * s));
+      b += L.RS.nnz_real * (s + 4) + L.nrs * (4 + 2 * s);
+      b += 2 * m * (4 + 2 * s) + L.nnew * (12 + 3 * s);
+    }
+    b += h.nc * h.nc * 8 + h.nc * (4 + 2 * s);
+  }
+  return b;
+}
+
+int finish(int rc) { return rc; }
+
+}  // namespace
+
+namespace asmg {
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+}  // namespace asmg
+
+#define API_BEGIN \
+  g_err.clear();  \
+  try {
+#define API_END                                   \
+  }                                               \
+  catch (const asmg::Error& e) {                  \
+    g_err = e.msg;                                \
+    return e.code;                                \
+  }                                               \
+  catch (const std::exception& e) {               \
+    g_err = std::string("internal error: ") + e.what(); \
+    return ASMG_ERR_CUDA;                         \
+  }
+
+extern "C" {
+
+const char* amg_last_error(void) { return g_err.c_str(); }
+
+int asmg_default_params(asmg_params* p) {
+  if (!p) return ASMG_ERR_INVALID_ARG;
+  p->n_min = 3;
+  p->nu_pre = 2;
+  p->nu_post = 2;
+  p->coarse_max_dofs = 512;
+  p->precision = ASMG_FP64;
+  p->max_iter = 500;
+  p->smoothing = 0;
+  p->use_graph = 1;
+  return ASMG_OK;
+}
+
+int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int32_t* elements, const uint8_t* boundary,
+              const double* coeff, const asmg_params* params, void* stream, asmg_handle* out) {
+  API_BEGIN
+  if (!out) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!vertices || !elements || !boundary) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null input array");
+  if (nv <= 0 || ne <= 0) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "nv and ne must be positive");
+  if (dim != 2) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "dim %d not supported (2D triangles only)", dim);
+  if (ne > (1LL << 31) / 9 || nv > (1LL << 31) - 1) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "mesh too large");
+  asmg_params prm;
+  asmg_default_params(&prm);
+  if (params) prm = *params;
+  if (prm.n_min < 1 || prm.nu_pre < 1 || prm.nu_post < 0 || prm.coarse_max_dofs < 1 || prm.max_iter < 1 ||
+      (prm.precision != ASMG_FP64 && prm.precision != ASMG_MIXED) || (prm.smoothing != 0 && prm.smoothing != 1) ||
+      prm.coarse_max_dofs > 8192)
+    ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
+  cudaStream_t s = (cudaStream_t)stream;
+  double t0 = now();
+  std::unique_ptr<asmg_s> h(new asmg_s());
+  h->prm = prm;
+  MeshHost& m = h->mesh;
+  m.dim = dim;
+  m.nv = nv;
+  m.ne = ne;
+  m.X = to_host(vertices, nv * dim, s);
+  m.E = to_host(elements, ne * (dim + 1), s);
+  m.bflag = to_host(boundary, nv, s);
+  if (coeff) m.coeff = to_host(coeff, ne, s);
+  for (int64_t v = 0; v < nv; ++v) {
+    if (m.bflag[v] == 2) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "Neumann vertices are not supported");
+    if (m.bflag[v] > 2) ASMG_FAIL(ASMG_ERR_BAD_MESH, "boundary flag %d at vertex %lld", (int)m.bflag[v], (long long)v);
+  }
+  for (int64_t e = 0; e < (int64_t)m.coeff.size(); ++e)
+    if (!(m.coeff[e] > 0) || !std::isfinite(m.coeff[e]))
+      ASMG_FAIL(ASMG_ERR_BAD_MESH, "coefficient of element %lld is not positive and finite", (long long)e);
+  h->dX.upload(m.X, s);
+  h->dE.upload(m.E, s);
+  if (!m.coeff.empty()) h->dCoeff.upload(m.coeff, s);
+  // cluster tree (also checks index range and orientation)
+  double tt = now();
+  build_tree_gpu(dim, nv, h->dX.p, ne, h->dE.p, prm.n_min, s, h->tree);
+  h->stats.t_tree = now() - tt;
+  // the domain must fill the root box (box domains only)
+  {
+    double area = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+      const int32_t* v = &m.E[3 * e];
+      area += 0.5 * ((m.X[2 * v[1]] - m.X[2 * v[0]]) * (m.X[2 * v[2] + 1] - m.X[2 * v[0] + 1]) -
+                     (m.X[2 * v[2]] - m.X[2 * v[0]]) * (m.X[2 * v[1] + 1] - m.X[2 * v[0] + 1]));
+    }
+    double box = h->tree.L * h->tree.L;
+    if (std::fabs(area - box) > 1e-12 * box)
+      ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "the domain is not the square spanned by the vertices (area %.17g vs %.17g)", area,
+                box);
+  }
+  build_all(*h, s);
+  h->bytes_iter = prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
+  h->stats.t_total = now() - t0;
+  *out = h.release();
+  return ASMG_OK;
+  API_END
+}
+
+void amg_destroy(asmg_handle h) { delete h; }
+
+int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* iterations, double* res_history,
+              void* stream) {
+  API_BEGIN
+  if (!h || !b || !u || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  if (!(rtol >= 0) || !std::isfinite(rtol)) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "rtol must be finite and >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv;
+  copy_in(h->vb.p, b, nv, s);
+  copy_in(h->vu.p, u, nv, s);
+  gather_rows(*h, h->vb.p, h->b.p, s);
+  gather_rows(*h, h->vu.p, h->x.p, s);
+  run_solve(*h, rtol, s);
+  scatter_rows(*h, h->x.p, false, h->vu.p, s);
+  copy_out(u, h->vu.p, nv, s);
+  PcgScalars sc;
+  ASMG_CUDA(cudaMemcpyAsync(&sc, h->scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  *iterations = sc.k;
+  if (res_history) {
+    ASMG_CUDA(cudaMemcpyAsync(res_history, h->hist.p, 8 * (size_t)(sc.k + 1), cudaMemcpyDeviceToHost, s));
+    ASMG_CUDA(cudaStreamSynchronize(s));
+  }
+  if (sc.status == ASMG_ERR_BREAKDOWN) {
+    g_err = "PCG breakdown: <p, A p> or <r, z> not positive";
+    return ASMG_ERR_BREAKDOWN;
+  }
+  return sc.status == 0 ? ASMG_OK : ASMG_NOT_CONVERGED;
+  API_END
+}
+
+int amg_mass_apply(asmg_handle h, const double* f, double* bout, void* stream) {
+  API_BEGIN
+  if (!h || !f || !bout) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv;
+  copy_in(h->vb.p, f, nv, s);
+  mass_apply_gpu(h->mesh.ne, h->dX.p, h->dE.p, h->vb.p, h->vu.p, nv, s);
+  gather_rows(*h, h->vu.p, h->q.p, s);
+  scatter_rows(*h, h->q.p, false, h->vu.p, s);  // zero at Dirichlet vertices
+  copy_out(bout, h->vu.p, nv, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return ASMG_OK;
+  API_END
+}
+
+int amg_precond_apply(asmg_handle h, const double* r, double* z, void* stream) {
+  API_BEGIN
+  if (!h || !r || !z) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv;
+  copy_in(h->vb.p, r, nv, s);
+  gather_rows(*h, h->vb.p, h->r.p, s);
+  precond_apply(*h, h->r.p, s);
+  if (h->prm.precision == ASMG_MIXED)
+    scatter_rows(*h, h->p32.uf.p, true, h->vu.p, s);
+  else
+    scatter_rows(*h, h->p64.uf.p, false, h->vu.p, s);
+  copy_out(z, h->vu.p, nv, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return ASMG_OK;
+  API_END
+}
+
+int amg_spmv(asmg_handle h, const double* x, double* y, void* stream) {
+  API_BEGIN
+  if (!h || !x || !y) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv;
+  copy_in(h->vb.p, x, nv, s);
+  gather_rows(*h, h->vb.p, h->p.p, s);
+  spmv64(*h, h->p.p, h->q.p, s);
+  scatter_rows(*h, h->q.p, false, h->vu.p, s);
+  copy_out(y, h->vu.p, nv, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return ASMG_OK;
+  API_END
+}
+
+int amg_element_grad(asmg_handle h, const double* u, const double* lambda, double* g, void* stream) {
+  API_BEGIN
+  if (!h || !u || !lambda || !g) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv, ne = h->mesh.ne;
+  // Dirichlet entries are treated as 0: gather/scatter through the free rows
+  copy_in(h->vb.p, u, nv, s);
+  gather_rows(*h, h->vb.p, h->p.p, s);
+  scatter_rows(*h, h->p.p, false, h->vb.p, s);
+  copy_in(h->vu.p, lambda, nv, s);
+  gather_rows(*h, h->vu.p, h->q.p, s);
+  scatter_rows(*h, h->q.p, false, h->vu.p, s);
+  DBuf<double> dg;
+  const bool dev = is_device(g);
+  double* out = g;
+  if (!dev) {
+    dg.alloc(ne);
+    out = dg.p;
+  }
+  element_grad_gpu(ne, h->dX.p, h->dE.p, h->vb.p, h->vu.p, out, s);
+  if (!dev) ASMG_CUDA(cudaMemcpyAsync(g, dg.p, 8 * ne, cudaMemcpyDeviceToHost, s));
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return ASMG_OK;
+  API_END
+}
+
+int amg_update_coefficients(asmg_handle h, const double* coeff, void* stream) {
+  API_BEGIN
+  if (!h || !coeff) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> c = to_host(coeff, h->mesh.ne, s);
+  for (int64_t e = 0; e < h->mesh.ne; ++e)
+    if (!(c[e] > 0) || !std::isfinite(c[e]))
+      ASMG_FAIL(ASMG_ERR_BAD_MESH, "coefficient of element %lld is not positive and finite", (long long)e);
+  h->mesh.coeff = c;
+  h->dCoeff.upload(c, s);
+  build_all(*h, s);
+  h->bytes_iter = h->prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
+  return ASMG_OK;
+  API_END
+}
+
+int amg_info(asmg_handle h, int what, int level, int64_t* value) {
+  API_BEGIN
+  if (!h || !value) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  auto lev_index = [&](int l) -> int {
+    int k = l - (h->aux.c + 1);
+    if (k < 0 || k >= (int)h->aux.levels.size()) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "level %d has no smoothing data", l);
+    return k;
+  };
+  auto nsm = [&](int k) -> int64_t {
+    return h->prm.precision == ASMG_MIXED ? h->p32.lev[k].nsm_real : h->p64.lev[k].nsm_real;
+  };
+  switch (what) {
+    case ASMG_INFO_NFREE: *value = h->n; break;
+    case ASMG_INFO_J: *value = h->aux.J; break;
+    case ASMG_INFO_COARSE: *value = h->aux.c; break;
+    case ASMG_INFO_NAUX:
+      if (level < 0 || level > h->aux.J) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
+      *value = h->aux.nlevel[level];
+      break;
+    case ASMG_INFO_NSMOOTH: *value = level < 0 ? h->n : nsm(lev_index(level)); break;
+    case ASMG_INFO_NCOLOURS:
+      if (level < 0) {
+        *value = (int64_t)h->fine_cstart.size() - 1;
+      } else {
+        int k = lev_index(level);
+        *value = h->prm.precision == ASMG_MIXED ? h->p32.lev[k].ncolours : h->p64.lev[k].ncolours;
+      }
+      break;
+    case ASMG_INFO_NTREE_LEVELS: *value = (int64_t)h->tree.seg.size(); break;
+    case ASMG_INFO_NSEG:
+      if (level < 0 || level >= (int)h->tree.seg.size()) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
+      *value = (int64_t)h->tree.seg[level].size() / 4;
+      break;
+    case ASMG_INFO_NSPLIT:
+      if (level < 0 || level >= (int)h->aux.split.size()) *value = 0;
+      else *value = (int64_t)h->aux.split[level].size();
+      break;
+    case ASMG_INFO_NNZ_A: *value = h->A64.nnz_real; break;
+    case ASMG_INFO_NNZ_P: *value = (int64_t)h->aux.P.r.size(); break;
+    case ASMG_INFO_NROWS_E: {
+      int k = lev_index(level);
+      *value = h->prm.precision == ASMG_MIXED ? h->p32.lev[k].nrs : h->p64.lev[k].nrs;
+      break;
+    }
+    case ASMG_INFO_BYTES_ITER: *value = h->bytes_iter; break;
+    case ASMG_INFO_NNZ_LEVEL: {
+      int k = lev_index(level);
+      *value = h->prm.precision == ASMG_MIXED ? h->p32.lev[k].SM.nnz_real + h->p32.lev[k].RS.nnz_real
+                                              : h->p64.lev[k].SM.nnz_real + h->p64.lev[k].RS.nnz_real;
+      break;
+    }
+    case 100: *value = h->gpu_launches_per_iter; break;
+    case 101: *value = (int64_t)(h->stats.t_total * 1e6); break;
+    case 102: *value = (int64_t)(h->stats.t_tree * 1e6); break;
+    case 103: *value = (int64_t)(h->stats.t_aux * 1e6); break;
+    case 104: *value = (int64_t)(h->stats.t_fine * 1e6); break;
+    case 105: *value = (int64_t)(h->stats.t_levels * 1e6); break;
+    default: ASMG_FAIL(ASMG_ERR_INVALID_ARG, "unknown info %d", what);
+  }
+  return ASMG_OK;
+  API_END
+}
+
+int amg_export(asmg_handle h, int what, int level, void* buf, int64_t* count) {
+  API_BEGIN
+  if (!h || !count) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = 0;
+  auto put = [&](const void* src, int64_t n, size_t elem) {
+    *count = n;
+    if (buf && n) std::memcpy(buf, src, elem * n);
+  };
+  auto trip = [&](const std::vector<uint64_t>& a, const std::vector<uint64_t>& b2, const std::vector<double>& v) {
+    *count = (int64_t)v.size();
+    if (!buf) return;
+    char* o = (char*)buf;
+    for (size_t k = 0; k < v.size(); ++k) {
+      std::memcpy(o + 24 * k, &a[k], 8);
+      std::memcpy(o + 24 * k + 8, &b2[k], 8);
+      std::memcpy(o + 24 * k + 16, &v[k], 8);
+    }
+  };
+  switch (what) {
+    case ASMG_EXPORT_KEYS: {
+      auto k = h->tree.keys.download(s);
+      put(k.data(), (int64_t)k.size(), 8);
+      break;
+    }
+    case ASMG_EXPORT_PERM: {
+      auto k = h->tree.perm.download(s);
+      put(k.data(), (int64_t)k.size(), 4);
+      break;
+    }
+    case ASMG_EXPORT_SEG:
+      if (level < 0 || level >= (int)h->tree.seg.size()) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
+      put(h->tree.seg[level].data(), (int64_t)h->tree.seg[level].size(), 8);
+      break;
+    case ASMG_EXPORT_SPLIT:
+      if (level < 0 || level >= (int)h->aux.split.size()) {
+        *count = 0;
+      } else {
+        put(h->aux.split[level].data(), (int64_t)h->aux.split[level].size(), 8);
+      }
+      break;
+    case ASMG_EXPORT_AUX_KEYS: put(h->aux.aux_key.data(), (int64_t)h->aux.aux_key.size(), 8); break;
+    case ASMG_EXPORT_FINE_COLOUR: put(h->fine_colour.data(), (int64_t)h->fine_colour.size(), 4); break;
+    case ASMG_EXPORT_SMOOTH: {
+      int k = level - (h->aux.c + 1);
+      if (k < 0 || k >= (int)h->level_smooth_keys.size()) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
+      std::vector<uint64_t> v;
+      for (size_t i = 0; i < h->level_smooth_keys[k].size(); ++i) {
+        v.push_back(h->level_smooth_keys[k][i]);
+        v.push_back((uint64_t)h->level_smooth_colour[k][i]);
+      }
+      put(v.data(), (int64_t)v.size(), 8);
+      break;
+    }
+    case ASMG_EXPORT_LEVEL_ROWS: {
+      int k = level - (h->aux.c + 1);
+      std::vector<uint64_t> a, b2;
+      std::vector<double> v;
+      if (level == h->aux.c) {
+        // coarsest level: full matrix from its triangles is not stored; export the inverse's source is not kept
+        ASMG_FAIL(ASMG_ERR_INVALID_ARG, "the coarsest level keeps only its inverse");
+      }
+      if (k < 0 || k >= (int)h->level_rows.size()) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
+      const Triplets& t = h->level_rows[k];
+      for (size_t q = 0; q < t.v.size(); ++q) {
+        a.push_back(h->aux.aux_key[t.r[q]]);
+        b2.push_back(h->aux.aux_key[t.c[q]]);
+        v.push_back(t.v[q]);
+      }
+      trip(a, b2, v);
+      break;
+    }
+    case ASMG_EXPORT_P: {
+      std::vector<uint64_t> a, b2;
+      std::vector<double> v;
+      const Triplets& t = h->aux.P;
+      for (size_t q = 0; q < t.v.size(); ++q) {
+        a.push_back((uint64_t)h->vertex_of_free[t.r[q]]);
+        b2.push_back(h->aux.aux_key[t.c[q]]);
+        v.push_back(t.v[q]);
+      }
+      trip(a, b2, v);
+      break;
+    }
+    case ASMG_EXPORT_FINE_A: {
+      std::vector<uint64_t> a, b2;
+      std::vector<double> v;
+      const HostCSR& A = h->A_host;
+      for (int64_t i = 0; i < A.nr; ++i)
+        for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+          a.push_back((uint64_t)h->vertex_of_free[i]);
+          b2.push_back((uint64_t)h->vertex_of_free[A.col[p]]);
+          v.push_back(A.val[p]);
+        }
+      trip(a, b2, v);
+      break;
+    }
+    default: ASMG_FAIL(ASMG_ERR_INVALID_ARG, "unknown export %d", what);
+  }
+  return ASMG_OK;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// The solver handle: everything amg_setup keeps on the device.
+#pragma once
+
+#include "internal.h"
+
+namespace asmg {
+
+template <class T>
+struct SellView {
+  const int64_t* off = nullptr;
+  const int32_t* col = nullptr;
+  const T* val = nullptr;
+};
+
+template <class T>
+SellView<T> view(const Sell<T>& S) {
+  return SellView<T>{S.off.p, S.col.p, S.val.p};
+}
+
+// Scalars of the PCG recurrences, device resident.
+struct PcgScalars {
+  double rz;      // <r_k, z_k>
+  double alpha, beta, pq, rr, bnorm, tol;
+  int k, maxit, status, cond;
+};
+
+// Preconditioner data in the precision T of the smoother and V-cycle.
+template <class T>
+struct Prec {
+  Sell<T> Af;                  // fine smoother matrix (mixed mode only; FP64 mode uses A64)
+  DBuf<T> dinv_f;
+  Sell<T> P, PT;               // Scott-Zhang transfer and its transpose
+  std::vector<AuxLevelDev<T>> lev;  // levels c+1..J (index 0 = c+1)
+  DBuf<T> uf, rho, F, U;       // fine work vector, fine residual, aux rhs / solution
+};
+
+}  // namespace asmg
+
+struct asmg_s {
+  asmg_params prm{};
+  asmg::MeshHost mesh;
+  asmg::DBuf<double> dX, dCoeff;
+  asmg::DBuf<int32_t> dE;
+  asmg::TreeResult tree;
+  asmg::AuxHost aux;
+
+  // fine grid
+  int64_t n = 0, npad = 0;
+  std::vector<int32_t> free_of_vertex, vertex_of_free, fine_colour, row_of_free;
+  std::vector<int64_t> fine_cstart;      // colour blocks in permuted rows (multiples of 32)
+  asmg::HostCSR A_host;                  // fine A, free-dof numbering (for export)
+  asmg::Sell<double> A64;
+  asmg::DBuf<double> dinv64;
+  asmg::DBuf<int32_t> d_vertex_of_row, d_row_of_vertex, d_free_of_vertex;
+
+  // auxiliary space
+  int64_t nJ = 0, nJpad = 0, nc = 0;
+  asmg::DBuf<int32_t> d_cid;
+  asmg::DBuf<double> d_cinv;             // explicit inverse of the coarsest operator
+  std::vector<std::vector<uint64_t>> level_smooth_keys;  // per level: node keys (export)
+  std::vector<std::vector<int32_t>> level_smooth_colour;
+  std::vector<asmg::Triplets> level_rows;                // per level: assembled rows (export)
+  asmg::Prec<double> p64;
+  asmg::Prec<float> p32;
+
+  // PCG state
+  asmg::DBuf<double> b, x, r, p, q;      // permuted, padded
+  asmg::DBuf<double> zd;                  // z in FP64 mode aliases p64.uf
+  asmg::DBuf<double> vb, vu;              // vertex-ordered staging for user arrays
+  asmg::DBuf<double> partial;
+  asmg::DBuf<unsigned int> ticket;
+  asmg::DBuf<asmg::PcgScalars> scal;
+  asmg::DBuf<double> hist;
+
+  // CUDA graph of the whole solve
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double graph_rtol = -1;
+  int64_t bytes_iter = 0;
+  asmg::Stats stats;
+  int gpu_launches_per_iter = 0;
+
+  ~asmg_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+namespace asmg {
+// solve.cu
+void setup_solve(asmg_s& h, cudaStream_t s);
+int run_solve(asmg_s& h, double rtol, cudaStream_t s);
+void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s);  // result in h.p*.uf
+void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);
+void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s);
+void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cudaStream_t s);
+// assemble.cu
+HostCSR assemble_mesh(int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree, const double* dCoef,
+                      int64_t nfree, cudaStream_t s);
+void mass_apply_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
+                    cudaStream_t s);
+void element_grad_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl, double* dg,
+                      cudaStream_t s);
+}  // namespace asmg

@@ -1,0 +1,210 @@
+// Internal declarations shared by the translation units of libasmg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/asmg.h"
+
+namespace asmg {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define ASMG_CUDA(call)                                                                          \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      throw ::asmg::Error{e_ == cudaErrorMemoryAllocation ? ASMG_ERR_OOM : ASMG_ERR_CUDA,        \
+                          std::string(#call) + ": " + cudaGetErrorString(e_)};                   \
+  } while (0)
+
+#define ASMG_FAIL(code, ...)                                                                     \
+  do {                                                                                           \
+    char b_[512];                                                                                \
+    snprintf(b_, sizeof b_, __VA_ARGS__);                                                        \
+    throw ::asmg::Error{code, b_};                                                               \
+  } while (0)
+
+// ------------------------------------------------------- device buffers
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  int64_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(int64_t count) {
+    release();
+    n = count;
+    if (count > 0) ASMG_CUDA(cudaMalloc((void**)&p, sizeof(T) * (size_t)count));
+  }
+  void zero(cudaStream_t s) {
+    if (n) ASMG_CUDA(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, s));
+  }
+  void upload(const std::vector<T>& h, cudaStream_t s) {
+    alloc((int64_t)h.size());
+    if (n) ASMG_CUDA(cudaMemcpyAsync(p, h.data(), sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s) const {
+    std::vector<T> h((size_t)n);
+    if (n) ASMG_CUDA(cudaMemcpyAsync(h.data(), p, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    ASMG_CUDA(cudaStreamSynchronize(s));
+    return h;
+  }
+  size_t bytes() const { return sizeof(T) * (size_t)n; }
+};
+
+// ---------------------------------------------------- host sparse rows
+struct Triplets {  // row, col, value (host)
+  std::vector<int32_t> r, c;
+  std::vector<double> v;
+};
+
+struct HostCSR {
+  int64_t nr = 0, nc = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+
+// SELL-32: rows in slices of 32; element k of row (32 s + t) at
+// off[s] + 32 k + t.  Padding entries have col = pad_col, val = 0.
+constexpr int SELL_C = 32;
+
+template <class T>
+struct Sell {
+  int64_t nrows = 0;   // multiple of 32
+  int64_t nslices = 0;
+  int64_t nnz = 0;     // stored (padded) entries
+  int64_t nnz_real = 0;
+  DBuf<int64_t> off;   // [nslices + 1]
+  DBuf<int32_t> col;   // [nnz]
+  DBuf<T> val;         // [nnz]
+};
+
+// Build SELL-32 from host rows given as CSR in the SELL row order
+// (row k of `rows` is SELL row k; rows.nr need not be a multiple of 32).
+template <class T>
+void sell_build(Sell<T>& S, const HostCSR& rows, int32_t pad_col, cudaStream_t s);
+
+// --------------------------------------------------------------- tree
+struct TreeResult {
+  double amin[3] = {0, 0, 0};
+  double L = 0;
+  int D = 31;
+  std::vector<std::vector<int64_t>> seg;       // per depth: prefix, begin, end, split (4 per node)
+  std::vector<std::vector<uint64_t>> split;    // per depth: sorted prefixes of split nodes
+  DBuf<uint64_t> keys;                         // element keys (element order)
+  DBuf<int32_t> perm;                          // elements sorted by key
+};
+
+// --------------------------------------------------------- aux hierarchy
+// One auxiliary level above the coarsest (host description, aux node IDs
+// index the free nodes of the finest level in lattice Morton order).
+struct AuxLevelHost {
+  int level = 0;
+  std::vector<int32_t> smooth;            // N~_l, ascending aux ID
+  std::vector<int32_t> new_id, new_p0, new_p1;  // new nodes and their parents (-1 = Dirichlet)
+  // assembly input: triangles (aux IDs, -1 = Dirichlet) with lattice corners
+  std::vector<int32_t> tri_id;            // [ntri * 3]
+  std::vector<uint64_t> tri_key;          // [ntri * 3] lattice Morton keys
+  std::vector<double> tri_coef;           // [ntri]
+};
+
+struct AuxHost {
+  int J = 0, c = 0;
+  std::vector<std::vector<uint64_t>> split;   // closed tree: split prefixes per depth (sorted)
+  std::vector<uint64_t> aux_key;               // free finest-level nodes, ascending key
+  std::vector<int64_t> nlevel;                 // free nodes per level 0..J
+  std::vector<AuxLevelHost> levels;            // levels c+1..J
+  std::vector<int32_t> coarse_id;              // free nodes of level c (aux IDs)
+  std::vector<int32_t> coarse_tri_id;          // triangles of level c
+  std::vector<uint64_t> coarse_tri_key;
+  std::vector<double> coarse_tri_coef;
+  Triplets P;                                  // (free fine dof, aux ID, value)
+};
+
+struct MeshHost {
+  int dim = 2;
+  int64_t nv = 0, ne = 0;
+  std::vector<double> X;
+  std::vector<int32_t> E;
+  std::vector<uint8_t> bflag;
+  std::vector<double> coeff;  // empty: a = 1
+};
+
+// closure of the cluster tree, auxiliary grids and the Scott-Zhang transfer
+void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
+                    const std::vector<int32_t>& free_of_vertex, AuxHost& out);
+
+// physical coordinate of a lattice key
+void lattice_point(const TreeResult& t, uint64_t key, double* p);
+uint64_t lattice_key2(uint64_t x, uint64_t y);
+void lattice_xy2(uint64_t key, uint64_t& x, uint64_t& y);
+
+// ----------------------------------------------------------------- GPU setup
+void build_tree_gpu(int dim, int64_t nv, const double* dX, int64_t ne, const int32_t* dE, int n_min,
+                    cudaStream_t s, TreeResult& out);
+
+// Assemble sum of element matrices into CSR on the device and download.
+//   dim-2 triangles given by vertex coordinates (dXY [3*ntri*2]) and row/col
+//   ids (dID [3*ntri], < 0 dropped), coefficient per triangle; entries are
+//   kept only where keep(row) || keep(col) (keep == nullptr keeps all).
+HostCSR assemble_triangles(int64_t ntri, const double* dXY, const int32_t* dID, const double* dCoef,
+                           const uint8_t* dKeep, int64_t nrows, cudaStream_t s);
+
+// Jones-Plassmann colouring of the rows in `set` (CSR adjacency over all rows,
+// priorities splitmix64(key)); returns colour per row (-1 outside the set).
+std::vector<int32_t> jp_colour_gpu(const HostCSR& A, const std::vector<uint8_t>& inset,
+                                   const std::vector<uint64_t>& prio_key, cudaStream_t s);
+
+// ------------------------------------------------------------ solve data
+template <class T>
+struct AuxLevelDev {
+  int level = 0;
+  int ncolours = 0;
+  std::vector<int64_t> cstart;   // colour class starts in SM rows (multiples of 32)
+  int64_t nsm = 0, nsm_real = 0; // padded / real smoothing rows
+  DBuf<int32_t> sm_rows;         // aux ID per SM row (-1 padding)
+  Sell<T> SM;                    // A_l rows of N~_l (all columns)
+  DBuf<T> sm_dinv;
+  int64_t nrs = 0;
+  DBuf<int32_t> rs_rows;         // aux ID per residual row
+  Sell<T> RS;                    // A_l rows of E_l, columns in N~_l only
+  int64_t nnew = 0;
+  DBuf<int32_t> nn_id, nn_p0, nn_p1;  // prolongation of new nodes
+  int64_t npar = 0;
+  DBuf<int32_t> rp_id;           // parents receiving restricted residuals
+  DBuf<int32_t> rp_ptr, rp_child;
+  DBuf<T> fs, us;                // saved rhs / pre-smoothed values on N~_l
+};
+
+struct Stats {
+  double t_tree = 0, t_aux = 0, t_fine = 0, t_levels = 0, t_total = 0;
+};
+
+}  // namespace asmg
+
+// ------------------------------------------------------------------ handle
+struct asmg_s;

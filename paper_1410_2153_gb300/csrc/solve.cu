@@ -1,0 +1,602 @@
+// The solve phase on the device: PCG (Sec. 5.2) preconditioned by the
+// multiplicative auxiliary-space preconditioner (Algorithm 1) whose
+// auxiliary correction is the V-cycle of Algorithm 2 on the nested grids.
+//
+// Layout.  Fine vectors live in a permuted, padded order: free dofs grouped
+// by colour, each colour block padded to a multiple of 32 rows, so a colour
+// sweep is one contiguous range of SELL-32 slices.  Auxiliary vectors are
+// indexed by the free nodes of the finest auxiliary level (lattice Morton
+// order); every coarser level's nodes are a subset, so one rhs vector F and
+// one correction vector U serve all levels and the V-cycle updates them in
+// place:
+//   down, level l:  save F on N~_l (first pre-sweep), nu_pre forward sweeps
+//                   of U on N~_l, F -= A_l U on the rows E_l touched by N~_l,
+//                   F[parent] += 1/2 F[new child] (I_l^T), save and clear U
+//                   on N~_l;
+//   coarsest:       U = A_c^{-1} F on its nodes (explicit FP64 inverse);
+//   up, level l:    U[new] = (U[p0] + U[p1]) / 2 (I_l), U += saved values,
+//                   nu_post backward sweeps with the saved F.
+// New nodes are midpoints of coarse edges (Sec. 3.3), hence the 1/2 weights.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "handle.h"
+
+namespace asmg {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
+
+int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
+
+template <class T, class X>
+__device__ __forceinline__ T sell_dot(int64_t row, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                      const T* __restrict__ val, const X* x) {
+  const int64_t sl = row >> 5, lane = row & 31;
+  const int64_t b = __ldg(off + sl), w = (__ldg(off + sl + 1) - b) >> 5;
+  T s = 0;
+  for (int64_t k = 0; k < w; ++k) {
+    const int64_t e = b + (k << 5) + lane;
+    s += __ldg(val + e) * (T)x[__ldg(col + e)];
+  }
+  return s;
+}
+
+// ------------------------------------------------------------- fine grid
+// one colour of a Gauss-Seidel sweep: u_i += (rhs_i - (A u)_i) / a_ii
+template <class T, class R>
+__global__ void k_gs_fine(int64_t r0, int64_t nrows, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                          const T* __restrict__ val, const T* __restrict__ dinv, const R* __restrict__ rhs, T* u) {
+  const int64_t i = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= r0 + nrows) return;
+  T s = (T)rhs[i] - sell_dot<T, T>(i, off, col, val, u);
+  u[i] += s * dinv[i];
+}
+
+// rho = r - A u
+template <class T>
+__global__ void k_resid_fine(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                             const T* __restrict__ val, const double* __restrict__ r, const T* __restrict__ u,
+                             T* __restrict__ rho) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rho[i] = (T)r[i] - sell_dot<T, T>(i, off, col, val, u);
+}
+
+// F = P^T rho on the auxiliary nodes, and U = 0 (start of the V-cycle)
+template <class T>
+__global__ void k_restrict_fine(int64_t nJ, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                                const T* __restrict__ val, const T* __restrict__ rho, T* __restrict__ F,
+                                T* __restrict__ U) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nJ) return;
+  F[k] = sell_dot<T, T>(k, off, col, val, rho);
+  U[k] = 0;
+}
+
+// u += P U
+template <class T>
+__global__ void k_prolong_fine(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                               const T* __restrict__ val, const T* __restrict__ U, T* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u[i] += sell_dot<T, T>(i, off, col, val, U);
+}
+
+// ------------------------------------------------------ auxiliary levels
+// one colour of a sweep on the smoothing rows of a level
+template <class T>
+__global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                         const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
+                         const T* __restrict__ rhs, int rhs_local, T* __restrict__ save, T* U) {
+  const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= k0 + nk) return;
+  const int32_t i = rows[k];
+  if (i < 0) return;
+  const T f = rhs_local ? rhs[k] : rhs[i];
+  if (save) save[k] = f;
+  const T s = f - sell_dot<T, T>(k, off, col, val, U);
+  U[i] += s * dinv[k];
+}
+
+// F_i -= sum_{j in N~_l} a_ij U_j on the rows E_l
+template <class T>
+__global__ void k_resid_aux(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                            const T* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
+                            T* __restrict__ F) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int32_t i = rows[k];
+  if (i < 0) return;
+  F[i] -= sell_dot<T, T>(k, off, col, val, U);
+}
+
+// I_l^T: F[parent] += 1/2 sum F[new children]; and save + clear U on N~_l
+template <class T>
+__global__ void k_restrict_aux(int64_t npar, const int32_t* __restrict__ pid, const int32_t* __restrict__ pptr,
+                               const int32_t* __restrict__ child, T* __restrict__ F, int64_t nsm,
+                               const int32_t* __restrict__ rows, T* __restrict__ U, T* __restrict__ us) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < npar) {
+    T acc = 0;
+    for (int32_t p = pptr[t]; p < pptr[t + 1]; ++p) acc += F[child[p]];
+    F[pid[t]] += (T)0.5 * acc;
+  }
+  if (t < nsm) {
+    const int32_t i = rows[t];
+    if (i >= 0) {
+      us[t] = U[i];
+      U[i] = 0;
+    }
+  }
+}
+
+// I_l: U[new] = (U[p0] + U[p1]) / 2, Dirichlet parents contribute 0
+template <class T>
+__global__ void k_prolong_aux(int64_t nnew, const int32_t* __restrict__ id, const int32_t* __restrict__ p0,
+                              const int32_t* __restrict__ p1, T* U) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnew) return;
+  const int32_t a = p0[t], b = p1[t];
+  T v = 0;
+  if (a >= 0) v += U[a];
+  if (b >= 0) v += U[b];
+  U[id[t]] = (T)0.5 * v;
+}
+
+template <class T>
+__global__ void k_addsaved_aux(int64_t nsm, const int32_t* __restrict__ rows, const T* __restrict__ us, T* U) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nsm) return;
+  const int32_t i = rows[t];
+  if (i >= 0) U[i] += us[t];
+}
+
+// coarsest level: U[cid] = A_c^{-1} F[cid] in FP64, one warp per row
+template <class T>
+__global__ void k_coarse(int64_t nc, const int32_t* __restrict__ cid, const double* __restrict__ inv,
+                         const T* __restrict__ F, T* __restrict__ U) {
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nc) return;
+  double s = 0;
+  for (int64_t j = lane; j < nc; j += 32) s += inv[row * nc + j] * (double)F[cid[j]];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) U[cid[row]] = (T)s;
+}
+
+// ------------------------------------------------------------------ PCG
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;  // valid in thread 0
+}
+
+// Deterministic grid reduction of NV values: partials per block, the last
+// block to finish sums them in block order.  Returns true in that block.
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], double* partial, unsigned int* ticket) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  for (int j = 0; j < NV; ++j) {
+    double t = block_sum(v[j], sh);
+    if (threadIdx.x == 0) partial[j * gridDim.x + blockIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int j = 0; j < NV; ++j) {
+    double s = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partial + j * gridDim.x + b);
+    v[j] = block_sum(s, sh);
+  }
+  if (threadIdx.x == 0) *ticket = 0;
+  return true;
+}
+
+__device__ __forceinline__ void set_cond(PcgScalars* sc, int cond, cudaGraphConditionalHandle hnd, int use_hnd) {
+  sc->cond = cond;
+  if (use_hnd) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
+}
+
+// r = b - A x;  ||b||, ||r||; PCG scalars initialised
+__global__ void k_pcg_init(int64_t n, SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
+                           double* __restrict__ r, double* partial, unsigned int* ticket, PcgScalars* sc, double rtol,
+                           int maxit, double* hist, cudaGraphConditionalHandle hnd, int use_hnd) {
+  double v[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double ri = b[i] - sell_dot<double, double>(i, A.off, A.col, A.val, x);
+    r[i] = ri;
+    v[0] += b[i] * b[i];
+    v[1] += ri * ri;
+  }
+  if (grid_reduce<2>(v, partial, ticket) && threadIdx.x == 0) {
+    sc->bnorm = sqrt(v[0]);
+    sc->tol = rtol * sc->bnorm;
+    sc->rr = v[1];
+    sc->k = 0;
+    sc->maxit = maxit;
+    sc->status = 1;
+    sc->rz = 0;
+    sc->alpha = 0;
+    sc->beta = 0;
+    hist[0] = sqrt(v[1]);
+    const bool conv = sqrt(v[1]) <= sc->tol;
+    if (conv) sc->status = 0;
+    set_cond(sc, (!conv && maxit > 0) ? 1 : 0, hnd, use_hnd);
+  }
+}
+
+// <z, r>, <z, q_prev>  ->  beta (flexible: -alpha <z_{k+1}, q_k> / <z_k, r_k>), rz
+template <class T>
+__global__ void k_dots(int64_t n, const T* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q,
+                       double* partial, unsigned int* ticket, PcgScalars* sc) {
+  double v[2] = {0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double zi = (double)z[i];
+    v[0] += zi * r[i];
+    v[1] += zi * q[i];
+  }
+  if (grid_reduce<2>(v, partial, ticket) && threadIdx.x == 0) {
+    if (sc->k == 0) {
+      sc->beta = 0;
+    } else {
+      sc->beta = -sc->alpha * v[1] / sc->rz;
+    }
+    sc->rz = v[0];
+    if (!(v[0] > 0)) sc->status = ASMG_ERR_BREAKDOWN;
+  }
+}
+
+// p = z + beta p
+template <class T>
+__global__ void k_pupd(int64_t n, const T* __restrict__ z, double* __restrict__ p, const PcgScalars* __restrict__ sc) {
+  const double beta = sc->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (double)z[i] + beta * p[i];
+}
+
+// q = A p, <p, q>  ->  alpha
+__global__ void k_spmv_dot(int64_t n, SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
+                           double* partial, unsigned int* ticket, PcgScalars* sc) {
+  double v[1] = {0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double qi = sell_dot<double, double>(i, A.off, A.col, A.val, p);
+    q[i] = qi;
+    v[0] += p[i] * qi;
+  }
+  if (grid_reduce<1>(v, partial, ticket) && threadIdx.x == 0) {
+    sc->pq = v[0];
+    if (!(v[0] > 0) || sc->status == ASMG_ERR_BREAKDOWN) {
+      sc->status = ASMG_ERR_BREAKDOWN;
+      sc->alpha = 0;
+    } else {
+      sc->alpha = sc->rz / v[0];
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, ||r||  ->  history, stopping test
+__global__ void k_axpy_norm(int64_t n, const double* __restrict__ p, const double* __restrict__ q,
+                            double* __restrict__ x, double* __restrict__ r, double* partial, unsigned int* ticket,
+                            PcgScalars* sc, double* hist, cudaGraphConditionalHandle hnd, int use_hnd) {
+  const double a = sc->alpha;
+  double v[1] = {0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    double ri = r[i] - a * q[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  if (grid_reduce<1>(v, partial, ticket) && threadIdx.x == 0) {
+    if (sc->status == ASMG_ERR_BREAKDOWN) {
+      set_cond(sc, 0, hnd, use_hnd);
+      return;
+    }
+    sc->k += 1;
+    sc->rr = v[0];
+    const double nr = sqrt(v[0]);
+    hist[sc->k] = nr;
+    bool conv = nr <= sc->tol;
+    if (conv) sc->status = 0;
+    bool more = !conv && sc->k < sc->maxit && isfinite(nr);
+    if (!isfinite(nr)) sc->status = ASMG_ERR_BREAKDOWN;
+    set_cond(sc, more ? 1 : 0, hnd, use_hnd);
+  }
+}
+
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ vrow, const double* __restrict__ src,
+                         double* __restrict__ dst) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = vrow[i];
+  dst[i] = v >= 0 ? src[v] : 0.0;
+}
+
+template <class S>
+__global__ void k_scatter(int64_t nv, const int32_t* __restrict__ rowv, const S* __restrict__ src,
+                          double* __restrict__ dst) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const int32_t r = rowv[v];
+  dst[v] = r >= 0 ? (double)src[r] : 0.0;
+}
+
+// --------------------------------------------------------- enqueueing
+template <class T>
+SellView<T> fine_smoother(asmg_s& h);
+template <>
+SellView<double> fine_smoother<double>(asmg_s& h) { return view(h.A64); }
+template <>
+SellView<float> fine_smoother<float>(asmg_s& h) { return view(h.p32.Af); }
+template <class T>
+const T* fine_dinv(asmg_s& h);
+template <>
+const double* fine_dinv<double>(asmg_s& h) { return h.dinv64.p; }
+template <>
+const float* fine_dinv<float>(asmg_s& h) { return h.p32.dinv_f.p; }
+
+template <class T>
+Prec<T>& prec(asmg_s& h);
+template <>
+Prec<double>& prec<double>(asmg_s& h) { return h.p64; }
+template <>
+Prec<float>& prec<float>(asmg_s& h) { return h.p32; }
+
+template <class T>
+int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
+  Prec<T>& P = prec<T>(h);
+  int launches = 0;
+  const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
+  for (int li = (int)P.lev.size() - 1; li >= 0; --li) {
+    AuxLevelDev<T>& L = P.lev[li];
+    auto SM = view(L.SM);
+    // the first pre-sweep also saves F on N~_l for the post-sweeps (nu_pre >= 1)
+    for (int sweep = 0; sweep < npre; ++sweep) {
+      for (int c = 0; c < L.ncolours; ++c) {
+        int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
+        if (!nk) continue;
+        k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
+                                              sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1,
+                                              sweep == 0 ? L.fs.p : nullptr, P.U.p);
+        ++launches;
+      }
+    }
+    auto RS = view(L.RS);
+    k_resid_aux<T><<<nblk(L.nrs), TPB, 0, s>>>(L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p);
+    k_restrict_aux<T><<<nblk(std::max(L.npar, L.nsm)), TPB, 0, s>>>(L.npar, L.rp_id.p, L.rp_ptr.p, L.rp_child.p, P.F.p,
+                                                                     L.nsm, L.sm_rows.p, P.U.p, L.us.p);
+    launches += 2;
+  }
+  if (h.nc > 0) {
+    k_coarse<T><<<nblk(h.nc * 32), TPB, 0, s>>>(h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p);
+    ++launches;
+  }
+  for (size_t li = 0; li < P.lev.size(); ++li) {
+    AuxLevelDev<T>& L = P.lev[li];
+    auto SM = view(L.SM);
+    if (L.nnew) k_prolong_aux<T><<<nblk(L.nnew), TPB, 0, s>>>(L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p);
+    k_addsaved_aux<T><<<nblk(L.nsm), TPB, 0, s>>>(L.nsm, L.sm_rows.p, L.us.p, P.U.p);
+    launches += 2;
+    for (int sweep = 0; sweep < npost; ++sweep)
+      for (int c = L.ncolours - 1; c >= 0; --c) {
+        int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
+        if (!nk) continue;
+        k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p, 1,
+                                              nullptr, P.U.p);
+        ++launches;
+      }
+  }
+  return launches;
+}
+
+template <class T>
+int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
+  Prec<T>& P = prec<T>(h);
+  const SellView<T> A = fine_smoother<T>(h);
+  const T* dinv = fine_dinv<T>(h);
+  int launches = 0;
+  ASMG_CUDA(cudaMemsetAsync(P.uf.p, 0, sizeof(T) * h.npad, s));
+  const int ncol = (int)h.fine_cstart.size() - 1;
+  // (1) u1 = S r: forward multicolour sweep from zero
+  for (int c = 0; c < ncol; ++c) {
+    int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
+    if (!nr) continue;
+    k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p);
+    ++launches;
+  }
+  // (2) u2 = u1 + P Btilde P^T (r - A u1)
+  if (h.nJ > 0) {
+    k_resid_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p);
+    auto PT = view(P.PT);
+    k_restrict_fine<T><<<nblk(h.nJpad), TPB, 0, s>>>(h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p);
+    launches += 2;
+    launches += enqueue_vcycle<T>(h, s);
+    auto PP = view(P.P);
+    k_prolong_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p);
+    ++launches;
+  }
+  // (3) u3 = u2 + S^T (r - A u2): backward multicolour sweep
+  for (int c = ncol - 1; c >= 0; --c) {
+    int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
+    if (!nr) continue;
+    k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p);
+    ++launches;
+  }
+  ASMG_CUDA(cudaGetLastError());
+  return launches;
+}
+
+template <class T>
+int enqueue_body(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  int launches = enqueue_precond<T>(h, h.r.p, s);
+  const T* z = prec<T>(h).uf.p;
+  const int G = RED_BLOCKS;
+  k_dots<T><<<G, TPB, 0, s>>>(h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p);
+  k_pupd<T><<<G, TPB, 0, s>>>(h.npad, z, h.p.p, h.scal.p);
+  k_spmv_dot<<<G, TPB, 0, s>>>(h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p);
+  k_axpy_norm<<<G, TPB, 0, s>>>(h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p, h.hist.p, hnd,
+                                use_hnd);
+  ASMG_CUDA(cudaGetLastError());
+  return launches + 4;
+}
+
+int enqueue_body_any(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  return h.prm.precision == ASMG_MIXED ? enqueue_body<float>(h, s, hnd, use_hnd)
+                                       : enqueue_body<double>(h, s, hnd, use_hnd);
+}
+
+void enqueue_init(asmg_s& h, double rtol, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  k_pcg_init<<<RED_BLOCKS, TPB, 0, s>>>(h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
+                                        rtol, h.prm.max_iter, h.hist.p, hnd, use_hnd);
+  ASMG_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s) {
+  k_gather<<<nblk(h.npad), TPB, 0, s>>>(h.npad, h.d_vertex_of_row.p, vsrc, dst);
+  ASMG_CUDA(cudaGetLastError());
+}
+
+void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cudaStream_t s) {
+  if (src_float)
+    k_scatter<float><<<nblk(h.mesh.nv), TPB, 0, s>>>(h.mesh.nv, h.d_row_of_vertex.p, (const float*)src, vdst);
+  else
+    k_scatter<double><<<nblk(h.mesh.nv), TPB, 0, s>>>(h.mesh.nv, h.d_row_of_vertex.p, (const double*)src, vdst);
+  ASMG_CUDA(cudaGetLastError());
+}
+
+void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s) {
+  if (h.prm.precision == ASMG_MIXED)
+    enqueue_precond<float>(h, r_perm, s);
+  else
+    enqueue_precond<double>(h, r_perm, s);
+}
+
+__global__ void k_spmv64(int64_t n, SellView<double> A, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = sell_dot<double, double>(i, A.off, A.col, A.val, x);
+}
+
+void spmv64(asmg_s& h, const double* x, double* y, cudaStream_t s) {
+  k_spmv64<<<nblk(h.npad), TPB, 0, s>>>(h.npad, view(h.A64), x, y);
+  ASMG_CUDA(cudaGetLastError());
+}
+
+// Build (once) the graph of the whole solve:
+//   init (r = b - A x, norms, condition) -> WHILE(cond) { body }.
+static void build_graph(asmg_s& h, double rtol, cudaStream_t s) {
+  (void)rtol;
+  if (h.gexec) {
+    cudaGraphExecDestroy(h.gexec);
+    h.gexec = nullptr;
+  }
+  if (h.graph) {
+    cudaGraphDestroy(h.graph);
+    h.graph = nullptr;
+  }
+  cudaGraph_t g;
+  ASMG_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hnd;
+  ASMG_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0));
+  // the init kernel is captured into the parent graph
+  cudaStream_t cs;
+  ASMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enqueue_init(h, rtol, cs, hnd, 1);
+  cudaGraph_t gg;
+  ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
+  // the WHILE node depends on every node captured so far (the init kernel)
+  size_t nnodes = 0;
+  ASMG_CUDA(cudaGraphGetNodes(g, nullptr, &nnodes));
+  std::vector<cudaGraphNode_t> deps(nnodes);
+  if (nnodes) ASMG_CUDA(cudaGraphGetNodes(g, deps.data(), &nnodes));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hnd;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  ASMG_CUDA(cudaGraphAddNode(&cnode, g, deps.data(), nullptr, nnodes, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  // body
+  ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  h.gpu_launches_per_iter = enqueue_body_any(h, cs, hnd, 1);
+  cudaGraph_t bb;
+  ASMG_CUDA(cudaStreamEndCapture(cs, &bb));
+  ASMG_CUDA(cudaStreamDestroy(cs));
+  ASMG_CUDA(cudaGraphInstantiate(&h.gexec, g, 0));
+  h.graph = g;
+}
+
+int run_solve(asmg_s& h, double rtol, cudaStream_t s) {
+  if (h.prm.use_graph) {
+    // the graph bakes rtol into the init kernel's arguments: rebuild when it changes
+    if (!h.gexec || h.graph_rtol != rtol) {
+      build_graph(h, rtol, s);
+      h.graph_rtol = rtol;
+    }
+    ASMG_CUDA(cudaGraphLaunch(h.gexec, s));
+  } else {
+    enqueue_init(h, rtol, s, 0, 0);
+    for (int it = 0; it < h.prm.max_iter; ++it) {
+      PcgScalars sc;
+      ASMG_CUDA(cudaMemcpyAsync(&sc, h.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+      ASMG_CUDA(cudaStreamSynchronize(s));
+      if (!sc.cond) break;
+      h.gpu_launches_per_iter = enqueue_body_any(h, s, 0, 0);
+    }
+  }
+  return 0;
+}
+
+void setup_solve(asmg_s& h, cudaStream_t s) {
+  h.b.alloc(h.npad);
+  h.x.alloc(h.npad);
+  h.r.alloc(h.npad);
+  h.p.alloc(h.npad);
+  h.q.alloc(h.npad);
+  h.b.zero(s);
+  h.x.zero(s);
+  h.r.zero(s);
+  h.p.zero(s);
+  h.q.zero(s);
+  h.vb.alloc(h.mesh.nv);
+  h.vu.alloc(h.mesh.nv);
+  h.partial.alloc(4 * RED_BLOCKS);
+  h.ticket.alloc(1);
+  h.ticket.zero(s);
+  h.scal.alloc(1);
+  h.scal.zero(s);
+  h.hist.alloc(h.prm.max_iter + 1);
+  auto alloc_prec = [&](auto& P) {
+    P.uf.alloc(h.npad);
+    P.rho.alloc(h.npad);
+    P.F.alloc(std::max<int64_t>(h.nJpad, 1));
+    P.U.alloc(std::max<int64_t>(h.nJpad, 1));
+    P.uf.zero(s);
+    P.rho.zero(s);
+    P.F.zero(s);
+    P.U.zero(s);
+  };
+  if (h.prm.precision == ASMG_MIXED)
+    alloc_prec(h.p32);
+  else
+    alloc_prec(h.p64);
+}
+
+}  // namespace asmg
