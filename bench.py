@@ -160,6 +160,7 @@ def main():
     ap.add_argument("--workload", default="graded2049")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="plain launches instead of the CUDA graph (ncu runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -184,7 +185,7 @@ def main():
     t0 = time.perf_counter()
     solvers = {}
     for prec in ([asmg.ASMG_MIXED] if args.no_fp64 else [asmg.ASMG_MIXED, asmg.ASMG_FP64]):
-        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream)
+        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1)
         solvers[prec] = s
     t_setup = time.perf_counter() - t0
     s = solvers[asmg.ASMG_MIXED]
@@ -249,10 +250,21 @@ def main():
     mix = results[asmg.ASMG_MIXED]
     ms_step = mix["ms"] / args.steps
     value = world * n / (ms_step / 1e3)
-    bytes_iter = s.info("bytes_iter")
     it_mix = int(np.median(mix["its"]))
-    achieved = bytes_iter * it_mix / (ms_step / 1e3) / 1e9
     peak, peak_kind = _peaks()
+    # live per-kernel timing: one solve with every launch bracketed by CUDA
+    # events on the solve's stream, tagged with algorithmic bytes
+    prof, it_prof = asmg.amg_profile(s.h, b, RTOL, sp)
+    tot_ms = sum(v["ms"] for v in prof.values())
+    tot_bytes = sum(v["bytes"] for v in prof.values())
+    launches_per_solve = sum(v["launches"] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    kernels = {k: {"launches_per_solve": v["launches"], "ms_per_solve": round(v["ms"], 3),
+                   "share": round(v["ms"] / tot_ms, 4),
+                   "GBps": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None}
+               for k, v in prof.items() if v["launches"]}
     line = {
         "metric": METRIC, "value": value, "unit": "dofs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -261,14 +273,17 @@ def main():
                    "nfree": n, "triangles": mesh.ne, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
                    "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
+                   "graph": not args.no_graph,
                    "l2": "working set (several GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * n / e2e_s, "unit": "dofs/s", "h2d_bytes_per_step": 8 * 2 * mesh.nv,
                 "d2h_bytes_per_step": 8 * mesh.nv + 8 * (it_mix + 1)},
-        "gpu_launches": int(s.info("launches_per_iter")) * it_mix * args.steps,
+        "gpu_launches": int(launches_per_solve) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "scope": f"whole solve: algorithmic bytes per iteration x iterations / solve time; "
-                              f"peak {peak_kind}"},
+                     "frac": achieved / peak, "traffic": None, "kernel": dom,
+                     "note": f"dominant kernel class by event-timed share; peak {peak_kind} (copy bandwidth)"},
+        "solve_bandwidth": {"achieved_GBps": tot_bytes / (ms_step / 1e3) / 1e9, "frac": tot_bytes / (ms_step / 1e3) / 1e9 / peak,
+                            "bytes_per_solve": tot_bytes, "event_timed_kernel_ms": tot_ms},
+        "kernels": kernels,
         "clocks": mix["clocks"],
     }
     if asmg.ASMG_FP64 in results:

@@ -177,6 +177,30 @@ enum asmg_export_what {
 };
 int amg_export(asmg_handle h, int what, int level, void* host_buf, int64_t* count);
 
+/*
+ * Profile one solve (tracing; not part of the paper): the solve of amg_solve
+ * from u = 0 is run without the CUDA graph and every kernel launch is timed
+ * with CUDA events on `stream`.  out: host float64 [3 * ASMG_PROF_NCLASS],
+ * per kernel class (enum asmg_prof_class) the number of launches, their total
+ * time in milliseconds and their algorithmic bytes (compulsory traffic of the
+ * real rows and non-zeros each launch touches).  b: float64 [nv] as in
+ * amg_solve.  The solution is discarded.
+ */
+enum asmg_prof_class {
+  ASMG_PROF_FINE_GS = 0,      /* fine-grid Gauss-Seidel colour sweeps (Algorithm 1, steps 1 and 3) */
+  ASMG_PROF_FINE_RESID = 1,   /* fine residual r - A u1 */
+  ASMG_PROF_RESTRICT = 2,     /* P^T: fine residual to the finest auxiliary level */
+  ASMG_PROF_PROLONG = 3,      /* P: auxiliary correction to the fine grid */
+  ASMG_PROF_AUX_GS = 4,       /* auxiliary-level Gauss-Seidel sweeps (Algorithm 2) */
+  ASMG_PROF_AUX_RESID = 5,    /* auxiliary-level residuals */
+  ASMG_PROF_AUX_TRANSFER = 6, /* auxiliary restriction / prolongation / bookkeeping */
+  ASMG_PROF_COARSE = 7,       /* coarsest-level solve */
+  ASMG_PROF_CG_SPMV = 8,      /* PCG q = A p with <p, q> (FP64) */
+  ASMG_PROF_CG_VECTOR = 9,    /* PCG vector updates and reductions */
+  ASMG_PROF_NCLASS = 10
+};
+int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
+
 /* Free the handle and all device memory it owns.  NULL is ignored. */
 void amg_destroy(asmg_handle h);
 

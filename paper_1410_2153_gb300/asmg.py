@@ -68,11 +68,13 @@ def lib():
         L.amg_update_coefficients.argtypes = [vp, vp, vp]
         L.amg_info.argtypes = [vp, i32, i32, ctypes.POINTER(i64)]
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
+        L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_destroy.argtypes = [vp]
         L.amg_destroy.restype = None
         L.amg_last_error.restype = ctypes.c_char_p
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
-                     "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export"):
+                     "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export",
+                     "amg_profile"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -164,6 +166,20 @@ def amg_export(h, what, level: int = 0) -> np.ndarray:
     if n:
         _check(lib().amg_export(h, code, level, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
     return out
+
+
+PROF_CLASSES = ["fine_gs", "fine_resid", "restrict", "prolong", "aux_gs", "aux_resid", "aux_transfer", "coarse",
+                "cg_spmv", "cg_vector"]
+
+
+def amg_profile(h, b, rtol: float, stream=None):
+    """Per kernel class: dict(launches, ms, bytes) of one event-timed solve, and the iterations."""
+    out = np.zeros(3 * len(PROF_CLASSES))
+    it = ctypes.c_int(0)
+    _check(lib().amg_profile(h, _ptr(b), float(rtol), _ptr(out), ctypes.byref(it), stream))
+    res = {c: dict(launches=int(out[3 * k]), ms=float(out[3 * k + 1]), bytes=float(out[3 * k + 2]))
+           for k, c in enumerate(PROF_CLASSES)}
+    return res, it.value
 
 
 def amg_destroy(h):

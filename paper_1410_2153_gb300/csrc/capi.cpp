@@ -104,6 +104,14 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
     }
   }
   HostCSR SM = select_rows(Arows, sel, nullptr, nullptr);
+  D.cnnz.assign(ncol, 0);
+  D.crows.assign(ncol, 0);
+  for (int c = 0; c < ncol; ++c)
+    for (int64_t k = D.cstart[c]; k < D.cstart[c + 1]; ++k)
+      if (sel[k] >= 0) {
+        D.crows[c] += 1;
+        D.cnnz[c] += SM.ptr[k + 1] - SM.ptr[k];
+      }
   sell_build<T>(D.SM, SM, 0, s);
   D.sm_rows.upload(rows, s);
   D.sm_dinv.upload(dinv, s);
@@ -114,6 +122,7 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
     for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1] && !any; ++p) any = inset[Arows.col[p]];
     if (any) rsel.push_back(i);
   }
+  D.nrs_real = (int64_t)rsel.size();
   while (rsel.size() % 32) rsel.push_back(-1);
   D.nrs = (int64_t)rsel.size();
   HostCSR RS = select_rows(Arows, rsel, nullptr, &inset);
@@ -141,6 +150,7 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
   }
   if (!pid.empty()) pptr.push_back((int32_t)child.size());
   D.npar = (int64_t)pid.size();
+  D.nchild = (int64_t)child.size();
   D.rp_id.upload(pid, s);
   D.rp_ptr.upload(pptr, s);
   D.rp_child.upload(child, s);
@@ -254,6 +264,14 @@ void build_all(asmg_s& h, cudaStream_t s) {
       if (Aperm.col[p] == k) dinv[k] = 1.0 / Aperm.val[p];
   sell_build<double>(h.A64, Aperm, 0, s);
   h.dinv64.upload(dinv, s);
+  h.fine_cnnz.assign(ncol, 0);
+  h.fine_crows.assign(ncol, 0);
+  for (int c = 0; c < ncol; ++c)
+    for (int64_t k = h.fine_cstart[c]; k < h.fine_cstart[c + 1]; ++k)
+      if (sel[k] >= 0) {
+        h.fine_crows[c] += 1;
+        h.fine_cnnz[c] += Aperm.ptr[k + 1] - Aperm.ptr[k];
+      }
   h.stats.t_fine = now() - t0;
 
   // ---- auxiliary hierarchy (host), transfer
@@ -506,6 +524,19 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
 }
 
 void amg_destroy(asmg_handle h) { delete h; }
+
+int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream) {
+  API_BEGIN
+  if (!h || !b || !out || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nv = h->mesh.nv;
+  copy_in(h->vb.p, b, nv, s);
+  gather_rows(*h, h->vb.p, h->b.p, s);
+  h->x.zero(s);
+  *iterations = profile_solve(*h, rtol, s, out);
+  return ASMG_OK;
+  API_END
+}
 
 int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* iterations, double* res_history,
               void* stream) {

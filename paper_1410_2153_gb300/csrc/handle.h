@@ -48,6 +48,7 @@ struct asmg_s {
   int64_t n = 0, npad = 0;
   std::vector<int32_t> free_of_vertex, vertex_of_free, fine_colour, row_of_free;
   std::vector<int64_t> fine_cstart;      // colour blocks in permuted rows (multiples of 32)
+  std::vector<int64_t> fine_cnnz, fine_crows;  // real non-zeros / rows per colour block
   asmg::HostCSR A_host;                  // fine A, free-dof numbering (for export)
   asmg::Sell<double> A64;
   asmg::DBuf<double> dinv64;
@@ -89,6 +90,7 @@ struct asmg_s {
 namespace asmg {
 // solve.cu
 void setup_solve(asmg_s& h, cudaStream_t s);
+int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out);
 int run_solve(asmg_s& h, double rtol, cudaStream_t s);
 void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s);  // result in h.p*.uf
 void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);

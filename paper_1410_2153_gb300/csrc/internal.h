@@ -185,16 +185,17 @@ struct AuxLevelDev {
   int level = 0;
   int ncolours = 0;
   std::vector<int64_t> cstart;   // colour class starts in SM rows (multiples of 32)
+  std::vector<int64_t> cnnz, crows;  // real non-zeros / rows per colour class
   int64_t nsm = 0, nsm_real = 0; // padded / real smoothing rows
   DBuf<int32_t> sm_rows;         // aux ID per SM row (-1 padding)
   Sell<T> SM;                    // A_l rows of N~_l (all columns)
   DBuf<T> sm_dinv;
-  int64_t nrs = 0;
+  int64_t nrs = 0, nrs_real = 0;
   DBuf<int32_t> rs_rows;         // aux ID per residual row
   Sell<T> RS;                    // A_l rows of E_l, columns in N~_l only
   int64_t nnew = 0;
   DBuf<int32_t> nn_id, nn_p0, nn_p1;  // prolongation of new nodes
-  int64_t npar = 0;
+  int64_t npar = 0, nchild = 0;
   DBuf<int32_t> rp_id;           // parents receiving restricted residuals
   DBuf<int32_t> rp_ptr, rp_child;
   DBuf<T> fs, us;                // saved rhs / pre-smoothed values on N~_l

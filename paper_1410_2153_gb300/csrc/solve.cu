@@ -335,6 +335,41 @@ __global__ void k_scatter(int64_t nv, const int32_t* __restrict__ rowv, const S*
   dst[v] = r >= 0 ? (double)src[r] : 0.0;
 }
 
+// --------------------------------------------------------- profiling
+// With a profiler installed, every launch of the solve is bracketed by CUDA
+// events on its stream and tagged with its kernel class and algorithmic bytes.
+struct Profiler {
+  cudaStream_t s = nullptr;
+  std::vector<cudaEvent_t> ev;
+  struct Rec {
+    int cls;
+    int64_t bytes;
+    int e0;
+  };
+  std::vector<Rec> recs;
+  int mark() {
+    cudaEvent_t e;
+    ASMG_CUDA(cudaEventCreate(&e));
+    ASMG_CUDA(cudaEventRecord(e, s));
+    ev.push_back(e);
+    return (int)ev.size() - 1;
+  }
+  ~Profiler() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+thread_local Profiler* g_prof = nullptr;
+
+#define LAUNCH(cls, bytes, ...)                                                  \
+  do {                                                                          \
+    int e0_ = g_prof ? g_prof->mark() : -1;                                     \
+    __VA_ARGS__;                                                                \
+    if (g_prof) {                                                               \
+      g_prof->mark();                                                           \
+      g_prof->recs.push_back(Profiler::Rec{(int)(cls), (int64_t)(bytes), e0_}); \
+    }                                                                           \
+  } while (0)
+
 // --------------------------------------------------------- enqueueing
 template <class T>
 SellView<T> fine_smoother(asmg_s& h);
@@ -360,6 +395,7 @@ template <class T>
 int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
   int launches = 0;
+  const int64_t sz = sizeof(T);
   const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
   for (int li = (int)P.lev.size() - 1; li >= 0; --li) {
     AuxLevelDev<T>& L = P.lev[li];
@@ -369,34 +405,46 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
       for (int c = 0; c < L.ncolours; ++c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
-                                              sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1,
-                                              sweep == 0 ? L.fs.p : nullptr, P.U.p);
+        const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
+        LAUNCH(ASMG_PROF_AUX_GS, by,
+               k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
+                                                    sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1,
+                                                    sweep == 0 ? L.fs.p : nullptr, P.U.p));
         ++launches;
       }
     }
     auto RS = view(L.RS);
-    k_resid_aux<T><<<nblk(L.nrs), TPB, 0, s>>>(L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p);
-    k_restrict_aux<T><<<nblk(std::max(L.npar, L.nsm)), TPB, 0, s>>>(L.npar, L.rp_id.p, L.rp_ptr.p, L.rp_child.p, P.F.p,
-                                                                     L.nsm, L.sm_rows.p, P.U.p, L.us.p);
+    LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
+           k_resid_aux<T><<<nblk(L.nrs), TPB, 0, s>>>(L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p));
+    LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
+           k_restrict_aux<T><<<nblk(std::max(L.npar, L.nsm)), TPB, 0, s>>>(L.npar, L.rp_id.p, L.rp_ptr.p,
+                                                                            L.rp_child.p, P.F.p, L.nsm, L.sm_rows.p,
+                                                                            P.U.p, L.us.p));
     launches += 2;
   }
   if (h.nc > 0) {
-    k_coarse<T><<<nblk(h.nc * 32), TPB, 0, s>>>(h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p);
+    LAUNCH(ASMG_PROF_COARSE, h.nc * h.nc * 8 + h.nc * (4 + 2 * sz),
+           k_coarse<T><<<nblk(h.nc * 32), TPB, 0, s>>>(h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p));
     ++launches;
   }
   for (size_t li = 0; li < P.lev.size(); ++li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
-    if (L.nnew) k_prolong_aux<T><<<nblk(L.nnew), TPB, 0, s>>>(L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p);
-    k_addsaved_aux<T><<<nblk(L.nsm), TPB, 0, s>>>(L.nsm, L.sm_rows.p, L.us.p, P.U.p);
-    launches += 2;
+    if (L.nnew) {
+      LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
+             k_prolong_aux<T><<<nblk(L.nnew), TPB, 0, s>>>(L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p));
+      ++launches;
+    }
+    LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
+           k_addsaved_aux<T><<<nblk(L.nsm), TPB, 0, s>>>(L.nsm, L.sm_rows.p, L.us.p, P.U.p));
+    ++launches;
     for (int sweep = 0; sweep < npost; ++sweep)
       for (int c = L.ncolours - 1; c >= 0; --c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p, 1,
-                                              nullptr, P.U.p);
+        LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
+               k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p,
+                                                    1, nullptr, P.U.p));
         ++launches;
       }
   }
@@ -408,6 +456,7 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
   const SellView<T> A = fine_smoother<T>(h);
   const T* dinv = fine_dinv<T>(h);
+  const int64_t sz = sizeof(T), n = h.n, nJ = h.nJ;
   int launches = 0;
   ASMG_CUDA(cudaMemsetAsync(P.uf.p, 0, sizeof(T) * h.npad, s));
   const int ncol = (int)h.fine_cstart.size() - 1;
@@ -415,25 +464,30 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
   for (int c = 0; c < ncol; ++c) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
-    k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p);
+    LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
+           k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
     ++launches;
   }
   // (2) u2 = u1 + P Btilde P^T (r - A u1)
   if (h.nJ > 0) {
-    k_resid_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p);
+    LAUNCH(ASMG_PROF_FINE_RESID, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
+           k_resid_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p));
     auto PT = view(P.PT);
-    k_restrict_fine<T><<<nblk(h.nJpad), TPB, 0, s>>>(h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p);
+    LAUNCH(ASMG_PROF_RESTRICT, P.PT.nnz_real * (sz + 4) + n * sz + 2 * nJ * sz,
+           k_restrict_fine<T><<<nblk(h.nJpad), TPB, 0, s>>>(h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p));
     launches += 2;
     launches += enqueue_vcycle<T>(h, s);
     auto PP = view(P.P);
-    k_prolong_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p);
+    LAUNCH(ASMG_PROF_PROLONG, P.P.nnz_real * (sz + 4) + nJ * sz + 2 * n * sz,
+           k_prolong_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p));
     ++launches;
   }
   // (3) u3 = u2 + S^T (r - A u2): backward multicolour sweep
   for (int c = ncol - 1; c >= 0; --c) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
-    k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p);
+    LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
+           k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
     ++launches;
   }
   ASMG_CUDA(cudaGetLastError());
@@ -445,11 +499,15 @@ int enqueue_body(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int 
   int launches = enqueue_precond<T>(h, h.r.p, s);
   const T* z = prec<T>(h).uf.p;
   const int G = RED_BLOCKS;
-  k_dots<T><<<G, TPB, 0, s>>>(h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p);
-  k_pupd<T><<<G, TPB, 0, s>>>(h.npad, z, h.p.p, h.scal.p);
-  k_spmv_dot<<<G, TPB, 0, s>>>(h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p);
-  k_axpy_norm<<<G, TPB, 0, s>>>(h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p, h.hist.p, hnd,
-                                use_hnd);
+  const int64_t n = h.n, sz = sizeof(T);
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16),
+         k_dots<T><<<G, TPB, 0, s>>>(h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), k_pupd<T><<<G, TPB, 0, s>>>(h.npad, z, h.p.p, h.scal.p));
+  LAUNCH(ASMG_PROF_CG_SPMV, h.A64.nnz_real * 12 + n * 16,
+         k_spmv_dot<<<G, TPB, 0, s>>>(h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * 48,
+         k_axpy_norm<<<G, TPB, 0, s>>>(h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
+                                       h.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
   return launches + 4;
 }
@@ -460,8 +518,9 @@ int enqueue_body_any(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, 
 }
 
 void enqueue_init(asmg_s& h, double rtol, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
-  k_pcg_init<<<RED_BLOCKS, TPB, 0, s>>>(h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
-                                        rtol, h.prm.max_iter, h.hist.p, hnd, use_hnd);
+  LAUNCH(ASMG_PROF_CG_VECTOR, h.A64.nnz_real * 12 + h.n * 32,
+         k_pcg_init<<<RED_BLOCKS, TPB, 0, s>>>(h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p,
+                                               h.scal.p, rtol, h.prm.max_iter, h.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
 }
 
@@ -562,6 +621,40 @@ int run_solve(asmg_s& h, double rtol, cudaStream_t s) {
     }
   }
   return 0;
+}
+
+// One solve without the graph, every launch timed: per class launches,
+// milliseconds and algorithmic bytes; returns the iteration count.
+int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
+  Profiler prof;
+  prof.s = s;
+  g_prof = &prof;
+  int its = 0;
+  try {
+    enqueue_init(h, rtol, s, 0, 0);
+    for (int it = 0; it < h.prm.max_iter; ++it) {
+      PcgScalars sc;
+      ASMG_CUDA(cudaMemcpyAsync(&sc, h.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+      ASMG_CUDA(cudaStreamSynchronize(s));
+      if (!sc.cond) break;
+      enqueue_body_any(h, s, 0, 0);
+      ++its;
+    }
+    ASMG_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    g_prof = nullptr;
+    throw;
+  }
+  g_prof = nullptr;
+  for (int k = 0; k < 3 * ASMG_PROF_NCLASS; ++k) out[k] = 0;
+  for (auto& r : prof.recs) {
+    float ms = 0;
+    ASMG_CUDA(cudaEventElapsedTime(&ms, prof.ev[r.e0], prof.ev[r.e0 + 1]));
+    out[3 * r.cls] += 1;
+    out[3 * r.cls + 1] += ms;
+    out[3 * r.cls + 2] += (double)r.bytes;
+  }
+  return its;
 }
 
 void setup_solve(asmg_s& h, cudaStream_t s) {
