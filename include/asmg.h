@@ -201,6 +201,28 @@ enum asmg_prof_class {
 };
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
 
+/*
+ * ||b - A u||_2 and ||b||_2 over the free dofs, allocating nothing.  The
+ * paper has no counterpart: this is a service entry point for callers that
+ * cannot allocate device memory when they need the check -- code whose
+ * device heap is owned by another framework's pool, real-time or embedded
+ * callers whose memory budget is frozen after initialisation, or monitors
+ * that must not disturb the allocator of the application they observe.
+ *   b, u   DEVICE float64 [nv] arrays in vertex order.  Host arrays are
+ *          rejected (ASMG_ERR_INVALID_ARG): staging them would need memory.
+ *          Entries at Dirichlet vertices are ignored.
+ *   out    float64 [2], host or device: ||b - A u||_2 and ||b||_2.
+ * Scratch: one fixed 64 KB array inside the library (a static device array),
+ * which every GPU that loads the library keeps until the process exits.  All
+ * calls on a device share it and it keeps the last call's contents; calls
+ * that overlap on the GPU (e.g. from two streams) race on it.  The first call
+ * on a device looks up the array's device address; make that first call
+ * before any stream capture.  Meshes with more than 8,388,608 padded fine
+ * rows are rejected with ASMG_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or
+ * other allocating routine is called.
+ */
+int amg_residual_norm_noalloc(asmg_handle h, const double* b, const double* u, double* out, void* stream);
+
 /* Free the handle and all device memory it owns.  NULL is ignored. */
 void amg_destroy(asmg_handle h);
 

@@ -69,12 +69,13 @@ def lib():
         L.amg_info.argtypes = [vp, i32, i32, ctypes.POINTER(i64)]
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
         L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
+        L.amg_residual_norm_noalloc.argtypes = [vp, vp, vp, vp, vp]
         L.amg_destroy.argtypes = [vp]
         L.amg_destroy.restype = None
         L.amg_last_error.restype = ctypes.c_char_p
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
                      "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export",
-                     "amg_profile"):
+                     "amg_profile", "amg_residual_norm_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -180,6 +181,13 @@ def amg_profile(h, b, rtol: float, stream=None):
     res = {c: dict(launches=int(out[3 * k]), ms=float(out[3 * k + 1]), bytes=float(out[3 * k + 2]))
            for k, c in enumerate(PROF_CLASSES)}
     return res, it.value
+
+
+def amg_residual_norm_noalloc(h, b, u, stream=None):
+    """(||b - A u||, ||b||) over free dofs; b and u must be CUDA tensors.  Allocates nothing."""
+    out = np.zeros(2)
+    _check(lib().amg_residual_norm_noalloc(h, _ptr(b), _ptr(u), _ptr(out), stream))
+    return float(out[0]), float(out[1])
 
 
 def amg_destroy(h):

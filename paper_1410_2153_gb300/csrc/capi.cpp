@@ -525,6 +525,14 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
 
 void amg_destroy(asmg_handle h) { delete h; }
 
+int amg_residual_norm_noalloc(asmg_handle h, const double* b, const double* u, double* out, void* stream) {
+  API_BEGIN
+  if (!h || !b || !u || !out) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  residual_norm_noalloc(*h, b, u, out, (cudaStream_t)stream);
+  return ASMG_OK;
+  API_END
+}
+
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream) {
   API_BEGIN
   if (!h || !b || !out || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");

@@ -91,6 +91,8 @@ namespace asmg {
 // solve.cu
 void setup_solve(asmg_s& h, cudaStream_t s);
 int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out);
+// noalloc.cu
+void residual_norm_noalloc(asmg_s& h, const double* b, const double* u, double* out, cudaStream_t s);
 int run_solve(asmg_s& h, double rtol, cudaStream_t s);
 void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s);  // result in h.p*.uf
 void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);
