@@ -161,6 +161,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of the CUDA graph (ncu runs)")
+    ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -185,7 +186,8 @@ def main():
     t0 = time.perf_counter()
     solvers = {}
     for prec in ([asmg.ASMG_MIXED] if args.no_fp64 else [asmg.ASMG_MIXED, asmg.ASMG_FP64]):
-        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1)
+        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1,
+                        use_pdl=0 if args.no_pdl else 1)
         solvers[prec] = s
     t_setup = time.perf_counter() - t0
     s = solvers[asmg.ASMG_MIXED]
@@ -273,7 +275,7 @@ def main():
                    "nfree": n, "triangles": mesh.ne, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
                    "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
-                   "graph": not args.no_graph,
+                   "graph": not args.no_graph, "pdl": not args.no_pdl,
                    "l2": "working set (several GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * n / e2e_s, "unit": "dofs/s", "h2d_bytes_per_step": 8 * 2 * mesh.nv,
                 "d2h_bytes_per_step": 8 * mesh.nv + 8 * (it_mix + 1)},

@@ -61,6 +61,7 @@ typedef struct {
   int32_t smoothing;       /* 0: smooth the new/changed nodes N~_l of each level (Sec. 4.2, eq.
                               decomposition); 1: smooth every node of every level */
   int32_t use_graph;       /* 1: run the PCG loop as one CUDA graph with a device-side WHILE node */
+  int32_t use_pdl;         /* 1: launch solve kernels with programmatic dependent launch */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */

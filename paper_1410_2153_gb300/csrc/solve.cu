@@ -33,6 +33,27 @@ constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
 
 int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
 
+// Kernel launch, optionally with programmatic dependent launch (the kernel may
+// start while its predecessor on the stream finishes; see pdl_wait below).
+template <typename... KArgs, typename... Args>
+void launch(bool pdl, void (*kern)(KArgs...), int64_t grid, int block, cudaStream_t s, Args... args) {
+  if (!pdl) {
+    kern<<<(unsigned)grid, (unsigned)block, 0, s>>>(static_cast<KArgs>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  ASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 template <class T, class X>
 __device__ __forceinline__ T sell_dot(int64_t row, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                       const T* __restrict__ val, const X* x) {
@@ -46,15 +67,73 @@ __device__ __forceinline__ T sell_dot(int64_t row, const int64_t* __restrict__ o
   return s;
 }
 
+// Programmatic dependent launch: every solve kernel first loads what was
+// written at setup (matrix rows, index lists), then waits for the preceding
+// kernel (griddepcontrol.wait), and lets the next kernel launch once its own
+// work is done (griddepcontrol.launch_dependents).  Launched without the
+// attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// A SELL-32 row held in registers (up to MAXW entries; longer rows read the rest later).
+constexpr int MAXW = 10;
+template <class T>
+struct Row {
+  int64_t b = 0, lane = 0;
+  int w = 0;
+  int32_t c[MAXW];
+  T v[MAXW];
+};
+
+template <class T>
+__device__ __forceinline__ void row_load(Row<T>& R, int64_t row, const int64_t* __restrict__ off,
+                                         const int32_t* __restrict__ col, const T* __restrict__ val) {
+  const int64_t sl = row >> 5;
+  R.lane = row & 31;
+  R.b = __ldg(off + sl);
+  R.w = (int)((__ldg(off + sl + 1) - R.b) >> 5);
+#pragma unroll
+  for (int k = 0; k < MAXW; ++k)
+    if (k < R.w) {
+      const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
+      R.c[k] = __ldg(col + e);
+      R.v[k] = __ldg(val + e);
+    }
+}
+
+template <class T, class X>
+__device__ __forceinline__ T row_dot(const Row<T>& R, const int32_t* __restrict__ col, const T* __restrict__ val,
+                                     const X* x) {
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < MAXW; ++k)
+    if (k < R.w) s += R.v[k] * (T)x[R.c[k]];
+  for (int k = MAXW; k < R.w; ++k) {
+    const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
+    s += __ldg(val + e) * (T)x[__ldg(col + e)];
+  }
+  return s;
+}
+
 // ------------------------------------------------------------- fine grid
 // one colour of a Gauss-Seidel sweep: u_i += (rhs_i - (A u)_i) / a_ii
 template <class T, class R>
 __global__ void k_gs_fine(int64_t r0, int64_t nrows, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                           const T* __restrict__ val, const T* __restrict__ dinv, const R* __restrict__ rhs, T* u) {
   const int64_t i = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= r0 + nrows) return;
-  T s = (T)rhs[i] - sell_dot<T, T>(i, off, col, val, u);
-  u[i] += s * dinv[i];
+  const bool act = i < r0 + nrows;
+  Row<T> row;
+  T di = 0;
+  if (act) {
+    row_load(row, i, off, col, val);
+    di = dinv[i];
+  }
+  pdl_wait();
+  if (act) {
+    const T s = (T)rhs[i] - row_dot(row, col, val, u);
+    u[i] += s * di;
+  }
+  pdl_trigger();
 }
 
 // rho = r - A u
@@ -63,8 +142,12 @@ __global__ void k_resid_fine(int64_t n, const int64_t* __restrict__ off, const i
                              const T* __restrict__ val, const double* __restrict__ r, const T* __restrict__ u,
                              T* __restrict__ rho) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  rho[i] = (T)r[i] - sell_dot<T, T>(i, off, col, val, u);
+  const bool act = i < n;
+  Row<T> row;
+  if (act) row_load(row, i, off, col, val);
+  pdl_wait();
+  if (act) rho[i] = (T)r[i] - row_dot(row, col, val, u);
+  pdl_trigger();
 }
 
 // F = P^T rho on the auxiliary nodes, and U = 0 (start of the V-cycle)
@@ -73,9 +156,15 @@ __global__ void k_restrict_fine(int64_t nJ, const int64_t* __restrict__ off, con
                                 const T* __restrict__ val, const T* __restrict__ rho, T* __restrict__ F,
                                 T* __restrict__ U) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= nJ) return;
-  F[k] = sell_dot<T, T>(k, off, col, val, rho);
-  U[k] = 0;
+  const bool act = k < nJ;
+  Row<T> row;
+  if (act) row_load(row, k, off, col, val);
+  pdl_wait();
+  if (act) {
+    F[k] = row_dot(row, col, val, rho);
+    U[k] = 0;
+  }
+  pdl_trigger();
 }
 
 // u += P U
@@ -83,8 +172,12 @@ template <class T>
 __global__ void k_prolong_fine(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                const T* __restrict__ val, const T* __restrict__ U, T* __restrict__ u) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  u[i] += sell_dot<T, T>(i, off, col, val, U);
+  const bool act = i < n;
+  Row<T> row;
+  if (act) row_load(row, i, off, col, val);
+  pdl_wait();
+  if (act) u[i] += row_dot(row, col, val, U);
+  pdl_trigger();
 }
 
 // ------------------------------------------------------ auxiliary levels
@@ -94,13 +187,24 @@ __global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off
                          const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
                          const T* __restrict__ rhs, int rhs_local, T* __restrict__ save, T* U) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= k0 + nk) return;
-  const int32_t i = rows[k];
-  if (i < 0) return;
-  const T f = rhs_local ? rhs[k] : rhs[i];
-  if (save) save[k] = f;
-  const T s = f - sell_dot<T, T>(k, off, col, val, U);
-  U[i] += s * dinv[k];
+  int32_t i = -1;
+  Row<T> row;
+  T di = 0;
+  if (k < k0 + nk) {
+    i = rows[k];
+    if (i >= 0) {
+      row_load(row, k, off, col, val);
+      di = dinv[k];
+    }
+  }
+  pdl_wait();
+  if (i >= 0) {
+    const T f = rhs_local ? rhs[k] : rhs[i];
+    if (save) save[k] = f;
+    const T s = f - row_dot(row, col, val, U);
+    U[i] += s * di;
+  }
+  pdl_trigger();
 }
 
 // F_i -= sum_{j in N~_l} a_ij U_j on the rows E_l
@@ -109,10 +213,15 @@ __global__ void k_resid_aux(int64_t n, const int64_t* __restrict__ off, const in
                             const T* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
                             T* __restrict__ F) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int32_t i = rows[k];
-  if (i < 0) return;
-  F[i] -= sell_dot<T, T>(k, off, col, val, U);
+  int32_t i = -1;
+  Row<T> row;
+  if (k < n) {
+    i = rows[k];
+    if (i >= 0) row_load(row, k, off, col, val);
+  }
+  pdl_wait();
+  if (i >= 0) F[i] -= row_dot(row, col, val, U);
+  pdl_trigger();
 }
 
 // I_l^T: F[parent] += 1/2 sum F[new children]; and save + clear U on N~_l
@@ -121,18 +230,24 @@ __global__ void k_restrict_aux(int64_t npar, const int32_t* __restrict__ pid, co
                                const int32_t* __restrict__ child, T* __restrict__ F, int64_t nsm,
                                const int32_t* __restrict__ rows, T* __restrict__ U, T* __restrict__ us) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int32_t par = -1, p0 = 0, p1 = 0, i = -1;
   if (t < npar) {
+    par = pid[t];
+    p0 = pptr[t];
+    p1 = pptr[t + 1];
+  }
+  if (t < nsm) i = rows[t];
+  pdl_wait();
+  if (par >= 0) {
     T acc = 0;
-    for (int32_t p = pptr[t]; p < pptr[t + 1]; ++p) acc += F[child[p]];
-    F[pid[t]] += (T)0.5 * acc;
+    for (int32_t p = p0; p < p1; ++p) acc += F[child[p]];
+    F[par] += (T)0.5 * acc;
   }
-  if (t < nsm) {
-    const int32_t i = rows[t];
-    if (i >= 0) {
-      us[t] = U[i];
-      U[i] = 0;
-    }
+  if (i >= 0) {
+    us[t] = U[i];
+    U[i] = 0;
   }
+  pdl_trigger();
 }
 
 // I_l: U[new] = (U[p0] + U[p1]) / 2, Dirichlet parents contribute 0
@@ -140,20 +255,29 @@ template <class T>
 __global__ void k_prolong_aux(int64_t nnew, const int32_t* __restrict__ id, const int32_t* __restrict__ p0,
                               const int32_t* __restrict__ p1, T* U) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nnew) return;
-  const int32_t a = p0[t], b = p1[t];
-  T v = 0;
-  if (a >= 0) v += U[a];
-  if (b >= 0) v += U[b];
-  U[id[t]] = (T)0.5 * v;
+  int32_t a = -1, b = -1, me = -1;
+  if (t < nnew) {
+    a = p0[t];
+    b = p1[t];
+    me = id[t];
+  }
+  pdl_wait();
+  if (me >= 0) {
+    T v = 0;
+    if (a >= 0) v += U[a];
+    if (b >= 0) v += U[b];
+    U[me] = (T)0.5 * v;
+  }
+  pdl_trigger();
 }
 
 template <class T>
 __global__ void k_addsaved_aux(int64_t nsm, const int32_t* __restrict__ rows, const T* __restrict__ us, T* U) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nsm) return;
-  const int32_t i = rows[t];
+  const int32_t i = t < nsm ? rows[t] : -1;
+  pdl_wait();
   if (i >= 0) U[i] += us[t];
+  pdl_trigger();
 }
 
 // coarsest level: U[cid] = A_c^{-1} F[cid] in FP64, one warp per row
@@ -162,11 +286,14 @@ __global__ void k_coarse(int64_t nc, const int32_t* __restrict__ cid, const doub
                          const T* __restrict__ F, T* __restrict__ U) {
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (row >= nc) return;
-  double s = 0;
-  for (int64_t j = lane; j < nc; j += 32) s += inv[row * nc + j] * (double)F[cid[j]];
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) U[cid[row]] = (T)s;
+  pdl_wait();
+  if (row < nc) {
+    double s = 0;
+    for (int64_t j = lane; j < nc; j += 32) s += inv[row * nc + j] * (double)F[cid[j]];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) U[cid[row]] = (T)s;
+  }
+  pdl_trigger();
 }
 
 // ------------------------------------------------------------------ PCG
@@ -216,6 +343,7 @@ __device__ __forceinline__ void set_cond(PcgScalars* sc, int cond, cudaGraphCond
 __global__ void k_pcg_init(int64_t n, SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
                            double* __restrict__ r, double* partial, unsigned int* ticket, PcgScalars* sc, double rtol,
                            int maxit, double* hist, cudaGraphConditionalHandle hnd, int use_hnd) {
+  pdl_wait();
   double v[2] = {0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double ri = b[i] - sell_dot<double, double>(i, A.off, A.col, A.val, x);
@@ -244,6 +372,7 @@ __global__ void k_pcg_init(int64_t n, SellView<double> A, const double* __restri
 template <class T>
 __global__ void k_dots(int64_t n, const T* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q,
                        double* partial, unsigned int* ticket, PcgScalars* sc) {
+  pdl_wait();
   double v[2] = {0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double zi = (double)z[i];
@@ -264,14 +393,17 @@ __global__ void k_dots(int64_t n, const T* __restrict__ z, const double* __restr
 // p = z + beta p
 template <class T>
 __global__ void k_pupd(int64_t n, const T* __restrict__ z, double* __restrict__ p, const PcgScalars* __restrict__ sc) {
+  pdl_wait();
   const double beta = sc->beta;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (double)z[i] + beta * p[i];
+  pdl_trigger();
 }
 
 // q = A p, <p, q>  ->  alpha
 __global__ void k_spmv_dot(int64_t n, SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
                            double* partial, unsigned int* ticket, PcgScalars* sc) {
+  pdl_wait();
   double v[1] = {0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double qi = sell_dot<double, double>(i, A.off, A.col, A.val, p);
@@ -293,6 +425,7 @@ __global__ void k_spmv_dot(int64_t n, SellView<double> A, const double* __restri
 __global__ void k_axpy_norm(int64_t n, const double* __restrict__ p, const double* __restrict__ q,
                             double* __restrict__ x, double* __restrict__ r, double* partial, unsigned int* ticket,
                             PcgScalars* sc, double* hist, cudaGraphConditionalHandle hnd, int use_hnd) {
+  pdl_wait();
   const double a = sc->alpha;
   double v[1] = {0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -407,7 +540,7 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
         if (!nk) continue;
         const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
         LAUNCH(ASMG_PROF_AUX_GS, by,
-               k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
                                                     sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1,
                                                     sweep == 0 ? L.fs.p : nullptr, P.U.p));
         ++launches;
@@ -415,16 +548,16 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
     }
     auto RS = view(L.RS);
     LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
-           k_resid_aux<T><<<nblk(L.nrs), TPB, 0, s>>>(L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p));
+           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs), TPB, s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p));
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
-           k_restrict_aux<T><<<nblk(std::max(L.npar, L.nsm)), TPB, 0, s>>>(L.npar, L.rp_id.p, L.rp_ptr.p,
+           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm)), TPB, s, L.npar, L.rp_id.p, L.rp_ptr.p,
                                                                             L.rp_child.p, P.F.p, L.nsm, L.sm_rows.p,
                                                                             P.U.p, L.us.p));
     launches += 2;
   }
   if (h.nc > 0) {
     LAUNCH(ASMG_PROF_COARSE, h.nc * h.nc * 8 + h.nc * (4 + 2 * sz),
-           k_coarse<T><<<nblk(h.nc * 32), TPB, 0, s>>>(h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p));
+           launch(h.prm.use_pdl, k_coarse<T>, nblk(h.nc * 32), TPB, s, h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p));
     ++launches;
   }
   for (size_t li = 0; li < P.lev.size(); ++li) {
@@ -432,18 +565,18 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
     auto SM = view(L.SM);
     if (L.nnew) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
-             k_prolong_aux<T><<<nblk(L.nnew), TPB, 0, s>>>(L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p));
+             launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew), TPB, s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p));
       ++launches;
     }
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
-           k_addsaved_aux<T><<<nblk(L.nsm), TPB, 0, s>>>(L.nsm, L.sm_rows.p, L.us.p, P.U.p));
+           launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm), TPB, s, L.nsm, L.sm_rows.p, L.us.p, P.U.p));
     ++launches;
     for (int sweep = 0; sweep < npost; ++sweep)
       for (int c = L.ncolours - 1; c >= 0; --c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
         LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
-               k_gs_aux<T><<<nblk(nk), TPB, 0, s>>>(k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p,
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p,
                                                     1, nullptr, P.U.p));
         ++launches;
       }
@@ -465,21 +598,21 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
     ++launches;
   }
   // (2) u2 = u1 + P Btilde P^T (r - A u1)
   if (h.nJ > 0) {
     LAUNCH(ASMG_PROF_FINE_RESID, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
-           k_resid_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p));
+           launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p));
     auto PT = view(P.PT);
     LAUNCH(ASMG_PROF_RESTRICT, P.PT.nnz_real * (sz + 4) + n * sz + 2 * nJ * sz,
-           k_restrict_fine<T><<<nblk(h.nJpad), TPB, 0, s>>>(h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p));
+           launch(h.prm.use_pdl, k_restrict_fine<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p));
     launches += 2;
     launches += enqueue_vcycle<T>(h, s);
     auto PP = view(P.P);
     LAUNCH(ASMG_PROF_PROLONG, P.P.nnz_real * (sz + 4) + nJ * sz + 2 * n * sz,
-           k_prolong_fine<T><<<nblk(h.npad), TPB, 0, s>>>(h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p));
+           launch(h.prm.use_pdl, k_prolong_fine<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p));
     ++launches;
   }
   // (3) u3 = u2 + S^T (r - A u2): backward multicolour sweep
@@ -487,7 +620,7 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           k_gs_fine<T, double><<<nblk(nr), TPB, 0, s>>>(r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
     ++launches;
   }
   ASMG_CUDA(cudaGetLastError());
@@ -501,12 +634,12 @@ int enqueue_body(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int 
   const int G = RED_BLOCKS;
   const int64_t n = h.n, sz = sizeof(T);
   LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16),
-         k_dots<T><<<G, TPB, 0, s>>>(h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
-  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), k_pupd<T><<<G, TPB, 0, s>>>(h.npad, z, h.p.p, h.scal.p));
+         launch(h.prm.use_pdl, k_dots<T>, G, TPB, s, h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_pupd<T>, G, TPB, s, h.npad, z, h.p.p, h.scal.p));
   LAUNCH(ASMG_PROF_CG_SPMV, h.A64.nnz_real * 12 + n * 16,
-         k_spmv_dot<<<G, TPB, 0, s>>>(h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
+         launch(h.prm.use_pdl, k_spmv_dot, G, TPB, s, h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
   LAUNCH(ASMG_PROF_CG_VECTOR, n * 48,
-         k_axpy_norm<<<G, TPB, 0, s>>>(h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
+         launch(h.prm.use_pdl, k_axpy_norm, G, TPB, s, h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
                                        h.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
   return launches + 4;
@@ -519,7 +652,7 @@ int enqueue_body_any(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, 
 
 void enqueue_init(asmg_s& h, double rtol, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
   LAUNCH(ASMG_PROF_CG_VECTOR, h.A64.nnz_real * 12 + h.n * 32,
-         k_pcg_init<<<RED_BLOCKS, TPB, 0, s>>>(h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p,
+         launch(h.prm.use_pdl, k_pcg_init, RED_BLOCKS, TPB, s, h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p,
                                                h.scal.p, rtol, h.prm.max_iter, h.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
 }
@@ -527,15 +660,15 @@ void enqueue_init(asmg_s& h, double rtol, cudaStream_t s, cudaGraphConditionalHa
 }  // namespace
 
 void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s) {
-  k_gather<<<nblk(h.npad), TPB, 0, s>>>(h.npad, h.d_vertex_of_row.p, vsrc, dst);
+  launch(false, k_gather, nblk(h.npad), TPB, s, h.npad, h.d_vertex_of_row.p, vsrc, dst);
   ASMG_CUDA(cudaGetLastError());
 }
 
 void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cudaStream_t s) {
   if (src_float)
-    k_scatter<float><<<nblk(h.mesh.nv), TPB, 0, s>>>(h.mesh.nv, h.d_row_of_vertex.p, (const float*)src, vdst);
+    launch(false, k_scatter<float>, nblk(h.mesh.nv), TPB, s, h.mesh.nv, h.d_row_of_vertex.p, (const float*)src, vdst);
   else
-    k_scatter<double><<<nblk(h.mesh.nv), TPB, 0, s>>>(h.mesh.nv, h.d_row_of_vertex.p, (const double*)src, vdst);
+    launch(false, k_scatter<double>, nblk(h.mesh.nv), TPB, s, h.mesh.nv, h.d_row_of_vertex.p, (const double*)src, vdst);
   ASMG_CUDA(cudaGetLastError());
 }
 
@@ -552,7 +685,7 @@ __global__ void k_spmv64(int64_t n, SellView<double> A, const double* __restrict
 }
 
 void spmv64(asmg_s& h, const double* x, double* y, cudaStream_t s) {
-  k_spmv64<<<nblk(h.npad), TPB, 0, s>>>(h.npad, view(h.A64), x, y);
+  launch(false, k_spmv64, nblk(h.npad), TPB, s, h.npad, view(h.A64), x, y);
   ASMG_CUDA(cudaGetLastError());
 }
 

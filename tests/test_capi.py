@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_params(lib):
     p = lib.asmg_default_params()
-    assert (p.n_min, p.nu_pre, p.nu_post, p.coarse_max_dofs, p.precision, p.max_iter, p.smoothing) == (3, 2, 2, 512, 0, 500, 0)
+    assert (p.n_min, p.nu_pre, p.nu_post, p.coarse_max_dofs, p.precision, p.max_iter, p.smoothing, p.use_graph,
+            p.use_pdl) == (3, 2, 2, 512, 0, 500, 0, 1, 1)
 
 
 def _mesh(gen):
