@@ -25,8 +25,10 @@
 //   R8  Algorithm 1 with "+" corrections applied from zero as a preconditioner
 //   R9  flexible (Polak-Ribiere) beta in PCG, stop at ||r|| <= rtol ||b||
 //   R10 colouring = Jones-Plassmann with splitmix64 priorities, smallest
-//       free colour; the same definition is implemented independently on
-//       the device, so no colouring is ever passed from one side to the other
+//       free colour, on the non-vanishing couplings, then three rounds of
+//       iterated greedy recolouring; the same definition is implemented
+//       independently on the device, so no colouring is ever passed from one
+//       side to the other
 //
 // 3D: fine assembly, mass matrix and the octree are dimension-generic; the
 // auxiliary hierarchy is built for d = 2 only.
@@ -900,11 +902,22 @@ void build_transfer(Oracle& o) {
 }
 
 // --------------------------------------------------------------------------
-// Colouring (R10): Jones-Plassmann with splitmix64 priorities.
+// Colouring (R10): Jones-Plassmann with splitmix64 priorities on the graph of
+// couplings |a_vw| > 1e-12 sqrt(a_vv a_ww) (entries that vanish by symmetry,
+// e.g. across the hypotenuse of a right isosceles triangle, are not
+// couplings), then `ig_rounds` rounds of iterated greedy recolouring (classes
+// visited in descending order; each node takes the smallest colour unused by
+// the neighbours already visited in that round).
 // --------------------------------------------------------------------------
 
+bool coupled(const CSR& A, int64_t p, int32_t v, const std::vector<double>& diag) {
+  int32_t w = A.col[p];
+  if (w == v) return false;
+  return std::fabs(A.val[p]) > 1e-12 * std::sqrt(diag[v] * diag[w]);
+}
+
 void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<uint64_t>& prio_key,
-               std::vector<int32_t>& colour, int mode) {
+               std::vector<int32_t>& colour, int mode, int ig_rounds) {
   colour.assign(A.nr, -1);
   std::vector<uint8_t> in(A.nr, 0);
   for (auto v : set) in[v] = 1;
@@ -914,6 +927,8 @@ void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<
     for (size_t k = 0; k < s.size(); ++k) colour[s[k]] = (int32_t)k;
     return;
   }
+  std::vector<double> diag(A.nr, 0.0);
+  for (int64_t i = 0; i < A.nr; ++i) diag[i] = A.get(i, (int32_t)i);
   auto prio = [&](int32_t v) { return std::make_pair(splitmix64(prio_key[v]), prio_key[v]); };
   std::vector<int32_t> todo = set;
   while (!todo.empty()) {
@@ -923,7 +938,7 @@ void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<
       auto pv = prio(v);
       for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
         int32_t w = A.col[p];
-        if (w == v || !in[w] || colour[w] >= 0) continue;
+        if (!in[w] || colour[w] >= 0 || !coupled(A, p, v, diag)) continue;
         if (prio(w) > pv) {
           win = false;
           break;
@@ -935,7 +950,7 @@ void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<
       std::vector<uint8_t> used;
       for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
         int32_t w = A.col[p];
-        if (w == v || !in[w] || colour[w] < 0) continue;
+        if (!in[w] || colour[w] < 0 || !coupled(A, p, v, diag)) continue;
         if ((size_t)colour[w] >= used.size()) used.resize(colour[w] + 1, 0);
         used[colour[w]] = 1;
       }
@@ -944,6 +959,26 @@ void jp_colour(const CSR& A, const std::vector<int32_t>& set, const std::vector<
       colour[v] = cc;
     }
     todo.swap(rest);
+  }
+  for (int round = 0; round < ig_rounds; ++round) {
+    int32_t ncol = 0;
+    for (auto v : set) ncol = std::max(ncol, colour[v] + 1);
+    std::vector<int32_t> next(A.nr, -1);
+    for (int32_t c = ncol - 1; c >= 0; --c)
+      for (auto v : set) {
+        if (colour[v] != c) continue;
+        std::vector<uint8_t> used;
+        for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+          int32_t w = A.col[p];
+          if (!in[w] || colour[w] <= c || !coupled(A, p, v, diag)) continue;  // visited earlier this round
+          if ((size_t)next[w] >= used.size()) used.resize(next[w] + 1, 0);
+          used[next[w]] = 1;
+        }
+        int32_t cc = 0;
+        while ((size_t)cc < used.size() && used[cc]) ++cc;
+        next[v] = cc;
+      }
+    for (auto v : set) colour[v] = next[v];
   }
 }
 
@@ -966,11 +1001,11 @@ void build_colourings(Oracle& o) {
     all[i] = (int32_t)i;
     pk[i] = (uint64_t)o.vertex_of_free[i];
   }
-  jp_colour(o.A, all, pk, o.fine_colour, o.prm.colouring);
+  jp_colour(o.A, all, pk, o.fine_colour, o.prm.colouring, 3);
   order_by_colour(all, o.fine_colour, o.fine_smooth, o.fine_cstart);
   for (int l = o.c + 1; l <= o.J; ++l) {
     Level& L = o.lv[l];
-    jp_colour(L.A, L.smooth, L.key, L.colour, o.prm.colouring);
+    jp_colour(L.A, L.smooth, L.key, L.colour, o.prm.colouring, 3);
     std::vector<int32_t> set = L.smooth;
     order_by_colour(set, L.colour, L.smooth, L.cstart);
   }

@@ -166,7 +166,13 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x ^ (x >> 31);
 }
 
+// a coupling of the colouring graph: |a_vw| > 1e-12 sqrt(a_vv a_ww), w != v
+__device__ __forceinline__ bool coupled(int32_t v, int32_t w, double a, const double* __restrict__ diag) {
+  return w != v && fabs(a) > 1e-12 * sqrt(diag[v] * diag[w]);
+}
+
 __global__ void k_jp_cand(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const double* __restrict__ diag,
                           const uint8_t* __restrict__ inset, const uint64_t* __restrict__ pk,
                           const int32_t* __restrict__ colour, uint8_t* __restrict__ cand) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -176,7 +182,7 @@ __global__ void k_jp_cand(int64_t n, const int64_t* __restrict__ ptr, const int3
   const uint64_t hv = mix64(pk[v]), kv = pk[v];
   for (int64_t p = ptr[v]; p < ptr[v + 1]; ++p) {
     int32_t w = col[p];
-    if (w == v || !inset[w] || colour[w] >= 0) continue;
+    if (!inset[w] || colour[w] >= 0 || !coupled((int32_t)v, w, val[p], diag)) continue;
     uint64_t hw = mix64(pk[w]);
     if (hw > hv || (hw == hv && pk[w] > kv)) return;
   }
@@ -184,6 +190,7 @@ __global__ void k_jp_cand(int64_t n, const int64_t* __restrict__ ptr, const int3
 }
 
 __global__ void k_jp_assign(int64_t n, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const double* __restrict__ diag,
                             const uint8_t* __restrict__ inset, const uint8_t* __restrict__ cand,
                             int32_t* __restrict__ colour, unsigned long long* __restrict__ ncol, int* bad) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -191,7 +198,7 @@ __global__ void k_jp_assign(int64_t n, const int64_t* __restrict__ ptr, const in
   uint64_t used[2] = {0, 0};
   for (int64_t p = ptr[v]; p < ptr[v + 1]; ++p) {
     int32_t w = col[p];
-    if (w == v || !inset[w]) continue;
+    if (!inset[w] || !coupled((int32_t)v, w, val[p], diag)) continue;
     int32_t c = colour[w];
     if (c >= 0 && c < 128) used[c >> 6] |= 1ULL << (c & 63);
   }
@@ -200,6 +207,27 @@ __global__ void k_jp_assign(int64_t n, const int64_t* __restrict__ ptr, const in
   if (c >= 128) atomicOr(bad, 1);
   colour[v] = c;
   atomicAdd(ncol, 1ULL);
+}
+
+// one class of an iterated-greedy round: nodes of class c take the smallest
+// colour unused by their neighbours of the classes already visited (> c)
+__global__ void k_ig_class(int64_t n, int32_t c, const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ diag,
+                           const uint8_t* __restrict__ inset, const int32_t* __restrict__ colour,
+                           int32_t* __restrict__ next, int* bad) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= n || !inset[v] || colour[v] != c) return;
+  uint64_t used[2] = {0, 0};
+  for (int64_t p = ptr[v]; p < ptr[v + 1]; ++p) {
+    int32_t w = col[p];
+    if (!inset[w] || colour[w] <= c || !coupled((int32_t)v, w, val[p], diag)) continue;
+    int32_t k = next[w];
+    if (k >= 0 && k < 128) used[k >> 6] |= 1ULL << (k & 63);
+  }
+  int k = 0;
+  while (k < 128 && ((used[k >> 6] >> (k & 63)) & 1)) ++k;
+  if (k >= 128) atomicOr(bad, 1);
+  next[v] = k;
 }
 
 }  // namespace
@@ -252,14 +280,21 @@ std::vector<int32_t> jp_colour_gpu(const HostCSR& A, const std::vector<uint8_t>&
   int64_t todo = 0;
   for (auto f : inset) todo += f;
   if (n == 0 || todo == 0) return out;
+  std::vector<double> diag(n, 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+      if (A.col[p] == i) diag[i] = A.val[p];
   DBuf<int64_t> ptr;
-  DBuf<int32_t> col, colour;
+  DBuf<int32_t> col, colour, next;
+  DBuf<double> val, dg;
   DBuf<uint8_t> ins, cand;
   DBuf<uint64_t> pk;
   DBuf<unsigned long long> cnt;
   DBuf<int> bad;
   ptr.upload(A.ptr, s);
   col.upload(A.col, s);
+  val.upload(A.val, s);
+  dg.upload(diag, s);
   ins.upload(inset, s);
   pk.upload(prio_key, s);
   colour.upload(out, s);
@@ -270,13 +305,26 @@ std::vector<int32_t> jp_colour_gpu(const HostCSR& A, const std::vector<uint8_t>&
   bad.zero(s);
   unsigned long long done = 0;
   for (int round = 0; round < 100000 && (int64_t)done < todo; ++round) {
-    k_jp_cand<<<nblk(n), 256, 0, s>>>(n, ptr.p, col.p, ins.p, pk.p, colour.p, cand.p);
-    k_jp_assign<<<nblk(n), 256, 0, s>>>(n, ptr.p, col.p, ins.p, cand.p, colour.p, cnt.p, bad.p);
+    k_jp_cand<<<nblk(n), 256, 0, s>>>(n, ptr.p, col.p, val.p, dg.p, ins.p, pk.p, colour.p, cand.p);
+    k_jp_assign<<<nblk(n), 256, 0, s>>>(n, ptr.p, col.p, val.p, dg.p, ins.p, cand.p, colour.p, cnt.p, bad.p);
     ASMG_CUDA(cudaGetLastError());
     ASMG_CUDA(cudaMemcpyAsync(&done, cnt.p, 8, cudaMemcpyDeviceToHost, s));
     ASMG_CUDA(cudaStreamSynchronize(s));
   }
   if ((int64_t)done != todo) ASMG_FAIL(ASMG_ERR_CUDA, "colouring did not finish");
+  // three rounds of iterated greedy recolouring, classes in descending order
+  next.alloc(n);
+  for (int round = 0; round < 3; ++round) {
+    std::vector<int32_t> hc = colour.download(s);
+    int32_t ncol = 0;
+    for (int64_t v = 0; v < n; ++v)
+      if (inset[v]) ncol = std::max(ncol, hc[v] + 1);
+    ASMG_CUDA(cudaMemsetAsync(next.p, 0xff, 4 * n, s));
+    for (int32_t c = ncol - 1; c >= 0; --c)
+      k_ig_class<<<nblk(n), 256, 0, s>>>(n, c, ptr.p, col.p, val.p, dg.p, ins.p, colour.p, next.p, bad.p);
+    ASMG_CUDA(cudaGetLastError());
+    ASMG_CUDA(cudaMemcpyAsync(colour.p, next.p, 4 * n, cudaMemcpyDeviceToDevice, s));
+  }
   auto hb = bad.download(s);
   if (hb[0]) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "more than 128 colours needed");
   return colour.download(s);

@@ -64,6 +64,7 @@ HostCSR select_rows(const HostCSR& A, const std::vector<int64_t>& sel, const std
       for (int64_t p = A.ptr[sel[k]]; p < A.ptr[sel[k] + 1]; ++p) {
         int32_t c = A.col[p];
         if (colkeep && !(*colkeep)[c]) continue;
+        if (A.val[p] == 0.0) continue;  // couplings that vanish by symmetry are not stored
         B.col.push_back(cmap ? (*cmap)[c] : c);
         B.val.push_back(A.val[p]);
       }
