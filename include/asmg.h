@@ -198,7 +198,8 @@ enum asmg_prof_class {
   ASMG_PROF_COARSE = 7,       /* coarsest-level solve */
   ASMG_PROF_CG_SPMV = 8,      /* PCG q = A p with <p, q> (FP64) */
   ASMG_PROF_CG_VECTOR = 9,    /* PCG vector updates and reductions */
-  ASMG_PROF_NCLASS = 10
+  ASMG_PROF_AUX_SMALL = 10,   /* runs of small auxiliary levels fused into one thread block */
+  ASMG_PROF_NCLASS = 11
 };
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
 

@@ -170,7 +170,7 @@ def amg_export(h, what, level: int = 0) -> np.ndarray:
 
 
 PROF_CLASSES = ["fine_gs", "fine_resid", "restrict", "prolong", "aux_gs", "aux_resid", "aux_transfer", "coarse",
-                "cg_spmv", "cg_vector"]
+                "cg_spmv", "cg_vector", "aux_small"]
 
 
 def amg_profile(h, b, rtol: float, stream=None):

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include "handle.h"
 
@@ -71,6 +72,110 @@ HostCSR select_rows(const HostCSR& A, const std::vector<int64_t>& sel, const std
     B.ptr[k + 1] = (int64_t)B.col.size();
   }
   return B;
+}
+
+// Shared-memory form of a small level: local numbering (smoothing nodes in
+// colour order first, then the other rows of E_l), 16-bit local columns.
+template <class T>
+void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<uint8_t>& inset,
+                 const std::vector<int64_t>& sel, const std::vector<int64_t>& rsel, const std::vector<T>& dinv_pad,
+                 const std::vector<int32_t>& pid, const std::vector<int32_t>& pptr, const std::vector<int32_t>& child,
+                 AuxLevelDev<T>& D, cudaStream_t s) {
+  SmallLevelDev<T>& S = D.small;
+  S.ok = false;
+  std::vector<int32_t> gid;
+  std::vector<T> dinv;
+  std::vector<int> cs(1, 0);
+  for (int c = 0; c < D.ncolours; ++c) {
+    for (int64_t k = D.cstart[c]; k < D.cstart[c + 1]; ++k)
+      if (sel[k] >= 0) {
+        gid.push_back((int32_t)sel[k]);
+        dinv.push_back(dinv_pad[k]);
+      }
+    cs.push_back((int)gid.size());
+  }
+  const int mS = (int)gid.size();
+  for (int64_t r : rsel)
+    if (r >= 0 && !inset[r]) gid.push_back((int32_t)r);
+  const int mE = (int)gid.size();
+  if (mE > SMALL_LMAX || D.ncolours > SMALL_MAXC) return;
+  std::unordered_map<int32_t, int32_t> loc;
+  loc.reserve(mE * 2);
+  for (int k = 0; k < mE; ++k) loc[gid[k]] = k;
+  auto L_ = [&](int32_t g) -> int32_t {
+    auto it = loc.find(g);
+    return it == loc.end() ? -1 : it->second;
+  };
+  std::vector<int32_t> sm_ptr(1, 0), rs_ptr(1, 0);
+  std::vector<uint16_t> sm_col, rs_col;
+  std::vector<T> sm_val, rs_val;
+  for (int k = 0; k < mE; ++k) {
+    const int32_t r = gid[k];
+    for (int64_t p = Arows.ptr[r]; p < Arows.ptr[r + 1]; ++p) {
+      if (Arows.val[p] == 0.0) continue;
+      const int32_t c = Arows.col[p];
+      if (k < mS) {
+        const int32_t lc = L_(c);
+        if (lc < 0) return;  // a neighbour outside E_l: keep the level on the general path
+        sm_col.push_back((uint16_t)lc);
+        sm_val.push_back((T)Arows.val[p]);
+      }
+      if (inset[c]) {
+        const int32_t lc = L_(c);
+        if (lc < 0) return;
+        rs_col.push_back((uint16_t)lc);
+        rs_val.push_back((T)Arows.val[p]);
+      }
+    }
+    if (k < mS) sm_ptr.push_back((int32_t)sm_col.size());
+    rs_ptr.push_back((int32_t)rs_col.size());
+  }
+  std::vector<uint16_t> nn_id, rp_id, rp_child;
+  std::vector<int32_t> nn_p0, nn_p1, rp_ptr(1, 0);
+  for (size_t t = 0; t < L.new_id.size(); ++t) {
+    const int32_t a = L_(L.new_id[t]);
+    const int32_t b0 = L.new_p0[t] >= 0 ? L_(L.new_p0[t]) : -1;
+    const int32_t b1 = L.new_p1[t] >= 0 ? L_(L.new_p1[t]) : -1;
+    if (a < 0 || (L.new_p0[t] >= 0 && b0 < 0) || (L.new_p1[t] >= 0 && b1 < 0)) return;
+    nn_id.push_back((uint16_t)a);
+    nn_p0.push_back(b0);
+    nn_p1.push_back(b1);
+  }
+  for (size_t t = 0; t < pid.size(); ++t) {
+    const int32_t a = L_(pid[t]);
+    if (a < 0) return;
+    rp_id.push_back((uint16_t)a);
+    for (int32_t p = pptr[t]; p < pptr[t + 1]; ++p) {
+      const int32_t b = L_(child[p]);
+      if (b < 0) return;
+      rp_child.push_back((uint16_t)b);
+    }
+    rp_ptr.push_back((int32_t)rp_child.size());
+  }
+  S.mS = mS;
+  S.mE = mE;
+  S.ncol = D.ncolours;
+  S.nnew = (int)nn_id.size();
+  S.npar = (int)rp_id.size();
+  S.nnz_sm = (int64_t)sm_col.size();
+  S.nnz_rs = (int64_t)rs_col.size();
+  S.nchild = (int64_t)rp_child.size();
+  S.cs = cs;
+  S.gid.upload(gid, s);
+  S.sm_ptr.upload(sm_ptr, s);
+  S.sm_col.upload(sm_col, s);
+  S.sm_val.upload(sm_val, s);
+  S.dinv.upload(dinv, s);
+  S.rs_ptr.upload(rs_ptr, s);
+  S.rs_col.upload(rs_col, s);
+  S.rs_val.upload(rs_val, s);
+  S.nn_id.upload(nn_id, s);
+  S.nn_p0.upload(nn_p0, s);
+  S.nn_p1.upload(nn_p1, s);
+  S.rp_id.upload(rp_id, s);
+  S.rp_ptr.upload(rp_ptr, s);
+  S.rp_child.upload(rp_child, s);
+  S.ok = true;
 }
 
 template <class T>
@@ -159,6 +264,7 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
   D.us.alloc(std::max<int64_t>(D.nsm, 1));
   D.fs.zero(s);
   D.us.zero(s);
+  build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, D, s);
 }
 
 // triangles given by lattice keys -> device coordinates, ids, coefficients

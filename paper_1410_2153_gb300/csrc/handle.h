@@ -32,6 +32,8 @@ struct Prec {
   Sell<T> P, PT;               // Scott-Zhang transfer and its transpose
   std::vector<AuxLevelDev<T>> lev;  // levels c+1..J (index 0 = c+1)
   DBuf<T> uf, rho, F, U;       // fine work vector, fine residual, aux rhs / solution
+  int n_deep = 0, n_bottom = 0;  // fused small-level runs (top of the hierarchy, bottom)
+  DBuf<SmallDesc<T>> deep_desc, bot_desc;
 };
 
 }  // namespace asmg

@@ -179,6 +179,45 @@ HostCSR assemble_triangles(int64_t ntri, const double* dXY, const int32_t* dID, 
 std::vector<int32_t> jp_colour_gpu(const HostCSR& A, const std::vector<uint8_t>& inset,
                                    const std::vector<uint64_t>& prio_key, cudaStream_t s);
 
+// A level small enough to run inside one thread block with its rhs and
+// correction in shared memory (see k_small_down / k_small_up).  Local node
+// k < mS is the k-th smoothing node (colour order); mS <= k < mE are the other
+// nodes of the rows E_l.  Column indices are local (16 bit).
+constexpr int SMALL_LMAX = 8192;
+constexpr int SMALL_MAXC = 24;
+template <class T>
+struct SmallDesc {
+  int mS, mE, ncol, nnew, npar;
+  int cs[SMALL_MAXC + 1];
+  const int32_t* gid;
+  const int32_t* sm_ptr;
+  const uint16_t* sm_col;
+  const T* sm_val;
+  const T* dinv;
+  const int32_t* rs_ptr;
+  const uint16_t* rs_col;
+  const T* rs_val;
+  const uint16_t* nn_id;
+  const int32_t* nn_p0;
+  const int32_t* nn_p1;
+  const uint16_t* rp_id;
+  const int32_t* rp_ptr;
+  const uint16_t* rp_child;
+  T* fs;
+  T* us;
+};
+
+template <class T>
+struct SmallLevelDev {
+  bool ok = false;  // level fits the small-level kernels
+  int mS = 0, mE = 0, ncol = 0, nnew = 0, npar = 0;
+  int64_t nnz_sm = 0, nnz_rs = 0, nchild = 0;
+  std::vector<int> cs;
+  DBuf<int32_t> gid, sm_ptr, rs_ptr, nn_p0, nn_p1, rp_ptr;
+  DBuf<uint16_t> sm_col, rs_col, nn_id, rp_id, rp_child;
+  DBuf<T> sm_val, dinv, rs_val;
+};
+
 // ------------------------------------------------------------ solve data
 template <class T>
 struct AuxLevelDev {
@@ -199,6 +238,7 @@ struct AuxLevelDev {
   DBuf<int32_t> rp_id;           // parents receiving restricted residuals
   DBuf<int32_t> rp_ptr, rp_child;
   DBuf<T> fs, us;                // saved rhs / pre-smoothed values on N~_l
+  SmallLevelDev<T> small;        // shared-memory form, when the level is small
 };
 
 struct Stats {

@@ -33,6 +33,23 @@ constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
 
 int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
 
+// Kernel launch with dynamic shared memory, optionally with programmatic dependent launch.
+template <typename... KArgs, typename... Args>
+void launch_smem(bool pdl, void (*kern)(KArgs...), int64_t grid, int block, size_t smem, cudaStream_t s,
+                 Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  ASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 // Kernel launch, optionally with programmatic dependent launch (the kernel may
 // start while its predecessor on the stream finishes; see pdl_wait below).
 template <typename... KArgs, typename... Args>
@@ -296,6 +313,101 @@ __global__ void k_coarse(int64_t nc, const int32_t* __restrict__ cid, const doub
   pdl_trigger();
 }
 
+// ---------------------------------------------------- small levels, fused
+// A run of small levels in one thread block.  Per level the rhs F and the
+// correction U of the rows E_l live in shared memory; colour phases are
+// separated by __syncthreads instead of kernel boundaries.  The steps are
+// those of k_gs_aux / k_resid_aux / k_restrict_aux (down) and
+// k_prolong_aux / k_addsaved_aux / k_gs_aux (up).
+constexpr int SMALL_TPB = 1024;
+
+template <class T>
+__global__ void __launch_bounds__(SMALL_TPB, 1)
+    k_small_down(const SmallDesc<T>* __restrict__ D, int nlev, T* F, int nu) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Ul = reinterpret_cast<T*>(smraw);
+  T* Fl = Ul + SMALL_LMAX;
+  pdl_wait();
+  for (int d = 0; d < nlev; ++d) {
+    const SmallDesc<T>& L = D[d];
+    const int mS = L.mS, mE = L.mE;
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
+      const T f = F[L.gid[k]];
+      Fl[k] = f;
+      Ul[k] = 0;
+      if (k < mS) L.fs[k] = f;
+    }
+    __syncthreads();
+    for (int sw = 0; sw < nu; ++sw)
+      for (int c = 0; c < L.ncol; ++c) {
+        for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
+          T acc = Fl[k];
+          for (int p = L.sm_ptr[k]; p < L.sm_ptr[k + 1]; ++p) acc -= L.sm_val[p] * Ul[L.sm_col[p]];
+          Ul[k] += acc * L.dinv[k];
+        }
+        __syncthreads();
+      }
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
+      T acc = 0;
+      for (int p = L.rs_ptr[k]; p < L.rs_ptr[k + 1]; ++p) acc += L.rs_val[p] * Ul[L.rs_col[p]];
+      Fl[k] -= acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L.npar; t += blockDim.x) {
+      T acc = 0;
+      for (int p = L.rp_ptr[t]; p < L.rp_ptr[t + 1]; ++p) acc += Fl[L.rp_child[p]];
+      Fl[L.rp_id[t]] += (T)0.5 * acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
+      F[L.gid[k]] = Fl[k];
+      if (k < mS) L.us[k] = Ul[k];
+    }
+    __syncthreads();
+  }
+  pdl_trigger();
+}
+
+template <class T>
+__global__ void __launch_bounds__(SMALL_TPB, 1)
+    k_small_up(const SmallDesc<T>* __restrict__ D, int nlev, T* U, int nu) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Ul = reinterpret_cast<T*>(smraw);
+  T* Fl = Ul + SMALL_LMAX;
+  pdl_wait();
+  for (int d = nlev - 1; d >= 0; --d) {
+    const SmallDesc<T>& L = D[d];
+    const int mS = L.mS, mE = L.mE;
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
+      Ul[k] = U[L.gid[k]];
+      if (k < mS) Fl[k] = L.fs[k];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < L.nnew; t += blockDim.x) {
+      const int32_t a = L.nn_p0[t], b = L.nn_p1[t];
+      T v = 0;
+      if (a >= 0) v += Ul[a];
+      if (b >= 0) v += Ul[b];
+      Ul[L.nn_id[t]] = (T)0.5 * v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < mS; k += blockDim.x) Ul[k] += L.us[k];
+    __syncthreads();
+    for (int sw = 0; sw < nu; ++sw)
+      for (int c = L.ncol - 1; c >= 0; --c) {
+        for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
+          T acc = Fl[k];
+          for (int p = L.sm_ptr[k]; p < L.sm_ptr[k + 1]; ++p) acc -= L.sm_val[p] * Ul[L.sm_col[p]];
+          Ul[k] += acc * L.dinv[k];
+        }
+        __syncthreads();
+      }
+    for (int k = threadIdx.x; k < mS; k += blockDim.x) U[L.gid[k]] = Ul[k];
+    __syncthreads();
+  }
+  pdl_trigger();
+}
+
 // ------------------------------------------------------------------ PCG
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -525,12 +637,36 @@ template <>
 Prec<float>& prec<float>(asmg_s& h) { return h.p32; }
 
 template <class T>
+int64_t small_bytes(const Prec<T>& P, int first, int count, int nu, bool down) {
+  const int64_t sz = sizeof(T);
+  int64_t by = 0;
+  for (int k = 0; k < count; ++k) {
+    const SmallLevelDev<T>& S = P.lev[first + k].small;
+    by += nu * (S.nnz_sm * (2 + sz) + (int64_t)S.mS * (4 + sz));
+    if (down)
+      by += (int64_t)S.mE * (4 + 2 * sz) + (int64_t)S.mS * 2 * sz + S.nnz_rs * (2 + sz) + (int64_t)S.mE * 4 +
+            (int64_t)S.npar * 10 + S.nchild * 2;
+    else
+      by += (int64_t)S.mE * (4 + sz) + (int64_t)S.mS * 3 * sz + (int64_t)S.nnew * 10;
+  }
+  return by;
+}
+
+template <class T>
 int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
   int launches = 0;
   const int64_t sz = sizeof(T);
   const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
-  for (int li = (int)P.lev.size() - 1; li >= 0; --li) {
+  const int nlev = (int)P.lev.size();
+  const int ndeep = P.n_deep, nbot = P.n_bottom;  // fused runs at the top and at the bottom
+  const size_t smem = 2 * SMALL_LMAX * sizeof(T);
+  if (ndeep) {
+    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npre, true),
+           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, P.deep_desc.p, ndeep, P.F.p, npre));
+    ++launches;
+  }
+  for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
     // the first pre-sweep also saves F on N~_l for the post-sweeps (nu_pre >= 1)
@@ -540,32 +676,43 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
         if (!nk) continue;
         const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
         LAUNCH(ASMG_PROF_AUX_GS, by,
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p,
-                                                    sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1,
-                                                    sweep == 0 ? L.fs.p : nullptr, P.U.p));
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
+                      L.sm_rows.p, sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1, sweep == 0 ? L.fs.p : nullptr,
+                      P.U.p));
         ++launches;
       }
     }
     auto RS = view(L.RS);
     LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
-           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs), TPB, s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p, P.U.p, P.F.p));
+           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs), TPB, s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
+                  P.U.p, P.F.p));
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
-           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm)), TPB, s, L.npar, L.rp_id.p, L.rp_ptr.p,
-                                                                            L.rp_child.p, P.F.p, L.nsm, L.sm_rows.p,
-                                                                            P.U.p, L.us.p));
+           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm)), TPB, s, L.npar, L.rp_id.p,
+                  L.rp_ptr.p, L.rp_child.p, P.F.p, L.nsm, L.sm_rows.p, P.U.p, L.us.p));
     launches += 2;
+  }
+  if (nbot) {
+    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npre, true),
+           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, P.bot_desc.p, nbot, P.F.p, npre));
+    ++launches;
   }
   if (h.nc > 0) {
     LAUNCH(ASMG_PROF_COARSE, h.nc * h.nc * 8 + h.nc * (4 + 2 * sz),
            launch(h.prm.use_pdl, k_coarse<T>, nblk(h.nc * 32), TPB, s, h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p));
     ++launches;
   }
-  for (size_t li = 0; li < P.lev.size(); ++li) {
+  if (nbot) {
+    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npost, false),
+           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, P.bot_desc.p, nbot, P.U.p, npost));
+    ++launches;
+  }
+  for (int li = nbot; li <= nlev - 1 - ndeep; ++li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
     if (L.nnew) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
-             launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew), TPB, s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p, P.U.p));
+             launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew), TPB, s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p,
+                    P.U.p));
       ++launches;
     }
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
@@ -576,10 +723,15 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
         LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p, L.sm_rows.p, L.fs.p,
-                                                    1, nullptr, P.U.p));
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
+                      L.sm_rows.p, L.fs.p, 1, nullptr, P.U.p));
         ++launches;
       }
+  }
+  if (ndeep) {
+    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npost, false),
+           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, P.deep_desc.p, ndeep, P.U.p, npost));
+    ++launches;
   }
   return launches;
 }
@@ -790,6 +942,56 @@ int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
   return its;
 }
 
+// The fused runs: the longest run of small levels from the finest level down
+// and from the coarsest V-cycle level up (a level is small when its rows E_l
+// fit SMALL_LMAX); their descriptors live in device memory.
+template <class T>
+void setup_small(Prec<T>& P, cudaStream_t s) {
+  const int nlev = (int)P.lev.size();
+  int nd = 0;
+  while (nd < nlev && P.lev[nlev - 1 - nd].small.ok) ++nd;
+  int nb = 0;
+  if (nd < nlev)
+    while (nb < nlev - nd && P.lev[nb].small.ok) ++nb;
+  P.n_deep = nd;
+  P.n_bottom = nb;
+  auto desc = [](AuxLevelDev<T>& L) {
+    SmallDesc<T> d;
+    SmallLevelDev<T>& S = L.small;
+    d.mS = S.mS;
+    d.mE = S.mE;
+    d.ncol = S.ncol;
+    d.nnew = S.nnew;
+    d.npar = S.npar;
+    for (int c = 0; c <= SMALL_MAXC; ++c) d.cs[c] = c <= S.ncol ? S.cs[c] : S.mS;
+    d.gid = S.gid.p;
+    d.sm_ptr = S.sm_ptr.p;
+    d.sm_col = S.sm_col.p;
+    d.sm_val = S.sm_val.p;
+    d.dinv = S.dinv.p;
+    d.rs_ptr = S.rs_ptr.p;
+    d.rs_col = S.rs_col.p;
+    d.rs_val = S.rs_val.p;
+    d.nn_id = S.nn_id.p;
+    d.nn_p0 = S.nn_p0.p;
+    d.nn_p1 = S.nn_p1.p;
+    d.rp_id = S.rp_id.p;
+    d.rp_ptr = S.rp_ptr.p;
+    d.rp_child = S.rp_child.p;
+    d.fs = L.fs.p;
+    d.us = L.us.p;
+    return d;
+  };
+  std::vector<SmallDesc<T>> deep, bot;
+  for (int k = 0; k < nd; ++k) deep.push_back(desc(P.lev[nlev - 1 - k]));  // finest first (down order)
+  for (int k = nb - 1; k >= 0; --k) bot.push_back(desc(P.lev[k]));
+  P.deep_desc.upload(deep, s);
+  P.bot_desc.upload(bot, s);
+  const int smem = (int)(2 * SMALL_LMAX * sizeof(T));
+  ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+}
+
 void setup_solve(asmg_s& h, cudaStream_t s) {
   h.b.alloc(h.npad);
   h.x.alloc(h.npad);
@@ -819,10 +1021,13 @@ void setup_solve(asmg_s& h, cudaStream_t s) {
     P.F.zero(s);
     P.U.zero(s);
   };
-  if (h.prm.precision == ASMG_MIXED)
+  if (h.prm.precision == ASMG_MIXED) {
     alloc_prec(h.p32);
-  else
+    setup_small(h.p32, s);
+  } else {
     alloc_prec(h.p64);
+    setup_small(h.p64, s);
+  }
 }
 
 }  // namespace asmg
