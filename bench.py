@@ -151,6 +151,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched workload: independent jittered-grid Poisson problems with vertex
+    counts drawn log-uniform in [1e4, 5e5] (seeded), 4 random right-hand sides
+    each, all solved by one graph launch; timed against looping single solves."""
+    import torch
+    from paper_1410_2153_gb300 import asmg, meshgen
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    sides = meshgen.workload_batch_sizes(seed=1)[: args.batch_count]
+    nrhs = 4
+    t0 = time.perf_counter()
+    meshes = [meshgen.grid2d(int(n), 1000 + i) for i, n in enumerate(sides)]
+    solvers = [asmg.Solver(m, precision=asmg.ASMG_MIXED, stream=sp) for m in meshes]
+    t_setup = time.perf_counter() - t0
+    bs, us = [], []
+    for i, (m, s) in enumerate(zip(meshes, solvers)):
+        for j in range(nrhs):
+            f = torch.from_numpy(meshgen.nodal_uniform(m, 7000 + 4 * i + j)).cuda()
+            bs.append(s.mass_apply(f))
+            us.append(torch.zeros(m.nv, dtype=torch.float64, device="cuda"))
+    ndofs = sum(s.info("nfree") for s in solvers) * nrhs
+    t1 = time.perf_counter()
+    batch = asmg.amg_batch_create([s.h for s in solvers], nrhs, RTOL, sp)
+    t_graph = time.perf_counter() - t1
+
+    def batched():
+        for u in us:
+            u.zero_()
+        rc, its, st = asmg.amg_batch_solve(batch, bs, us, sp)
+        assert rc == asmg.ASMG_OK
+        return its
+
+    def looped():
+        its = []
+        for k, u in enumerate(us):
+            u.zero_()
+            rc, it = asmg.amg_solve(solvers[k // nrhs].h, bs[k], u, RTOL, None, sp)
+            assert rc == asmg.ASMG_OK
+            its.append(it)
+        return its
+
+    res = {}
+    for name, fn in (("batched", batched), ("looped", looped)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            its = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = (e0.elapsed_time(e1) / args.steps, its)
+    ms = res["batched"][0]
+    line = {"metric": METRIC, "value": ndofs / (ms / 1e3), "unit": "dofs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch: {len(sides)} jittered grids (nv log-uniform 1e4..5e5) x {nrhs} rhs",
+                       "total_dofs_x_rhs": ndofs, "precision": "mixed", "setup_s": t_setup, "graph_build_s": t_graph,
+                       "iterations_median": float(np.median(res["batched"][1]))},
+            "looped_single_solves": {"value": ndofs / (res["looped"][0] / 1e3), "ms_per_step": res["looped"][0]},
+            "batched_vs_looped_speedup": res["looped"][0] / ms}
+    print(json.dumps(line), flush=True)
+    asmg.amg_batch_destroy(batch)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,7 +229,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of the CUDA graph (ncu runs)")
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
+    ap.add_argument("--batch-count", type=int, default=256, help="problems of the batch workload")
     args = ap.parse_args()
+    if args.workload == "batch256":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

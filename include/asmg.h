@@ -204,6 +204,30 @@ enum asmg_prof_class {
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
 
 /*
+ * Batched solves (not in the paper): many independent problems, each with
+ * several right-hand sides, solved by one CUDA graph launch.
+ *   amg_batch_create  nprob handles (distinct meshes, any precisions), nrhs
+ *                     right-hand sides per handle, the relative tolerance.
+ *                     The batch adds nrhs work slots to every handle and
+ *                     captures one graph in which every (problem, rhs) solve
+ *                     -- gather, PCG start, WHILE loop, scatter -- is an
+ *                     independent branch, so the device runs the solves of
+ *                     all problems concurrently.  Handles must outlive the
+ *                     batch and may not be destroyed before it.
+ *   amg_batch_solve   bs[p * nrhs + j]: float64 [nv_p] right-hand side j of
+ *                     problem p; us[...]: initial guess in, solution out (host
+ *                     or device arrays).  iterations, status: host int
+ *                     [nprob * nrhs], the PCG steps and the per-solve status
+ *                     (ASMG_OK, ASMG_NOT_CONVERGED, ASMG_ERR_BREAKDOWN).
+ *                     Returns the worst status.
+ */
+typedef struct asmg_batch_s* asmg_batch;
+int amg_batch_create(int nprob, const asmg_handle* handles, int nrhs, double rtol, void* stream, asmg_batch* out);
+int amg_batch_solve(asmg_batch batch, const double* const* bs, double* const* us, int* iterations, int* status,
+                    void* stream);
+void amg_batch_destroy(asmg_batch batch);
+
+/*
  * ||b - A u||_2 and ||b||_2 over the free dofs, allocating nothing.  The
  * paper has no counterpart: this is a service entry point for callers that
  * cannot allocate device memory when they need the check -- code whose

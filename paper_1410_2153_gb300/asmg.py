@@ -70,12 +70,16 @@ def lib():
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
         L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_residual_norm_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        L.amg_batch_create.argtypes = [i32, vp, i32, ctypes.c_double, vp, ctypes.POINTER(vp)]
+        L.amg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.amg_batch_destroy.argtypes = [vp]
+        L.amg_batch_destroy.restype = None
         L.amg_destroy.argtypes = [vp]
         L.amg_destroy.restype = None
         L.amg_last_error.restype = ctypes.c_char_p
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
                      "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export",
-                     "amg_profile", "amg_residual_norm_noalloc"):
+                     "amg_profile", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -193,6 +197,30 @@ def amg_residual_norm_noalloc(h, b, u, stream=None):
 def amg_destroy(h):
     if h:
         lib().amg_destroy(h)
+
+
+def amg_batch_create(handles, nrhs: int, rtol: float, stream=None):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    out = ctypes.c_void_p()
+    _check(lib().amg_batch_create(len(handles), arr, nrhs, float(rtol), stream, ctypes.byref(out)))
+    return out
+
+
+def amg_batch_solve(batch, bs, us, stream=None):
+    """bs, us: flat lists (problem-major) of arrays; returns (worst status, iterations, statuses)."""
+    n = len(bs)
+    pb = (ctypes.c_void_p * n)(*[_ptr(x).value for x in bs])
+    pu = (ctypes.c_void_p * n)(*[_ptr(x).value for x in us])
+    its = np.zeros(n, dtype=np.int32)
+    st = np.zeros(n, dtype=np.int32)
+    rc = _check(lib().amg_batch_solve(batch, pb, pu, _ptr(its), _ptr(st), stream),
+                allow=(ASMG_OK, ASMG_NOT_CONVERGED))
+    return rc, its, st
+
+
+def amg_batch_destroy(batch):
+    if batch:
+        lib().amg_batch_destroy(batch)
 
 
 class Solver:

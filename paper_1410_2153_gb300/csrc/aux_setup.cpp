@@ -11,6 +11,7 @@
 // are among them because the grids are nested).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <thread>
@@ -515,9 +516,18 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   }
 
   // ---- levels c+1..J: smoothing sets, assembly triangles, new nodes
-  out.levels.clear();
-  for (int l = c + 1; l <= J; ++l) {
-    AuxLevelHost L;
+  // (levels are independent: one thread per level, largest first)
+  out.levels.assign(std::max(0, J - c), AuxLevelHost());
+  std::vector<int> order;
+  for (int l = c + 1; l <= J; ++l) order.push_back(l);
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return BX[x - 1].size() > BX[y - 1].size(); });
+  std::atomic<int> next_level(0);
+  auto level_worker = [&]() {
+   for (;;) {
+    const int oi = next_level.fetch_add(1);
+    if (oi >= (int)order.size()) return;
+    const int l = order[oi];
+    AuxLevelHost& L = out.levels[l - (c + 1)];
     L.level = l;
     const int d = l - 1;
     const uint64_t s = 1ULL << (T.D - d);
@@ -599,7 +609,13 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
       L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
     }
-    out.levels.push_back(std::move(L));
+  }
+  };
+  {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(level_worker);
+    for (auto& x : th) x.join();
   }
 
   // ---- Scott-Zhang transfer (Sec. 4.1): P_ik = int_{sigma_i} psi_i phi_k,

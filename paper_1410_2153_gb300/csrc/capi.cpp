@@ -260,10 +260,6 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
   D.rp_id.upload(pid, s);
   D.rp_ptr.upload(pptr, s);
   D.rp_child.upload(child, s);
-  D.fs.alloc(std::max<int64_t>(D.nsm, 1));
-  D.us.alloc(std::max<int64_t>(D.nsm, 1));
-  D.fs.zero(s);
-  D.us.zero(s);
   build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, D, s);
 }
 
@@ -485,14 +481,6 @@ void build_all(asmg_s& h, cudaStream_t s) {
   setup_solve(h, s);
   ASMG_CUDA(cudaStreamSynchronize(s));
   h.stats.t_levels = now() - t2;
-  if (h.gexec) {
-    cudaGraphExecDestroy(h.gexec);
-    h.gexec = nullptr;
-  }
-  if (h.graph) {
-    cudaGraphDestroy(h.graph);
-    h.graph = nullptr;
-  }
 }
 
 // algorithmic bytes of one PCG iteration (compulsory traffic, real non-zeros)
@@ -633,6 +621,104 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
 
 void amg_destroy(asmg_handle h) { delete h; }
 
+}  // extern "C"
+
+struct asmg_batch_s {
+  std::vector<asmg_handle> H;
+  int nrhs = 0;
+  double rtol = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~asmg_batch_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+  Slot& slot(int p, int j) { return *H[p]->slots.at(1 + j); }
+};
+
+extern "C" {
+
+int amg_batch_create(int nprob, const asmg_handle* handles, int nrhs, double rtol, void* stream, asmg_batch* out) {
+  API_BEGIN
+  if (!handles || !out || nprob <= 0 || nrhs <= 0) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid batch arguments");
+  if (!(rtol >= 0) || !std::isfinite(rtol)) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "rtol must be finite and >= 0");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<asmg_batch_s> B(new asmg_batch_s());
+  B->H.assign(handles, handles + nprob);
+  B->nrhs = nrhs;
+  B->rtol = rtol;
+  for (auto h : B->H) {
+    if (!h) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null handle in batch");
+    while ((int)h->slots.size() < 1 + nrhs) add_slot(*h, s);
+  }
+  ASMG_CUDA(cudaGraphCreate(&B->graph, 0));
+  cudaStream_t cs;
+  ASMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  for (int p = 0; p < nprob; ++p)
+    for (int j = 0; j < nrhs; ++j) {
+      asmg_s& h = *B->H[p];
+      Slot& S = B->slot(p, j);
+      // gather the staged rhs / initial guess (a root of its own branch)
+      ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, B->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      gather_rows(h, S.vb.p, S.b.p, cs);
+      gather_rows(h, S.vu.p, S.x.p, cs);
+      cudaStreamCaptureStatus st;
+      const cudaGraphNode_t* leaf = nullptr;
+      size_t nleaf = 0;
+      ASMG_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &leaf, nullptr, &nleaf));
+      std::vector<cudaGraphNode_t> leaves(leaf, leaf + nleaf);
+      cudaGraph_t gg;
+      ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
+      cudaGraphNode_t wnode = capture_solve(h, S, rtol, B->graph, leaves.data(), leaves.size());
+      ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, B->graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+      scatter_rows(h, S.x.p, false, S.vu.p, cs);
+      ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
+    }
+  ASMG_CUDA(cudaStreamDestroy(cs));
+  ASMG_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+  *out = B.release();
+  return ASMG_OK;
+  API_END
+}
+
+int amg_batch_solve(asmg_batch B, const double* const* bs, double* const* us, int* iterations, int* status,
+                    void* stream) {
+  API_BEGIN
+  if (!B || !bs || !us || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int np = (int)B->H.size(), nr = B->nrhs;
+  for (int p = 0; p < np; ++p)
+    for (int j = 0; j < nr; ++j) {
+      Slot& S = B->slot(p, j);
+      const int64_t nv = B->H[p]->mesh.nv;
+      if (!bs[p * nr + j] || !us[p * nr + j]) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null array in batch");
+      copy_in(S.vb.p, bs[p * nr + j], nv, s);
+      copy_in(S.vu.p, us[p * nr + j], nv, s);
+    }
+  ASMG_CUDA(cudaGraphLaunch(B->exec, s));
+  std::vector<PcgScalars> sc((size_t)np * nr);
+  for (int p = 0; p < np; ++p)
+    for (int j = 0; j < nr; ++j) {
+      Slot& S = B->slot(p, j);
+      copy_out(us[p * nr + j], S.vu.p, B->H[p]->mesh.nv, s);
+      ASMG_CUDA(cudaMemcpyAsync(&sc[p * nr + j], S.scal.p, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    }
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  int worst = ASMG_OK;
+  for (size_t k = 0; k < sc.size(); ++k) {
+    iterations[k] = sc[k].k;
+    const int st = sc[k].status == 0 ? ASMG_OK : sc[k].status == ASMG_ERR_BREAKDOWN ? ASMG_ERR_BREAKDOWN : ASMG_NOT_CONVERGED;
+    if (status) status[k] = st;
+    if (st < 0 || (worst == ASMG_OK && st != ASMG_OK)) worst = st;
+  }
+  if (worst == ASMG_ERR_BREAKDOWN) g_err = "PCG breakdown in a batched solve";
+  return worst;
+  API_END
+}
+
+void amg_batch_destroy(asmg_batch B) { delete B; }
+
 int amg_residual_norm_noalloc(asmg_handle h, const double* b, const double* u, double* out, void* stream) {
   API_BEGIN
   if (!h || !b || !u || !out) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
@@ -645,10 +731,11 @@ int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* i
   API_BEGIN
   if (!h || !b || !out || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
-  copy_in(h->vb.p, b, nv, s);
-  gather_rows(*h, h->vb.p, h->b.p, s);
-  h->x.zero(s);
+  copy_in(S0.vb.p, b, nv, s);
+  gather_rows(*h, S0.vb.p, S0.b.p, s);
+  S0.x.zero(s);
   *iterations = profile_solve(*h, rtol, s, out);
   return ASMG_OK;
   API_END
@@ -660,20 +747,21 @@ int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* itera
   if (!h || !b || !u || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   if (!(rtol >= 0) || !std::isfinite(rtol)) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "rtol must be finite and >= 0");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
-  copy_in(h->vb.p, b, nv, s);
-  copy_in(h->vu.p, u, nv, s);
-  gather_rows(*h, h->vb.p, h->b.p, s);
-  gather_rows(*h, h->vu.p, h->x.p, s);
-  run_solve(*h, rtol, s);
-  scatter_rows(*h, h->x.p, false, h->vu.p, s);
-  copy_out(u, h->vu.p, nv, s);
+  copy_in(S0.vb.p, b, nv, s);
+  copy_in(S0.vu.p, u, nv, s);
+  gather_rows(*h, S0.vb.p, S0.b.p, s);
+  gather_rows(*h, S0.vu.p, S0.x.p, s);
+  run_solve(*h, S0, rtol, s);
+  scatter_rows(*h, S0.x.p, false, S0.vu.p, s);
+  copy_out(u, S0.vu.p, nv, s);
   PcgScalars sc;
-  ASMG_CUDA(cudaMemcpyAsync(&sc, h->scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+  ASMG_CUDA(cudaMemcpyAsync(&sc, S0.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
   ASMG_CUDA(cudaStreamSynchronize(s));
   *iterations = sc.k;
   if (res_history) {
-    ASMG_CUDA(cudaMemcpyAsync(res_history, h->hist.p, 8 * (size_t)(sc.k + 1), cudaMemcpyDeviceToHost, s));
+    ASMG_CUDA(cudaMemcpyAsync(res_history, S0.hist.p, 8 * (size_t)(sc.k + 1), cudaMemcpyDeviceToHost, s));
     ASMG_CUDA(cudaStreamSynchronize(s));
   }
   if (sc.status == ASMG_ERR_BREAKDOWN) {
@@ -688,12 +776,13 @@ int amg_mass_apply(asmg_handle h, const double* f, double* bout, void* stream) {
   API_BEGIN
   if (!h || !f || !bout) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
-  copy_in(h->vb.p, f, nv, s);
-  mass_apply_gpu(h->mesh.ne, h->dX.p, h->dE.p, h->vb.p, h->vu.p, nv, s);
-  gather_rows(*h, h->vu.p, h->q.p, s);
-  scatter_rows(*h, h->q.p, false, h->vu.p, s);  // zero at Dirichlet vertices
-  copy_out(bout, h->vu.p, nv, s);
+  copy_in(S0.vb.p, f, nv, s);
+  mass_apply_gpu(h->mesh.ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, nv, s);
+  gather_rows(*h, S0.vu.p, S0.q.p, s);
+  scatter_rows(*h, S0.q.p, false, S0.vu.p, s);  // zero at Dirichlet vertices
+  copy_out(bout, S0.vu.p, nv, s);
   ASMG_CUDA(cudaStreamSynchronize(s));
   return ASMG_OK;
   API_END
@@ -703,15 +792,16 @@ int amg_precond_apply(asmg_handle h, const double* r, double* z, void* stream) {
   API_BEGIN
   if (!h || !r || !z) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
-  copy_in(h->vb.p, r, nv, s);
-  gather_rows(*h, h->vb.p, h->r.p, s);
-  precond_apply(*h, h->r.p, s);
+  copy_in(S0.vb.p, r, nv, s);
+  gather_rows(*h, S0.vb.p, S0.r.p, s);
+  precond_apply(*h, S0.r.p, s);
   if (h->prm.precision == ASMG_MIXED)
-    scatter_rows(*h, h->p32.uf.p, true, h->vu.p, s);
+    scatter_rows(*h, S0.s32.uf.p, true, S0.vu.p, s);
   else
-    scatter_rows(*h, h->p64.uf.p, false, h->vu.p, s);
-  copy_out(z, h->vu.p, nv, s);
+    scatter_rows(*h, S0.s64.uf.p, false, S0.vu.p, s);
+  copy_out(z, S0.vu.p, nv, s);
   ASMG_CUDA(cudaStreamSynchronize(s));
   return ASMG_OK;
   API_END
@@ -721,12 +811,13 @@ int amg_spmv(asmg_handle h, const double* x, double* y, void* stream) {
   API_BEGIN
   if (!h || !x || !y) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
-  copy_in(h->vb.p, x, nv, s);
-  gather_rows(*h, h->vb.p, h->p.p, s);
-  spmv64(*h, h->p.p, h->q.p, s);
-  scatter_rows(*h, h->q.p, false, h->vu.p, s);
-  copy_out(y, h->vu.p, nv, s);
+  copy_in(S0.vb.p, x, nv, s);
+  gather_rows(*h, S0.vb.p, S0.p.p, s);
+  spmv64(*h, S0.p.p, S0.q.p, s);
+  scatter_rows(*h, S0.q.p, false, S0.vu.p, s);
+  copy_out(y, S0.vu.p, nv, s);
   ASMG_CUDA(cudaStreamSynchronize(s));
   return ASMG_OK;
   API_END
@@ -736,14 +827,15 @@ int amg_element_grad(asmg_handle h, const double* u, const double* lambda, doubl
   API_BEGIN
   if (!h || !u || !lambda || !g) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv, ne = h->mesh.ne;
   // Dirichlet entries are treated as 0: gather/scatter through the free rows
-  copy_in(h->vb.p, u, nv, s);
-  gather_rows(*h, h->vb.p, h->p.p, s);
-  scatter_rows(*h, h->p.p, false, h->vb.p, s);
-  copy_in(h->vu.p, lambda, nv, s);
-  gather_rows(*h, h->vu.p, h->q.p, s);
-  scatter_rows(*h, h->q.p, false, h->vu.p, s);
+  copy_in(S0.vb.p, u, nv, s);
+  gather_rows(*h, S0.vb.p, S0.p.p, s);
+  scatter_rows(*h, S0.p.p, false, S0.vb.p, s);
+  copy_in(S0.vu.p, lambda, nv, s);
+  gather_rows(*h, S0.vu.p, S0.q.p, s);
+  scatter_rows(*h, S0.q.p, false, S0.vu.p, s);
   DBuf<double> dg;
   const bool dev = is_device(g);
   double* out = g;
@@ -751,7 +843,7 @@ int amg_element_grad(asmg_handle h, const double* u, const double* lambda, doubl
     dg.alloc(ne);
     out = dg.p;
   }
-  element_grad_gpu(ne, h->dX.p, h->dE.p, h->vb.p, h->vu.p, out, s);
+  element_grad_gpu(ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, out, s);
   if (!dev) ASMG_CUDA(cudaMemcpyAsync(g, dg.p, 8 * ne, cudaMemcpyDeviceToHost, s));
   ASMG_CUDA(cudaStreamSynchronize(s));
   return ASMG_OK;

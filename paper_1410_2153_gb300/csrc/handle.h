@@ -31,9 +31,34 @@ struct Prec {
   DBuf<T> dinv_f;
   Sell<T> P, PT;               // Scott-Zhang transfer and its transpose
   std::vector<AuxLevelDev<T>> lev;  // levels c+1..J (index 0 = c+1)
-  DBuf<T> uf, rho, F, U;       // fine work vector, fine residual, aux rhs / solution
   int n_deep = 0, n_bottom = 0;  // fused small-level runs (top of the hierarchy, bottom)
+};
+
+// Per-solve work state in precision T.
+template <class T>
+struct SlotPrec {
+  DBuf<T> uf, rho, F, U;            // fine work vector, fine residual, aux rhs / correction
+  std::vector<DBuf<T>> fs, us;      // per level: saved rhs / pre-smoothed values on N~_l
   DBuf<SmallDesc<T>> deep_desc, bot_desc;
+};
+
+// Everything one solve writes: several slots let independent right-hand
+// sides of one handle run concurrently (batched solves).
+struct Slot {
+  DBuf<double> b, x, r, p, q;        // permuted, padded
+  DBuf<double> vb, vu;               // vertex-ordered staging for user arrays
+  DBuf<double> partial, hist;
+  DBuf<unsigned int> ticket;
+  DBuf<PcgScalars> scal;
+  SlotPrec<double> s64;
+  SlotPrec<float> s32;
+  cudaGraph_t graph = nullptr;       // single-solve graph
+  cudaGraphExec_t gexec = nullptr;
+  double graph_rtol = -1;
+  ~Slot() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+  }
 };
 
 }  // namespace asmg
@@ -66,27 +91,13 @@ struct asmg_s {
   asmg::Prec<double> p64;
   asmg::Prec<float> p32;
 
-  // PCG state
-  asmg::DBuf<double> b, x, r, p, q;      // permuted, padded
-  asmg::DBuf<double> zd;                  // z in FP64 mode aliases p64.uf
-  asmg::DBuf<double> vb, vu;              // vertex-ordered staging for user arrays
-  asmg::DBuf<double> partial;
-  asmg::DBuf<unsigned int> ticket;
-  asmg::DBuf<asmg::PcgScalars> scal;
-  asmg::DBuf<double> hist;
-
-  // CUDA graph of the whole solve
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  double graph_rtol = -1;
+  // per-solve state (slot 0 serves amg_solve)
+  std::vector<std::unique_ptr<asmg::Slot>> slots;
   int64_t bytes_iter = 0;
   asmg::Stats stats;
   int gpu_launches_per_iter = 0;
 
-  ~asmg_s() {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-  }
+  asmg::Slot& slot0() { return *slots.at(0); }
 };
 
 namespace asmg {
@@ -95,7 +106,10 @@ void setup_solve(asmg_s& h, cudaStream_t s);
 int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out);
 // noalloc.cu
 void residual_norm_noalloc(asmg_s& h, const double* b, const double* u, double* out, cudaStream_t s);
-int run_solve(asmg_s& h, double rtol, cudaStream_t s);
+int run_solve(asmg_s& h, Slot& S, double rtol, cudaStream_t s);
+Slot& add_slot(asmg_s& h, cudaStream_t s);
+cudaGraphNode_t capture_solve(asmg_s& h, Slot& S, double rtol, cudaGraph_t g, const cudaGraphNode_t* deps,
+                              size_t ndeps);
 void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s);  // result in h.p*.uf
 void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);
 void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s);

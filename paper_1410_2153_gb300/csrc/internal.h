@@ -237,7 +237,6 @@ struct AuxLevelDev {
   int64_t npar = 0, nchild = 0;
   DBuf<int32_t> rp_id;           // parents receiving restricted residuals
   DBuf<int32_t> rp_ptr, rp_child;
-  DBuf<T> fs, us;                // saved rhs / pre-smoothed values on N~_l
   SmallLevelDev<T> small;        // shared-memory form, when the level is small
 };
 

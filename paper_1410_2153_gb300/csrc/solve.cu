@@ -637,6 +637,13 @@ template <>
 Prec<float>& prec<float>(asmg_s& h) { return h.p32; }
 
 template <class T>
+SlotPrec<T>& slotprec(Slot& S);
+template <>
+SlotPrec<double>& slotprec<double>(Slot& S) { return S.s64; }
+template <>
+SlotPrec<float>& slotprec<float>(Slot& S) { return S.s32; }
+
+template <class T>
 int64_t small_bytes(const Prec<T>& P, int first, int count, int nu, bool down) {
   const int64_t sz = sizeof(T);
   int64_t by = 0;
@@ -653,8 +660,9 @@ int64_t small_bytes(const Prec<T>& P, int first, int count, int nu, bool down) {
 }
 
 template <class T>
-int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
+int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
+  SlotPrec<T>& SP = slotprec<T>(S);
   int launches = 0;
   const int64_t sz = sizeof(T);
   const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
@@ -663,7 +671,7 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
   const size_t smem = 2 * SMALL_LMAX * sizeof(T);
   if (ndeep) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npre, true),
-           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, P.deep_desc.p, ndeep, P.F.p, npre));
+           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.F.p, npre));
     ++launches;
   }
   for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
@@ -677,33 +685,33 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
         const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
         LAUNCH(ASMG_PROF_AUX_GS, by,
                launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
-                      L.sm_rows.p, sweep == 0 ? P.F.p : L.fs.p, sweep == 0 ? 0 : 1, sweep == 0 ? L.fs.p : nullptr,
-                      P.U.p));
+                      L.sm_rows.p, sweep == 0 ? SP.F.p : SP.fs[li].p, sweep == 0 ? 0 : 1, sweep == 0 ? SP.fs[li].p : nullptr,
+                      SP.U.p));
         ++launches;
       }
     }
     auto RS = view(L.RS);
     LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
            launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs), TPB, s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
-                  P.U.p, P.F.p));
+                  SP.U.p, SP.F.p));
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
            launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm)), TPB, s, L.npar, L.rp_id.p,
-                  L.rp_ptr.p, L.rp_child.p, P.F.p, L.nsm, L.sm_rows.p, P.U.p, L.us.p));
+                  L.rp_ptr.p, L.rp_child.p, SP.F.p, L.nsm, L.sm_rows.p, SP.U.p, SP.us[li].p));
     launches += 2;
   }
   if (nbot) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npre, true),
-           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, P.bot_desc.p, nbot, P.F.p, npre));
+           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.F.p, npre));
     ++launches;
   }
   if (h.nc > 0) {
     LAUNCH(ASMG_PROF_COARSE, h.nc * h.nc * 8 + h.nc * (4 + 2 * sz),
-           launch(h.prm.use_pdl, k_coarse<T>, nblk(h.nc * 32), TPB, s, h.nc, h.d_cid.p, h.d_cinv.p, P.F.p, P.U.p));
+           launch(h.prm.use_pdl, k_coarse<T>, nblk(h.nc * 32), TPB, s, h.nc, h.d_cid.p, h.d_cinv.p, SP.F.p, SP.U.p));
     ++launches;
   }
   if (nbot) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npost, false),
-           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, P.bot_desc.p, nbot, P.U.p, npost));
+           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.U.p, npost));
     ++launches;
   }
   for (int li = nbot; li <= nlev - 1 - ndeep; ++li) {
@@ -712,11 +720,11 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
     if (L.nnew) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
              launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew), TPB, s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p,
-                    P.U.p));
+                    SP.U.p));
       ++launches;
     }
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
-           launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm), TPB, s, L.nsm, L.sm_rows.p, L.us.p, P.U.p));
+           launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm), TPB, s, L.nsm, L.sm_rows.p, SP.us[li].p, SP.U.p));
     ++launches;
     for (int sweep = 0; sweep < npost; ++sweep)
       for (int c = L.ncolours - 1; c >= 0; --c) {
@@ -724,47 +732,48 @@ int enqueue_vcycle(asmg_s& h, cudaStream_t s) {
         if (!nk) continue;
         LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
                launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
-                      L.sm_rows.p, L.fs.p, 1, nullptr, P.U.p));
+                      L.sm_rows.p, SP.fs[li].p, 1, nullptr, SP.U.p));
         ++launches;
       }
   }
   if (ndeep) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npost, false),
-           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, P.deep_desc.p, ndeep, P.U.p, npost));
+           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.U.p, npost));
     ++launches;
   }
   return launches;
 }
 
 template <class T>
-int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
+int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
+  SlotPrec<T>& SP = slotprec<T>(S);
   const SellView<T> A = fine_smoother<T>(h);
   const T* dinv = fine_dinv<T>(h);
   const int64_t sz = sizeof(T), n = h.n, nJ = h.nJ;
   int launches = 0;
-  ASMG_CUDA(cudaMemsetAsync(P.uf.p, 0, sizeof(T) * h.npad, s));
+  ASMG_CUDA(cudaMemsetAsync(SP.uf.p, 0, sizeof(T) * h.npad, s));
   const int ncol = (int)h.fine_cstart.size() - 1;
   // (1) u1 = S r: forward multicolour sweep from zero
   for (int c = 0; c < ncol; ++c) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
     ++launches;
   }
   // (2) u2 = u1 + P Btilde P^T (r - A u1)
   if (h.nJ > 0) {
     LAUNCH(ASMG_PROF_FINE_RESID, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
-           launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, P.uf.p, P.rho.p));
+           launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, SP.uf.p, SP.rho.p));
     auto PT = view(P.PT);
     LAUNCH(ASMG_PROF_RESTRICT, P.PT.nnz_real * (sz + 4) + n * sz + 2 * nJ * sz,
-           launch(h.prm.use_pdl, k_restrict_fine<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, P.rho.p, P.F.p, P.U.p));
+           launch(h.prm.use_pdl, k_restrict_fine<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, SP.rho.p, SP.F.p, SP.U.p));
     launches += 2;
-    launches += enqueue_vcycle<T>(h, s);
+    launches += enqueue_vcycle<T>(h, S, s);
     auto PP = view(P.P);
     LAUNCH(ASMG_PROF_PROLONG, P.P.nnz_real * (sz + 4) + nJ * sz + 2 * n * sz,
-           launch(h.prm.use_pdl, k_prolong_fine<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, P.U.p, P.uf.p));
+           launch(h.prm.use_pdl, k_prolong_fine<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, SP.U.p, SP.uf.p));
     ++launches;
   }
   // (3) u3 = u2 + S^T (r - A u2): backward multicolour sweep
@@ -772,7 +781,7 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, P.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
     ++launches;
   }
   ASMG_CUDA(cudaGetLastError());
@@ -780,32 +789,32 @@ int enqueue_precond(asmg_s& h, const double* r, cudaStream_t s) {
 }
 
 template <class T>
-int enqueue_body(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
-  int launches = enqueue_precond<T>(h, h.r.p, s);
-  const T* z = prec<T>(h).uf.p;
+int enqueue_body(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  int launches = enqueue_precond<T>(h, S, S.r.p, s);
+  const T* z = slotprec<T>(S).uf.p;
   const int G = RED_BLOCKS;
   const int64_t n = h.n, sz = sizeof(T);
   LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16),
-         launch(h.prm.use_pdl, k_dots<T>, G, TPB, s, h.npad, z, h.r.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
-  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_pupd<T>, G, TPB, s, h.npad, z, h.p.p, h.scal.p));
+         launch(h.prm.use_pdl, k_dots<T>, G, TPB, s, h.npad, z, S.r.p, S.q.p, S.partial.p, S.ticket.p, S.scal.p));
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_pupd<T>, G, TPB, s, h.npad, z, S.p.p, S.scal.p));
   LAUNCH(ASMG_PROF_CG_SPMV, h.A64.nnz_real * 12 + n * 16,
-         launch(h.prm.use_pdl, k_spmv_dot, G, TPB, s, h.npad, view(h.A64), h.p.p, h.q.p, h.partial.p, h.ticket.p, h.scal.p));
+         launch(h.prm.use_pdl, k_spmv_dot, G, TPB, s, h.npad, view(h.A64), S.p.p, S.q.p, S.partial.p, S.ticket.p, S.scal.p));
   LAUNCH(ASMG_PROF_CG_VECTOR, n * 48,
-         launch(h.prm.use_pdl, k_axpy_norm, G, TPB, s, h.npad, h.p.p, h.q.p, h.x.p, h.r.p, h.partial.p, h.ticket.p, h.scal.p,
-                                       h.hist.p, hnd, use_hnd));
+         launch(h.prm.use_pdl, k_axpy_norm, G, TPB, s, h.npad, S.p.p, S.q.p, S.x.p, S.r.p, S.partial.p, S.ticket.p, S.scal.p,
+                                       S.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
   return launches + 4;
 }
 
-int enqueue_body_any(asmg_s& h, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
-  return h.prm.precision == ASMG_MIXED ? enqueue_body<float>(h, s, hnd, use_hnd)
-                                       : enqueue_body<double>(h, s, hnd, use_hnd);
+int enqueue_body_any(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  return h.prm.precision == ASMG_MIXED ? enqueue_body<float>(h, S, s, hnd, use_hnd)
+                                       : enqueue_body<double>(h, S, s, hnd, use_hnd);
 }
 
-void enqueue_init(asmg_s& h, double rtol, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+void enqueue_init(asmg_s& h, Slot& S, double rtol, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
   LAUNCH(ASMG_PROF_CG_VECTOR, h.A64.nnz_real * 12 + h.n * 32,
-         launch(h.prm.use_pdl, k_pcg_init, RED_BLOCKS, TPB, s, h.npad, view(h.A64), h.b.p, h.x.p, h.r.p, h.partial.p, h.ticket.p,
-                                               h.scal.p, rtol, h.prm.max_iter, h.hist.p, hnd, use_hnd));
+         launch(h.prm.use_pdl, k_pcg_init, RED_BLOCKS, TPB, s, h.npad, view(h.A64), S.b.p, S.x.p, S.r.p, S.partial.p, S.ticket.p,
+                                               S.scal.p, rtol, h.prm.max_iter, S.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
 }
 
@@ -825,10 +834,11 @@ void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cuda
 }
 
 void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s) {
+  Slot& S = *h.slots[0];
   if (h.prm.precision == ASMG_MIXED)
-    enqueue_precond<float>(h, r_perm, s);
+    enqueue_precond<float>(h, S, r_perm, s);
   else
-    enqueue_precond<double>(h, r_perm, s);
+    enqueue_precond<double>(h, S, r_perm, s);
 }
 
 __global__ void k_spmv64(int64_t n, SellView<double> A, const double* __restrict__ x, double* __restrict__ y) {
@@ -841,68 +851,73 @@ void spmv64(asmg_s& h, const double* x, double* y, cudaStream_t s) {
   ASMG_CUDA(cudaGetLastError());
 }
 
-// Build (once) the graph of the whole solve:
+// Capture the graph of one solve into `g` (independent of other nodes):
 //   init (r = b - A x, norms, condition) -> WHILE(cond) { body }.
-static void build_graph(asmg_s& h, double rtol, cudaStream_t s) {
-  (void)rtol;
-  if (h.gexec) {
-    cudaGraphExecDestroy(h.gexec);
-    h.gexec = nullptr;
-  }
-  if (h.graph) {
-    cudaGraphDestroy(h.graph);
-    h.graph = nullptr;
-  }
-  cudaGraph_t g;
-  ASMG_CUDA(cudaGraphCreate(&g, 0));
+// Returns the WHILE node.
+cudaGraphNode_t capture_solve(asmg_s& h, Slot& S, double rtol, cudaGraph_t g, const cudaGraphNode_t* deps,
+                              size_t ndeps) {
   cudaGraphConditionalHandle hnd;
   ASMG_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0));
-  // the init kernel is captured into the parent graph
   cudaStream_t cs;
   ASMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  enqueue_init(h, rtol, cs, hnd, 1);
+  ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, deps, nullptr, ndeps, cudaStreamCaptureModeThreadLocal));
+  enqueue_init(h, S, rtol, cs, hnd, 1);
+  // the WHILE node depends on the captured init kernel (the leaf of this capture)
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* leaf = nullptr;
+  size_t nleaf = 0;
+  ASMG_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &leaf, nullptr, &nleaf));
+  std::vector<cudaGraphNode_t> leaves(leaf, leaf + nleaf);
   cudaGraph_t gg;
   ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
-  // the WHILE node depends on every node captured so far (the init kernel)
-  size_t nnodes = 0;
-  ASMG_CUDA(cudaGraphGetNodes(g, nullptr, &nnodes));
-  std::vector<cudaGraphNode_t> deps(nnodes);
-  if (nnodes) ASMG_CUDA(cudaGraphGetNodes(g, deps.data(), &nnodes));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = hnd;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cnode;
-  ASMG_CUDA(cudaGraphAddNode(&cnode, g, deps.data(), nullptr, nnodes, &cp));
+  ASMG_CUDA(cudaGraphAddNode(&cnode, g, leaves.data(), nullptr, leaves.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  // body
   ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  h.gpu_launches_per_iter = enqueue_body_any(h, cs, hnd, 1);
+  h.gpu_launches_per_iter = enqueue_body_any(h, S, cs, hnd, 1);
   cudaGraph_t bb;
   ASMG_CUDA(cudaStreamEndCapture(cs, &bb));
   ASMG_CUDA(cudaStreamDestroy(cs));
-  ASMG_CUDA(cudaGraphInstantiate(&h.gexec, g, 0));
-  h.graph = g;
+  return cnode;
 }
 
-int run_solve(asmg_s& h, double rtol, cudaStream_t s) {
+static void build_graph(asmg_s& h, Slot& S, double rtol) {
+  if (S.gexec) {
+    cudaGraphExecDestroy(S.gexec);
+    S.gexec = nullptr;
+  }
+  if (S.graph) {
+    cudaGraphDestroy(S.graph);
+    S.graph = nullptr;
+  }
+  cudaGraph_t g;
+  ASMG_CUDA(cudaGraphCreate(&g, 0));
+  capture_solve(h, S, rtol, g, nullptr, 0);
+  ASMG_CUDA(cudaGraphInstantiate(&S.gexec, g, 0));
+  S.graph = g;
+}
+
+int run_solve(asmg_s& h, Slot& S, double rtol, cudaStream_t s) {
   if (h.prm.use_graph) {
     // the graph bakes rtol into the init kernel's arguments: rebuild when it changes
-    if (!h.gexec || h.graph_rtol != rtol) {
-      build_graph(h, rtol, s);
-      h.graph_rtol = rtol;
+    if (!S.gexec || S.graph_rtol != rtol) {
+      build_graph(h, S, rtol);
+      S.graph_rtol = rtol;
     }
-    ASMG_CUDA(cudaGraphLaunch(h.gexec, s));
+    ASMG_CUDA(cudaGraphLaunch(S.gexec, s));
   } else {
-    enqueue_init(h, rtol, s, 0, 0);
+    enqueue_init(h, S, rtol, s, 0, 0);
     for (int it = 0; it < h.prm.max_iter; ++it) {
       PcgScalars sc;
-      ASMG_CUDA(cudaMemcpyAsync(&sc, h.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+      ASMG_CUDA(cudaMemcpyAsync(&sc, S.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
       ASMG_CUDA(cudaStreamSynchronize(s));
       if (!sc.cond) break;
-      h.gpu_launches_per_iter = enqueue_body_any(h, s, 0, 0);
+      h.gpu_launches_per_iter = enqueue_body_any(h, S, s, 0, 0);
     }
   }
   return 0;
@@ -911,18 +926,19 @@ int run_solve(asmg_s& h, double rtol, cudaStream_t s) {
 // One solve without the graph, every launch timed: per class launches,
 // milliseconds and algorithmic bytes; returns the iteration count.
 int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
+  Slot& S = *h.slots[0];
   Profiler prof;
   prof.s = s;
   g_prof = &prof;
   int its = 0;
   try {
-    enqueue_init(h, rtol, s, 0, 0);
+    enqueue_init(h, S, rtol, s, 0, 0);
     for (int it = 0; it < h.prm.max_iter; ++it) {
       PcgScalars sc;
-      ASMG_CUDA(cudaMemcpyAsync(&sc, h.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+      ASMG_CUDA(cudaMemcpyAsync(&sc, S.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
       ASMG_CUDA(cudaStreamSynchronize(s));
       if (!sc.cond) break;
-      enqueue_body_any(h, s, 0, 0);
+      enqueue_body_any(h, S, s, 0, 0);
       ++its;
     }
     ASMG_CUDA(cudaStreamSynchronize(s));
@@ -946,7 +962,7 @@ int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
 // and from the coarsest V-cycle level up (a level is small when its rows E_l
 // fit SMALL_LMAX); their descriptors live in device memory.
 template <class T>
-void setup_small(Prec<T>& P, cudaStream_t s) {
+void setup_small(Prec<T>& P) {
   const int nlev = (int)P.lev.size();
   int nd = 0;
   while (nd < nlev && P.lev[nlev - 1 - nd].small.ok) ++nd;
@@ -955,79 +971,106 @@ void setup_small(Prec<T>& P, cudaStream_t s) {
     while (nb < nlev - nd && P.lev[nb].small.ok) ++nb;
   P.n_deep = nd;
   P.n_bottom = nb;
-  auto desc = [](AuxLevelDev<T>& L) {
-    SmallDesc<T> d;
-    SmallLevelDev<T>& S = L.small;
-    d.mS = S.mS;
-    d.mE = S.mE;
-    d.ncol = S.ncol;
-    d.nnew = S.nnew;
-    d.npar = S.npar;
-    for (int c = 0; c <= SMALL_MAXC; ++c) d.cs[c] = c <= S.ncol ? S.cs[c] : S.mS;
-    d.gid = S.gid.p;
-    d.sm_ptr = S.sm_ptr.p;
-    d.sm_col = S.sm_col.p;
-    d.sm_val = S.sm_val.p;
-    d.dinv = S.dinv.p;
-    d.rs_ptr = S.rs_ptr.p;
-    d.rs_col = S.rs_col.p;
-    d.rs_val = S.rs_val.p;
-    d.nn_id = S.nn_id.p;
-    d.nn_p0 = S.nn_p0.p;
-    d.nn_p1 = S.nn_p1.p;
-    d.rp_id = S.rp_id.p;
-    d.rp_ptr = S.rp_ptr.p;
-    d.rp_child = S.rp_child.p;
-    d.fs = L.fs.p;
-    d.us = L.us.p;
-    return d;
-  };
-  std::vector<SmallDesc<T>> deep, bot;
-  for (int k = 0; k < nd; ++k) deep.push_back(desc(P.lev[nlev - 1 - k]));  // finest first (down order)
-  for (int k = nb - 1; k >= 0; --k) bot.push_back(desc(P.lev[k]));
-  P.deep_desc.upload(deep, s);
-  P.bot_desc.upload(bot, s);
   const int smem = (int)(2 * SMALL_LMAX * sizeof(T));
   ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
 }
 
-void setup_solve(asmg_s& h, cudaStream_t s) {
-  h.b.alloc(h.npad);
-  h.x.alloc(h.npad);
-  h.r.alloc(h.npad);
-  h.p.alloc(h.npad);
-  h.q.alloc(h.npad);
-  h.b.zero(s);
-  h.x.zero(s);
-  h.r.zero(s);
-  h.p.zero(s);
-  h.q.zero(s);
-  h.vb.alloc(h.mesh.nv);
-  h.vu.alloc(h.mesh.nv);
-  h.partial.alloc(4 * RED_BLOCKS);
-  h.ticket.alloc(1);
-  h.ticket.zero(s);
-  h.scal.alloc(1);
-  h.scal.zero(s);
-  h.hist.alloc(h.prm.max_iter + 1);
-  auto alloc_prec = [&](auto& P) {
-    P.uf.alloc(h.npad);
-    P.rho.alloc(h.npad);
-    P.F.alloc(std::max<int64_t>(h.nJpad, 1));
-    P.U.alloc(std::max<int64_t>(h.nJpad, 1));
-    P.uf.zero(s);
-    P.rho.zero(s);
-    P.F.zero(s);
-    P.U.zero(s);
-  };
-  if (h.prm.precision == ASMG_MIXED) {
-    alloc_prec(h.p32);
-    setup_small(h.p32, s);
-  } else {
-    alloc_prec(h.p64);
-    setup_small(h.p64, s);
+// Work state of one solve in precision T: vectors, per-level saved values,
+// descriptors of the fused small-level runs (they point at this slot's
+// saved values).
+template <class T>
+void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
+  SP.uf.alloc(h.npad);
+  SP.rho.alloc(h.npad);
+  SP.F.alloc(std::max<int64_t>(h.nJpad, 1));
+  SP.U.alloc(std::max<int64_t>(h.nJpad, 1));
+  SP.uf.zero(s);
+  SP.rho.zero(s);
+  SP.F.zero(s);
+  SP.U.zero(s);
+  const int nlev = (int)P.lev.size();
+  SP.fs.clear();
+  SP.us.clear();
+  SP.fs.resize(nlev);
+  SP.us.resize(nlev);
+  for (int li = 0; li < nlev; ++li) {
+    SP.fs[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
+    SP.us[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
+    SP.fs[li].zero(s);
+    SP.us[li].zero(s);
   }
+  auto desc = [&](int li) {
+    AuxLevelDev<T>& L = P.lev[li];
+    SmallDesc<T> d;
+    SmallLevelDev<T>& M = L.small;
+    d.mS = M.mS;
+    d.mE = M.mE;
+    d.ncol = M.ncol;
+    d.nnew = M.nnew;
+    d.npar = M.npar;
+    for (int c = 0; c <= SMALL_MAXC; ++c) d.cs[c] = c <= M.ncol ? M.cs[c] : M.mS;
+    d.gid = M.gid.p;
+    d.sm_ptr = M.sm_ptr.p;
+    d.sm_col = M.sm_col.p;
+    d.sm_val = M.sm_val.p;
+    d.dinv = M.dinv.p;
+    d.rs_ptr = M.rs_ptr.p;
+    d.rs_col = M.rs_col.p;
+    d.rs_val = M.rs_val.p;
+    d.nn_id = M.nn_id.p;
+    d.nn_p0 = M.nn_p0.p;
+    d.nn_p1 = M.nn_p1.p;
+    d.rp_id = M.rp_id.p;
+    d.rp_ptr = M.rp_ptr.p;
+    d.rp_child = M.rp_child.p;
+    d.fs = SP.fs[li].p;
+    d.us = SP.us[li].p;
+    return d;
+  };
+  std::vector<SmallDesc<T>> deep, bot;
+  for (int k = 0; k < P.n_deep; ++k) deep.push_back(desc(nlev - 1 - k));  // finest first (down order)
+  for (int k = P.n_bottom - 1; k >= 0; --k) bot.push_back(desc(k));
+  SP.deep_desc.upload(deep, s);
+  SP.bot_desc.upload(bot, s);
+}
+
+Slot& add_slot(asmg_s& h, cudaStream_t s) {
+  h.slots.emplace_back(new Slot());
+  Slot& S = *h.slots.back();
+  S.b.alloc(h.npad);
+  S.x.alloc(h.npad);
+  S.r.alloc(h.npad);
+  S.p.alloc(h.npad);
+  S.q.alloc(h.npad);
+  S.b.zero(s);
+  S.x.zero(s);
+  S.r.zero(s);
+  S.p.zero(s);
+  S.q.zero(s);
+  S.vb.alloc(h.mesh.nv);
+  S.vu.alloc(h.mesh.nv);
+  S.partial.alloc(4 * RED_BLOCKS);
+  S.ticket.alloc(1);
+  S.ticket.zero(s);
+  S.scal.alloc(1);
+  S.scal.zero(s);
+  S.hist.alloc(h.prm.max_iter + 1);
+  if (h.prm.precision == ASMG_MIXED)
+    alloc_slot_prec(h, h.p32, S.s32, s);
+  else
+    alloc_slot_prec(h, h.p64, S.s64, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return S;
+}
+
+void setup_solve(asmg_s& h, cudaStream_t s) {
+  if (h.prm.precision == ASMG_MIXED)
+    setup_small(h.p32);
+  else
+    setup_small(h.p64);
+  h.slots.clear();
+  add_slot(h, s);
 }
 
 }  // namespace asmg
