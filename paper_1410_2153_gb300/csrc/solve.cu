@@ -33,6 +33,11 @@ constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
 
 int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
 
+// Block size of a row-parallel launch: 256 threads when that fills every SM
+// twice, else 64 so that small colour classes still spread over all SMs.
+constexpr int NSM = 152;
+inline int rows_tpb(int64_t rows) { return rows >= (int64_t)NSM * 2 * 256 ? 256 : 64; }
+
 // Kernel launch with dynamic shared memory, optionally with programmatic dependent launch.
 template <typename... KArgs, typename... Args>
 void launch_smem(bool pdl, void (*kern)(KArgs...), int64_t grid, int block, size_t smem, cudaStream_t s,
@@ -684,7 +689,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
         if (!nk) continue;
         const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
         LAUNCH(ASMG_PROF_AUX_GS, by,
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
                       L.sm_rows.p, sweep == 0 ? SP.F.p : SP.fs[li].p, sweep == 0 ? 0 : 1, sweep == 0 ? SP.fs[li].p : nullptr,
                       SP.U.p));
         ++launches;
@@ -692,10 +697,10 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     }
     auto RS = view(L.RS);
     LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
-           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs), TPB, s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
+           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
                   SP.U.p, SP.F.p));
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
-           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm)), TPB, s, L.npar, L.rp_id.p,
+           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm), rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.npar, L.rp_id.p,
                   L.rp_ptr.p, L.rp_child.p, SP.F.p, L.nsm, L.sm_rows.p, SP.U.p, SP.us[li].p));
     launches += 2;
   }
@@ -719,19 +724,19 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     auto SM = view(L.SM);
     if (L.nnew) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
-             launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew), TPB, s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p,
+             launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew, rows_tpb(L.nnew)), rows_tpb(L.nnew), s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p,
                     SP.U.p));
       ++launches;
     }
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
-           launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm), TPB, s, L.nsm, L.sm_rows.p, SP.us[li].p, SP.U.p));
+           launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p, SP.us[li].p, SP.U.p));
     ++launches;
     for (int sweep = 0; sweep < npost; ++sweep)
       for (int c = L.ncolours - 1; c >= 0; --c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
         LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk), TPB, s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
+               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
                       L.sm_rows.p, SP.fs[li].p, 1, nullptr, SP.U.p));
         ++launches;
       }
@@ -759,7 +764,7 @@ int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr, rows_tpb(nr)), rows_tpb(nr), s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
     ++launches;
   }
   // (2) u2 = u1 + P Btilde P^T (r - A u1)
@@ -781,7 +786,7 @@ int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
     int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
     if (!nr) continue;
     LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr), TPB, s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
+           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr, rows_tpb(nr)), rows_tpb(nr), s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
     ++launches;
   }
   ASMG_CUDA(cudaGetLastError());
