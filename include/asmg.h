@@ -139,6 +139,16 @@ int amg_element_grad(asmg_handle h, const double* u, const double* lambda, doubl
  */
 int amg_update_coefficients(asmg_handle h, const double* coeff, void* stream);
 
+/*
+ * The cluster tree alone (Sec. 3.1) for a 2D (triangles) or 3D (tetrahedra)
+ * mesh: Morton keys of the quantised element barycenters (D = 31 bits per
+ * coordinate in 2D, 21 in 3D) and the elements sorted by key (stable).
+ *   keys  uint64 [ne] (element order), perm int32 [ne]; host or device.
+ * Index range and orientation are checked (ASMG_ERR_BAD_MESH).
+ */
+int amg_cluster_tree(int dim, int64_t nv, const double* vertices, int64_t ne, const int32_t* elements, uint64_t* keys,
+                     int32_t* perm, void* stream);
+
 /* Integer facts about a handle (see enum asmg_info_what); *value receives it. */
 enum asmg_info_what {
   ASMG_INFO_NFREE = 0,        /* free fine dofs n */

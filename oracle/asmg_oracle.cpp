@@ -1206,7 +1206,7 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     o->prm.colouring = params[6];
     o->prm.stage = params[7];
   }
-  assemble_fine(*o);
+  if (o->prm.stage >= 0) assemble_fine(*o);  // stage -1: cluster tree only
   build_tree(*o);
   if (o->prm.stage >= 1) build_closure(*o);
   if (o->prm.stage >= 2) {

@@ -74,12 +74,13 @@ def lib():
         L.amg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         L.amg_batch_destroy.argtypes = [vp]
         L.amg_batch_destroy.restype = None
+        L.amg_cluster_tree.argtypes = [i32, i64, vp, i64, vp, vp, vp, vp]
         L.amg_destroy.argtypes = [vp]
         L.amg_destroy.restype = None
         L.amg_last_error.restype = ctypes.c_char_p
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
                      "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export",
-                     "amg_profile", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve"):
+                     "amg_profile", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -192,6 +193,16 @@ def amg_residual_norm_noalloc(h, b, u, stream=None):
     out = np.zeros(2)
     _check(lib().amg_residual_norm_noalloc(h, _ptr(b), _ptr(u), _ptr(out), stream))
     return float(out[0]), float(out[1])
+
+
+def amg_cluster_tree(mesh, stream=None):
+    """(keys, perm) of the cluster tree of a 2D or 3D mesh (host arrays out)."""
+    X = np.ascontiguousarray(mesh.verts, dtype=np.float64)
+    E = np.ascontiguousarray(mesh.elems, dtype=np.int32)
+    keys = np.empty(mesh.ne, dtype=np.uint64)
+    perm = np.empty(mesh.ne, dtype=np.int32)
+    _check(lib().amg_cluster_tree(mesh.dim, mesh.nv, _ptr(X), mesh.ne, _ptr(E), _ptr(keys), _ptr(perm), stream))
+    return keys, perm
 
 
 def amg_destroy(h):

@@ -621,6 +621,26 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
 
 void amg_destroy(asmg_handle h) { delete h; }
 
+int amg_cluster_tree(int dim, int64_t nv, const double* vertices, int64_t ne, const int32_t* elements, uint64_t* keys,
+                     int32_t* perm, void* stream) {
+  API_BEGIN
+  if (!vertices || !elements || !keys || !perm) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  if (dim != 2 && dim != 3) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "dim %d not supported", dim);
+  if (nv <= 0 || ne <= 0) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "nv and ne must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  DBuf<double> dX;
+  DBuf<int32_t> dE;
+  dX.upload(to_host(vertices, nv * dim, s), s);
+  dE.upload(to_host(elements, ne * (dim + 1), s), s);
+  TreeResult t;
+  build_tree_gpu(dim, nv, dX.p, ne, dE.p, 3, s, t);
+  ASMG_CUDA(cudaMemcpyAsync(keys, t.keys.p, 8 * ne, cudaMemcpyDefault, s));
+  ASMG_CUDA(cudaMemcpyAsync(perm, t.perm.p, 4 * ne, cudaMemcpyDefault, s));
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return ASMG_OK;
+  API_END
+}
+
 }  // extern "C"
 
 struct asmg_batch_s {

@@ -214,3 +214,14 @@ def test_zero_rhs_and_empty_aux(gen, A):
     o = oracle.Oracle(m)
     assert abs(u[4] - 1.0 / o.A().toarray()[0, 0]) < 1e-14
     s.close()
+
+
+@pytest.mark.parametrize("nside", [9, 17, 129])
+def test_3d_cluster_tree_bit_exact(gen, A, nside):
+    # Kuhn tetrahedra of a jittered cube grid; 129^3 vertices is the 3D
+    # workload at full size (12,582,912 tetrahedra)
+    m = gen.grid3d(nside, 4, jitter=0.15)
+    keys, perm = A.amg_cluster_tree(m)
+    o = oracle.Oracle(m, stage=-1)
+    assert np.array_equal(keys, o.keys())
+    assert np.array_equal(perm, o.perm())

@@ -540,3 +540,28 @@ def test_element_gradient_matches_central_differences(gen):
         dL = 0.5 * (ups[0] - ups[1]) @ (ups[0] + ups[1] - 2 * u_obs)
         fd = dL / (2 * h)
         assert abs(fd - m.coeff[e] * dLda[e]) <= 1e-6 * np.abs(m.coeff * dLda).max(), (e, fd, m.coeff[e] * dLda[e])
+
+
+def test_octree_membership_and_counts(gen):
+    # the 3D cluster tree: every node's barycenters lie in its box, leaves hold
+    # at most n_min, split nodes more, each split node has all 8 children
+    m = gen.grid3d(9, 2)
+    o = oracle.Oracle(m, stage=-1)
+    levels = o.tree_levels()
+    perm = o.perm()
+    a = o.root()
+    bc = m.verts[m.elems].sum(1) / 4.0
+    assert np.array_equal(np.sort(perm), np.arange(m.ne))
+    for d, segs in enumerate(levels):
+        w = a[3] / 2 ** d
+        for prefix, b, e, split in segs:
+            q = np.zeros(3, np.int64)
+            for j in range(d):
+                for k in range(3):
+                    q[k] |= ((int(prefix) >> (3 * j + k)) & 1) << j
+            lo = a[:3] + q * w
+            pts = bc[perm[b:e]]
+            assert (pts >= lo - 1e-12).all() and (pts <= lo + w + 1e-12).all()
+            assert (e - b > 3) if split else (e - b <= 3)
+        if d + 1 < len(levels):
+            assert levels[d + 1].shape[0] == 8 * int(segs[:, 3].sum())
