@@ -143,8 +143,12 @@ class Oracle:
     def level_tri(self, l: int):
         return self._get("level_tri", l, (self.info("ntri", l), 3), np.uint64)
 
+    def level_tet(self, l: int):
+        return self._get("level_tet", l, (self.info("ntet", l), 4), np.uint64)
+
     def finest_coef(self):
-        return self._get("finest_coef", 0, (self.info("ntri", self.J),), np.float64)
+        n = self.info("ntri", self.J) if self.dim == 2 else self.info("ntet", self.J)
+        return self._get("finest_coef", 0, (n,), np.float64)
 
     def _csr(self, prefix: str, level: int, nr: int, nc: int, nnz: int):
         import scipy.sparse as sp

@@ -30,8 +30,8 @@
 //       independently on the device, so no colouring is ever passed from one
 //       side to the other
 //
-// 3D: fine assembly, mass matrix and the octree are dimension-generic; the
-// auxiliary hierarchy is built for d = 2 only.
+// 3D: the same steps on an octree with tetrahedral auxiliary grids (R4-3D
+// below); fine assembly, mass matrix and the tree are dimension-generic.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -148,6 +148,7 @@ struct Level {
   std::vector<uint64_t> key;                 // free nodes, ascending lattice Morton key
   std::vector<uint64_t> allkey;              // all nodes incl. boundary, ascending
   std::vector<std::array<uint64_t, 3>> tri;  // level triangles (lattice Morton keys, CCW)
+  std::vector<std::array<uint64_t, 4>> tet;  // level tetrahedra (3D, positively oriented)
   CSR A;                                     // level operator on free nodes
   CSR I;                                     // nodal interpolation from level l-1
   std::vector<int32_t> smooth;               // smoothing set sorted by (colour, index)
@@ -180,6 +181,7 @@ struct Oracle {
   // closed box tree (Sec. 3.2): per depth, packed box coordinates -> split
   std::vector<std::unordered_map<uint64_t, uint8_t>> boxes;
   int J = 0;  // finest auxiliary level (depth)
+  int LB = 0; // 3D: lattice bits of the auxiliary nodes (J + 1)
   int c = 0;  // coarsest level used by the V-cycle
   std::vector<Level> lv;
   std::vector<double> finest_coef;  // per triangle of level J
@@ -902,6 +904,637 @@ void build_transfer(Oracle& o) {
 }
 
 // --------------------------------------------------------------------------
+// 3D (Sec. 1: the octree version "without intrinsic difficulties"): nested
+// conforming tetrahedral auxiliary grids.  Reading R4-3D: a box without edge
+// midpoints or subdivided faces is split into the 6 Kuhn tetrahedra of its
+// (0,0,0)-(1,1,1) diagonal; otherwise every face is triangulated -- a face
+// whose neighbour is split by its 4 sub-squares, each along its
+// min-to-max diagonal; a face with an edge midpoint by a fan about its
+// centre; other faces by their min-to-max diagonal -- and each face triangle
+// is coned to the box centre.  Nodes lie on the 2^(J+1) lattice of the root
+// cube and are named by their 63-bit Morton key.
+// --------------------------------------------------------------------------
+
+uint64_t key3(uint64_t x, uint64_t y, uint64_t z) {
+  uint64_t q[3] = {x, y, z};
+  return interleave(q, 3, 21);
+}
+
+void xyz3(uint64_t key, uint64_t* q) { deinterleave(key, 3, 21, q); }
+
+bool on_boundary3(const Oracle& o, uint64_t key) {
+  uint64_t q[3];
+  xyz3(key, q);
+  const uint64_t top = 1ULL << o.LB;
+  for (int k = 0; k < 3; ++k)
+    if (q[k] == 0 || q[k] == top) return true;
+  return false;
+}
+
+void physical3(const Oracle& o, uint64_t key, double* p) {
+  uint64_t q[3];
+  xyz3(key, q);
+  for (int k = 0; k < 3; ++k) p[k] = o.amin[k] + std::ldexp((double)q[k], -o.LB) * o.L;
+}
+
+i128 det3(const i128* a, const i128* b, const i128* c) {
+  return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+i128 orient3(const std::array<uint64_t, 4>& t) {
+  i128 P[4][3];
+  for (int v = 0; v < 4; ++v) {
+    uint64_t q[3];
+    xyz3(t[v], q);
+    for (int k = 0; k < 3; ++k) P[v][k] = (i128)q[k];
+  }
+  i128 a[3], b[3], c[3];
+  for (int k = 0; k < 3; ++k) {
+    a[k] = P[1][k] - P[0][k];
+    b[k] = P[2][k] - P[0][k];
+    c[k] = P[3][k] - P[0][k];
+  }
+  return det3(a, b, c);
+}
+
+bool split3(const Oracle& o, int depth, const int64_t* q) {
+  const int64_t nb = 1LL << depth;
+  uint64_t u[3];
+  for (int k = 0; k < 3; ++k) {
+    if (q[k] < 0 || q[k] >= nb) return false;
+    u[k] = (uint64_t)q[k];
+  }
+  uint8_t sp = 0;
+  return box_exists(o, depth, u, &sp) && sp;
+}
+
+// Tetrahedra of box (depth, q) as seen at level lvl.
+void box_tets(const Oracle& o, int depth, const uint64_t* q, int lvl, std::vector<std::array<uint64_t, 4>>& out) {
+  const uint64_t s = 1ULL << (o.LB - depth), h = s / 2;
+  const int64_t qi[3] = {(int64_t)q[0], (int64_t)q[1], (int64_t)q[2]};
+  auto pt = [&](int u0, int u1, int u2) {  // local coordinates in units of h (0..2)
+    return key3(q[0] * s + u0 * h, q[1] * s + u1 * h, q[2] * s + u2 * h);
+  };
+  bool facesub[3][2] = {{false, false}, {false, false}, {false, false}};
+  bool anyhang = false;
+  // edge midpoint of the cube edge along axis e at sides (sf, sg) of the other axes
+  auto edgemid = [&](int e, int f, int sf, int g, int sg) {
+    if (depth >= lvl) return false;
+    int64_t n1[3] = {qi[0], qi[1], qi[2]}, n2[3] = {qi[0], qi[1], qi[2]}, n3[3] = {qi[0], qi[1], qi[2]};
+    (void)e;
+    n1[f] += sf ? 1 : -1;
+    n2[g] += sg ? 1 : -1;
+    n3[f] += sf ? 1 : -1;
+    n3[g] += sg ? 1 : -1;
+    return split3(o, depth, n1) || split3(o, depth, n2) || split3(o, depth, n3);
+  };
+  if (depth < lvl) {
+    for (int a = 0; a < 3; ++a)
+      for (int sd = 0; sd < 2; ++sd) {
+        int64_t n[3] = {qi[0], qi[1], qi[2]};
+        n[a] += sd ? 1 : -1;
+        facesub[a][sd] = split3(o, depth, n);
+      }
+    for (int e = 0; e < 3 && !anyhang; ++e) {
+      int f = (e + 1) % 3, g = (e + 2) % 3;
+      for (int sf = 0; sf < 2 && !anyhang; ++sf)
+        for (int sg = 0; sg < 2 && !anyhang; ++sg)
+          if (edgemid(e, f, sf, g, sg)) anyhang = true;
+    }
+  }
+  auto push = [&](std::array<uint64_t, 4> t) {
+    if (orient3(t) < 0) std::swap(t[2], t[3]);
+    out.push_back(t);
+  };
+  if (!anyhang) {  // Kuhn: (0, e_a, e_a + e_b, 1)
+    const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (auto& pm : perm) {
+      int u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
+      u1[pm[0]] = 2;
+      u2[pm[0]] = 2;
+      u2[pm[1]] = 2;
+      push({pt(0, 0, 0), pt(u1[0], u1[1], u1[2]), pt(u2[0], u2[1], u2[2]), pt(2, 2, 2)});
+    }
+    return;
+  }
+  const uint64_t C = pt(1, 1, 1);
+  for (int a = 0; a < 3; ++a) {
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;  // in-plane axes, b < c
+    for (int sd = 0; sd < 2; ++sd) {
+      auto fp = [&](int ub, int uc) {
+        int u[3];
+        u[a] = 2 * sd;
+        u[b] = ub;
+        u[c] = uc;
+        return pt(u[0], u[1], u[2]);
+      };
+      std::vector<std::array<uint64_t, 3>> tris;
+      if (facesub[a][sd]) {
+        for (int sb = 0; sb < 2; ++sb)
+          for (int sc = 0; sc < 2; ++sc) {
+            tris.push_back({fp(sb, sc), fp(sb + 1, sc), fp(sb + 1, sc + 1)});
+            tris.push_back({fp(sb, sc), fp(sb + 1, sc + 1), fp(sb, sc + 1)});
+          }
+      } else {
+        // edges of this face: along b at c = 0 / 2, along c at b = 0 / 2
+        bool m_c0 = edgemid(b, a, sd, c, 0), m_c2 = edgemid(b, a, sd, c, 1);
+        bool m_b0 = edgemid(c, a, sd, b, 0), m_b2 = edgemid(c, a, sd, b, 1);
+        if (m_c0 || m_c2 || m_b0 || m_b2) {
+          std::vector<uint64_t> ring;
+          ring.push_back(fp(0, 0));
+          if (m_c0) ring.push_back(fp(1, 0));
+          ring.push_back(fp(2, 0));
+          if (m_b2) ring.push_back(fp(2, 1));
+          ring.push_back(fp(2, 2));
+          if (m_c2) ring.push_back(fp(1, 2));
+          ring.push_back(fp(0, 2));
+          if (m_b0) ring.push_back(fp(0, 1));
+          for (size_t i = 0; i < ring.size(); ++i) tris.push_back({ring[i], ring[(i + 1) % ring.size()], fp(1, 1)});
+        } else {
+          tris.push_back({fp(0, 0), fp(2, 0), fp(2, 2)});
+          tris.push_back({fp(0, 0), fp(2, 2), fp(0, 2)});
+        }
+      }
+      for (auto& t : tris) push({t[0], t[1], t[2], C});
+    }
+  }
+}
+
+void level_tets(const Oracle& o, int lvl, std::vector<std::array<uint64_t, 4>>& tet) {
+  tet.clear();
+  for (int depth = 0; depth <= lvl && depth < (int)o.boxes.size(); ++depth) {
+    std::vector<std::pair<uint64_t, uint8_t>> bx(o.boxes[depth].begin(), o.boxes[depth].end());
+    std::sort(bx.begin(), bx.end());
+    for (auto& kv : bx) {
+      if (depth < lvl && kv.second) continue;
+      uint64_t q[3];
+      unpack_box(kv.first, 3, q);
+      box_tets(o, depth, q, lvl, tet);
+    }
+  }
+}
+
+typedef std::array<double, 3> P3;
+
+// barycentric coordinates of x in tetrahedron T (Cramer's rule)
+void bary3(const P3* T, const P3& x, double* lam) {
+  double e1[3], e2[3], e3[3], r[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = T[1][k] - T[0][k];
+    e2[k] = T[2][k] - T[0][k];
+    e3[k] = T[3][k] - T[0][k];
+    r[k] = x[k] - T[0][k];
+  }
+  auto det = [](const double* a, const double* b, const double* c) {
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+  };
+  const double d = det(e1, e2, e3);
+  lam[1] = det(r, e2, e3) / d;
+  lam[2] = det(e1, r, e3) / d;
+  lam[3] = det(e1, e2, r) / d;
+  lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+}
+
+double tet_volume(const P3& a, const P3& b, const P3& c, const P3& d) {
+  double e1[3], e2[3], e3[3];
+  for (int k = 0; k < 3; ++k) {
+    e1[k] = b[k] - a[k];
+    e2[k] = c[k] - a[k];
+    e3[k] = d[k] - a[k];
+  }
+  return (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+          e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+}
+
+// P1 stiffness of a tetrahedron: |T| grad lambda_i . grad lambda_j
+void tet_stiffness(const P3* T, double K[4][4]) {
+  double Jm[3][3];
+  for (int k = 1; k <= 3; ++k)
+    for (int r = 0; r < 3; ++r) Jm[r][k - 1] = T[k][r] - T[0][r];
+  double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) - Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
+               Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+  double inv[3][3];
+  inv[0][0] = (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) / det;
+  inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
+  inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
+  inv[1][0] = (Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2]) / det;
+  inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
+  inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
+  inv[2][0] = (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]) / det;
+  inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
+  inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
+  double G[4][3];
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < 3; ++r) G[k + 1][r] = inv[k][r];
+  for (int r = 0; r < 3; ++r) G[0][r] = -(G[1][r] + G[2][r] + G[3][r]);
+  const double vol = det / 6.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) K[i][j] = vol * (G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2]);
+}
+
+// Convex polyhedron as a list of face polygons; clipping keeps n.x <= c.
+struct Polyh {
+  std::vector<std::vector<P3>> f;
+};
+
+Polyh clip_poly3(const Polyh& in, const P3& n, double c, double tol) {
+  // a plane that does not cross the (convex) polyhedron keeps it whole or
+  // leaves nothing of positive volume; faces lying in the plane are not cut
+  double dmin = INFINITY, dmax = -INFINITY;
+  for (auto& face : in.f)
+    for (auto& A : face) {
+      double d = n[0] * A[0] + n[1] * A[1] + n[2] * A[2] - c;
+      dmin = std::min(dmin, d);
+      dmax = std::max(dmax, d);
+    }
+  if (dmax <= tol) return in;
+  if (dmin >= -tol) return Polyh();
+  Polyh out;
+  std::vector<P3> cap;
+  for (auto& face : in.f) {
+    std::vector<P3> nf;
+    const size_t m = face.size();
+    for (size_t i = 0; i < m; ++i) {
+      const P3& A = face[i];
+      const P3& B = face[(i + 1) % m];
+      double dA = n[0] * A[0] + n[1] * A[1] + n[2] * A[2] - c;
+      double dB = n[0] * B[0] + n[1] * B[1] + n[2] * B[2] - c;
+      if (dA <= 0) nf.push_back(A);
+      if (std::fabs(dA) <= tol) cap.push_back(A);
+      if ((dA <= 0) != (dB <= 0)) {
+        double t = dA / (dA - dB);
+        P3 X = {A[0] + t * (B[0] - A[0]), A[1] + t * (B[1] - A[1]), A[2] + t * (B[2] - A[2])};
+        nf.push_back(X);
+        cap.push_back(X);
+      }
+    }
+    if (nf.size() >= 3) out.f.push_back(nf);
+  }
+  // cap: distinct points ordered by angle about their centroid in the plane
+  std::vector<P3> pts;
+  for (auto& X : cap) {
+    bool dup = false;
+    for (auto& Y : pts)
+      if (std::fabs(X[0] - Y[0]) <= tol && std::fabs(X[1] - Y[1]) <= tol && std::fabs(X[2] - Y[2]) <= tol) dup = true;
+    if (!dup) pts.push_back(X);
+  }
+  if (pts.size() >= 3) {
+    P3 cen = {0, 0, 0};
+    for (auto& X : pts)
+      for (int k = 0; k < 3; ++k) cen[k] += X[k] / pts.size();
+    P3 u = {pts[0][0] - cen[0], pts[0][1] - cen[1], pts[0][2] - cen[2]};
+    double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    if (un > 0) {
+      for (int k = 0; k < 3; ++k) u[k] /= un;
+      P3 v = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
+      std::vector<std::pair<double, P3>> ang;
+      for (auto& X : pts) {
+        double dx = X[0] - cen[0], dy = X[1] - cen[1], dz = X[2] - cen[2];
+        ang.push_back({std::atan2(dx * v[0] + dy * v[1] + dz * v[2], dx * u[0] + dy * u[1] + dz * u[2]), X});
+      }
+      std::sort(ang.begin(), ang.end(), [](const std::pair<double, P3>& a, const std::pair<double, P3>& b) {
+        return a.first < b.first;
+      });
+      std::vector<P3> capf;
+      for (auto& a : ang) capf.push_back(a.second);
+      out.f.push_back(capf);
+    }
+  }
+  return out;
+}
+
+// int over the polyhedron of f * g for affine f, g given as evaluators:
+// cone every face fan to the vertex centroid; on a tetrahedron
+// int f g = |T|/20 (sum_i f_i g_i + sum_i f_i sum_i g_i).
+template <class F, class G>
+double poly_integral(const Polyh& P, F f, G g) {
+  P3 cen = {0, 0, 0};
+  size_t cnt = 0;
+  for (auto& face : P.f)
+    for (auto& X : face) {
+      for (int k = 0; k < 3; ++k) cen[k] += X[k];
+      ++cnt;
+    }
+  if (cnt == 0) return 0.0;
+  for (int k = 0; k < 3; ++k) cen[k] /= cnt;
+  double sum = 0.0;
+  for (auto& face : P.f)
+    for (size_t i = 1; i + 1 < face.size(); ++i) {
+      const P3* V[4] = {&cen, &face[0], &face[i], &face[i + 1]};
+      double vol = std::fabs(tet_volume(*V[0], *V[1], *V[2], *V[3]));
+      double fv[4], gv[4], sf = 0, sg = 0, sfg = 0;
+      for (int k = 0; k < 4; ++k) {
+        fv[k] = f(*V[k]);
+        gv[k] = g(*V[k]);
+        sf += fv[k];
+        sg += gv[k];
+        sfg += fv[k] * gv[k];
+      }
+      sum += vol / 20.0 * (sfg + sf * sg);
+    }
+  return sum;
+}
+
+Polyh tet_poly(const P3* T) {
+  Polyh P;
+  const int fc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  for (auto& fi : fc) P.f.push_back({T[fi[0]], T[fi[1]], T[fi[2]]});
+  return P;
+}
+
+// sigma cut by the 4 half-spaces of K
+Polyh clip_by_tet(const P3* S, const P3* K) {
+  Polyh P = tet_poly(S);
+  double diam = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 3; ++k) diam = std::max(diam, std::fabs(S[i][k] - S[j][k]));
+  const double tol = 1e-13 * diam;
+  const int fc[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};  // face + opposite vertex
+  for (auto& f : fc) {
+    const P3 &a = K[f[0]], &b = K[f[1]], &c = K[f[2]], &d = K[f[3]];
+    P3 e1 = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2 = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    P3 n = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) n[k] /= nn;
+    double cc = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+    if (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > cc) {  // inside is the side of the opposite vertex
+      for (int k = 0; k < 3; ++k) n[k] = -n[k];
+      cc = -cc;
+    }
+    P = clip_poly3(P, n, cc, tol);
+    if (P.f.size() < 4) return Polyh();
+  }
+  return P;
+}
+
+void leaves_overlapping3(const Oracle& o, const double* lo, const double* hi, std::vector<std::array<uint64_t, 4>>& out) {
+  std::vector<std::array<uint64_t, 4>> st;
+  st.push_back({0, 0, 0, 0});
+  while (!st.empty()) {
+    auto b = st.back();
+    st.pop_back();
+    int depth = (int)b[0];
+    double w = std::ldexp(o.L, -depth);
+    bool meet = true;
+    for (int k = 0; k < 3; ++k) {
+      double x0 = o.amin[k] + (double)b[1 + k] * w;
+      if (x0 > hi[k] || x0 + w < lo[k]) meet = false;
+    }
+    if (!meet) continue;
+    uint64_t q[3] = {b[1], b[2], b[3]};
+    uint8_t sp = 0;
+    if (!box_exists(o, depth, q, &sp)) continue;
+    if (!sp) {
+      out.push_back(b);
+      continue;
+    }
+    for (int ch = 0; ch < 8; ++ch)
+      st.push_back({(uint64_t)depth + 1, 2 * b[1] + (ch & 1), 2 * b[2] + ((ch >> 1) & 1), 2 * b[3] + (ch >> 2)});
+  }
+}
+
+void tet_points(const Oracle& o, const std::array<uint64_t, 4>& t, P3* K) {
+  for (int v = 0; v < 4; ++v) {
+    double p[3];
+    physical3(o, t[v], p);
+    K[v] = {p[0], p[1], p[2]};
+  }
+}
+
+void build_aux3(Oracle& o) {
+  const int J = o.J;
+  o.LB = J + 1;
+  if (o.LB > 21) {
+    o.err = "oracle: 3D auxiliary hierarchy deeper than 20 levels";
+    return;
+  }
+  o.lv.assign(J + 1, Level());
+  for (int l = 0; l <= J; ++l) {
+    Level& L = o.lv[l];
+    level_tets(o, l, L.tet);
+    for (auto& t : L.tet)
+      for (int k = 0; k < 4; ++k) L.allkey.push_back(t[k]);
+    std::sort(L.allkey.begin(), L.allkey.end());
+    L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
+    for (auto k : L.allkey)
+      if (!on_boundary3(o, k)) L.key.push_back(k);
+  }
+  o.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if ((int64_t)o.lv[l].key.size() <= o.prm.coarse_max) o.c = l;
+  // finest coefficient: volume-weighted mean of the fine coefficients (clipping)
+  Level& LJ = o.lv[J];
+  std::map<std::array<uint64_t, 4>, int64_t> tet_index;
+  for (size_t t = 0; t < LJ.tet.size(); ++t) tet_index[LJ.tet[t]] = (int64_t)t;
+  std::vector<double> num(LJ.tet.size(), 0.0);
+  std::vector<std::array<uint64_t, 4>> leaves, kt;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    P3 T[4];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < 4; ++v)
+      for (int k = 0; k < 3; ++k) {
+        T[v][k] = o.X[(int64_t)o.E[4 * e + v] * 3 + k];
+        lo[k] = std::min(lo[k], T[v][k]);
+        hi[k] = std::max(hi[k], T[v][k]);
+      }
+    leaves.clear();
+    leaves_overlapping3(o, lo, hi, leaves);
+    const double a = o.coeff.empty() ? 1.0 : o.coeff[e];
+    for (auto& b : leaves) {
+      kt.clear();
+      uint64_t q[3] = {b[1], b[2], b[3]};
+      box_tets(o, (int)b[0], q, J, kt);
+      for (auto& k4 : kt) {
+        P3 K[4];
+        tet_points(o, k4, K);
+        Polyh P = clip_by_tet(T, K);
+        if (P.f.empty()) continue;
+        double vol = poly_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
+        num[tet_index.at(k4)] += a * vol;
+      }
+    }
+  }
+  o.finest_coef.resize(LJ.tet.size());
+  for (size_t t = 0; t < LJ.tet.size(); ++t) {
+    P3 K[4];
+    tet_points(o, LJ.tet[t], K);
+    o.finest_coef[t] = num[t] / tet_volume(K[0], K[1], K[2], K[3]);
+  }
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(LJ.key.size());
+    for (size_t t = 0; t < LJ.tet.size(); ++t) {
+      P3 K[4];
+      tet_points(o, LJ.tet[t], K);
+      int32_t id[4];
+      for (int k = 0; k < 4; ++k) id[k] = find_index(LJ.key, LJ.tet[t][k]);
+      double Ke[4][4];
+      tet_stiffness(K, Ke);
+      for (int i = 0; i < 4; ++i)
+        if (id[i] >= 0)
+          for (int j = 0; j < 4; ++j)
+            if (id[j] >= 0) rows[id[i]].push_back({id[j], o.finest_coef[t] * Ke[i][j]});
+    }
+    LJ.A = csr_from_rows(LJ.key.size(), LJ.key.size(), rows);
+  }
+  // nodal interpolation from level l-1
+  for (int l = std::max(1, o.c + 1); l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    Level& Lc = o.lv[l - 1];
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(Lf.key.size());
+    for (size_t k = 0; k < Lf.key.size(); ++k) {
+      int32_t j = find_index(Lc.key, Lf.key[k]);
+      if (j >= 0) {
+        rows[k].push_back({j, 1.0});
+        continue;
+      }
+      uint64_t x[3];
+      xyz3(Lf.key[k], x);
+      int depth = 0;
+      uint64_t bq[3] = {0, 0, 0};
+      for (;;) {
+        uint8_t sp = 0;
+        box_exists(o, depth, bq, &sp);
+        if (depth == l - 1 || !sp) break;
+        uint64_t half = 1ULL << (o.LB - depth - 1);
+        for (int d = 0; d < 3; ++d) bq[d] = 2 * bq[d] + ((x[d] - bq[d] * 2 * half) >= half ? 1 : 0);
+        ++depth;
+      }
+      std::vector<std::array<uint64_t, 4>> tets;
+      box_tets(o, depth, bq, l - 1, tets);
+      bool found = false;
+      for (auto& t : tets) {
+        i128 P[4][3];
+        for (int v = 0; v < 4; ++v) {
+          uint64_t q[3];
+          xyz3(t[v], q);
+          for (int d = 0; d < 3; ++d) P[v][d] = (i128)q[d];
+        }
+        i128 e1[3], e2[3], e3[3], r[3];
+        for (int d = 0; d < 3; ++d) {
+          e1[d] = P[1][d] - P[0][d];
+          e2[d] = P[2][d] - P[0][d];
+          e3[d] = P[3][d] - P[0][d];
+          r[d] = (i128)x[d] - P[0][d];
+        }
+        i128 det = det3(e1, e2, e3);
+        i128 n1 = det3(r, e2, e3), n2 = det3(e1, r, e3), n3 = det3(e1, e2, r);
+        i128 n0 = det - n1 - n2 - n3;
+        if (n0 < 0 || n1 < 0 || n2 < 0 || n3 < 0) continue;
+        i128 nn[4] = {n0, n1, n2, n3};
+        for (int v = 0; v < 4; ++v) {
+          if (nn[v] == 0) continue;
+          int32_t jj = find_index(Lc.key, t[v]);
+          if (jj < 0) continue;
+          rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
+        }
+        found = true;
+        break;
+      }
+      if (!found) {
+        o.err = "oracle: 3D interpolation point not located";
+        return;
+      }
+    }
+    Lf.I = csr_from_rows(Lf.key.size(), Lc.key.size(), rows);
+  }
+  for (int l = J; l > o.c; --l) {
+    CSR It = transpose(o.lv[l].I);
+    CSR AI = matmul(o.lv[l].A, o.lv[l].I);
+    o.lv[l - 1].A = matmul(It, AI);
+  }
+  for (int l = o.c + 1; l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    std::vector<int32_t> set;
+    if (o.prm.smoothing == 1) {
+      for (size_t k = 0; k < Lf.key.size(); ++k) set.push_back((int32_t)k);
+    } else {
+      std::set<std::array<uint64_t, 4>> prev;
+      for (auto t : o.lv[l - 1].tet) {
+        std::sort(t.begin(), t.end());
+        prev.insert(t);
+      }
+      std::vector<uint8_t> mark(Lf.key.size(), 0);
+      for (auto t : Lf.tet) {
+        auto ts = t;
+        std::sort(ts.begin(), ts.end());
+        if (prev.count(ts)) continue;
+        for (int v = 0; v < 4; ++v) {
+          int32_t id = find_index(Lf.key, t[v]);
+          if (id >= 0) mark[id] = 1;
+        }
+      }
+      for (size_t k = 0; k < Lf.key.size(); ++k)
+        if (mark[k]) set.push_back((int32_t)k);
+    }
+    Lf.smooth = set;
+  }
+}
+
+// Scott-Zhang in 3D: psi_i = (20 lambda_i - 4)/|sigma_i| on the lowest-index
+// tetrahedron at node i; P_ik = int_{sigma_i} psi_i phi_k by exact clipping.
+void build_transfer3(Oracle& o) {
+  const Level& LJ = o.lv[o.J];
+  const int64_t n = o.vertex_of_free.size();
+  std::vector<int32_t> sigma(o.nv, -1);
+  for (int64_t e = 0; e < o.ne; ++e)
+    for (int k = 0; k < 4; ++k) {
+      int32_t v = o.E[4 * e + k];
+      if (sigma[v] < 0) sigma[v] = (int32_t)e;
+    }
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(n), rows_full(n);
+  std::vector<std::array<uint64_t, 4>> leaves, kt;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t v = o.vertex_of_free[i];
+    int32_t e = sigma[v];
+    P3 T[4];
+    int loc = -1;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = 0; k < 4; ++k) {
+      int32_t vk = o.E[4 * (int64_t)e + k];
+      for (int d = 0; d < 3; ++d) {
+        T[k][d] = o.X[(int64_t)vk * 3 + d];
+        lo[d] = std::min(lo[d], T[k][d]);
+        hi[d] = std::max(hi[d], T[k][d]);
+      }
+      if (vk == v) loc = k;
+    }
+    const double vol = tet_volume(T[0], T[1], T[2], T[3]);
+    auto psi = [&](const P3& x) {
+      double l4[4];
+      bary3(T, x, l4);
+      return (20.0 * l4[loc] - 4.0) / vol;
+    };
+    leaves.clear();
+    leaves_overlapping3(o, lo, hi, leaves);
+    for (auto& b : leaves) {
+      kt.clear();
+      uint64_t q[3] = {b[1], b[2], b[3]};
+      box_tets(o, (int)b[0], q, o.J, kt);
+      for (auto& k4 : kt) {
+        P3 K[4];
+        tet_points(o, k4, K);
+        Polyh P = clip_by_tet(T, K);
+        if (P.f.empty()) continue;
+        for (int k = 0; k < 4; ++k) {
+          auto phi = [&](const P3& x) {
+            double l4[4];
+            bary3(K, x, l4);
+            return l4[k];
+          };
+          double val = poly_integral(P, psi, phi);
+          rows_full[i].push_back({find_index(LJ.allkey, k4[k]), val});
+          int32_t jj = find_index(LJ.key, k4[k]);
+          if (jj >= 0) rows[i].push_back({jj, val});
+        }
+      }
+    }
+  }
+  o.P = csr_from_rows(n, LJ.key.size(), rows);
+  o.Pfull = csr_from_rows(n, LJ.allkey.size(), rows_full);
+}
+
+// --------------------------------------------------------------------------
 // Colouring (R10): Jones-Plassmann with splitmix64 priorities on the graph of
 // couplings |a_vw| > 1e-12 sqrt(a_vv a_ww) (entries that vanish by symmetry,
 // e.g. across the hypotenuse of a right isosceles triangle, are not
@@ -1210,14 +1843,15 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
   build_tree(*o);
   if (o->prm.stage >= 1) build_closure(*o);
   if (o->prm.stage >= 2) {
-    if (dim != 2) {
-      o->err = "oracle: auxiliary hierarchy is built for 2D meshes only";
-    } else {
+    if (dim == 2) {
       build_aux(*o);
       if (o->err.empty()) build_transfer(*o);
-      if (o->err.empty()) build_colourings(*o);
-      if (o->err.empty()) build_coarse(*o);
+    } else {
+      build_aux3(*o);
+      if (o->err.empty()) build_transfer3(*o);
     }
+    if (o->err.empty()) build_colourings(*o);
+    if (o->err.empty()) build_coarse(*o);
   }
   if (!o->err.empty()) {
     if (err) snprintf(err, errlen, "%s", o->err.c_str());
@@ -1246,6 +1880,8 @@ int64_t orc_info(void* h, const char* what, int l) {
   if (w == "nlevel") return (int64_t)o.lv.at(l).key.size();
   if (w == "nall") return (int64_t)o.lv.at(l).allkey.size();
   if (w == "ntri") return (int64_t)o.lv.at(l).tri.size();
+  if (w == "ntet") return (int64_t)o.lv.at(l).tet.size();
+  if (w == "LB") return o.LB;
   if (w == "nnzA") return l < 0 ? (int64_t)o.A.col.size() : (int64_t)o.lv.at(l).A.col.size();
   if (w == "nI") return (int64_t)o.lv.at(l).I.col.size();
   if (w == "nsmooth") return l < 0 ? (int64_t)o.fine_smooth.size() : (int64_t)o.lv.at(l).smooth.size();
@@ -1286,6 +1922,7 @@ int orc_get(void* h, const char* what, int l, void* out) {
   if (w == "level_key") { memcpy(out, o.lv.at(l).key.data(), o.lv[l].key.size() * 8); return 0; }
   if (w == "level_allkey") { memcpy(out, o.lv.at(l).allkey.data(), o.lv[l].allkey.size() * 8); return 0; }
   if (w == "level_tri") { memcpy(out, o.lv.at(l).tri.data(), o.lv[l].tri.size() * 24); return 0; }
+  if (w == "level_tet") { memcpy(out, o.lv.at(l).tet.data(), o.lv[l].tet.size() * 32); return 0; }
   if (w == "finest_coef") { memcpy(out, o.finest_coef.data(), o.finest_coef.size() * 8); return 0; }
   if (w == "smooth") {
     if (l < 0) memcpy(out, o.fine_smooth.data(), o.fine_smooth.size() * 4);

@@ -565,3 +565,149 @@ def test_octree_membership_and_counts(gen):
             assert (e - b > 3) if split else (e - b <= 3)
         if d + 1 < len(levels):
             assert levels[d + 1].shape[0] == 8 * int(segs[:, 3].sum())
+
+
+# --------------------------------------------------------------------------
+# 3D: octree closure, tetrahedral auxiliary grids, clipping transfer
+# --------------------------------------------------------------------------
+
+def _xyz3(keys):
+    k = keys.astype(np.uint64)
+    out = [np.zeros_like(k) for _ in range(3)]
+    for j in range(21):
+        for d in range(3):
+            out[d] |= ((k >> np.uint64(3 * j + d)) & np.uint64(1)) << np.uint64(j)
+    return [o.astype(object) for o in out]
+
+
+@pytest.fixture(scope="module")
+def o3(gen):
+    m = gen.grid3d(9, 5)
+    return m, oracle.Oracle(m)
+
+
+def test_3d_aux_grids_conforming_positive_nested(o3):
+    m, o = o3
+    LB = o.info("LB")
+    top = 1 << LB
+    prev = None
+    for l in range(o.J + 1):
+        tet = o.level_tet(l)
+        X, Y, Z = (a.reshape(-1, 4) for a in _xyz3(tet.reshape(-1)))
+        vol6 = []
+        for t in range(tet.shape[0]):
+            e = [(X[t, v] - X[t, 0], Y[t, v] - Y[t, 0], Z[t, v] - Z[t, 0]) for v in (1, 2, 3)]
+            d = (e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0])
+                 + e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]))
+            vol6.append(d)
+        assert all(v > 0 for v in vol6)
+        assert sum(vol6) == 6 * top ** 3                    # tiles the root cube
+        faces = {}
+        for t in range(tet.shape[0]):
+            for skip in range(4):
+                f = tuple(sorted(int(tet[t, v]) for v in range(4) if v != skip))
+                faces[f] = faces.get(f, 0) + 1
+        for f, cnt in faces.items():
+            fx, fy, fz = _xyz3(np.array(f, np.uint64))
+            on_bnd = any(len(set(c)) == 1 and c[0] in (0, top) for c in (fx, fy, fz))
+            assert cnt == (1 if on_bnd else 2)              # conforming, no hanging nodes
+        if prev is not None and tet.shape[0] < 4000:
+            # nested: every vertex of a level-l tetrahedron lies in one level-(l-1) tetrahedron with it
+            PX, PY, PZ = prev
+            cen = [(sum(X[t]) / 4, sum(Y[t]) / 4, sum(Z[t]) / 4) for t in range(tet.shape[0])]
+            for t in range(tet.shape[0]):
+                ok = False
+                for s in range(PX.shape[0]):
+                    inside = True
+                    for pt in [(X[t, v], Y[t, v], Z[t, v]) for v in range(4)] + [cen[t]]:
+                        # barycentric signs (exact in rationals)
+                        A = [(PX[s, v] - PX[s, 0], PY[s, v] - PY[s, 0], PZ[s, v] - PZ[s, 0]) for v in (1, 2, 3)]
+                        r = (pt[0] - PX[s, 0], pt[1] - PY[s, 0], pt[2] - PZ[s, 0])
+
+                        def det(a, b, c):
+                            return (a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+                                    + a[2] * (b[0] * c[1] - b[1] * c[0]))
+                        d0 = det(*A)
+                        ls = [det(r, A[1], A[2]), det(A[0], r, A[2]), det(A[0], A[1], r)]
+                        if min(ls) < 0 or sum(ls) > d0:
+                            inside = False
+                            break
+                    if inside:
+                        ok = True
+                        break
+                assert ok
+        prev = (X, Y, Z)
+
+
+def test_3d_interpolation_and_transfer_reproduce_linears(o3):
+    m, o = o3
+    LB = o.info("LB")
+    a0, a1, a2, L = o.root()
+    for l in range(max(1, o.c + 1), o.J + 1):
+        I = o.I(l)
+        fx, fy, fz = (np.array(v, np.float64) for v in _xyz3(o.level_keys(l)))
+        cx, cy, cz = (np.array(v, np.float64) for v in _xyz3(o.level_keys(l - 1)))
+        full = np.abs(np.asarray(I.sum(1)).ravel() - 1.0) < 1e-15
+        for f, c in ((fx, cx), (fy, cy), (fz, cz)):
+            assert np.allclose((I @ c)[full], f[full], atol=1e-6)
+    Pf = o.P(full=True)
+    X, Y, Z = (a + np.ldexp(np.array(v, np.float64), -LB) * L for a, v in zip((a0, a1, a2), _xyz3(o.level_keys(o.J, True))))
+    vf = o.vertex_of_free()
+    for c0, gx, gy, gz in ((1.0, 0, 0, 0), (0.2, 1.0, -2.0, 0.5)):
+        got = Pf @ (c0 + gx * X + gy * Y + gz * Z)
+        want = c0 + gx * m.verts[vf, 0] + gy * m.verts[vf, 1] + gz * m.verts[vf, 2]
+        assert np.abs(got - want).max() < 1e-10
+
+
+def test_3d_galerkin_equals_rediscretisation(o3):
+    m, o = o3
+    LB = o.info("LB")
+    a0, a1, a2, L = o.root()
+    for l in range(o.c, o.J + 1):
+        tet = o.level_tet(l)
+        keys = o.level_keys(l)
+        P = [a + np.ldexp(np.array(v, np.float64), -LB) * L for a, v in zip((a0, a1, a2), _xyz3(tet.reshape(-1)))]
+        P = np.stack(P, 1).reshape(-1, 4, 3)
+        n = keys.size
+        R = np.zeros((n, n))
+        for t in range(tet.shape[0]):
+            Jm = (P[t, 1:] - P[t, 0]).T
+            G = np.vstack([-np.linalg.inv(Jm).sum(0), np.linalg.inv(Jm)])
+            K = abs(np.linalg.det(Jm)) / 6.0 * G @ G.T
+            idx = np.searchsorted(keys, tet[t])
+            ok = (idx < n) & (keys[np.minimum(idx, n - 1)] == tet[t])
+            for i in range(4):
+                for j in range(4):
+                    if ok[i] and ok[j]:
+                        R[idx[i], idx[j]] += K[i, j]
+        Al = o.A(l).toarray()
+        assert np.abs(Al - R).max() <= 1e-12 * np.abs(R).max()
+
+
+def test_3d_pcg_dense_and_symmetric_preconditioner(gen):
+    m = gen.grid3d(5, 6)
+    o = oracle.Oracle(m, coarse_max=4)
+    b = o.mass_apply(gen.nodal_uniform(m, 8))
+    u, st, it, _ = o.solve(b, rtol=1e-14)
+    ref = np.linalg.solve(o.A().toarray(), b)
+    assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+    n = o.nfree
+    B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_3d_manufactured_solution_second_order(gen):
+    errs = []
+    for n in (5, 9, 17):
+        m = gen.grid3d(n, 7)
+        x, y, z = m.verts.T
+        f = 3 * math.pi ** 2 * np.sin(math.pi * x) * np.sin(math.pi * y) * np.sin(math.pi * z)
+        o = oracle.Oracle(m)
+        u, st, it, _ = o.solve(o.mass_apply(f), rtol=1e-12)
+        assert st == 0
+        vf = o.vertex_of_free()
+        ue = np.sin(math.pi * x[vf]) * np.sin(math.pi * y[vf]) * np.sin(math.pi * z[vf])
+        errs.append(np.sqrt(np.mean((u - ue) ** 2)))
+    r = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.0 < q < 5.0 for q in r), (errs, r)
