@@ -1132,140 +1132,103 @@ void tet_stiffness(const P3* T, double K[4][4]) {
     for (int j = 0; j < 4; ++j) K[i][j] = vol * (G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2]);
 }
 
-// Convex polyhedron as a list of face polygons; clipping keeps n.x <= c.
-struct Polyh {
-  std::vector<std::vector<P3>> f;
+// K cut by the four half-spaces of S, kept as a list of tetrahedra with
+// signs +1 / -1 whose signed sum is the intersection.  A plane cut of one
+// tetrahedron keeps (by the exact sign of each vertex's distance):
+//   1 vertex inside   the corner tetrahedron at that vertex
+//   3 vertices inside the tetrahedron minus the corner at the outside vertex
+//   2 vertices inside the wedge between the two inside vertices, as three
+//                     tetrahedra
+// Every cut point lies on its edge (parameter in [0, 1]), so no tolerance is
+// needed; pieces of zero volume are harmless.
+struct SignedTet {
+  P3 v[4];
+  double sign;
 };
 
-Polyh clip_poly3(const Polyh& in, const P3& n, double c, double tol) {
-  // a plane that does not cross the (convex) polyhedron keeps it whole or
-  // leaves nothing of positive volume; faces lying in the plane are not cut
-  double dmin = INFINITY, dmax = -INFINITY;
-  for (auto& face : in.f)
-    for (auto& A : face) {
-      double d = n[0] * A[0] + n[1] * A[1] + n[2] * A[2] - c;
-      dmin = std::min(dmin, d);
-      dmax = std::max(dmax, d);
-    }
-  if (dmax <= tol) return in;
-  if (dmin >= -tol) return Polyh();
-  Polyh out;
-  std::vector<P3> cap;
-  for (auto& face : in.f) {
-    std::vector<P3> nf;
-    const size_t m = face.size();
-    for (size_t i = 0; i < m; ++i) {
-      const P3& A = face[i];
-      const P3& B = face[(i + 1) % m];
-      double dA = n[0] * A[0] + n[1] * A[1] + n[2] * A[2] - c;
-      double dB = n[0] * B[0] + n[1] * B[1] + n[2] * B[2] - c;
-      if (dA <= 0) nf.push_back(A);
-      if (std::fabs(dA) <= tol) cap.push_back(A);
-      if ((dA <= 0) != (dB <= 0)) {
-        double t = dA / (dA - dB);
-        P3 X = {A[0] + t * (B[0] - A[0]), A[1] + t * (B[1] - A[1]), A[2] + t * (B[2] - A[2])};
-        nf.push_back(X);
-        cap.push_back(X);
-      }
-    }
-    if (nf.size() >= 3) out.f.push_back(nf);
-  }
-  // cap: distinct points ordered by angle about their centroid in the plane
-  std::vector<P3> pts;
-  for (auto& X : cap) {
-    bool dup = false;
-    for (auto& Y : pts)
-      if (std::fabs(X[0] - Y[0]) <= tol && std::fabs(X[1] - Y[1]) <= tol && std::fabs(X[2] - Y[2]) <= tol) dup = true;
-    if (!dup) pts.push_back(X);
-  }
-  if (pts.size() >= 3) {
-    P3 cen = {0, 0, 0};
-    for (auto& X : pts)
-      for (int k = 0; k < 3; ++k) cen[k] += X[k] / pts.size();
-    P3 u = {pts[0][0] - cen[0], pts[0][1] - cen[1], pts[0][2] - cen[2]};
-    double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    if (un > 0) {
-      for (int k = 0; k < 3; ++k) u[k] /= un;
-      P3 v = {n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]};
-      std::vector<std::pair<double, P3>> ang;
-      for (auto& X : pts) {
-        double dx = X[0] - cen[0], dy = X[1] - cen[1], dz = X[2] - cen[2];
-        ang.push_back({std::atan2(dx * v[0] + dy * v[1] + dz * v[2], dx * u[0] + dy * u[1] + dz * u[2]), X});
-      }
-      std::sort(ang.begin(), ang.end(), [](const std::pair<double, P3>& a, const std::pair<double, P3>& b) {
-        return a.first < b.first;
-      });
-      std::vector<P3> capf;
-      for (auto& a : ang) capf.push_back(a.second);
-      out.f.push_back(capf);
-    }
-  }
-  return out;
+P3 edge_point(const P3& a, const P3& b, double da, double db) {
+  const double t = da / (da - db);
+  return {a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2])};
 }
 
-// int over the polyhedron of f * g for affine f, g given as evaluators:
-// cone every face fan to the vertex centroid; on a tetrahedron
-// int f g = |T|/20 (sum_i f_i g_i + sum_i f_i sum_i g_i).
-template <class F, class G>
-double poly_integral(const Polyh& P, F f, G g) {
-  P3 cen = {0, 0, 0};
-  size_t cnt = 0;
-  for (auto& face : P.f)
-    for (auto& X : face) {
-      for (int k = 0; k < 3; ++k) cen[k] += X[k];
-      ++cnt;
+void halfspace_cut(std::vector<SignedTet>& pieces, const P3& n, double c) {
+  std::vector<SignedTet> kept;
+  for (const SignedTet& T : pieces) {
+    double d[4];
+    int in[4], out[4], ni = 0, no = 0;
+    for (int k = 0; k < 4; ++k) {
+      d[k] = n[0] * T.v[k][0] + n[1] * T.v[k][1] + n[2] * T.v[k][2] - c;
+      if (d[k] <= 0) in[ni++] = k; else out[no++] = k;
     }
-  if (cnt == 0) return 0.0;
-  for (int k = 0; k < 3; ++k) cen[k] /= cnt;
-  double sum = 0.0;
-  for (auto& face : P.f)
-    for (size_t i = 1; i + 1 < face.size(); ++i) {
-      const P3* V[4] = {&cen, &face[0], &face[i], &face[i + 1]};
-      double vol = std::fabs(tet_volume(*V[0], *V[1], *V[2], *V[3]));
-      double fv[4], gv[4], sf = 0, sg = 0, sfg = 0;
-      for (int k = 0; k < 4; ++k) {
-        fv[k] = f(*V[k]);
-        gv[k] = g(*V[k]);
-        sf += fv[k];
-        sg += gv[k];
-        sfg += fv[k] * gv[k];
-      }
-      sum += vol / 20.0 * (sfg + sf * sg);
+    if (no == 0) {
+      kept.push_back(T);
+    } else if (ni == 1) {
+      const int a = in[0];
+      SignedTet C;
+      C.v[0] = T.v[a];
+      for (int k = 0; k < 3; ++k) C.v[k + 1] = edge_point(T.v[a], T.v[out[k]], d[a], d[out[k]]);
+      C.sign = T.sign;
+      kept.push_back(C);
+    } else if (ni == 3) {
+      const int o = out[0];
+      SignedTet C;
+      C.v[0] = T.v[o];
+      for (int k = 0; k < 3; ++k) C.v[k + 1] = edge_point(T.v[o], T.v[in[k]], d[o], d[in[k]]);
+      C.sign = -T.sign;
+      kept.push_back(T);
+      kept.push_back(C);
+    } else if (ni == 2) {
+      const P3 &i0 = T.v[in[0]], &i1 = T.v[in[1]];
+      const P3 x00 = edge_point(i0, T.v[out[0]], d[in[0]], d[out[0]]);
+      const P3 x01 = edge_point(i0, T.v[out[1]], d[in[0]], d[out[1]]);
+      const P3 x10 = edge_point(i1, T.v[out[0]], d[in[1]], d[out[0]]);
+      const P3 x11 = edge_point(i1, T.v[out[1]], d[in[1]], d[out[1]]);
+      kept.push_back({{i0, i1, x00, x01}, T.sign});
+      kept.push_back({{i1, x00, x01, x11}, T.sign});
+      kept.push_back({{i1, x00, x11, x10}, T.sign});
     }
-  return sum;
+  }
+  pieces.swap(kept);
 }
 
-Polyh tet_poly(const P3* T) {
-  Polyh P;
-  const int fc[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
-  for (auto& fi : fc) P.f.push_back({T[fi[0]], T[fi[1]], T[fi[2]]});
-  return P;
-}
-
-// sigma cut by the 4 half-spaces of K
-Polyh clip_by_tet(const P3* S, const P3* K) {
-  Polyh P = tet_poly(S);
-  double diam = 0;
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j)
-      for (int k = 0; k < 3; ++k) diam = std::max(diam, std::fabs(S[i][k] - S[j][k]));
-  const double tol = 1e-13 * diam;
+// sigma (S) intersected with the auxiliary tetrahedron K
+std::vector<SignedTet> intersect_tets(const P3* S, const P3* K) {
+  std::vector<SignedTet> pieces(1);
+  for (int k = 0; k < 4; ++k) pieces[0].v[k] = K[k];
+  pieces[0].sign = 1.0;
   const int fc[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};  // face + opposite vertex
   for (auto& f : fc) {
-    const P3 &a = K[f[0]], &b = K[f[1]], &c = K[f[2]], &d = K[f[3]];
+    const P3 &a = S[f[0]], &b = S[f[1]], &c = S[f[2]], &d = S[f[3]];
     P3 e1 = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2 = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
     P3 n = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    for (int k = 0; k < 3; ++k) n[k] /= nn;
     double cc = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
     if (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > cc) {  // inside is the side of the opposite vertex
       for (int k = 0; k < 3; ++k) n[k] = -n[k];
       cc = -cc;
     }
-    P = clip_poly3(P, n, cc, tol);
-    if (P.f.size() < 4) return Polyh();
+    halfspace_cut(pieces, n, cc);
+    if (pieces.empty()) break;
   }
-  return P;
+  return pieces;
+}
+
+// int over the signed pieces of f * g for affine f, g given as evaluators;
+// on a tetrahedron int f g = |T|/20 (sum_i f_i g_i + sum_i f_i sum_i g_i).
+template <class F, class G>
+double pieces_integral(const std::vector<SignedTet>& pieces, F f, G g) {
+  double sum = 0.0;
+  for (const SignedTet& T : pieces) {
+    const double vol = std::fabs(tet_volume(T.v[0], T.v[1], T.v[2], T.v[3]));
+    double sf = 0, sg = 0, sfg = 0;
+    for (int k = 0; k < 4; ++k) {
+      const double fv = f(T.v[k]), gv = g(T.v[k]);
+      sf += fv;
+      sg += gv;
+      sfg += fv * gv;
+    }
+    sum += T.sign * vol / 20.0 * (sfg + sf * sg);
+  }
+  return sum;
 }
 
 void leaves_overlapping3(const Oracle& o, const double* lo, const double* hi, std::vector<std::array<uint64_t, 4>>& out) {
@@ -1348,9 +1311,9 @@ void build_aux3(Oracle& o) {
       for (auto& k4 : kt) {
         P3 K[4];
         tet_points(o, k4, K);
-        Polyh P = clip_by_tet(T, K);
-        if (P.f.empty()) continue;
-        double vol = poly_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
+        std::vector<SignedTet> P = intersect_tets(T, K);
+        if (P.empty()) continue;
+        double vol = pieces_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
         num[tet_index.at(k4)] += a * vol;
       }
     }
@@ -1514,15 +1477,15 @@ void build_transfer3(Oracle& o) {
       for (auto& k4 : kt) {
         P3 K[4];
         tet_points(o, k4, K);
-        Polyh P = clip_by_tet(T, K);
-        if (P.f.empty()) continue;
+        std::vector<SignedTet> P = intersect_tets(T, K);
+        if (P.empty()) continue;
         for (int k = 0; k < 4; ++k) {
           auto phi = [&](const P3& x) {
             double l4[4];
             bary3(K, x, l4);
             return l4[k];
           };
-          double val = poly_integral(P, psi, phi);
+          double val = pieces_integral(P, psi, phi);
           rows_full[i].push_back({find_index(LJ.allkey, k4[k]), val});
           int32_t jj = find_index(LJ.key, k4[k]);
           if (jj >= 0) rows[i].push_back({jj, val});

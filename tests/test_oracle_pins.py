@@ -656,7 +656,33 @@ def test_3d_interpolation_and_transfer_reproduce_linears(o3):
     for c0, gx, gy, gz in ((1.0, 0, 0, 0), (0.2, 1.0, -2.0, 0.5)):
         got = Pf @ (c0 + gx * X + gy * Y + gz * Z)
         want = c0 + gx * m.verts[vf, 0] + gy * m.verts[vf, 1] + gz * m.verts[vf, 2]
-        assert np.abs(got - want).max() < 1e-10
+        assert np.abs(got - want).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed", [4, 11])
+def test_3d_finest_coefficient_is_the_volume_average(gen, seed):
+    # Sec. 4: the finest auxiliary coefficient on a tetrahedron t is
+    # (1/|t|) sum_e a_e |e cap t|.  A constant a is reproduced exactly; for
+    # any a the integral over the cube is conserved (both grids tile it) and
+    # every average lies between the extreme fine values.
+    m = gen.grid3d(9, seed)
+    m.coeff = np.full(m.ne, 3.7)
+    o = oracle.Oracle(m)
+    assert np.abs(o.finest_coef() / 3.7 - 1).max() < 1e-13
+    rng = np.random.default_rng(seed)
+    m.coeff = np.exp(rng.normal(size=m.ne))
+    o = oracle.Oracle(m)
+    LB = o.info("LB")
+    a0, a1, a2, L = o.root()
+    tet = o.level_tet(o.J)
+    P = np.stack([a + np.ldexp(np.array(v, np.float64), -LB) * L
+                  for a, v in zip((a0, a1, a2), _xyz3(tet.reshape(-1)))], 1).reshape(-1, 4, 3)
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6
+    E = m.verts[m.elems]
+    fvol = np.abs(np.linalg.det(E[:, 1:] - E[:, :1])) / 6
+    c = o.finest_coef()
+    assert abs(c @ vol - m.coeff @ fvol) <= 1e-13 * (m.coeff @ fvol)
+    assert c.min() >= m.coeff.min() * (1 - 1e-13) and c.max() <= m.coeff.max() * (1 + 1e-13)
 
 
 def test_3d_galerkin_equals_rediscretisation(o3):
