@@ -43,7 +43,27 @@ def _workload(name: str, seed: int):
     if name.startswith("jitter"):
         m = meshgen.grid2d(int(name[6:]), seed)
         return m, meshgen.nodal_uniform(m, seed + 1000)
+    if name.startswith("kuhn"):
+        return meshgen.workload_3d(seed=seed, nside=int(name[4:]))
     raise ValueError(name)
+
+
+def _describe(name: str) -> str:
+    if name.startswith("graded"):
+        return f"{name}: graded jittered random-diagonal grid, x->x^2, y->y^2"
+    if name.startswith("kuhn"):
+        n = int(name[4:])
+        return (f"{name}: {n}^3 jittered cube grid, 6 Kuhn tetrahedra per cell, coefficient 1 or 1e3 on 8^3 "
+                f"subcubes, f = 1, n_min = 6")
+    if name == "poisson65":
+        return "poisson65: 65^2 jittered random-diagonal grid, sin*sin load"
+    return f"{name}: jittered random-diagonal grid"
+
+
+def _solver_options(name: str) -> dict:
+    # 3D: a leaf holds one cell's six Kuhn tetrahedra, as n_min = 3 makes a
+    # leaf one cell of two triangles in 2D
+    return {"n_min": 6} if name.startswith("kuhn") else {}
 
 
 class ClockSampler:
@@ -258,7 +278,7 @@ def main():
     solvers = {}
     for prec in ([asmg.ASMG_MIXED] if args.no_fp64 else [asmg.ASMG_MIXED, asmg.ASMG_FP64]):
         s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1,
-                        use_pdl=0 if args.no_pdl else 1)
+                        use_pdl=0 if args.no_pdl else 1, **_solver_options(args.workload))
         solvers[prec] = s
     t_setup = time.perf_counter() - t0
     s = solvers[asmg.ASMG_MIXED]
@@ -342,8 +362,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "dofs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: graded jittered random-diagonal grid, x->x^2, y->y^2",
-                   "nfree": n, "triangles": mesh.ne, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
+        "config": {"workload": _describe(args.workload),
+                   "nfree": n, "elements": mesh.ne, "dim": mesh.dim, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
                    "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
                    "setup_breakdown_s": {k: s.info(f"t_{k}_us") / 1e6 for k in ("tree", "aux", "fine", "levels")},

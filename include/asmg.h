@@ -69,10 +69,14 @@ int asmg_default_params(asmg_params* p);
 
 /*
  * Build the solver for one mesh (Sec. 2-4).
- *   dim        2 (triangles).  Other values return ASMG_ERR_UNSUPPORTED.
+ *   dim        2 (triangles; quadtree, triangular auxiliary grids) or 3
+ *              (tetrahedra; octree, Kuhn and coned tetrahedral auxiliary
+ *              grids on the 2^(J+1) lattice of the root cube, Sec. 3 in 3D).
+ *              Other values return ASMG_ERR_UNSUPPORTED.
  *   nv, vertices   float64 [nv * dim], row-major coordinates.
  *   ne, elements   int32 [ne * (dim + 1)], vertex indices of each simplex,
- *                  positively oriented (counter-clockwise).
+ *                  positively oriented (counter-clockwise triangles;
+ *                  tetrahedra with (p1-p0).((p2-p0)x(p3-p0)) > 0).
  *   boundary   uint8 [nv]: 0 free vertex, 1 Dirichlet vertex (u = 0).  The
  *              value 2 (Neumann) returns ASMG_ERR_UNSUPPORTED.
  *   coeff      float64 [ne] per-element coefficient a_e > 0, or NULL for a = 1.
@@ -178,7 +182,8 @@ enum asmg_export_what {
   ASMG_EXPORT_PERM = 1,        /* int32 [ne] elements sorted by key (stable) */
   ASMG_EXPORT_SEG = 2,         /* int64 [nseg(level) * 4]: prefix, begin, end, split */
   ASMG_EXPORT_SPLIT = 3,       /* uint64 [nsplit(level)] Morton prefixes of split boxes, ascending */
-  ASMG_EXPORT_AUX_KEYS = 4,    /* uint64 [naux(J)] lattice Morton keys of the finest-level free nodes */
+  ASMG_EXPORT_AUX_KEYS = 4,    /* uint64 [naux(J)] lattice Morton keys of the finest-level free nodes
+                                  (2D: 2^31 lattice; 3D: 2^(J+1) lattice, 21 bits per coordinate) */
   ASMG_EXPORT_FINE_COLOUR = 5, /* int32 [nfree] colour of each free dof (free dofs in vertex order) */
   ASMG_EXPORT_SMOOTH = 6,      /* uint64 [nsmooth(level) * 2]: node key, colour */
   ASMG_EXPORT_LEVEL_ROWS = 7,  /* (row key, col key, value) triplets of level `level`, as

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libasmg.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cu", "assemble.cu", "solve.cu", "noalloc.cu", "aux_setup.cpp", "capi.cpp"]
+SOURCES = ["tree.cu", "assemble.cu", "solve.cu", "noalloc.cu", "aux_setup.cpp", "aux_setup3.cpp", "capi.cpp"]
 
 
 def _nvcc() -> str:

@@ -74,6 +74,73 @@ __global__ void k_mesh_coo(int64_t ne, const double* __restrict__ X, const int32
   emit9(t, id, K, nullptr, key, val);
 }
 
+// Element stiffness of a tetrahedron: with edge vectors e_k = p_k - p_0 and
+// c_1 = e_2 x e_3, c_2 = e_3 x e_1, c_3 = e_1 x e_2, c_0 = -(c_1 + c_2 + c_3),
+// grad lambda_k = c_k / det (det = e_1 . c_1 = 6 |T|), so
+// K_ij = a |T| grad lambda_i . grad lambda_j = a (c_i . c_j) / (6 det).
+__device__ __forceinline__ void tet_K(const double P[4][3], double a, double K[4][4]) {
+  double e[3][3], c[4][3];
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < 3; ++r) e[k][r] = P[k + 1][r] - P[0][r];
+  for (int k = 0; k < 3; ++k) {
+    const double* u = e[(k + 1) % 3];
+    const double* w = e[(k + 2) % 3];
+    c[k + 1][0] = u[1] * w[2] - u[2] * w[1];
+    c[k + 1][1] = u[2] * w[0] - u[0] * w[2];
+    c[k + 1][2] = u[0] * w[1] - u[1] * w[0];
+  }
+  for (int r = 0; r < 3; ++r) c[0][r] = -(c[1][r] + c[2][r] + c[3][r]);
+  const double det = e[0][0] * c[1][0] + e[0][1] * c[1][1] + e[0][2] * c[1][2];
+  const double sc = a / (6.0 * det);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) K[i][j] = sc * (c[i][0] * c[j][0] + c[i][1] * c[j][1] + c[i][2] * c[j][2]);
+}
+
+__device__ __forceinline__ void emit16(int64_t t, const int32_t id[4], const double K[4][4], const uint8_t* keep,
+                                       uint64_t* key, double* val) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      bool ok = id[i] >= 0 && id[j] >= 0 && (keep == nullptr || keep[id[i]] || keep[id[j]]);
+      key[16 * t + 4 * i + j] = ok ? (((uint64_t)(uint32_t)id[i] << 32) | (uint32_t)id[j]) : ~0ULL;
+      val[16 * t + 4 * i + j] = ok ? K[i][j] : 0.0;
+    }
+}
+
+// tetrahedra given by coordinates and row ids
+__global__ void k_tet_coo(int64_t ntet, const double* __restrict__ XYZ, const int32_t* __restrict__ ID,
+                          const double* __restrict__ coef, const uint8_t* __restrict__ keep, uint64_t* key,
+                          double* val) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ntet) return;
+  double P[4][3];
+  int32_t id[4];
+  for (int k = 0; k < 4; ++k) {
+    for (int r = 0; r < 3; ++r) P[k][r] = XYZ[12 * t + 3 * k + r];
+    id[k] = ID[4 * t + k];
+  }
+  double K[4][4];
+  tet_K(P, coef ? coef[t] : 1.0, K);
+  emit16(t, id, K, keep, key, val);
+}
+
+// tetrahedra of the fine mesh: rows are free-dof numbers
+__global__ void k_mesh_coo3(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
+                            const int32_t* __restrict__ fv, const double* __restrict__ coef, uint64_t* key,
+                            double* val) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne) return;
+  double P[4][3];
+  int32_t id[4];
+  for (int k = 0; k < 4; ++k) {
+    int32_t v = E[4 * t + k];
+    for (int r = 0; r < 3; ++r) P[k][r] = X[3 * (int64_t)v + r];
+    id[k] = fv[v];
+  }
+  double K[4][4];
+  tet_K(P, coef ? coef[t] : 1.0, K);
+  emit16(t, id, K, nullptr, key, val);
+}
+
 HostCSR coo_to_csr(int64_t m, DBuf<uint64_t>& key, DBuf<double>& val, int64_t nrows, cudaStream_t s) {
   DBuf<uint64_t> skey;
   DBuf<double> sval;
@@ -135,6 +202,46 @@ __global__ void k_mass(int64_t ne, const double* __restrict__ X, const int32_t* 
   atomicAdd(&b[v0], w * (sum + f[v0]));
   atomicAdd(&b[v1], w * (sum + f[v1]));
   atomicAdd(&b[v2], w * (sum + f[v2]));
+}
+
+// consistent P1 mass on tetrahedra: b_i += |T|/20 (f_i + sum_j f_j)
+__global__ void k_mass3(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
+                        const double* __restrict__ f, double* __restrict__ b) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne) return;
+  int32_t v[4];
+  double P[4][3];
+  for (int k = 0; k < 4; ++k) {
+    v[k] = E[4 * t + k];
+    for (int r = 0; r < 3; ++r) P[k][r] = X[3 * (int64_t)v[k] + r];
+  }
+  double e[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int r = 0; r < 3; ++r) e[k][r] = P[k + 1][r] - P[0][r];
+  const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) + e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
+                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+  const double w = det / 120.0;  // |T| / 20
+  const double sum = f[v[0]] + f[v[1]] + f[v[2]] + f[v[3]];
+  for (int k = 0; k < 4; ++k) atomicAdd(&b[v[k]], w * (sum + f[v[k]]));
+}
+
+__global__ void k_elem_grad3(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
+                             const double* __restrict__ u, const double* __restrict__ lam, double* __restrict__ g) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ne) return;
+  double P[4][3], ue[4], le[4];
+  for (int k = 0; k < 4; ++k) {
+    int32_t v = E[4 * t + k];
+    for (int r = 0; r < 3; ++r) P[k][r] = X[3 * (int64_t)v + r];
+    ue[k] = u[v];
+    le[k] = lam[v];
+  }
+  double K[4][4];
+  tet_K(P, 1.0, K);
+  double s = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) s += le[i] * K[i][j] * ue[j];
+  g[t] = -s;
 }
 
 // dL/da_e = -lambda_e^T K_e^(1) u_e
@@ -232,44 +339,58 @@ __global__ void k_ig_class(int64_t n, int32_t c, const int64_t* __restrict__ ptr
 
 }  // namespace
 
-HostCSR assemble_triangles(int64_t ntri, const double* dXY, const int32_t* dID, const double* dCoef,
+HostCSR assemble_simplices(int dim, int64_t n, const double* dP, const int32_t* dID, const double* dCoef,
                            const uint8_t* dKeep, int64_t nrows, cudaStream_t s) {
-  if (ntri == 0) {
+  if (n == 0) {
     HostCSR A;
     A.nr = A.nc = nrows;
     A.ptr.assign(nrows + 1, 0);
     return A;
   }
+  const int64_t m = (int64_t)(dim + 1) * (dim + 1) * n;
   DBuf<uint64_t> key;
   DBuf<double> val;
-  key.alloc(9 * ntri);
-  val.alloc(9 * ntri);
-  k_tri_coo<<<nblk(ntri), 256, 0, s>>>(ntri, dXY, dID, dCoef, dKeep, key.p, val.p);
+  key.alloc(m);
+  val.alloc(m);
+  if (dim == 2)
+    k_tri_coo<<<nblk(n), 256, 0, s>>>(n, dP, dID, dCoef, dKeep, key.p, val.p);
+  else
+    k_tet_coo<<<nblk(n), 256, 0, s>>>(n, dP, dID, dCoef, dKeep, key.p, val.p);
   ASMG_CUDA(cudaGetLastError());
-  return coo_to_csr(9 * ntri, key, val, nrows, s);
+  return coo_to_csr(m, key, val, nrows, s);
 }
 
-HostCSR assemble_mesh(int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree, const double* dCoef,
-                      int64_t nfree, cudaStream_t s) {
+HostCSR assemble_mesh(int dim, int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree,
+                      const double* dCoef, int64_t nfree, cudaStream_t s) {
+  const int64_t m = (int64_t)(dim + 1) * (dim + 1) * ne;
   DBuf<uint64_t> key;
   DBuf<double> val;
-  key.alloc(9 * ne);
-  val.alloc(9 * ne);
-  k_mesh_coo<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, dFree, dCoef, key.p, val.p);
+  key.alloc(m);
+  val.alloc(m);
+  if (dim == 2)
+    k_mesh_coo<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, dFree, dCoef, key.p, val.p);
+  else
+    k_mesh_coo3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, dFree, dCoef, key.p, val.p);
   ASMG_CUDA(cudaGetLastError());
-  return coo_to_csr(9 * ne, key, val, nfree, s);
+  return coo_to_csr(m, key, val, nfree, s);
 }
 
-void mass_apply_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
+void mass_apply_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
                     cudaStream_t s) {
   ASMG_CUDA(cudaMemsetAsync(db, 0, 8 * nv, s));
-  k_mass<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, df, db);
+  if (dim == 2)
+    k_mass<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, df, db);
+  else
+    k_mass3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, df, db);
   ASMG_CUDA(cudaGetLastError());
 }
 
-void element_grad_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl, double* dg,
-                      cudaStream_t s) {
-  k_elem_grad<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dg);
+void element_grad_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl,
+                      double* dg, cudaStream_t s) {
+  if (dim == 2)
+    k_elem_grad<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dg);
+  else
+    k_elem_grad3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dg);
   ASMG_CUDA(cudaGetLastError());
 }
 

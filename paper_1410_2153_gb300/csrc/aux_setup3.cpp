@@ -1,0 +1,910 @@
+// Host setup of the 3D auxiliary hierarchy (octree; tetrahedral grids).
+//
+// Closure (Sec. 3.2 in 3D): a split box needs its 6 face and 12 edge
+// neighbours of the same depth, so the parents of those neighbours are
+// refined one level up, finest depth first.
+// Triangulation of a box shown at level l (the 3D counterpart of the
+// "closure2" templates): without edge midpoints or subdivided faces, the 6
+// Kuhn tetrahedra of its (0,0,0)-(1,1,1) diagonal; otherwise each face --
+// subdivided face: its 4 sub-squares split along their min-to-max diagonal;
+// face with an edge midpoint: fan about the face centre; other faces: the
+// min-to-max diagonal -- coned to the box centre.  Nodes lie on the 2^(J+1)
+// lattice of the root cube, named by 63-bit Morton keys; the free nodes of
+// the finest level, in key order, are the auxiliary unknowns.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace asmg {
+
+namespace {
+
+typedef __int128 i128;
+
+inline uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+
+inline uint64_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x1fffffULL;
+  return v;
+}
+
+inline uint64_t m3(uint64_t x, uint64_t y, uint64_t z) { return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2); }
+inline void um3(uint64_t k, uint64_t* q) {
+  q[0] = compact3(k);
+  q[1] = compact3(k >> 1);
+  q[2] = compact3(k >> 2);
+}
+
+struct Tree3 {
+  int LB = 1;  // lattice bits of auxiliary nodes
+  std::vector<std::vector<uint64_t>> S;
+  bool split(int d, uint64_t p) const {
+    if (d < 0 || d >= (int)S.size()) return false;
+    return std::binary_search(S[d].begin(), S[d].end(), p);
+  }
+  bool exists(int d, uint64_t p) const { return d == 0 ? p == 0 : split(d - 1, p >> 3); }
+  bool offset(int d, uint64_t p, const int* o, uint64_t& q) const {
+    uint64_t c[3];
+    um3(p, c);
+    const int64_t nb = 1LL << d;
+    int64_t n[3];
+    for (int k = 0; k < 3; ++k) {
+      n[k] = (int64_t)c[k] + o[k];
+      if (n[k] < 0 || n[k] >= nb) return false;
+    }
+    q = m3(n[0], n[1], n[2]);
+    return true;
+  }
+  bool split_at(int d, uint64_t p, int ox, int oy, int oz) const {
+    int o[3] = {ox, oy, oz};
+    uint64_t q;
+    return offset(d, p, o, q) && split(d, q);
+  }
+};
+
+typedef std::array<uint64_t, 4> Tet;
+
+inline i128 orient(const Tet& t) {
+  i128 P[4][3];
+  for (int v = 0; v < 4; ++v) {
+    uint64_t q[3];
+    um3(t[v], q);
+    for (int k = 0; k < 3; ++k) P[v][k] = (i128)q[k];
+  }
+  i128 a[3], b[3], c[3];
+  for (int k = 0; k < 3; ++k) {
+    a[k] = P[1][k] - P[0][k];
+    b[k] = P[2][k] - P[0][k];
+    c[k] = P[3][k] - P[0][k];
+  }
+  return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+struct BoxShape {
+  bool fsub[3][2];     // face subdivided (axis, side)
+  bool hang = false;   // any edge midpoint
+};
+
+// Is the midpoint of the box edge along axis e, at side sf of axis f and side
+// sg of axis g, a node (some other box of that edge is split)?
+bool edge_mid(const Tree3& T, int d, uint64_t p, int f, int sf, int g, int sg) {
+  int o1[3] = {0, 0, 0}, o2[3] = {0, 0, 0}, o3[3] = {0, 0, 0};
+  o1[f] = sf ? 1 : -1;
+  o2[g] = sg ? 1 : -1;
+  o3[f] = o1[f];
+  o3[g] = o2[g];
+  return T.split_at(d, p, o1[0], o1[1], o1[2]) || T.split_at(d, p, o2[0], o2[1], o2[2]) ||
+         T.split_at(d, p, o3[0], o3[1], o3[2]);
+}
+
+BoxShape shape(const Tree3& T, int d, uint64_t p, int lvl) {
+  BoxShape s;
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd) s.fsub[a][sd] = false;
+  if (d >= lvl) return s;
+  for (int a = 0; a < 3; ++a)
+    for (int sd = 0; sd < 2; ++sd) {
+      int o[3] = {0, 0, 0};
+      o[a] = sd ? 1 : -1;
+      s.fsub[a][sd] = T.split_at(d, p, o[0], o[1], o[2]);
+    }
+  for (int e = 0; e < 3 && !s.hang; ++e) {
+    const int f = (e + 1) % 3, g = (e + 2) % 3;
+    for (int sf = 0; sf < 2 && !s.hang; ++sf)
+      for (int sg = 0; sg < 2 && !s.hang; ++sg)
+        if (edge_mid(T, d, p, f, sf, g, sg)) s.hang = true;
+  }
+  return s;
+}
+
+// Tetrahedra of box (d, p) as seen at level lvl; `kuhn` tells which form.
+void box_tets(const Tree3& T, int d, uint64_t p, int lvl, std::vector<Tet>& out, bool* kuhn = nullptr) {
+  uint64_t c[3];
+  um3(p, c);
+  const uint64_t s = 1ULL << (T.LB - d), h = s / 2;
+  auto pt = [&](int u0, int u1, int u2) { return m3(c[0] * s + u0 * h, c[1] * s + u1 * h, c[2] * s + u2 * h); };
+  auto add = [&](Tet t) {
+    if (orient(t) < 0) std::swap(t[2], t[3]);
+    out.push_back(t);
+  };
+  BoxShape sh = shape(T, d, p, lvl);
+  if (kuhn) *kuhn = !sh.hang;
+  if (!sh.hang) {
+    static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (auto& pm : perm) {
+      int u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
+      u1[pm[0]] = 2;
+      u2[pm[0]] = 2;
+      u2[pm[1]] = 2;
+      add({pt(0, 0, 0), pt(u1[0], u1[1], u1[2]), pt(u2[0], u2[1], u2[2]), pt(2, 2, 2)});
+    }
+    return;
+  }
+  const uint64_t C = pt(1, 1, 1);
+  for (int a = 0; a < 3; ++a) {
+    const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+    for (int sd = 0; sd < 2; ++sd) {
+      auto fp = [&](int ub, int uc) {
+        int u[3];
+        u[a] = 2 * sd;
+        u[b] = ub;
+        u[cc] = uc;
+        return pt(u[0], u[1], u[2]);
+      };
+      if (sh.fsub[a][sd]) {
+        for (int sb = 0; sb < 2; ++sb)
+          for (int sc = 0; sc < 2; ++sc) {
+            add({fp(sb, sc), fp(sb + 1, sc), fp(sb + 1, sc + 1), C});
+            add({fp(sb, sc), fp(sb + 1, sc + 1), fp(sb, sc + 1), C});
+          }
+        continue;
+      }
+      const bool mc0 = edge_mid(T, d, p, a, sd, cc, 0), mc2 = edge_mid(T, d, p, a, sd, cc, 1);
+      const bool mb0 = edge_mid(T, d, p, a, sd, b, 0), mb2 = edge_mid(T, d, p, a, sd, b, 1);
+      if (mc0 || mc2 || mb0 || mb2) {
+        uint64_t ring[8];
+        int n = 0;
+        ring[n++] = fp(0, 0);
+        if (mc0) ring[n++] = fp(1, 0);
+        ring[n++] = fp(2, 0);
+        if (mb2) ring[n++] = fp(2, 1);
+        ring[n++] = fp(2, 2);
+        if (mc2) ring[n++] = fp(1, 2);
+        ring[n++] = fp(0, 2);
+        if (mb0) ring[n++] = fp(0, 1);
+        const uint64_t FC = fp(1, 1);
+        for (int i = 0; i < n; ++i) add({ring[i], ring[(i + 1) % n], FC, C});
+      } else {
+        add({fp(0, 0), fp(2, 0), fp(2, 2), C});
+        add({fp(0, 0), fp(2, 2), fp(0, 2), C});
+      }
+    }
+  }
+}
+
+inline bool bnd3(const Tree3& T, uint64_t k) {
+  uint64_t q[3];
+  um3(k, q);
+  const uint64_t top = 1ULL << T.LB;
+  return q[0] == 0 || q[1] == 0 || q[2] == 0 || q[0] == top || q[1] == top || q[2] == top;
+}
+
+inline int32_t idx_of(const std::vector<uint64_t>& keys, uint64_t k) {
+  auto it = std::lower_bound(keys.begin(), keys.end(), k);
+  return (it != keys.end() && *it == k) ? (int32_t)(it - keys.begin()) : -1;
+}
+
+void uniq(std::vector<uint64_t>& v) {
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+std::vector<uint64_t> boxes_at(const Tree3& T, int d) {
+  if (d == 0) return {0};
+  std::vector<uint64_t> b;
+  if (d - 1 >= (int)T.S.size()) return b;
+  b.reserve(T.S[d - 1].size() * 8);
+  for (uint64_t p : T.S[d - 1])
+    for (uint64_t c = 0; c < 8; ++c) b.push_back((p << 3) | c);
+  return b;
+}
+
+// ---------------------------------------------------------------- clipping
+// A convex region kept as a list of tetrahedra; a plane cut replaces every
+// tetrahedron by the tetrahedra of its kept part (0, 1 or 3 pieces).
+typedef std::array<double, 3> V3;
+typedef std::array<V3, 4> TetP;
+
+inline double vol6(const V3& a, const V3& b, const V3& c, const V3& d) {
+  const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]},
+               e3[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+  return e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+         e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
+}
+
+inline V3 lerp(const V3& a, const V3& b, double da, double db) {
+  const double t = da / (da - db);
+  return V3{a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2])};
+}
+
+// keep the part with n.x - c <= 0; vertices are classified by the exact sign
+// of their distance, so every intersection parameter lies in [0, 1) and no
+// point is moved across a plane (pieces of zero volume are harmless)
+void cut(std::vector<TetP>& tets, std::vector<TetP>& out, const V3& n, double c) {
+  out.clear();
+  for (const TetP& t : tets) {
+    double dv[4];
+    int in[4], ni = 0, ou[4], no = 0;
+    for (int v = 0; v < 4; ++v) {
+      dv[v] = n[0] * t[v][0] + n[1] * t[v][1] + n[2] * t[v][2] - c;
+      if (dv[v] <= 0) in[ni++] = v; else ou[no++] = v;
+    }
+    if (no == 0) {
+      out.push_back(t);
+      continue;
+    }
+    if (ni == 0) continue;
+    if (ni == 1) {
+      const V3& a = t[in[0]];
+      out.push_back({a, lerp(a, t[ou[0]], dv[in[0]], dv[ou[0]]), lerp(a, t[ou[1]], dv[in[0]], dv[ou[1]]),
+                     lerp(a, t[ou[2]], dv[in[0]], dv[ou[2]])});
+    } else if (ni == 3) {
+      // prism: inside triangle (a0 a1 a2), cut triangle (b0 b1 b2), ak - bk edges
+      V3 A[3], B[3];
+      for (int k = 0; k < 3; ++k) {
+        A[k] = t[in[k]];
+        B[k] = lerp(t[in[k]], t[ou[0]], dv[in[k]], dv[ou[0]]);
+      }
+      out.push_back({A[0], A[1], A[2], B[0]});
+      out.push_back({A[1], A[2], B[0], B[1]});
+      out.push_back({A[2], B[0], B[1], B[2]});
+    } else {
+      // two inside (i0, i1), two outside (o0, o1): prism with triangles
+      // (i0, p00, p01) and (i1, p10, p11)
+      const V3 &i0 = t[in[0]], &i1 = t[in[1]];
+      V3 A[3] = {i0, lerp(i0, t[ou[0]], dv[in[0]], dv[ou[0]]), lerp(i0, t[ou[1]], dv[in[0]], dv[ou[1]])};
+      V3 B[3] = {i1, lerp(i1, t[ou[0]], dv[in[1]], dv[ou[0]]), lerp(i1, t[ou[1]], dv[in[1]], dv[ou[1]])};
+      out.push_back({A[0], A[1], A[2], B[0]});
+      out.push_back({A[1], A[2], B[0], B[1]});
+      out.push_back({A[2], B[0], B[1], B[2]});
+    }
+  }
+}
+
+// S cut by the four half-spaces of tetrahedron K (scratch: a work buffer);
+// disjoint bounding boxes give no pieces
+void clip_tets(const TetP& S, const TetP& K, std::vector<TetP>& out, std::vector<TetP>& scratch) {
+  out.clear();
+  for (int k = 0; k < 3; ++k) {
+    double s0 = S[0][k], s1 = S[0][k], k0 = K[0][k], k1 = K[0][k];
+    for (int v = 1; v < 4; ++v) {
+      s0 = std::min(s0, S[v][k]);
+      s1 = std::max(s1, S[v][k]);
+      k0 = std::min(k0, K[v][k]);
+      k1 = std::max(k1, K[v][k]);
+    }
+    if (s1 <= k0 || k1 <= s0) return;
+  }
+  out.push_back(S);
+  static const int fc[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};
+  for (auto& f : fc) {
+    const V3 &a = K[f[0]], &b = K[f[1]], &c = K[f[2]], &d = K[f[3]];
+    const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    V3 n = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) n[k] /= nn;
+    double cc = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+    if (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > cc) {
+      for (int k = 0; k < 3; ++k) n[k] = -n[k];
+      cc = -cc;
+    }
+    cut(out, scratch, n, cc);
+    out.swap(scratch);
+    if (out.empty()) return;
+  }
+}
+
+// affine function of x: f0 + f.x
+struct Aff {
+  double c0, g[3];
+  double operator()(const V3& x) const { return c0 + g[0] * x[0] + g[1] * x[1] + g[2] * x[2]; }
+};
+
+// barycentric function of vertex j of tetrahedron T as an affine function
+Aff bary(const TetP& T, int j) {
+  double Jm[3][3];
+  for (int k = 1; k <= 3; ++k)
+    for (int r = 0; r < 3; ++r) Jm[r][k - 1] = T[k][r] - T[0][r];
+  double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) - Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
+               Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+  double inv[3][3];
+  inv[0][0] = (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) / det;
+  inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
+  inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
+  inv[1][0] = (Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2]) / det;
+  inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
+  inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
+  inv[2][0] = (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]) / det;
+  inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
+  inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
+  Aff f;
+  if (j == 0) {
+    for (int r = 0; r < 3; ++r) f.g[r] = -(inv[0][r] + inv[1][r] + inv[2][r]);
+  } else {
+    for (int r = 0; r < 3; ++r) f.g[r] = inv[j - 1][r];
+  }
+  f.c0 = 1.0 * (j == 0) - (f.g[0] * T[0][0] + f.g[1] * T[0][1] + f.g[2] * T[0][2]);
+  return f;
+}
+
+// int over tetrahedron t of f * g (affine f, g) by the symmetric 4-point
+// degree-2 rule: points a v_i + b (sum of the other three vertices) with
+// a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights |t|/4.
+double prod4(const TetP& t, const Aff& f, const Aff& g) {
+  static const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
+  const double vol = std::fabs(vol6(t[0], t[1], t[2], t[3])) / 6.0;
+  double s = 0;
+  for (int i = 0; i < 4; ++i) {
+    V3 x;
+    for (int k = 0; k < 3; ++k) x[k] = a * t[i][k] + b * (t[(i + 1) % 4][k] + t[(i + 2) % 4][k] + t[(i + 3) % 4][k]);
+    s += f(x) * g(x);
+  }
+  return s * vol / 4.0;
+}
+
+void leaves_in(const Tree3& T, const int64_t* lo, const int64_t* hi, std::vector<std::pair<int, uint64_t>>& out,
+               std::vector<std::pair<int, uint64_t>>& st) {
+  st.clear();
+  st.push_back({0, 0});
+  while (!st.empty()) {
+    auto b = st.back();
+    st.pop_back();
+    const int64_t s = 1LL << (T.LB - b.first);
+    uint64_t c[3];
+    um3(b.second, c);
+    bool meet = true;  // positive-volume overlap with the window
+    for (int k = 0; k < 3; ++k) {
+      const int64_t x0 = (int64_t)c[k] * s;
+      if (x0 >= hi[k] || x0 + s <= lo[k]) meet = false;
+    }
+    if (!meet) continue;
+    if (!T.split(b.first, b.second)) {
+      out.push_back(b);
+      continue;
+    }
+    for (uint64_t ch = 0; ch < 8; ++ch) st.push_back({b.first + 1, (b.second << 3) | ch});
+  }
+}
+
+template <class F>
+void pfor(int64_t n, F f) {
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 2048) nt = 1;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) th.emplace_back([&, t] { f(t, n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
+// index of the Kuhn tetrahedron of a box holding point u (local coordinates
+// in units of the box, 0..1): the order of the coordinates
+int kuhn_index(const double* u) {
+  static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  for (int k = 0; k < 6; ++k) {
+    const int* pm = perm[k];
+    if (u[pm[0]] >= u[pm[1]] && u[pm[1]] >= u[pm[2]]) return k;
+  }
+  return 0;
+}
+
+}  // namespace
+
+void lattice_point3(const TreeResult& t, int LB, uint64_t key, double* p) {
+  uint64_t q[3];
+  um3(key, q);
+  for (int k = 0; k < 3; ++k) p[k] = t.amin[k] + std::ldexp((double)q[k], -LB) * t.L;
+}
+
+void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
+                     const std::vector<int32_t>& free_of_vertex, AuxHost& out) {
+  Tree3 T;
+  T.S = tree.split;
+  // closure, finest depth first: the parents of all face and edge neighbours
+  // of every split box are split
+  for (int d = (int)T.S.size() - 1; d >= 1; --d) {
+    std::vector<uint64_t> add;
+    for (uint64_t p : T.S[d])
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int nz = (ox != 0) + (oy != 0) + (oz != 0);
+            if (nz < 1 || nz > 2) continue;
+            int o[3] = {ox, oy, oz};
+            uint64_t q;
+            if (T.offset(d, p, o, q)) add.push_back(q >> 3);
+          }
+    auto& up = T.S[d - 1];
+    up.insert(up.end(), add.begin(), add.end());
+    uniq(up);
+  }
+  out.split = T.S;
+  const int J = (int)T.S.size();
+  out.J = J;
+  if (J + 1 > 21) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "3D auxiliary hierarchy deeper than 20 levels");
+  T.LB = J + 1;
+  out.LB = T.LB;
+  std::vector<std::vector<uint64_t>> BX(J + 1);
+  for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
+
+  // finest-level free nodes
+  {
+    std::vector<uint64_t> keys;
+    std::vector<Tet> tt;
+    for (int d = 0; d <= J; ++d)
+      for (uint64_t p : BX[d]) {
+        if (T.split(d, p)) continue;
+        tt.clear();
+        box_tets(T, d, p, J, tt);
+        for (auto& t : tt)
+          for (int k = 0; k < 4; ++k)
+            if (!bnd3(T, t[k])) keys.push_back(t[k]);
+      }
+    uniq(keys);
+    out.aux_key = std::move(keys);
+  }
+  const std::vector<uint64_t>& AK = out.aux_key;
+
+  // per level: changed boxes at depth l-1, new nodes and their two parents
+  out.nlevel.assign(J + 1, 0);
+  std::vector<std::vector<uint64_t>> changed(J + 1);
+  std::vector<std::vector<std::array<uint64_t, 3>>> newnodes(J + 1);
+  for (int l = 1; l <= J; ++l) {
+    const int d = l - 1;
+    const uint64_t s = 1ULL << (T.LB - d), h = s / 2;
+    std::vector<std::array<uint64_t, 3>> nn;
+    for (uint64_t p : BX[d]) {
+      const bool sp = T.split(d, p);
+      BoxShape sh = shape(T, d, p, l);
+      if (!sp && !sh.hang) continue;
+      changed[l].push_back(p);
+      uint64_t c[3];
+      um3(p, c);
+      auto pt = [&](int u0, int u1, int u2) { return m3(c[0] * s + u0 * h, c[1] * s + u1 * h, c[2] * s + u2 * h); };
+      nn.push_back({pt(1, 1, 1), pt(0, 0, 0), pt(2, 2, 2)});  // centre: midpoint of the main diagonal
+      for (int a = 0; a < 3; ++a) {
+        const int b = a == 0 ? 1 : 0, cc = a == 2 ? 1 : 2;
+        for (int sd = 0; sd < 2; ++sd) {
+          auto fp = [&](int ub, int uc) {
+            int u[3];
+            u[a] = 2 * sd;
+            u[b] = ub;
+            u[cc] = uc;
+            return pt(u[0], u[1], u[2]);
+          };
+          // face centre (midpoint of the face's min-to-max diagonal) is a node
+          // of split boxes and of fanned or subdivided faces
+          bool fan = sp || sh.fsub[a][sd] || edge_mid(T, d, p, a, sd, cc, 0) || edge_mid(T, d, p, a, sd, cc, 1) ||
+                     edge_mid(T, d, p, a, sd, b, 0) || edge_mid(T, d, p, a, sd, b, 1);
+          if (fan) nn.push_back({fp(1, 1), fp(0, 0), fp(2, 2)});
+        }
+      }
+      if (sp)
+        for (int e = 0; e < 3; ++e) {
+          const int f = (e + 1) % 3, g = (e + 2) % 3;
+          for (int sf = 0; sf < 2; ++sf)
+            for (int sg = 0; sg < 2; ++sg) {
+              int u0[3], u1[3], um[3];
+              u0[e] = 0;
+              u1[e] = 2;
+              um[e] = 1;
+              u0[f] = u1[f] = um[f] = 2 * sf;
+              u0[g] = u1[g] = um[g] = 2 * sg;
+              nn.push_back({pt(um[0], um[1], um[2]), pt(u0[0], u0[1], u0[2]), pt(u1[0], u1[1], u1[2])});
+            }
+        }
+    }
+    std::sort(nn.begin(), nn.end());
+    nn.erase(std::unique(nn.begin(), nn.end(),
+                         [](const std::array<uint64_t, 3>& x, const std::array<uint64_t, 3>& y) { return x[0] == y[0]; }),
+             nn.end());
+    int64_t nf = 0;
+    for (auto& v : nn)
+      if (!bnd3(T, v[0])) ++nf;
+    out.nlevel[l] = out.nlevel[l - 1] + nf;
+    newnodes[l] = std::move(nn);
+  }
+  out.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  const int c = out.c;
+
+  // tetrahedra of every leaf box at the finest level: ftet[first[d][i] ..
+  // first[d][i] + nft[d][i]) for leaf i of depth d (first = -1: split box)
+  std::vector<Tet> ftet;
+  std::vector<std::vector<int64_t>> first(J + 1);
+  std::vector<std::vector<uint8_t>> nft(J + 1);
+  for (int d = 0; d <= J; ++d) {
+    first[d].assign(BX[d].size(), -1);
+    nft[d].assign(BX[d].size(), 0);
+    for (size_t i = 0; i < BX[d].size(); ++i) {
+      if (T.split(d, BX[d][i])) continue;
+      first[d][i] = (int64_t)ftet.size();
+      box_tets(T, d, BX[d][i], J, ftet);
+      nft[d][i] = (uint8_t)(ftet.size() - first[d][i]);
+    }
+  }
+  const double lat_scale = std::ldexp(1.0, T.LB) / tree.L;
+  // lattice window holding a fine tetrahedron's bounding box (widened by
+  // 1e-9 lattice units against rounding of the scaling)
+  auto window = [&](const TetP& S, int64_t* lo, int64_t* hi) {
+    for (int k = 0; k < 3; ++k) {
+      double mn = S[0][k], mx = S[0][k];
+      for (int v = 1; v < 4; ++v) {
+        mn = std::min(mn, S[v][k]);
+        mx = std::max(mx, S[v][k]);
+      }
+      lo[k] = (int64_t)std::floor((mn - tree.amin[k]) * lat_scale - 1e-9);
+      hi[k] = (int64_t)std::ceil((mx - tree.amin[k]) * lat_scale + 1e-9);
+    }
+  };
+  auto fine_tet = [&](int64_t e, TetP& S) {
+    for (int v = 0; v < 4; ++v)
+      for (int k = 0; k < 3; ++k) S[v][k] = mesh.X[(int64_t)mesh.E[4 * e + v] * 3 + k];
+  };
+  auto leaf_tet = [&](int64_t q, TetP& K) {
+    for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, ftet[q][v], K[v].data());
+  };
+  auto leaf_range = [&](const std::pair<int, uint64_t>& lf, int64_t& f0, int& nq) {
+    const auto& bx = BX[lf.first];
+    const size_t bi = std::lower_bound(bx.begin(), bx.end(), lf.second) - bx.begin();
+    f0 = first[lf.first][bi];
+    nq = nft[lf.first][bi];
+  };
+
+  // element coefficients: integrals of a over the 6 Kuhn tetrahedra of every
+  // box (bottom-up) and over the fan tetrahedra of fanned leaves
+  const bool varcoef = !mesh.coeff.empty();
+  std::vector<std::vector<std::array<double, 6>>> kint(J + 1);
+  std::unordered_map<uint64_t, double> fanint;  // keyed by the sorted tet's hash below
+  auto tet_hash = [](Tet t) {
+    std::sort(t.begin(), t.end());
+    uint64_t hsh = 1469598103934665603ULL;
+    for (auto v : t) hsh = (hsh ^ v) * 1099511628211ULL;
+    return hsh;
+  };
+  if (varcoef) {
+    // elements in Morton order of their lowest corner, in chunks of 4096;
+    // each chunk sums its overlaps per leaf tetrahedron, and the chunk sums
+    // are added in chunk order (deterministic for any thread count)
+    std::vector<std::pair<uint64_t, int32_t>> order(mesh.ne);
+    for (int64_t e = 0; e < mesh.ne; ++e) {
+      TetP S;
+      fine_tet(e, S);
+      uint64_t q[3];
+      for (int k = 0; k < 3; ++k) {
+        double mn = std::min(std::min(S[0][k], S[1][k]), std::min(S[2][k], S[3][k]));
+        double u = std::floor((mn - tree.amin[k]) * lat_scale);
+        q[k] = (uint64_t)std::min(std::max(u, 0.0), std::ldexp(1.0, T.LB) - 1);
+      }
+      order[e] = {m3(q[0], q[1], q[2]), (int32_t)e};
+    }
+    std::sort(order.begin(), order.end());
+    const int64_t CH = 4096, nch = (mesh.ne + CH - 1) / CH;
+    std::vector<std::vector<std::pair<int64_t, double>>> csum(nch);
+    std::atomic<int64_t> nextc(0);
+    auto work = [&]() {
+      std::vector<std::pair<int, uint64_t>> lv, st;
+      std::vector<TetP> pieces, scratch;
+      std::vector<std::pair<int64_t, double>> acc;
+      for (;;) {
+        const int64_t ch = nextc.fetch_add(1);
+        if (ch >= nch) return;
+        acc.clear();
+        for (int64_t k = ch * CH; k < std::min(mesh.ne, (ch + 1) * CH); ++k) {
+          const int64_t e = order[k].second;
+          TetP S;
+          fine_tet(e, S);
+          int64_t lo[3], hi[3];
+          window(S, lo, hi);
+          lv.clear();
+          leaves_in(T, lo, hi, lv, st);
+          for (auto& lf : lv) {
+            int64_t f0;
+            int nq;
+            leaf_range(lf, f0, nq);
+            for (int q = 0; q < nq; ++q) {
+              TetP K;
+              leaf_tet(f0 + q, K);
+              clip_tets(S, K, pieces, scratch);
+              double vol = 0;
+              for (auto& pc : pieces) vol += std::fabs(vol6(pc[0], pc[1], pc[2], pc[3])) / 6.0;
+              if (vol > 0) acc.push_back({f0 + q, vol * mesh.coeff[e]});
+            }
+          }
+        }
+        std::stable_sort(acc.begin(), acc.end(),
+                         [](const std::pair<int64_t, double>& x, const std::pair<int64_t, double>& y) {
+                           return x.first < y.first;
+                         });
+        auto& out = csum[ch];
+        for (size_t i = 0; i < acc.size();) {
+          size_t j = i;
+          double sum = 0;
+          while (j < acc.size() && acc[j].first == acc[i].first) sum += acc[j++].second;
+          out.push_back({acc[i].first, sum});
+          i = j;
+        }
+      }
+    };
+    {
+      unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < nt; ++t) th.emplace_back(work);
+      for (auto& x : th) x.join();
+    }
+    std::vector<double> I(ftet.size(), 0.0);
+    for (auto& v : csum)
+      for (auto& pr : v) I[pr.first] += pr.second;
+    csum.clear();
+    // bottom-up Kuhn integrals
+    for (int d = J; d >= 0; --d) {
+      kint[d].assign(BX[d].size(), {0, 0, 0, 0, 0, 0});
+      const uint64_t s = 1ULL << (T.LB - d);
+      for (size_t i = 0; i < BX[d].size(); ++i) {
+        const uint64_t p = BX[d][i];
+        uint64_t cb[3];
+        um3(p, cb);
+        auto local_kuhn = [&](const Tet& t) {  // Kuhn index of t's centroid in this box
+          double u[3] = {0, 0, 0};
+          for (int v = 0; v < 4; ++v) {
+            uint64_t q[3];
+            um3(t[v], q);
+            for (int k = 0; k < 3; ++k) u[k] += ((double)q[k] - (double)(cb[k] * s)) / (4.0 * (double)s);
+          }
+          return kuhn_index(u);
+        };
+        if (!T.split(d, p)) {
+          const int64_t f0 = first[d][i];
+          const int nq = nft[d][i];
+          const bool kuhn = nq == 6;  // a coned box has at least 12 tetrahedra
+          for (int q = 0; q < nq; ++q) {
+            kint[d][i][local_kuhn(ftet[f0 + q])] += I[f0 + q];
+            if (!kuhn) fanint[tet_hash(ftet[f0 + q])] = I[f0 + q];
+          }
+        } else {
+          const auto& ch = BX[d + 1];
+          const size_t j = std::lower_bound(ch.begin(), ch.end(), p << 3) - ch.begin();
+          for (int cidx = 0; cidx < 8; ++cidx) {
+            const uint64_t cp = ch[j + cidx];
+            std::vector<Tet> kt;
+            box_tets(T, d + 1, cp, d + 1, kt);  // the child's 6 Kuhn tetrahedra
+            for (int q = 0; q < 6; ++q) kint[d][i][local_kuhn(kt[q])] += kint[d + 1][j + cidx][q];
+          }
+        }
+      }
+    }
+  }
+  auto tet_coef = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> double {
+    if (!varcoef) return 1.0;
+    double P[4][3];
+    for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, t[v], P[v]);
+    V3 a = {P[0][0], P[0][1], P[0][2]}, b = {P[1][0], P[1][1], P[1][2]}, cc = {P[2][0], P[2][1], P[2][2]},
+       dd = {P[3][0], P[3][1], P[3][2]};
+    const double vol = std::fabs(vol6(a, b, cc, dd)) / 6.0;
+    if (kuhn) {
+      const auto& bx = BX[d];
+      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      return kint[d][i][q] / vol;
+    }
+    return fanint.at(tet_hash(t)) / vol;
+  };
+
+  auto emit_box = [&](int d, uint64_t p, int l, std::vector<int32_t>& ids, std::vector<uint64_t>& keys,
+                      std::vector<double>& coef) {
+    std::vector<Tet> kt;
+    bool kuhn = false;
+    box_tets(T, d, p, l, kt, &kuhn);
+    for (size_t q = 0; q < kt.size(); ++q) {
+      for (int v = 0; v < 4; ++v) {
+        keys.push_back(kt[q][v]);
+        ids.push_back(bnd3(T, kt[q][v]) ? -1 : idx_of(AK, kt[q][v]));
+      }
+      coef.push_back(tet_coef(d, p, kuhn, (int)q, kt[q]));
+    }
+  };
+
+  // coarsest level
+  for (int d = 0; d <= c; ++d)
+    for (uint64_t p : BX[d]) {
+      if (d < c && T.split(d, p)) continue;
+      emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef);
+    }
+  for (auto id : out.coarse_tri_id)
+    if (id >= 0) out.coarse_id.push_back(id);
+  std::sort(out.coarse_id.begin(), out.coarse_id.end());
+  out.coarse_id.erase(std::unique(out.coarse_id.begin(), out.coarse_id.end()), out.coarse_id.end());
+
+  // levels c+1..J
+  out.levels.assign(std::max(0, J - c), AuxLevelHost());
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    for (;;) {
+      const int l = c + 1 + next.fetch_add(1);
+      if (l > J) return;
+      AuxLevelHost& L = out.levels[l - (c + 1)];
+      L.level = l;
+      const int d = l - 1;
+      std::vector<std::pair<int, uint64_t>> rel;
+      if (prm.smoothing == 1) {
+        for (int dd = 0; dd <= l; ++dd)
+          for (uint64_t p : BX[dd])
+            if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
+      } else {
+        for (uint64_t p : changed[l]) {
+          if (T.split(d, p)) {
+            for (uint64_t ch = 0; ch < 8; ++ch) rel.push_back({d + 1, (p << 3) | ch});
+          } else {
+            rel.push_back({d, p});
+          }
+          for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+              for (int ox = -1; ox <= 1; ++ox) {
+                if (!ox && !oy && !oz) continue;
+                int o[3] = {ox, oy, oz};
+                uint64_t q;
+                if (!T.offset(d, p, o, q)) continue;
+                int dd = d;
+                while (!T.exists(dd, q)) {
+                  --dd;
+                  q >>= 3;
+                }
+                if (dd == d && T.split(d, q)) {
+                  for (uint64_t ch = 0; ch < 8; ++ch) rel.push_back({d + 1, (q << 3) | ch});
+                } else {
+                  rel.push_back({dd, q});
+                }
+              }
+        }
+      }
+      std::sort(rel.begin(), rel.end());
+      rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+      // smoothing set: vertices of the level-l tetrahedra of the changed boxes
+      std::vector<uint64_t> sm;
+      if (prm.smoothing == 1) {
+        for (auto& b : rel) {
+          std::vector<Tet> kt;
+          box_tets(T, b.first, b.second, l, kt);
+          for (auto& t : kt)
+            for (int v = 0; v < 4; ++v)
+              if (!bnd3(T, t[v])) sm.push_back(t[v]);
+        }
+      } else {
+        for (uint64_t p : changed[l]) {
+          std::vector<Tet> kt;
+          if (T.split(d, p)) {
+            for (uint64_t ch = 0; ch < 8; ++ch) box_tets(T, d + 1, (p << 3) | ch, l, kt);
+          } else {
+            box_tets(T, d, p, l, kt);
+          }
+          for (auto& t : kt)
+            for (int v = 0; v < 4; ++v)
+              if (!bnd3(T, t[v])) sm.push_back(t[v]);
+        }
+      }
+      uniq(sm);
+      for (uint64_t k : sm) L.smooth.push_back(idx_of(AK, k));
+      for (auto& b : rel) emit_box(b.first, b.second, l, L.tri_id, L.tri_key, L.tri_coef);
+      for (auto& v : newnodes[l]) {
+        if (bnd3(T, v[0])) continue;
+        L.new_id.push_back(idx_of(AK, v[0]));
+        L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
+        L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
+      }
+    }
+  };
+  {
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(worker);
+    for (auto& x : th) x.join();
+  }
+
+  // Scott-Zhang (Sec. 4.1) in 3D: psi_i = (20 lambda_i - 4)/|sigma_i|
+  std::vector<int32_t> sigma(mesh.nv, -1);
+  for (int64_t e = mesh.ne - 1; e >= 0; --e)
+    for (int k = 0; k < 4; ++k) sigma[mesh.E[4 * e + k]] = (int32_t)e;
+  std::vector<int32_t> vert_of_free;
+  for (int64_t v = 0; v < mesh.nv; ++v)
+    if (free_of_vertex[v] >= 0) vert_of_free.push_back((int32_t)v);
+  const int64_t n = (int64_t)vert_of_free.size();
+  unsigned nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  if (n < 2048) nth = 1;
+  std::vector<Triplets> parts(nth);
+  {
+    std::vector<std::thread> th;
+    for (unsigned tix = 0; tix < nth; ++tix)
+      th.emplace_back([&, tix] {
+        Triplets& mine = parts[tix];
+        std::vector<std::pair<int, uint64_t>> lv, st;
+        std::vector<TetP> pieces, scratch;
+        std::vector<std::pair<int32_t, double>> row;
+        const int64_t b0 = n * tix / nth, b1 = n * (tix + 1) / nth;
+        for (int64_t i = b0; i < b1; ++i) {
+          const int32_t v = vert_of_free[i];
+          const int32_t e = sigma[v];
+          TetP S;
+          fine_tet(e, S);
+          int loc = 0;
+          for (int k = 0; k < 4; ++k)
+            if (mesh.E[4 * (int64_t)e + k] == v) loc = k;
+          int64_t lo[3], hi[3];
+          window(S, lo, hi);
+          const double vol = std::fabs(vol6(S[0], S[1], S[2], S[3])) / 6.0;
+          Aff lam = bary(S, loc), psi;
+          psi.c0 = (20.0 * lam.c0 - 4.0) / vol;
+          for (int r = 0; r < 3; ++r) psi.g[r] = 20.0 * lam.g[r] / vol;
+          lv.clear();
+          leaves_in(T, lo, hi, lv, st);
+          row.clear();
+          for (auto& lf : lv) {
+            int64_t f0;
+            int nq;
+            leaf_range(lf, f0, nq);
+            for (int q = 0; q < nq; ++q) {
+              TetP K;
+              leaf_tet(f0 + q, K);
+              clip_tets(S, K, pieces, scratch);
+              if (pieces.empty()) continue;
+              for (int w = 0; w < 4; ++w) {
+                const uint64_t key = ftet[f0 + q][w];
+                if (bnd3(T, key)) continue;
+                Aff phi = bary(K, w);
+                double val = 0;
+                for (auto& pc : pieces) val += prod4(pc, psi, phi);
+                row.push_back({idx_of(AK, key), val});
+              }
+            }
+          }
+          std::stable_sort(row.begin(), row.end(),
+                           [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                             return x.first < y.first;
+                           });
+          for (size_t k = 0; k < row.size();) {
+            size_t j = k;
+            double sum = 0;
+            while (j < row.size() && row[j].first == row[k].first) sum += row[j++].second;
+            mine.r.push_back((int32_t)i);
+            mine.c.push_back(row[k].first);
+            mine.v.push_back(sum);
+            k = j;
+          }
+        }
+      });
+    for (auto& x : th) x.join();
+  }
+  for (auto& p : parts) {
+    out.P.r.insert(out.P.r.end(), p.r.begin(), p.r.end());
+    out.P.c.insert(out.P.c.end(), p.c.begin(), p.c.end());
+    out.P.v.insert(out.P.v.end(), p.v.begin(), p.v.end());
+  }
+}
+
+}  // namespace asmg

@@ -271,8 +271,14 @@ struct TriDev {
 
 void upload_tris(const asmg_s& h, const std::vector<uint64_t>& keys, const std::vector<int32_t>& ids,
                  const std::vector<double>& coef, TriDev& T, cudaStream_t s) {
-  std::vector<double> xy(keys.size() * 2);
-  for (size_t k = 0; k < keys.size(); ++k) lattice_point(h.tree, keys[k], &xy[2 * k]);
+  const int dim = h.mesh.dim;
+  std::vector<double> xy(keys.size() * dim);
+  for (size_t k = 0; k < keys.size(); ++k) {
+    if (dim == 2)
+      lattice_point(h.tree, keys[k], &xy[2 * k]);
+    else
+      lattice_point3(h.tree, h.aux.LB, keys[k], &xy[3 * k]);
+  }
   T.xy.upload(xy, s);
   T.id.upload(ids, s);
   T.coef.upload(coef, s);
@@ -330,7 +336,7 @@ void build_all(asmg_s& h, cudaStream_t s) {
   h.n = (int64_t)h.vertex_of_free.size();
   if (h.n == 0) ASMG_FAIL(ASMG_ERR_BAD_MESH, "no free vertices");
   h.d_free_of_vertex.upload(h.free_of_vertex, s);
-  h.A_host = assemble_mesh(ne, h.dX.p, h.dE.p, h.d_free_of_vertex.p, h.dCoeff.p, h.n, s);
+  h.A_host = assemble_mesh(m.dim, ne, h.dX.p, h.dE.p, h.d_free_of_vertex.p, h.dCoeff.p, h.n, s);
   {
     std::vector<uint8_t> all(h.n, 1);
     std::vector<uint64_t> pk(h.vertex_of_free.begin(), h.vertex_of_free.end());
@@ -380,7 +386,10 @@ void build_all(asmg_s& h, cudaStream_t s) {
   // ---- auxiliary hierarchy (host), transfer
   double t1 = now();
   h.aux = AuxHost();
-  build_aux_host(m, h.tree, h.prm, h.free_of_vertex, h.aux);
+  if (m.dim == 2)
+    build_aux_host(m, h.tree, h.prm, h.free_of_vertex, h.aux);
+  else
+    build_aux_host3(m, h.tree, h.prm, h.free_of_vertex, h.aux);
   h.stats.t_aux = now() - t1;
   double t2 = now();
   h.nJ = (int64_t)h.aux.aux_key.size();
@@ -399,7 +408,7 @@ void build_all(asmg_s& h, cudaStream_t s) {
     upload_tris(h, L.tri_key, L.tri_id, L.tri_coef, T, s);
     DBuf<uint8_t> dkeep;
     dkeep.upload(inset, s);
-    HostCSR Arows = assemble_triangles((int64_t)L.tri_coef.size(), T.xy.p, T.id.p, T.coef.p, dkeep.p, h.nJ, s);
+    HostCSR Arows = assemble_simplices(m.dim, (int64_t)L.tri_coef.size(), T.xy.p, T.id.p, T.coef.p, dkeep.p, h.nJ, s);
     std::vector<int32_t> colour = jp_colour_gpu(Arows, inset, h.aux.aux_key, s);
     // export copies
     std::vector<uint64_t> sk;
@@ -438,7 +447,8 @@ void build_all(asmg_s& h, cudaStream_t s) {
     }
     TriDev T;
     upload_tris(h, h.aux.coarse_tri_key, loc, h.aux.coarse_tri_coef, T, s);
-    HostCSR Ac = assemble_triangles((int64_t)h.aux.coarse_tri_coef.size(), T.xy.p, T.id.p, T.coef.p, nullptr, h.nc, s);
+    HostCSR Ac = assemble_simplices(m.dim, (int64_t)h.aux.coarse_tri_coef.size(), T.xy.p, T.id.p, T.coef.p, nullptr,
+                                    h.nc, s);
     const int64_t n = h.nc;
     std::vector<double> M(n * n, 0.0);
     for (int64_t i = 0; i < n; ++i)
@@ -563,8 +573,9 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   *out = nullptr;
   if (!vertices || !elements || !boundary) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null input array");
   if (nv <= 0 || ne <= 0) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "nv and ne must be positive");
-  if (dim != 2) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "dim %d not supported (2D triangles only)", dim);
-  if (ne > (1LL << 31) / 9 || nv > (1LL << 31) - 1) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "mesh too large");
+  if (dim != 2 && dim != 3) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "dim %d not supported (2 or 3)", dim);
+  if (ne > (1LL << 31) / ((dim + 1) * (dim + 1)) || nv > (1LL << 31) - 1)
+    ASMG_FAIL(ASMG_ERR_INVALID_ARG, "mesh too large");
   asmg_params prm;
   asmg_default_params(&prm);
   if (params) prm = *params;
@@ -598,18 +609,29 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   double tt = now();
   build_tree_gpu(dim, nv, h->dX.p, ne, h->dE.p, prm.n_min, s, h->tree);
   h->stats.t_tree = now() - tt;
-  // the domain must fill the root box (box domains only)
+  // the domain must fill the root box (box domains only): the element
+  // measures add up to L^dim
   {
-    double area = 0;
+    double meas = 0;
     for (int64_t e = 0; e < ne; ++e) {
-      const int32_t* v = &m.E[3 * e];
-      area += 0.5 * ((m.X[2 * v[1]] - m.X[2 * v[0]]) * (m.X[2 * v[2] + 1] - m.X[2 * v[0] + 1]) -
-                     (m.X[2 * v[2]] - m.X[2 * v[0]]) * (m.X[2 * v[1] + 1] - m.X[2 * v[0] + 1]));
+      const int32_t* v = &m.E[(dim + 1) * e];
+      if (dim == 2) {
+        meas += 0.5 * ((m.X[2 * v[1]] - m.X[2 * v[0]]) * (m.X[2 * v[2] + 1] - m.X[2 * v[0] + 1]) -
+                       (m.X[2 * v[2]] - m.X[2 * v[0]]) * (m.X[2 * v[1] + 1] - m.X[2 * v[0] + 1]));
+      } else {
+        double e3[3][3];
+        for (int k = 0; k < 3; ++k)
+          for (int r = 0; r < 3; ++r) e3[k][r] = m.X[3 * (int64_t)v[k + 1] + r] - m.X[3 * (int64_t)v[0] + r];
+        meas += (e3[0][0] * (e3[1][1] * e3[2][2] - e3[1][2] * e3[2][1]) -
+                 e3[0][1] * (e3[1][0] * e3[2][2] - e3[1][2] * e3[2][0]) +
+                 e3[0][2] * (e3[1][0] * e3[2][1] - e3[1][1] * e3[2][0])) /
+                6.0;
+      }
     }
-    double box = h->tree.L * h->tree.L;
-    if (std::fabs(area - box) > 1e-12 * box)
-      ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "the domain is not the square spanned by the vertices (area %.17g vs %.17g)", area,
-                box);
+    const double box = std::pow(h->tree.L, dim);
+    if (std::fabs(meas - box) > 1e-11 * box)
+      ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "the domain is not the %s spanned by the vertices (measure %.17g vs %.17g)",
+                dim == 2 ? "square" : "cube", meas, box);
   }
   build_all(*h, s);
   h->bytes_iter = prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
@@ -799,7 +821,7 @@ int amg_mass_apply(asmg_handle h, const double* f, double* bout, void* stream) {
   Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
   copy_in(S0.vb.p, f, nv, s);
-  mass_apply_gpu(h->mesh.ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, nv, s);
+  mass_apply_gpu(h->mesh.dim, h->mesh.ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, nv, s);
   gather_rows(*h, S0.vu.p, S0.q.p, s);
   scatter_rows(*h, S0.q.p, false, S0.vu.p, s);  // zero at Dirichlet vertices
   copy_out(bout, S0.vu.p, nv, s);
@@ -863,7 +885,7 @@ int amg_element_grad(asmg_handle h, const double* u, const double* lambda, doubl
     dg.alloc(ne);
     out = dg.p;
   }
-  element_grad_gpu(ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, out, s);
+  element_grad_gpu(h->mesh.dim, ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, out, s);
   if (!dev) ASMG_CUDA(cudaMemcpyAsync(g, dg.p, 8 * ne, cudaMemcpyDeviceToHost, s));
   ASMG_CUDA(cudaStreamSynchronize(s));
   return ASMG_OK;

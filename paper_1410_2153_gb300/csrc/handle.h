@@ -115,10 +115,10 @@ void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);
 void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s);
 void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cudaStream_t s);
 // assemble.cu
-HostCSR assemble_mesh(int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree, const double* dCoef,
-                      int64_t nfree, cudaStream_t s);
-void mass_apply_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
+HostCSR assemble_mesh(int dim, int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree,
+                      const double* dCoef, int64_t nfree, cudaStream_t s);
+void mass_apply_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
                     cudaStream_t s);
-void element_grad_gpu(int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl, double* dg,
-                      cudaStream_t s);
+void element_grad_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl,
+                      double* dg, cudaStream_t s);
 }  // namespace asmg

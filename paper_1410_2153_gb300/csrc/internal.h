@@ -134,6 +134,7 @@ struct AuxLevelHost {
 
 struct AuxHost {
   int J = 0, c = 0;
+  int LB = 0;                                  // 3D: lattice bits of the node keys (J + 1)
   std::vector<std::vector<uint64_t>> split;   // closed tree: split prefixes per depth (sorted)
   std::vector<uint64_t> aux_key;               // free finest-level nodes, ascending key
   std::vector<int64_t> nlevel;                 // free nodes per level 0..J
@@ -158,8 +159,14 @@ struct MeshHost {
 void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
                     const std::vector<int32_t>& free_of_vertex, AuxHost& out);
 
-// physical coordinate of a lattice key
+// the same in 3D (octree, Kuhn / coned tetrahedral grids); tri_* arrays of
+// the levels then hold 4 keys / ids per tetrahedron
+void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
+                     const std::vector<int32_t>& free_of_vertex, AuxHost& out);
+
+// physical coordinate of a lattice key (2D: 2^D lattice; 3D: 2^LB lattice)
 void lattice_point(const TreeResult& t, uint64_t key, double* p);
+void lattice_point3(const TreeResult& t, int LB, uint64_t key, double* p);
 uint64_t lattice_key2(uint64_t x, uint64_t y);
 void lattice_xy2(uint64_t key, uint64_t& x, uint64_t& y);
 
@@ -168,10 +175,11 @@ void build_tree_gpu(int dim, int64_t nv, const double* dX, int64_t ne, const int
                     cudaStream_t s, TreeResult& out);
 
 // Assemble sum of element matrices into CSR on the device and download.
-//   dim-2 triangles given by vertex coordinates (dXY [3*ntri*2]) and row/col
-//   ids (dID [3*ntri], < 0 dropped), coefficient per triangle; entries are
-//   kept only where keep(row) || keep(col) (keep == nullptr keeps all).
-HostCSR assemble_triangles(int64_t ntri, const double* dXY, const int32_t* dID, const double* dCoef,
+//   simplices (triangles, dim 2; tetrahedra, dim 3) given by vertex
+//   coordinates (dP [(dim+1)*n*dim]) and row/col ids (dID [(dim+1)*n], < 0
+//   dropped), coefficient per simplex; entries are kept only where
+//   keep(row) || keep(col) (keep == nullptr keeps all).
+HostCSR assemble_simplices(int dim, int64_t n, const double* dP, const int32_t* dID, const double* dCoef,
                            const uint8_t* dKeep, int64_t nrows, cudaStream_t s);
 
 // Jones-Plassmann colouring of the rows in `set` (CSR adjacency over all rows,

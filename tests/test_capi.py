@@ -61,7 +61,16 @@ def _setup_code(lib, m, **kw):
 
 def test_rejections_before_any_gpu_work(lib, gen):
     m = _mesh(gen)
-    assert _setup_code(lib, m, dim=3) == lib.ASMG_ERR_UNSUPPORTED
+    assert _setup_code(lib, m, dim=4) == lib.ASMG_ERR_UNSUPPORTED
+    assert _setup_code(lib, m, dim=1) == lib.ASMG_ERR_UNSUPPORTED
+    t = gen.grid3d(3, 1)                                         # tetrahedra take the same checks
+    t.bflag = t.bflag.copy()
+    t.bflag[0] = 2
+    assert _setup_code(lib, t, dim=3) == lib.ASMG_ERR_UNSUPPORTED
+    t = gen.grid3d(3, 1)
+    t.coeff = np.ones(t.ne)
+    t.coeff[5] = 0.0
+    assert _setup_code(lib, t, dim=3) == lib.ASMG_ERR_BAD_MESH
     m2 = _mesh(gen)
     m2.bflag = m2.bflag.copy()
     m2.bflag[0] = 2
