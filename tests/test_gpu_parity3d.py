@@ -33,14 +33,18 @@ def A():
 def _meshes(gen):
     m17 = gen.grid3d(17, 3)
     m17.coeff = gen.subcube_coefficient(m17, 5, ncube=4)     # 1 / 1e3 on 4^3 subcubes
-    return {"kuhn9": gen.grid3d(9, 2), "kuhn17_jump": m17, "kuhn12": gen.grid3d(12, 6)}
+    m17b = gen.grid3d(17, 8)
+    m17b.coeff = gen.subcube_coefficient(m17b, 9, ncube=4)
+    # n_min = 6 (one cell of six Kuhn tetrahedra per leaf) is the 3D workload's setting
+    return {"kuhn9": (gen.grid3d(9, 2), {}), "kuhn17_jump": (m17, {}), "kuhn12": (gen.grid3d(12, 6), {}),
+            "kuhn17_jump_nmin6": (m17b, {"n_min": 6}), "kuhn12_nmin6": (gen.grid3d(12, 10), {"n_min": 6})}
 
 
 @pytest.fixture(scope="module")
 def cases(gen, A):
     out = {}
-    for name, m in _meshes(gen).items():
-        out[name] = (m, oracle.Oracle(m), A.Solver(m, precision=A.ASMG_FP64))
+    for name, (m, p) in _meshes(gen).items():
+        out[name] = (m, oracle.Oracle(m, **p), A.Solver(m, precision=A.ASMG_FP64, **p), p)
     return out
 
 
@@ -52,12 +56,12 @@ def _spread3(v):
     return v
 
 
-NAMES = ["kuhn9", "kuhn17_jump", "kuhn12"]
+NAMES = ["kuhn9", "kuhn17_jump", "kuhn12", "kuhn17_jump_nmin6", "kuhn12_nmin6"]
 
 
 @pytest.mark.parametrize("name", NAMES)
 def test_3d_tree_closure_aux_nodes_and_colours_bit_exact(cases, name):
-    m, o, s = cases[name]
+    m, o, s, p = cases[name]
     assert np.array_equal(s.export("keys"), o.keys())
     assert np.array_equal(s.export("perm"), o.perm())
     for d, seg in enumerate(o.tree_levels()):
@@ -83,7 +87,7 @@ def test_3d_tree_closure_aux_nodes_and_colours_bit_exact(cases, name):
 
 @pytest.mark.parametrize("name", NAMES)
 def test_3d_fine_operator_transfer_and_level_operators(cases, name):
-    m, o, s = cases[name]
+    m, o, s, p = cases[name]
     vf = o.vertex_of_free()
     pos = {int(v): i for i, v in enumerate(vf)}
     Ao = o.A().tocoo()
@@ -118,7 +122,7 @@ def test_3d_fine_operator_transfer_and_level_operators(cases, name):
 
 @pytest.mark.parametrize("name", NAMES)
 def test_3d_preconditioner_spmv_and_mass(cases, name):
-    m, o, s = cases[name]
+    m, o, s, p = cases[name]
     rng = np.random.default_rng(5)
     vf = o.vertex_of_free()
     r = np.zeros(m.nv)
@@ -138,7 +142,7 @@ def test_3d_preconditioner_spmv_and_mass(cases, name):
 
 @pytest.mark.parametrize("name", NAMES)
 def test_3d_solves_match_oracle(cases, gen, A, name):
-    m, o, s = cases[name]
+    m, o, s, p = cases[name]
     f = gen.nodal_uniform(m, 11)
     vf = o.vertex_of_free()
     b_ref = o.mass_apply(f)
@@ -149,7 +153,7 @@ def test_3d_solves_match_oracle(cases, gen, A, name):
     assert rc == A.ASMG_OK and abs(it - it_ref) <= 2, (it, it_ref)
     assert np.linalg.norm(u[vf] - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
     assert np.linalg.norm(b_ref - o.spmv(u[vf])) <= 2e-8 * np.linalg.norm(b_ref)
-    sm = A.Solver(m, precision=A.ASMG_MIXED)
+    sm = A.Solver(m, precision=A.ASMG_MIXED, **p)
     u2, rc2, it2, _ = sm.solve(sm.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
     u2 = u2.cpu().numpy()
     assert rc2 == A.ASMG_OK and abs(it2 - it_ref) <= max(2, 0.1 * it_ref), (it2, it_ref)
@@ -158,7 +162,7 @@ def test_3d_solves_match_oracle(cases, gen, A, name):
 
 
 def test_3d_element_gradient(cases):
-    m, o, s = cases["kuhn17_jump"]
+    m, o, s, p = cases["kuhn17_jump"]
     rng = np.random.default_rng(4)
     vf = o.vertex_of_free()
     u = np.zeros(m.nv)
