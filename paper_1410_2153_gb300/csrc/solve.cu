@@ -320,11 +320,38 @@ __global__ void k_coarse(int64_t nc, const int32_t* __restrict__ cid, const doub
 
 // ---------------------------------------------------- small levels, fused
 // A run of small levels in one thread block.  Per level the rhs F and the
-// correction U of the rows E_l live in shared memory; colour phases are
-// separated by __syncthreads instead of kernel boundaries.  The steps are
-// those of k_gs_aux / k_resid_aux / k_restrict_aux (down) and
-// k_prolong_aux / k_addsaved_aux / k_gs_aux (up).
+// correction U of the rows E_l, and the row pointers of its smoothing and
+// residual rows, live in shared memory; colour phases are separated by
+// __syncthreads instead of kernel boundaries.  The steps are those of
+// k_gs_aux / k_resid_aux / k_restrict_aux (down) and k_prolong_aux /
+// k_addsaved_aux / k_gs_aux (up).
 constexpr int SMALL_TPB = 1024;
+constexpr int SMALL_B = 8;  // row entries loaded in one batch
+
+template <class T>
+constexpr size_t small_smem() {
+  return 2 * SMALL_LMAX * sizeof(T) + 2 * (SMALL_LMAX + 1) * sizeof(int32_t);
+}
+
+// acc - sum_p val[p] * x[col[p]] over p0 <= p < p1, the first SMALL_B
+// entries loaded together (ascending p, as a plain loop would add them)
+template <class T>
+__device__ __forceinline__ T small_row(T acc, int p0, int p1, const T* __restrict__ val,
+                                       const uint16_t* __restrict__ col, const T* x) {
+  T v[SMALL_B];
+  uint16_t c[SMALL_B];
+#pragma unroll
+  for (int q = 0; q < SMALL_B; ++q)
+    if (p0 + q < p1) {
+      v[q] = val[p0 + q];
+      c[q] = col[p0 + q];
+    }
+#pragma unroll
+  for (int q = 0; q < SMALL_B; ++q)
+    if (p0 + q < p1) acc -= v[q] * x[c[q]];
+  for (int p = p0 + SMALL_B; p < p1; ++p) acc -= val[p] * x[col[p]];
+  return acc;
+}
 
 template <class T>
 __global__ void __launch_bounds__(SMALL_TPB, 1)
@@ -332,31 +359,32 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + SMALL_LMAX;
+  int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
+  int32_t* Prs = Psm + SMALL_LMAX + 1;
   pdl_wait();
   for (int d = 0; d < nlev; ++d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
-    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
-      const T f = F[L.gid[k]];
-      Fl[k] = f;
-      Ul[k] = 0;
-      if (k < mS) L.fs[k] = f;
+    for (int k = threadIdx.x; k <= mE; k += blockDim.x) {
+      if (k < mE) {
+        const T f = F[L.gid[k]];
+        Fl[k] = f;
+        Ul[k] = 0;
+        if (k < mS) L.fs[k] = f;
+      }
+      if (k <= mS) Psm[k] = L.sm_ptr[k];
+      Prs[k] = L.rs_ptr[k];
     }
     __syncthreads();
     for (int sw = 0; sw < nu; ++sw)
       for (int c = 0; c < L.ncol; ++c) {
         for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
-          T acc = Fl[k];
-          for (int p = L.sm_ptr[k]; p < L.sm_ptr[k + 1]; ++p) acc -= L.sm_val[p] * Ul[L.sm_col[p]];
+          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
           Ul[k] += acc * L.dinv[k];
         }
         __syncthreads();
       }
-    for (int k = threadIdx.x; k < mE; k += blockDim.x) {
-      T acc = 0;
-      for (int p = L.rs_ptr[k]; p < L.rs_ptr[k + 1]; ++p) acc += L.rs_val[p] * Ul[L.rs_col[p]];
-      Fl[k] -= acc;
-    }
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) Fl[k] = small_row(Fl[k], Prs[k], Prs[k + 1], L.rs_val, L.rs_col, Ul);
     __syncthreads();
     for (int t = threadIdx.x; t < L.npar; t += blockDim.x) {
       T acc = 0;
@@ -379,6 +407,7 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + SMALL_LMAX;
+  int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
   pdl_wait();
   for (int d = nlev - 1; d >= 0; --d) {
     const SmallDesc<T>& L = D[d];
@@ -386,7 +415,9 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
     for (int k = threadIdx.x; k < mE; k += blockDim.x) {
       Ul[k] = U[L.gid[k]];
       if (k < mS) Fl[k] = L.fs[k];
+      if (k <= mS) Psm[k] = L.sm_ptr[k];
     }
+    if (mS == mE && threadIdx.x == 0) Psm[mS] = L.sm_ptr[mS];
     __syncthreads();
     for (int t = threadIdx.x; t < L.nnew; t += blockDim.x) {
       const int32_t a = L.nn_p0[t], b = L.nn_p1[t];
@@ -401,8 +432,7 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
     for (int sw = 0; sw < nu; ++sw)
       for (int c = L.ncol - 1; c >= 0; --c) {
         for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
-          T acc = Fl[k];
-          for (int p = L.sm_ptr[k]; p < L.sm_ptr[k + 1]; ++p) acc -= L.sm_val[p] * Ul[L.sm_col[p]];
+          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
           Ul[k] += acc * L.dinv[k];
         }
         __syncthreads();
@@ -673,7 +703,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
   const int nlev = (int)P.lev.size();
   const int ndeep = P.n_deep, nbot = P.n_bottom;  // fused runs at the top and at the bottom
-  const size_t smem = 2 * SMALL_LMAX * sizeof(T);
+  const size_t smem = small_smem<T>();
   if (ndeep) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npre, true),
            launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.F.p, npre));
@@ -976,7 +1006,7 @@ void setup_small(Prec<T>& P) {
     while (nb < nlev - nd && P.lev[nb].small.ok) ++nb;
   P.n_deep = nd;
   P.n_bottom = nb;
-  const int smem = (int)(2 * SMALL_LMAX * sizeof(T));
+  const int smem = (int)small_smem<T>();
   ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
 }
