@@ -118,8 +118,8 @@ __device__ __forceinline__ void row_load(Row<T>& R, int64_t row, const int64_t* 
   for (int k = 0; k < MAXW; ++k)
     if (k < R.w) {
       const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
-      R.c[k] = __ldg(col + e);
-      R.v[k] = __ldg(val + e);
+      R.c[k] = __ldcs(col + e);
+      R.v[k] = __ldcs(val + e);
     }
 }
 
