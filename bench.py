@@ -252,6 +252,61 @@ def run_batch(args):
     asmg.amg_batch_destroy(batch)
 
 
+def run_inverse(args):
+    """Coefficient-inversion workload: 1025^2 jittered grid, a = exp(g) with g a
+    Gaussian random field; one step is the gradient of L = 1/2 ||u(a) - u_obs||^2
+    with respect to g: the forward solve, the adjoint solve and the element
+    gradient (mixed precision, rtol 1e-8)."""
+    import torch
+    from paper_1410_2153_gb300 import asmg, meshgen
+    from paper_1410_2153_gb300 import autograd as ag
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    nside = int(args.workload[7:]) if len(args.workload) > 7 else 1025
+    m, g, g_obs = meshgen.workload_inverse(seed=1, nside=nside)
+    f = meshgen.nodal_uniform(m, 31)
+    t0 = time.perf_counter()
+    cs = ag.CoefficientSolver(m, precision=asmg.ASMG_MIXED, rtol=RTOL)
+    t_setup = time.perf_counter() - t0
+    b = cs.solver.mass_apply(torch.from_numpy(f).cuda())
+    m_obs = meshgen.grid2d(nside, 1, jitter=0.2, random_diag=True)
+    m_obs.coeff = np.exp(g_obs)
+    s_obs = asmg.Solver(m_obs, precision=asmg.ASMG_FP64)
+    u_obs, rc, _, _ = s_obs.solve(b, rtol=1e-12)
+    assert rc == asmg.ASMG_OK
+    s_obs.close()
+    gd = torch.from_numpy(g).cuda()
+    n = cs.solver.info("nfree")
+
+    def step():
+        return ag.inversion_loss_and_grad(cs, gd, b, u_obs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cs.last_iterations.clear()
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss, dg, u = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    its = cs.last_iterations
+    line = {"metric": METRIC, "value": 2 * n / (ms / 1e3), "unit": "dofs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"inverse{nside}: {nside}^2 jittered random-diagonal grid, a = exp(g), g a "
+                                   f"Gaussian random field (length 0.1); step = forward solve + adjoint solve + "
+                                   f"element gradient", "nfree": n, "elements": m.ne, "rtol": RTOL,
+                       "precision": "mixed", "setup_s": t_setup,
+                       "iterations_forward_adjoint": [int(its[0]), int(its[1])] if len(its) >= 2 else its,
+                       "value_counts": "two solves per step"},
+            "ms_per_gradient": ms}
+    print(json.dumps(line), flush=True)
+    cs.solver.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +322,9 @@ def main():
     args = ap.parse_args()
     if args.workload == "batch256":
         run_batch(args)
+        return
+    if args.workload.startswith("inverse") and args.impl != "reference":
+        run_inverse(args)
         return
     if args.impl == "reference":
         run_reference(args)
