@@ -118,6 +118,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when it was taken on another workload or the kernel source has changed
+    since (git blob hash of the source file)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel") != kernel or d.get("workload") != workload:
+        return None
+    src = open(os.path.join(ROOT, d["source"]), "rb").read()
+    blob = hashlib.sha1(b"blob %d\0" % len(src) + src).hexdigest()
+    return float(d["traffic_bytes_per_launch"]) if blob == d.get("source_blob") else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -445,7 +461,8 @@ def main():
                 "d2h_bytes_per_step": 8 * mesh.nv + 8 * (it_mix + 1)},
         "gpu_launches": int(launches_per_solve) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": dom,
+                     "frac": achieved / peak, "traffic": _measured_traffic(dom, args.workload), "kernel": dom,
+                     "algorithmic_bytes_per_launch": d["bytes"] / max(d["launches"], 1),
                      "note": f"dominant kernel class by event-timed share; peak {peak_kind} (copy bandwidth)"},
         "solve_bandwidth": {"achieved_GBps": tot_bytes / (ms_step / 1e3) / 1e9, "frac": tot_bytes / (ms_step / 1e3) / 1e9 / peak,
                             "bytes_per_solve": tot_bytes, "event_timed_kernel_ms": tot_ms},
