@@ -62,6 +62,13 @@ typedef struct {
                               decomposition); 1: smooth every node of every level */
   int32_t use_graph;       /* 1: run the PCG loop as one CUDA graph with a device-side WHILE node */
   int32_t use_pdl;         /* 1: launch solve kernels with programmatic dependent launch */
+  int32_t smoother;        /* fine smoother S (Sec. 4.1): 0 Gauss-Seidel (D - L)^{-1}, multicolour;
+                              1 Jacobi D^{-1}; 0 */
+  int32_t additive;        /* 0: multiplicative B of Algorithm 1; 1: additive B = S + Pi Btilde Pi^t
+                              (eq. fasp), for use with PCG; 0 */
+  int32_t fine_sweeps;     /* smoothing steps per application of S and of S^t, 1..8; 1 */
+  int32_t iteration;       /* 0: PCG (Sec. 5.2); 1: the ASMG iteration u <- u + B (b - A u) (Sec. 5.1
+                              rates), meaningful with the multiplicative B; 0 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */

@@ -20,7 +20,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 PARAM_DEFAULTS = dict(n_min=3, nu_pre=2, nu_post=2, coarse_max=512, smoothing=0, max_iter=500,
-                      colouring=0, stage=2)
+                      colouring=0, stage=2, smoother=0, additive=0, fine_sweeps=1, iteration=0)
+PARAM_ORDER = ("n_min", "nu_pre", "nu_post", "coarse_max", "smoothing", "max_iter", "colouring", "stage",
+               "smoother", "additive", "fine_sweeps", "iteration")
 
 
 def build(force: bool = False) -> str:
@@ -76,8 +78,7 @@ class Oracle:
         self._E = np.ascontiguousarray(mesh.elems, dtype=np.int32)
         self._B = np.ascontiguousarray(mesh.bflag, dtype=np.uint8)
         self._C = None if mesh.coeff is None else np.ascontiguousarray(mesh.coeff, dtype=np.float64)
-        prm = np.array([p[k] for k in ("n_min", "nu_pre", "nu_post", "coarse_max", "smoothing", "max_iter",
-                                        "colouring", "stage")], dtype=np.int32)
+        prm = np.array([p[k] for k in PARAM_ORDER], dtype=np.int32)
         err = ctypes.create_string_buffer(512)
         h = lib.orc_create(mesh.dim, mesh.nv, _ptr(self._X), mesh.ne, _ptr(self._E), _ptr(self._B), _ptr(self._C),
                            _ptr(prm), err, 512)

@@ -136,6 +136,10 @@ uint64_t splitmix64(uint64_t x) {
 
 struct Params {
   int n_min = 3, nu_pre = 2, nu_post = 2, coarse_max = 512, smoothing = 0, max_iter = 500, colouring = 0, stage = 2;
+  int smoother = 0;     // fine smoother S: 0 Gauss-Seidel (D - L)^{-1}, 1 Jacobi D^{-1} (Sec. 4.1)
+  int additive = 0;     // 0: multiplicative (Algorithm 1); 1: additive B = S + Pi Btilde Pi^t (eq. fasp)
+  int fine_sweeps = 1;  // smoothing steps per application of S (and of S^t)
+  int iteration = 0;    // 0: PCG (Sec. 5.2); 1: the ASMG iteration u <- u + B (b - A u)
 };
 
 struct Seg {
@@ -1699,14 +1703,37 @@ void vcycle(const Oracle& o, int l, const std::vector<double>& f, std::vector<do
   for (int s = 0; s < o.prm.nu_post; ++s) gs_sweep(L.A, L.smooth, L.cstart, f.data(), u.data(), false);
 }
 
+// u <- u + S (r - A u), fine_sweeps times: Gauss-Seidel is one multicolour
+// sweep in place (forward for S, backward for S^t); Jacobi takes the whole
+// residual first and adds D^{-1} of it (S = S^t = D^{-1}).
+void fine_smooth(const Oracle& o, const double* r, double* u, bool forward) {
+  const int64_t n = o.A.nr;
+  std::vector<double> Au(n);
+  for (int m = 0; m < o.prm.fine_sweeps; ++m) {
+    if (o.prm.smoother == 0) {
+      gs_sweep(o.A, o.fine_smooth, o.fine_cstart, r, u, forward);
+    } else {
+      spmv(o.A, u, Au.data());
+      for (int64_t i = 0; i < n; ++i) u[i] += (r[i] - Au[i]) / o.A.get(i, (int32_t)i);
+    }
+  }
+}
+
+// One application z = B r.
+//   multiplicative (Algorithm 1):  u1 = S r;  u2 = u1 + Pi Btilde Pi^t (r - A u1);
+//                                  z = u2 + S^t (r - A u2)
+//   additive (eq. fasp):           z = S r + Pi Btilde Pi^t r
+// with Btilde the V-cycle of Algorithm 2 on the auxiliary hierarchy.
 void precond(const Oracle& o, const double* r, double* z) {
   const int64_t n = o.A.nr;
   std::vector<double> u(n, 0.0), Au(n), rho(n);
-  // (1) u1 = S r : one forward multicolour sweep from zero
-  gs_sweep(o.A, o.fine_smooth, o.fine_cstart, r, u.data(), true);
-  // (2) u2 = u1 + P Btilde P^T (r - A u1)
-  spmv(o.A, u.data(), Au.data());
-  for (int64_t i = 0; i < n; ++i) rho[i] = r[i] - Au[i];
+  fine_smooth(o, r, u.data(), true);
+  if (o.prm.additive) {
+    for (int64_t i = 0; i < n; ++i) rho[i] = r[i];
+  } else {
+    spmv(o.A, u.data(), Au.data());
+    for (int64_t i = 0; i < n; ++i) rho[i] = r[i] - Au[i];
+  }
   const int64_t nJ = o.lv[o.J].key.size();
   if (nJ > 0) {
     std::vector<double> fJ(nJ, 0.0), eJ;
@@ -1719,9 +1746,39 @@ void precond(const Oracle& o, const double* r, double* z) {
       u[i] += s;
     }
   }
-  // (3) u3 = u2 + S^T (r - A u2) : one backward multicolour sweep
-  gs_sweep(o.A, o.fine_smooth, o.fine_cstart, r, u.data(), false);
+  if (!o.prm.additive) fine_smooth(o, r, u.data(), false);
   for (int64_t i = 0; i < n; ++i) z[i] = u[i];
+}
+
+// The ASMG iteration as a solver (Sec. 5.1, "convergence rates for the ASMG
+// iteration"): u <- u + B (b - A u) until ||b - A u|| <= rtol ||b||.
+// Returns 0 converged, 1 not converged, -4 on a non-finite residual.
+int asmg_iteration(const Oracle& o, const double* b, double* u, double rtol, int* iters, double* hist) {
+  const int64_t n = o.A.nr;
+  std::vector<double> bb(b, b + n), x(u, u + n), r(n), z(n), Ax(n);
+  const double nb = std::sqrt(dot(bb, bb));
+  int status = 1;
+  *iters = 0;
+  for (int k = 0;; ++k) {
+    spmv(o.A, x.data(), Ax.data());
+    for (int64_t i = 0; i < n; ++i) r[i] = bb[i] - Ax[i];
+    const double nr = std::sqrt(dot(r, r));
+    hist[k] = nr;
+    *iters = k;
+    if (!std::isfinite(nr)) {
+      status = -4;
+      break;
+    }
+    if (nr <= rtol * nb) {
+      status = 0;
+      break;
+    }
+    if (k == o.prm.max_iter) break;
+    precond(o, r.data(), z.data());
+    for (int64_t i = 0; i < n; ++i) x[i] += z[i];
+  }
+  for (int64_t i = 0; i < n; ++i) u[i] = x[i];
+  return status;
 }
 
 // PCG with the flexible beta (R9); returns 0 converged, 1 not converged,
@@ -1801,6 +1858,10 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     o->prm.max_iter = params[5];
     o->prm.colouring = params[6];
     o->prm.stage = params[7];
+    o->prm.smoother = params[8];
+    o->prm.additive = params[9];
+    o->prm.fine_sweeps = params[10];
+    o->prm.iteration = params[11];
   }
   if (o->prm.stage >= 0) assemble_fine(*o);  // stage -1: cluster tree only
   build_tree(*o);
@@ -1938,7 +1999,8 @@ void orc_gs_sweep(void* h, const double* f, double* u, int forward) {
 }
 
 int orc_solve(void* h, const double* b, double* u, double rtol, int* iters, double* hist) {
-  return pcg(*(Oracle*)h, b, u, rtol, iters, hist);
+  Oracle& o = *(Oracle*)h;
+  return o.prm.iteration ? asmg_iteration(o, b, u, rtol, iters, hist) : pcg(o, b, u, rtol, iters, hist);
 }
 
 // dL/da_e = -lambda_e^T K_e^(1) u_e, with u, lambda given on free nodes

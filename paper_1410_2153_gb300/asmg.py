@@ -38,7 +38,9 @@ EXPORT = dict(keys=0, perm=1, seg=2, split=3, aux_keys=4, fine_colour=5, smooth=
 class asmg_params(ctypes.Structure):
     _fields_ = [("n_min", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("coarse_max_dofs", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
-                ("smoothing", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("use_pdl", ctypes.c_int32)]
+                ("smoothing", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("use_pdl", ctypes.c_int32),
+                ("smoother", ctypes.c_int32), ("additive", ctypes.c_int32), ("fine_sweeps", ctypes.c_int32),
+                ("iteration", ctypes.c_int32)]
 
 
 class AsmgError(RuntimeError):

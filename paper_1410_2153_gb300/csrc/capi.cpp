@@ -563,6 +563,10 @@ int asmg_default_params(asmg_params* p) {
   p->smoothing = 0;
   p->use_graph = 1;
   p->use_pdl = 1;
+  p->smoother = 0;
+  p->additive = 0;
+  p->fine_sweeps = 1;
+  p->iteration = 0;
   return ASMG_OK;
 }
 
@@ -581,7 +585,9 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   if (params) prm = *params;
   if (prm.n_min < 1 || prm.nu_pre < 1 || prm.nu_post < 0 || prm.coarse_max_dofs < 1 || prm.max_iter < 1 ||
       (prm.precision != ASMG_FP64 && prm.precision != ASMG_MIXED) || (prm.smoothing != 0 && prm.smoothing != 1) ||
-      prm.coarse_max_dofs > 8192 || (prm.use_pdl != 0 && prm.use_pdl != 1) || (prm.use_graph != 0 && prm.use_graph != 1))
+      prm.coarse_max_dofs > 8192 || (prm.use_pdl != 0 && prm.use_pdl != 1) || (prm.use_graph != 0 && prm.use_graph != 1) ||
+      (prm.smoother != 0 && prm.smoother != 1) || (prm.additive != 0 && prm.additive != 1) || prm.fine_sweeps < 1 ||
+      prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1))
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();

@@ -202,6 +202,37 @@ __global__ void k_prolong_fine(int64_t n, const int64_t* __restrict__ off, const
   pdl_trigger();
 }
 
+// Jacobi smoother (S = D^{-1}): first step from zero, u = D^{-1} r
+template <class T>
+__global__ void k_jac_first(int64_t n, const T* __restrict__ dinv, const double* __restrict__ r, T* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = i < n;
+  const T di = act ? dinv[i] : (T)0;
+  pdl_wait();
+  if (act) u[i] = di * (T)r[i];
+  pdl_trigger();
+}
+
+// a further Jacobi step, u += D^{-1} rho with rho = r - A u taken before
+template <class T>
+__global__ void k_jac_add(int64_t n, const T* __restrict__ dinv, const T* __restrict__ rho, T* __restrict__ u) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = i < n;
+  const T di = act ? dinv[i] : (T)0;
+  pdl_wait();
+  if (act) u[i] += di * rho[i];
+  pdl_trigger();
+}
+
+// additive form: the auxiliary correction acts on r itself (rho = r)
+template <class T>
+__global__ void k_cast_fine(int64_t n, const double* __restrict__ r, T* __restrict__ rho) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  pdl_wait();
+  if (i < n) rho[i] = (T)r[i];
+  pdl_trigger();
+}
+
 // ------------------------------------------------------ auxiliary levels
 // one colour of a sweep on the smoothing rows of a level
 template <class T>
@@ -598,6 +629,38 @@ __global__ void k_axpy_norm(int64_t n, const double* __restrict__ p, const doubl
   }
 }
 
+// ASMG iteration: x += z
+template <class T>
+__global__ void k_xpz(int64_t n, const T* __restrict__ z, double* __restrict__ x) {
+  pdl_wait();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)z[i];
+  pdl_trigger();
+}
+
+// ASMG iteration: r = b - A x, ||r||  ->  history, stopping test
+__global__ void k_iter_resid(int64_t n, SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
+                             double* __restrict__ r, double* partial, unsigned int* ticket, PcgScalars* sc, double* hist,
+                             cudaGraphConditionalHandle hnd, int use_hnd) {
+  pdl_wait();
+  double v[1] = {0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = b[i] - sell_dot<double, double>(i, A.off, A.col, A.val, x);
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  if (grid_reduce<1>(v, partial, ticket) && threadIdx.x == 0) {
+    sc->k += 1;
+    sc->rr = v[0];
+    const double nr = sqrt(v[0]);
+    hist[sc->k] = nr;
+    const bool conv = nr <= sc->tol;
+    if (conv) sc->status = 0;
+    if (!isfinite(nr)) sc->status = ASMG_ERR_BREAKDOWN;
+    set_cond(sc, (!conv && sc->k < sc->maxit && isfinite(nr)) ? 1 : 0, hnd, use_hnd);
+  }
+}
+
 __global__ void k_gather(int64_t n, const int32_t* __restrict__ vrow, const double* __restrict__ src,
                          double* __restrict__ dst) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -786,21 +849,51 @@ int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
   const SellView<T> A = fine_smoother<T>(h);
   const T* dinv = fine_dinv<T>(h);
   const int64_t sz = sizeof(T), n = h.n, nJ = h.nJ;
+  const bool jacobi = h.prm.smoother == 1, additive = h.prm.additive == 1;
   int launches = 0;
   ASMG_CUDA(cudaMemsetAsync(SP.uf.p, 0, sizeof(T) * h.npad, s));
   const int ncol = (int)h.fine_cstart.size() - 1;
-  // (1) u1 = S r: forward multicolour sweep from zero
-  for (int c = 0; c < ncol; ++c) {
-    int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
-    if (!nr) continue;
-    LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr, rows_tpb(nr)), rows_tpb(nr), s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
-    ++launches;
-  }
-  // (2) u2 = u1 + P Btilde P^T (r - A u1)
+  bool zero = true;  // uf is still 0
+  // u <- u + S (r - A u) (forward) or u + S^t (r - A u) (backward), fine_sweeps times
+  auto smooth = [&](bool forward) {
+    for (int m = 0; m < h.prm.fine_sweeps; ++m) {
+      if (!jacobi) {
+        for (int q = 0; q < ncol; ++q) {
+          const int c = forward ? q : ncol - 1 - q;
+          int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
+          if (!nr) continue;
+          LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
+                 launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr, rows_tpb(nr)), rows_tpb(nr), s, r0, nr, A.off,
+                        A.col, A.val, dinv, r, SP.uf.p));
+          ++launches;
+        }
+      } else if (zero) {
+        LAUNCH(ASMG_PROF_FINE_GS, n * (8 + 2 * sz),
+               launch(h.prm.use_pdl, k_jac_first<T>, nblk(h.npad), TPB, s, h.npad, dinv, r, SP.uf.p));
+        ++launches;
+      } else {
+        LAUNCH(ASMG_PROF_FINE_GS, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
+               launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, SP.uf.p,
+                      SP.rho.p));
+        LAUNCH(ASMG_PROF_FINE_GS, n * 4 * sz,
+               launch(h.prm.use_pdl, k_jac_add<T>, nblk(h.npad), TPB, s, h.npad, dinv, SP.rho.p, SP.uf.p));
+        launches += 2;
+      }
+      zero = false;
+    }
+  };
+  // (1) u1 = S r
+  smooth(true);
+  // (2) multiplicative: u2 = u1 + P Btilde P^T (r - A u1);  additive: u1 + P Btilde P^T r
   if (h.nJ > 0) {
-    LAUNCH(ASMG_PROF_FINE_RESID, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
-           launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, SP.uf.p, SP.rho.p));
+    if (additive) {
+      LAUNCH(ASMG_PROF_FINE_RESID, n * (8 + sz),
+             launch(h.prm.use_pdl, k_cast_fine<T>, nblk(h.npad), TPB, s, h.npad, r, SP.rho.p));
+    } else {
+      LAUNCH(ASMG_PROF_FINE_RESID, h.A64.nnz_real * (sz + 4) + n * (8 + 2 * sz),
+             launch(h.prm.use_pdl, k_resid_fine<T>, nblk(h.npad), TPB, s, h.npad, A.off, A.col, A.val, r, SP.uf.p,
+                    SP.rho.p));
+    }
     auto PT = view(P.PT);
     LAUNCH(ASMG_PROF_RESTRICT, P.PT.nnz_real * (sz + 4) + n * sz + 2 * nJ * sz,
            launch(h.prm.use_pdl, k_restrict_fine<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, SP.rho.p, SP.F.p, SP.U.p));
@@ -811,14 +904,8 @@ int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
            launch(h.prm.use_pdl, k_prolong_fine<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, SP.U.p, SP.uf.p));
     ++launches;
   }
-  // (3) u3 = u2 + S^T (r - A u2): backward multicolour sweep
-  for (int c = ncol - 1; c >= 0; --c) {
-    int64_t r0 = h.fine_cstart[c], nr = h.fine_cstart[c + 1] - r0;
-    if (!nr) continue;
-    LAUNCH(ASMG_PROF_FINE_GS, h.fine_cnnz[c] * (sz + 4) + h.fine_crows[c] * (8 + 4 * sz),
-           launch(h.prm.use_pdl, k_gs_fine<T, double>, nblk(nr, rows_tpb(nr)), rows_tpb(nr), s, r0, nr, A.off, A.col, A.val, dinv, r, SP.uf.p));
-    ++launches;
-  }
+  // (3) multiplicative only: u3 = u2 + S^T (r - A u2)
+  if (!additive) smooth(false);
   ASMG_CUDA(cudaGetLastError());
   return launches;
 }
@@ -841,7 +928,25 @@ int enqueue_body(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle 
   return launches + 4;
 }
 
+// the ASMG iteration: z = B r, x += z, r = b - A x, stopping test
+template <class T>
+int enqueue_iteration(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  int launches = enqueue_precond<T>(h, S, S.r.p, s);
+  const T* z = slotprec<T>(S).uf.p;
+  const int G = RED_BLOCKS;
+  const int64_t n = h.n, sz = sizeof(T);
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_xpz<T>, G, TPB, s, h.npad, z, S.x.p));
+  LAUNCH(ASMG_PROF_CG_SPMV, h.A64.nnz_real * 12 + n * 24,
+         launch(h.prm.use_pdl, k_iter_resid, G, TPB, s, h.npad, view(h.A64), S.b.p, S.x.p, S.r.p, S.partial.p,
+                S.ticket.p, S.scal.p, S.hist.p, hnd, use_hnd));
+  ASMG_CUDA(cudaGetLastError());
+  return launches + 2;
+}
+
 int enqueue_body_any(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
+  if (h.prm.iteration == 1)
+    return h.prm.precision == ASMG_MIXED ? enqueue_iteration<float>(h, S, s, hnd, use_hnd)
+                                         : enqueue_iteration<double>(h, S, s, hnd, use_hnd);
   return h.prm.precision == ASMG_MIXED ? enqueue_body<float>(h, S, s, hnd, use_hnd)
                                        : enqueue_body<double>(h, S, s, hnd, use_hnd);
 }

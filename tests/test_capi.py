@@ -100,3 +100,14 @@ def test_null_arguments(lib):
     assert L.amg_solve(None, None, None, 1e-8, None, None, None) == lib.ASMG_ERR_INVALID_ARG
     assert L.asmg_default_params(None) == lib.ASMG_ERR_INVALID_ARG
     L.amg_destroy(None)
+
+
+def test_variant_parameters_validated(lib, gen):
+    m = _mesh(gen)
+    assert _setup_code(lib, m, smoother=2) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, m, additive=-1) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, m, fine_sweeps=0) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, m, fine_sweeps=9) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, m, iteration=2) == lib.ASMG_ERR_INVALID_ARG
+    p = lib.asmg_default_params()
+    assert (p.smoother, p.additive, p.fine_sweeps, p.iteration) == (0, 0, 1, 0)

@@ -737,3 +737,69 @@ def test_3d_manufactured_solution_second_order(gen):
         errs.append(np.sqrt(np.mean((u - ue) ** 2)))
     r = [errs[i] / errs[i + 1] for i in range(2)]
     assert all(3.0 < q < 5.0 for q in r), (errs, r)
+
+
+# --------------------------------------------------------------------------
+# Variants of B (Sec. 4.1 smoothers, eq. fasp additive form) and the ASMG
+# iteration (Sec. 5.1 rates)
+# --------------------------------------------------------------------------
+
+def _exact_aux(gen, **kw):
+    # one auxiliary level solved exactly (coarse_max above its size): Btilde = A_J^{-1}
+    m = gen.grid2d(9, 4)
+    o = oracle.Oracle(m, coarse_max=100000, **kw)
+    assert o.c == o.J
+    return m, o
+
+
+def _dense_parts(o):
+    A = o.A().toarray()
+    P = o.P().toarray()
+    AJ = o.A(o.J).toarray()
+    return A, np.diag(1.0 / np.diag(A)), P, np.linalg.inv(AJ)
+
+
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_additive_jacobi_preconditioner_closed_form(gen, sweeps):
+    # eq. fasp with S = D^{-1} (Sec. 4.1): B r = S_m r + Pi A_J^{-1} Pi^t r, where m
+    # Jacobi steps from zero give S_1 r = D^{-1} r, S_2 r = D^{-1} (2 r - A D^{-1} r)
+    m, o = _exact_aux(gen, smoother=1, additive=1, fine_sweeps=sweeps)
+    A, Dinv, P, AJinv = _dense_parts(o)
+    r = np.random.default_rng(1).standard_normal(o.nfree)
+    s = Dinv @ r if sweeps == 1 else Dinv @ (2 * r - A @ (Dinv @ r))
+    want = s + P @ (AJinv @ (P.T @ r))
+    assert np.abs(o.precond(r) - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_multiplicative_jacobi_preconditioner_closed_form(gen):
+    # Algorithm 1 with S = S^t = D^{-1}: u1 = D^{-1} r, u2 = u1 + Pi A_J^{-1} Pi^t (r - A u1),
+    # u3 = u2 + D^{-1} (r - A u2); B is then symmetric positive definite
+    m, o = _exact_aux(gen, smoother=1)
+    A, Dinv, P, AJinv = _dense_parts(o)
+    r = np.random.default_rng(2).standard_normal(o.nfree)
+    u1 = Dinv @ r
+    u2 = u1 + P @ (AJinv @ (P.T @ (r - A @ u1)))
+    u3 = u2 + Dinv @ (r - A @ u2)
+    assert np.abs(o.precond(r) - u3).max() <= 1e-12 * np.abs(u3).max()
+    n = o.nfree
+    B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_asmg_iteration_rates_bounded_and_mesh_independent(gen):
+    # Sec. 5.1: the ASMG iteration u <- u + B (b - A u) contracts at a rate bounded away
+    # from 1 (roughly 0.4 on the paper's mesh) uniformly in h
+    rates = []
+    for n in (17, 33, 65):
+        m = gen.grid2d(n, 3)
+        o = oracle.Oracle(m, iteration=1, max_iter=100)
+        b = o.mass_apply(gen.nodal_uniform(m, 1))
+        u, st, it, hist = o.solve(b, rtol=1e-8)
+        assert st == 0 and hist.size == it + 1
+        assert np.all(hist[1:] < hist[:-1])
+        rates.append((hist[-1] / hist[0]) ** (1.0 / it))
+        # the iterate is the solution of A u = b to the stopping tolerance
+        assert np.linalg.norm(b - o.spmv(u)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-12)
+    assert max(rates) <= 0.4, rates
+    assert max(rates) <= 2.5 * min(rates), rates
