@@ -210,15 +210,24 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
     }
   }
   HostCSR SM = select_rows(Arows, sel, nullptr, nullptr);
+  // SM row index of every node of N~_l: the down sweeps and the residual work
+  // on the level's own correction us (SM order), where every other node is 0
+  std::vector<int32_t> pos(Arows.nr, -1);
+  for (size_t k = 0; k < sel.size(); ++k)
+    if (sel[k] >= 0) pos[sel[k]] = (int32_t)k;
+  HostCSR SMd = select_rows(Arows, sel, &pos, &inset);
   D.cnnz.assign(ncol, 0);
+  D.cnnz_d.assign(ncol, 0);
   D.crows.assign(ncol, 0);
   for (int c = 0; c < ncol; ++c)
     for (int64_t k = D.cstart[c]; k < D.cstart[c + 1]; ++k)
       if (sel[k] >= 0) {
         D.crows[c] += 1;
         D.cnnz[c] += SM.ptr[k + 1] - SM.ptr[k];
+        D.cnnz_d[c] += SMd.ptr[k + 1] - SMd.ptr[k];
       }
   sell_build<T>(D.SM, SM, 0, s);
+  sell_build<T>(D.SMd, SMd, 0, s);
   D.sm_rows.upload(rows, s);
   D.sm_dinv.upload(dinv, s);
   // residual rows: every row with an entry in a smoothing column
@@ -231,7 +240,7 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
   D.nrs_real = (int64_t)rsel.size();
   while (rsel.size() % 32) rsel.push_back(-1);
   D.nrs = (int64_t)rsel.size();
-  HostCSR RS = select_rows(Arows, rsel, nullptr, &inset);
+  HostCSR RS = select_rows(Arows, rsel, &pos, &inset);
   sell_build<T>(D.RS, RS, 0, s);
   std::vector<int32_t> rsrows(rsel.begin(), rsel.end());
   D.rs_rows.upload(rsrows, s);

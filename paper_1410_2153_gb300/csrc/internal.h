@@ -235,11 +235,13 @@ struct AuxLevelDev {
   std::vector<int64_t> cnnz, crows;  // real non-zeros / rows per colour class
   int64_t nsm = 0, nsm_real = 0; // padded / real smoothing rows
   DBuf<int32_t> sm_rows;         // aux ID per SM row (-1 padding)
-  Sell<T> SM;                    // A_l rows of N~_l (all columns)
+  Sell<T> SM;                    // A_l rows of N~_l (all columns; the up sweeps)
+  Sell<T> SMd;                   // the same rows, columns in N~_l only, as SM row indices (the down sweeps)
+  std::vector<int64_t> cnnz_d;   // real non-zeros of SMd per colour class
   DBuf<T> sm_dinv;
   int64_t nrs = 0, nrs_real = 0;
   DBuf<int32_t> rs_rows;         // aux ID per residual row
-  Sell<T> RS;                    // A_l rows of E_l, columns in N~_l only
+  Sell<T> RS;                    // A_l rows of E_l, columns in N~_l only, as SM row indices
   int64_t nnew = 0;
   DBuf<int32_t> nn_id, nn_p0, nn_p1;  // prolongation of new nodes
   int64_t npar = 0, nchild = 0;

@@ -10,9 +10,10 @@
 // one correction vector U serve all levels and the V-cycle updates them in
 // place:
 //   down, level l:  save F on N~_l (first pre-sweep), nu_pre forward sweeps
-//                   of U on N~_l, F -= A_l U on the rows E_l touched by N~_l,
-//                   F[parent] += 1/2 F[new child] (I_l^T), save and clear U
-//                   on N~_l;
+//                   on N~_l, F -= A_l U on the rows E_l touched by N~_l,
+//                   F[parent] += 1/2 F[new child] (I_l^T).  U is 0 on the
+//                   whole down path: the level's correction lives in its
+//                   saved array us (SM row order) and never enters U there;
 //   coarsest:       U = A_c^{-1} F on its nodes (explicit FP64 inverse);
 //   up, level l:    U[new] = (U[p0] + U[p1]) / 2 (I_l), U += saved values,
 //                   nu_post backward sweeps with the saved F.
@@ -234,11 +235,12 @@ __global__ void k_cast_fine(int64_t n, const double* __restrict__ r, T* __restri
 }
 
 // ------------------------------------------------------ auxiliary levels
-// one colour of a sweep on the smoothing rows of a level
+// one colour of an up (post-smoothing) sweep on the smoothing rows of a
+// level: U[i] += (fs_k - (A_l U)_i) / a_ii with the F saved on the way down
 template <class T>
 __global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                          const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
-                         const T* __restrict__ rhs, int rhs_local, T* __restrict__ save, T* U) {
+                         const T* __restrict__ fs, T* U) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
   Row<T> row;
@@ -252,10 +254,54 @@ __global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off
   }
   pdl_wait();
   if (i >= 0) {
-    const T f = rhs_local ? rhs[k] : rhs[i];
-    if (save) save[k] = f;
-    const T s = f - row_dot(row, col, val, U);
+    const T s = fs[k] - row_dot(row, col, val, U);
     U[i] += s * di;
+  }
+  pdl_trigger();
+}
+
+// one colour of a down (pre-smoothing) sweep, on the level's own correction
+// us in SM row order.  The V-cycle reaches level l with U = 0, and the down
+// path changes U only on N~_l, so the sweeps run on us alone with the rows'
+// columns in N~_l (SMd).  In the first sweep us is 0 on this class and the
+// later ones: only columns of earlier classes (below k0) are read, and the
+// class's rows are set rather than updated.  The first sweep takes F and
+// saves it in fs.
+template <class T>
+__global__ void k_gs_aux_down(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                              const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
+                              const T* __restrict__ F, int first, T* __restrict__ fs, T* us) {
+  const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int32_t i = -1;
+  Row<T> row;
+  T di = 0;
+  if (k < k0 + nk) {
+    i = rows[k];
+    if (i >= 0) {
+      row_load(row, k, off, col, val);
+      di = dinv[k];
+    }
+  }
+  pdl_wait();
+  if (i >= 0) {
+    T f, acc = 0;
+    if (first) {
+      f = F[i];
+      fs[k] = f;
+#pragma unroll
+      for (int q = 0; q < MAXW; ++q)
+        if (q < row.w && row.c[q] < k0) acc += row.v[q] * us[row.c[q]];
+      for (int q = MAXW; q < row.w; ++q) {
+        const int64_t e = row.b + ((int64_t)q << 5) + row.lane;
+        const int32_t c = __ldg(col + e);
+        if (c < k0) acc += __ldg(val + e) * us[c];
+      }
+      us[k] = (f - acc) * di;
+    } else {
+      f = fs[k];
+      acc = row_dot(row, col, val, us);
+      us[k] += (f - acc) * di;
+    }
   }
   pdl_trigger();
 }
@@ -277,28 +323,22 @@ __global__ void k_resid_aux(int64_t n, const int64_t* __restrict__ off, const in
   pdl_trigger();
 }
 
-// I_l^T: F[parent] += 1/2 sum F[new children]; and save + clear U on N~_l
+// I_l^T: F[parent] += 1/2 sum F[new children]
 template <class T>
 __global__ void k_restrict_aux(int64_t npar, const int32_t* __restrict__ pid, const int32_t* __restrict__ pptr,
-                               const int32_t* __restrict__ child, T* __restrict__ F, int64_t nsm,
-                               const int32_t* __restrict__ rows, T* __restrict__ U, T* __restrict__ us) {
+                               const int32_t* __restrict__ child, T* __restrict__ F) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int32_t par = -1, p0 = 0, p1 = 0, i = -1;
+  int32_t par = -1, p0 = 0, p1 = 0;
   if (t < npar) {
     par = pid[t];
     p0 = pptr[t];
     p1 = pptr[t + 1];
   }
-  if (t < nsm) i = rows[t];
   pdl_wait();
   if (par >= 0) {
     T acc = 0;
     for (int32_t p = p0; p < p1; ++p) acc += F[child[p]];
     F[par] += (T)0.5 * acc;
-  }
-  if (i >= 0) {
-    us[t] = U[i];
-    U[i] = 0;
   }
   pdl_trigger();
 }
@@ -774,27 +814,28 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   }
   for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
     AuxLevelDev<T>& L = P.lev[li];
-    auto SM = view(L.SM);
-    // the first pre-sweep also saves F on N~_l for the post-sweeps (nu_pre >= 1)
+    auto SMd = view(L.SMd);
+    // pre-sweeps on us (SM order); the first also saves F on N~_l for the
+    // post-sweeps (nu_pre >= 1)
     for (int sweep = 0; sweep < npre; ++sweep) {
       for (int c = 0; c < L.ncolours; ++c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        const int64_t by = L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz + (sweep == 0 ? sz : 0));
+        const int64_t by = L.cnnz_d[c] * (sz + 4) + L.crows[c] * (4 + (sweep == 0 ? 4 + 4 * sz : 4 * sz));
         LAUNCH(ASMG_PROF_AUX_GS, by,
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
-                      L.sm_rows.p, sweep == 0 ? SP.F.p : SP.fs[li].p, sweep == 0 ? 0 : 1, sweep == 0 ? SP.fs[li].p : nullptr,
-                      SP.U.p));
+               launch(h.prm.use_pdl, k_gs_aux_down<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SMd.off,
+                      SMd.col, SMd.val, L.sm_dinv.p, L.sm_rows.p, (const T*)SP.F.p, sweep == 0 ? 1 : 0, SP.fs[li].p,
+                      SP.us[li].p));
         ++launches;
       }
     }
     auto RS = view(L.RS);
     LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
            launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
-                  SP.U.p, SP.F.p));
-    LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz) + L.nsm_real * (4 + 3 * sz),
-           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(std::max(L.npar, L.nsm), rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.npar, L.rp_id.p,
-                  L.rp_ptr.p, L.rp_child.p, SP.F.p, L.nsm, L.sm_rows.p, SP.U.p, SP.us[li].p));
+                  (const T*)SP.us[li].p, SP.F.p));
+    LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz),
+           launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(L.npar, rows_tpb(L.npar)), rows_tpb(L.npar), s, L.npar, L.rp_id.p,
+                  L.rp_ptr.p, L.rp_child.p, SP.F.p));
     launches += 2;
   }
   if (nbot) {
@@ -830,7 +871,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
         if (!nk) continue;
         LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
                launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
-                      L.sm_rows.p, SP.fs[li].p, 1, nullptr, SP.U.p));
+                      L.sm_rows.p, (const T*)SP.fs[li].p, SP.U.p));
         ++launches;
       }
   }
