@@ -4,6 +4,7 @@
 #include <cub/cub.cuh>
 
 #include <cmath>
+#include <thread>
 
 #include "internal.h"
 
@@ -451,29 +452,45 @@ std::vector<int32_t> jp_colour_gpu(const HostCSR& A, const std::vector<uint8_t>&
   return colour.download(s);
 }
 
+// Host-side packing, parallel over slices (slice widths, then the column-
+// major fill of each slice).
 template <class T>
 void sell_build(Sell<T>& S, const HostCSR& rows, int32_t pad_col, cudaStream_t s) {
   const int64_t nr = rows.nr;
   S.nslices = (nr + SELL_C - 1) / SELL_C;
   S.nrows = S.nslices * SELL_C;
+  const unsigned nt = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), S.nslices / 4096));
+  auto par = [&](auto body) {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+      th.emplace_back([&, t] { body(S.nslices * t / nt, S.nslices * (t + 1) / nt); });
+    for (auto& x : th) x.join();
+  };
   std::vector<int64_t> off(S.nslices + 1, 0);
-  for (int64_t sl = 0; sl < S.nslices; ++sl) {
-    int64_t w = 0;
-    for (int64_t r = sl * SELL_C; r < std::min(nr, (sl + 1) * SELL_C); ++r) w = std::max(w, rows.ptr[r + 1] - rows.ptr[r]);
-    off[sl + 1] = off[sl] + w * SELL_C;
-  }
+  par([&](int64_t s0, int64_t s1) {
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      int64_t w = 0;
+      for (int64_t r = sl * SELL_C; r < std::min(nr, (sl + 1) * SELL_C); ++r)
+        w = std::max(w, rows.ptr[r + 1] - rows.ptr[r]);
+      off[sl + 1] = w * SELL_C;
+    }
+  });
+  for (int64_t sl = 0; sl < S.nslices; ++sl) off[sl + 1] += off[sl];
   S.nnz = off[S.nslices];
   S.nnz_real = rows.ptr[nr];
   std::vector<int32_t> col(S.nnz, pad_col);
   std::vector<T> val(S.nnz, (T)0);
-  for (int64_t r = 0; r < nr; ++r) {
-    int64_t sl = r / SELL_C, t = r % SELL_C;
-    int64_t k = 0;
-    for (int64_t p = rows.ptr[r]; p < rows.ptr[r + 1]; ++p, ++k) {
-      col[off[sl] + k * SELL_C + t] = rows.col[p];
-      val[off[sl] + k * SELL_C + t] = (T)rows.val[p];
+  par([&](int64_t s0, int64_t s1) {
+    for (int64_t r = s0 * SELL_C; r < std::min(nr, s1 * SELL_C); ++r) {
+      const int64_t sl = r / SELL_C, t = r % SELL_C;
+      int64_t k = 0;
+      for (int64_t p = rows.ptr[r]; p < rows.ptr[r + 1]; ++p, ++k) {
+        col[off[sl] + k * SELL_C + t] = rows.col[p];
+        val[off[sl] + k * SELL_C + t] = (T)rows.val[p];
+      }
     }
-  }
+  });
   S.off.upload(off, s);
   S.col.upload(col, s);
   S.val.upload(val, s);

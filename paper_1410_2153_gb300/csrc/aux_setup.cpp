@@ -218,14 +218,38 @@ void leaves_in(const BoxTree& T, int64_t lox, int64_t loy, int64_t hix, int64_t 
   }
 }
 
+constexpr unsigned MAX_THREADS = 64;
+
+// f(thread, nthreads, begin, end) over contiguous ranges of [0, n), in order
 template <class F>
 void parallel_for(int64_t n, F f) {
-  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  unsigned nt = std::max(1u, std::min(MAX_THREADS, std::thread::hardware_concurrency()));
   if (n < 4096) nt = 1;
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t)
     th.emplace_back([&, t] { f(t, nt, n * t / nt, n * (t + 1) / nt); });
   for (auto& x : th) x.join();
+}
+
+// sorted unique union of per-thread lists (each part deduplicated in
+// parallel first)
+template <class V>
+std::vector<V> merge_unique(std::vector<std::vector<V>>& parts) {
+  auto su = [](std::vector<V>& v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  };
+  std::vector<std::thread> th;
+  for (auto& v : parts)
+    if (!v.empty()) th.emplace_back([&v, &su] { su(v); });
+  for (auto& x : th) x.join();
+  std::vector<V> all;
+  for (auto& v : parts) {
+    all.insert(all.end(), v.begin(), v.end());
+    std::vector<V>().swap(v);
+  }
+  su(all);
+  return all;
 }
 
 }  // namespace
@@ -269,22 +293,24 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
 
   // ---- finest-level nodes (aux unknowns)
   {
-    std::vector<uint64_t> keys;
-    std::vector<std::array<uint64_t, 3>> tri;
-    for (int d = 0; d <= J; ++d) {
-      for (uint64_t p : BX[d]) {
-        if (T.split(d, p)) continue;
+    std::vector<std::pair<int, uint64_t>> leaves;
+    for (int d = 0; d <= J; ++d)
+      for (uint64_t p : BX[d])
+        if (!T.split(d, p)) leaves.push_back({d, p});
+    std::vector<std::vector<uint64_t>> part(MAX_THREADS);
+    parallel_for((int64_t)leaves.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::array<uint64_t, 3>> tri;
+      for (int64_t q = b0; q < b1; ++q) {
         bool h[4];
-        T.hanging(d, p, h);
+        T.hanging(leaves[q].first, leaves[q].second, h);
         tri.clear();
-        box_tris(T, d, p, h, tri);
-        for (auto& t : tri)
+        box_tris(T, leaves[q].first, leaves[q].second, h, tri);
+        for (auto& x : tri)
           for (int k = 0; k < 3; ++k)
-            if (!boundary_key(T, t[k])) keys.push_back(t[k]);
+            if (!boundary_key(T, x[k])) part[t].push_back(x[k]);
       }
-    }
-    sort_unique(keys);
-    out.aux_key = std::move(keys);
+    });
+    out.aux_key = merge_unique(part);
   }
   const std::vector<uint64_t>& AK = out.aux_key;
 
@@ -295,7 +321,12 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   std::vector<LevelInfo> info(J + 1);
   out.nlevel.assign(J + 1, 0);
   std::vector<std::vector<std::array<uint64_t, 3>>> newnodes(J + 1);  // key, parent0, parent1
-  for (int l = 1; l <= J; ++l) {
+  std::vector<int64_t> nfree_new(J + 1, 0);
+  std::atomic<int> next_nn(1);
+  auto nn_worker = [&]() {
+   for (;;) {
+    const int l = next_nn.fetch_add(1);
+    if (l > J) return;
     const int d = l - 1;
     const auto& bx = BX[d];
     std::vector<std::array<uint64_t, 3>> nn;
@@ -332,9 +363,17 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     int64_t nfree = 0;
     for (auto& v : nn)
       if (!boundary_key(T, v[0])) ++nfree;
-    out.nlevel[l] = out.nlevel[l - 1] + nfree;
+    nfree_new[l] = nfree;
     newnodes[l] = std::move(nn);
+   }
+  };
+  {
+    unsigned nt = std::max(1u, std::min(MAX_THREADS, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(nn_worker);
+    for (auto& x : th) x.join();
   }
+  for (int l = 1; l <= J; ++l) out.nlevel[l] = out.nlevel[l - 1] + nfree_new[l];
   // coarsest level used: finest level with at most coarse_max_dofs free nodes
   out.c = 0;
   for (int l = 0; l <= J; ++l)
@@ -515,18 +554,12 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     out.coarse_id.erase(std::unique(out.coarse_id.begin(), out.coarse_id.end()), out.coarse_id.end());
   }
 
-  // ---- levels c+1..J: smoothing sets, assembly triangles, new nodes
-  // (levels are independent: one thread per level, largest first)
+  // ---- levels c+1..J: smoothing sets, assembly triangles, new nodes; each
+  // level in parallel over its changed boxes (per-thread lists merged,
+  // sorted, unique), then over its relevant boxes (triangles concatenated in
+  // order)
   out.levels.assign(std::max(0, J - c), AuxLevelHost());
-  std::vector<int> order;
-  for (int l = c + 1; l <= J; ++l) order.push_back(l);
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return BX[x - 1].size() > BX[y - 1].size(); });
-  std::atomic<int> next_level(0);
-  auto level_worker = [&]() {
-   for (;;) {
-    const int oi = next_level.fetch_add(1);
-    if (oi >= (int)order.size()) return;
-    const int l = order[oi];
+  for (int l = c + 1; l <= J; ++l) {
     AuxLevelHost& L = out.levels[l - (c + 1)];
     L.level = l;
     const int d = l - 1;
@@ -534,74 +567,92 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     std::vector<uint64_t> changed = info[l].fanned;  // plus the split boxes
     changed.insert(changed.end(), T.S[d].begin(), T.S[d].end());
     sort_unique(changed);
-    // N~_l
     std::vector<uint64_t> sm;
-    if (prm.smoothing == 1) {
-      // every node of the level
-      for (int dd = 0; dd <= l; ++dd) {
-        for (uint64_t p : BX[dd]) {
-          if (dd < l && T.split(dd, p)) continue;
-          bool h[4] = {false, false, false, false};
-          if (dd < l) T.hanging(dd, p, h);
-          std::vector<std::array<uint64_t, 3>> kt;
-          box_tris(T, dd, p, h, kt);
-          for (auto& t : kt)
-            for (int v = 0; v < 3; ++v)
-              if (!boundary_key(T, t[v])) sm.push_back(t[v]);
-        }
-      }
-    } else {
-      for (uint64_t p : changed) {
-        const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s, m = s >> 1;
-        bool sp = T.split(d, p);
-        for (int iy = 0; iy <= 2; ++iy)
-          for (int ix = 0; ix <= 2; ++ix) {
-            bool mid = (ix == 1) || (iy == 1);
-            if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
-            uint64_t k = mort(x0 + ix * m, y0 + iy * m);
-            if (!boundary_key(T, k)) sm.push_back(k);
-          }
-      }
-    }
-    sort_unique(sm);
-    for (uint64_t k : sm) L.smooth.push_back(id_of(AK, k));
-
-    // relevant boxes: changed boxes and the level-l leaves around them
     std::vector<std::pair<int, uint64_t>> rel;
     if (prm.smoothing == 1) {
+      // every node of the level, every box shown at the level
       for (int dd = 0; dd <= l; ++dd)
         for (uint64_t p : BX[dd])
           if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
-    } else {
-      for (uint64_t p : changed) {
-        if (T.split(d, p)) {
-          for (uint64_t ch = 0; ch < 4; ++ch) rel.push_back({d + 1, (p << 2) | ch});
-        } else {
-          rel.push_back({d, p});
+      std::vector<std::vector<uint64_t>> part(MAX_THREADS);
+      parallel_for((int64_t)rel.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+        std::vector<std::array<uint64_t, 3>> kt;
+        for (int64_t q = b0; q < b1; ++q) {
+          const int dd = rel[q].first;
+          bool h[4] = {false, false, false, false};
+          if (dd < l) T.hanging(dd, rel[q].second, h);
+          kt.clear();
+          box_tris(T, dd, rel[q].second, h, kt);
+          for (auto& x : kt)
+            for (int v = 0; v < 3; ++v)
+              if (!boundary_key(T, x[v])) part[t].push_back(x[v]);
         }
-        const int64_t x = (int64_t)compact(p), y = (int64_t)compact(p >> 1), nb = 1LL << d;
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            if (!dx && !dy) continue;
-            if (x + dx < 0 || y + dy < 0 || x + dx >= nb || y + dy >= nb) continue;
-            int dd = d;
-            uint64_t q = mort((uint64_t)(x + dx), (uint64_t)(y + dy));
-            while (!T.exists(dd, q)) {
-              --dd;
-              q >>= 2;
+      });
+      sm = merge_unique(part);
+    } else {
+      // N~_l: the corners and centres of the changed boxes, and the edge
+      // midpoints of the split ones; relevant boxes: the changed boxes and the
+      // level-l leaves around them
+      std::vector<std::vector<uint64_t>> spart(MAX_THREADS);
+      std::vector<std::vector<std::pair<int, uint64_t>>> rpart(MAX_THREADS);
+      parallel_for((int64_t)changed.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+        auto& M = spart[t];
+        auto& R = rpart[t];
+        for (int64_t q = b0; q < b1; ++q) {
+          const uint64_t p = changed[q];
+          const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s, m = s >> 1;
+          const bool sp = T.split(d, p);
+          for (int iy = 0; iy <= 2; ++iy)
+            for (int ix = 0; ix <= 2; ++ix) {
+              bool mid = (ix == 1) || (iy == 1);
+              if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
+              uint64_t k = mort(x0 + ix * m, y0 + iy * m);
+              if (!boundary_key(T, k)) M.push_back(k);
             }
-            if (dd == d && T.split(d, q)) {
-              for (uint64_t ch = 0; ch < 4; ++ch) rel.push_back({d + 1, (q << 2) | ch});
-            } else {
-              rel.push_back({dd, q});
-            }
+          if (sp) {
+            for (uint64_t ch = 0; ch < 4; ++ch) R.push_back({d + 1, (p << 2) | ch});
+          } else {
+            R.push_back({d, p});
           }
-      }
+          const int64_t x = (int64_t)compact(p), y = (int64_t)compact(p >> 1), nb = 1LL << d;
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (!dx && !dy) continue;
+              if (x + dx < 0 || y + dy < 0 || x + dx >= nb || y + dy >= nb) continue;
+              int dd = d;
+              uint64_t nq = mort((uint64_t)(x + dx), (uint64_t)(y + dy));
+              while (!T.exists(dd, nq)) {
+                --dd;
+                nq >>= 2;
+              }
+              if (dd == d && T.split(d, nq)) {
+                for (uint64_t ch = 0; ch < 4; ++ch) R.push_back({d + 1, (nq << 2) | ch});
+              } else {
+                R.push_back({dd, nq});
+              }
+            }
+        }
+      });
+      sm = merge_unique(spart);
+      rel = merge_unique(rpart);
     }
-    std::sort(rel.begin(), rel.end());
+    L.smooth.resize(sm.size());
+    parallel_for((int64_t)sm.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+      for (int64_t q = b0; q < b1; ++q) L.smooth[q] = id_of(AK, sm[q]);
+    });
+    std::sort(rel.begin(), rel.end());  // (already unique in the default mode)
     rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
-    for (auto& b : rel) emit_box(b.first, b.second, l, L.tri_id, L.tri_key, L.tri_coef);
-
+    std::vector<std::vector<int32_t>> ids(MAX_THREADS);
+    std::vector<std::vector<uint64_t>> keys(MAX_THREADS);
+    std::vector<std::vector<double>> coefs(MAX_THREADS);
+    parallel_for((int64_t)rel.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t]);
+    });
+    for (unsigned t = 0; t < MAX_THREADS; ++t) {
+      L.tri_id.insert(L.tri_id.end(), ids[t].begin(), ids[t].end());
+      L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
+      L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
+    }
     // new nodes with their parents
     for (auto& v : newnodes[l]) {
       if (boundary_key(T, v[0])) continue;
@@ -609,13 +660,6 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
       L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
     }
-  }
-  };
-  {
-    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(level_worker);
-    for (auto& x : th) x.join();
   }
 
   // ---- Scott-Zhang transfer (Sec. 4.1): P_ik = int_{sigma_i} psi_i phi_k,

@@ -395,13 +395,35 @@ void leaves_in(const Tree3& T, const int64_t* lo, const int64_t* hi, std::vector
   }
 }
 
+// f(thread, begin, end) over contiguous ranges of [0, n), in thread order
 template <class F>
 void pfor(int64_t n, F f) {
-  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   if (n < 2048) nt = 1;
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t) th.emplace_back([&, t] { f(t, n * t / nt, n * (t + 1) / nt); });
   for (auto& x : th) x.join();
+}
+
+// sorted unique union of per-thread lists (each part deduplicated in
+// parallel first)
+template <class V>
+std::vector<V> uniq_parts(std::vector<std::vector<V>>& parts) {
+  auto su = [](std::vector<V>& v) {
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+  };
+  std::vector<std::thread> th;
+  for (auto& v : parts)
+    if (!v.empty()) th.emplace_back([&v, &su] { su(v); });
+  for (auto& x : th) x.join();
+  std::vector<V> all;
+  for (auto& v : parts) {
+    all.insert(all.end(), v.begin(), v.end());
+    std::vector<V>().swap(v);
+  }
+  su(all);
+  return all;
 }
 
 // index of the Kuhn tetrahedron of a box holding point u (local coordinates
@@ -454,21 +476,26 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   std::vector<std::vector<uint64_t>> BX(J + 1);
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
 
-  // finest-level free nodes
+  // finest-level free nodes: the non-boundary vertices of the leaves'
+  // tetrahedra
   {
-    std::vector<uint64_t> keys;
-    std::vector<Tet> tt;
+    std::vector<std::pair<int, uint64_t>> leaves;
     for (int d = 0; d <= J; ++d)
-      for (uint64_t p : BX[d]) {
-        if (T.split(d, p)) continue;
+      for (uint64_t p : BX[d])
+        if (!T.split(d, p)) leaves.push_back({d, p});
+    const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::vector<uint64_t>> part(nt);
+    pfor((int64_t)leaves.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+      std::vector<Tet> tt;
+      for (int64_t q = b0; q < b1; ++q) {
         tt.clear();
-        box_tets(T, d, p, J, tt);
-        for (auto& t : tt)
+        box_tets(T, leaves[q].first, leaves[q].second, J, tt);
+        for (auto& x : tt)
           for (int k = 0; k < 4; ++k)
-            if (!bnd3(T, t[k])) keys.push_back(t[k]);
+            if (!bnd3(T, x[k])) part[t].push_back(x[k]);
       }
-    uniq(keys);
-    out.aux_key = std::move(keys);
+    });
+    out.aux_key = uniq_parts(part);
   }
   const std::vector<uint64_t>& AK = out.aux_key;
 
@@ -541,14 +568,18 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   std::vector<Tet> ftet;
   std::vector<std::vector<int64_t>> first(J + 1);
   std::vector<std::vector<uint8_t>> nft(J + 1);
+  std::vector<std::vector<int32_t>> lid(J + 1);  // leaf number
+  int64_t nleaf = 0;
   for (int d = 0; d <= J; ++d) {
     first[d].assign(BX[d].size(), -1);
     nft[d].assign(BX[d].size(), 0);
+    lid[d].assign(BX[d].size(), -1);
     for (size_t i = 0; i < BX[d].size(); ++i) {
       if (T.split(d, BX[d][i])) continue;
       first[d][i] = (int64_t)ftet.size();
       box_tets(T, d, BX[d][i], J, ftet);
       nft[d][i] = (uint8_t)(ftet.size() - first[d][i]);
+      lid[d][i] = (int32_t)nleaf++;
     }
   }
   const double lat_scale = std::ldexp(1.0, T.LB) / tree.L;
@@ -572,11 +603,12 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   auto leaf_tet = [&](int64_t q, TetP& K) {
     for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, ftet[q][v], K[v].data());
   };
-  auto leaf_range = [&](const std::pair<int, uint64_t>& lf, int64_t& f0, int& nq) {
+  auto leaf_range = [&](const std::pair<int, uint64_t>& lf, int64_t& f0, int& nq, int32_t* leaf = nullptr) {
     const auto& bx = BX[lf.first];
     const size_t bi = std::lower_bound(bx.begin(), bx.end(), lf.second) - bx.begin();
     f0 = first[lf.first][bi];
     nq = nft[lf.first][bi];
+    if (leaf) *leaf = lid[lf.first][bi];
   };
 
   // element coefficients: integrals of a over the 6 Kuhn tetrahedra of every
@@ -608,6 +640,39 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     }
     std::sort(order.begin(), order.end());
     const int64_t CH = 4096, nch = (mesh.ne + CH - 1) / CH;
+    // A leaf whose overlapping elements all have one coefficient value a has
+    // the average a on each of its tetrahedra (the fine elements tile it): only
+    // leaves that see two values are clipped.  The elements whose bounding
+    // boxes meet a leaf include every element that overlaps it.  Per leaf:
+    // the bits of the first value seen (0: none yet) and a "mixed" flag.
+    std::vector<std::atomic<uint64_t>> lval(nleaf);
+    std::vector<std::atomic<uint8_t>> lmixed(nleaf);
+    for (int64_t q = 0; q < nleaf; ++q) {
+      lval[q].store(0, std::memory_order_relaxed);
+      lmixed[q].store(0, std::memory_order_relaxed);
+    }
+    pfor(mesh.ne, [&](unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::pair<int, uint64_t>> lv, st;
+      for (int64_t e = b0; e < b1; ++e) {
+        TetP S;
+        fine_tet(e, S);
+        int64_t lo[3], hi[3];
+        window(S, lo, hi);
+        lv.clear();
+        leaves_in(T, lo, hi, lv, st);
+        uint64_t bits;
+        std::memcpy(&bits, &mesh.coeff[e], 8);
+        for (auto& lf : lv) {
+          int64_t f0;
+          int nq;
+          int32_t leaf;
+          leaf_range(lf, f0, nq, &leaf);
+          uint64_t expect = 0;
+          if (!lval[leaf].compare_exchange_strong(expect, bits, std::memory_order_relaxed) && expect != bits)
+            lmixed[leaf].store(1, std::memory_order_relaxed);
+        }
+      }
+    });
     std::vector<std::vector<std::pair<int64_t, double>>> csum(nch);
     std::atomic<int64_t> nextc(0);
     auto work = [&]() {
@@ -629,7 +694,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           for (auto& lf : lv) {
             int64_t f0;
             int nq;
-            leaf_range(lf, f0, nq);
+            int32_t leaf;
+            leaf_range(lf, f0, nq, &leaf);
+            if (!lmixed[leaf].load(std::memory_order_relaxed) && lval[leaf].load(std::memory_order_relaxed) != 0)
+              continue;
             for (int q = 0; q < nq; ++q) {
               TetP K;
               leaf_tet(f0 + q, K);
@@ -664,6 +732,19 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (auto& v : csum)
       for (auto& pr : v) I[pr.first] += pr.second;
     csum.clear();
+    for (int d = 0; d <= J; ++d)
+      for (size_t i = 0; i < BX[d].size(); ++i) {
+        const int32_t leaf = lid[d][i];
+        if (leaf < 0 || lmixed[leaf].load() || lval[leaf].load() == 0) continue;
+        const uint64_t bits = lval[leaf].load();
+        double a;
+        std::memcpy(&a, &bits, 8);
+        for (int q = 0; q < nft[d][i]; ++q) {
+          TetP K;
+          leaf_tet(first[d][i] + q, K);
+          I[first[d][i] + q] = a * (std::fabs(vol6(K[0], K[1], K[2], K[3])) / 6.0);
+        }
+      }
     // bottom-up Kuhn integrals
     for (int d = J; d >= 0; --d) {
       kint[d].assign(BX[d].size(), {0, 0, 0, 0, 0, 0});
@@ -742,89 +823,100 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   std::sort(out.coarse_id.begin(), out.coarse_id.end());
   out.coarse_id.erase(std::unique(out.coarse_id.begin(), out.coarse_id.end()), out.coarse_id.end());
 
-  // levels c+1..J
+  // levels c+1..J, each in parallel over its changed boxes: relevant boxes
+  // and smoothing nodes per chunk (merged, sorted, unique), then the level
+  // tetrahedra per chunk of relevant boxes, concatenated in order
   out.levels.assign(std::max(0, J - c), AuxLevelHost());
-  std::atomic<int> next(0);
-  auto worker = [&]() {
-    for (;;) {
-      const int l = c + 1 + next.fetch_add(1);
-      if (l > J) return;
-      AuxLevelHost& L = out.levels[l - (c + 1)];
-      L.level = l;
-      const int d = l - 1;
-      std::vector<std::pair<int, uint64_t>> rel;
-      if (prm.smoothing == 1) {
-        for (int dd = 0; dd <= l; ++dd)
-          for (uint64_t p : BX[dd])
-            if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
-      } else {
-        for (uint64_t p : changed[l]) {
+  unsigned nthr = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  for (int l = c + 1; l <= J; ++l) {
+    AuxLevelHost& L = out.levels[l - (c + 1)];
+    L.level = l;
+    const int d = l - 1;
+    std::vector<std::pair<int, uint64_t>> rel;
+    std::vector<uint64_t> sm;
+    if (prm.smoothing == 1) {
+      for (int dd = 0; dd <= l; ++dd)
+        for (uint64_t p : BX[dd])
+          if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
+      std::vector<std::vector<uint64_t>> part(nthr);
+      pfor((int64_t)rel.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+        std::vector<Tet> kt;
+        for (int64_t q = b0; q < b1; ++q) {
+          kt.clear();
+          box_tets(T, rel[q].first, rel[q].second, l, kt);
+          for (auto& tt : kt)
+            for (int v = 0; v < 4; ++v)
+              if (!bnd3(T, tt[v])) part[t].push_back(tt[v]);
+        }
+      });
+      sm = uniq_parts(part);
+    } else {
+      const std::vector<uint64_t>& ch = changed[l];
+      std::vector<std::vector<std::pair<int, uint64_t>>> rpart(nthr);
+      std::vector<std::vector<uint64_t>> spart(nthr);
+      pfor((int64_t)ch.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+        auto& R = rpart[t];
+        auto& M = spart[t];
+        std::vector<Tet> kt;
+        for (int64_t q = b0; q < b1; ++q) {
+          const uint64_t p = ch[q];
+          kt.clear();
           if (T.split(d, p)) {
-            for (uint64_t ch = 0; ch < 8; ++ch) rel.push_back({d + 1, (p << 3) | ch});
+            for (uint64_t cc = 0; cc < 8; ++cc) {
+              R.push_back({d + 1, (p << 3) | cc});
+              box_tets(T, d + 1, (p << 3) | cc, l, kt);
+            }
           } else {
-            rel.push_back({d, p});
+            R.push_back({d, p});
+            box_tets(T, d, p, l, kt);
           }
+          for (auto& tt : kt)
+            for (int v = 0; v < 4; ++v)
+              if (!bnd3(T, tt[v])) M.push_back(tt[v]);
           for (int oz = -1; oz <= 1; ++oz)
             for (int oy = -1; oy <= 1; ++oy)
               for (int ox = -1; ox <= 1; ++ox) {
                 if (!ox && !oy && !oz) continue;
                 int o[3] = {ox, oy, oz};
-                uint64_t q;
-                if (!T.offset(d, p, o, q)) continue;
+                uint64_t nq;
+                if (!T.offset(d, p, o, nq)) continue;
                 int dd = d;
-                while (!T.exists(dd, q)) {
+                while (!T.exists(dd, nq)) {
                   --dd;
-                  q >>= 3;
+                  nq >>= 3;
                 }
-                if (dd == d && T.split(d, q)) {
-                  for (uint64_t ch = 0; ch < 8; ++ch) rel.push_back({d + 1, (q << 3) | ch});
+                if (dd == d && T.split(d, nq)) {
+                  for (uint64_t cc = 0; cc < 8; ++cc) R.push_back({d + 1, (nq << 3) | cc});
                 } else {
-                  rel.push_back({dd, q});
+                  R.push_back({dd, nq});
                 }
               }
         }
-      }
-      std::sort(rel.begin(), rel.end());
-      rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
-      // smoothing set: vertices of the level-l tetrahedra of the changed boxes
-      std::vector<uint64_t> sm;
-      if (prm.smoothing == 1) {
-        for (auto& b : rel) {
-          std::vector<Tet> kt;
-          box_tets(T, b.first, b.second, l, kt);
-          for (auto& t : kt)
-            for (int v = 0; v < 4; ++v)
-              if (!bnd3(T, t[v])) sm.push_back(t[v]);
-        }
-      } else {
-        for (uint64_t p : changed[l]) {
-          std::vector<Tet> kt;
-          if (T.split(d, p)) {
-            for (uint64_t ch = 0; ch < 8; ++ch) box_tets(T, d + 1, (p << 3) | ch, l, kt);
-          } else {
-            box_tets(T, d, p, l, kt);
-          }
-          for (auto& t : kt)
-            for (int v = 0; v < 4; ++v)
-              if (!bnd3(T, t[v])) sm.push_back(t[v]);
-        }
-      }
-      uniq(sm);
-      for (uint64_t k : sm) L.smooth.push_back(idx_of(AK, k));
-      for (auto& b : rel) emit_box(b.first, b.second, l, L.tri_id, L.tri_key, L.tri_coef);
-      for (auto& v : newnodes[l]) {
-        if (bnd3(T, v[0])) continue;
-        L.new_id.push_back(idx_of(AK, v[0]));
-        L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
-        L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
-      }
+      });
+      rel = uniq_parts(rpart);
+      sm = uniq_parts(spart);
     }
-  };
-  {
-    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t) th.emplace_back(worker);
-    for (auto& x : th) x.join();
+    std::sort(rel.begin(), rel.end());
+    rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+    uniq(sm);
+    for (uint64_t k : sm) L.smooth.push_back(idx_of(AK, k));
+    std::vector<std::vector<int32_t>> ids(nthr);
+    std::vector<std::vector<uint64_t>> keys(nthr);
+    std::vector<std::vector<double>> coefs(nthr);
+    pfor((int64_t)rel.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t]);
+    });
+    for (unsigned t = 0; t < nthr; ++t) {
+      L.tri_id.insert(L.tri_id.end(), ids[t].begin(), ids[t].end());
+      L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
+      L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
+    }
+    for (auto& v : newnodes[l]) {
+      if (bnd3(T, v[0])) continue;
+      L.new_id.push_back(idx_of(AK, v[0]));
+      L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
+      L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
+    }
   }
 
   // Scott-Zhang (Sec. 4.1) in 3D: psi_i = (20 lambda_i - 4)/|sigma_i|

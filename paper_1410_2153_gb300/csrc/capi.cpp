@@ -300,34 +300,46 @@ void build_prec(asmg_s& h, Prec<T>& P, const HostCSR& Aperm, const std::vector<d
     std::vector<T> d(dinv_perm.begin(), dinv_perm.end());
     P.dinv_f.upload(d, s);
   }
-  // transfer P (rows: permuted fine rows) and P^T (rows: aux nodes)
+  // transfer P (rows: permuted fine rows) and P^T (rows: aux nodes), built
+  // by counting sort into flat CSR arrays; each row sorted by column
   const Triplets& Tp = h.aux.P;
-  {
-    std::vector<std::vector<std::pair<int32_t, double>>> rows(h.npad), trows(h.nJpad);
-    for (size_t k = 0; k < Tp.r.size(); ++k) {
-      int32_t pr = h.row_of_free[Tp.r[k]];
-      rows[pr].push_back({Tp.c[k], Tp.v[k]});
-      trows[Tp.c[k]].push_back({pr, Tp.v[k]});
+  const int64_t m = (int64_t)Tp.r.size();
+  auto to_csr = [&](int64_t nr, int64_t nc, bool transpose) {
+    HostCSR A;
+    A.nr = nr;
+    A.nc = nc;
+    A.ptr.assign(nr + 1, 0);
+    for (int64_t k = 0; k < m; ++k) ++A.ptr[1 + (transpose ? Tp.c[k] : h.row_of_free[Tp.r[k]])];
+    for (int64_t i = 0; i < nr; ++i) A.ptr[i + 1] += A.ptr[i];
+    A.col.resize(m);
+    A.val.resize(m);
+    std::vector<int64_t> fill(A.ptr.begin(), A.ptr.end() - 1);
+    for (int64_t k = 0; k < m; ++k) {
+      const int32_t pr = h.row_of_free[Tp.r[k]];
+      const int64_t row = transpose ? Tp.c[k] : pr;
+      const int64_t q = fill[row]++;
+      A.col[q] = transpose ? pr : Tp.c[k];
+      A.val[q] = Tp.v[k];
     }
-    auto to_csr = [](std::vector<std::vector<std::pair<int32_t, double>>>& rr, int64_t nc) {
-      HostCSR A;
-      A.nr = (int64_t)rr.size();
-      A.nc = nc;
-      A.ptr.assign(A.nr + 1, 0);
-      for (int64_t i = 0; i < A.nr; ++i) {
-        std::sort(rr[i].begin(), rr[i].end());
-        for (auto& e : rr[i]) {
-          A.col.push_back(e.first);
-          A.val.push_back(e.second);
-        }
-        A.ptr[i + 1] = (int64_t)A.col.size();
+    std::vector<std::pair<int32_t, double>> tmp;
+    for (int64_t i = 0; i < nr; ++i) {
+      const int64_t b = A.ptr[i], e = A.ptr[i + 1];
+      bool sorted = true;
+      for (int64_t q = b + 1; q < e && sorted; ++q) sorted = A.col[q - 1] < A.col[q];
+      if (sorted) continue;
+      tmp.clear();
+      for (int64_t q = b; q < e; ++q) tmp.push_back({A.col[q], A.val[q]});
+      std::sort(tmp.begin(), tmp.end());
+      for (int64_t q = b; q < e; ++q) {
+        A.col[q] = tmp[q - b].first;
+        A.val[q] = tmp[q - b].second;
       }
-      return A;
-    };
-    HostCSR Pc = to_csr(rows, h.nJpad), Ptc = to_csr(trows, h.npad);
-    sell_build<T>(P.P, Pc, 0, s);
-    sell_build<T>(P.PT, Ptc, 0, s);
-  }
+    }
+    return A;
+  };
+  HostCSR Pc = to_csr(h.npad, h.nJpad, false), Ptc = to_csr(h.nJpad, h.npad, true);
+  sell_build<T>(P.P, Pc, 0, s);
+  sell_build<T>(P.PT, Ptc, 0, s);
 }
 
 void build_all(asmg_s& h, cudaStream_t s) {
@@ -410,7 +422,9 @@ void build_all(asmg_s& h, cudaStream_t s) {
   h.level_rows.clear();
   h.p64.lev.clear();
   h.p32.lev.clear();
+  h.stats.t_lv_assemble = h.stats.t_lv_colour = h.stats.t_lv_pack = h.stats.t_lv_export = 0;
   for (const AuxLevelHost& L : h.aux.levels) {
+    double ta = now();
     std::vector<uint8_t> inset(h.nJ, 0);
     for (int32_t id : L.smooth) inset[id] = 1;
     TriDev T;
@@ -418,7 +432,11 @@ void build_all(asmg_s& h, cudaStream_t s) {
     DBuf<uint8_t> dkeep;
     dkeep.upload(inset, s);
     HostCSR Arows = assemble_simplices(m.dim, (int64_t)L.tri_coef.size(), T.xy.p, T.id.p, T.coef.p, dkeep.p, h.nJ, s);
+    double tb = now();
+    h.stats.t_lv_assemble += tb - ta;
     std::vector<int32_t> colour = jp_colour_gpu(Arows, inset, h.aux.aux_key, s);
+    double tc = now();
+    h.stats.t_lv_colour += tc - tb;
     // export copies
     std::vector<uint64_t> sk;
     std::vector<int32_t> sc;
@@ -436,6 +454,8 @@ void build_all(asmg_s& h, cudaStream_t s) {
         tr.v.push_back(Arows.val[p]);
       }
     h.level_rows.push_back(std::move(tr));
+    double td = now();
+    h.stats.t_lv_export += td - tc;
     if (h.prm.precision == ASMG_MIXED) {
       h.p32.lev.emplace_back();
       build_level_dev<float>(h, L, Arows, colour, inset, h.p32.lev.back(), s);
@@ -443,7 +463,9 @@ void build_all(asmg_s& h, cudaStream_t s) {
       h.p64.lev.emplace_back();
       build_level_dev<double>(h, L, Arows, colour, inset, h.p64.lev.back(), s);
     }
+    h.stats.t_lv_pack += now() - td;
   }
+  double te = now();
   // ---- coarsest level: explicit inverse of A_c (B_0 = A_0^{-1})
   h.nc = (int64_t)h.aux.coarse_id.size();
   if (h.nc > 0) {
@@ -492,13 +514,19 @@ void build_all(asmg_s& h, cudaStream_t s) {
     h.d_cinv.upload(inv, s);
     h.d_cid.upload(h.aux.coarse_id, s);
   }
+  double tf = now();
+  h.stats.t_coarse = tf - te;
   // ---- transfer and fine smoother copy
   if (h.prm.precision == ASMG_MIXED)
     build_prec<float>(h, h.p32, Aperm, dinv, s);
   else
     build_prec<double>(h, h.p64, Aperm, dinv, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  double tg = now();
+  h.stats.t_transfer = tg - tf;
   setup_solve(h, s);
   ASMG_CUDA(cudaStreamSynchronize(s));
+  h.stats.t_slots = now() - tg;
   h.stats.t_levels = now() - t2;
 }
 
@@ -980,6 +1008,13 @@ int amg_info(asmg_handle h, int what, int level, int64_t* value) {
     case 103: *value = (int64_t)(h->stats.t_aux * 1e6); break;
     case 104: *value = (int64_t)(h->stats.t_fine * 1e6); break;
     case 105: *value = (int64_t)(h->stats.t_levels * 1e6); break;
+    case 108: *value = (int64_t)(h->stats.t_lv_assemble * 1e6); break;
+    case 109: *value = (int64_t)(h->stats.t_lv_colour * 1e6); break;
+    case 110: *value = (int64_t)(h->stats.t_lv_pack * 1e6); break;
+    case 111: *value = (int64_t)(h->stats.t_lv_export * 1e6); break;
+    case 112: *value = (int64_t)(h->stats.t_coarse * 1e6); break;
+    case 113: *value = (int64_t)(h->stats.t_transfer * 1e6); break;
+    case 114: *value = (int64_t)(h->stats.t_slots * 1e6); break;
     default: ASMG_FAIL(ASMG_ERR_INVALID_ARG, "unknown info %d", what);
   }
   return ASMG_OK;

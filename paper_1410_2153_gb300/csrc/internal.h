@@ -252,6 +252,10 @@ struct AuxLevelDev {
 
 struct Stats {
   double t_tree = 0, t_aux = 0, t_fine = 0, t_levels = 0, t_total = 0;
+  // parts of t_levels: level assembly, colouring, row selection + SELL packing
+  // (+ shared-memory forms), export copies, coarsest inverse, transfer, solve state
+  double t_lv_assemble = 0, t_lv_colour = 0, t_lv_pack = 0, t_lv_export = 0, t_coarse = 0, t_transfer = 0,
+         t_slots = 0;
 };
 
 }  // namespace asmg
