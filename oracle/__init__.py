@@ -144,6 +144,10 @@ class Oracle:
     def level_tri(self, l: int):
         return self._get("level_tri", l, (self.info("ntri", l), 3), np.uint64)
 
+    def level_alltri(self, l: int):
+        """Every triangle of sigma^(l), also those outside a non-box domain."""
+        return self._get("level_alltri", l, (self.info("nalltri", l), 3), np.uint64)
+
     def level_tet(self, l: int):
         return self._get("level_tet", l, (self.info("ntet", l), 4), np.uint64)
 

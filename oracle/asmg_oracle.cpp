@@ -187,6 +187,7 @@ struct Oracle {
   int J = 0;  // finest auxiliary level (depth)
   int LB = 0; // 3D: lattice bits of the auxiliary nodes (J + 1)
   int c = 0;  // coarsest level used by the V-cycle
+  bool boxdomain = true;  // the fine elements fill the root box (else Dirichlet auxiliary grids, R17)
   std::vector<Level> lv;
   std::vector<double> finest_coef;  // per triangle of level J
   CSR P, Pfull;                     // Scott-Zhang transfer (free / all aux columns)
@@ -651,18 +652,171 @@ void leaves_overlapping(const Oracle& o, double lox, double loy, double hix, dou
   }
 }
 
+// The triangle of sigma^(l) containing the point (X3/3, Y3/3) (lattice
+// units): descend the truncated tree to the level-l box holding it, then test
+// its triangles with integer barycentric coordinates.  The point must lie
+// strictly inside a triangle (a centroid of a finer nested triangle).
+bool locate_level_triangle(const Oracle& o, int l, uint64_t X3, uint64_t Y3, std::array<uint64_t, 3>& out) {
+  int depth = 0;
+  uint64_t bx = 0, by = 0;
+  for (;;) {
+    uint64_t q[2] = {bx, by};
+    uint8_t sp = 0;
+    box_exists(o, depth, q, &sp);
+    if (depth == l || !sp) break;
+    const uint64_t half3 = 3 * (1ULL << (o.D - depth - 1));
+    const uint64_t cx = (X3 - bx * 2 * half3) >= half3 ? 1 : 0;
+    const uint64_t cy = (Y3 - by * 2 * half3) >= half3 ? 1 : 0;
+    bx = 2 * bx + cx;
+    by = 2 * by + cy;
+    ++depth;
+  }
+  std::vector<std::array<uint64_t, 3>> ktri;
+  box_triangles(o, depth, bx, by, l, ktri);
+  for (auto& kt : ktri) {
+    i128 P[3][2];
+    for (int v = 0; v < 3; ++v) {
+      uint64_t vx, vy;
+      node_xy(kt[v], vx, vy);
+      P[v][0] = 3 * (i128)vx;
+      P[v][1] = 3 * (i128)vy;
+    }
+    const i128 x = (i128)X3, y = (i128)Y3;
+    const i128 det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+    const i128 n1 = (x - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (y - P[0][1]);
+    const i128 n2 = (P[1][0] - P[0][0]) * (y - P[0][1]) - (x - P[0][0]) * (P[1][1] - P[0][1]);
+    if (n1 > 0 && n2 > 0 && det - n1 - n2 > 0) {
+      out = kt;
+      return true;
+    }
+  }
+  return false;
+}
+
+// R17: Dirichlet auxiliary grids (Sec. 3.4, Def. "Dirichlet auxiliary grids")
+// for a domain that does not fill the root box.  T^D_l keeps the triangles of
+// sigma^(l) inside Omega: the fine elements cover at least (1 - 1e-9) of their
+// area.  Coverage of the level-J triangles is clipped exactly; a coarser
+// triangle's coverage is the sum over the level-J triangles nested in it (found
+// by their centroids).  Returns, per level, the inside triangles.
+void dirichlet_triangles(Oracle& o, std::vector<std::vector<std::array<uint64_t, 3>>>& inside) {
+  const int J = o.J;
+  std::vector<std::array<uint64_t, 3>> tJ;
+  level_triangles(o, J, tJ);
+  std::map<std::array<uint64_t, 3>, int64_t> idx;
+  for (size_t t = 0; t < tJ.size(); ++t) idx[tJ[t]] = (int64_t)t;
+  std::vector<double> cov(tJ.size(), 0.0);
+  std::vector<std::array<uint64_t, 3>> leaves, ktri;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    Pt T[3];
+    for (int k = 0; k < 3; ++k) T[k] = Pt{o.X[(int64_t)o.E[3 * e + k] * 2], o.X[(int64_t)o.E[3 * e + k] * 2 + 1]};
+    double lox = std::min({T[0].x, T[1].x, T[2].x}), hix = std::max({T[0].x, T[1].x, T[2].x});
+    double loy = std::min({T[0].y, T[1].y, T[2].y}), hiy = std::max({T[0].y, T[1].y, T[2].y});
+    leaves.clear();
+    leaves_overlapping(o, lox, loy, hix, hiy, leaves);
+    std::vector<Pt> poly(T, T + 3);
+    for (auto& b : leaves) {
+      ktri.clear();
+      box_triangles(o, (int)b[0], b[1], b[2], J, ktri);
+      for (auto& kt : ktri) {
+        Pt K[3];
+        for (int k = 0; k < 3; ++k) {
+          double p[2];
+          physical(o, kt[k], p);
+          K[k] = Pt{p[0], p[1]};
+        }
+        auto cp = clip(poly, K);
+        if (cp.size() < 3) continue;
+        cov[idx.at(kt)] += poly_area(cp);
+      }
+    }
+  }
+  auto area_of = [&](const std::array<uint64_t, 3>& t) {
+    double p0[2], p1[2], p2[2];
+    physical(o, t[0], p0);
+    physical(o, t[1], p1);
+    physical(o, t[2], p2);
+    return 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]));
+  };
+  inside.assign(J + 1, {});
+  for (int l = 0; l <= J; ++l) {
+    std::vector<std::array<uint64_t, 3>> tl;
+    level_triangles(o, l, tl);
+    std::map<std::array<uint64_t, 3>, double> cl;
+    if (l == J) {
+      for (size_t t = 0; t < tJ.size(); ++t) cl[tJ[t]] = cov[t];
+    } else {
+      for (size_t t = 0; t < tJ.size(); ++t) {
+        uint64_t X3 = 0, Y3 = 0;
+        for (int v = 0; v < 3; ++v) {
+          uint64_t x, y;
+          node_xy(tJ[t][v], x, y);
+          X3 += x;
+          Y3 += y;
+        }
+        std::array<uint64_t, 3> anc;
+        if (!locate_level_triangle(o, l, X3, Y3, anc)) {
+          o.err = "oracle: nested triangle not located";
+          return;
+        }
+        cl[anc] += cov[t];
+      }
+    }
+    for (auto& t : tl)
+      if (cl[t] >= (1.0 - 1e-9) * area_of(t)) inside[l].push_back(t);
+  }
+}
+
 void build_aux(Oracle& o) {
   const int J = o.J;
   o.lv.assign(J + 1, Level());
+  // does the domain fill the root box?
+  {
+    double area = 0.0;
+    for (int64_t e = 0; e < o.ne; ++e) {
+      const double* p0 = &o.X[(int64_t)o.E[3 * e] * 2];
+      const double* p1 = &o.X[(int64_t)o.E[3 * e + 1] * 2];
+      const double* p2 = &o.X[(int64_t)o.E[3 * e + 2] * 2];
+      area += 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]));
+    }
+    o.boxdomain = std::fabs(area - o.L * o.L) <= 1e-12 * o.L * o.L;
+  }
+  std::vector<std::vector<std::array<uint64_t, 3>>> inside;
+  if (!o.boxdomain) {
+    dirichlet_triangles(o, inside);
+    if (!o.err.empty()) return;
+  }
   for (int l = 0; l <= J; ++l) {
     Level& L = o.lv[l];
-    level_triangles(o, l, L.tri);
+    if (o.boxdomain)
+      level_triangles(o, l, L.tri);
+    else
+      L.tri = inside[l];
     for (auto& t : L.tri)
       for (int k = 0; k < 3; ++k) L.allkey.push_back(t[k]);
     std::sort(L.allkey.begin(), L.allkey.end());
     L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
-    for (auto k : L.allkey)
-      if (!on_boundary(o, k)) L.key.push_back(k);
+    if (o.boxdomain) {
+      for (auto k : L.allkey)
+        if (!on_boundary(o, k)) L.key.push_back(k);
+    } else {
+      // Gamma_l = boundary of the union of T^D_l: endpoints of edges that
+      // belong to one triangle only
+      std::map<std::pair<uint64_t, uint64_t>, int> edges;
+      for (auto& t : L.tri)
+        for (int k = 0; k < 3; ++k) {
+          uint64_t a = t[k], b = t[(k + 1) % 3];
+          edges[{std::min(a, b), std::max(a, b)}] += 1;
+        }
+      std::set<uint64_t> gamma;
+      for (auto& kv : edges)
+        if (kv.second == 1) {
+          gamma.insert(kv.first.first);
+          gamma.insert(kv.first.second);
+        }
+      for (auto k : L.allkey)
+        if (!gamma.count(k)) L.key.push_back(k);
+    }
   }
   // coarsest level used: the finest level with at most coarse_max free nodes
   o.c = 0;
@@ -697,7 +851,9 @@ void build_aux(Oracle& o) {
         }
         auto cp = clip(poly, K);
         if (cp.size() < 3) continue;
-        num[tri_index.at(kt)] += a * poly_area(cp);
+        auto it = tri_index.find(kt);
+        if (it == tri_index.end()) continue;  // outside Omega (not in T^D_J)
+        num[it->second] += a * poly_area(cp);
       }
     }
   }
@@ -851,6 +1007,7 @@ void build_transfer(Oracle& o) {
     }
   std::vector<std::vector<std::pair<int32_t, double>>> rows(n), rows_full(n);
   std::vector<std::array<uint64_t, 3>> leaves, ktri;
+  std::set<std::array<uint64_t, 3>> tri_in(LJ.tri.begin(), LJ.tri.end());
   for (int64_t i = 0; i < n; ++i) {
     int32_t v = o.vertex_of_free[i];
     int32_t e = sigma[v];
@@ -871,6 +1028,7 @@ void build_transfer(Oracle& o) {
       ktri.clear();
       box_triangles(o, (int)b[0], b[1], b[2], o.J, ktri);
       for (auto& kt : ktri) {
+        if (!o.boxdomain && !tri_in.count(kt)) continue;  // aux hat functions vanish outside Omega^D_J
         Pt K[3];
         for (int k = 0; k < 3; ++k) {
           double p[2];
@@ -1904,6 +2062,11 @@ int64_t orc_info(void* h, const char* what, int l) {
   if (w == "nlevel") return (int64_t)o.lv.at(l).key.size();
   if (w == "nall") return (int64_t)o.lv.at(l).allkey.size();
   if (w == "ntri") return (int64_t)o.lv.at(l).tri.size();
+  if (w == "nalltri") {
+    std::vector<std::array<uint64_t, 3>> t;
+    level_triangles(o, l, t);
+    return (int64_t)t.size();
+  }
   if (w == "ntet") return (int64_t)o.lv.at(l).tet.size();
   if (w == "LB") return o.LB;
   if (w == "nnzA") return l < 0 ? (int64_t)o.A.col.size() : (int64_t)o.lv.at(l).A.col.size();
@@ -1946,6 +2109,12 @@ int orc_get(void* h, const char* what, int l, void* out) {
   if (w == "level_key") { memcpy(out, o.lv.at(l).key.data(), o.lv[l].key.size() * 8); return 0; }
   if (w == "level_allkey") { memcpy(out, o.lv.at(l).allkey.data(), o.lv[l].allkey.size() * 8); return 0; }
   if (w == "level_tri") { memcpy(out, o.lv.at(l).tri.data(), o.lv[l].tri.size() * 24); return 0; }
+  if (w == "level_alltri") {  // every triangle of sigma^(l), inside Omega or not
+    std::vector<std::array<uint64_t, 3>> t;
+    level_triangles(o, l, t);
+    memcpy(out, t.data(), t.size() * 24);
+    return 0;
+  }
   if (w == "level_tet") { memcpy(out, o.lv.at(l).tet.data(), o.lv[l].tet.size() * 32); return 0; }
   if (w == "finest_coef") { memcpy(out, o.finest_coef.data(), o.finest_coef.size() * 8); return 0; }
   if (w == "smooth") {

@@ -203,6 +203,37 @@ def centroids(mesh: Mesh) -> np.ndarray:
     return mesh.verts[mesh.elems].mean(axis=1)
 
 
+def grid2d_domain(nside: int, seed: int, shape: str = "L", jitter: float = 0.2) -> Mesh:
+    """A non-box domain cut from ``grid2d(nside, seed, jitter)``.
+
+    shape "L": the elements whose centroid lies in (1/2, 1]^2 are removed (an
+    L-shaped domain); "hole": those with centroid within 1/4 (max norm) of
+    (1/2, 1/2) are removed (a square with a square hole).  Jittered vertices
+    make the cut boundaries jagged.  Unused vertices are dropped; every vertex
+    on a boundary edge (an edge of one element only) is Dirichlet.  The bounding
+    box stays [0,1]^2.
+    """
+    m = grid2d(nside, seed, jitter=jitter)
+    c = centroids(m)
+    if shape == "L":
+        drop = (c[:, 0] > 0.5) & (c[:, 1] > 0.5)
+    elif shape == "hole":
+        drop = (np.abs(c[:, 0] - 0.5) < 0.25) & (np.abs(c[:, 1] - 0.5) < 0.25)
+    else:
+        raise ValueError(shape)
+    E = m.elems[~drop]
+    used = np.unique(E)
+    remap = -np.ones(m.nv, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    E = remap[E].astype(np.int32)
+    V = m.verts[used]
+    ed = np.sort(np.concatenate([E[:, [0, 1]], E[:, [1, 2]], E[:, [2, 0]]]), axis=1)
+    uniq, cnt = np.unique(ed, axis=0, return_counts=True)
+    bflag = np.zeros(V.shape[0], dtype=np.uint8)
+    bflag[np.unique(uniq[cnt == 1])] = DIRICHLET
+    return Mesh(2, V, E, bflag, None, dict(kind="grid2d_domain", nside=nside, seed=seed, shape=shape, jitter=jitter))
+
+
 def nodal_uniform(mesh: Mesh, seed: int, k: int = 1) -> np.ndarray:
     """Nodal source values U[-1, 1], shape [nv] (k=1) or [k, nv]; 0 on Dirichlet vertices."""
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -803,3 +803,136 @@ def test_asmg_iteration_rates_bounded_and_mesh_independent(gen):
         assert np.linalg.norm(b - o.spmv(u)) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-12)
     assert max(rates) <= 0.4, rates
     assert max(rates) <= 2.5 * min(rates), rates
+
+
+# --------------------------------------------------------------------------
+# Domains that do not fill the root box: Dirichlet auxiliary grids
+# T^D_l = {tau in sigma^(l) | tau in Omega} (Sec. 3.4), checked against an
+# independent computation of each triangle's coverage by the fine elements
+# (polygon clipping written here) and of each node's interior angle sum.
+# --------------------------------------------------------------------------
+
+def _clip_poly(poly, tri):
+    # Sutherland-Hodgman: poly (list of (x, y)) cut by the three half-planes of a CCW triangle
+    out = poly
+    for k in range(3):
+        ax, ay = tri[k]
+        bx, by = tri[(k + 1) % 3]
+        inp, out = out, []
+        if not inp:
+            break
+        side = lambda p: (bx - ax) * (p[1] - ay) - (by - ay) * (p[0] - ax)
+        for i in range(len(inp)):
+            p, q = inp[i], inp[(i + 1) % len(inp)]
+            sp, sq = side(p), side(q)
+            if sp >= 0:
+                out.append(p)
+            if (sp >= 0) != (sq >= 0):
+                t = sp / (sp - sq)
+                out.append((p[0] + t * (q[0] - p[0]), p[1] + t * (q[1] - p[1])))
+    return out
+
+
+def _area(poly):
+    return 0.5 * sum(poly[i][0] * poly[(i + 1) % len(poly)][1] - poly[(i + 1) % len(poly)][0] * poly[i][1]
+                     for i in range(len(poly))) if len(poly) >= 3 else 0.0
+
+
+@pytest.fixture(scope="module")
+def lshape(gen):
+    m = gen.grid2d_domain(17, 3, "L")
+    return m, oracle.Oracle(m)
+
+
+def _lattice_pts(o, keys):
+    x, y = oracle.lattice_xy(keys)
+    a0, a1, _, L = o.root()
+    return a0 + np.ldexp(x.astype(np.float64), -31) * L, a1 + np.ldexp(y.astype(np.float64), -31) * L
+
+
+def test_dirichlet_aux_triangles_are_those_inside_omega(gen, lshape):
+    m, o = lshape
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    boxarea = 1.0
+    for l in range(o.J + 1):
+        # every triangle of sigma^(l): the inside ones are the oracle's level triangles; the
+        # others are found from the full box triangulation of the oracle run on the square
+        tri = o.level_tri(l)
+        X, Y = _lattice_pts(o, tri.reshape(-1))
+        X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+        tot = 0.0
+        for t in range(tri.shape[0]):
+            T = [(X[t, k], Y[t, k]) for k in range(3)]
+            a = _area(T)
+            tot += a
+            tlo, thi = np.array([X[t].min(), Y[t].min()]), np.array([X[t].max(), Y[t].max()])
+            sel = np.where(np.all(lo <= thi, axis=1) & np.all(hi >= tlo, axis=1))[0]
+            cov = sum(_area(_clip_poly([tuple(p) for p in E[e]], T)) for e in sel)
+            assert cov >= (1 - 1e-9) * a, (l, t, cov, a)       # inside Omega
+        # Omega^D_l grows with l and stays inside Omega
+        assert tot <= 0.75 * boxarea * (1 + 1e-9) + 0.05
+        if l:
+            assert tot >= prev - 1e-12
+        prev = tot
+
+
+def test_dirichlet_aux_grids_are_maximal(gen, lshape):
+    # the triangles of sigma^(l) left out are not covered by the fine elements
+    m, o = lshape
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    for l in range(o.J + 1):
+        inside = set(map(tuple, o.level_tri(l).tolist()))
+        tri = o.level_alltri(l)
+        X, Y = _lattice_pts(o, tri.reshape(-1))
+        X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+        left_out = 0
+        for t in range(tri.shape[0]):
+            if tuple(tri[t].tolist()) in inside:
+                continue
+            left_out += 1
+            T = [(X[t, k], Y[t, k]) for k in range(3)]
+            tlo, thi = np.array([X[t].min(), Y[t].min()]), np.array([X[t].max(), Y[t].max()])
+            sel = np.where(np.all(lo <= thi, axis=1) & np.all(hi >= tlo, axis=1))[0]
+            cov = sum(_area(_clip_poly([tuple(p) for p in E[e]], T)) for e in sel)
+            assert cov < (1 - 1e-9) * _area(T), (l, t)
+        assert left_out > 0
+
+
+def test_dirichlet_free_nodes_are_interior_by_angle_sum(lshape):
+    # a node of T^D_J is free exactly when the inside triangles around it close
+    # up (interior angles sum to 2 pi)
+    m, o = lshape
+    tri = o.level_tri(o.J)
+    X, Y = _lattice_pts(o, tri.reshape(-1))
+    X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+    ang = {}
+    for t in range(tri.shape[0]):
+        for k in range(3):
+            p = np.array([X[t, k], Y[t, k]])
+            u = np.array([X[t, (k + 1) % 3], Y[t, (k + 1) % 3]]) - p
+            v = np.array([X[t, (k + 2) % 3], Y[t, (k + 2) % 3]]) - p
+            a = np.arccos(np.clip(u @ v / np.linalg.norm(u) / np.linalg.norm(v), -1, 1))
+            ang[int(tri[t, k])] = ang.get(int(tri[t, k]), 0.0) + a
+    free = set(int(k) for k in o.level_keys(o.J))
+    interior = set(k for k, a in ang.items() if abs(a - 2 * np.pi) < 1e-9)
+    assert free == interior
+
+
+@pytest.mark.parametrize("shape", ["L", "hole"])
+def test_dirichlet_domain_pcg_dense_and_spd(gen, shape):
+    m = gen.grid2d_domain(17, 5, shape)
+    o = oracle.Oracle(m, coarse_max=8)
+    assert o.c < o.J
+    b = o.mass_apply(gen.nodal_uniform(m, 2))
+    u, st, it, _ = o.solve(b, rtol=1e-13)
+    ref = np.linalg.solve(o.A().toarray(), b)
+    assert st == 0 and np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+    n = o.nfree
+    B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    # nested Dirichlet hierarchies: every level's free nodes are free on the finer levels
+    for l in range(o.c + 1, o.J + 1):
+        assert set(o.level_keys(l - 1).tolist()) <= set(o.level_keys(l).tolist())
