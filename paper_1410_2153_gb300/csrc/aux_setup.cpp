@@ -291,28 +291,6 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   std::vector<std::vector<uint64_t>> BX(J + 1);  // boxes per depth, ascending prefix
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
 
-  // ---- finest-level nodes (aux unknowns)
-  {
-    std::vector<std::pair<int, uint64_t>> leaves;
-    for (int d = 0; d <= J; ++d)
-      for (uint64_t p : BX[d])
-        if (!T.split(d, p)) leaves.push_back({d, p});
-    std::vector<std::vector<uint64_t>> part(MAX_THREADS);
-    parallel_for((int64_t)leaves.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
-      std::vector<std::array<uint64_t, 3>> tri;
-      for (int64_t q = b0; q < b1; ++q) {
-        bool h[4];
-        T.hanging(leaves[q].first, leaves[q].second, h);
-        tri.clear();
-        box_tris(T, leaves[q].first, leaves[q].second, h, tri);
-        for (auto& x : tri)
-          for (int k = 0; k < 3; ++k)
-            if (!boundary_key(T, x[k])) part[t].push_back(x[k]);
-      }
-    });
-    out.aux_key = merge_unique(part);
-  }
-  const std::vector<uint64_t>& AK = out.aux_key;
 
   // ---- per level: changed boxes, new nodes and their parents, level sizes
   struct LevelInfo {
@@ -374,25 +352,25 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     for (auto& x : th) x.join();
   }
   for (int l = 1; l <= J; ++l) out.nlevel[l] = out.nlevel[l - 1] + nfree_new[l];
-  // coarsest level used: finest level with at most coarse_max_dofs free nodes
-  out.c = 0;
-  for (int l = 0; l <= J; ++l)
-    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
-  const int c = out.c;
 
   // ---- finest auxiliary coefficient: area-weighted mean of the fine
   // coefficients (exact clipping), accumulated per box half for coarser levels
   const bool varcoef = !mesh.coeff.empty();
+  // R17: a domain that does not fill the root box uses the Dirichlet
+  // auxiliary grids T^D_l (triangles inside Omega); the same clipping pass
+  // then also measures how much of each triangle the fine elements cover
+  const bool dgrid = !mesh.boxdomain;
   // integral of a over the lower-right (0) / upper-left (1) diagonal halves
-  // of every box, per depth, aligned with boxes_at(T, d)
-  std::vector<std::vector<std::array<double, 2>>> half(J + 1);
+  // of every box, per depth, aligned with boxes_at(T, d); the covered area
+  // of the same halves
+  std::vector<std::vector<std::array<double, 2>>> half(J + 1), halfcov(J + 1);
   // integrals over the fan triangles of fanned leaves (key: sorted triangle)
-  std::vector<std::pair<std::array<uint64_t, 3>, double>> fanint;
+  std::vector<std::pair<std::array<uint64_t, 3>, double>> fanint, fancov;
   auto tri_sorted = [](std::array<uint64_t, 3> t) {
     std::sort(t.begin(), t.end());
     return t;
   };
-  if (varcoef) {
+  if (varcoef || dgrid) {
     // finest triangles, indexed by leaf order
     std::vector<std::array<uint64_t, 3>> ftri;
     std::vector<std::vector<int64_t>> first(J + 1);
@@ -408,7 +386,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       }
     }
     // clip every fine element against the finest triangles it meets
-    std::vector<std::vector<std::pair<int64_t, double>>> contrib(64);
+    std::vector<std::vector<std::pair<int64_t, double>>> contrib(64), ccontrib(64);
     parallel_for(mesh.ne, [&](unsigned t, unsigned, int64_t b, int64_t e) {
       auto& mine = contrib[t];
       std::vector<std::pair<int, uint64_t>> lv;
@@ -450,19 +428,29 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
             double M[6];
             moments(poly, m, M);
             if (!(M[0] > 0)) continue;
-            mine.push_back({f0 + (int64_t)q, M[0] * mesh.coeff[el]});
+            if (varcoef) mine.push_back({f0 + (int64_t)q, M[0] * mesh.coeff[el]});
+            if (dgrid) ccontrib[t].push_back({f0 + (int64_t)q, M[0]});
           }
         }
       }
     });
     // reduce into finest-triangle integrals (fixed order: thread, then element)
-    std::vector<double> I(ftri.size(), 0.0);
+    std::vector<double> I(ftri.size(), 0.0), C(ftri.size(), 0.0);
     for (auto& v : contrib)
       for (auto& pr : v) I[pr.first] += pr.second;
-    // box-half integrals, bottom-up
+    for (auto& v : ccontrib)
+      for (auto& pr : v) C[pr.first] += pr.second;
+    // box-half integrals, bottom-up: a (half, fanint) and the covered area
+    // (halfcov, fancov)
+    for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 0 && !varcoef) continue;
+    if (pass == 1 && !dgrid) continue;
+    const std::vector<double>& IA = pass == 0 ? I : C;
+    auto& H = pass == 0 ? half : halfcov;
+    auto& FI = pass == 0 ? fanint : fancov;
     for (int d = J; d >= 0; --d) {
       const auto& bx = BX[d];
-      half[d].assign(bx.size(), {0.0, 0.0});
+      H[d].assign(bx.size(), {0.0, 0.0});
       for (size_t i = 0; i < bx.size(); ++i) {
         uint64_t p = bx[i];
         if (!T.split(d, p)) {
@@ -472,7 +460,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
           box_tris(T, d, p, h, kt);
           const int64_t f0 = first[d][i];
           if (!(h[0] || h[1] || h[2] || h[3])) {
-            half[d][i] = {I[f0], I[f0 + 1]};
+            H[d][i] = {IA[f0], IA[f0 + 1]};
           } else {
             // fan triangles on the S and E edges form the lower-right half
             const uint64_t s = 1ULL << (T.D - d);
@@ -481,25 +469,154 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
               uint64_t ax = compact(kt[k][0]), ay = compact(kt[k][0] >> 1);
               uint64_t bxx = compact(kt[k][1]), by = compact(kt[k][1] >> 1);
               bool lr = (ay == y0 && by == y0) || (ax == x0 + s && bxx == x0 + s);
-              half[d][i][lr ? 0 : 1] += I[f0 + k];
-              fanint.push_back({tri_sorted(kt[k]), I[f0 + k]});
+              H[d][i][lr ? 0 : 1] += IA[f0 + k];
+              FI.push_back({tri_sorted(kt[k]), IA[f0 + k]});
             }
           }
         } else {
           const auto& ch = BX[d + 1];
           size_t j = std::lower_bound(ch.begin(), ch.end(), p << 2) - ch.begin();
           // children: 0 SW, 1 SE, 2 NW, 3 NE (bit 0 = x, bit 1 = y)
-          const auto& sw = half[d + 1][j];
-          const auto& se = half[d + 1][j + 1];
-          const auto& nw = half[d + 1][j + 2];
-          const auto& ne = half[d + 1][j + 3];
-          half[d][i][0] = sw[0] + se[0] + se[1] + ne[0];
-          half[d][i][1] = sw[1] + nw[0] + nw[1] + ne[1];
+          const auto& sw = H[d + 1][j];
+          const auto& se = H[d + 1][j + 1];
+          const auto& nw = H[d + 1][j + 2];
+          const auto& ne = H[d + 1][j + 3];
+          H[d][i][0] = sw[0] + se[0] + se[1] + ne[0];
+          H[d][i][1] = sw[1] + nw[0] + nw[1] + ne[1];
         }
       }
     }
+    }
     std::sort(fanint.begin(), fanint.end());
+    std::sort(fancov.begin(), fancov.end());
   }
+  // covered area of one triangle of box (d, p) at a level where the box
+  // shows as diagonal split (k = 0 lower-right, 1 upper-left) or as fan; the
+  // triangle belongs to T^D_l when the fine elements cover (1 - 1e-9) of it
+  auto tri_area = [&](const std::array<uint64_t, 3>& t) {
+    double pa[2], pb[2], pc[2];
+    lattice_point(tree, t[0], pa);
+    lattice_point(tree, t[1], pb);
+    lattice_point(tree, t[2], pc);
+    return 0.5 * ((pb[0] - pa[0]) * (pc[1] - pa[1]) - (pc[0] - pa[0]) * (pb[1] - pa[1]));
+  };
+  auto tri_inside = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> bool {
+    if (!dgrid) return true;
+    double cov;
+    if (diag) {
+      const auto& bx = BX[d];
+      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      cov = halfcov[d][i][k];
+    } else {
+      auto it = std::lower_bound(fancov.begin(), fancov.end(),
+                                 std::pair<std::array<uint64_t, 3>, double>(tri_sorted(t), -HUGE_VAL));
+      cov = it->second;
+    }
+    return cov >= (1.0 - 1e-9) * tri_area(t);
+  };
+  // node x is free at level l (a vertex of sigma^(l) off the boundary of
+  // Omega^D_l): every level-l triangle around it is inside.  The box shown
+  // at level l around x in each quadrant holds those triangles.
+  auto free_at = [&](uint64_t x, int l, std::vector<std::array<uint64_t, 3>>& kt) -> bool {
+    if (boundary_key(T, x)) return false;
+    const uint64_t X = compact(x), Y = compact(x >> 1);
+    bool node = false;
+    for (int q = 0; q < 4; ++q) {
+      const bool px = q & 1, py = q & 2;
+      int d = 0;
+      uint64_t p = 0;
+      while (d < l && T.split(d, p)) {
+        const uint64_t sz = 1ULL << (T.D - d), hf = sz >> 1;
+        const uint64_t x0 = compact(p) * sz, y0 = compact(p >> 1) * sz;
+        const uint64_t cx = px ? (X >= x0 + hf) : (X > x0 + hf);
+        const uint64_t cy = py ? (Y >= y0 + hf) : (Y > y0 + hf);
+        p = (p << 2) | (cy << 1) | cx;
+        ++d;
+      }
+      bool h[4] = {false, false, false, false};
+      if (d < l) T.hanging(d, p, h);
+      kt.clear();
+      box_tris(T, d, p, h, kt);
+      const bool diag = !(h[0] || h[1] || h[2] || h[3]);
+      for (size_t k = 0; k < kt.size(); ++k) {
+        if (kt[k][0] != x && kt[k][1] != x && kt[k][2] != x) continue;
+        node = true;
+        if (!tri_inside(d, p, diag, (int)k, kt[k])) return false;
+      }
+    }
+    return node;
+  };
+
+  // ---- finest-level nodes (aux unknowns): free at level J
+  {
+    std::vector<std::pair<int, uint64_t>> leaves;
+    for (int d = 0; d <= J; ++d)
+      for (uint64_t p : BX[d])
+        if (!T.split(d, p)) leaves.push_back({d, p});
+    std::vector<std::vector<uint64_t>> part(MAX_THREADS);
+    parallel_for((int64_t)leaves.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::array<uint64_t, 3>> tri;
+      for (int64_t q = b0; q < b1; ++q) {
+        bool h[4];
+        T.hanging(leaves[q].first, leaves[q].second, h);
+        tri.clear();
+        box_tris(T, leaves[q].first, leaves[q].second, h, tri);
+        for (auto& x : tri)
+          for (int k = 0; k < 3; ++k)
+            if (!boundary_key(T, x[k])) part[t].push_back(x[k]);
+      }
+    });
+    out.aux_key = merge_unique(part);
+  }
+  if (dgrid) {
+    // keep the vertices of inside level-J triangles that are free at J
+    std::vector<int32_t> keep(out.aux_key.size(), 0);
+    parallel_for((int64_t)out.aux_key.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::array<uint64_t, 3>> kt;
+      for (int64_t q = b0; q < b1; ++q) keep[q] = free_at(out.aux_key[q], J, kt);
+    });
+    std::vector<uint64_t> ak;
+    for (size_t q = 0; q < keep.size(); ++q)
+      if (keep[q]) ak.push_back(out.aux_key[q]);
+    out.aux_key.swap(ak);
+  }
+  const std::vector<uint64_t>& AK = out.aux_key;
+  // first level at which each node is free: its birth level in a box domain;
+  // with T^D_l the first level from its birth on whose triangles around it
+  // are all inside (free at one level, free at all finer ones)
+  std::vector<int32_t> phi;
+  if (dgrid) {
+    std::vector<std::pair<uint64_t, int32_t>> born;
+    for (int l = 1; l <= J; ++l)
+      for (auto& v : newnodes[l]) born.push_back({v[0], l});
+    std::sort(born.begin(), born.end());
+    phi.assign(AK.size(), J + 1);
+    parallel_for((int64_t)AK.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::array<uint64_t, 3>> kt;
+      for (int64_t q = b0; q < b1; ++q) {
+        auto it = std::lower_bound(born.begin(), born.end(), std::pair<uint64_t, int32_t>(AK[q], 0));
+        int l = (it != born.end() && it->first == AK[q]) ? it->second : 0;
+        while (l < J && !free_at(AK[q], l, kt)) ++l;
+        phi[q] = l;
+      }
+    });
+    out.nlevel.assign(J + 1, 0);
+    for (int32_t f : phi) out.nlevel[f] += 1;
+    for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
+  }
+  // aux ID of node x at level l, or -1 where it is not a free node there
+  auto level_id = [&](uint64_t x, int l) -> int32_t {
+    if (boundary_key(T, x)) return -1;
+    const int32_t id = id_of(AK, x);
+    if (dgrid && (id < 0 || phi[id] > l)) return -1;
+    return id;
+  };
+  // coarsest level used: finest level with at most coarse_max_dofs free nodes
+  out.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  const int c = out.c;
+
   // coefficient of one triangle of box (d, p) at a level where the box shows
   // as diagonal split (k = 0 lower-right, 1 upper-left) or as fan
   auto tri_coef = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> double {
@@ -531,9 +648,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     box_tris(T, d, p, h, kt);
     bool diag = !(h[0] || h[1] || h[2] || h[3]);
     for (size_t k = 0; k < kt.size(); ++k) {
+      if (!tri_inside(d, p, diag, (int)k, kt[k])) continue;  // outside Omega: not in T^D_l
       for (int v = 0; v < 3; ++v) {
         keys.push_back(kt[k][v]);
-        ids.push_back(boundary_key(T, kt[k][v]) ? -1 : id_of(AK, kt[k][v]));
+        ids.push_back(level_id(kt[k][v], l));
       }
       coef.push_back(tri_coef(d, p, diag, (int)k, kt[k]));
     }
@@ -585,7 +703,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
           box_tris(T, dd, rel[q].second, h, kt);
           for (auto& x : kt)
             for (int v = 0; v < 3; ++v)
-              if (!boundary_key(T, x[v])) part[t].push_back(x[v]);
+              if (level_id(x[v], l) >= 0) part[t].push_back(x[v]);
         }
       });
       sm = merge_unique(part);
@@ -598,17 +716,39 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       parallel_for((int64_t)changed.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
         auto& M = spart[t];
         auto& R = rpart[t];
+        std::vector<std::array<uint64_t, 3>> kt;
         for (int64_t q = b0; q < b1; ++q) {
           const uint64_t p = changed[q];
           const uint64_t x0 = compact(p) * s, y0 = compact(p >> 1) * s, m = s >> 1;
           const bool sp = T.split(d, p);
-          for (int iy = 0; iy <= 2; ++iy)
-            for (int ix = 0; ix <= 2; ++ix) {
-              bool mid = (ix == 1) || (iy == 1);
-              if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
-              uint64_t k = mort(x0 + ix * m, y0 + iy * m);
-              if (!boundary_key(T, k)) M.push_back(k);
+          if (!dgrid) {
+            for (int iy = 0; iy <= 2; ++iy)
+              for (int ix = 0; ix <= 2; ++ix) {
+                bool mid = (ix == 1) || (iy == 1);
+                if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
+                uint64_t k = mort(x0 + ix * m, y0 + iy * m);
+                if (!boundary_key(T, k)) M.push_back(k);
+              }
+          } else {
+            // free vertices of the box's new triangles that lie inside Omega
+            auto add_inside = [&](int dd, uint64_t pp, const bool* h) {
+              kt.clear();
+              box_tris(T, dd, pp, h, kt);
+              const bool diag = !(h[0] || h[1] || h[2] || h[3]);
+              for (size_t k = 0; k < kt.size(); ++k) {
+                if (!tri_inside(dd, pp, diag, (int)k, kt[k])) continue;
+                for (int v = 0; v < 3; ++v)
+                  if (level_id(kt[k][v], l) >= 0) M.push_back(kt[k][v]);
+              }
+            };
+            bool h[4] = {false, false, false, false};
+            if (sp) {
+              for (uint64_t ch = 0; ch < 4; ++ch) add_inside(d + 1, (p << 2) | ch, h);
+            } else {
+              T.hanging(d, p, h);
+              add_inside(d, p, h);
             }
+          }
           if (sp) {
             for (uint64_t ch = 0; ch < 4; ++ch) R.push_back({d + 1, (p << 2) | ch});
           } else {
@@ -654,11 +794,27 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
     }
     // new nodes with their parents
-    for (auto& v : newnodes[l]) {
-      if (boundary_key(T, v[0])) continue;
-      L.new_id.push_back(id_of(AK, v[0]));
-      L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
-      L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
+    if (!dgrid) {
+      for (auto& v : newnodes[l]) {
+        if (boundary_key(T, v[0])) continue;
+        L.new_id.push_back(id_of(AK, v[0]));
+        L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
+        L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
+      }
+    } else {
+      // nodes free from level l on: born at l, the interpolant of the
+      // level-(l-1) function at the edge midpoint (a parent off the free
+      // nodes of l-1 contributes 0); born earlier on the boundary of
+      // Omega^D_(l-1), where that function vanishes: no parents
+      const auto& nn = newnodes[l];
+      for (size_t q = 0; q < AK.size(); ++q) {
+        if (phi[q] != l) continue;
+        auto it = std::lower_bound(nn.begin(), nn.end(), std::array<uint64_t, 3>{AK[q], 0, 0});
+        const bool born = it != nn.end() && (*it)[0] == AK[q];
+        L.new_id.push_back((int32_t)q);
+        L.new_p0.push_back(born ? level_id((*it)[1], l - 1) : -1);
+        L.new_p1.push_back(born ? level_id((*it)[2], l - 1) : -1);
+      }
     }
   }
 
@@ -708,7 +864,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
         T.hanging(lf.first, lf.second, h);
         kt.clear();
         box_tris(T, lf.first, lf.second, h, kt);
-        for (auto& k3 : kt) {
+        const bool diag = !(h[0] || h[1] || h[2] || h[3]);
+        for (size_t q = 0; q < kt.size(); ++q) {
+          const auto& k3 = kt[q];
+          if (!tri_inside(lf.first, lf.second, diag, (int)q, k3)) continue;  // hats vanish outside Omega^D_J
           V2 K[3];
           for (int k = 0; k < 3; ++k) {
             double p[2];
@@ -722,10 +881,11 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
           moments(poly, m, M);
           if (!(M[0] > 0)) continue;
           for (int k = 0; k < 3; ++k) {
-            if (boundary_key(T, k3[k])) continue;
-            double phi[3];
-            bary_affine(K, k, phi);
-            row.push_back({id_of(AK, k3[k]), prod_int(psi, phi, M)});
+            const int32_t col = level_id(k3[k], J);
+            if (col < 0) continue;
+            double lam3[3];
+            bary_affine(K, k, lam3);
+            row.push_back({col, prod_int(psi, lam3, M)});
           }
         }
       }

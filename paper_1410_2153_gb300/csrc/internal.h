@@ -153,6 +153,7 @@ struct MeshHost {
   std::vector<int32_t> E;
   std::vector<uint8_t> bflag;
   std::vector<double> coeff;  // empty: a = 1
+  bool boxdomain = true;      // the elements fill the root box (else Dirichlet auxiliary grids, 2D)
 };
 
 // closure of the cluster tree, auxiliary grids and the Scott-Zhang transfer

@@ -1,0 +1,157 @@
+"""Parity of the CUDA path with the CPU oracle on 2D domains that do not fill
+the root box: an L-shaped domain and a square with a square hole, cut from
+jittered grids so that the cut boundaries are jagged.  The auxiliary grids are
+then the Dirichlet grids of Sec. 3.4: the triangles of sigma^(l) that the fine
+elements cover, with the nodes on the boundary of their union held at zero.
+
+Integer work (keys, tree, closure, the free nodes of every level, smoothing
+sets, colourings) must be bit-exact; floating point as in the box-domain
+parity tests: fine A and level operators 1e-12 of the largest entry, P 1e-11
+absolute, one B_co application 1e-11 relative, FP64 solutions 1e-10 relative
+with iterations within 2, mixed solutions 1e-6 relative with iterations within
+2.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_1410_2153_gb300 import asmg
+    assert torch.cuda.is_available()
+    asmg.lib()
+    return asmg
+
+
+def _meshes(gen):
+    lj = gen.grid2d_domain(65, 3, "L")
+    lj.coeff = np.exp(np.random.default_rng(7).normal(size=lj.ne))     # lognormal element coefficient
+    # (mesh, oracle parameters, library parameters)
+    return {
+        "L65": (gen.grid2d_domain(65, 1, "L"), {}, {}),
+        "hole65": (gen.grid2d_domain(65, 2, "hole"), {}, {}),
+        "L65_lognormal": (lj, {}, {}),
+        "hole129_c40": (gen.grid2d_domain(129, 4, "hole"), {"coarse_max": 40}, {"coarse_max_dofs": 40}),
+        "L97_all": (gen.grid2d_domain(97, 5, "L"), {"smoothing": 1}, {"smoothing": 1}),
+    }
+
+
+NAMES = ["L65", "hole65", "L65_lognormal", "hole129_c40", "L97_all"]
+
+
+@pytest.fixture(scope="module")
+def cases(gen, A):
+    out = {}
+    for name, (m, po, pl) in _meshes(gen).items():
+        out[name] = (m, oracle.Oracle(m, **po), A.Solver(m, precision=A.ASMG_FP64, **pl), pl)
+    return out
+
+
+def _spread(v):
+    v = v.astype(np.uint64) & np.uint64(0xFFFFFFFF)
+    for s, mk in ((16, 0x0000FFFF0000FFFF), (8, 0x00FF00FF00FF00FF), (4, 0x0F0F0F0F0F0F0F0F),
+                  (2, 0x3333333333333333), (1, 0x5555555555555555)):
+        v = (v | (v << np.uint64(s))) & np.uint64(mk)
+    return v
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_domain_tree_free_nodes_smoothing_sets_bit_exact(cases, name):
+    m, o, s, p = cases[name]
+    assert np.array_equal(s.export("keys"), o.keys())
+    assert np.array_equal(s.export("perm"), o.perm())
+    for d, arr in enumerate(o.boxes()):
+        sp = arr[arr[:, 1] == 1, 0]
+        want = np.sort(_spread(sp & np.uint64(0xFFFFFFFF)) | (_spread(sp >> np.uint64(32)) << np.uint64(1)))
+        assert np.array_equal(s.export("split", d), want), d
+    assert s.info("J") == o.J and s.info("coarse") == o.c
+    # the free nodes of T^D_J, and how many are free at every level
+    assert np.array_equal(s.export("aux_keys"), o.level_keys(o.J))
+    for l in range(o.J + 1):
+        assert s.info("naux", l) == o.info("nlevel", l), l
+    # the domain really cuts the aux grids: T^D_J has fewer triangles than sigma^(J)
+    assert o.level_tri(o.J).shape[0] < o.info("nalltri", o.J)
+    assert np.array_equal(s.export("fine_colour"), o.smoothing_set(-1)[2])
+    for l in range(o.c + 1, o.J + 1):
+        sm = s.export("smooth", l).reshape(-1, 2)
+        osm, _, ocol = o.smoothing_set(l)
+        keys = o.level_keys(l)
+        want = sorted(zip(keys[osm].tolist(), ocol[osm].tolist()))
+        got = sorted(zip(sm[:, 0].tolist(), sm[:, 1].tolist()))
+        assert got == want, l
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_domain_fine_operator_transfer_and_level_operators(cases, name):
+    m, o, s, p = cases[name]
+    vf = o.vertex_of_free()
+    pos = {int(v): i for i, v in enumerate(vf)}
+    Ao = o.A().tocoo()
+    t = s.export("fine_A")
+    got = {(pos[int(r)], pos[int(c)]): v for r, c, v in zip(t["row"], t["col"], t["val"])}
+    want = {(int(r), int(c)): v for r, c, v in zip(Ao.row, Ao.col, Ao.data)}
+    assert max(abs(got.get(k, 0.0) - want.get(k, 0.0)) for k in set(got) | set(want)) <= 1e-12 * np.abs(Ao.data).max()
+    keys = o.level_keys(o.J)
+    kpos = {int(k): i for i, k in enumerate(keys)}
+    t = s.export("P")
+    got = {(pos[int(r)], kpos[int(c)]): v for r, c, v in zip(t["row"], t["col"], t["val"])}
+    Po = o.P().tocoo()
+    want = {(int(r), int(c)): v for r, c, v in zip(Po.row, Po.col, Po.data)}
+    # (entries that are exactly 0 may be stored on one side only)
+    assert max(abs(got.get(k, 0.0) - want.get(k, 0.0)) for k in set(got) | set(want)) <= 1e-11
+    for l in range(o.c + 1, o.J + 1):
+        lk = o.level_keys(l)
+        lpos = {int(k): i for i, k in enumerate(lk)}
+        osm = set(lk[o.smoothing_set(l)[0]].tolist())
+        ins = np.array([int(k) in osm for k in lk])
+        Al = o.A(l).tocoo()
+        want = {(int(r), int(c)): v for r, c, v in zip(Al.row, Al.col, Al.data) if ins[r] or ins[c]}
+        t = s.export("level_rows", l)
+        got = {(lpos[int(r)], lpos[int(c)]): v for r, c, v in zip(t["row"], t["col"], t["val"])}
+        got = {k: v for k, v in got.items() if ins[k[0]] or ins[k[1]]}
+        scale = np.abs(Al.data).max()
+        err = max(abs(got.get(k, 0.0) - want.get(k, 0.0)) for k in set(got) | set(want))
+        assert err <= 1e-12 * scale, (l, err, scale)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_domain_preconditioner_and_spmv(cases, name):
+    m, o, s, p = cases[name]
+    rng = np.random.default_rng(8)
+    vf = o.vertex_of_free()
+    r = np.zeros(m.nv)
+    r[vf] = rng.uniform(-1, 1, o.nfree)
+    z_ref = o.precond(r[vf])
+    z = s.precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    assert np.linalg.norm(z[vf] - z_ref) <= 1e-11 * np.linalg.norm(z_ref)
+    assert np.all(z[m.bflag == 1] == 0)
+    y = s.spmv(torch.from_numpy(r).cuda()).cpu().numpy()
+    yr = o.spmv(r[vf])
+    assert np.abs(y[vf] - yr).max() <= 1e-12 * np.abs(yr).max()
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_domain_solves_match_oracle(cases, gen, A, name):
+    m, o, s, p = cases[name]
+    f = gen.nodal_uniform(m, 21)
+    vf = o.vertex_of_free()
+    b_ref = o.mass_apply(f)
+    u_ref, st, it_ref, _ = o.solve(b_ref, rtol=1e-8)
+    assert st == 0
+    u, rc, it, hist = s.solve(s.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
+    u = u.cpu().numpy()
+    assert rc == A.ASMG_OK and abs(it - it_ref) <= 2, (it, it_ref)
+    assert np.linalg.norm(u[vf] - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    assert np.linalg.norm(b_ref - o.spmv(u[vf])) <= 2e-8 * np.linalg.norm(b_ref)
+    assert np.all(u[m.bflag == 1] == 0)
+    sm = A.Solver(m, precision=A.ASMG_MIXED, **p)
+    u2, rc2, it2, _ = sm.solve(sm.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
+    u2 = u2.cpu().numpy()
+    assert rc2 == A.ASMG_OK and abs(it2 - it_ref) <= 2, (it2, it_ref)
+    assert np.linalg.norm(u2[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+    sm.close()
