@@ -455,7 +455,7 @@ def main():
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
                    "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
                    "setup_breakdown_s": {k: s.info(f"t_{k}_us") / 1e6 for k in
-                                         ("tree", "aux", "fine", "levels", "lv_assemble", "lv_colour", "lv_pack",
+                                         ("tree", "aux", "sz", "fine", "levels", "lv_assemble", "lv_colour", "lv_pack",
                                           "lv_export", "coarse", "transfer", "slots")},
                    "graph": not args.no_graph, "pdl": not args.no_pdl,
                    "l2": "working set (several GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},

@@ -10,7 +10,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libasmg.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cu", "assemble.cu", "solve.cu", "noalloc.cu", "aux_setup.cpp", "aux_setup3.cpp", "capi.cpp"]
+SOURCES = ["tree.cu", "assemble.cu", "transfer.cu", "solve.cu", "noalloc.cu", "aux_setup.cpp", "aux_setup3.cpp", "capi.cpp"]
+# the transfer kernel rounds like the host code (separate multiply and add),
+# so the clipped integrals carry no extra rounding differences into parity
+EXTRA = {"transfer.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -37,7 +40,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(obj)
         if not force and not _stale(obj, [path] + headers):
             continue
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-c", path, "-o", obj]
+        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", *EXTRA.get(src, []), "-Xcompiler", "-fPIC,-O2", "-c",
+               path, "-o", obj]
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "cu"] if False else []
         if verbose:

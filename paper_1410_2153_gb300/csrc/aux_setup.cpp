@@ -16,6 +16,7 @@
 #include <cstring>
 #include <thread>
 
+#include "clip.h"
 #include "internal.h"
 
 namespace asmg {
@@ -122,82 +123,9 @@ std::vector<uint64_t> boxes_at(const BoxTree& T, int d) {
   return b;
 }
 
-// ---------------------------------------------------------------- clipping
-struct V2 {
-  double x, y;
-};
-
-// Clip the convex polygon `in` (CCW) to the half-plane n.x <= c.
-int clip_half(const V2* in, int n, double nx, double ny, double c, V2* out) {
-  int m = 0;
-  for (int i = 0; i < n; ++i) {
-    const V2& a = in[i];
-    const V2& b = in[(i + 1) % n];
-    double fa = nx * a.x + ny * a.y - c, fb = nx * b.x + ny * b.y - c;
-    if (fa <= 0) out[m++] = a;
-    if ((fa <= 0) != (fb <= 0)) {
-      double t = fa / (fa - fb);
-      out[m++] = V2{a.x + t * (b.x - a.x), a.y + t * (b.y - a.y)};
-    }
-  }
-  return m;
-}
-
-// Clip polygon P (CCW, local coordinates) by triangle K (CCW).
-int clip_tri(const V2* P, int n, const V2* K, V2* out) {
-  V2 buf[2][16];
-  int m = n;
-  for (int i = 0; i < n; ++i) buf[0][i] = P[i];
-  int cur = 0;
-  for (int e = 0; e < 3 && m >= 3; ++e) {
-    const V2& a = K[e];
-    const V2& b = K[(e + 1) % 3];
-    // inside of a CCW edge a->b: cross(b - a, x - a) >= 0  <=>  n.x <= c
-    double nx = (b.y - a.y), ny = -(b.x - a.x);
-    double c = nx * a.x + ny * a.y;
-    m = clip_half(buf[cur], m, nx, ny, c, buf[1 - cur]);
-    cur = 1 - cur;
-  }
-  for (int i = 0; i < m; ++i) out[i] = buf[cur][i];
-  return m;
-}
-
-// Moments of a polygon by Green's theorem: [1, x, y, x^2, xy, y^2].
-void moments(const V2* p, int n, double M[6]) {
-  for (int k = 0; k < 6; ++k) M[k] = 0;
-  for (int i = 0; i < n; ++i) {
-    const V2& a = p[i];
-    const V2& b = p[(i + 1) % n];
-    double c = a.x * b.y - b.x * a.y;
-    M[0] += c;
-    M[1] += (a.x + b.x) * c;
-    M[2] += (a.y + b.y) * c;
-    M[3] += (a.x * a.x + a.x * b.x + b.x * b.x) * c;
-    M[4] += (a.x * b.y + 2 * a.x * a.y + 2 * b.x * b.y + b.x * a.y) * c;
-    M[5] += (a.y * a.y + a.y * b.y + b.y * b.y) * c;
-  }
-  M[0] /= 2;
-  M[1] /= 6;
-  M[2] /= 6;
-  M[3] /= 12;
-  M[4] /= 24;
-  M[5] /= 12;
-}
-
-// Affine coefficients (c0 + c1 x + c2 y) of the barycentric function of vertex j.
-void bary_affine(const V2* T, int j, double c[3]) {
-  const V2 &p = T[(j + 1) % 3], &q = T[(j + 2) % 3];
-  double twoA = (T[1].x - T[0].x) * (T[2].y - T[0].y) - (T[2].x - T[0].x) * (T[1].y - T[0].y);
-  c[0] = (p.x * q.y - q.x * p.y) / twoA;
-  c[1] = (p.y - q.y) / twoA;
-  c[2] = (q.x - p.x) / twoA;
-}
-
-// int (f0 + f1 x + f2 y)(g0 + g1 x + g2 y) from the moments
-inline double prod_int(const double f[3], const double g[3], const double M[6]) {
-  return f[0] * g[0] * M[0] + (f[0] * g[1] + f[1] * g[0]) * M[1] + (f[0] * g[2] + f[2] * g[0]) * M[2] +
-         f[1] * g[1] * M[3] + (f[1] * g[2] + f[2] * g[1]) * M[4] + f[2] * g[2] * M[5];
-}
+using clip::clip_tri;
+using clip::moments;
+using clip::V2;
 
 // Leaves of the closed tree meeting the closed lattice rectangle [lo, hi].
 void leaves_in(const BoxTree& T, int64_t lox, int64_t loy, int64_t hix, int64_t hiy,
@@ -370,21 +298,75 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     std::sort(t.begin(), t.end());
     return t;
   };
-  if (varcoef || dgrid) {
-    // finest triangles, indexed by leaf order
-    std::vector<std::array<uint64_t, 3>> ftri;
-    std::vector<std::vector<int64_t>> first(J + 1);
+  // ---- the leaves' finest triangles (leaves numbered in depth-major box
+  // order; first[d][i]: first triangle of box i of depth d, -1 if split), and
+  // the node table of the device transfer build
+  std::vector<std::vector<int64_t>> first(J + 1);
+  std::vector<std::array<uint64_t, 3>> ftri;
+  {
+    SZTable& z = out.sz;
+    z.dim = 2;
+    z.D = T.D;
+    z.amin[0] = tree.amin[0];
+    z.amin[1] = tree.amin[1];
+    z.L = tree.L;
+    std::vector<int64_t> doff(J + 2, 0);
+    for (int d = 0; d <= J; ++d) doff[d + 1] = doff[d] + (int64_t)BX[d].size();
+    const int64_t nb = doff[J + 1];
+    z.node_key.assign(nb, 0);
+    z.node_pay.assign(nb, -1);
+    std::vector<int32_t> ntri(nb, 0);
     for (int d = 0; d <= J; ++d) {
       const auto& bx = BX[d];
-      first[d].assign(bx.size(), -1);
-      for (size_t i = 0; i < bx.size(); ++i) {
-        if (T.split(d, bx[i])) continue;
-        bool h[4];
-        T.hanging(d, bx[i], h);
-        first[d][i] = (int64_t)ftri.size();
-        box_tris(T, d, bx[i], h, ftri);
+      parallel_for((int64_t)bx.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+        for (int64_t i = b0; i < b1; ++i) {
+          const int64_t k = doff[d] + i;
+          z.node_key[k] = bx[i];
+          if (d < (int)T.S.size()) {
+            auto it = std::lower_bound(T.S[d].begin(), T.S[d].end(), bx[i]);
+            if (it != T.S[d].end() && *it == bx[i]) {
+              z.node_pay[k] = doff[d + 1] + 4 * (int64_t)(it - T.S[d].begin());
+              continue;
+            }
+          }
+          bool h[4];
+          T.hanging(d, bx[i], h);
+          const int nh = (int)h[0] + (int)h[1] + (int)h[2] + (int)h[3];
+          ntri[k] = nh ? 4 + nh : 2;
+        }
+      });
+    }
+    int64_t nleaf = 0, nt = 0;
+    for (int d = 0; d <= J; ++d) {
+      first[d].assign(BX[d].size(), -1);
+      for (size_t i = 0; i < BX[d].size(); ++i) {
+        const int64_t k = doff[d] + (int64_t)i;
+        if (z.node_pay[k] >= 0) continue;
+        z.node_pay[k] = -(nleaf + 1);
+        z.leaf_first.push_back(nt);
+        first[d][i] = nt;
+        ++nleaf;
+        nt += ntri[k];
       }
     }
+    z.leaf_first.push_back(nt);
+    ftri.resize(nt);
+    for (int d = 0; d <= J; ++d) {
+      const auto& bx = BX[d];
+      parallel_for((int64_t)bx.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+        std::vector<std::array<uint64_t, 3>> kt;
+        for (int64_t i = b0; i < b1; ++i) {
+          if (first[d][i] < 0) continue;
+          bool h[4];
+          T.hanging(d, bx[i], h);
+          kt.clear();
+          box_tris(T, d, bx[i], h, kt);
+          std::copy(kt.begin(), kt.end(), ftri.begin() + first[d][i]);
+        }
+      });
+    }
+  }
+  if (varcoef || dgrid) {
     // clip every fine element against the finest triangles it meets
     std::vector<std::vector<std::pair<int64_t, double>>> contrib(64), ccontrib(64);
     parallel_for(mesh.ne, [&](unsigned t, unsigned, int64_t b, int64_t e) {
@@ -818,95 +800,32 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     }
   }
 
-  // ---- Scott-Zhang transfer (Sec. 4.1): P_ik = int_{sigma_i} psi_i phi_k,
-  // sigma_i the lowest-index element at node i, psi_i = (12 lambda_i - 3)/|sigma_i|
-  std::vector<int32_t> sigma(mesh.nv, -1);
-  for (int64_t e = mesh.ne - 1; e >= 0; --e)
-    for (int k = 0; k < 3; ++k) sigma[mesh.E[3 * e + k]] = (int32_t)e;
-  std::vector<int32_t> vert_of_free;
-  for (int64_t v = 0; v < mesh.nv; ++v)
-    if (free_of_vertex[v] >= 0) vert_of_free.push_back((int32_t)v);
-  const int64_t n = (int64_t)vert_of_free.size();
-  std::vector<Triplets> parts(64);
-  parallel_for(n, [&](unsigned t, unsigned, int64_t b, int64_t e) {
-    Triplets& mine = parts[t];
-    std::vector<std::pair<int, uint64_t>> lv;
-    std::vector<std::array<uint64_t, 3>> kt;
-    std::vector<std::pair<int32_t, double>> row;
-    const double sc = std::ldexp(1.0, T.D) / tree.L;
-    for (int64_t i = b; i < e; ++i) {
-      const int32_t v = vert_of_free[i];
-      const int32_t el = sigma[v];
-      V2 P[3];
-      int loc = 0;
-      for (int k = 0; k < 3; ++k) {
-        int32_t w = mesh.E[3 * (int64_t)el + k];
-        P[k] = V2{mesh.X[2 * w], mesh.X[2 * w + 1]};
-        if (w == v) loc = k;
-      }
-      const V2 o = P[0];
-      V2 Pl[3];
-      for (int k = 0; k < 3; ++k) Pl[k] = V2{P[k].x - o.x, P[k].y - o.y};
-      const double area = 0.5 * (Pl[1].x * Pl[2].y - Pl[2].x * Pl[1].y);
-      double lam[3], psi[3];
-      bary_affine(Pl, loc, lam);
-      psi[0] = (12.0 * lam[0] - 3.0) / area;
-      psi[1] = 12.0 * lam[1] / area;
-      psi[2] = 12.0 * lam[2] / area;
-      double mnx = std::min({P[0].x, P[1].x, P[2].x}), mxx = std::max({P[0].x, P[1].x, P[2].x});
-      double mny = std::min({P[0].y, P[1].y, P[2].y}), mxy = std::max({P[0].y, P[1].y, P[2].y});
-      lv.clear();
-      leaves_in(T, (int64_t)std::floor((mnx - tree.amin[0]) * sc) - 2, (int64_t)std::floor((mny - tree.amin[1]) * sc) - 2,
-                (int64_t)std::ceil((mxx - tree.amin[0]) * sc) + 2, (int64_t)std::ceil((mxy - tree.amin[1]) * sc) + 2, lv);
-      row.clear();
-      for (auto& lf : lv) {
-        bool h[4];
-        T.hanging(lf.first, lf.second, h);
-        kt.clear();
-        box_tris(T, lf.first, lf.second, h, kt);
-        const bool diag = !(h[0] || h[1] || h[2] || h[3]);
-        for (size_t q = 0; q < kt.size(); ++q) {
-          const auto& k3 = kt[q];
-          if (!tri_inside(lf.first, lf.second, diag, (int)q, k3)) continue;  // hats vanish outside Omega^D_J
-          V2 K[3];
-          for (int k = 0; k < 3; ++k) {
-            double p[2];
-            lattice_point(tree, k3[k], p);
-            K[k] = V2{p[0] - o.x, p[1] - o.y};
-          }
-          V2 poly[16];
-          int m = clip_tri(Pl, 3, K, poly);
-          if (m < 3) continue;
-          double M[6];
-          moments(poly, m, M);
-          if (!(M[0] > 0)) continue;
-          for (int k = 0; k < 3; ++k) {
-            const int32_t col = level_id(k3[k], J);
-            if (col < 0) continue;
-            double lam3[3];
-            bary_affine(K, k, lam3);
-            row.push_back({col, prod_int(psi, lam3, M)});
+  // ---- columns of the finest triangles for the device Scott-Zhang build
+  // (Sec. 4.1): the aux ID of every vertex with a hat function at level J;
+  // none on the triangles outside Omega^D_J
+  {
+    SZTable& z = out.sz;
+    z.simp_key.resize(3 * ftri.size());
+    z.simp_col.assign(3 * ftri.size(), -1);
+    if (!ftri.empty()) std::memcpy(z.simp_key.data(), ftri.data(), ftri.size() * sizeof(ftri[0]));
+    for (int d = 0; d <= J; ++d) {
+      const auto& bx = BX[d];
+      parallel_for((int64_t)bx.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+        for (int64_t i = b0; i < b1; ++i) {
+          const int64_t f0 = first[d][i];
+          if (f0 < 0) continue;
+          bool h[4];
+          T.hanging(d, bx[i], h);
+          const int nh = (int)h[0] + (int)h[1] + (int)h[2] + (int)h[3];
+          const int nt = nh ? 4 + nh : 2;
+          for (int k = 0; k < nt; ++k) {
+            const auto& t = ftri[f0 + k];
+            if (!tri_inside(d, bx[i], nh == 0, k, t)) continue;
+            for (int v = 0; v < 3; ++v) z.simp_col[3 * (f0 + k) + v] = level_id(t[v], J);
           }
         }
-      }
-      std::sort(row.begin(), row.end(), [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b2) {
-        return a.first < b2.first;
       });
-      for (size_t k = 0; k < row.size();) {
-        size_t j = k;
-        double sum = 0.0;
-        while (j < row.size() && row[j].first == row[k].first) sum += row[j++].second;
-        mine.r.push_back((int32_t)i);
-        mine.c.push_back(row[k].first);
-        mine.v.push_back(sum);
-        k = j;
-      }
     }
-  });
-  for (auto& p : parts) {
-    out.P.r.insert(out.P.r.end(), p.r.begin(), p.r.end());
-    out.P.c.insert(out.P.c.end(), p.c.begin(), p.c.end());
-    out.P.v.insert(out.P.v.end(), p.v.begin(), p.v.end());
   }
 }
 

@@ -19,6 +19,7 @@
 #include <thread>
 #include <unordered_map>
 
+#include "clip.h"
 #include "internal.h"
 
 namespace asmg {
@@ -241,134 +242,11 @@ inline double vol6(const V3& a, const V3& b, const V3& c, const V3& d) {
          e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
 }
 
-inline V3 lerp(const V3& a, const V3& b, double da, double db) {
-  const double t = da / (da - db);
-  return V3{a[0] + t * (b[0] - a[0]), a[1] + t * (b[1] - a[1]), a[2] + t * (b[2] - a[2])};
-}
-
-// keep the part with n.x - c <= 0; vertices are classified by the exact sign
-// of their distance, so every intersection parameter lies in [0, 1) and no
-// point is moved across a plane (pieces of zero volume are harmless)
-void cut(std::vector<TetP>& tets, std::vector<TetP>& out, const V3& n, double c) {
-  out.clear();
-  for (const TetP& t : tets) {
-    double dv[4];
-    int in[4], ni = 0, ou[4], no = 0;
-    for (int v = 0; v < 4; ++v) {
-      dv[v] = n[0] * t[v][0] + n[1] * t[v][1] + n[2] * t[v][2] - c;
-      if (dv[v] <= 0) in[ni++] = v; else ou[no++] = v;
-    }
-    if (no == 0) {
-      out.push_back(t);
-      continue;
-    }
-    if (ni == 0) continue;
-    if (ni == 1) {
-      const V3& a = t[in[0]];
-      out.push_back({a, lerp(a, t[ou[0]], dv[in[0]], dv[ou[0]]), lerp(a, t[ou[1]], dv[in[0]], dv[ou[1]]),
-                     lerp(a, t[ou[2]], dv[in[0]], dv[ou[2]])});
-    } else if (ni == 3) {
-      // prism: inside triangle (a0 a1 a2), cut triangle (b0 b1 b2), ak - bk edges
-      V3 A[3], B[3];
-      for (int k = 0; k < 3; ++k) {
-        A[k] = t[in[k]];
-        B[k] = lerp(t[in[k]], t[ou[0]], dv[in[k]], dv[ou[0]]);
-      }
-      out.push_back({A[0], A[1], A[2], B[0]});
-      out.push_back({A[1], A[2], B[0], B[1]});
-      out.push_back({A[2], B[0], B[1], B[2]});
-    } else {
-      // two inside (i0, i1), two outside (o0, o1): prism with triangles
-      // (i0, p00, p01) and (i1, p10, p11)
-      const V3 &i0 = t[in[0]], &i1 = t[in[1]];
-      V3 A[3] = {i0, lerp(i0, t[ou[0]], dv[in[0]], dv[ou[0]]), lerp(i0, t[ou[1]], dv[in[0]], dv[ou[1]])};
-      V3 B[3] = {i1, lerp(i1, t[ou[0]], dv[in[1]], dv[ou[0]]), lerp(i1, t[ou[1]], dv[in[1]], dv[ou[1]])};
-      out.push_back({A[0], A[1], A[2], B[0]});
-      out.push_back({A[1], A[2], B[0], B[1]});
-      out.push_back({A[2], B[0], B[1], B[2]});
-    }
-  }
-}
-
-// S cut by the four half-spaces of tetrahedron K (scratch: a work buffer);
-// disjoint bounding boxes give no pieces
-void clip_tets(const TetP& S, const TetP& K, std::vector<TetP>& out, std::vector<TetP>& scratch) {
-  out.clear();
-  for (int k = 0; k < 3; ++k) {
-    double s0 = S[0][k], s1 = S[0][k], k0 = K[0][k], k1 = K[0][k];
-    for (int v = 1; v < 4; ++v) {
-      s0 = std::min(s0, S[v][k]);
-      s1 = std::max(s1, S[v][k]);
-      k0 = std::min(k0, K[v][k]);
-      k1 = std::max(k1, K[v][k]);
-    }
-    if (s1 <= k0 || k1 <= s0) return;
-  }
-  out.push_back(S);
-  static const int fc[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};
-  for (auto& f : fc) {
-    const V3 &a = K[f[0]], &b = K[f[1]], &c = K[f[2]], &d = K[f[3]];
-    const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-    V3 n = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    for (int k = 0; k < 3; ++k) n[k] /= nn;
-    double cc = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
-    if (n[0] * d[0] + n[1] * d[1] + n[2] * d[2] > cc) {
-      for (int k = 0; k < 3; ++k) n[k] = -n[k];
-      cc = -cc;
-    }
-    cut(out, scratch, n, cc);
-    out.swap(scratch);
-    if (out.empty()) return;
-  }
-}
-
-// affine function of x: f0 + f.x
-struct Aff {
-  double c0, g[3];
-  double operator()(const V3& x) const { return c0 + g[0] * x[0] + g[1] * x[1] + g[2] * x[2]; }
-};
-
-// barycentric function of vertex j of tetrahedron T as an affine function
-Aff bary(const TetP& T, int j) {
-  double Jm[3][3];
-  for (int k = 1; k <= 3; ++k)
-    for (int r = 0; r < 3; ++r) Jm[r][k - 1] = T[k][r] - T[0][r];
-  double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) - Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
-               Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
-  double inv[3][3];
-  inv[0][0] = (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) / det;
-  inv[0][1] = (Jm[0][2] * Jm[2][1] - Jm[0][1] * Jm[2][2]) / det;
-  inv[0][2] = (Jm[0][1] * Jm[1][2] - Jm[0][2] * Jm[1][1]) / det;
-  inv[1][0] = (Jm[1][2] * Jm[2][0] - Jm[1][0] * Jm[2][2]) / det;
-  inv[1][1] = (Jm[0][0] * Jm[2][2] - Jm[0][2] * Jm[2][0]) / det;
-  inv[1][2] = (Jm[0][2] * Jm[1][0] - Jm[0][0] * Jm[1][2]) / det;
-  inv[2][0] = (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]) / det;
-  inv[2][1] = (Jm[0][1] * Jm[2][0] - Jm[0][0] * Jm[2][1]) / det;
-  inv[2][2] = (Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0]) / det;
-  Aff f;
-  if (j == 0) {
-    for (int r = 0; r < 3; ++r) f.g[r] = -(inv[0][r] + inv[1][r] + inv[2][r]);
-  } else {
-    for (int r = 0; r < 3; ++r) f.g[r] = inv[j - 1][r];
-  }
-  f.c0 = 1.0 * (j == 0) - (f.g[0] * T[0][0] + f.g[1] * T[0][1] + f.g[2] * T[0][2]);
-  return f;
-}
-
-// int over tetrahedron t of f * g (affine f, g) by the symmetric 4-point
-// degree-2 rule: points a v_i + b (sum of the other three vertices) with
-// a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20, weights |t|/4.
-double prod4(const TetP& t, const Aff& f, const Aff& g) {
-  static const double a = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, b = (5.0 - std::sqrt(5.0)) / 20.0;
-  const double vol = std::fabs(vol6(t[0], t[1], t[2], t[3])) / 6.0;
-  double s = 0;
-  for (int i = 0; i < 4; ++i) {
-    V3 x;
-    for (int k = 0; k < 3; ++k) x[k] = a * t[i][k] + b * (t[(i + 1) % 4][k] + t[(i + 2) % 4][k] + t[(i + 3) % 4][k]);
-    s += f(x) * g(x);
-  }
-  return s * vol / 4.0;
+clip::Tet4 tet4(const TetP& t) {
+  clip::Tet4 r;
+  for (int v = 0; v < 4; ++v)
+    for (int k = 0; k < 3; ++k) r.p[v].v[k] = t[v][k];
+  return r;
 }
 
 void leaves_in(const Tree3& T, const int64_t* lo, const int64_t* hi, std::vector<std::pair<int, uint64_t>>& out,
@@ -677,7 +555,6 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     std::atomic<int64_t> nextc(0);
     auto work = [&]() {
       std::vector<std::pair<int, uint64_t>> lv, st;
-      std::vector<TetP> pieces, scratch;
       std::vector<std::pair<int64_t, double>> acc;
       for (;;) {
         const int64_t ch = nextc.fetch_add(1);
@@ -701,9 +578,8 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             for (int q = 0; q < nq; ++q) {
               TetP K;
               leaf_tet(f0 + q, K);
-              clip_tets(S, K, pieces, scratch);
               double vol = 0;
-              for (auto& pc : pieces) vol += std::fabs(vol6(pc[0], pc[1], pc[2], pc[3])) / 6.0;
+              clip::clip_tets(tet4(S), tet4(K), [&](const clip::Tet4& pc) { vol += clip::volume(pc); });
               if (vol > 0) acc.push_back({f0 + q, vol * mesh.coeff[e]});
             }
           }
@@ -919,83 +795,43 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     }
   }
 
-  // Scott-Zhang (Sec. 4.1) in 3D: psi_i = (20 lambda_i - 4)/|sigma_i|
-  std::vector<int32_t> sigma(mesh.nv, -1);
-  for (int64_t e = mesh.ne - 1; e >= 0; --e)
-    for (int k = 0; k < 4; ++k) sigma[mesh.E[4 * e + k]] = (int32_t)e;
-  std::vector<int32_t> vert_of_free;
-  for (int64_t v = 0; v < mesh.nv; ++v)
-    if (free_of_vertex[v] >= 0) vert_of_free.push_back((int32_t)v);
-  const int64_t n = (int64_t)vert_of_free.size();
-  unsigned nth = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-  if (n < 2048) nth = 1;
-  std::vector<Triplets> parts(nth);
+  // ---- table of the device Scott-Zhang build (Sec. 4.1): the boxes of
+  // every depth with their first child or leaf number, the leaves' finest
+  // tetrahedra and the aux ID of every vertex (-1 on the boundary)
   {
-    std::vector<std::thread> th;
-    for (unsigned tix = 0; tix < nth; ++tix)
-      th.emplace_back([&, tix] {
-        Triplets& mine = parts[tix];
-        std::vector<std::pair<int, uint64_t>> lv, st;
-        std::vector<TetP> pieces, scratch;
-        std::vector<std::pair<int32_t, double>> row;
-        const int64_t b0 = n * tix / nth, b1 = n * (tix + 1) / nth;
+    SZTable& z = out.sz;
+    z.dim = 3;
+    z.D = T.LB;
+    for (int k = 0; k < 3; ++k) z.amin[k] = tree.amin[k];
+    z.L = tree.L;
+    std::vector<int64_t> doff(J + 2, 0);
+    for (int d = 0; d <= J; ++d) doff[d + 1] = doff[d] + (int64_t)BX[d].size();
+    z.node_key.assign(doff[J + 1], 0);
+    z.node_pay.assign(doff[J + 1], 0);
+    z.leaf_first.assign(nleaf + 1, (int64_t)ftet.size());
+    for (int d = 0; d <= J; ++d) {
+      const auto& bx = BX[d];
+      pfor((int64_t)bx.size(), [&](unsigned, int64_t b0, int64_t b1) {
         for (int64_t i = b0; i < b1; ++i) {
-          const int32_t v = vert_of_free[i];
-          const int32_t e = sigma[v];
-          TetP S;
-          fine_tet(e, S);
-          int loc = 0;
-          for (int k = 0; k < 4; ++k)
-            if (mesh.E[4 * (int64_t)e + k] == v) loc = k;
-          int64_t lo[3], hi[3];
-          window(S, lo, hi);
-          const double vol = std::fabs(vol6(S[0], S[1], S[2], S[3])) / 6.0;
-          Aff lam = bary(S, loc), psi;
-          psi.c0 = (20.0 * lam.c0 - 4.0) / vol;
-          for (int r = 0; r < 3; ++r) psi.g[r] = 20.0 * lam.g[r] / vol;
-          lv.clear();
-          leaves_in(T, lo, hi, lv, st);
-          row.clear();
-          for (auto& lf : lv) {
-            int64_t f0;
-            int nq;
-            leaf_range(lf, f0, nq);
-            for (int q = 0; q < nq; ++q) {
-              TetP K;
-              leaf_tet(f0 + q, K);
-              clip_tets(S, K, pieces, scratch);
-              if (pieces.empty()) continue;
-              for (int w = 0; w < 4; ++w) {
-                const uint64_t key = ftet[f0 + q][w];
-                if (bnd3(T, key)) continue;
-                Aff phi = bary(K, w);
-                double val = 0;
-                for (auto& pc : pieces) val += prod4(pc, psi, phi);
-                row.push_back({idx_of(AK, key), val});
-              }
-            }
-          }
-          std::stable_sort(row.begin(), row.end(),
-                           [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
-                             return x.first < y.first;
-                           });
-          for (size_t k = 0; k < row.size();) {
-            size_t j = k;
-            double sum = 0;
-            while (j < row.size() && row[j].first == row[k].first) sum += row[j++].second;
-            mine.r.push_back((int32_t)i);
-            mine.c.push_back(row[k].first);
-            mine.v.push_back(sum);
-            k = j;
+          const int64_t k = doff[d] + i;
+          z.node_key[k] = bx[i];
+          if (lid[d][i] >= 0) {
+            z.node_pay[k] = -((int64_t)lid[d][i] + 1);
+            z.leaf_first[lid[d][i]] = first[d][i];
+          } else {
+            const auto& sd = T.S[d];
+            z.node_pay[k] = doff[d + 1] + 8 * (int64_t)(std::lower_bound(sd.begin(), sd.end(), bx[i]) - sd.begin());
           }
         }
       });
-    for (auto& x : th) x.join();
-  }
-  for (auto& p : parts) {
-    out.P.r.insert(out.P.r.end(), p.r.begin(), p.r.end());
-    out.P.c.insert(out.P.c.end(), p.c.begin(), p.c.end());
-    out.P.v.insert(out.P.v.end(), p.v.begin(), p.v.end());
+    }
+    z.simp_key.resize(4 * ftet.size());
+    if (!ftet.empty()) std::memcpy(z.simp_key.data(), ftet.data(), ftet.size() * sizeof(ftet[0]));
+    z.simp_col.assign(4 * ftet.size(), -1);
+    pfor((int64_t)z.simp_key.size(), [&](unsigned, int64_t b0, int64_t b1) {
+      for (int64_t q = b0; q < b1; ++q)
+        if (!bnd3(T, z.simp_key[q])) z.simp_col[q] = idx_of(AK, z.simp_key[q]);
+    });
   }
 }
 

@@ -412,6 +412,10 @@ void build_all(asmg_s& h, cudaStream_t s) {
   else
     build_aux_host3(m, h.tree, h.prm, h.free_of_vertex, h.aux);
   h.stats.t_aux = now() - t1;
+  t1 = now();
+  build_transfer(m, h.dX.p, h.dE.p, h.vertex_of_free, h.aux.sz, h.aux.P, s);
+  h.aux.sz = SZTable();
+  h.stats.t_sz = now() - t1;
   double t2 = now();
   h.nJ = (int64_t)h.aux.aux_key.size();
   h.nJpad = pad32(h.nJ);
@@ -1018,6 +1022,7 @@ int amg_info(asmg_handle h, int what, int level, int64_t* value) {
     case 112: *value = (int64_t)(h->stats.t_coarse * 1e6); break;
     case 113: *value = (int64_t)(h->stats.t_transfer * 1e6); break;
     case 114: *value = (int64_t)(h->stats.t_slots * 1e6); break;
+    case 115: *value = (int64_t)(h->stats.t_sz * 1e6); break;
     default: ASMG_FAIL(ASMG_ERR_INVALID_ARG, "unknown info %d", what);
   }
   return ASMG_OK;

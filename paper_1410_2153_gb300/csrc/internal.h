@@ -132,6 +132,23 @@ struct AuxLevelHost {
   std::vector<double> tri_coef;           // [ntri]
 };
 
+// What the device Scott-Zhang kernel needs of the closed tree and the finest
+// auxiliary grid: the boxes of every depth (ascending prefix within a depth,
+// depths one after another) with, per box, the node index of its first child
+// (children are consecutive) or -(leaf + 1); per leaf its finest simplices
+// as lattice keys and the aux ID of every vertex (-1: no hat function there,
+// i.e. a Dirichlet node, or a simplex outside Omega^D_J).
+struct SZTable {
+  int dim = 2;
+  int D = 31;                     // lattice bits of a coordinate
+  double amin[3] = {0, 0, 0}, L = 1;
+  std::vector<uint64_t> node_key;
+  std::vector<int64_t> node_pay;
+  std::vector<int64_t> leaf_first;  // simplices of leaf q: [leaf_first[q], leaf_first[q + 1])
+  std::vector<uint64_t> simp_key;   // dim + 1 keys per simplex
+  std::vector<int32_t> simp_col;    // dim + 1 aux IDs per simplex
+};
+
 struct AuxHost {
   int J = 0, c = 0;
   int LB = 0;                                  // 3D: lattice bits of the node keys (J + 1)
@@ -144,6 +161,7 @@ struct AuxHost {
   std::vector<uint64_t> coarse_tri_key;
   std::vector<double> coarse_tri_coef;
   Triplets P;                                  // (free fine dof, aux ID, value)
+  SZTable sz;                                  // input of the device transfer build
 };
 
 struct MeshHost {
@@ -164,6 +182,13 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
 // the levels then hold 4 keys / ids per tetrahedron
 void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
                      const std::vector<int32_t>& free_of_vertex, AuxHost& out);
+
+// Scott-Zhang transfer (transfer.cu, Sec. 4.1) from the table the host setup
+// leaves in AuxHost::sz: P (rows: free fine dofs in free order, columns: aux
+// IDs) as host triplets.  2D rows are computed on the device, 3D rows on host
+// threads (the same row code).
+void build_transfer(const MeshHost& mesh, const double* dX, const int32_t* dE,
+                        const std::vector<int32_t>& vertex_of_free, const SZTable& tab, Triplets& P, cudaStream_t s);
 
 // physical coordinate of a lattice key (2D: 2^D lattice; 3D: 2^LB lattice)
 void lattice_point(const TreeResult& t, uint64_t key, double* p);
@@ -257,6 +282,7 @@ struct Stats {
   // (+ shared-memory forms), export copies, coarsest inverse, transfer, solve state
   double t_lv_assemble = 0, t_lv_colour = 0, t_lv_pack = 0, t_lv_export = 0, t_coarse = 0, t_transfer = 0,
          t_slots = 0;
+  double t_sz = 0;  // device Scott-Zhang build (after t_aux)
 };
 
 }  // namespace asmg

@@ -9,6 +9,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+from conftest import oracle_iterate  # noqa: E402
 
 
 def test_batched_solves_match_single_solves_and_oracle(gen):
@@ -53,8 +54,10 @@ def test_batched_solves_match_single_solves_and_oracle(gen):
                 u_ref, st_o, it_o, _ = o.solve(b, rtol=1e-8)
                 tol = 1e-10 if precisions[p] == 0 else 1e-6
                 vf = o.vertex_of_free()
-                assert np.linalg.norm(u[vf] - u_ref) <= tol * np.linalg.norm(u_ref)
                 assert abs(its[k] - it_o) <= 2
+                if precisions[p] == 0 and its[k] != it_o:
+                    u_ref = oracle_iterate(m, b, its[k])
+                assert np.linalg.norm(u[vf] - u_ref) <= tol * np.linalg.norm(u_ref)
                 k += 1
     asmg.amg_batch_destroy(batch)
     for s in solvers:

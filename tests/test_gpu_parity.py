@@ -21,6 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+from conftest import oracle_iterate  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -162,7 +163,8 @@ def test_solve_fp64_matches_oracle(cases, gen, A, name, graph):
     u = u.cpu().numpy()
     assert rc == A.ASMG_OK and st == 0
     assert abs(it - it_ref) <= 2, (it, it_ref)
-    assert np.linalg.norm(u[vf] - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    u_same = u_ref if it == it_ref else oracle_iterate(m, b_ref, it)
+    assert np.linalg.norm(u[vf] - u_same) <= 1e-10 * np.linalg.norm(u_same)
     assert np.all(u[m.bflag == 1] == 0)
     # the residual history is the recurrence residual: it ends below rtol
     assert hist[-1] <= 1e-8 * np.linalg.norm(b_ref) * (1 + 1e-12)

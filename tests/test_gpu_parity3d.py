@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+from conftest import oracle_iterate  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -151,7 +152,8 @@ def test_3d_solves_match_oracle(cases, gen, A, name):
     u, rc, it, hist = s.solve(s.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
     u = u.cpu().numpy()
     assert rc == A.ASMG_OK and abs(it - it_ref) <= 2, (it, it_ref)
-    assert np.linalg.norm(u[vf] - u_ref) <= 1e-10 * np.linalg.norm(u_ref)
+    u_same = u_ref if it == it_ref else oracle_iterate(m, b_ref, it, **p)
+    assert np.linalg.norm(u[vf] - u_same) <= 1e-10 * np.linalg.norm(u_same)
     assert np.linalg.norm(b_ref - o.spmv(u[vf])) <= 2e-8 * np.linalg.norm(b_ref)
     sm = A.Solver(m, precision=A.ASMG_MIXED, **p)
     u2, rc2, it2, _ = sm.solve(sm.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
