@@ -148,6 +148,10 @@ class Oracle:
         """Every triangle of sigma^(l), also those outside a non-box domain."""
         return self._get("level_alltri", l, (self.info("nalltri", l), 3), np.uint64)
 
+    def level_alltet(self, l: int):
+        """Every tetrahedron of sigma^(l), also those outside a non-box domain."""
+        return self._get("level_alltet", l, (self.info("nalltet", l), 4), np.uint64)
+
     def level_tet(self, l: int):
         return self._get("level_tet", l, (self.info("ntet", l), 4), np.uint64)
 

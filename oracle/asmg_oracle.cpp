@@ -1427,6 +1427,117 @@ void tet_points(const Oracle& o, const std::array<uint64_t, 4>& t, P3* K) {
   }
 }
 
+// The tetrahedron of sigma^(l) containing the point (X4/4) (lattice units,
+// per axis): descend the truncated octree to the level-l box holding it,
+// then test its tetrahedra with integer barycentric coordinates.  The point
+// must lie strictly inside a tetrahedron (a centroid of a finer nested one).
+bool locate_level_tet(const Oracle& o, int l, const uint64_t* X4, std::array<uint64_t, 4>& out) {
+  int depth = 0;
+  uint64_t bq[3] = {0, 0, 0};
+  for (;;) {
+    uint8_t sp = 0;
+    box_exists(o, depth, bq, &sp);
+    if (depth == l || !sp) break;
+    const uint64_t half4 = 4 * (1ULL << (o.LB - depth - 1));
+    for (int d = 0; d < 3; ++d) bq[d] = 2 * bq[d] + ((X4[d] - bq[d] * 2 * half4) >= half4 ? 1 : 0);
+    ++depth;
+  }
+  std::vector<std::array<uint64_t, 4>> tets;
+  box_tets(o, depth, bq, l, tets);
+  for (auto& t : tets) {
+    i128 P[4][3];
+    for (int v = 0; v < 4; ++v) {
+      uint64_t q[3];
+      xyz3(t[v], q);
+      for (int d = 0; d < 3; ++d) P[v][d] = 4 * (i128)q[d];
+    }
+    i128 e1[3], e2[3], e3[3], r[3];
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = P[1][d] - P[0][d];
+      e2[d] = P[2][d] - P[0][d];
+      e3[d] = P[3][d] - P[0][d];
+      r[d] = (i128)X4[d] - P[0][d];
+    }
+    const i128 det = det3(e1, e2, e3);
+    const i128 n1 = det3(r, e2, e3), n2 = det3(e1, r, e3), n3 = det3(e1, e2, r);
+    const i128 n0 = det - n1 - n2 - n3;
+    // same sign as det for all four: strictly inside
+    if ((det > 0 && n0 > 0 && n1 > 0 && n2 > 0 && n3 > 0) || (det < 0 && n0 < 0 && n1 < 0 && n2 < 0 && n3 < 0)) {
+      out = t;
+      return true;
+    }
+  }
+  return false;
+}
+
+// R17 in 3D: T^D_l keeps the tetrahedra of sigma^(l) that the fine elements
+// cover to at least (1 - 1e-9) of their volume.  The coverage of the level-J
+// tetrahedra is the exact intersection volume with the fine elements; a
+// coarser tetrahedron's coverage is the sum over the level-J tetrahedra
+// nested in it (found by their centroids).
+void dirichlet_tets(Oracle& o, std::vector<std::vector<std::array<uint64_t, 4>>>& inside) {
+  const int J = o.J;
+  std::vector<std::array<uint64_t, 4>> tJ;
+  level_tets(o, J, tJ);
+  std::map<std::array<uint64_t, 4>, int64_t> idx;
+  for (size_t t = 0; t < tJ.size(); ++t) idx[tJ[t]] = (int64_t)t;
+  std::vector<double> cov(tJ.size(), 0.0);
+  std::vector<std::array<uint64_t, 4>> leaves, kt;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    P3 T[4];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < 4; ++v)
+      for (int k = 0; k < 3; ++k) {
+        T[v][k] = o.X[(int64_t)o.E[4 * e + v] * 3 + k];
+        lo[k] = std::min(lo[k], T[v][k]);
+        hi[k] = std::max(hi[k], T[v][k]);
+      }
+    leaves.clear();
+    leaves_overlapping3(o, lo, hi, leaves);
+    for (auto& b : leaves) {
+      kt.clear();
+      uint64_t q[3] = {b[1], b[2], b[3]};
+      box_tets(o, (int)b[0], q, J, kt);
+      for (auto& k4 : kt) {
+        P3 K[4];
+        tet_points(o, k4, K);
+        std::vector<SignedTet> P = intersect_tets(T, K);
+        if (P.empty()) continue;
+        cov[idx.at(k4)] += pieces_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
+      }
+    }
+  }
+  inside.assign(J + 1, {});
+  for (int l = 0; l <= J; ++l) {
+    std::vector<std::array<uint64_t, 4>> tl;
+    level_tets(o, l, tl);
+    std::map<std::array<uint64_t, 4>, double> cl;
+    if (l == J) {
+      for (size_t t = 0; t < tJ.size(); ++t) cl[tJ[t]] = cov[t];
+    } else {
+      for (size_t t = 0; t < tJ.size(); ++t) {
+        uint64_t X4[3] = {0, 0, 0};
+        for (int v = 0; v < 4; ++v) {
+          uint64_t q[3];
+          xyz3(tJ[t][v], q);
+          for (int d = 0; d < 3; ++d) X4[d] += q[d];
+        }
+        std::array<uint64_t, 4> anc;
+        if (!locate_level_tet(o, l, X4, anc)) {
+          o.err = "oracle: nested tetrahedron not located";
+          return;
+        }
+        cl[anc] += cov[t];
+      }
+    }
+    for (auto& t : tl) {
+      P3 K[4];
+      tet_points(o, t, K);
+      if (cl[t] >= (1.0 - 1e-9) * tet_volume(K[0], K[1], K[2], K[3])) inside[l].push_back(t);
+    }
+  }
+}
+
 void build_aux3(Oracle& o) {
   const int J = o.J;
   o.LB = J + 1;
@@ -1435,15 +1546,52 @@ void build_aux3(Oracle& o) {
     return;
   }
   o.lv.assign(J + 1, Level());
+  // does the domain fill the root cube?
+  {
+    double vol = 0.0;
+    for (int64_t e = 0; e < o.ne; ++e) {
+      P3 T[4];
+      for (int v = 0; v < 4; ++v)
+        for (int k = 0; k < 3; ++k) T[v][k] = o.X[(int64_t)o.E[4 * e + v] * 3 + k];
+      vol += tet_volume(T[0], T[1], T[2], T[3]);
+    }
+    o.boxdomain = std::fabs(vol - o.L * o.L * o.L) <= 1e-12 * o.L * o.L * o.L;
+  }
+  std::vector<std::vector<std::array<uint64_t, 4>>> inside;
+  if (!o.boxdomain) {
+    dirichlet_tets(o, inside);
+    if (!o.err.empty()) return;
+  }
   for (int l = 0; l <= J; ++l) {
     Level& L = o.lv[l];
-    level_tets(o, l, L.tet);
+    if (o.boxdomain)
+      level_tets(o, l, L.tet);
+    else
+      L.tet = inside[l];
     for (auto& t : L.tet)
       for (int k = 0; k < 4; ++k) L.allkey.push_back(t[k]);
     std::sort(L.allkey.begin(), L.allkey.end());
     L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
-    for (auto k : L.allkey)
-      if (!on_boundary3(o, k)) L.key.push_back(k);
+    if (o.boxdomain) {
+      for (auto k : L.allkey)
+        if (!on_boundary3(o, k)) L.key.push_back(k);
+    } else {
+      // Gamma_l = boundary of the union of T^D_l: vertices of faces that
+      // belong to one tetrahedron only
+      std::map<std::array<uint64_t, 3>, int> faces;
+      for (auto& t : L.tet)
+        for (int k = 0; k < 4; ++k) {
+          std::array<uint64_t, 3> f = {t[(k + 1) % 4], t[(k + 2) % 4], t[(k + 3) % 4]};
+          std::sort(f.begin(), f.end());
+          faces[f] += 1;
+        }
+      std::set<uint64_t> gamma;
+      for (auto& kv : faces)
+        if (kv.second == 1)
+          for (int k = 0; k < 3; ++k) gamma.insert(kv.first[k]);
+      for (auto k : L.allkey)
+        if (!gamma.count(k)) L.key.push_back(k);
+    }
   }
   o.c = 0;
   for (int l = 0; l <= J; ++l)
@@ -1473,10 +1621,12 @@ void build_aux3(Oracle& o) {
       for (auto& k4 : kt) {
         P3 K[4];
         tet_points(o, k4, K);
+        auto it = tet_index.find(k4);
+        if (it == tet_index.end()) continue;  // outside Omega (not in T^D_J)
         std::vector<SignedTet> P = intersect_tets(T, K);
         if (P.empty()) continue;
         double vol = pieces_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
-        num[tet_index.at(k4)] += a * vol;
+        num[it->second] += a * vol;
       }
     }
   }
@@ -1609,6 +1759,7 @@ void build_transfer3(Oracle& o) {
     }
   std::vector<std::vector<std::pair<int32_t, double>>> rows(n), rows_full(n);
   std::vector<std::array<uint64_t, 4>> leaves, kt;
+  std::set<std::array<uint64_t, 4>> tet_in(LJ.tet.begin(), LJ.tet.end());
   for (int64_t i = 0; i < n; ++i) {
     int32_t v = o.vertex_of_free[i];
     int32_t e = sigma[v];
@@ -1637,6 +1788,7 @@ void build_transfer3(Oracle& o) {
       uint64_t q[3] = {b[1], b[2], b[3]};
       box_tets(o, (int)b[0], q, o.J, kt);
       for (auto& k4 : kt) {
+        if (!o.boxdomain && !tet_in.count(k4)) continue;  // aux hat functions vanish outside Omega^D_J
         P3 K[4];
         tet_points(o, k4, K);
         std::vector<SignedTet> P = intersect_tets(T, K);
@@ -2068,6 +2220,11 @@ int64_t orc_info(void* h, const char* what, int l) {
     return (int64_t)t.size();
   }
   if (w == "ntet") return (int64_t)o.lv.at(l).tet.size();
+  if (w == "nalltet") {
+    std::vector<std::array<uint64_t, 4>> t;
+    level_tets(o, l, t);
+    return (int64_t)t.size();
+  }
   if (w == "LB") return o.LB;
   if (w == "nnzA") return l < 0 ? (int64_t)o.A.col.size() : (int64_t)o.lv.at(l).A.col.size();
   if (w == "nI") return (int64_t)o.lv.at(l).I.col.size();
@@ -2116,6 +2273,12 @@ int orc_get(void* h, const char* what, int l, void* out) {
     return 0;
   }
   if (w == "level_tet") { memcpy(out, o.lv.at(l).tet.data(), o.lv[l].tet.size() * 32); return 0; }
+  if (w == "level_alltet") {  // every tetrahedron of sigma^(l), inside Omega or not
+    std::vector<std::array<uint64_t, 4>> t;
+    level_tets(o, l, t);
+    memcpy(out, t.data(), t.size() * 32);
+    return 0;
+  }
   if (w == "finest_coef") { memcpy(out, o.finest_coef.data(), o.finest_coef.size() * 8); return 0; }
   if (w == "smooth") {
     if (l < 0) memcpy(out, o.fine_smooth.data(), o.fine_smooth.size() * 4);

@@ -234,6 +234,36 @@ def grid2d_domain(nside: int, seed: int, shape: str = "L", jitter: float = 0.2) 
     return Mesh(2, V, E, bflag, None, dict(kind="grid2d_domain", nside=nside, seed=seed, shape=shape, jitter=jitter))
 
 
+def grid3d_domain(nside: int, seed: int, shape: str = "L", jitter: float = 0.15) -> Mesh:
+    """A non-box domain cut from ``grid3d(nside, seed, jitter)``.
+
+    shape "L": the elements whose centroid lies in (1/2, 1]^2 x [0, 1] are
+    removed (an L-shaped prism); "hole": those with centroid within 1/4 (max
+    norm) of (1/2, 1/2, 1/2) are removed (a cube with a cubic cavity).
+    Unused vertices are dropped; every vertex on a boundary face (a face of one
+    element only) is Dirichlet.  The bounding box stays [0,1]^3.
+    """
+    m = grid3d(nside, seed, jitter=jitter)
+    c = m.verts[m.elems].mean(axis=1)
+    if shape == "L":
+        drop = (c[:, 0] > 0.5) & (c[:, 1] > 0.5)
+    elif shape == "hole":
+        drop = np.all(np.abs(c - 0.5) < 0.25, axis=1)
+    else:
+        raise ValueError(shape)
+    E = m.elems[~drop]
+    used = np.unique(E)
+    remap = -np.ones(m.nv, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    E = remap[E].astype(np.int32)
+    V = m.verts[used]
+    fc = np.sort(np.concatenate([E[:, [1, 2, 3]], E[:, [0, 2, 3]], E[:, [0, 1, 3]], E[:, [0, 1, 2]]]), axis=1)
+    uniq, cnt = np.unique(fc, axis=0, return_counts=True)
+    bflag = np.zeros(V.shape[0], dtype=np.uint8)
+    bflag[np.unique(uniq[cnt == 1])] = DIRICHLET
+    return Mesh(3, V, E, bflag, None, dict(kind="grid3d_domain", nside=nside, seed=seed, shape=shape, jitter=jitter))
+
+
 def nodal_uniform(mesh: Mesh, seed: int, k: int = 1) -> np.ndarray:
     """Nodal source values U[-1, 1], shape [nv] (k=1) or [k, nv]; 0 on Dirichlet vertices."""
     rng = np.random.Generator(np.random.PCG64(seed))

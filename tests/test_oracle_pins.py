@@ -936,3 +936,49 @@ def test_dirichlet_domain_pcg_dense_and_spd(gen, shape):
     # nested Dirichlet hierarchies: every level's free nodes are free on the finer levels
     for l in range(o.c + 1, o.J + 1):
         assert set(o.level_keys(l - 1).tolist()) <= set(o.level_keys(l).tolist())
+
+
+# ------------------------------------------------ Dirichlet grids in 3D (R17)
+def test_dirichlet3d_aligned_l_prism_tets_and_free_nodes(gen):
+    # Unjittered L-shaped prism: the cut planes x = 1/2 and y = 1/2 are box
+    # faces from depth 1 on, so a tetrahedron of sigma^(l >= 1) lies in Omega
+    # exactly when its centroid does; the root cube's six tetrahedra all
+    # contain the diagonal point (3/4, 3/4, 3/4) of the removed quarter.  The
+    # free nodes are the lattice nodes of sigma^(l) off the boundary of Omega.
+    m = gen.grid3d_domain(9, 1, "L", jitter=0.0)
+    o = oracle.Oracle(m)
+    a = o.root()
+    amin, L = np.array(a[:3]), a[3]
+    top = 2 ** (o.J + 1)
+    for l in range(o.J + 1):
+        allt = o.level_alltet(l)
+        x, y, z = (np.asarray(v, dtype=np.float64).reshape(-1, 4) for v in _xyz3(allt.reshape(-1)))
+        cx, cy = amin[0] + x.mean(1) / top * L, amin[1] + y.mean(1) / top * L
+        want = {tuple(t) for t, ok in zip(allt.tolist(), (cx < 0.5) | (cy < 0.5)) if ok and l >= 1}
+        got = {tuple(t) for t in o.level_tet(l).tolist()}
+        assert got == want, l
+        keys = np.unique(allt.reshape(-1))
+        qx, qy, qz = (np.asarray(v, dtype=np.float64) / top for v in _xyz3(keys))
+        px, py = amin[0] + qx * L, amin[1] + qy * L
+        interior = (qx > 0) & (qx < 1) & (qy > 0) & (qy < 1) & (qz > 0) & (qz < 1)
+        interior &= ~((px >= 0.5 - 1e-12) & (py >= 0.5 - 1e-12))
+        assert np.array_equal(np.sort(keys[interior]), o.level_keys(l)), l
+
+
+@pytest.mark.parametrize("shape", ["L", "hole"])
+def test_dirichlet3d_domain_pcg_dense_and_spd(gen, shape):
+    m = gen.grid3d_domain(7, 5, shape)
+    o = oracle.Oracle(m, coarse_max=8)
+    assert o.c < o.J
+    # the domain cuts the finest grid: fewer tetrahedra than sigma^(J)
+    assert o.level_tet(o.J).shape[0] < o.info("nalltet", o.J)
+    b = o.mass_apply(gen.nodal_uniform(m, 2))
+    u, st, it, _ = o.solve(b, rtol=1e-13)
+    ref = np.linalg.solve(o.A().toarray(), b)
+    assert st == 0 and np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+    n = o.nfree
+    B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    for l in range(o.c + 1, o.J + 1):
+        assert set(o.level_keys(l - 1).tolist()) <= set(o.level_keys(l).tolist())
