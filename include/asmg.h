@@ -39,7 +39,7 @@ enum asmg_status {
   ASMG_NOT_CONVERGED = 1,     /* max_iter reached; u holds the last iterate */
   ASMG_ERR_INVALID_ARG = -1,  /* null pointer, bad size or bad parameter */
   ASMG_ERR_BAD_MESH = -2,     /* index out of range, non-positive measure, bad flag or coefficient */
-  ASMG_ERR_UNSUPPORTED = -3,  /* Neumann flags, dim not supported, non-box 3D domain */
+  ASMG_ERR_UNSUPPORTED = -3,  /* Neumann flags, dim not supported */
   ASMG_ERR_BREAKDOWN = -4,    /* <p, A p> <= 0 or NaN, or <r, z> <= 0 in PCG */
   ASMG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
   ASMG_ERR_OOM = -6,          /* device allocation failed */
@@ -89,13 +89,12 @@ int asmg_default_params(asmg_params* p);
  *   coeff      float64 [ne] per-element coefficient a_e > 0, or NULL for a = 1.
  *   params     NULL for the defaults.
  *   out        receives the handle (NULL on error).
- * In 2D the domain may be any polygon inside the square spanned by the
- * vertices' bounding box (the root box of Sec. 3.1).  When the element areas
- * do not add up to that square (within 1e-12 relative), the auxiliary grids
- * are the Dirichlet grids of Sec. 3.4: the auxiliary triangles the elements
- * cover, with zero values on the boundary of their union.  In 3D the domain
- * must be the cube spanned by the bounding box; otherwise
- * ASMG_ERR_UNSUPPORTED.  Inputs are
+ * The domain may be any polygon (polyhedron) inside the square (cube)
+ * spanned by the vertices' bounding box (the root box of Sec. 3.1).  When the
+ * element measures do not add up to that box (within 1e-12 relative), the
+ * auxiliary grids are the Dirichlet grids of Sec. 3.4: the auxiliary
+ * triangles (tetrahedra) the elements cover, with zero values on the
+ * boundary of their union.  Inputs are
  * validated before any other work (ASMG_ERR_BAD_MESH).  The call copies what
  * it keeps: the caller may free every input afterwards.
  */

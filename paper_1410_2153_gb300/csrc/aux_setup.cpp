@@ -601,8 +601,12 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
 
   // coefficient of one triangle of box (d, p) at a level where the box shows
   // as diagonal split (k = 0 lower-right, 1 upper-left) or as fan
+  // (the mean of a over the triangle, a = 0 outside Omega and a = 1 inside
+  // when no coefficient is given)
   auto tri_coef = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> double {
-    if (!varcoef) return 1.0;
+    if (!varcoef && !dgrid) return 1.0;
+    const auto& H = varcoef ? half : halfcov;
+    const auto& FI = varcoef ? fanint : fancov;
     double pa[2], pb[2], pc[2];
     lattice_point(tree, t[0], pa);
     lattice_point(tree, t[1], pb);
@@ -612,10 +616,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     if (diag) {
       const auto& bx = BX[d];
       size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
-      integral = half[d][i][k];
+      integral = H[d][i][k];
     } else {
       auto key = tri_sorted(t);
-      auto it = std::lower_bound(fanint.begin(), fanint.end(), std::pair<std::array<uint64_t, 3>, double>(key, -HUGE_VAL));
+      auto it = std::lower_bound(FI.begin(), FI.end(), std::pair<std::array<uint64_t, 3>, double>(key, -HUGE_VAL));
       integral = it->second;
     }
     return integral / area;

@@ -436,11 +436,6 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     out.nlevel[l] = out.nlevel[l - 1] + nf;
     newnodes[l] = std::move(nn);
   }
-  out.c = 0;
-  for (int l = 0; l <= J; ++l)
-    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
-  const int c = out.c;
-
   // tetrahedra of every leaf box at the finest level: ftet[first[d][i] ..
   // first[d][i] + nft[d][i]) for leaf i of depth d (first = -1: split box)
   std::vector<Tet> ftet;
@@ -492,15 +487,21 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   // element coefficients: integrals of a over the 6 Kuhn tetrahedra of every
   // box (bottom-up) and over the fan tetrahedra of fanned leaves
   const bool varcoef = !mesh.coeff.empty();
-  std::vector<std::vector<std::array<double, 6>>> kint(J + 1);
-  std::unordered_map<uint64_t, double> fanint;  // keyed by the sorted tet's hash below
+  // R17: a domain that does not fill the root cube uses the Dirichlet grids
+  // T^D_l (tetrahedra inside Omega); the clipping pass then also measures how
+  // much of each tetrahedron the fine elements cover (kcov, fancov)
+  const bool dgrid = !mesh.boxdomain;
+  std::vector<std::vector<std::array<double, 6>>> kint(J + 1), kcov(J + 1);
+  std::unordered_map<uint64_t, double> fanint, fancov;  // keyed by the sorted tet's hash below
   auto tet_hash = [](Tet t) {
     std::sort(t.begin(), t.end());
     uint64_t hsh = 1469598103934665603ULL;
     for (auto v : t) hsh = (hsh ^ v) * 1099511628211ULL;
     return hsh;
   };
-  if (varcoef) {
+  if (varcoef || dgrid) {
+    // the constant-leaf shortcut below needs elements that tile every leaf
+    const bool skip_const = varcoef && !dgrid;
     // elements in Morton order of their lowest corner, in chunks of 4096;
     // each chunk sums its overlaps per leaf tetrahedron, and the chunk sums
     // are added in chunk order (deterministic for any thread count)
@@ -529,7 +530,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       lval[q].store(0, std::memory_order_relaxed);
       lmixed[q].store(0, std::memory_order_relaxed);
     }
-    pfor(mesh.ne, [&](unsigned, int64_t b0, int64_t b1) {
+    if (skip_const) pfor(mesh.ne, [&](unsigned, int64_t b0, int64_t b1) {
       std::vector<std::pair<int, uint64_t>> lv, st;
       for (int64_t e = b0; e < b1; ++e) {
         TetP S;
@@ -551,15 +552,16 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         }
       }
     });
-    std::vector<std::vector<std::pair<int64_t, double>>> csum(nch);
+    std::vector<std::vector<std::pair<int64_t, double>>> csum(nch), ccov(nch);
     std::atomic<int64_t> nextc(0);
     auto work = [&]() {
       std::vector<std::pair<int, uint64_t>> lv, st;
-      std::vector<std::pair<int64_t, double>> acc;
+      std::vector<std::pair<int64_t, double>> acc, cac;
       for (;;) {
         const int64_t ch = nextc.fetch_add(1);
         if (ch >= nch) return;
         acc.clear();
+        cac.clear();
         for (int64_t k = ch * CH; k < std::min(mesh.ne, (ch + 1) * CH); ++k) {
           const int64_t e = order[k].second;
           TetP S;
@@ -573,29 +575,33 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             int nq;
             int32_t leaf;
             leaf_range(lf, f0, nq, &leaf);
-            if (!lmixed[leaf].load(std::memory_order_relaxed) && lval[leaf].load(std::memory_order_relaxed) != 0)
+            if (skip_const && !lmixed[leaf].load(std::memory_order_relaxed) &&
+                lval[leaf].load(std::memory_order_relaxed) != 0)
               continue;
             for (int q = 0; q < nq; ++q) {
               TetP K;
               leaf_tet(f0 + q, K);
               double vol = 0;
               clip::clip_tets(tet4(S), tet4(K), [&](const clip::Tet4& pc) { vol += clip::volume(pc); });
-              if (vol > 0) acc.push_back({f0 + q, vol * mesh.coeff[e]});
+              if (!(vol > 0)) continue;
+              if (varcoef) acc.push_back({f0 + q, vol * mesh.coeff[e]});
+              if (dgrid) cac.push_back({f0 + q, vol});
             }
           }
         }
-        std::stable_sort(acc.begin(), acc.end(),
-                         [](const std::pair<int64_t, double>& x, const std::pair<int64_t, double>& y) {
-                           return x.first < y.first;
-                         });
-        auto& out = csum[ch];
-        for (size_t i = 0; i < acc.size();) {
-          size_t j = i;
-          double sum = 0;
-          while (j < acc.size() && acc[j].first == acc[i].first) sum += acc[j++].second;
-          out.push_back({acc[i].first, sum});
-          i = j;
-        }
+        auto reduce = [](std::vector<std::pair<int64_t, double>>& a, std::vector<std::pair<int64_t, double>>& out) {
+          std::stable_sort(a.begin(), a.end(), [](const std::pair<int64_t, double>& x,
+                                                  const std::pair<int64_t, double>& y) { return x.first < y.first; });
+          for (size_t i = 0; i < a.size();) {
+            size_t j = i;
+            double sum = 0;
+            while (j < a.size() && a[j].first == a[i].first) sum += a[j++].second;
+            out.push_back({a[i].first, sum});
+            i = j;
+          }
+        };
+        reduce(acc, csum[ch]);
+        reduce(cac, ccov[ch]);
       }
     };
     {
@@ -604,10 +610,14 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       for (unsigned t = 0; t < nt; ++t) th.emplace_back(work);
       for (auto& x : th) x.join();
     }
-    std::vector<double> I(ftet.size(), 0.0);
+    std::vector<double> I(ftet.size(), 0.0), C(ftet.size(), 0.0);
     for (auto& v : csum)
       for (auto& pr : v) I[pr.first] += pr.second;
+    for (auto& v : ccov)
+      for (auto& pr : v) C[pr.first] += pr.second;
     csum.clear();
+    ccov.clear();
+    if (skip_const)
     for (int d = 0; d <= J; ++d)
       for (size_t i = 0; i < BX[d].size(); ++i) {
         const int32_t leaf = lid[d][i];
@@ -621,9 +631,16 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           I[first[d][i] + q] = a * (std::fabs(vol6(K[0], K[1], K[2], K[3])) / 6.0);
         }
       }
-    // bottom-up Kuhn integrals
+    // bottom-up Kuhn integrals: a (kint, fanint) and the covered volume
+    // (kcov, fancov)
+    for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 0 && !varcoef) continue;
+    if (pass == 1 && !dgrid) continue;
+    const std::vector<double>& IA = pass == 0 ? I : C;
+    auto& KI = pass == 0 ? kint : kcov;
+    auto& FI = pass == 0 ? fanint : fancov;
     for (int d = J; d >= 0; --d) {
-      kint[d].assign(BX[d].size(), {0, 0, 0, 0, 0, 0});
+      KI[d].assign(BX[d].size(), {0, 0, 0, 0, 0, 0});
       const uint64_t s = 1ULL << (T.LB - d);
       for (size_t i = 0; i < BX[d].size(); ++i) {
         const uint64_t p = BX[d][i];
@@ -643,8 +660,8 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           const int nq = nft[d][i];
           const bool kuhn = nq == 6;  // a coned box has at least 12 tetrahedra
           for (int q = 0; q < nq; ++q) {
-            kint[d][i][local_kuhn(ftet[f0 + q])] += I[f0 + q];
-            if (!kuhn) fanint[tet_hash(ftet[f0 + q])] = I[f0 + q];
+            KI[d][i][local_kuhn(ftet[f0 + q])] += IA[f0 + q];
+            if (!kuhn) FI[tet_hash(ftet[f0 + q])] = IA[f0 + q];
           }
         } else {
           const auto& ch = BX[d + 1];
@@ -653,14 +670,120 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             const uint64_t cp = ch[j + cidx];
             std::vector<Tet> kt;
             box_tets(T, d + 1, cp, d + 1, kt);  // the child's 6 Kuhn tetrahedra
-            for (int q = 0; q < 6; ++q) kint[d][i][local_kuhn(kt[q])] += kint[d + 1][j + cidx][q];
+            for (int q = 0; q < 6; ++q) KI[d][i][local_kuhn(kt[q])] += KI[d + 1][j + cidx][q];
           }
         }
       }
     }
+    }
   }
+  // tetrahedron q of box (d, p) at a level where the box shows as Kuhn
+  // (kuhn) or coned: in T^D_l when the fine elements cover (1 - 1e-9) of it
+  auto tet_vol = [&](const Tet& t) {
+    double P[4][3];
+    for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, t[v], P[v]);
+    V3 a = {P[0][0], P[0][1], P[0][2]}, b = {P[1][0], P[1][1], P[1][2]}, cc = {P[2][0], P[2][1], P[2][2]},
+       dd = {P[3][0], P[3][1], P[3][2]};
+    return std::fabs(vol6(a, b, cc, dd)) / 6.0;
+  };
+  auto tet_inside = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> bool {
+    if (!dgrid) return true;
+    double cov;
+    if (kuhn) {
+      const auto& bx = BX[d];
+      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      cov = kcov[d][i][q];
+    } else {
+      auto it = fancov.find(tet_hash(t));
+      cov = it == fancov.end() ? 0.0 : it->second;
+    }
+    return cov >= (1.0 - 1e-9) * tet_vol(t);
+  };
+  // node x is free at level l (a vertex of sigma^(l) off the boundary of
+  // Omega^D_l): every level-l tetrahedron around it is inside.  The box
+  // shown at level l around x in each octant holds those tetrahedra.
+  auto free_at = [&](uint64_t x, int l, std::vector<Tet>& kt) -> bool {
+    if (bnd3(T, x)) return false;
+    uint64_t X[3];
+    um3(x, X);
+    bool node = false;
+    for (int oct = 0; oct < 8; ++oct) {
+      int d = 0;
+      uint64_t p = 0;
+      while (d < l && T.split(d, p)) {
+        const uint64_t sz = 1ULL << (T.LB - d), hf = sz >> 1;
+        uint64_t cb[3], ch = 0;
+        um3(p, cb);
+        for (int a = 0; a < 3; ++a) {
+          const uint64_t x0 = cb[a] * sz;
+          const bool pos = (oct >> a) & 1;
+          const uint64_t bit = pos ? (X[a] >= x0 + hf) : (X[a] > x0 + hf);
+          ch |= bit << a;
+        }
+        p = (p << 3) | ch;
+        ++d;
+      }
+      kt.clear();
+      bool kuhn = false;
+      box_tets(T, d, p, l, kt, &kuhn);
+      for (size_t q = 0; q < kt.size(); ++q) {
+        if (kt[q][0] != x && kt[q][1] != x && kt[q][2] != x && kt[q][3] != x) continue;
+        node = true;
+        if (!tet_inside(d, p, kuhn, (int)q, kt[q])) return false;
+      }
+    }
+    return node;
+  };
+  std::vector<int32_t> phi;  // first level at which each aux node is free (Dirichlet grids)
+  if (dgrid) {
+    std::vector<int32_t> keep(out.aux_key.size(), 0);
+    pfor((int64_t)out.aux_key.size(), [&](unsigned, int64_t b0, int64_t b1) {
+      std::vector<Tet> kt;
+      for (int64_t q = b0; q < b1; ++q) keep[q] = free_at(out.aux_key[q], J, kt);
+    });
+    std::vector<uint64_t> ak;
+    for (size_t q = 0; q < keep.size(); ++q)
+      if (keep[q]) ak.push_back(out.aux_key[q]);
+    out.aux_key.swap(ak);
+    // from its birth level on, a node is free from the first level whose
+    // tetrahedra around it are all inside (they only shrink inside covered ones)
+    std::vector<std::pair<uint64_t, int32_t>> born;
+    for (int l = 1; l <= J; ++l)
+      for (auto& v : newnodes[l]) born.push_back({v[0], l});
+    std::sort(born.begin(), born.end());
+    phi.assign(AK.size(), J + 1);
+    pfor((int64_t)AK.size(), [&](unsigned, int64_t b0, int64_t b1) {
+      std::vector<Tet> kt;
+      for (int64_t q = b0; q < b1; ++q) {
+        auto it = std::lower_bound(born.begin(), born.end(), std::pair<uint64_t, int32_t>(AK[q], 0));
+        int l = (it != born.end() && it->first == AK[q]) ? it->second : 0;
+        while (l < J && !free_at(AK[q], l, kt)) ++l;
+        phi[q] = l;
+      }
+    });
+    out.nlevel.assign(J + 1, 0);
+    for (int32_t f : phi) out.nlevel[f] += 1;
+    for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
+  }
+  // aux ID of node x at level l, or -1 where it is not a free node there
+  auto level_id = [&](uint64_t x, int l) -> int32_t {
+    if (bnd3(T, x)) return -1;
+    const int32_t id = idx_of(AK, x);
+    if (dgrid && (id < 0 || phi[id] > l)) return -1;
+    return id;
+  };
+  // coarsest level used: finest level with at most coarse_max_dofs free nodes
+  out.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  const int c = out.c;
+
+  // mean of a over the tetrahedron (a = 0 outside Omega, a = 1 inside when no
+  // coefficient is given)
   auto tet_coef = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> double {
-    if (!varcoef) return 1.0;
+    if (!varcoef && !dgrid) return 1.0;
+    const auto& KI = varcoef ? kint : kcov;
+    const auto& FI = varcoef ? fanint : fancov;
     double P[4][3];
     for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, t[v], P[v]);
     V3 a = {P[0][0], P[0][1], P[0][2]}, b = {P[1][0], P[1][1], P[1][2]}, cc = {P[2][0], P[2][1], P[2][2]},
@@ -669,9 +792,9 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     if (kuhn) {
       const auto& bx = BX[d];
       const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
-      return kint[d][i][q] / vol;
+      return KI[d][i][q] / vol;
     }
-    return fanint.at(tet_hash(t)) / vol;
+    return FI.at(tet_hash(t)) / vol;
   };
 
   auto emit_box = [&](int d, uint64_t p, int l, std::vector<int32_t>& ids, std::vector<uint64_t>& keys,
@@ -680,9 +803,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     bool kuhn = false;
     box_tets(T, d, p, l, kt, &kuhn);
     for (size_t q = 0; q < kt.size(); ++q) {
+      if (!tet_inside(d, p, kuhn, (int)q, kt[q])) continue;  // outside Omega: not in T^D_l
       for (int v = 0; v < 4; ++v) {
         keys.push_back(kt[q][v]);
-        ids.push_back(bnd3(T, kt[q][v]) ? -1 : idx_of(AK, kt[q][v]));
+        ids.push_back(level_id(kt[q][v], l));
       }
       coef.push_back(tet_coef(d, p, kuhn, (int)q, kt[q]));
     }
@@ -722,7 +846,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           box_tets(T, rel[q].first, rel[q].second, l, kt);
           for (auto& tt : kt)
             for (int v = 0; v < 4; ++v)
-              if (!bnd3(T, tt[v])) part[t].push_back(tt[v]);
+              if (level_id(tt[v], l) >= 0) part[t].push_back(tt[v]);
         }
       });
       sm = uniq_parts(part);
@@ -736,19 +860,26 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         std::vector<Tet> kt;
         for (int64_t q = b0; q < b1; ++q) {
           const uint64_t p = ch[q];
-          kt.clear();
+          // free vertices of the box's new tetrahedra (inside Omega)
+          auto add = [&](int dd, uint64_t pp) {
+            kt.clear();
+            bool kuhn = false;
+            box_tets(T, dd, pp, l, kt, &kuhn);
+            for (size_t k = 0; k < kt.size(); ++k) {
+              if (!tet_inside(dd, pp, kuhn, (int)k, kt[k])) continue;
+              for (int v = 0; v < 4; ++v)
+                if (level_id(kt[k][v], l) >= 0) M.push_back(kt[k][v]);
+            }
+          };
           if (T.split(d, p)) {
             for (uint64_t cc = 0; cc < 8; ++cc) {
               R.push_back({d + 1, (p << 3) | cc});
-              box_tets(T, d + 1, (p << 3) | cc, l, kt);
+              add(d + 1, (p << 3) | cc);
             }
           } else {
             R.push_back({d, p});
-            box_tets(T, d, p, l, kt);
+            add(d, p);
           }
-          for (auto& tt : kt)
-            for (int v = 0; v < 4; ++v)
-              if (!bnd3(T, tt[v])) M.push_back(tt[v]);
           for (int oz = -1; oz <= 1; ++oz)
             for (int oy = -1; oy <= 1; ++oy)
               for (int ox = -1; ox <= 1; ++ox) {
@@ -787,11 +918,27 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
       L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
     }
-    for (auto& v : newnodes[l]) {
-      if (bnd3(T, v[0])) continue;
-      L.new_id.push_back(idx_of(AK, v[0]));
-      L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
-      L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
+    if (!dgrid) {
+      for (auto& v : newnodes[l]) {
+        if (bnd3(T, v[0])) continue;
+        L.new_id.push_back(idx_of(AK, v[0]));
+        L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
+        L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
+      }
+    } else {
+      // nodes free from level l on: born at l, the interpolant of the
+      // level-(l-1) function at the edge midpoint (a parent off the free
+      // nodes of l-1 contributes 0); born earlier on the boundary of
+      // Omega^D_(l-1), where that function vanishes: no parents
+      const auto& nn = newnodes[l];
+      for (size_t q = 0; q < AK.size(); ++q) {
+        if (phi[q] != l) continue;
+        auto it = std::lower_bound(nn.begin(), nn.end(), std::array<uint64_t, 3>{AK[q], 0, 0});
+        const bool born = it != nn.end() && (*it)[0] == AK[q];
+        L.new_id.push_back((int32_t)q);
+        L.new_p0.push_back(born ? level_id((*it)[1], l - 1) : -1);
+        L.new_p1.push_back(born ? level_id((*it)[2], l - 1) : -1);
+      }
     }
   }
 
@@ -828,10 +975,20 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     z.simp_key.resize(4 * ftet.size());
     if (!ftet.empty()) std::memcpy(z.simp_key.data(), ftet.data(), ftet.size() * sizeof(ftet[0]));
     z.simp_col.assign(4 * ftet.size(), -1);
-    pfor((int64_t)z.simp_key.size(), [&](unsigned, int64_t b0, int64_t b1) {
-      for (int64_t q = b0; q < b1; ++q)
-        if (!bnd3(T, z.simp_key[q])) z.simp_col[q] = idx_of(AK, z.simp_key[q]);
-    });
+    for (int d = 0; d <= J; ++d) {
+      const auto& bx = BX[d];
+      pfor((int64_t)bx.size(), [&](unsigned, int64_t b0, int64_t b1) {
+        for (int64_t i = b0; i < b1; ++i) {
+          const int64_t f0 = first[d][i];
+          if (f0 < 0) continue;
+          const int nq = nft[d][i];
+          for (int q = 0; q < nq; ++q) {
+            if (!tet_inside(d, bx[i], nq == 6, q, ftet[f0 + q])) continue;  // hats vanish outside Omega^D_J
+            for (int v = 0; v < 4; ++v) z.simp_col[4 * (f0 + q) + v] = level_id(ftet[f0 + q][v], J);
+          }
+        }
+      });
+    }
   }
 }
 

@@ -657,8 +657,8 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   build_tree_gpu(dim, nv, h->dX.p, ne, h->dE.p, prm.n_min, s, h->tree);
   h->stats.t_tree = now() - tt;
   // does the domain fill the root box (the element measures add up to
-  // L^dim)?  In 2D a domain that does not uses the Dirichlet auxiliary grids
-  // (Sec. 3.4); in 3D it must
+  // L^dim)?  A domain that does not uses the Dirichlet auxiliary grids
+  // (Sec. 3.4)
   {
     double meas = 0;
     for (int64_t e = 0; e < ne; ++e) {
@@ -677,11 +677,7 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       }
     }
     const double box = std::pow(h->tree.L, dim);
-    if (dim == 2)
-      m.boxdomain = std::fabs(meas - box) <= 1e-12 * box;
-    else if (std::fabs(meas - box) > 1e-11 * box)
-      ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "the domain is not the %s spanned by the vertices (measure %.17g vs %.17g)",
-                dim == 2 ? "square" : "cube", meas, box);
+    m.boxdomain = std::fabs(meas - box) <= 1e-12 * box;
   }
   build_all(*h, s);
   h->bytes_iter = prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
