@@ -32,6 +32,21 @@ METRIC = "dofs/s to rel. residual 1e-8"
 RTOL = 1e-8
 
 
+def replica_throughput(dist, device, units: float, ms_local: float):
+    """Replicas only (the solve does not shard): every rank solved its own
+    problem in ms_local milliseconds.  Returns the slowest rank's time and all
+    ranks' units divided by it (units per second).  `dist` is
+    torch.distributed or None (one process)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(u.item()) / (ms / 1e3)
+
+
 def _workload(name: str, seed: int):
     from paper_1410_2153_gb300 import meshgen
     if name == "graded2049":
@@ -403,12 +418,9 @@ def main():
             assert rc == asmg.ASMG_OK, (rc, asmg.amg_last_error())
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
         clocks = clk.stop() if clk else None
-        t = torch.tensor([ms], device=dev)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        results[prec] = dict(ms=float(t.item()), its=its, clocks=clocks)
+        ms, rate = replica_throughput(dist, dev, n * args.steps, e0.elapsed_time(e1))
+        results[prec] = dict(ms=ms, rate=rate, its=its, clocks=clocks)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     bh = b.cpu().numpy()
@@ -423,14 +435,12 @@ def main():
         asmg.amg_solve(s.h, bh, uh, RTOL, hist, sp)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / args.steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_ms, e2e_rate = replica_throughput(dist, dev, n, e2e_s * 1e3)
+    e2e_s = e2e_ms / 1e3
 
     mix = results[asmg.ASMG_MIXED]
     ms_step = mix["ms"] / args.steps
-    value = world * n / (ms_step / 1e3)
+    value = mix["rate"]
     it_mix = int(np.median(mix["its"]))
     peak, peak_kind = _peaks()
     # live per-kernel timing: one solve with every launch bracketed by CUDA
@@ -459,7 +469,7 @@ def main():
                                           "lv_export", "coarse", "transfer", "slots")},
                    "graph": not args.no_graph, "pdl": not args.no_pdl,
                    "l2": "working set (several GB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
-        "e2e": {"value": world * n / e2e_s, "unit": "dofs/s", "h2d_bytes_per_step": 8 * 2 * mesh.nv,
+        "e2e": {"value": e2e_rate, "unit": "dofs/s", "h2d_bytes_per_step": 8 * 2 * mesh.nv,
                 "d2h_bytes_per_step": 8 * mesh.nv + 8 * (it_mix + 1)},
         "gpu_launches": int(launches_per_solve) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -474,7 +484,7 @@ def main():
     if asmg.ASMG_FP64 in results:
         r64 = results[asmg.ASMG_FP64]
         ms64 = r64["ms"] / args.steps
-        line["fp64"] = {"value": world * n / (ms64 / 1e3), "ms_per_step": ms64,
+        line["fp64"] = {"value": r64["rate"], "ms_per_step": ms64,
                         "iterations": int(np.median(r64["its"]))}
         line["mixed_vs_fp64_speedup"] = ms64 / ms_step
     if rank == 0 and not args.no_cpu_baseline and world == 1:
