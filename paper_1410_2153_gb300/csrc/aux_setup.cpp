@@ -171,12 +171,26 @@ std::vector<V> merge_unique(std::vector<std::vector<V>>& parts) {
   for (auto& v : parts)
     if (!v.empty()) th.emplace_back([&v, &su] { su(v); });
   for (auto& x : th) x.join();
+  // concatenate the sorted parts, merge them pairwise in parallel rounds,
+  // then drop the duplicates that lay in different parts
   std::vector<V> all;
+  std::vector<size_t> cut(1, 0);
   for (auto& v : parts) {
+    if (v.empty()) continue;
     all.insert(all.end(), v.begin(), v.end());
+    cut.push_back(all.size());
     std::vector<V>().swap(v);
   }
-  su(all);
+  const size_t np = cut.size() - 1;
+  for (size_t w = 1; w < np; w *= 2) {
+    std::vector<std::thread> mt;
+    for (size_t t = 0; t + w < np; t += 2 * w) {
+      const size_t a = cut[t], m = cut[t + w], b = cut[std::min(np, t + 2 * w)];
+      mt.emplace_back([&all, a, m, b] { std::inplace_merge(all.begin() + a, all.begin() + m, all.begin() + b); });
+    }
+    for (auto& x : mt) x.join();
+  }
+  all.erase(std::unique(all.begin(), all.end()), all.end());
   return all;
 }
 
@@ -433,7 +447,9 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     for (int d = J; d >= 0; --d) {
       const auto& bx = BX[d];
       H[d].assign(bx.size(), {0.0, 0.0});
-      for (size_t i = 0; i < bx.size(); ++i) {
+      std::vector<std::vector<std::pair<std::array<uint64_t, 3>, double>>> fparts(MAX_THREADS);
+      parallel_for((int64_t)bx.size(), [&](unsigned tix, unsigned, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
         uint64_t p = bx[i];
         if (!T.split(d, p)) {
           bool h[4];
@@ -452,7 +468,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
               uint64_t bxx = compact(kt[k][1]), by = compact(kt[k][1] >> 1);
               bool lr = (ay == y0 && by == y0) || (ax == x0 + s && bxx == x0 + s);
               H[d][i][lr ? 0 : 1] += IA[f0 + k];
-              FI.push_back({tri_sorted(kt[k]), IA[f0 + k]});
+              fparts[tix].push_back({tri_sorted(kt[k]), IA[f0 + k]});
             }
           }
         } else {
@@ -467,6 +483,8 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
           H[d][i][1] = sw[1] + nw[0] + nw[1] + ne[1];
         }
       }
+      });
+      for (auto& fp : fparts) FI.insert(FI.end(), fp.begin(), fp.end());
     }
     }
     std::sort(fanint.begin(), fanint.end());

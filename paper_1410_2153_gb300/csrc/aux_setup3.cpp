@@ -295,13 +295,51 @@ std::vector<V> uniq_parts(std::vector<std::vector<V>>& parts) {
   for (auto& v : parts)
     if (!v.empty()) th.emplace_back([&v, &su] { su(v); });
   for (auto& x : th) x.join();
+  // concatenate the sorted parts, merge them pairwise in parallel rounds,
+  // then drop the duplicates that lay in different parts
   std::vector<V> all;
+  std::vector<size_t> cut(1, 0);
   for (auto& v : parts) {
+    if (v.empty()) continue;
     all.insert(all.end(), v.begin(), v.end());
+    cut.push_back(all.size());
     std::vector<V>().swap(v);
   }
-  su(all);
+  const size_t np = cut.size() - 1;
+  for (size_t w = 1; w < np; w *= 2) {
+    std::vector<std::thread> mt;
+    for (size_t t = 0; t + w < np; t += 2 * w) {
+      const size_t a = cut[t], m = cut[t + w], b = cut[std::min(np, t + 2 * w)];
+      mt.emplace_back([&all, a, m, b] { std::inplace_merge(all.begin() + a, all.begin() + m, all.begin() + b); });
+    }
+    for (auto& x : mt) x.join();
+  }
+  all.erase(std::unique(all.begin(), all.end()), all.end());
   return all;
+}
+
+// sort v: contiguous chunks sorted in parallel, then merged pairwise in
+// parallel rounds (the result is the sorted sequence, as from std::sort)
+template <class V>
+void psort(std::vector<V>& v) {
+  const int64_t n = (int64_t)v.size();
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < (1 << 16)) nt = 1;
+  std::vector<int64_t> cut(nt + 1);
+  for (unsigned t = 0; t <= nt; ++t) cut[t] = n * t / nt;
+  {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back([&, t] { std::sort(v.begin() + cut[t], v.begin() + cut[t + 1]); });
+    for (auto& x : th) x.join();
+  }
+  for (unsigned w = 1; w < nt; w *= 2) {
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t + w < nt; t += 2 * w) {
+      const int64_t a = cut[t], m = cut[t + w], b = cut[std::min(nt, t + 2 * w)];
+      th.emplace_back([&v, a, m, b] { std::inplace_merge(v.begin() + a, v.begin() + m, v.begin() + b); });
+    }
+    for (auto& x : th) x.join();
+  }
 }
 
 // index of the Kuhn tetrahedron of a box holding point u (local coordinates
@@ -384,12 +422,18 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   for (int l = 1; l <= J; ++l) {
     const int d = l - 1;
     const uint64_t s = 1ULL << (T.LB - d), h = s / 2;
-    std::vector<std::array<uint64_t, 3>> nn;
-    for (uint64_t p : BX[d]) {
+    // per-thread runs of consecutive boxes, appended in box order
+    const unsigned ntn = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::vector<std::array<uint64_t, 3>>> nparts(ntn);
+    std::vector<std::vector<uint64_t>> cparts(ntn);
+    pfor((int64_t)BX[d].size(), [&](unsigned tix, int64_t b0, int64_t b1) {
+    auto& nn = nparts[tix];
+    for (int64_t bi = b0; bi < b1; ++bi) {
+      const uint64_t p = BX[d][bi];
       const bool sp = T.split(d, p);
       BoxShape sh = shape(T, d, p, l);
       if (!sp && !sh.hang) continue;
-      changed[l].push_back(p);
+      cparts[tix].push_back(p);
       uint64_t c[3];
       um3(p, c);
       auto pt = [&](int u0, int u1, int u2) { return m3(c[0] * s + u0 * h, c[1] * s + u1 * h, c[2] * s + u2 * h); };
@@ -426,6 +470,12 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             }
         }
     }
+    });
+    std::vector<std::array<uint64_t, 3>> nn;
+    for (unsigned t = 0; t < ntn; ++t) {
+      nn.insert(nn.end(), nparts[t].begin(), nparts[t].end());
+      changed[l].insert(changed[l].end(), cparts[t].begin(), cparts[t].end());
+    }
     std::sort(nn.begin(), nn.end());
     nn.erase(std::unique(nn.begin(), nn.end(),
                          [](const std::array<uint64_t, 3>& x, const std::array<uint64_t, 3>& y) { return x[0] == y[0]; }),
@@ -447,12 +497,32 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     first[d].assign(BX[d].size(), -1);
     nft[d].assign(BX[d].size(), 0);
     lid[d].assign(BX[d].size(), -1);
+    // per-thread runs of consecutive boxes, appended in box order
+    const unsigned ntl = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::vector<Tet>> tparts(ntl);
+    std::vector<uint8_t> isleaf(BX[d].size(), 0);
+    pfor((int64_t)BX[d].size(), [&](unsigned t, int64_t b0, int64_t b1) {
+      for (int64_t i = b0; i < b1; ++i) {
+        if (T.split(d, BX[d][i])) continue;
+        isleaf[i] = 1;
+        const size_t before = tparts[t].size();
+        box_tets(T, d, BX[d][i], J, tparts[t]);
+        nft[d][i] = (uint8_t)(tparts[t].size() - before);
+      }
+    });
+    const int64_t base = (int64_t)ftet.size();
+    int64_t at = base;
     for (size_t i = 0; i < BX[d].size(); ++i) {
-      if (T.split(d, BX[d][i])) continue;
-      first[d][i] = (int64_t)ftet.size();
-      box_tets(T, d, BX[d][i], J, ftet);
-      nft[d][i] = (uint8_t)(ftet.size() - first[d][i]);
+      if (!isleaf[i]) continue;
+      first[d][i] = at;
       lid[d][i] = (int32_t)nleaf++;
+      at += nft[d][i];
+    }
+    ftet.resize(at);
+    int64_t pos = base;
+    for (auto& tp : tparts) {
+      std::copy(tp.begin(), tp.end(), ftet.begin() + pos);
+      pos += (int64_t)tp.size();
     }
   }
   const double lat_scale = std::ldexp(1.0, T.LB) / tree.L;
@@ -506,18 +576,20 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     // each chunk sums its overlaps per leaf tetrahedron, and the chunk sums
     // are added in chunk order (deterministic for any thread count)
     std::vector<std::pair<uint64_t, int32_t>> order(mesh.ne);
-    for (int64_t e = 0; e < mesh.ne; ++e) {
-      TetP S;
-      fine_tet(e, S);
-      uint64_t q[3];
-      for (int k = 0; k < 3; ++k) {
-        double mn = std::min(std::min(S[0][k], S[1][k]), std::min(S[2][k], S[3][k]));
-        double u = std::floor((mn - tree.amin[k]) * lat_scale);
-        q[k] = (uint64_t)std::min(std::max(u, 0.0), std::ldexp(1.0, T.LB) - 1);
+    pfor(mesh.ne, [&](unsigned, int64_t b0, int64_t b1) {
+      for (int64_t e = b0; e < b1; ++e) {
+        TetP S;
+        fine_tet(e, S);
+        uint64_t q[3];
+        for (int k = 0; k < 3; ++k) {
+          double mn = std::min(std::min(S[0][k], S[1][k]), std::min(S[2][k], S[3][k]));
+          double u = std::floor((mn - tree.amin[k]) * lat_scale);
+          q[k] = (uint64_t)std::min(std::max(u, 0.0), std::ldexp(1.0, T.LB) - 1);
+        }
+        order[e] = {m3(q[0], q[1], q[2]), (int32_t)e};
       }
-      order[e] = {m3(q[0], q[1], q[2]), (int32_t)e};
-    }
-    std::sort(order.begin(), order.end());
+    });
+    psort(order);
     const int64_t CH = 4096, nch = (mesh.ne + CH - 1) / CH;
     // A leaf whose overlapping elements all have one coefficient value a has
     // the average a on each of its tetrahedra (the fine elements tile it): only
@@ -642,7 +714,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (int d = J; d >= 0; --d) {
       KI[d].assign(BX[d].size(), {0, 0, 0, 0, 0, 0});
       const uint64_t s = 1ULL << (T.LB - d);
-      for (size_t i = 0; i < BX[d].size(); ++i) {
+      const unsigned ntb = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+      std::vector<std::vector<std::pair<uint64_t, double>>> fparts(ntb);
+      pfor((int64_t)BX[d].size(), [&](unsigned tix, int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i) {
         const uint64_t p = BX[d][i];
         uint64_t cb[3];
         um3(p, cb);
@@ -661,7 +736,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           const bool kuhn = nq == 6;  // a coned box has at least 12 tetrahedra
           for (int q = 0; q < nq; ++q) {
             KI[d][i][local_kuhn(ftet[f0 + q])] += IA[f0 + q];
-            if (!kuhn) FI[tet_hash(ftet[f0 + q])] = IA[f0 + q];
+            if (!kuhn) fparts[tix].push_back({tet_hash(ftet[f0 + q]), IA[f0 + q]});
           }
         } else {
           const auto& ch = BX[d + 1];
@@ -674,6 +749,9 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           }
         }
       }
+      });
+      for (auto& fp : fparts)
+        for (auto& kv : fp) FI[kv.first] = kv.second;
     }
     }
   }
