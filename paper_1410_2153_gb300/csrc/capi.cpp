@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include "handle.h"
@@ -52,25 +53,52 @@ void copy_out(double* dst, const double* src, int64_t n, cudaStream_t s) {
 
 int64_t pad32(int64_t n) { return (n + 31) / 32 * 32; }
 
+// f(begin, end) over contiguous ranges of [0, n) on host threads
+template <class F>
+void host_for(int64_t n, F f) {
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < (1 << 15)) nt = 1;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt); });
+  for (auto& x : th) x.join();
+}
+
 // rows of a host CSR selected and renumbered: out row k = A row sel[k] (or
-// empty when sel[k] < 0), columns mapped by cmap (dropped when < 0)
+// empty when sel[k] < 0), columns mapped by cmap (dropped when < 0); rows
+// counted, then filled, in parallel
 HostCSR select_rows(const HostCSR& A, const std::vector<int64_t>& sel, const std::vector<int32_t>* cmap,
                     const std::vector<uint8_t>* colkeep) {
   HostCSR B;
   B.nr = (int64_t)sel.size();
   B.nc = A.nc;
   B.ptr.assign(B.nr + 1, 0);
-  for (int64_t k = 0; k < B.nr; ++k) {
-    if (sel[k] >= 0)
-      for (int64_t p = A.ptr[sel[k]]; p < A.ptr[sel[k] + 1]; ++p) {
-        int32_t c = A.col[p];
-        if (colkeep && !(*colkeep)[c]) continue;
-        if (A.val[p] == 0.0) continue;  // couplings that vanish by symmetry are not stored
-        B.col.push_back(cmap ? (*cmap)[c] : c);
-        B.val.push_back(A.val[p]);
-      }
-    B.ptr[k + 1] = (int64_t)B.col.size();
-  }
+  auto keep = [&](int64_t p) {
+    // couplings that vanish by symmetry are not stored
+    return !(colkeep && !(*colkeep)[A.col[p]]) && A.val[p] != 0.0;
+  };
+  host_for(B.nr, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) {
+      int64_t c = 0;
+      if (sel[k] >= 0)
+        for (int64_t p = A.ptr[sel[k]]; p < A.ptr[sel[k] + 1]; ++p) c += keep(p);
+      B.ptr[k + 1] = c;
+    }
+  });
+  for (int64_t k = 0; k < B.nr; ++k) B.ptr[k + 1] += B.ptr[k];
+  B.col.resize(B.ptr[B.nr]);
+  B.val.resize(B.ptr[B.nr]);
+  host_for(B.nr, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) {
+      if (sel[k] < 0) continue;
+      int64_t q = B.ptr[k];
+      for (int64_t p = A.ptr[sel[k]]; p < A.ptr[sel[k] + 1]; ++p)
+        if (keep(p)) {
+          B.col[q] = cmap ? (*cmap)[A.col[p]] : A.col[p];
+          B.val[q] = A.val[p];
+          ++q;
+        }
+    }
+  });
   return B;
 }
 
@@ -231,12 +259,18 @@ void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, con
   D.sm_rows.upload(rows, s);
   D.sm_dinv.upload(dinv, s);
   // residual rows: every row with an entry in a smoothing column
+  std::vector<uint8_t> touched(Arows.nr, 0);
+  host_for(Arows.nr, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1]; ++p)
+        if (inset[Arows.col[p]]) {
+          touched[i] = 1;
+          break;
+        }
+  });
   std::vector<int64_t> rsel;
-  for (int64_t i = 0; i < Arows.nr; ++i) {
-    bool any = false;
-    for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1] && !any; ++p) any = inset[Arows.col[p]];
-    if (any) rsel.push_back(i);
-  }
+  for (int64_t i = 0; i < Arows.nr; ++i)
+    if (touched[i]) rsel.push_back(i);
   D.nrs_real = (int64_t)rsel.size();
   while (rsel.size() % 32) rsel.push_back(-1);
   D.nrs = (int64_t)rsel.size();
@@ -451,12 +485,14 @@ void build_all(asmg_s& h, cudaStream_t s) {
     h.level_smooth_keys.push_back(sk);
     h.level_smooth_colour.push_back(sc);
     Triplets tr;
-    for (int64_t i = 0; i < Arows.nr; ++i)
-      for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1]; ++p) {
-        tr.r.push_back((int32_t)i);
-        tr.c.push_back(Arows.col[p]);
-        tr.v.push_back(Arows.val[p]);
-      }
+    const int64_t nz = Arows.ptr[Arows.nr];
+    tr.r.resize(nz);
+    tr.c.assign(Arows.col.begin(), Arows.col.begin() + nz);
+    tr.v.assign(Arows.val.begin(), Arows.val.begin() + nz);
+    host_for(Arows.nr, [&](int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; ++i)
+        for (int64_t p = Arows.ptr[i]; p < Arows.ptr[i + 1]; ++p) tr.r[p] = (int32_t)i;
+    });
     h.level_rows.push_back(std::move(tr));
     double td = now();
     h.stats.t_lv_export += td - tc;
