@@ -982,3 +982,22 @@ def test_dirichlet3d_domain_pcg_dense_and_spd(gen, shape):
     assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
     for l in range(o.c + 1, o.J + 1):
         assert set(o.level_keys(l - 1).tolist()) <= set(o.level_keys(l).tolist())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dirichlet_aligned_l_kept_simplices_fully_covered(gen, dim):
+    # Unjittered L domains: the cut lies on box faces from depth 1 on, so every
+    # kept simplex of sigma^(J) is covered exactly and its mean coefficient
+    # (a = 1 inside, 0 outside) is 1; and in 2D, as in 3D, a triangle of
+    # sigma^(l >= 1) is kept exactly when its centroid lies in Omega.
+    m = gen.grid2d_domain(17, 1, "L", jitter=0.0) if dim == 2 else gen.grid3d_domain(9, 1, "L", jitter=0.0)
+    o = oracle.Oracle(m)
+    assert np.abs(o.finest_coef() - 1.0).max() <= 1e-12
+    if dim == 2:
+        a0, a1, _, L = o.root()
+        for l in range(o.J + 1):
+            allt = o.level_alltri(l)
+            X, Y = _lattice_pts(o, allt.reshape(-1))
+            cx, cy = X.reshape(-1, 3).mean(1), Y.reshape(-1, 3).mean(1)
+            want = {tuple(t) for t, ok in zip(allt.tolist(), (cx < 0.5) | (cy < 0.5)) if ok and l >= 1}
+            assert {tuple(t) for t in o.level_tri(l).tolist()} == want, l
