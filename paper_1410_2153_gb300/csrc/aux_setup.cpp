@@ -207,8 +207,7 @@ void lattice_point(const TreeResult& t, uint64_t key, double* p) {
   p[1] = t.amin[1] + std::ldexp((double)compact(key >> 1), -t.D) * t.L;
 }
 
-void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
-                    const std::vector<int32_t>& free_of_vertex, AuxHost& out) {
+void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out) {
   BoxTree T;
   T.D = tree.D;
   T.S = tree.split;

@@ -361,8 +361,7 @@ void lattice_point3(const TreeResult& t, int LB, uint64_t key, double* p) {
   for (int k = 0; k < 3; ++k) p[k] = t.amin[k] + std::ldexp((double)q[k], -LB) * t.L;
 }
 
-void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
-                     const std::vector<int32_t>& free_of_vertex, AuxHost& out) {
+void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out) {
   Tree3 T;
   T.S = tree.split;
   // closure, finest depth first: the parents of all face and edge neighbours

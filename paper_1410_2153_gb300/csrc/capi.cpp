@@ -207,7 +207,7 @@ void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<
 }
 
 template <class T>
-void build_level_dev(asmg_s& h, const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
+void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
                      const std::vector<uint8_t>& inset, AuxLevelDev<T>& D, cudaStream_t s) {
   D.level = L.level;
   // smoothing rows ordered by (colour, id), colour blocks padded to 32
@@ -442,9 +442,9 @@ void build_all(asmg_s& h, cudaStream_t s) {
   double t1 = now();
   h.aux = AuxHost();
   if (m.dim == 2)
-    build_aux_host(m, h.tree, h.prm, h.free_of_vertex, h.aux);
+    build_aux_host(m, h.tree, h.prm, h.aux);
   else
-    build_aux_host3(m, h.tree, h.prm, h.free_of_vertex, h.aux);
+    build_aux_host3(m, h.tree, h.prm, h.aux);
   h.stats.t_aux = now() - t1;
   t1 = now();
   build_transfer(m, h.dX.p, h.dE.p, h.vertex_of_free, h.aux.sz, h.aux.P, s);
@@ -498,10 +498,10 @@ void build_all(asmg_s& h, cudaStream_t s) {
     h.stats.t_lv_export += td - tc;
     if (h.prm.precision == ASMG_MIXED) {
       h.p32.lev.emplace_back();
-      build_level_dev<float>(h, L, Arows, colour, inset, h.p32.lev.back(), s);
+      build_level_dev<float>(L, Arows, colour, inset, h.p32.lev.back(), s);
     } else {
       h.p64.lev.emplace_back();
-      build_level_dev<double>(h, L, Arows, colour, inset, h.p64.lev.back(), s);
+      build_level_dev<double>(L, Arows, colour, inset, h.p64.lev.back(), s);
     }
     h.stats.t_lv_pack += now() - td;
   }

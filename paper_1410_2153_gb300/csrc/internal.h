@@ -175,13 +175,11 @@ struct MeshHost {
 };
 
 // closure of the cluster tree, auxiliary grids and the Scott-Zhang transfer
-void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
-                    const std::vector<int32_t>& free_of_vertex, AuxHost& out);
+void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out);
 
 // the same in 3D (octree, Kuhn / coned tetrahedral grids); tri_* arrays of
 // the levels then hold 4 keys / ids per tetrahedron
-void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm,
-                     const std::vector<int32_t>& free_of_vertex, AuxHost& out);
+void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out);
 
 // Scott-Zhang transfer (transfer.cu, Sec. 4.1) from the table the host setup
 // leaves in AuxHost::sz: P (rows: free fine dofs in free order, columns: aux
