@@ -45,12 +45,49 @@ inline uint64_t compact(uint64_t v) {
 
 inline uint64_t mort(uint64_t x, uint64_t y) { return spread(x) | (spread(y) << 1); }
 
+// Position lookup in a sorted key array through a table of bucket starts
+// over the top key bits: a short binary search inside one bucket instead of
+// one over the whole array (same results as id_of).
+struct KeyIndex {
+  const std::vector<uint64_t>* keys = nullptr;
+  int shift = 64;
+  std::vector<int64_t> start;  // first position of bucket b; start[nb] = size
+  void build(const std::vector<uint64_t>& k, int bits) {
+    keys = &k;
+    uint64_t top = k.empty() ? 0 : k.back();
+    int hb = 0;
+    while (hb < 64 && (top >> hb)) ++hb;
+    shift = std::max(0, hb - bits);
+    const int64_t nb = (int64_t)(top >> shift) + 1;
+    start.assign(nb + 1, (int64_t)k.size());
+    for (int64_t i = (int64_t)k.size() - 1; i >= 0; --i) start[k[i] >> shift] = i;
+    for (int64_t b = nb - 1; b >= 0; --b) start[b] = std::min(start[b], start[b + 1]);
+  }
+  int32_t find(uint64_t x) const {
+    const uint64_t b = x >> shift;
+    if (b + 1 >= start.size()) return -1;
+    auto lo = keys->begin() + start[b], hi = keys->begin() + start[b + 1];
+    auto it = std::lower_bound(lo, hi, x);
+    return (it != hi && *it == x) ? (int32_t)(it - keys->begin()) : -1;
+  }
+};
+
 struct BoxTree {
   int D = 31;
   std::vector<std::vector<uint64_t>> S;  // split prefixes per depth, sorted
+  std::vector<KeyIndex> SI;              // lookup tables of S once it is final (index())
 
+  void index() {
+    SI.assign(S.size(), KeyIndex());
+    for (size_t d = 0; d < S.size(); ++d) {
+      int bits = 1;
+      while (bits < 20 && ((size_t)1 << bits) < S[d].size()) ++bits;
+      SI[d].build(S[d], bits);
+    }
+  }
   bool split(int d, uint64_t p) const {
     if (d < 0 || d >= (int)S.size()) return false;
+    if (!SI.empty()) return SI[d].find(p) >= 0;
     return std::binary_search(S[d].begin(), S[d].end(), p);
   }
   bool exists(int d, uint64_t p) const { return d == 0 ? p == 0 : split(d - 1, p >> 2); }
@@ -106,6 +143,7 @@ inline int32_t id_of(const std::vector<uint64_t>& keys, uint64_t k) {
   auto it = std::lower_bound(keys.begin(), keys.end(), k);
   return (it != keys.end() && *it == k) ? (int32_t)(it - keys.begin()) : -1;
 }
+
 
 void sort_unique(std::vector<uint64_t>& v) {
   std::sort(v.begin(), v.end());
@@ -232,6 +270,8 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   std::vector<std::vector<uint64_t>> BX(J + 1);  // boxes per depth, ascending prefix
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
 
+
+  T.index();
 
   // ---- per level: changed boxes, new nodes and their parents, level sizes
   struct LevelInfo {
@@ -603,10 +643,12 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     for (int32_t f : phi) out.nlevel[f] += 1;
     for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
   }
+  KeyIndex AKI;
+  AKI.build(AK, 20);
   // aux ID of node x at level l, or -1 where it is not a free node there
   auto level_id = [&](uint64_t x, int l) -> int32_t {
     if (boundary_key(T, x)) return -1;
-    const int32_t id = id_of(AK, x);
+    const int32_t id = AKI.find(x);
     if (dgrid && (id < 0 || phi[id] > l)) return -1;
     return id;
   };
@@ -644,10 +686,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
 
   // emit the triangles of box (d, p) as shown at level l
   auto emit_box = [&](int d, uint64_t p, int l, std::vector<int32_t>& ids, std::vector<uint64_t>& keys,
-                      std::vector<double>& coef) {
+                      std::vector<double>& coef, std::vector<std::array<uint64_t, 3>>& kt) {
     bool h[4] = {false, false, false, false};
     if (d < l) T.hanging(d, p, h);
-    std::vector<std::array<uint64_t, 3>> kt;
+    kt.clear();
     box_tris(T, d, p, h, kt);
     bool diag = !(h[0] || h[1] || h[2] || h[3]);
     for (size_t k = 0; k < kt.size(); ++k) {
@@ -662,11 +704,11 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
 
   // ---- coarsest level: all triangles of sigma^(c)
   {
-    std::vector<uint64_t> ck;
+    std::vector<std::array<uint64_t, 3>> ck;  // scratch
     for (int d = 0; d <= c; ++d) {
       for (uint64_t p : BX[d]) {
         if (d < c && T.split(d, p)) continue;
-        emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef);
+        emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef, ck);
       }
     }
     for (auto id : out.coarse_tri_id)
@@ -781,7 +823,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     }
     L.smooth.resize(sm.size());
     parallel_for((int64_t)sm.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
-      for (int64_t q = b0; q < b1; ++q) L.smooth[q] = id_of(AK, sm[q]);
+      for (int64_t q = b0; q < b1; ++q) L.smooth[q] = AKI.find(sm[q]);
     });
     std::sort(rel.begin(), rel.end());  // (already unique in the default mode)
     rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
@@ -789,7 +831,8 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     std::vector<std::vector<uint64_t>> keys(MAX_THREADS);
     std::vector<std::vector<double>> coefs(MAX_THREADS);
     parallel_for((int64_t)rel.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
-      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t]);
+      std::vector<std::array<uint64_t, 3>> kt;  // scratch of this thread
+      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t], kt);
     });
     for (unsigned t = 0; t < MAX_THREADS; ++t) {
       L.tri_id.insert(L.tri_id.end(), ids[t].begin(), ids[t].end());
@@ -800,9 +843,9 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     if (!dgrid) {
       for (auto& v : newnodes[l]) {
         if (boundary_key(T, v[0])) continue;
-        L.new_id.push_back(id_of(AK, v[0]));
-        L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : id_of(AK, v[1]));
-        L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : id_of(AK, v[2]));
+        L.new_id.push_back(AKI.find(v[0]));
+        L.new_p0.push_back(boundary_key(T, v[1]) ? -1 : AKI.find(v[1]));
+        L.new_p1.push_back(boundary_key(T, v[2]) ? -1 : AKI.find(v[2]));
       }
     } else {
       // nodes free from level l on: born at l, the interpolant of the
