@@ -1,0 +1,213 @@
+"""The library's host part of the setup against the oracle, on CPU.
+
+The closure, the auxiliary grids (box and Dirichlet), the free nodes of
+every level, the smoothing sets, the level simplices with their averaged
+coefficients, the new nodes with their parents and the Scott-Zhang transfer
+rows come from the library's own sources (`aux_setup.cpp`, `aux_setup3.cpp`,
+the row routine of `sz_row.h`), built here with g++ around
+`tests/host_setup_shim.cpp` and run on the oracle's cluster tree (the tree
+itself is checked bit for bit on the GPU).  Integer results must be equal;
+the level operators rediscretised from the shim's simplices agree with the
+oracle's Galerkin products to 1e-12 of the largest entry (1e-10 on 3D
+domains cut by Omega, whose boundary tetrahedra are clipped by two different
+exact methods), and P to 1e-11.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1410_2153_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    cuda_inc, cuda_lib = os.path.join(cuda, "include"), os.path.join(cuda, "lib64")
+    if not shutil.which("g++") or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers are missing")
+    out = str(tmp_path_factory.mktemp("shim") / "libshim.so")
+    # (the CUDA runtime is linked for the device-buffer types in the shared
+    # headers; nothing here calls it)
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I", cuda_inc,
+                           os.path.join(ROOT, "tests", "host_setup_shim.cpp"), os.path.join(CSRC, "aux_setup.cpp"),
+                           os.path.join(CSRC, "aux_setup3.cpp"), "-o", out, "-L", cuda_lib, "-lcudart",
+                           "-Wl,-rpath," + cuda_lib])
+    lib = ctypes.CDLL(out)
+    lib.shim_build.restype = ctypes.c_void_p
+    lib.shim_build.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.shim_error.restype = ctypes.c_char_p
+    lib.shim_error.argtypes = [ctypes.c_void_p]
+    lib.shim_free.argtypes = [ctypes.c_void_p]
+    lib.shim_get.restype = ctypes.c_int64
+    lib.shim_get.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p]
+    return lib
+
+
+def _get(lib, h, what, l, dt):
+    n = lib.shim_get(h, what.encode(), l, None)
+    assert n >= 0, what
+    a = np.empty(n, dt)
+    if n:
+        lib.shim_get(h, what.encode(), l, a.ctypes.data_as(ctypes.c_void_p))
+    return a
+
+
+def _deinterleave(keys, dim, bits):
+    k = keys.astype(np.uint64)
+    out = []
+    for a in range(dim):
+        v = np.zeros_like(k)
+        for j in range(bits):
+            v |= ((k >> np.uint64(dim * j + a)) & np.uint64(1)) << np.uint64(j)
+        out.append(v)
+    return out
+
+
+def _interleave(coords, dim):
+    out = np.zeros_like(coords[0], dtype=np.uint64)
+    for a, c in enumerate(coords):
+        c = c.astype(np.uint64)
+        for j in range(32 if dim == 2 else 21):
+            out |= ((c >> np.uint64(j)) & np.uint64(1)) << np.uint64(dim * j + a)
+    return out
+
+
+def _stiffness(P, a):
+    """P1 element stiffness (per simplex: (dim+1) x (dim+1)) times the coefficient a."""
+    dim = P.shape[2]
+    e = P[:, 1:, :] - P[:, :1, :]              # rows: edge vectors from vertex 0
+    G = np.linalg.inv(e)                       # column k: gradient of lambda_(k+1)
+    grads = np.concatenate([-G.sum(axis=2)[:, None, :], G.transpose(0, 2, 1)], axis=1)
+    vol = np.abs(np.linalg.det(e)) / (2.0 if dim == 2 else 6.0)
+    return a[:, None, None] * vol[:, None, None] * np.einsum("tir,tjr->tij", grads, grads)
+
+
+def _compare(lib, m, o, params, dim, op_tol):
+    segs = o.tree_levels()
+    splits = [s_[s_[:, 3] == 1, 0].astype(np.uint64) for s_ in segs]
+    while splits and len(splits[-1]) == 0:
+        splits.pop()
+    cnt = np.array([len(s_) for s_ in splits], np.int64)
+    flat = np.concatenate(splits) if splits else np.zeros(0, np.uint64)
+    r = o.root()
+    amin = np.ascontiguousarray(r[:dim], dtype=np.float64)
+    L = float(r[3])
+    X = np.ascontiguousarray(m.verts, dtype=np.float64)
+    E = np.ascontiguousarray(m.elems, dtype=np.int32)
+    B = np.ascontiguousarray(m.bflag, dtype=np.uint8)
+    C = None if m.coeff is None else np.ascontiguousarray(m.coeff, dtype=np.float64)
+    h = lib.shim_build(dim, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
+                       None if C is None else C.ctypes.data, len(cnt), cnt.ctypes.data, flat.ctypes.data,
+                       amin.ctypes.data, L, params.get("n_min", 3), params.get("coarse_max", 512),
+                       params.get("smoothing", 0))
+    try:
+        assert lib.shim_error(h) == b"", lib.shim_error(h)
+        # closure: the split boxes of every depth
+        for d, arr in enumerate(o.boxes()):
+            spl = arr[arr[:, 1] == 1, 0]
+            bits = 32 if dim == 2 else 21
+            coords = [(spl >> np.uint64(bits * a)) & np.uint64((1 << bits) - 1) for a in range(dim)]
+            want = np.sort(_interleave(coords, dim))
+            assert np.array_equal(_get(lib, h, "split", d, np.uint64), want), ("closure", d)
+        J, c = lib.shim_get(h, b"J", 0, None), lib.shim_get(h, b"c", 0, None)
+        assert J == o.J and c == o.c, (J, o.J, c, o.c)
+        ak = _get(lib, h, "aux_key", 0, np.uint64)
+        assert np.array_equal(ak, o.level_keys(o.J))
+        nl = _get(lib, h, "nlevel", 0, np.int64)
+        assert [int(v) for v in nl] == [o.info("nlevel", l) for l in range(J + 1)]
+        assert np.array_equal(ak[_get(lib, h, "coarse_id", 0, np.int32)], o.level_keys(c))
+        lb = 31 if dim == 2 else o.info("LB")
+        for l in range(c + 1, J + 1):
+            sm = _get(lib, h, "smooth", l, np.int32)
+            lk = o.level_keys(l)
+            assert np.array_equal(np.sort(ak[sm]), np.sort(lk[o.smoothing_set(l)[0]])), ("smooth", l)
+            # the level operator on the rows and columns of N~_l, rediscretised from the
+            # shim's simplices, against the oracle's Galerkin product
+            tk = _get(lib, h, "tri_key", l, np.uint64)
+            tid = _get(lib, h, "tri_id", l, np.int32).reshape(-1, dim + 1)
+            tc = _get(lib, h, "tri_coef", l, np.float64)
+            P = np.stack([amin[a] + np.ldexp(v.astype(np.float64), -lb) * L
+                          for a, v in enumerate(_deinterleave(tk, dim, 32 if dim == 2 else 21))], -1)
+            K = _stiffness(P.reshape(-1, dim + 1, dim), tc)
+            inset = np.zeros(len(ak), bool)
+            inset[sm] = True
+            got = {}
+            for t in range(len(tc)):
+                for i in range(dim + 1):
+                    for j in range(dim + 1):
+                        a_, b_ = tid[t, i], tid[t, j]
+                        if a_ >= 0 and b_ >= 0 and (inset[a_] or inset[b_]):
+                            got[(a_, b_)] = got.get((a_, b_), 0.0) + K[t, i, j]
+            idx = {int(k): i for i, k in enumerate(ak)}
+            Ag = o.A(l).tocoo()
+            want = {}
+            for r_, c_, v_ in zip(Ag.row, Ag.col, Ag.data):
+                ri, ci = idx[int(lk[r_])], idx[int(lk[c_])]
+                if inset[ri] or inset[ci]:
+                    want[(ri, ci)] = v_
+            scale = max(abs(v) for v in want.values())
+            err = max(abs(got.get(k, 0.0) - want.get(k, 0.0)) for k in set(got) | set(want))
+            assert err <= op_tol * scale, ("A level", l, err)
+            # new nodes: parents against the oracle's interpolation rows
+            nid = _get(lib, h, "new_id", l, np.int32)
+            p0 = _get(lib, h, "new_p0", l, np.int32)
+            p1 = _get(lib, h, "new_p1", l, np.int32)
+            I = o.I(l).tocsr()
+            lkc = o.level_keys(l - 1)
+            lpos = {int(k): i for i, k in enumerate(lk)}
+            for a_, b_, c2 in zip(nid, p0, p1):
+                row = I[lpos[int(ak[a_])]]
+                w = {int(lkc[j]): v for j, v in zip(row.indices, row.data)}
+                g = {}
+                for q in (b_, c2):
+                    if q >= 0:
+                        g[int(ak[q])] = g.get(int(ak[q]), 0.0) + 0.5
+                assert w.keys() == g.keys() and all(abs(w[k] - g[k]) < 1e-15 for k in w), ("I", l)
+            assert set(int(k) for k in lk) - set(int(k) for k in lkc) == set(int(ak[a_]) for a_ in nid)
+        Pr = _get(lib, h, "P_r", 0, np.int32)
+        Pc = _get(lib, h, "P_c", 0, np.int32)
+        Pv = _get(lib, h, "P_v", 0, np.float64)
+        Ph = sp.csr_matrix((Pv, (Pr, Pc)), shape=(o.nfree, len(ak)))
+        assert abs(Ph - o.P()).max() <= 1e-11
+    finally:
+        lib.shim_free(h)
+
+
+def _cases(gen):
+    jump = gen.grid2d(33, 7, graded=True)
+    jump.coeff = np.exp(np.random.default_rng(0).normal(size=jump.ne))
+    lc = gen.grid2d_domain(17, 3, "L")
+    lc.coeff = np.exp(np.random.default_rng(1).normal(size=lc.ne))
+    t3 = gen.grid3d(9, 3)
+    t3.coeff = gen.subcube_coefficient(t3, 5, ncube=4)
+    return {
+        "2d_jitter17": (gen.grid2d(17, 3), {}, 2, 1e-12),
+        "2d_graded33_lognormal": (jump, {}, 2, 1e-12),
+        "2d_graded33_all_levels": (gen.grid2d(33, 4, graded=True), {"smoothing": 1}, 2, 1e-12),
+        "2d_L17_lognormal": (lc, {}, 2, 1e-12),
+        "2d_hole33_c10": (gen.grid2d_domain(33, 5, "hole"), {"coarse_max": 10}, 2, 1e-12),
+        "3d_kuhn5": (gen.grid3d(5, 1), {}, 3, 1e-12),
+        "3d_kuhn9_jump": (t3, {}, 3, 1e-12),
+        "3d_kuhn9_nmin6": (gen.grid3d(9, 8), {"n_min": 6}, 3, 1e-12),
+        "3d_L7": (gen.grid3d_domain(7, 1, "L"), {}, 3, 1e-10),
+        "3d_cavity7": (gen.grid3d_domain(7, 2, "hole"), {"coarse_max": 10}, 3, 1e-10),
+    }
+
+
+@pytest.mark.parametrize("name", ["2d_jitter17", "2d_graded33_lognormal", "2d_graded33_all_levels",
+                                  "2d_L17_lognormal", "2d_hole33_c10", "3d_kuhn5", "3d_kuhn9_jump",
+                                  "3d_kuhn9_nmin6", "3d_L7", "3d_cavity7"])
+def test_host_setup_matches_oracle(shim, gen, name):
+    m, params, dim, op_tol = _cases(gen)[name]
+    o = oracle.Oracle(m, **params)
+    _compare(shim, m, o, params, dim, op_tol)
