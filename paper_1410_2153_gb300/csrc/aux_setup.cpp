@@ -18,6 +18,7 @@
 
 #include "clip.h"
 #include "internal.h"
+#include "keyindex.h"
 
 namespace asmg {
 
@@ -45,32 +46,6 @@ inline uint64_t compact(uint64_t v) {
 
 inline uint64_t mort(uint64_t x, uint64_t y) { return spread(x) | (spread(y) << 1); }
 
-// Position lookup in a sorted key array through a table of bucket starts
-// over the top key bits: a short binary search inside one bucket instead of
-// one over the whole array (same results as id_of).
-struct KeyIndex {
-  const std::vector<uint64_t>* keys = nullptr;
-  int shift = 64;
-  std::vector<int64_t> start;  // first position of bucket b; start[nb] = size
-  void build(const std::vector<uint64_t>& k, int bits) {
-    keys = &k;
-    uint64_t top = k.empty() ? 0 : k.back();
-    int hb = 0;
-    while (hb < 64 && (top >> hb)) ++hb;
-    shift = std::max(0, hb - bits);
-    const int64_t nb = (int64_t)(top >> shift) + 1;
-    start.assign(nb + 1, (int64_t)k.size());
-    for (int64_t i = (int64_t)k.size() - 1; i >= 0; --i) start[k[i] >> shift] = i;
-    for (int64_t b = nb - 1; b >= 0; --b) start[b] = std::min(start[b], start[b + 1]);
-  }
-  int32_t find(uint64_t x) const {
-    const uint64_t b = x >> shift;
-    if (b + 1 >= start.size()) return -1;
-    auto lo = keys->begin() + start[b], hi = keys->begin() + start[b + 1];
-    auto it = std::lower_bound(lo, hi, x);
-    return (it != hi && *it == x) ? (int32_t)(it - keys->begin()) : -1;
-  }
-};
 
 struct BoxTree {
   int D = 31;
@@ -139,10 +114,6 @@ inline bool boundary_key(const BoxTree& T, uint64_t k) {
   return x == 0 || y == 0 || x == top || y == top;
 }
 
-inline int32_t id_of(const std::vector<uint64_t>& keys, uint64_t k) {
-  auto it = std::lower_bound(keys.begin(), keys.end(), k);
-  return (it != keys.end() && *it == k) ? (int32_t)(it - keys.begin()) : -1;
-}
 
 
 void sort_unique(std::vector<uint64_t>& v) {

@@ -21,6 +21,7 @@
 
 #include "clip.h"
 #include "internal.h"
+#include "keyindex.h"
 
 namespace asmg {
 
@@ -58,8 +59,18 @@ inline void um3(uint64_t k, uint64_t* q) {
 struct Tree3 {
   int LB = 1;  // lattice bits of auxiliary nodes
   std::vector<std::vector<uint64_t>> S;
+  std::vector<KeyIndex> SI;  // lookup tables of S once it is final (index())
+  void index() {
+    SI.assign(S.size(), KeyIndex());
+    for (size_t d = 0; d < S.size(); ++d) {
+      int bits = 1;
+      while (bits < 20 && ((size_t)1 << bits) < S[d].size()) ++bits;
+      SI[d].build(S[d], bits);
+    }
+  }
   bool split(int d, uint64_t p) const {
     if (d < 0 || d >= (int)S.size()) return false;
+    if (!SI.empty()) return SI[d].find(p) >= 0;
     return std::binary_search(S[d].begin(), S[d].end(), p);
   }
   bool exists(int d, uint64_t p) const { return d == 0 ? p == 0 : split(d - 1, p >> 3); }
@@ -209,10 +220,6 @@ inline bool bnd3(const Tree3& T, uint64_t k) {
   return q[0] == 0 || q[1] == 0 || q[2] == 0 || q[0] == top || q[1] == top || q[2] == top;
 }
 
-inline int32_t idx_of(const std::vector<uint64_t>& keys, uint64_t k) {
-  auto it = std::lower_bound(keys.begin(), keys.end(), k);
-  return (it != keys.end() && *it == k) ? (int32_t)(it - keys.begin()) : -1;
-}
 
 void uniq(std::vector<uint64_t>& v) {
   std::sort(v.begin(), v.end());
@@ -388,6 +395,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   if (J + 1 > 21) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "3D auxiliary hierarchy deeper than 20 levels");
   T.LB = J + 1;
   out.LB = T.LB;
+  T.index();
   std::vector<std::vector<uint64_t>> BX(J + 1);
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
 
@@ -842,10 +850,12 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (int32_t f : phi) out.nlevel[f] += 1;
     for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
   }
+  KeyIndex AKI;
+  AKI.build(AK, 20);
   // aux ID of node x at level l, or -1 where it is not a free node there
   auto level_id = [&](uint64_t x, int l) -> int32_t {
     if (bnd3(T, x)) return -1;
-    const int32_t id = idx_of(AK, x);
+    const int32_t id = AKI.find(x);
     if (dgrid && (id < 0 || phi[id] > l)) return -1;
     return id;
   };
@@ -983,7 +993,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     std::sort(rel.begin(), rel.end());
     rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
     uniq(sm);
-    for (uint64_t k : sm) L.smooth.push_back(idx_of(AK, k));
+    for (uint64_t k : sm) L.smooth.push_back(AKI.find(k));
     std::vector<std::vector<int32_t>> ids(nthr);
     std::vector<std::vector<uint64_t>> keys(nthr);
     std::vector<std::vector<double>> coefs(nthr);
@@ -998,9 +1008,9 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     if (!dgrid) {
       for (auto& v : newnodes[l]) {
         if (bnd3(T, v[0])) continue;
-        L.new_id.push_back(idx_of(AK, v[0]));
-        L.new_p0.push_back(bnd3(T, v[1]) ? -1 : idx_of(AK, v[1]));
-        L.new_p1.push_back(bnd3(T, v[2]) ? -1 : idx_of(AK, v[2]));
+        L.new_id.push_back(AKI.find(v[0]));
+        L.new_p0.push_back(bnd3(T, v[1]) ? -1 : AKI.find(v[1]));
+        L.new_p1.push_back(bnd3(T, v[2]) ? -1 : AKI.find(v[2]));
       }
     } else {
       // nodes free from level l on: born at l, the interpolant of the
