@@ -11,6 +11,7 @@
 #include <string>
 
 #include "../paper_1410_2153_gb300/csrc/internal.h"
+#include "../paper_1410_2153_gb300/csrc/keyindex.h"
 #include "../paper_1410_2153_gb300/csrc/sz_row.h"
 
 using namespace asmg;
@@ -174,6 +175,15 @@ int64_t shim_get(void* hp, const char* what, int l, void* out) {
   if (w == "tri_id") return put(L.tri_id.data(), (int64_t)L.tri_id.size(), 4);
   if (w == "tri_coef") return put(L.tri_coef.data(), (int64_t)L.tri_coef.size(), 8);
   return -1;
+}
+
+// positions of the queries in the sorted keys through the host setup's
+// bucket index (-1: absent)
+void shim_keyindex(const uint64_t* keys, int64_t n, int bits, const uint64_t* q, int64_t m, int32_t* out) {
+  std::vector<uint64_t> k(keys, keys + n);
+  KeyIndex idx;
+  idx.build(k, bits);
+  for (int64_t i = 0; i < m; ++i) out[i] = idx.find(q[i]);
 }
 
 }  // extern "C"

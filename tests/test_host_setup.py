@@ -50,7 +50,35 @@ def shim(tmp_path_factory):
     lib.shim_free.argtypes = [ctypes.c_void_p]
     lib.shim_get.restype = ctypes.c_int64
     lib.shim_get.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p]
+    lib.shim_keyindex.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_void_p]
     return lib
+
+
+@pytest.mark.parametrize("kind", ["empty", "one", "uniform", "clustered", "top_bits"])
+@pytest.mark.parametrize("bits", [1, 8, 20])
+def test_key_index_matches_binary_search(shim, kind, bits):
+    rng = np.random.default_rng(bits)
+    if kind == "empty":
+        keys = np.zeros(0, np.uint64)
+    elif kind == "one":
+        keys = np.array([12345], np.uint64)
+    elif kind == "uniform":
+        keys = np.unique(rng.integers(0, 2 ** 62, 5000, dtype=np.uint64))
+    elif kind == "clustered":                    # graded meshes: keys crowd near one corner
+        keys = np.unique(np.concatenate([rng.integers(0, 2 ** 20, 4000, dtype=np.uint64),
+                                         rng.integers(0, 2 ** 62, 100, dtype=np.uint64)]))
+    else:
+        keys = np.unique(rng.integers(2 ** 63 - 2 ** 40, 2 ** 63, 3000, dtype=np.uint64))
+    present = keys[rng.integers(0, max(1, keys.size), 200)] if keys.size else np.zeros(0, np.uint64)
+    q = np.concatenate([present, rng.integers(0, 2 ** 63, 300, dtype=np.uint64), keys[:1] + np.uint64(1),
+                        np.array([0, 2 ** 63 - 1], np.uint64)]).astype(np.uint64)
+    out = np.empty(q.size, np.int32)
+    shim.shim_keyindex(keys.ctypes.data, keys.size, bits, q.ctypes.data, q.size, out.ctypes.data)
+    pos = np.searchsorted(keys, q)
+    want = np.where((pos < keys.size) & (keys[np.minimum(pos, max(keys.size - 1, 0))] == q) if keys.size
+                    else np.zeros(q.size, bool), pos, -1)
+    assert np.array_equal(out, want)
 
 
 def _get(lib, h, what, l, dt):
