@@ -229,12 +229,21 @@ def _cases(gen):
         "3d_kuhn9_nmin6": (gen.grid3d(9, 8), {"n_min": 6}, 3, 1e-12),
         "3d_L7": (gen.grid3d_domain(7, 1, "L"), {}, 3, 1e-10),
         "3d_cavity7": (gen.grid3d_domain(7, 2, "hole"), {"coarse_max": 10}, 3, 1e-10),
+        # small and degenerate hierarchies: one free vertex, a coarse level of one
+        # node, one-element leaves, every level smoothed with a tiny coarse cap
+        "2d_grid3": (gen.grid2d(3, 1), {}, 2, 1e-12),
+        "2d_L5_c1": (gen.grid2d_domain(5, 1, "L"), {"coarse_max": 1}, 2, 1e-12),
+        "2d_L9_nmin1": (gen.grid2d_domain(9, 3, "L"), {"n_min": 1}, 2, 1e-12),
+        "2d_L9_all_c2": (gen.grid2d_domain(9, 3, "L"), {"smoothing": 1, "coarse_max": 2}, 2, 1e-12),
+        "3d_grid3": (gen.grid3d(3, 1), {}, 3, 1e-12),
+        "3d_L5_nmin1": (gen.grid3d_domain(5, 3, "L"), {"n_min": 1}, 3, 1e-10),
     }
 
 
 @pytest.mark.parametrize("name", ["2d_jitter17", "2d_graded33_lognormal", "2d_graded33_all_levels",
                                   "2d_L17_lognormal", "2d_hole33_c10", "3d_kuhn5", "3d_kuhn9_jump",
-                                  "3d_kuhn9_nmin6", "3d_L7", "3d_cavity7"])
+                                  "3d_kuhn9_nmin6", "3d_L7", "3d_cavity7", "2d_grid3", "2d_L5_c1",
+                                  "2d_L9_nmin1", "2d_L9_all_c2", "3d_grid3", "3d_L5_nmin1"])
 def test_host_setup_matches_oracle(shim, gen, name):
     m, params, dim, op_tol = _cases(gen)[name]
     o = oracle.Oracle(m, **params)
