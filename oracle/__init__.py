@@ -20,9 +20,9 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 PARAM_DEFAULTS = dict(n_min=3, nu_pre=2, nu_post=2, coarse_max=512, smoothing=0, max_iter=500,
-                      colouring=0, stage=2, smoother=0, additive=0, fine_sweeps=1, iteration=0)
+                      colouring=0, stage=2, smoother=0, additive=0, fine_sweeps=1, iteration=0, nb_layers=2)
 PARAM_ORDER = ("n_min", "nu_pre", "nu_post", "coarse_max", "smoothing", "max_iter", "colouring", "stage",
-               "smoother", "additive", "fine_sweeps", "iteration")
+               "smoother", "additive", "fine_sweeps", "iteration", "nb_layers")
 
 
 def build(force: bool = False) -> str:
@@ -186,6 +186,10 @@ class Oracle:
         nc = self.info("ncolours", level)
         return (self._get("smooth", level, (ns,), np.int32), self._get("cstart", level, (nc + 1,), np.int32),
                 self._get("colour", level, (n,), np.int32))
+
+    def near_boundary_set(self, level: int):
+        """Level-l free-node indices J_{l,j} of the near-boundary correction (Algorithm 3)."""
+        return self._get("nbset", level, (self.info("nnb", level),), np.int32)
 
     def vertex_of_free(self):
         return self._get("vertex_of_free", 0, (self.nfree,), np.int32)

@@ -29,6 +29,12 @@
 //       iterated greedy recolouring; the same definition is implemented
 //       independently on the device, so no colouring is ever passed from one
 //       side to the other
+//   R18 mixed Dirichlet/Neumann boundaries (2D): contact of a triangle with
+//       Omega or Gamma_D means contact of its interior; Dirichlet auxiliary
+//       nodes lie on Gamma_D or on a triangle removed for Gamma_D
+//   R19 near-boundary correction: after the coarse correction of every level
+//       above the coarsest, the free nodes of the j-th layer around the
+//       level's boundary are solved exactly (dense Cholesky)
 //
 // 3D: the same steps on an octree with tetrahedral auxiliary grids (R4-3D
 // below); fine assembly, mass matrix and the tree are dimension-generic.
@@ -140,6 +146,7 @@ struct Params {
   int additive = 0;     // 0: multiplicative (Algorithm 1); 1: additive B = S + Pi Btilde Pi^t (eq. fasp)
   int fine_sweeps = 1;  // smoothing steps per application of S (and of S^t)
   int iteration = 0;    // 0: PCG (Sec. 5.2); 1: the ASMG iteration u <- u + B (b - A u)
+  int nb_layers = 2;    // mixed boundaries: layers j of the near-boundary correction (Algorithm 3); < 0: none
 };
 
 struct Seg {
@@ -158,6 +165,8 @@ struct Level {
   std::vector<int32_t> smooth;               // smoothing set sorted by (colour, index)
   std::vector<int32_t> colour;               // colour per free node, -1 outside the set
   std::vector<int32_t> cstart;               // colour class starts in `smooth`
+  std::vector<int32_t> nbset;                // near-boundary free nodes J_{l,j} (Algorithm 3)
+  std::vector<double> nbchol;                // Cholesky factor of A restricted to nbset
 };
 
 struct Oracle {
@@ -188,6 +197,7 @@ struct Oracle {
   int LB = 0; // 3D: lattice bits of the auxiliary nodes (J + 1)
   int c = 0;  // coarsest level used by the V-cycle
   bool boxdomain = true;  // the fine elements fill the root box (else Dirichlet auxiliary grids, R17)
+  bool neumann = false;   // some vertex is Neumann: mixed auxiliary grids (R18) and Algorithm 3
   std::vector<Level> lv;
   std::vector<double> finest_coef;  // per triangle of level J
   CSR P, Pfull;                     // Scott-Zhang transfer (free / all aux columns)
@@ -767,7 +777,302 @@ void dirichlet_triangles(Oracle& o, std::vector<std::vector<std::array<uint64_t,
   }
 }
 
+bool cholesky(std::vector<double>& M, int64_t n);
+void chol_solve(const std::vector<double>& Lm, int64_t n, const double* b, double* x);
+
+// Orientation of r against the directed line p -> q (twice the signed area).
+double orient2(const Pt& p, const Pt& q, const Pt& r) {
+  return (q.x - p.x) * (r.y - p.y) - (q.y - p.y) * (r.x - p.x);
+}
+
+// r on the closed segment [p, q] (orientation zero and inside the bounding box)
+bool on_segment(const Pt& p, const Pt& q, const Pt& r) {
+  return orient2(p, q, r) == 0 && std::min(p.x, q.x) <= r.x && r.x <= std::max(p.x, q.x) &&
+         std::min(p.y, q.y) <= r.y && r.y <= std::max(p.y, q.y);
+}
+
+// The closed segment [a, b] meets the interior of the CCW triangle K.  By
+// orientation signs: a segment on an edge's line cannot; an endpoint strictly
+// inside does; two endpoints in the closed triangle do when their midpoint is
+// strictly inside; otherwise the segment must cross an edge at an interior
+// point of both, or pass through a vertex between the other two.
+bool seg_meets_open_triangle(const Pt& a, const Pt& b, const Pt* K) {
+  double oa[3], ob[3];
+  for (int e = 0; e < 3; ++e) {
+    oa[e] = orient2(K[e], K[(e + 1) % 3], a);
+    ob[e] = orient2(K[e], K[(e + 1) % 3], b);
+    if (oa[e] == 0 && ob[e] == 0) return false;
+  }
+  const bool ina = oa[0] >= 0 && oa[1] >= 0 && oa[2] >= 0, inb = ob[0] >= 0 && ob[1] >= 0 && ob[2] >= 0;
+  if ((oa[0] > 0 && oa[1] > 0 && oa[2] > 0) || (ob[0] > 0 && ob[1] > 0 && ob[2] > 0)) return true;
+  if (ina && inb) return oa[0] + ob[0] > 0 && oa[1] + ob[1] > 0 && oa[2] + ob[2] > 0;
+  for (int e = 0; e < 3; ++e) {
+    const Pt &p = K[e], &q = K[(e + 1) % 3];
+    const double dp = orient2(a, b, p), dq = orient2(a, b, q);
+    if (((oa[e] > 0 && ob[e] < 0) || (oa[e] < 0 && ob[e] > 0)) && ((dp > 0 && dq < 0) || (dp < 0 && dq > 0)))
+      return true;
+  }
+  for (int v = 0; v < 3; ++v) {
+    const Pt &r = K[v], &p = K[(v + 1) % 3], &q = K[(v + 2) % 3];
+    if (!on_segment(a, b, r) || (r.x == a.x && r.y == a.y) || (r.x == b.x && r.y == b.y)) continue;
+    const double dp = orient2(a, b, p), dq = orient2(a, b, q);
+    if ((dp > 0 && dq < 0) || (dp < 0 && dq > 0)) return true;
+  }
+  return false;
+}
+
+// R18: mixed Dirichlet / Neumann boundaries (Sec. 3.4, the remark on mixed
+// boundary conditions), 2D.  Gamma_D is the union of the fine boundary edges
+// (edges of one element) whose two endpoints are Dirichlet.  T^M_l keeps the
+// triangles of sigma^(l) whose interior meets Omega (positive covered area)
+// and does not meet Gamma_D.  The Dirichlet nodes of level l are the nodes of
+// kept triangles that lie on Gamma_D or belong to a triangle removed for
+// Gamma_D; every other node of T^M_l is free (natural conditions on the rest
+// of the boundary of Omega^M_l).  The grids are not nested, so every level is
+// its own P1 discretisation with the mean of a over tau n Omega; the transfer
+// between levels is nodal interpolation (zero where the coarse function has no
+// kept triangle), every level is smoothed as a whole, and Algorithm 3 adds the
+// near-boundary correction (R19).
+void build_aux_mixed(Oracle& o) {
+  const int J = o.J;
+  o.lv.assign(J + 1, Level());
+  std::vector<std::array<uint64_t, 3>> tJ;
+  level_triangles(o, J, tJ);
+  std::map<std::array<uint64_t, 3>, int64_t> idx;
+  for (size_t t = 0; t < tJ.size(); ++t) idx[tJ[t]] = (int64_t)t;
+  // covered area and integral of a over tau n Omega (exact clipping)
+  std::vector<double> cov(tJ.size(), 0.0), num(tJ.size(), 0.0);
+  std::vector<std::array<uint64_t, 3>> leaves, ktri;
+  auto tri_pts = [&](const std::array<uint64_t, 3>& kt, Pt* K) {
+    for (int k = 0; k < 3; ++k) {
+      double p[2];
+      physical(o, kt[k], p);
+      K[k] = Pt{p[0], p[1]};
+    }
+  };
+  for (int64_t e = 0; e < o.ne; ++e) {
+    Pt T[3];
+    for (int k = 0; k < 3; ++k) T[k] = Pt{o.X[(int64_t)o.E[3 * e + k] * 2], o.X[(int64_t)o.E[3 * e + k] * 2 + 1]};
+    const double lox = std::min({T[0].x, T[1].x, T[2].x}), hix = std::max({T[0].x, T[1].x, T[2].x});
+    const double loy = std::min({T[0].y, T[1].y, T[2].y}), hiy = std::max({T[0].y, T[1].y, T[2].y});
+    leaves.clear();
+    leaves_overlapping(o, lox, loy, hix, hiy, leaves);
+    const double a = o.coeff.empty() ? 1.0 : o.coeff[e];
+    std::vector<Pt> poly(T, T + 3);
+    for (auto& b : leaves) {
+      ktri.clear();
+      box_triangles(o, (int)b[0], b[1], b[2], J, ktri);
+      for (auto& kt : ktri) {
+        Pt K[3];
+        tri_pts(kt, K);
+        auto cp = clip(poly, K);
+        if (cp.size() < 3) continue;
+        const double ar = poly_area(cp);
+        cov[idx.at(kt)] += ar;
+        num[idx.at(kt)] += a * ar;
+      }
+    }
+  }
+  // Gamma_D: fine boundary edges (of one element only) with Dirichlet endpoints
+  std::map<std::pair<int32_t, int32_t>, int> ecount;
+  for (int64_t e = 0; e < o.ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      int32_t a = o.E[3 * e + k], b = o.E[3 * e + (k + 1) % 3];
+      ecount[{std::min(a, b), std::max(a, b)}] += 1;
+    }
+  std::vector<std::array<Pt, 2>> gamma_d;
+  for (auto& kv : ecount)
+    if (kv.second == 1 && o.bflag[kv.first.first] == 1 && o.bflag[kv.first.second] == 1)
+      gamma_d.push_back({Pt{o.X[2 * (int64_t)kv.first.first], o.X[2 * (int64_t)kv.first.first + 1]},
+                         Pt{o.X[2 * (int64_t)kv.first.second], o.X[2 * (int64_t)kv.first.second + 1]}});
+  auto area_of = [&](const std::array<uint64_t, 3>& t) {
+    Pt K[3];
+    tri_pts(t, K);
+    return 0.5 * ((K[1].x - K[0].x) * (K[2].y - K[0].y) - (K[2].x - K[0].x) * (K[1].y - K[0].y));
+  };
+  // every level: kept triangles, their coefficients, free nodes
+  std::vector<std::vector<double>> coef(J + 1);
+  for (int l = 0; l <= J; ++l) {
+    std::vector<std::array<uint64_t, 3>> tl;
+    level_triangles(o, l, tl);
+    std::map<std::array<uint64_t, 3>, double> cl, nl;
+    for (size_t t = 0; t < tJ.size(); ++t) {
+      std::array<uint64_t, 3> anc = tJ[t];
+      if (l < J) {
+        uint64_t X3 = 0, Y3 = 0;
+        for (int v = 0; v < 3; ++v) {
+          uint64_t x, y;
+          node_xy(tJ[t][v], x, y);
+          X3 += x;
+          Y3 += y;
+        }
+        if (!locate_level_triangle(o, l, X3, Y3, anc)) {
+          o.err = "oracle: nested triangle not located";
+          return;
+        }
+      }
+      cl[anc] += cov[t];
+      nl[anc] += num[t];
+    }
+    Level& L = o.lv[l];
+    // Dirichlet nodes: those of triangles whose interior meets Gamma_D, and
+    // those lying on Gamma_D
+    std::set<uint64_t> dirn;
+    for (auto& t : tl) {
+      Pt K[3];
+      tri_pts(t, K);
+      bool hit = false;
+      for (auto& sg : gamma_d) hit = hit || seg_meets_open_triangle(sg[0], sg[1], K);
+      if (hit) {
+        for (int v = 0; v < 3; ++v) dirn.insert(t[v]);
+        continue;
+      }
+      if (!(cl[t] > 1e-12 * area_of(t))) continue;  // outside Omega
+      L.tri.push_back(t);
+      coef[l].push_back(nl[t] / cl[t]);
+    }
+    for (auto& t : L.tri)
+      for (int k = 0; k < 3; ++k) L.allkey.push_back(t[k]);
+    std::sort(L.allkey.begin(), L.allkey.end());
+    L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
+    for (auto k : L.allkey) {
+      double p[2];
+      physical(o, k, p);
+      bool ond = false;
+      for (auto& sg : gamma_d) ond = ond || on_segment(sg[0], sg[1], Pt{p[0], p[1]});
+      if (!dirn.count(k) && !ond) L.key.push_back(k);
+    }
+  }
+  o.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if ((int64_t)o.lv[l].key.size() <= o.prm.coarse_max) o.c = l;
+  o.finest_coef = coef[J];
+  // every level's own P1 stiffness
+  for (int l = o.c; l <= J; ++l) {
+    Level& L = o.lv[l];
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(L.key.size());
+    for (size_t t = 0; t < L.tri.size(); ++t) {
+      double p[3][2];
+      int32_t id[3];
+      for (int k = 0; k < 3; ++k) {
+        physical(o, L.tri[t][k], p[k]);
+        id[k] = find_index(L.key, L.tri[t][k]);
+      }
+      double K[3][3];
+      tri_stiffness(p[0], p[1], p[2], K);
+      for (int i = 0; i < 3; ++i)
+        if (id[i] >= 0)
+          for (int j = 0; j < 3; ++j)
+            if (id[j] >= 0) rows[id[i]].push_back({id[j], coef[l][t] * K[i][j]});
+    }
+    L.A = csr_from_rows(L.key.size(), L.key.size(), rows);
+  }
+  // nodal interpolation from level l-1: the coarse function on its kept
+  // triangles, zero outside them and at its Dirichlet nodes
+  for (int l = std::max(1, o.c + 1); l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    Level& Lc = o.lv[l - 1];
+    std::set<std::array<uint64_t, 3>> kept(Lc.tri.begin(), Lc.tri.end());
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(Lf.key.size());
+    for (size_t k = 0; k < Lf.key.size(); ++k) {
+      const int32_t j = find_index(Lc.key, Lf.key[k]);
+      if (j >= 0) {
+        rows[k].push_back({j, 1.0});
+        continue;
+      }
+      uint64_t x, y;
+      node_xy(Lf.key[k], x, y);
+      int depth = 0;
+      uint64_t bx = 0, by = 0;
+      for (;;) {
+        uint64_t q[2] = {bx, by};
+        uint8_t sp = 0;
+        box_exists(o, depth, q, &sp);
+        if (depth == l - 1 || !sp) break;
+        uint64_t half = 1ULL << (o.D - depth - 1);
+        uint64_t cx = (x - bx * (2 * half)) >= half ? 1 : 0;
+        uint64_t cy = (y - by * (2 * half)) >= half ? 1 : 0;
+        if (x == (bx + 1) * 2 * half) cx = 1;
+        if (y == (by + 1) * 2 * half) cy = 1;
+        bx = 2 * bx + cx;
+        by = 2 * by + cy;
+        ++depth;
+      }
+      std::vector<std::array<uint64_t, 3>> ct;
+      box_triangles(o, depth, bx, by, l - 1, ct);
+      for (auto& kt : ct) {
+        if (!kept.count(kt)) continue;
+        i128 P[3][2];
+        for (int v = 0; v < 3; ++v) {
+          uint64_t vx, vy;
+          node_xy(kt[v], vx, vy);
+          P[v][0] = (i128)vx;
+          P[v][1] = (i128)vy;
+        }
+        const i128 det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+        const i128 n1 = ((i128)x - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * ((i128)y - P[0][1]);
+        const i128 n2 = (P[1][0] - P[0][0]) * ((i128)y - P[0][1]) - ((i128)x - P[0][0]) * (P[1][1] - P[0][1]);
+        const i128 n0 = det - n1 - n2;
+        if (n0 < 0 || n1 < 0 || n2 < 0) continue;
+        const i128 nn[3] = {n0, n1, n2};
+        for (int v = 0; v < 3; ++v) {
+          if (nn[v] == 0) continue;
+          const int32_t jj = find_index(Lc.key, kt[v]);
+          if (jj >= 0) rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
+        }
+        break;
+      }
+    }
+    Lf.I = csr_from_rows(Lf.key.size(), Lc.key.size(), rows);
+  }
+  // every level smoothed as a whole; near-boundary sets of Algorithm 3
+  for (int l = o.c + 1; l <= J; ++l) {
+    Level& L = o.lv[l];
+    L.smooth.resize(L.key.size());
+    for (size_t k = 0; k < L.key.size(); ++k) L.smooth[k] = (int32_t)k;
+    if (o.prm.nb_layers < 0) continue;
+    // Gamma_l: endpoints of edges of one kept triangle only; layer 0 = kept
+    // triangles with a vertex on Gamma_l, layer i = those with a vertex in layer i-1
+    std::map<std::pair<uint64_t, uint64_t>, int> edges;
+    for (auto& t : L.tri)
+      for (int k = 0; k < 3; ++k) edges[{std::min(t[k], t[(k + 1) % 3]), std::max(t[k], t[(k + 1) % 3])}] += 1;
+    std::set<uint64_t> verts;
+    for (auto& kv : edges)
+      if (kv.second == 1) {
+        verts.insert(kv.first.first);
+        verts.insert(kv.first.second);
+      }
+    std::set<uint64_t> layer;
+    for (int i = 0; i <= o.prm.nb_layers; ++i) {
+      layer.clear();
+      for (auto& t : L.tri)
+        if (verts.count(t[0]) || verts.count(t[1]) || verts.count(t[2]))
+          for (int k = 0; k < 3; ++k) layer.insert(t[k]);
+      if (layer == verts) break;
+      verts = layer;
+    }
+    for (auto k : verts) {
+      const int32_t id = find_index(L.key, k);
+      if (id >= 0) L.nbset.push_back(id);
+    }
+    std::sort(L.nbset.begin(), L.nbset.end());
+    const int64_t m = (int64_t)L.nbset.size();
+    L.nbchol.assign(m * m, 0.0);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = 0; b < m; ++b) L.nbchol[a * m + b] = L.A.get(L.nbset[a], L.nbset[b]);
+    if (m && !cholesky(L.nbchol, m)) {
+      o.err = "oracle: near-boundary block not positive definite";
+      return;
+    }
+  }
+}
+
 void build_aux(Oracle& o) {
+  for (int64_t v = 0; v < o.nv; ++v) o.neumann = o.neumann || o.bflag[v] == 2;
+  if (o.neumann) {
+    build_aux_mixed(o);
+    return;
+  }
   const int J = o.J;
   o.lv.assign(J + 1, Level());
   // does the domain fill the root box?
@@ -1028,7 +1333,7 @@ void build_transfer(Oracle& o) {
       ktri.clear();
       box_triangles(o, (int)b[0], b[1], b[2], o.J, ktri);
       for (auto& kt : ktri) {
-        if (!o.boxdomain && !tri_in.count(kt)) continue;  // aux hat functions vanish outside Omega^D_J
+        if ((!o.boxdomain || o.neumann) && !tri_in.count(kt)) continue;  // hats only on the kept triangles
         Pt K[3];
         for (int k = 0; k < 3; ++k) {
           double p[2];
@@ -2010,6 +2315,15 @@ void vcycle(const Oracle& o, int l, const std::vector<double>& f, std::vector<do
   vcycle(o, l - 1, fc, ec);
   for (int64_t i = 0; i < I.nr; ++i)
     for (int64_t p = I.ptr[i]; p < I.ptr[i + 1]; ++p) u[i] += I.val[p] * ec[I.col[p]];
+  if (!L.nbset.empty()) {
+    // Algorithm 3: near-boundary correction, u_J += (A_JJ)^{-1} (f - A u)_J
+    spmv(L.A, u.data(), Au.data());
+    const int64_t m = (int64_t)L.nbset.size();
+    std::vector<double> rj(m), dj(m);
+    for (int64_t a = 0; a < m; ++a) rj[a] = f[L.nbset[a]] - Au[L.nbset[a]];
+    chol_solve(L.nbchol, m, rj.data(), dj.data());
+    for (int64_t a = 0; a < m; ++a) u[L.nbset[a]] += dj[a];
+  }
   for (int s = 0; s < o.prm.nu_post; ++s) gs_sweep(L.A, L.smooth, L.cstart, f.data(), u.data(), false);
 }
 
@@ -2172,6 +2486,7 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     o->prm.additive = params[9];
     o->prm.fine_sweeps = params[10];
     o->prm.iteration = params[11];
+    o->prm.nb_layers = params[12];
   }
   if (o->prm.stage >= 0) assemble_fine(*o);  // stage -1: cluster tree only
   build_tree(*o);
@@ -2180,6 +2495,8 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     if (dim == 2) {
       build_aux(*o);
       if (o->err.empty()) build_transfer(*o);
+    } else if (std::find(o->bflag.begin(), o->bflag.end(), (uint8_t)2) != o->bflag.end()) {
+      o->err = "oracle: mixed Dirichlet/Neumann boundaries are built in 2D only";
     } else {
       build_aux3(*o);
       if (o->err.empty()) build_transfer3(*o);
@@ -2230,6 +2547,7 @@ int64_t orc_info(void* h, const char* what, int l) {
   if (w == "nI") return (int64_t)o.lv.at(l).I.col.size();
   if (w == "nsmooth") return l < 0 ? (int64_t)o.fine_smooth.size() : (int64_t)o.lv.at(l).smooth.size();
   if (w == "ncolours") return l < 0 ? (int64_t)o.fine_cstart.size() - 1 : (int64_t)o.lv.at(l).cstart.size() - 1;
+  if (w == "nnb") return (int64_t)o.lv.at(l).nbset.size();
   if (w == "nP") return (int64_t)o.P.col.size();
   if (w == "nPfull") return (int64_t)o.Pfull.col.size();
   return -1;
@@ -2280,6 +2598,7 @@ int orc_get(void* h, const char* what, int l, void* out) {
     return 0;
   }
   if (w == "finest_coef") { memcpy(out, o.finest_coef.data(), o.finest_coef.size() * 8); return 0; }
+  if (w == "nbset") { memcpy(out, o.lv.at(l).nbset.data(), o.lv[l].nbset.size() * 4); return 0; }
   if (w == "smooth") {
     if (l < 0) memcpy(out, o.fine_smooth.data(), o.fine_smooth.size() * 4);
     else memcpy(out, o.lv.at(l).smooth.data(), o.lv[l].smooth.size() * 4);

@@ -5,6 +5,7 @@ an invariant the paper states, a library routine for a special case, or a
 brute-force recomputation by a different characterisation.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -1001,3 +1002,303 @@ def test_dirichlet_aligned_l_kept_simplices_fully_covered(gen, dim):
             cx, cy = X.reshape(-1, 3).mean(1), Y.reshape(-1, 3).mean(1)
             want = {tuple(t) for t, ok in zip(allt.tolist(), (cx < 0.5) | (cy < 0.5)) if ok and l >= 1}
             assert {tuple(t) for t in o.level_tri(l).tolist()} == want, l
+
+
+# --------------------------------------------------------------------------
+# Mixed Dirichlet / Neumann boundaries (Sec. 3.4, remark on mixed boundary
+# conditions) and the near-boundary correction (Sec. 3.5, Algorithm 3).
+# Reading: a triangle meets Omega or Gamma_D when its interior does; Gamma_D
+# is the union of the fine boundary edges with two Dirichlet endpoints.
+# Checked against exact rational geometry, graph distances, point location
+# and the textbook natural-boundary stencil, all written here.
+# --------------------------------------------------------------------------
+
+NEUMANN = 2
+
+
+def _with_neumann(m, sel):
+    m.bflag = m.bflag.copy()
+    m.bflag[sel & (m.bflag == 1)] = NEUMANN
+    return m
+
+
+def _mixed_domain(gen, n, shape, where, seed=2):
+    m = gen.grid2d_domain(n, seed, shape)
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    inner = (x > 0) & (x < 1) & (y > 0) & (y < 1)
+    return _with_neumann(m, inner if where == "inner" else ((x == 0) & (y > 0) & (y < 1)))
+
+
+def test_mixed_square_levels_are_the_natural_boundary_stencil(gen):
+    # Unit square, Neumann on x = 1 (0 < y < 1): every triangle of sigma^(l) is
+    # kept, the free nodes are the lattice nodes off x = 0, y = 0, y = 1, and
+    # each level operator is the P1 Laplacian with the natural condition on
+    # x = 1: K_y (x) M_x + I (x) K_x with K the 1D stiffness (last diagonal 1
+    # on the Neumann end) and M_x = diag(1, ..., 1, 1/2) the lumped 1D mass.
+    m, _ = gen.workload_small_poisson()
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    m = _with_neumann(m, (x == 1.0) & (y > 0) & (y < 1))
+    o = oracle.Oracle(m, coarse_max=1)
+    for l in range(1, o.J + 1):
+        assert {tuple(t) for t in o.level_tri(l).tolist()} == {tuple(t) for t in o.level_alltri(l).tolist()}
+        ak = o.level_keys(l, all_nodes=True)
+        ax, ay = lattice_xy(ak)
+        want = np.sort(ak[(ax > 0) & (ay > 0) & (ay < TOP)])
+        assert np.array_equal(o.level_keys(l), want), l
+        nx, ny = 2 ** l, 2 ** l - 1
+        kx, ky = lattice_xy(o.level_keys(l))
+        step = TOP >> l
+        rm = ((ky // step - 1) * nx + (kx // step - 1)).astype(np.int64)
+        Pm = np.zeros((nx * ny, nx * ny))
+        Pm[rm, np.arange(nx * ny)] = 1
+        Ky = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(ny, ny)).toarray()
+        Kx = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(nx, nx)).toarray()
+        Kx[-1, -1] = 1
+        Mx = np.eye(nx)
+        Mx[-1, -1] = 0.5
+        want_A = np.kron(Ky, Mx) + np.kron(np.eye(ny), Kx)
+        assert np.abs(Pm @ o.A(l).toarray() @ Pm.T - want_A).max() < 1e-12, l
+
+
+def _fr_pt(p):
+    return (Fraction(float(p[0])), Fraction(float(p[1])))
+
+
+def _fr_orient(p, q, r):
+    return (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0])
+
+
+def _seg_hits_open_triangle(a, b, T):
+    # exact: clip a + t (b - a), 0 <= t <= 1, by the three closed half-planes of
+    # T; the interior is met when a piece of positive length remains and its
+    # midpoint lies strictly inside
+    t0, t1 = Fraction(0), Fraction(1)
+    for k in range(3):
+        p, q = T[k], T[(k + 1) % 3]
+        fa, fb = _fr_orient(p, q, a), _fr_orient(p, q, b)
+        if fa == fb:
+            if fa < 0:
+                return False
+            continue
+        tc = fa / (fa - fb)
+        if fb > fa:
+            t0 = max(t0, tc)
+        else:
+            t1 = min(t1, tc)
+    if t1 <= t0:
+        return False
+    tm = (t0 + t1) / 2
+    mid = (a[0] + tm * (b[0] - a[0]), a[1] + tm * (b[1] - a[1]))
+    return all(_fr_orient(T[k], T[(k + 1) % 3], mid) > 0 for k in range(3))
+
+
+def _fr_on_segment(a, b, p):
+    return (_fr_orient(a, b, p) == 0 and min(a[0], b[0]) <= p[0] <= max(a[0], b[0])
+            and min(a[1], b[1]) <= p[1] <= max(a[1], b[1]))
+
+
+def _gamma_d(m):
+    ed = np.sort(np.concatenate([m.elems[:, [0, 1]], m.elems[:, [1, 2]], m.elems[:, [2, 0]]]), axis=1)
+    uniq, cnt = np.unique(ed, axis=0, return_counts=True)
+    bd = uniq[cnt == 1]
+    bd = bd[(m.bflag[bd[:, 0]] == 1) & (m.bflag[bd[:, 1]] == 1)]
+    return [(_fr_pt(m.verts[a]), _fr_pt(m.verts[b])) for a, b in bd]
+
+
+@pytest.mark.parametrize("shape,where", [("L", "inner"), ("hole", "outer")])
+def test_mixed_kept_triangles_and_dirichlet_nodes_exact(gen, shape, where):
+    m = _mixed_domain(gen, 17, shape, where)
+    o = oracle.Oracle(m)
+    gd = _gamma_d(m)
+    assert gd and (m.bflag == NEUMANN).any()
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    for l in range(o.J + 1):
+        allt = o.level_alltri(l)
+        X, Y = _lattice_pts(o, allt.reshape(-1))
+        X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+        kept, dirn = set(), set()
+        for t in range(allt.shape[0]):
+            T = [(X[t, k], Y[t, k]) for k in range(3)]
+            Tf = [_fr_pt(p) for p in T]
+            tlo, thi = (X[t].min(), Y[t].min()), (X[t].max(), Y[t].max())
+            hit = any(_seg_hits_open_triangle(a, b, Tf) for a, b in gd
+                      if min(a[0], b[0]) <= thi[0] and max(a[0], b[0]) >= tlo[0]
+                      and min(a[1], b[1]) <= thi[1] and max(a[1], b[1]) >= tlo[1])
+            if hit:
+                dirn.update(allt[t].tolist())
+                continue
+            sel = np.where(np.all(lo <= thi, axis=1) & np.all(hi >= tlo, axis=1))[0]
+            cov = sum(_area(_clip_poly([tuple(p) for p in E[e]], T)) for e in sel)
+            if cov > 1e-12 * _area(T):
+                kept.add(tuple(allt[t].tolist()))
+        assert {tuple(t) for t in o.level_tri(l).tolist()} == kept, l
+        nodes = sorted({k for t in kept for k in t})
+        PX, PY = _lattice_pts(o, np.array(nodes, dtype=np.uint64))
+        free = [k for k, px, py in zip(nodes, PX, PY) if k not in dirn
+                and not any(_fr_on_segment(a, b, _fr_pt((px, py))) for a, b in gd)]
+        assert o.level_keys(l).tolist() == free, l
+
+
+def _angle_sums(o, tri):
+    X, Y = _lattice_pts(o, tri.reshape(-1))
+    X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+    ang = {}
+    for t in range(tri.shape[0]):
+        for k in range(3):
+            p = np.array([X[t, k], Y[t, k]])
+            u = np.array([X[t, (k + 1) % 3], Y[t, (k + 1) % 3]]) - p
+            v = np.array([X[t, (k + 2) % 3], Y[t, (k + 2) % 3]]) - p
+            a = np.arccos(np.clip(u @ v / np.linalg.norm(u) / np.linalg.norm(v), -1, 1))
+            ang[int(tri[t, k])] = ang.get(int(tri[t, k]), 0.0) + a
+    return ang
+
+
+@pytest.mark.parametrize("layers", [0, 2])
+def test_near_boundary_sets_are_graph_balls_around_the_boundary(gen, layers):
+    # Layer 0 holds the triangles touching Gamma_l, layer i those touching layer
+    # i-1; on a conforming grid the nodes of layer j are exactly the nodes within
+    # j + 1 edges of a boundary node (boundary nodes found here by angle sums)
+    from scipy.sparse.csgraph import shortest_path
+    m = _mixed_domain(gen, 17, "L", "inner")
+    o = oracle.Oracle(m, coarse_max=8, nb_layers=layers)
+    assert o.c < o.J
+    for l in range(o.c + 1, o.J + 1):
+        tri = o.level_tri(l)
+        nodes = np.unique(tri.reshape(-1))
+        pos = {int(k): i for i, k in enumerate(nodes)}
+        r, c = [], []
+        for t in tri.tolist():
+            for a in range(3):
+                r.append(pos[t[a]])
+                c.append(pos[t[(a + 1) % 3]])
+        G = sp.coo_matrix((np.ones(len(r)), (r, c)), shape=(nodes.size, nodes.size)).tocsr()
+        bnd = [pos[k] for k, a in _angle_sums(o, tri).items() if abs(a - 2 * np.pi) > 1e-9]
+        dist = shortest_path(G, directed=False, unweighted=True, indices=bnd).min(axis=0)
+        ball = set(int(k) for k in nodes[dist <= layers + 1])
+        keys = o.level_keys(l)
+        want = [i for i, k in enumerate(keys.tolist()) if k in ball]
+        assert o.near_boundary_set(l).tolist() == want, l
+        assert len(want) > 0 and (l < o.J or len(want) < keys.size)
+
+
+def test_mixed_interpolation_is_the_coarse_function_at_fine_nodes(gen):
+    # I_l e = the coarse P1 function (zero at Dirichlet nodes and outside the
+    # kept coarse triangles) evaluated at the fine free nodes, by point location
+    m = _mixed_domain(gen, 17, "hole", "outer")
+    o = oracle.Oracle(m, coarse_max=8)
+    rng = np.random.default_rng(7)
+    for l in range(o.c + 1, o.J + 1):
+        ctri, ckeys = o.level_tri(l - 1), o.level_keys(l - 1)
+        ec = rng.standard_normal(ckeys.size)
+        val = dict(zip(ckeys.tolist(), ec))
+        CX, CY = _lattice_pts(o, ctri.reshape(-1))
+        CX, CY = CX.reshape(-1, 3), CY.reshape(-1, 3)
+        FX, FY = _lattice_pts(o, o.level_keys(l))
+        want = np.zeros(FX.size)
+        for i in range(FX.size):
+            for t in range(ctri.shape[0]):
+                x0, y0 = CX[t, 0], CY[t, 0]
+                det = (CX[t, 1] - x0) * (CY[t, 2] - y0) - (CX[t, 2] - x0) * (CY[t, 1] - y0)
+                l1 = ((FX[i] - x0) * (CY[t, 2] - y0) - (CX[t, 2] - x0) * (FY[i] - y0)) / det
+                l2 = ((CX[t, 1] - x0) * (FY[i] - y0) - (FX[i] - x0) * (CY[t, 1] - y0)) / det
+                lam = (1 - l1 - l2, l1, l2)
+                if min(lam) >= -1e-12:
+                    want[i] = sum(lam[k] * val.get(int(ctri[t, k]), 0.0) for k in range(3))
+                    break
+        got = o.I(l) @ ec
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), l
+
+
+@pytest.mark.parametrize("layers", [-1, 2])
+def test_two_level_cycle_is_coarse_then_near_boundary_solve(gen, layers):
+    # Algorithm 3 with no smoothing steps on two levels: u1 = I A_c^{-1} I^t f,
+    # then u2 = u1 + E (E^t A_J E)^{-1} E^t (f - A_J u1), E the injection of J_{J,j}
+    m = _mixed_domain(gen, 17, "L", "inner")
+    o0 = oracle.Oracle(m)
+    J = o0.J
+    o = oracle.Oracle(m, coarse_max=o0.info("nlevel", J - 1), nu_pre=0, nu_post=0, nb_layers=layers)
+    assert o.c == J - 1
+    AJ, Ac, I = o.A(J).toarray(), o.A(J - 1).toarray(), o.I(J).toarray()
+    f = np.random.default_rng(3).standard_normal(AJ.shape[0])
+    u = I @ np.linalg.solve(Ac, I.T @ f)
+    nb = o.near_boundary_set(J)
+    assert (nb.size > 0) == (layers >= 0)
+    if nb.size:
+        r = f - AJ @ u
+        u[nb] += np.linalg.solve(AJ[np.ix_(nb, nb)], r[nb])
+    assert np.abs(o.vcycle(f) - u).max() <= 1e-11 * np.abs(u).max()
+
+
+def test_mixed_level_coefficient_is_the_mean_over_the_covered_part(gen):
+    # each level is rediscretised: A_l = sum over kept triangles of
+    # a_tau K_tau with a_tau the area-weighted mean of a over tau n Omega
+    m = _mixed_domain(gen, 17, "L", "inner")
+    m.coeff = gen.subcube_coefficient(m, 5, ncube=4)
+    o = oracle.Oracle(m, coarse_max=8)
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    for l in range(o.c, o.J + 1):
+        tri, keys = o.level_tri(l), o.level_keys(l)
+        pos = {int(k): i for i, k in enumerate(keys)}
+        X, Y = _lattice_pts(o, tri.reshape(-1))
+        X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+        A = np.zeros((keys.size, keys.size))
+        coef = []
+        for t in range(tri.shape[0]):
+            T = [(X[t, k], Y[t, k]) for k in range(3)]
+            tlo, thi = (X[t].min(), Y[t].min()), (X[t].max(), Y[t].max())
+            sel = np.where(np.all(lo <= thi, axis=1) & np.all(hi >= tlo, axis=1))[0]
+            ar = np.array([_area(_clip_poly([tuple(p) for p in E[e]], T)) for e in sel])
+            a_t = (ar * m.coeff[sel]).sum() / ar.sum()
+            coef.append(a_t)
+            B = np.array([[X[t, 1] - X[t, 0], X[t, 2] - X[t, 0]], [Y[t, 1] - Y[t, 0], Y[t, 2] - Y[t, 0]]])
+            G = np.linalg.inv(B).T @ np.array([[-1.0, 1.0, 0.0], [-1.0, 0.0, 1.0]])
+            K = a_t * abs(np.linalg.det(B)) / 2 * (G.T @ G)
+            for i in range(3):
+                for j in range(3):
+                    if int(tri[t, i]) in pos and int(tri[t, j]) in pos:
+                        A[pos[int(tri[t, i])], pos[int(tri[t, j])]] += K[i, j]
+        assert np.abs(o.A(l).toarray() - A).max() <= 1e-12 * np.abs(A).max(), l
+        if l == o.J:
+            assert np.abs(o.finest_coef() - np.array(coef)).max() <= 1e-12 * max(coef)
+
+
+def test_mixed_pcg_and_iteration_reach_the_dense_solution(gen):
+    m = _mixed_domain(gen, 17, "hole", "outer")
+    b = None
+    for layers in (-1, 2):
+        o = oracle.Oracle(m, coarse_max=8, nb_layers=layers)
+        assert o.c < o.J
+        if b is None:
+            b = o.mass_apply(gen.nodal_uniform(m, 2))
+            ref = np.linalg.solve(o.A().toarray(), b)
+        u, st, it, _ = o.solve(b, rtol=1e-13)
+        assert st == 0 and np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
+        if layers < 0:
+            # without the correction the cycle is symmetric and B is SPD
+            n = o.nfree
+            B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+            assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+            assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+        oi = oracle.Oracle(m, coarse_max=8, nb_layers=layers, iteration=1, max_iter=200)
+        u, st, it, hist = oi.solve(b, rtol=1e-10)
+        assert st == 0 and np.linalg.norm(u - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_near_boundary_correction_speeds_up_the_mixed_iteration(gen):
+    # Sec. 3.5: the non-matching boundaries of the auxiliary grids slow the
+    # cycle near the boundary; the correction on j = 2 layers restores a
+    # mesh-independent rate
+    rates = {}
+    for n in (17, 33, 65):
+        m = _mixed_domain(gen, n, "L", "inner")
+        for layers in (-1, 2):
+            o = oracle.Oracle(m, coarse_max=8, nb_layers=layers, iteration=1, max_iter=300)
+            b = o.mass_apply(gen.nodal_uniform(m, 1))
+            u, st, it, hist = o.solve(b, rtol=1e-8)
+            assert st == 0
+            rates[n, layers] = (hist[-1] / hist[0]) ** (1.0 / it)
+    for n in (17, 33, 65):
+        assert rates[n, 2] < 0.8 * rates[n, -1], rates
+        assert rates[n, 2] <= 0.25, rates
