@@ -1302,3 +1302,38 @@ def test_near_boundary_correction_speeds_up_the_mixed_iteration(gen):
     for n in (17, 33, 65):
         assert rates[n, 2] < 0.8 * rates[n, -1], rates
         assert rates[n, 2] <= 0.25, rates
+
+
+# --------------------------------------------------------------------------
+# Values printed by the paper: Table t_gmg (Sec. 6), tests/golden/t_gmg_dofs.txt
+# --------------------------------------------------------------------------
+
+def _golden_gmg():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "t_gmg_dofs.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                lab, n = line.split()
+                rows.append((int(lab), int(n)))
+    return rows
+
+
+def test_gmg_table_sizes_are_uniform_grid_vertices(gen):
+    rows = _golden_gmg()
+    assert [r[0] for r in rows] == [9, 10, 11]
+    for lab, n in rows:
+        assert n == (2 ** (lab + 1) + 1) ** 2
+    # the two smaller grids built and counted: vertices as printed, free unknowns
+    # (interior vertices) as the text's n_l = (2^l - 1)^2 with l = label + 1
+    for lab, n in rows[:2]:
+        side = 2 ** (lab + 1) + 1
+        m = gen.grid2d(side, 1, jitter=0.0, random_diag=False)
+        assert m.nv == n
+        o = oracle.Oracle(m, stage=0)
+        assert o.nfree == (2 ** (lab + 1) - 1) ** 2
+    # and the auxiliary hierarchy of a uniform grid has n_l = (2^l - 1)^2 free nodes per level
+    m = gen.grid2d(129, 1, jitter=0.0, random_diag=False)
+    o = oracle.Oracle(m)
+    assert [o.info("nlevel", l) for l in range(o.J + 1)] == [(2 ** l - 1) ** 2 for l in range(o.J + 1)]
