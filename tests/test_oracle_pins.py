@@ -1337,3 +1337,29 @@ def test_gmg_table_sizes_are_uniform_grid_vertices(gen):
     m = gen.grid2d(129, 1, jitter=0.0, random_diag=False)
     o = oracle.Oracle(m)
     assert [o.info("nlevel", l) for l in range(o.J + 1)] == [(2 ** l - 1) ** 2 for l in range(o.J + 1)]
+
+
+@pytest.mark.parametrize("shape,where", [("L", "inner"), ("hole", "outer"), ("hole", "inner")])
+def test_mixed_hierarchy_keeps_the_in_place_properties(gen, shape, where):
+    # What lets one in-place auxiliary vector carry the non-nested mixed
+    # hierarchy: a free node never turns Dirichlet on the next level, a node
+    # that left the grid never comes back, and every interpolation row is an
+    # identity, a midpoint (one or two halves) or empty
+    left = 0  # node-levels where a free node leaves the grid
+    for n, seed in ((17, 1), (33, 2), (33, 3)):
+        m = _mixed_domain(gen, n, shape, where, seed=seed)
+        o = oracle.Oracle(m, coarse_max=8)
+        ever = set(o.level_keys(o.c).tolist())
+        for l in range(o.c + 1, o.J + 1):
+            Fc, Ff = set(o.level_keys(l - 1).tolist()), set(o.level_keys(l).tolist())
+            allf = set(o.level_keys(l, all_nodes=True).tolist())
+            assert not (Fc & (allf - Ff)), (n, l)
+            assert not ((ever - Fc) & Ff), (n, l)
+            left += len(Fc - allf)
+            I = o.I(l).tocsr()
+            for r in range(I.shape[0]):
+                vs = sorted(v for v in I.data[I.indptr[r]:I.indptr[r + 1]] if v != 0)
+                assert vs in ([], [1.0], [0.5], [0.5, 0.5]), (n, l, vs)
+            ever |= Fc | Ff
+    # a Neumann cut through the lattice thins the coverage level by level
+    assert left > 0 if where == "inner" else left == 0
