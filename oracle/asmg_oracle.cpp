@@ -982,45 +982,55 @@ void build_aux_mixed(Oracle& o) {
       }
       uint64_t x, y;
       node_xy(Lf.key[k], x, y);
-      int depth = 0;
-      uint64_t bx = 0, by = 0;
-      for (;;) {
-        uint64_t q[2] = {bx, by};
+      // every box shown at level l-1 whose closed square holds the point; the
+      // first kept triangle containing it gives the coarse function's value
+      // (the same in every kept triangle that contains it)
+      std::vector<std::array<uint64_t, 3>> hold, stack;
+      stack.push_back({0, 0, 0});
+      while (!stack.empty()) {
+        const auto b = stack.back();
+        stack.pop_back();
+        const int depth = (int)b[0];
+        const uint64_t s = 1ULL << (o.D - depth);
+        if (x < b[1] * s || x > (b[1] + 1) * s || y < b[2] * s || y > (b[2] + 1) * s) continue;
+        uint64_t q[2] = {b[1], b[2]};
         uint8_t sp = 0;
-        box_exists(o, depth, q, &sp);
-        if (depth == l - 1 || !sp) break;
-        uint64_t half = 1ULL << (o.D - depth - 1);
-        uint64_t cx = (x - bx * (2 * half)) >= half ? 1 : 0;
-        uint64_t cy = (y - by * (2 * half)) >= half ? 1 : 0;
-        if (x == (bx + 1) * 2 * half) cx = 1;
-        if (y == (by + 1) * 2 * half) cy = 1;
-        bx = 2 * bx + cx;
-        by = 2 * by + cy;
-        ++depth;
+        if (!box_exists(o, depth, q, &sp)) continue;
+        if (depth == l - 1 || !sp) {
+          hold.push_back(b);
+          continue;
+        }
+        for (uint64_t ch = 0; ch < 4; ++ch)
+          stack.push_back({(uint64_t)depth + 1, 2 * b[1] + (ch & 1), 2 * b[2] + (ch >> 1)});
       }
-      std::vector<std::array<uint64_t, 3>> ct;
-      box_triangles(o, depth, bx, by, l - 1, ct);
-      for (auto& kt : ct) {
-        if (!kept.count(kt)) continue;
-        i128 P[3][2];
-        for (int v = 0; v < 3; ++v) {
-          uint64_t vx, vy;
-          node_xy(kt[v], vx, vy);
-          P[v][0] = (i128)vx;
-          P[v][1] = (i128)vy;
+      bool found = false;
+      for (const auto& b : hold) {
+        if (found) break;
+        std::vector<std::array<uint64_t, 3>> ct;
+        box_triangles(o, (int)b[0], b[1], b[2], l - 1, ct);
+        for (auto& kt : ct) {
+          if (!kept.count(kt)) continue;
+          i128 P[3][2];
+          for (int v = 0; v < 3; ++v) {
+            uint64_t vx, vy;
+            node_xy(kt[v], vx, vy);
+            P[v][0] = (i128)vx;
+            P[v][1] = (i128)vy;
+          }
+          const i128 det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
+          const i128 n1 = ((i128)x - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * ((i128)y - P[0][1]);
+          const i128 n2 = (P[1][0] - P[0][0]) * ((i128)y - P[0][1]) - ((i128)x - P[0][0]) * (P[1][1] - P[0][1]);
+          const i128 n0 = det - n1 - n2;
+          if (n0 < 0 || n1 < 0 || n2 < 0) continue;
+          const i128 nn[3] = {n0, n1, n2};
+          for (int v = 0; v < 3; ++v) {
+            if (nn[v] == 0) continue;
+            const int32_t jj = find_index(Lc.key, kt[v]);
+            if (jj >= 0) rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
+          }
+          found = true;
+          break;
         }
-        const i128 det = (P[1][0] - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * (P[1][1] - P[0][1]);
-        const i128 n1 = ((i128)x - P[0][0]) * (P[2][1] - P[0][1]) - (P[2][0] - P[0][0]) * ((i128)y - P[0][1]);
-        const i128 n2 = (P[1][0] - P[0][0]) * ((i128)y - P[0][1]) - ((i128)x - P[0][0]) * (P[1][1] - P[0][1]);
-        const i128 n0 = det - n1 - n2;
-        if (n0 < 0 || n1 < 0 || n2 < 0) continue;
-        const i128 nn[3] = {n0, n1, n2};
-        for (int v = 0; v < 3; ++v) {
-          if (nn[v] == 0) continue;
-          const int32_t jj = find_index(Lc.key, kt[v]);
-          if (jj >= 0) rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
-        }
-        break;
       }
     }
     Lf.I = csr_from_rows(Lf.key.size(), Lc.key.size(), rows);

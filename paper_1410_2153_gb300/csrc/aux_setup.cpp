@@ -157,6 +157,41 @@ void leaves_in(const BoxTree& T, int64_t lox, int64_t loy, int64_t hix, int64_t 
 
 constexpr unsigned MAX_THREADS = 64;
 
+// A fine boundary segment of Gamma_D (mixed boundaries).
+struct GSeg {
+  double ax, ay, bx, by;
+};
+
+inline double orient2(double px, double py, double qx, double qy, double rx, double ry) {
+  return (qx - px) * (ry - py) - (qy - py) * (rx - px);
+}
+
+// The closed segment s meets the interior of the CCW triangle K exactly when
+// no line among K's edge lines and s's own line separates them, touching
+// allowed (separating axes of the Minkowski difference of two convex
+// polygons; only signs of orientations are used).
+inline bool seg_cuts_open_tri(const double K[3][2], const GSeg& s) {
+  for (int e = 0; e < 3; ++e) {
+    const double* p = K[e];
+    const double* q = K[(e + 1) % 3];
+    if (orient2(p[0], p[1], q[0], q[1], s.ax, s.ay) <= 0 && orient2(p[0], p[1], q[0], q[1], s.bx, s.by) <= 0)
+      return false;
+  }
+  int pos = 0, neg = 0;
+  for (int v = 0; v < 3; ++v) {
+    const double o = orient2(s.ax, s.ay, s.bx, s.by, K[v][0], K[v][1]);
+    pos += o > 0;
+    neg += o < 0;
+  }
+  return pos > 0 && neg > 0;
+}
+
+// The point (x, y) lies on the closed segment s.
+inline bool on_seg(const GSeg& s, double x, double y) {
+  return orient2(s.ax, s.ay, s.bx, s.by, x, y) == 0 && std::min(s.ax, s.bx) <= x && x <= std::max(s.ax, s.bx) &&
+         std::min(s.ay, s.by) <= y && y <= std::max(s.ay, s.by);
+}
+
 // f(thread, nthreads, begin, end) over contiguous ranges of [0, n), in order
 template <class F>
 void parallel_for(int64_t n, F f) {
@@ -311,7 +346,13 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   // R17: a domain that does not fill the root box uses the Dirichlet
   // auxiliary grids T^D_l (triangles inside Omega); the same clipping pass
   // then also measures how much of each triangle the fine elements cover
-  const bool dgrid = !mesh.boxdomain;
+  const bool dgrid = !mesh.boxdomain && !mesh.mixed;
+  // R18: a Neumann vertex selects the mixed grids T^M_l of the remark on
+  // mixed boundary conditions (Sec. 3.4): the triangles whose interior meets
+  // Omega and not Gamma_D, every node of them free except those on Gamma_D
+  // or on a triangle cut by it.  They need the covered areas as well.
+  const bool mixed = mesh.mixed;
+  const bool cover = dgrid || mixed;
   // integral of a over the lower-right (0) / upper-left (1) diagonal halves
   // of every box, per depth, aligned with boxes_at(T, d); the covered area
   // of the same halves
@@ -390,7 +431,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       });
     }
   }
-  if (varcoef || dgrid) {
+  if (varcoef || cover) {
     // clip every fine element against the finest triangles it meets
     std::vector<std::vector<std::pair<int64_t, double>>> contrib(64), ccontrib(64);
     parallel_for(mesh.ne, [&](unsigned t, unsigned, int64_t b, int64_t e) {
@@ -435,7 +476,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
             moments(poly, m, M);
             if (!(M[0] > 0)) continue;
             if (varcoef) mine.push_back({f0 + (int64_t)q, M[0] * mesh.coeff[el]});
-            if (dgrid) ccontrib[t].push_back({f0 + (int64_t)q, M[0]});
+            if (cover) ccontrib[t].push_back({f0 + (int64_t)q, M[0]});
           }
         }
       }
@@ -450,7 +491,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     // (halfcov, fancov)
     for (int pass = 0; pass < 2; ++pass) {
     if (pass == 0 && !varcoef) continue;
-    if (pass == 1 && !dgrid) continue;
+    if (pass == 1 && !cover) continue;
     const std::vector<double>& IA = pass == 0 ? I : C;
     auto& H = pass == 0 ? half : halfcov;
     auto& FI = pass == 0 ? fanint : fancov;
@@ -510,25 +551,114 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     lattice_point(tree, t[2], pc);
     return 0.5 * ((pb[0] - pa[0]) * (pc[1] - pa[1]) - (pc[0] - pa[0]) * (pb[1] - pa[1]));
   };
-  auto tri_inside = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> bool {
-    if (!dgrid) return true;
-    double cov;
+  // the value stored for one triangle in a box-half table H or a fan table FI
+  auto tri_value = [&](const std::vector<std::vector<std::array<double, 2>>>& H,
+                       const std::vector<std::pair<std::array<uint64_t, 3>, double>>& FI, int d, uint64_t p, bool diag,
+                       int k, const std::array<uint64_t, 3>& t) -> double {
     if (diag) {
       const auto& bx = BX[d];
       const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
-      cov = halfcov[d][i][k];
-    } else {
-      auto it = std::lower_bound(fancov.begin(), fancov.end(),
-                                 std::pair<std::array<uint64_t, 3>, double>(tri_sorted(t), -HUGE_VAL));
-      cov = it->second;
+      return H[d][i][k];
     }
-    return cov >= (1.0 - 1e-9) * tri_area(t);
+    auto it = std::lower_bound(FI.begin(), FI.end(), std::pair<std::array<uint64_t, 3>, double>(tri_sorted(t), -HUGE_VAL));
+    return it->second;
+  };
+  // Gamma_D (mixed): the fine boundary edges (edges of one element) with two
+  // Dirichlet endpoints, binned by bounding box on a uniform grid of gn x gn
+  // cells over the root box
+  std::vector<GSeg> gd;
+  int gn = 1;
+  std::vector<int64_t> gstart(2, 0);
+  std::vector<int32_t> gitem;
+  auto gcell = [&](double v, int a, double slack) {
+    const double c = (v - tree.amin[a]) / tree.L * gn + slack;
+    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(c)));
+  };
+  if (mixed) {
+    std::vector<std::array<int32_t, 2>> ed;
+    ed.reserve(3 * mesh.ne);
+    for (int64_t e = 0; e < mesh.ne; ++e)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t a = mesh.E[3 * e + k], b = mesh.E[3 * e + (k + 1) % 3];
+        ed.push_back({std::min(a, b), std::max(a, b)});
+      }
+    std::sort(ed.begin(), ed.end());
+    for (size_t i = 0; i < ed.size();) {
+      size_t j = i;
+      while (j < ed.size() && ed[j] == ed[i]) ++j;
+      const int32_t a = ed[i][0], b = ed[i][1];
+      if (j - i == 1 && mesh.bflag[a] == 1 && mesh.bflag[b] == 1)
+        gd.push_back(GSeg{mesh.X[2 * (int64_t)a], mesh.X[2 * (int64_t)a + 1], mesh.X[2 * (int64_t)b],
+                          mesh.X[2 * (int64_t)b + 1]});
+      i = j;
+    }
+    gn = std::max(1, std::min(1024, (int)std::sqrt((double)gd.size())));
+    gstart.assign((size_t)gn * gn + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int64_t> fill(gstart.begin(), gstart.end() - 1);
+      for (size_t q = 0; q < gd.size(); ++q) {
+        const GSeg& g = gd[q];
+        const int x0 = gcell(std::min(g.ax, g.bx), 0, -1e-9), x1 = gcell(std::max(g.ax, g.bx), 0, 1e-9);
+        const int y0 = gcell(std::min(g.ay, g.by), 1, -1e-9), y1 = gcell(std::max(g.ay, g.by), 1, 1e-9);
+        for (int y = y0; y <= y1; ++y)
+          for (int x = x0; x <= x1; ++x) {
+            const int64_t cidx = (int64_t)y * gn + x;
+            if (pass == 0) gstart[cidx + 1] += 1;
+            else gitem[fill[cidx]++] = (int32_t)q;
+          }
+      }
+      if (pass == 0) {
+        for (size_t cidx = 0; cidx + 1 < gstart.size(); ++cidx) gstart[cidx + 1] += gstart[cidx];
+        gitem.assign(gstart.back(), 0);
+      }
+    }
+  }
+  // f(segment) for the Gamma_D segments binned in the cells that the box
+  // [lo, hi] meets; stops when f returns true
+  auto gd_any = [&](double lox, double loy, double hix, double hiy, auto&& f) -> bool {
+    const int x0 = gcell(lox, 0, -1e-9), x1 = gcell(hix, 0, 1e-9);
+    const int y0 = gcell(loy, 1, -1e-9), y1 = gcell(hiy, 1, 1e-9);
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const int64_t cidx = (int64_t)y * gn + x;
+        for (int64_t q = gstart[cidx]; q < gstart[cidx + 1]; ++q)
+          if (f(gd[gitem[q]])) return true;
+      }
+    return false;
+  };
+  // the interior of lattice triangle t meets Gamma_D
+  auto gd_cuts = [&](const std::array<uint64_t, 3>& t) -> bool {
+    if (gd.empty()) return false;
+    double K[3][2];
+    for (int v = 0; v < 3; ++v) lattice_point(tree, t[v], K[v]);
+    const double lox = std::min({K[0][0], K[1][0], K[2][0]}), hix = std::max({K[0][0], K[1][0], K[2][0]});
+    const double loy = std::min({K[0][1], K[1][1], K[2][1]}), hiy = std::max({K[0][1], K[1][1], K[2][1]});
+    return gd_any(lox, loy, hix, hiy, [&](const GSeg& g) { return seg_cuts_open_tri(K, g); });
+  };
+  // lattice node x lies on Gamma_D
+  auto on_gd = [&](uint64_t x) -> bool {
+    if (gd.empty()) return false;
+    double P[2];
+    lattice_point(tree, x, P);
+    return gd_any(P[0], P[1], P[0], P[1], [&](const GSeg& g) { return on_seg(g, P[0], P[1]); });
+  };
+  // mixed: a triangle belongs to T^M_l when its interior meets Omega
+  // (positive covered area) and not Gamma_D
+  auto tri_kept = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> bool {
+    return tri_value(halfcov, fancov, d, p, diag, k, t) > 1e-12 * tri_area(t) && !gd_cuts(t);
+  };
+  auto tri_inside = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> bool {
+    if (mixed) return tri_kept(d, p, diag, k, t);
+    if (!dgrid) return true;
+    return tri_value(halfcov, fancov, d, p, diag, k, t) >= (1.0 - 1e-9) * tri_area(t);
   };
   // node x is free at level l (a vertex of sigma^(l) off the boundary of
   // Omega^D_l): every level-l triangle around it is inside.  The box shown
   // at level l around x in each quadrant holds those triangles.
+  // Mixed: x is free when it is a node of a kept triangle, lies on no
+  // triangle cut by Gamma_D and not on Gamma_D itself.
   auto free_at = [&](uint64_t x, int l, std::vector<std::array<uint64_t, 3>>& kt) -> bool {
-    if (boundary_key(T, x)) return false;
+    if (!mixed && boundary_key(T, x)) return false;
     const uint64_t X = compact(x), Y = compact(x >> 1);
     bool node = false;
     for (int q = 0; q < 4; ++q) {
@@ -550,11 +680,16 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       const bool diag = !(h[0] || h[1] || h[2] || h[3]);
       for (size_t k = 0; k < kt.size(); ++k) {
         if (kt[k][0] != x && kt[k][1] != x && kt[k][2] != x) continue;
+        if (mixed) {
+          if (gd_cuts(kt[k])) return false;
+          if (tri_value(halfcov, fancov, d, p, diag, (int)k, kt[k]) > 1e-12 * tri_area(kt[k])) node = true;
+          continue;
+        }
         node = true;
         if (!tri_inside(d, p, diag, (int)k, kt[k])) return false;
       }
     }
-    return node;
+    return node && !(mixed && on_gd(x));
   };
 
   // ---- finest-level nodes (aux unknowns): free at level J
@@ -573,7 +708,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
         box_tris(T, leaves[q].first, leaves[q].second, h, tri);
         for (auto& x : tri)
           for (int k = 0; k < 3; ++k)
-            if (!boundary_key(T, x[k])) part[t].push_back(x[k]);
+            if (mixed || !boundary_key(T, x[k])) part[t].push_back(x[k]);
       }
     });
     out.aux_key = merge_unique(part);
@@ -594,7 +729,44 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   // first level at which each node is free: its birth level in a box domain;
   // with T^D_l the first level from its birth on whose triangles around it
   // are all inside (free at one level, free at all finer ones)
-  std::vector<int32_t> phi;
+  std::vector<int32_t> phi, psi;
+  if (mixed) {
+    // every lattice node of sigma^(J) is a candidate: phi = first free level
+    // from its birth on, psi = the first level after that where it is no
+    // longer free (a node that leaves the grid does not come back)
+    std::vector<std::pair<uint64_t, int32_t>> born;
+    for (int l = 1; l <= J; ++l)
+      for (auto& v : newnodes[l]) born.push_back({v[0], l});
+    std::sort(born.begin(), born.end());
+    const std::vector<uint64_t>& cand = out.aux_key;
+    std::vector<int32_t> cphi(cand.size(), J + 1), cpsi(cand.size(), J + 1);
+    parallel_for((int64_t)cand.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+      std::vector<std::array<uint64_t, 3>> kt;
+      for (int64_t q = b0; q < b1; ++q) {
+        auto it = std::lower_bound(born.begin(), born.end(), std::pair<uint64_t, int32_t>(cand[q], 0));
+        int l = (it != born.end() && it->first == cand[q]) ? it->second : 0;
+        while (l <= J && !free_at(cand[q], l, kt)) ++l;
+        cphi[q] = l;
+        if (l > J) continue;
+        ++l;
+        while (l <= J && free_at(cand[q], l, kt)) ++l;
+        cpsi[q] = l;
+      }
+    });
+    std::vector<uint64_t> ak;
+    for (size_t q = 0; q < cand.size(); ++q)
+      if (cphi[q] <= J) {
+        ak.push_back(cand[q]);
+        phi.push_back(cphi[q]);
+        psi.push_back(cpsi[q]);
+      }
+    out.aux_key.swap(ak);
+    out.nlevel.assign(J + 1, 0);
+    for (int32_t f : phi) out.nlevel[f] += 1;
+    for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
+    out.phi = phi;
+    out.psi = psi;
+  }
   if (dgrid) {
     std::vector<std::pair<uint64_t, int32_t>> born;
     for (int l = 1; l <= J; ++l)
@@ -618,6 +790,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   AKI.build(AK, 20);
   // aux ID of node x at level l, or -1 where it is not a free node there
   auto level_id = [&](uint64_t x, int l) -> int32_t {
+    if (mixed) {
+      const int32_t id = AKI.find(x);
+      return (id >= 0 && phi[id] <= l && l < psi[id]) ? id : -1;
+    }
     if (boundary_key(T, x)) return -1;
     const int32_t id = AKI.find(x);
     if (dgrid && (id < 0 || phi[id] > l)) return -1;
@@ -625,8 +801,20 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   };
   // coarsest level used: finest level with at most coarse_max_dofs free nodes
   out.c = 0;
-  for (int l = 0; l <= J; ++l)
-    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  if (mixed) {
+    // by the free nodes of each level (the nodes that left the grid excluded)
+    std::vector<int64_t> nreal(J + 2, 0);
+    for (size_t q = 0; q < phi.size(); ++q) {
+      nreal[phi[q]] += 1;
+      nreal[psi[q]] -= 1;
+    }
+    for (int l = 1; l <= J; ++l) nreal[l] += nreal[l - 1];
+    for (int l = 0; l <= J; ++l)
+      if (nreal[l] <= prm.coarse_max_dofs) out.c = l;
+  } else {
+    for (int l = 0; l <= J; ++l)
+      if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  }
   const int c = out.c;
 
   // coefficient of one triangle of box (d, p) at a level where the box shows
@@ -634,6 +822,11 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   // (the mean of a over the triangle, a = 0 outside Omega and a = 1 inside
   // when no coefficient is given)
   auto tri_coef = [&](int d, uint64_t p, bool diag, int k, const std::array<uint64_t, 3>& t) -> double {
+    if (mixed) {
+      // the mean of a over tau n Omega (R18)
+      if (!varcoef) return 1.0;
+      return tri_value(half, fanint, d, p, diag, k, t) / tri_value(halfcov, fancov, d, p, diag, k, t);
+    }
     if (!varcoef && !dgrid) return 1.0;
     const auto& H = varcoef ? half : halfcov;
     const auto& FI = varcoef ? fanint : fancov;
@@ -703,8 +896,9 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     sort_unique(changed);
     std::vector<uint64_t> sm;
     std::vector<std::pair<int, uint64_t>> rel;
-    if (prm.smoothing == 1) {
-      // every node of the level, every box shown at the level
+    if (prm.smoothing == 1 || mixed) {
+      // every node of the level, every box shown at the level (always for
+      // the mixed grids, which are not nested)
       for (int dd = 0; dd <= l; ++dd)
         for (uint64_t p : BX[dd])
           if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
@@ -810,8 +1004,71 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
       L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
     }
+    if (mixed && mesh.nb_layers >= 0) {
+      // Algorithm 3: J_{l,j} = the free nodes of the j-th layer of triangles
+      // around Gamma_l, i.e. the nodes within j + 1 edges of a vertex of an
+      // edge of one kept triangle only (breadth-first over the level's edges)
+      std::vector<uint64_t> nodes(L.tri_key.begin(), L.tri_key.end());
+      sort_unique(nodes);
+      auto loc = [&](uint64_t k) { return (int64_t)(std::lower_bound(nodes.begin(), nodes.end(), k) - nodes.begin()); };
+      std::vector<std::array<int64_t, 2>> ed;
+      const size_t nt = L.tri_coef.size();
+      ed.reserve(3 * nt);
+      for (size_t t = 0; t < nt; ++t)
+        for (int e = 0; e < 3; ++e) {
+          const int64_t a = loc(L.tri_key[3 * t + e]), b = loc(L.tri_key[3 * t + (e + 1) % 3]);
+          ed.push_back({std::min(a, b), std::max(a, b)});
+        }
+      std::sort(ed.begin(), ed.end());
+      std::vector<int32_t> dist(nodes.size(), -1);
+      std::vector<int64_t> frontier;
+      std::vector<int64_t> adjs(nodes.size() + 1, 0);
+      std::vector<int64_t> adj;
+      std::vector<std::array<int64_t, 2>> ue;
+      for (size_t i = 0; i < ed.size();) {
+        size_t j = i;
+        while (j < ed.size() && ed[j] == ed[i]) ++j;
+        if (j - i == 1)
+          for (int v = 0; v < 2; ++v)
+            if (dist[ed[i][v]] < 0) {
+              dist[ed[i][v]] = 0;
+              frontier.push_back(ed[i][v]);
+            }
+        ue.push_back(ed[i]);
+        i = j;
+      }
+      for (auto& e : ue) {
+        adjs[e[0] + 1] += 1;
+        adjs[e[1] + 1] += 1;
+      }
+      for (size_t i = 0; i < nodes.size(); ++i) adjs[i + 1] += adjs[i];
+      adj.assign(adjs.back(), 0);
+      {
+        std::vector<int64_t> fill(adjs.begin(), adjs.end() - 1);
+        for (auto& e : ue) {
+          adj[fill[e[0]]++] = e[1];
+          adj[fill[e[1]]++] = e[0];
+        }
+      }
+      for (int r = 1; r <= mesh.nb_layers + 1 && !frontier.empty(); ++r) {
+        std::vector<int64_t> next;
+        for (int64_t v : frontier)
+          for (int64_t q = adjs[v]; q < adjs[v + 1]; ++q)
+            if (dist[adj[q]] < 0) {
+              dist[adj[q]] = r;
+              next.push_back(adj[q]);
+            }
+        frontier.swap(next);
+      }
+      for (size_t i = 0; i < nodes.size(); ++i) {
+        if (dist[i] < 0) continue;
+        const int32_t id = level_id(nodes[i], l);
+        if (id >= 0) L.nb_id.push_back(id);
+      }
+      std::sort(L.nb_id.begin(), L.nb_id.end());
+    }
     // new nodes with their parents
-    if (!dgrid) {
+    if (!dgrid && !mixed) {
       for (auto& v : newnodes[l]) {
         if (boundary_key(T, v[0])) continue;
         L.new_id.push_back(AKI.find(v[0]));

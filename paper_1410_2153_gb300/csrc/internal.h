@@ -130,6 +130,9 @@ struct AuxLevelHost {
   std::vector<int32_t> tri_id;            // [ntri * 3]
   std::vector<uint64_t> tri_key;          // [ntri * 3] lattice Morton keys
   std::vector<double> tri_coef;           // [ntri]
+  // mixed boundaries: the near-boundary set J_{l,j} of Algorithm 3 (aux IDs,
+  // ascending); empty otherwise
+  std::vector<int32_t> nb_id;
 };
 
 // What the device Scott-Zhang kernel needs of the closed tree and the finest
@@ -162,6 +165,9 @@ struct AuxHost {
   std::vector<double> coarse_tri_coef;
   Triplets P;                                  // (free fine dof, aux ID, value)
   SZTable sz;                                  // input of the device transfer build
+  // mixed boundaries: aux ID q is a free node of the levels phi[q] <= l <
+  // psi[q] (free on one interval of levels); empty otherwise
+  std::vector<int32_t> phi, psi;
 };
 
 struct MeshHost {
@@ -172,6 +178,8 @@ struct MeshHost {
   std::vector<uint8_t> bflag;
   std::vector<double> coeff;  // empty: a = 1
   bool boxdomain = true;      // the elements fill the root box (else Dirichlet auxiliary grids, 2D)
+  bool mixed = false;         // some vertex is Neumann (flag 2): mixed auxiliary grids (2D)
+  int nb_layers = 2;          // mixed: layers j of the near-boundary sets (< 0: none)
 };
 
 // closure of the cluster tree, auxiliary grids and the Scott-Zhang transfer

@@ -80,7 +80,7 @@ extern "C" {
 // root box: amin[dim], side L; returns a handle (errors: see shim_error)
 void* shim_build(int dim, int64_t nv, const double* X, int64_t ne, const int32_t* E, const uint8_t* bflag,
                  const double* coeff, int nlev, const int64_t* cnt, const uint64_t* flat, const double* amin, double L,
-                 int n_min, int coarse_max, int smoothing) {
+                 int n_min, int coarse_max, int smoothing, int nb_layers) {
   Shim* h = new Shim();
   try {
     const int nvpe = dim + 1;
@@ -111,6 +111,8 @@ void* shim_build(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     }
     const double box = std::pow(L, dim);
     m.boxdomain = std::fabs(meas - box) <= 1e-12 * box;
+    m.mixed = std::find(bflag, bflag + nv, (uint8_t)2) != bflag + nv;
+    m.nb_layers = nb_layers;
     TreeResult tree;
     for (int k = 0; k < dim; ++k) tree.amin[k] = amin[k];
     tree.L = L;
@@ -131,7 +133,7 @@ void* shim_build(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     p.fine_sweeps = 1;
     std::vector<int32_t> vof;
     for (int64_t v = 0; v < nv; ++v)
-      if (bflag[v] == 0) vof.push_back((int32_t)v);
+      if (bflag[v] != 1) vof.push_back((int32_t)v);  // Neumann vertices are unknowns too
     if (dim == 2)
       build_aux_host(m, tree, p, h->aux);
     else
@@ -164,6 +166,8 @@ int64_t shim_get(void* hp, const char* what, int l, void* out) {
   if (w == "P_r") return put(a.P.r.data(), (int64_t)a.P.r.size(), 4);
   if (w == "P_c") return put(a.P.c.data(), (int64_t)a.P.c.size(), 4);
   if (w == "P_v") return put(a.P.v.data(), (int64_t)a.P.v.size(), 8);
+  if (w == "phi") return put(a.phi.data(), (int64_t)a.phi.size(), 4);
+  if (w == "psi") return put(a.psi.data(), (int64_t)a.psi.size(), 4);
   const int k = l - (a.c + 1);
   if (k < 0 || k >= (int)a.levels.size()) return -1;
   AuxLevelHost& L = a.levels[k];
@@ -174,6 +178,7 @@ int64_t shim_get(void* hp, const char* what, int l, void* out) {
   if (w == "tri_key") return put(L.tri_key.data(), (int64_t)L.tri_key.size(), 8);
   if (w == "tri_id") return put(L.tri_id.data(), (int64_t)L.tri_id.size(), 4);
   if (w == "tri_coef") return put(L.tri_coef.data(), (int64_t)L.tri_coef.size(), 8);
+  if (w == "nb_id") return put(L.nb_id.data(), (int64_t)L.nb_id.size(), 4);
   return -1;
 }
 

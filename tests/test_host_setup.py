@@ -44,7 +44,8 @@ def shim(tmp_path_factory):
     lib.shim_build.restype = ctypes.c_void_p
     lib.shim_build.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                               ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                               ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int]
     lib.shim_error.restype = ctypes.c_char_p
     lib.shim_error.argtypes = [ctypes.c_void_p]
     lib.shim_free.argtypes = [ctypes.c_void_p]
@@ -137,7 +138,7 @@ def _compare(lib, m, o, params, dim, op_tol):
     h = lib.shim_build(dim, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
                        None if C is None else C.ctypes.data, len(cnt), cnt.ctypes.data, flat.ctypes.data,
                        amin.ctypes.data, L, params.get("n_min", 3), params.get("coarse_max", 512),
-                       params.get("smoothing", 0))
+                       params.get("smoothing", 0), params.get("nb_layers", 2))
     try:
         assert lib.shim_error(h) == b"", lib.shim_error(h)
         # closure: the split boxes of every depth
@@ -248,3 +249,140 @@ def test_host_setup_matches_oracle(shim, gen, name):
     m, params, dim, op_tol = _cases(gen)[name]
     o = oracle.Oracle(m, **params)
     _compare(shim, m, o, params, dim, op_tol)
+
+
+# --------------------------------------------------------------------------
+# Mixed Dirichlet / Neumann boundaries (2D): the library's host setup of the
+# mixed grids against the oracle's construction of the same grids.  The
+# library keeps one aux ID per node that is free on some level, free on the
+# levels phi <= l < psi; the oracle keeps each level's free nodes.
+# --------------------------------------------------------------------------
+
+def _mixed_mesh(gen, kind, n, seed):
+    if kind == "square":
+        m = gen.grid2d(n, seed)
+    elif kind == "graded":
+        m = gen.grid2d(n, seed, graded=True)
+    else:
+        m = gen.grid2d_domain(n, seed, kind)
+    x, y = m.verts[:, 0], m.verts[:, 1]
+    return m, x, y
+
+
+def _mixed_cases(gen):
+    out = {}
+    m, x, y = _mixed_mesh(gen, "square", 17, 1)
+    m.bflag = m.bflag.copy()
+    m.bflag[(x == 1.0) & (y > 0) & (y < 1)] = 2
+    out["square17_right"] = (m, {})
+    m, x, y = _mixed_mesh(gen, "L", 17, 2)
+    m.bflag = m.bflag.copy()
+    m.bflag[(m.bflag == 1) & (x > 0) & (x < 1) & (y > 0) & (y < 1)] = 2
+    out["L17_cut_c8"] = (m, {"coarse_max": 8})
+    m, x, y = _mixed_mesh(gen, "hole", 17, 2)
+    m.bflag = m.bflag.copy()
+    m.bflag[(m.bflag == 1) & (x == 0) & (y > 0) & (y < 1)] = 2
+    m.coeff = np.exp(np.random.default_rng(4).normal(size=m.ne))
+    out["hole17_left_lognormal"] = (m, {"coarse_max": 8})
+    m, x, y = _mixed_mesh(gen, "L", 33, 3)
+    m.bflag = m.bflag.copy()
+    m.bflag[(m.bflag == 1) & (x > 0) & (x < 1) & (y > 0) & (y < 1)] = 2
+    out["L33_cut_nb0"] = (m, {"coarse_max": 8, "nb_layers": 0})
+    m, x, y = _mixed_mesh(gen, "graded", 33, 5)
+    m.bflag = m.bflag.copy()
+    m.bflag[((x == 1.0) | (y == 1.0)) & (x > 0) & (y > 0)] = 2
+    out["graded33_two_sides_nb3"] = (m, {"coarse_max": 16, "nb_layers": 3})
+    return out
+
+
+def _compare_mixed(lib, m, o, params):
+    segs = o.tree_levels()
+    splits = [s_[s_[:, 3] == 1, 0].astype(np.uint64) for s_ in segs]
+    while splits and len(splits[-1]) == 0:
+        splits.pop()
+    cnt = np.array([len(s_) for s_ in splits], np.int64)
+    flat = np.concatenate(splits) if splits else np.zeros(0, np.uint64)
+    r = o.root()
+    amin = np.ascontiguousarray(r[:2], dtype=np.float64)
+    L = float(r[3])
+    X = np.ascontiguousarray(m.verts, dtype=np.float64)
+    E = np.ascontiguousarray(m.elems, dtype=np.int32)
+    B = np.ascontiguousarray(m.bflag, dtype=np.uint8)
+    C = None if m.coeff is None else np.ascontiguousarray(m.coeff, dtype=np.float64)
+    h = lib.shim_build(2, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
+                       None if C is None else C.ctypes.data, len(cnt), cnt.ctypes.data, flat.ctypes.data,
+                       amin.ctypes.data, L, params.get("n_min", 3), params.get("coarse_max", 512), 1,
+                       params.get("nb_layers", 2))
+    try:
+        assert lib.shim_error(h) == b"", lib.shim_error(h)
+        J, c = lib.shim_get(h, b"J", 0, None), lib.shim_get(h, b"c", 0, None)
+        assert J == o.J and c == o.c, (J, o.J, c, o.c)
+        ak = _get(lib, h, "aux_key", 0, np.uint64)
+        phi = _get(lib, h, "phi", 0, np.int32)
+        psi = _get(lib, h, "psi", 0, np.int32)
+        assert phi.size == ak.size == psi.size and np.all(phi < psi)
+        # the free nodes of every level
+        for l in range(J + 1):
+            assert np.array_equal(ak[(phi <= l) & (l < psi)], o.level_keys(l)), ("free", l)
+        assert np.array_equal(ak[_get(lib, h, "coarse_id", 0, np.int32)], o.level_keys(c))
+        for l in range(c + 1, J + 1):
+            lk, lkc = o.level_keys(l), o.level_keys(l - 1)
+            pos = {int(k): i for i, k in enumerate(lk)}
+            sm = _get(lib, h, "smooth", l, np.int32)
+            assert np.array_equal(np.sort(ak[sm]), lk), ("smooth", l)
+            # the level operator rediscretised from the shim's kept triangles
+            tk = _get(lib, h, "tri_key", l, np.uint64)
+            tid = _get(lib, h, "tri_id", l, np.int32).reshape(-1, 3)
+            tc = _get(lib, h, "tri_coef", l, np.float64)
+            P = np.stack([amin[a] + np.ldexp(v.astype(np.float64), -31) * L
+                          for a, v in enumerate(_deinterleave(tk, 2, 32))], -1)
+            K = _stiffness(P.reshape(-1, 3, 2), tc)
+            n = lk.size
+            Ah = np.zeros((n, n))
+            for t in range(len(tc)):
+                for i in range(3):
+                    for j in range(3):
+                        if tid[t, i] >= 0 and tid[t, j] >= 0:
+                            Ah[pos[int(ak[tid[t, i]])], pos[int(ak[tid[t, j]])]] += K[t, i, j]
+            Ao = o.A(l).toarray()
+            assert np.abs(Ah - Ao).max() <= 1e-12 * np.abs(Ao).max(), ("A level", l)
+            # interpolation: nodes free on both levels carry over, new ones take
+            # the midpoint of their free parents
+            I = o.I(l).tocsr()
+            nid = _get(lib, h, "new_id", l, np.int32)
+            p0 = _get(lib, h, "new_p0", l, np.int32)
+            p1 = _get(lib, h, "new_p1", l, np.int32)
+            assert set(int(ak[q]) for q in nid) == set(int(k) for k in lk) - set(int(k) for k in lkc)
+            for a_, b_, c2 in zip(nid, p0, p1):
+                row = I[pos[int(ak[a_])]]
+                w = {int(lkc[j]): v for j, v in zip(row.indices, row.data) if v != 0}
+                g = {}
+                for q in (b_, c2):
+                    if q >= 0:
+                        g[int(ak[q])] = g.get(int(ak[q]), 0.0) + 0.5
+                assert w.keys() == g.keys() and all(abs(w[k] - g[k]) < 1e-15 for k in w), ("I", l)
+            cpos = {int(k): i for i, k in enumerate(lkc)}
+            for k in set(int(k) for k in lk) & set(cpos):
+                row = I[pos[k]]
+                assert {int(lkc[j]): v for j, v in zip(row.indices, row.data) if v != 0} == {k: 1.0}
+            # the near-boundary set J_{l,j}
+            nb = _get(lib, h, "nb_id", l, np.int32)
+            want = o.near_boundary_set(l)
+            assert sorted(pos[int(ak[q])] for q in nb) == want.tolist(), ("J_lj", l)
+        # Scott-Zhang rows, columns mapped to the oracle's free nodes of level J
+        lkJ = {int(k): i for i, k in enumerate(o.level_keys(J))}
+        Pr = _get(lib, h, "P_r", 0, np.int32)
+        Pc = np.array([lkJ[int(ak[q])] for q in _get(lib, h, "P_c", 0, np.int32)], dtype=np.int64)
+        Pv = _get(lib, h, "P_v", 0, np.float64)
+        Ph = sp.csr_matrix((Pv, (Pr, Pc)), shape=(o.nfree, len(lkJ)))
+        assert abs(Ph - o.P()).max() <= 1e-11
+    finally:
+        lib.shim_free(h)
+
+
+@pytest.mark.parametrize("name", ["square17_right", "L17_cut_c8", "hole17_left_lognormal", "L33_cut_nb0",
+                                  "graded33_two_sides_nb3"])
+def test_host_setup_mixed_grids_match_oracle(shim, gen, name):
+    m, params = _mixed_cases(gen)[name]
+    o = oracle.Oracle(m, **params)
+    _compare_mixed(shim, m, o, params)

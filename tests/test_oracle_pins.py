@@ -1182,10 +1182,13 @@ def test_near_boundary_sets_are_graph_balls_around_the_boundary(gen, layers):
         assert len(want) > 0 and (l < o.J or len(want) < keys.size)
 
 
-def test_mixed_interpolation_is_the_coarse_function_at_fine_nodes(gen):
+@pytest.mark.parametrize("shape,where", [("hole", "outer"), ("L", "inner")])
+def test_mixed_interpolation_is_the_coarse_function_at_fine_nodes(gen, shape, where):
     # I_l e = the coarse P1 function (zero at Dirichlet nodes and outside the
     # kept coarse triangles) evaluated at the fine free nodes, by point location
-    m = _mixed_domain(gen, 17, "hole", "outer")
+    # over every kept coarse triangle (on the L with a Neumann cut, fine nodes
+    # on box edges lie between kept and removed coarse triangles)
+    m = _mixed_domain(gen, 17, shape, where)
     o = oracle.Oracle(m, coarse_max=8)
     rng = np.random.default_rng(7)
     for l in range(o.c + 1, o.J + 1):
