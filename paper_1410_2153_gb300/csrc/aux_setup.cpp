@@ -14,6 +14,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <thread>
 
 #include "clip.h"
@@ -886,6 +887,20 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   // sorted, unique), then over its relevant boxes (triangles concatenated in
   // order)
   out.levels.assign(std::max(0, J - c), AuxLevelHost());
+  // local smoothing: the smoothing nodes (by aux ID) and the relevant boxes
+  // (by index within their depth) of one level are marked in flag arrays and
+  // gathered in ascending order, then the flags are cleared for the next level
+  const bool local = prm.smoothing != 1 && !mixed;
+  std::unique_ptr<std::atomic<uint8_t>[]> sflag;
+  std::vector<std::unique_ptr<std::atomic<uint8_t>[]>> rflag(J + 1);
+  if (local) {
+    sflag.reset(new std::atomic<uint8_t>[AK.size() + 1]);
+    for (size_t q = 0; q <= AK.size(); ++q) sflag[q].store(0, std::memory_order_relaxed);
+    for (int dd = 0; dd <= J; ++dd) {
+      rflag[dd].reset(new std::atomic<uint8_t>[BX[dd].size() + 1]);
+      for (size_t q = 0; q <= BX[dd].size(); ++q) rflag[dd][q].store(0, std::memory_order_relaxed);
+    }
+  }
   for (int l = c + 1; l <= J; ++l) {
     AuxLevelHost& L = out.levels[l - (c + 1)];
     L.level = l;
@@ -894,9 +909,10 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     std::vector<uint64_t> changed = info[l].fanned;  // plus the split boxes
     changed.insert(changed.end(), T.S[d].begin(), T.S[d].end());
     sort_unique(changed);
-    std::vector<uint64_t> sm;
+    std::vector<uint64_t> sm;     // whole level: smoothing nodes by key
+    std::vector<int32_t> smid;    // local: smoothing nodes by aux ID, ascending
     std::vector<std::pair<int, uint64_t>> rel;
-    if (prm.smoothing == 1 || mixed) {
+    if (!local) {
       // every node of the level, every box shown at the level (always for
       // the mixed grids, which are not nested)
       for (int dd = 0; dd <= l; ++dd)
@@ -921,11 +937,14 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       // N~_l: the corners and centres of the changed boxes, and the edge
       // midpoints of the split ones; relevant boxes: the changed boxes and the
       // level-l leaves around them
-      std::vector<std::vector<uint64_t>> spart(MAX_THREADS);
-      std::vector<std::vector<std::pair<int, uint64_t>>> rpart(MAX_THREADS);
-      parallel_for((int64_t)changed.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
-        auto& M = spart[t];
-        auto& R = rpart[t];
+      auto mark_node = [&](int32_t id) {
+        if (id >= 0) sflag[id].store(1, std::memory_order_relaxed);
+      };
+      auto mark_box = [&](int dd, uint64_t pp) {
+        const auto& bx = BX[dd];
+        rflag[dd][std::lower_bound(bx.begin(), bx.end(), pp) - bx.begin()].store(1, std::memory_order_relaxed);
+      };
+      parallel_for((int64_t)changed.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
         std::vector<std::array<uint64_t, 3>> kt;
         for (int64_t q = b0; q < b1; ++q) {
           const uint64_t p = changed[q];
@@ -937,7 +956,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
                 bool mid = (ix == 1) || (iy == 1);
                 if (mid && !sp && !(ix == 1 && iy == 1)) continue;  // fanned leaf: corners and centre
                 uint64_t k = mort(x0 + ix * m, y0 + iy * m);
-                if (!boundary_key(T, k)) M.push_back(k);
+                if (!boundary_key(T, k)) mark_node(AKI.find(k));
               }
           } else {
             // free vertices of the box's new triangles that lie inside Omega
@@ -948,7 +967,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
               for (size_t k = 0; k < kt.size(); ++k) {
                 if (!tri_inside(dd, pp, diag, (int)k, kt[k])) continue;
                 for (int v = 0; v < 3; ++v)
-                  if (level_id(kt[k][v], l) >= 0) M.push_back(kt[k][v]);
+                  mark_node(level_id(kt[k][v], l));
               }
             };
             bool h[4] = {false, false, false, false};
@@ -960,9 +979,9 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
             }
           }
           if (sp) {
-            for (uint64_t ch = 0; ch < 4; ++ch) R.push_back({d + 1, (p << 2) | ch});
+            for (uint64_t ch = 0; ch < 4; ++ch) mark_box(d + 1, (p << 2) | ch);
           } else {
-            R.push_back({d, p});
+            mark_box(d, p);
           }
           const int64_t x = (int64_t)compact(p), y = (int64_t)compact(p >> 1), nb = 1LL << d;
           for (int dy = -1; dy <= 1; ++dy)
@@ -976,22 +995,48 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
                 nq >>= 2;
               }
               if (dd == d && T.split(d, nq)) {
-                for (uint64_t ch = 0; ch < 4; ++ch) R.push_back({d + 1, (nq << 2) | ch});
+                for (uint64_t ch = 0; ch < 4; ++ch) mark_box(d + 1, (nq << 2) | ch);
               } else {
-                R.push_back({dd, nq});
+                mark_box(dd, nq);
               }
             }
         }
       });
-      sm = merge_unique(spart);
-      rel = merge_unique(rpart);
+      // gather (contiguous ranges per thread, concatenated in order) and clear
+      {
+        std::vector<std::vector<int32_t>> sp(MAX_THREADS);
+        parallel_for((int64_t)AK.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+          for (int64_t q = b0; q < b1; ++q)
+            if (sflag[q].load(std::memory_order_relaxed)) {
+              sp[t].push_back((int32_t)q);
+              sflag[q].store(0, std::memory_order_relaxed);
+            }
+        });
+        for (auto& v : sp) smid.insert(smid.end(), v.begin(), v.end());
+      }
+      for (int dd = 0; dd <= d + 1; ++dd) {
+        const auto& bx = BX[dd];
+        std::vector<std::vector<std::pair<int, uint64_t>>> rp(MAX_THREADS);
+        parallel_for((int64_t)bx.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
+          for (int64_t q = b0; q < b1; ++q)
+            if (rflag[dd][q].load(std::memory_order_relaxed)) {
+              rp[t].push_back({dd, bx[q]});
+              rflag[dd][q].store(0, std::memory_order_relaxed);
+            }
+        });
+        for (auto& v : rp) rel.insert(rel.end(), v.begin(), v.end());
+      }
     }
-    L.smooth.resize(sm.size());
-    parallel_for((int64_t)sm.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
-      for (int64_t q = b0; q < b1; ++q) L.smooth[q] = AKI.find(sm[q]);
-    });
-    std::sort(rel.begin(), rel.end());  // (already unique in the default mode)
-    rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+    if (local) {
+      L.smooth.swap(smid);
+    } else {
+      L.smooth.resize(sm.size());
+      parallel_for((int64_t)sm.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
+        for (int64_t q = b0; q < b1; ++q) L.smooth[q] = AKI.find(sm[q]);
+      });
+      std::sort(rel.begin(), rel.end());
+      rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+    }
     std::vector<std::vector<int32_t>> ids(MAX_THREADS);
     std::vector<std::vector<uint64_t>> keys(MAX_THREADS);
     std::vector<std::vector<double>> coefs(MAX_THREADS);
@@ -999,10 +1044,26 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
       std::vector<std::array<uint64_t, 3>> kt;  // scratch of this thread
       for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t], kt);
     });
-    for (unsigned t = 0; t < MAX_THREADS; ++t) {
-      L.tri_id.insert(L.tri_id.end(), ids[t].begin(), ids[t].end());
-      L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
-      L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
+    // concatenate in thread order: sizes first, then one copy per part in parallel
+    {
+      std::vector<size_t> o3(MAX_THREADS + 1, 0), o1(MAX_THREADS + 1, 0);
+      for (unsigned t = 0; t < MAX_THREADS; ++t) {
+        o3[t + 1] = o3[t] + ids[t].size();
+        o1[t + 1] = o1[t] + coefs[t].size();
+      }
+      L.tri_id.resize(o3[MAX_THREADS]);
+      L.tri_key.resize(o3[MAX_THREADS]);
+      L.tri_coef.resize(o1[MAX_THREADS]);
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < MAX_THREADS; ++t) {
+        if (coefs[t].empty() && ids[t].empty()) continue;
+        th.emplace_back([&, t] {
+          std::copy(ids[t].begin(), ids[t].end(), L.tri_id.begin() + o3[t]);
+          std::copy(keys[t].begin(), keys[t].end(), L.tri_key.begin() + o3[t]);
+          std::copy(coefs[t].begin(), coefs[t].end(), L.tri_coef.begin() + o1[t]);
+        });
+      }
+      for (auto& x : th) x.join();
     }
     if (mixed && mesh.nb_layers >= 0) {
       // Algorithm 3: J_{l,j} = the free nodes of the j-th layer of triangles
