@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <thread>
 #include <unordered_map>
 
@@ -603,14 +604,37 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     // leaves that see two values are clipped.  The elements whose bounding
     // boxes meet a leaf include every element that overlaps it.  Per leaf:
     // the bits of the first value seen (0: none yet) and a "mixed" flag.
-    std::vector<std::atomic<uint64_t>> lval(nleaf);
+    // A leaf that sees two values keeps the smallest bit pattern seen, a0
+    // (deterministic for any thread count): since the elements tile it,
+    // int_K a = a0 |K| + sum_e (a_e - a0) |e n K|, and only its elements with
+    // a_e != a0 are clipped.
+    std::vector<std::atomic<uint64_t>> lval(nleaf), lmin(nleaf);
     std::vector<std::atomic<uint8_t>> lmixed(nleaf);
     for (int64_t q = 0; q < nleaf; ++q) {
       lval[q].store(0, std::memory_order_relaxed);
+      lmin[q].store(~0ULL, std::memory_order_relaxed);
       lmixed[q].store(0, std::memory_order_relaxed);
     }
-    if (skip_const) pfor(mesh.ne, [&](unsigned, int64_t b0, int64_t b1) {
+    // The leaves each element meets are kept from this pass for the clipping
+    // pass (CSR over the elements, in the order leaves_in gives them), with
+    // every leaf's first finest tetrahedron and count.
+    std::vector<int64_t> eoff, lf0(nleaf, 0);
+    std::vector<int32_t> eleaf, lnq(nleaf, 0);
+    std::vector<std::vector<int32_t>> tl(64);
+    std::vector<int64_t> tb0(64, -1);
+    std::vector<uint32_t> ecnt;
+    if (skip_const) {
+      for (int d = 0; d <= J; ++d)
+        for (size_t i = 0; i < BX[d].size(); ++i)
+          if (lid[d][i] >= 0) {
+            lf0[lid[d][i]] = first[d][i];
+            lnq[lid[d][i]] = nft[d][i];
+          }
+      ecnt.assign(mesh.ne, 0);
+    }
+    if (skip_const) pfor(mesh.ne, [&](unsigned t, int64_t b0, int64_t b1) {
       std::vector<std::pair<int, uint64_t>> lv, st;
+      tb0[t] = b0;
       for (int64_t e = b0; e < b1; ++e) {
         TetP S;
         fine_tet(e, S);
@@ -620,17 +644,35 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         leaves_in(T, lo, hi, lv, st);
         uint64_t bits;
         std::memcpy(&bits, &mesh.coeff[e], 8);
+        ecnt[e] = (uint32_t)lv.size();
         for (auto& lf : lv) {
           int64_t f0;
           int nq;
           int32_t leaf;
           leaf_range(lf, f0, nq, &leaf);
+          tl[t].push_back(leaf);
           uint64_t expect = 0;
           if (!lval[leaf].compare_exchange_strong(expect, bits, std::memory_order_relaxed) && expect != bits)
             lmixed[leaf].store(1, std::memory_order_relaxed);
+          uint64_t cur = lmin[leaf].load(std::memory_order_relaxed);
+          while (bits < cur && !lmin[leaf].compare_exchange_weak(cur, bits, std::memory_order_relaxed)) {
+          }
         }
       }
     });
+    if (skip_const) {
+      eoff.assign(mesh.ne + 1, 0);
+      for (int64_t e = 0; e < mesh.ne; ++e) eoff[e + 1] = eoff[e] + ecnt[e];
+      eleaf.resize(eoff[mesh.ne]);
+      std::vector<std::thread> th;
+      for (int t = 0; t < 64; ++t) {
+        if (tb0[t] < 0 || tl[t].empty()) continue;
+        th.emplace_back([&, t] { std::copy(tl[t].begin(), tl[t].end(), eleaf.begin() + eoff[tb0[t]]); });
+      }
+      for (auto& x : th) x.join();
+      std::vector<std::vector<int32_t>>().swap(tl);
+      std::vector<uint32_t>().swap(ecnt);
+    }
     std::vector<std::vector<std::pair<int64_t, double>>> csum(nch), ccov(nch);
     std::atomic<int64_t> nextc(0);
     auto work = [&]() {
@@ -645,25 +687,44 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           const int64_t e = order[k].second;
           TetP S;
           fine_tet(e, S);
-          int64_t lo[3], hi[3];
-          window(S, lo, hi);
-          lv.clear();
-          leaves_in(T, lo, hi, lv, st);
-          for (auto& lf : lv) {
+          int64_t nl;
+          if (skip_const) {
+            nl = eoff[e + 1] - eoff[e];
+          } else {
+            int64_t lo[3], hi[3];
+            window(S, lo, hi);
+            lv.clear();
+            leaves_in(T, lo, hi, lv, st);
+            nl = (int64_t)lv.size();
+          }
+          for (int64_t r = 0; r < nl; ++r) {
             int64_t f0;
             int nq;
             int32_t leaf;
-            leaf_range(lf, f0, nq, &leaf);
-            if (skip_const && !lmixed[leaf].load(std::memory_order_relaxed) &&
-                lval[leaf].load(std::memory_order_relaxed) != 0)
-              continue;
+            if (skip_const) {
+              leaf = eleaf[eoff[e] + r];
+              f0 = lf0[leaf];
+              nq = lnq[leaf];
+            } else {
+              leaf_range(lv[r], f0, nq, &leaf);
+            }
+            double a0 = 0;  // mixed leaf: the part a0 |K| is added after the sums
+            if (skip_const) {
+              if (!lmixed[leaf].load(std::memory_order_relaxed) && lval[leaf].load(std::memory_order_relaxed) != 0)
+                continue;
+              const uint64_t mb = lmin[leaf].load(std::memory_order_relaxed);
+              uint64_t bits;
+              std::memcpy(&bits, &mesh.coeff[e], 8);
+              if (bits == mb) continue;
+              std::memcpy(&a0, &mb, 8);
+            }
             for (int q = 0; q < nq; ++q) {
               TetP K;
               leaf_tet(f0 + q, K);
               double vol = 0;
               clip::clip_tets(tet4(S), tet4(K), [&](const clip::Tet4& pc) { vol += clip::volume(pc); });
               if (!(vol > 0)) continue;
-              if (varcoef) acc.push_back({f0 + q, vol * mesh.coeff[e]});
+              if (varcoef) acc.push_back({f0 + q, vol * (mesh.coeff[e] - a0)});
               if (dgrid) cac.push_back({f0 + q, vol});
             }
           }
@@ -700,14 +761,16 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (int d = 0; d <= J; ++d)
       for (size_t i = 0; i < BX[d].size(); ++i) {
         const int32_t leaf = lid[d][i];
-        if (leaf < 0 || lmixed[leaf].load() || lval[leaf].load() == 0) continue;
-        const uint64_t bits = lval[leaf].load();
+        if (leaf < 0 || lval[leaf].load() == 0) continue;
+        const bool mixedleaf = lmixed[leaf].load() != 0;
+        const uint64_t bits = mixedleaf ? lmin[leaf].load() : lval[leaf].load();
         double a;
         std::memcpy(&a, &bits, 8);
         for (int q = 0; q < nft[d][i]; ++q) {
           TetP K;
           leaf_tet(first[d][i] + q, K);
-          I[first[d][i] + q] = a * (std::fabs(vol6(K[0], K[1], K[2], K[3])) / 6.0);
+          const double part = a * (std::fabs(vol6(K[0], K[1], K[2], K[3])) / 6.0);
+          I[first[d][i] + q] = mixedleaf ? I[first[d][i] + q] + part : part;
         }
       }
     // bottom-up Kuhn integrals: a (kint, fanint) and the covered volume
@@ -915,6 +978,20 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   // tetrahedra per chunk of relevant boxes, concatenated in order
   out.levels.assign(std::max(0, J - c), AuxLevelHost());
   unsigned nthr = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  // local smoothing: smoothing nodes (by aux ID) and relevant boxes (by index
+  // within their depth) of one level are marked in flag arrays and gathered
+  // in ascending order; the flags are cleared for the next level
+  const bool local = prm.smoothing != 1;
+  std::unique_ptr<std::atomic<uint8_t>[]> sflag;
+  std::vector<std::unique_ptr<std::atomic<uint8_t>[]>> rflag(J + 1);
+  if (local) {
+    sflag.reset(new std::atomic<uint8_t>[AK.size() + 1]);
+    for (size_t q = 0; q <= AK.size(); ++q) sflag[q].store(0, std::memory_order_relaxed);
+    for (int dd = 0; dd <= J; ++dd) {
+      rflag[dd].reset(new std::atomic<uint8_t>[BX[dd].size() + 1]);
+      for (size_t q = 0; q <= BX[dd].size(); ++q) rflag[dd][q].store(0, std::memory_order_relaxed);
+    }
+  }
   for (int l = c + 1; l <= J; ++l) {
     AuxLevelHost& L = out.levels[l - (c + 1)];
     L.level = l;
@@ -939,11 +1016,14 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       sm = uniq_parts(part);
     } else {
       const std::vector<uint64_t>& ch = changed[l];
-      std::vector<std::vector<std::pair<int, uint64_t>>> rpart(nthr);
-      std::vector<std::vector<uint64_t>> spart(nthr);
-      pfor((int64_t)ch.size(), [&](unsigned t, int64_t b0, int64_t b1) {
-        auto& R = rpart[t];
-        auto& M = spart[t];
+      auto mark_node = [&](int32_t id) {
+        if (id >= 0) sflag[id].store(1, std::memory_order_relaxed);
+      };
+      auto mark_box = [&](int dd, uint64_t pp) {
+        const auto& bx = BX[dd];
+        rflag[dd][std::lower_bound(bx.begin(), bx.end(), pp) - bx.begin()].store(1, std::memory_order_relaxed);
+      };
+      pfor((int64_t)ch.size(), [&](unsigned, int64_t b0, int64_t b1) {
         std::vector<Tet> kt;
         for (int64_t q = b0; q < b1; ++q) {
           const uint64_t p = ch[q];
@@ -954,17 +1034,16 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             box_tets(T, dd, pp, l, kt, &kuhn);
             for (size_t k = 0; k < kt.size(); ++k) {
               if (!tet_inside(dd, pp, kuhn, (int)k, kt[k])) continue;
-              for (int v = 0; v < 4; ++v)
-                if (level_id(kt[k][v], l) >= 0) M.push_back(kt[k][v]);
+              for (int v = 0; v < 4; ++v) mark_node(level_id(kt[k][v], l));
             }
           };
           if (T.split(d, p)) {
             for (uint64_t cc = 0; cc < 8; ++cc) {
-              R.push_back({d + 1, (p << 3) | cc});
+              mark_box(d + 1, (p << 3) | cc);
               add(d + 1, (p << 3) | cc);
             }
           } else {
-            R.push_back({d, p});
+            mark_box(d, p);
             add(d, p);
           }
           for (int oz = -1; oz <= 1; ++oz)
@@ -980,30 +1059,70 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
                   nq >>= 3;
                 }
                 if (dd == d && T.split(d, nq)) {
-                  for (uint64_t cc = 0; cc < 8; ++cc) R.push_back({d + 1, (nq << 3) | cc});
+                  for (uint64_t cc = 0; cc < 8; ++cc) mark_box(d + 1, (nq << 3) | cc);
                 } else {
-                  R.push_back({dd, nq});
+                  mark_box(dd, nq);
                 }
               }
         }
       });
-      rel = uniq_parts(rpart);
-      sm = uniq_parts(spart);
+      // gather (contiguous ranges per thread, concatenated in order) and clear
+      {
+        std::vector<std::vector<int32_t>> sp(nthr);
+        pfor((int64_t)AK.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+          for (int64_t q = b0; q < b1; ++q)
+            if (sflag[q].load(std::memory_order_relaxed)) {
+              sp[t].push_back((int32_t)q);
+              sflag[q].store(0, std::memory_order_relaxed);
+            }
+        });
+        for (auto& v : sp) L.smooth.insert(L.smooth.end(), v.begin(), v.end());
+      }
+      for (int dd = 0; dd <= d + 1; ++dd) {
+        const auto& bx = BX[dd];
+        std::vector<std::vector<std::pair<int, uint64_t>>> rp(nthr);
+        pfor((int64_t)bx.size(), [&](unsigned t, int64_t b0, int64_t b1) {
+          for (int64_t q = b0; q < b1; ++q)
+            if (rflag[dd][q].load(std::memory_order_relaxed)) {
+              rp[t].push_back({dd, bx[q]});
+              rflag[dd][q].store(0, std::memory_order_relaxed);
+            }
+        });
+        for (auto& v : rp) rel.insert(rel.end(), v.begin(), v.end());
+      }
     }
-    std::sort(rel.begin(), rel.end());
-    rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
-    uniq(sm);
-    for (uint64_t k : sm) L.smooth.push_back(AKI.find(k));
+    if (!local) {
+      std::sort(rel.begin(), rel.end());
+      rel.erase(std::unique(rel.begin(), rel.end()), rel.end());
+      uniq(sm);
+      for (uint64_t k : sm) L.smooth.push_back(AKI.find(k));
+    }
     std::vector<std::vector<int32_t>> ids(nthr);
     std::vector<std::vector<uint64_t>> keys(nthr);
     std::vector<std::vector<double>> coefs(nthr);
     pfor((int64_t)rel.size(), [&](unsigned t, int64_t b0, int64_t b1) {
       for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t]);
     });
-    for (unsigned t = 0; t < nthr; ++t) {
-      L.tri_id.insert(L.tri_id.end(), ids[t].begin(), ids[t].end());
-      L.tri_key.insert(L.tri_key.end(), keys[t].begin(), keys[t].end());
-      L.tri_coef.insert(L.tri_coef.end(), coefs[t].begin(), coefs[t].end());
+    // concatenate in thread order: sizes first, then one copy per part in parallel
+    {
+      std::vector<size_t> o4(nthr + 1, 0), o1(nthr + 1, 0);
+      for (unsigned t = 0; t < nthr; ++t) {
+        o4[t + 1] = o4[t] + ids[t].size();
+        o1[t + 1] = o1[t] + coefs[t].size();
+      }
+      L.tri_id.resize(o4[nthr]);
+      L.tri_key.resize(o4[nthr]);
+      L.tri_coef.resize(o1[nthr]);
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < nthr; ++t) {
+        if (ids[t].empty() && coefs[t].empty()) continue;
+        th.emplace_back([&, t] {
+          std::copy(ids[t].begin(), ids[t].end(), L.tri_id.begin() + o4[t]);
+          std::copy(keys[t].begin(), keys[t].end(), L.tri_key.begin() + o4[t]);
+          std::copy(coefs[t].begin(), coefs[t].end(), L.tri_coef.begin() + o1[t]);
+        });
+      }
+      for (auto& x : th) x.join();
     }
     if (!dgrid) {
       for (auto& v : newnodes[l]) {
