@@ -276,6 +276,18 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
   out.J = J;
   std::vector<std::vector<uint64_t>> BX(J + 1);  // boxes per depth, ascending prefix
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
+  // position of box p in BX[d] through a bucket index over the top key bits
+  // (the same position as a binary search over the whole depth)
+  std::vector<KeyIndex> BXI(J + 1);
+  for (int d = 0; d <= J; ++d) {
+    int bits = 1;
+    while (bits < 20 && ((size_t)1 << bits) < BX[d].size()) ++bits;
+    BXI[d].build(BX[d], bits);
+  }
+  auto box_at = [&](int d, uint64_t p) -> size_t {
+    const int32_t i = BXI[d].find(p);
+    return i >= 0 ? (size_t)i : (size_t)(std::lower_bound(BX[d].begin(), BX[d].end(), p) - BX[d].begin());
+  };
 
 
   T.index();
@@ -456,8 +468,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
         V2 Pl[3];
         for (int k = 0; k < 3; ++k) Pl[k] = V2{P[k].x - o.x, P[k].y - o.y};
         for (auto& lf : lv) {
-          const auto& bx = BX[lf.first];
-          const size_t bi = std::lower_bound(bx.begin(), bx.end(), lf.second) - bx.begin();
+          const size_t bi = box_at(lf.first, lf.second);
           const int64_t f0 = first[lf.first][bi];
           bool h[4];
           T.hanging(lf.first, lf.second, h);
@@ -524,8 +535,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
             }
           }
         } else {
-          const auto& ch = BX[d + 1];
-          size_t j = std::lower_bound(ch.begin(), ch.end(), p << 2) - ch.begin();
+          size_t j = box_at(d + 1, p << 2);
           // children: 0 SW, 1 SE, 2 NW, 3 NE (bit 0 = x, bit 1 = y)
           const auto& sw = H[d + 1][j];
           const auto& se = H[d + 1][j + 1];
@@ -557,8 +567,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
                        const std::vector<std::pair<std::array<uint64_t, 3>, double>>& FI, int d, uint64_t p, bool diag,
                        int k, const std::array<uint64_t, 3>& t) -> double {
     if (diag) {
-      const auto& bx = BX[d];
-      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      const size_t i = box_at(d, p);
       return H[d][i][k];
     }
     auto it = std::lower_bound(FI.begin(), FI.end(), std::pair<std::array<uint64_t, 3>, double>(tri_sorted(t), -HUGE_VAL));
@@ -838,8 +847,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     double area = 0.5 * ((pb[0] - pa[0]) * (pc[1] - pa[1]) - (pc[0] - pa[0]) * (pb[1] - pa[1]));
     double integral;
     if (diag) {
-      const auto& bx = BX[d];
-      size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      size_t i = box_at(d, p);
       integral = H[d][i][k];
     } else {
       auto key = tri_sorted(t);
@@ -941,8 +949,7 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
         if (id >= 0) sflag[id].store(1, std::memory_order_relaxed);
       };
       auto mark_box = [&](int dd, uint64_t pp) {
-        const auto& bx = BX[dd];
-        rflag[dd][std::lower_bound(bx.begin(), bx.end(), pp) - bx.begin()].store(1, std::memory_order_relaxed);
+        rflag[dd][box_at(dd, pp)].store(1, std::memory_order_relaxed);
       };
       parallel_for((int64_t)changed.size(), [&](unsigned, unsigned, int64_t b0, int64_t b1) {
         std::vector<std::array<uint64_t, 3>> kt;

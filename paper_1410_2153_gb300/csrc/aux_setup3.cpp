@@ -257,27 +257,35 @@ clip::Tet4 tet4(const TetP& t) {
   return r;
 }
 
-void leaves_in(const Tree3& T, const int64_t* lo, const int64_t* hi, std::vector<std::pair<int, uint64_t>>& out,
-               std::vector<std::pair<int, uint64_t>>& st) {
-  st.clear();
-  st.push_back({0, 0});
-  while (!st.empty()) {
-    auto b = st.back();
-    st.pop_back();
-    const int64_t s = 1LL << (T.LB - b.first);
-    uint64_t c[3];
-    um3(b.second, c);
-    bool meet = true;  // positive-volume overlap with the window
-    for (int k = 0; k < 3; ++k) {
-      const int64_t x0 = (int64_t)c[k] * s;
-      if (x0 >= hi[k] || x0 + s <= lo[k]) meet = false;
-    }
-    if (!meet) continue;
-    if (!T.split(b.first, b.second)) {
-      out.push_back(b);
+void leaves_in(const Tree3& T, const int64_t* lo, const int64_t* hi, std::vector<std::pair<int, uint64_t>>& out) {
+  // depth first; a split box pushes only the children that meet the window,
+  // in ascending child order, carrying each box's lattice corner (the depth
+  // is at most 20, so at most 7 * 20 + 8 entries are pending)
+  struct Ent {
+    int d;
+    uint64_t p;
+    int64_t x[3];
+  };
+  Ent st[168];
+  int top = 0;
+  auto meets = [&](int64_t x0, int64_t s, int k) { return !(x0 >= hi[k] || x0 + s <= lo[k]); };
+  {
+    const int64_t s = 1LL << T.LB;
+    if (!(meets(0, s, 0) && meets(0, s, 1) && meets(0, s, 2))) return;
+    st[top++] = Ent{0, 0, {0, 0, 0}};
+  }
+  while (top > 0) {
+    const Ent b = st[--top];
+    if (!T.split(b.d, b.p)) {
+      out.push_back({b.d, b.p});
       continue;
     }
-    for (uint64_t ch = 0; ch < 8; ++ch) st.push_back({b.first + 1, (b.second << 3) | ch});
+    const int64_t h = 1LL << (T.LB - b.d - 1);
+    for (uint64_t ch = 0; ch < 8; ++ch) {
+      const int64_t cx = b.x[0] + (int64_t)(ch & 1) * h, cy = b.x[1] + (int64_t)((ch >> 1) & 1) * h,
+                    cz = b.x[2] + (int64_t)((ch >> 2) & 1) * h;
+      if (meets(cx, h, 0) && meets(cy, h, 1) && meets(cz, h, 2)) st[top++] = Ent{b.d + 1, (b.p << 3) | ch, {cx, cy, cz}};
+    }
   }
 }
 
@@ -399,6 +407,18 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   T.index();
   std::vector<std::vector<uint64_t>> BX(J + 1);
   for (int d = 0; d <= J; ++d) BX[d] = boxes_at(T, d);
+  // position of box p in BX[d] through a bucket index over the top key bits
+  // (the same position as a binary search over the whole depth)
+  std::vector<KeyIndex> BXI(J + 1);
+  for (int d = 0; d <= J; ++d) {
+    int bits = 1;
+    while (bits < 20 && ((size_t)1 << bits) < BX[d].size()) ++bits;
+    BXI[d].build(BX[d], bits);
+  }
+  auto box_at = [&](int d, uint64_t p) -> size_t {
+    const int32_t i = BXI[d].find(p);
+    return i >= 0 ? (size_t)i : (size_t)(std::lower_bound(BX[d].begin(), BX[d].end(), p) - BX[d].begin());
+  };
 
   // finest-level free nodes: the non-boundary vertices of the leaves'
   // tetrahedra
@@ -555,8 +575,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, ftet[q][v], K[v].data());
   };
   auto leaf_range = [&](const std::pair<int, uint64_t>& lf, int64_t& f0, int& nq, int32_t* leaf = nullptr) {
-    const auto& bx = BX[lf.first];
-    const size_t bi = std::lower_bound(bx.begin(), bx.end(), lf.second) - bx.begin();
+    const size_t bi = box_at(lf.first, lf.second);
     f0 = first[lf.first][bi];
     nq = nft[lf.first][bi];
     if (leaf) *leaf = lid[lf.first][bi];
@@ -616,8 +635,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       lmixed[q].store(0, std::memory_order_relaxed);
     }
     // The leaves each element meets are kept from this pass for the clipping
-    // pass (CSR over the elements, in the order leaves_in gives them), with
-    // every leaf's first finest tetrahedron and count.
+    // pass (CSR over the elements in Morton order, each list in the order
+    // leaves_in gives it), with every leaf's first finest tetrahedron and
+    // count.  Morton order keeps the tree lookups of neighbouring elements
+    // close together.
     std::vector<int64_t> eoff, lf0(nleaf, 0);
     std::vector<int32_t> eleaf, lnq(nleaf, 0);
     std::vector<std::vector<int32_t>> tl(64);
@@ -633,18 +654,19 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       ecnt.assign(mesh.ne, 0);
     }
     if (skip_const) pfor(mesh.ne, [&](unsigned t, int64_t b0, int64_t b1) {
-      std::vector<std::pair<int, uint64_t>> lv, st;
+      std::vector<std::pair<int, uint64_t>> lv;
       tb0[t] = b0;
-      for (int64_t e = b0; e < b1; ++e) {
+      for (int64_t k = b0; k < b1; ++k) {
+        const int64_t e = order[k].second;
         TetP S;
         fine_tet(e, S);
         int64_t lo[3], hi[3];
         window(S, lo, hi);
         lv.clear();
-        leaves_in(T, lo, hi, lv, st);
+        leaves_in(T, lo, hi, lv);
         uint64_t bits;
         std::memcpy(&bits, &mesh.coeff[e], 8);
-        ecnt[e] = (uint32_t)lv.size();
+        ecnt[k] = (uint32_t)lv.size();
         for (auto& lf : lv) {
           int64_t f0;
           int nq;
@@ -676,7 +698,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     std::vector<std::vector<std::pair<int64_t, double>>> csum(nch), ccov(nch);
     std::atomic<int64_t> nextc(0);
     auto work = [&]() {
-      std::vector<std::pair<int, uint64_t>> lv, st;
+      std::vector<std::pair<int, uint64_t>> lv;
       std::vector<std::pair<int64_t, double>> acc, cac;
       for (;;) {
         const int64_t ch = nextc.fetch_add(1);
@@ -689,12 +711,12 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           fine_tet(e, S);
           int64_t nl;
           if (skip_const) {
-            nl = eoff[e + 1] - eoff[e];
+            nl = eoff[k + 1] - eoff[k];
           } else {
             int64_t lo[3], hi[3];
             window(S, lo, hi);
             lv.clear();
-            leaves_in(T, lo, hi, lv, st);
+            leaves_in(T, lo, hi, lv);
             nl = (int64_t)lv.size();
           }
           for (int64_t r = 0; r < nl; ++r) {
@@ -702,7 +724,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
             int nq;
             int32_t leaf;
             if (skip_const) {
-              leaf = eleaf[eoff[e] + r];
+              leaf = eleaf[eoff[k] + r];
               f0 = lf0[leaf];
               nq = lnq[leaf];
             } else {
@@ -810,7 +832,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
           }
         } else {
           const auto& ch = BX[d + 1];
-          const size_t j = std::lower_bound(ch.begin(), ch.end(), p << 3) - ch.begin();
+          const size_t j = box_at(d + 1, p << 3);
           for (int cidx = 0; cidx < 8; ++cidx) {
             const uint64_t cp = ch[j + cidx];
             std::vector<Tet> kt;
@@ -838,8 +860,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     if (!dgrid) return true;
     double cov;
     if (kuhn) {
-      const auto& bx = BX[d];
-      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      const size_t i = box_at(d, p);
       cov = kcov[d][i][q];
     } else {
       auto it = fancov.find(tet_hash(t));
@@ -940,8 +961,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
        dd = {P[3][0], P[3][1], P[3][2]};
     const double vol = std::fabs(vol6(a, b, cc, dd)) / 6.0;
     if (kuhn) {
-      const auto& bx = BX[d];
-      const size_t i = std::lower_bound(bx.begin(), bx.end(), p) - bx.begin();
+      const size_t i = box_at(d, p);
       return KI[d][i][q] / vol;
     }
     return FI.at(tet_hash(t)) / vol;
@@ -1020,8 +1040,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         if (id >= 0) sflag[id].store(1, std::memory_order_relaxed);
       };
       auto mark_box = [&](int dd, uint64_t pp) {
-        const auto& bx = BX[dd];
-        rflag[dd][std::lower_bound(bx.begin(), bx.end(), pp) - bx.begin()].store(1, std::memory_order_relaxed);
+        rflag[dd][box_at(dd, pp)].store(1, std::memory_order_relaxed);
       };
       pfor((int64_t)ch.size(), [&](unsigned, int64_t b0, int64_t b1) {
         std::vector<Tet> kt;
