@@ -35,7 +35,7 @@ def test_stiffness_is_five_point_laplacian_on_right_triangles(gen):
     o = oracle.Oracle(m, stage=0)
     A = o.A().toarray()
     m1 = n - 2
-    T = sp.diags([-1, 2, -1], [-1, 0, 1], shape=(m1, m1))
+    T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(m1, m1))
     L5 = (sp.kron(sp.eye(m1), T) + sp.kron(T, sp.eye(m1))).toarray()
     assert np.abs(A - L5).max() < 1e-13
 
@@ -393,7 +393,7 @@ def test_uniform_aux_levels_are_five_point(gen):
         rm = (y // step - 1) * n1 + (x // step - 1)
         Pm = np.zeros((n1 * n1, n1 * n1))
         Pm[rm.astype(np.int64), np.arange(n1 * n1)] = 1
-        T = sp.diags([-1, 2, -1], [-1, 0, 1], shape=(n1, n1))
+        T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(n1, n1))
         L5 = (sp.kron(sp.eye(n1), T) + sp.kron(T, sp.eye(n1))).toarray()
         assert np.abs(Pm @ A @ Pm.T - L5).max() < 1e-12
 
