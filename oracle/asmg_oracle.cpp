@@ -29,7 +29,7 @@
 //       iterated greedy recolouring; the same definition is implemented
 //       independently on the device, so no colouring is ever passed from one
 //       side to the other
-//   R18 mixed Dirichlet/Neumann boundaries (2D): contact of a triangle with
+//   R18 mixed Dirichlet/Neumann boundaries (2D and 3D): contact of a simplex with
 //       Omega or Gamma_D means contact of its interior; Dirichlet auxiliary
 //       nodes lie on Gamma_D or on a triangle removed for Gamma_D
 //   R19 near-boundary correction: after the coarse correction of every level
@@ -1853,6 +1853,341 @@ void dirichlet_tets(Oracle& o, std::vector<std::vector<std::array<uint64_t, 4>>>
   }
 }
 
+// R18 in 3D.  Gamma_D is the union of the fine boundary faces (faces of one
+// element) whose three vertices are Dirichlet.  T^M_l keeps the tetrahedra of
+// sigma^(l) whose interior meets Omega (positive covered volume) and no Gamma_D
+// triangle; the Dirichlet nodes are the kept-tetrahedron nodes on Gamma_D or on
+// a tetrahedron removed for Gamma_D.  Each level is its own P1 discretisation
+// with the mean of a over tau n Omega; nodal interpolation between levels; the
+// near-boundary sets J_{l,j} of Algorithm 3 are built from the faces of one
+// kept tetrahedron only.
+
+P3 sub3(const P3& a, const P3& b) { return P3{a[0] - b[0], a[1] - b[1], a[2] - b[2]}; }
+P3 cross3(const P3& a, const P3& b) {
+  return P3{a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+}
+double dot3(const P3& a, const P3& b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// The closed triangle T meets the interior of the tetrahedron K exactly when
+// no separating direction exists with touching allowed; the candidate
+// directions are K's face normals, T's normal and the cross products of an
+// edge of K with an edge of T (the facet normals of K - T).  Projections are
+// computed in FP64, so an overlap below 1e-12 |a| L along direction a (L the
+// root box side) counts as touching: a lattice node on the edge of a jittered
+// Gamma_D triangle touches it, and rounding must not turn that into a cut.
+bool tri_meets_open_tet(const P3* T, const P3* K, double L) {
+  std::vector<P3> axes;
+  const int fv[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  for (auto& f : fv) axes.push_back(cross3(sub3(K[f[1]], K[f[0]]), sub3(K[f[2]], K[f[0]])));
+  axes.push_back(cross3(sub3(T[1], T[0]), sub3(T[2], T[0])));
+  const int ke[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  for (auto& e : ke)
+    for (int t = 0; t < 3; ++t) axes.push_back(cross3(sub3(K[e[1]], K[e[0]]), sub3(T[(t + 1) % 3], T[t])));
+  for (auto& a : axes) {
+    if (a[0] == 0 && a[1] == 0 && a[2] == 0) continue;
+    const double tol = 1e-12 * std::sqrt(dot3(a, a)) * L;
+    double kmin = INFINITY, kmax = -INFINITY, tmin = INFINITY, tmax = -INFINITY;
+    for (int v = 0; v < 4; ++v) {
+      const double d = dot3(a, K[v]);
+      kmin = std::min(kmin, d);
+      kmax = std::max(kmax, d);
+    }
+    for (int v = 0; v < 3; ++v) {
+      const double d = dot3(a, T[v]);
+      tmin = std::min(tmin, d);
+      tmax = std::max(tmax, d);
+    }
+    if (tmax <= kmin + tol || tmin >= kmax - tol) return false;
+  }
+  return true;
+}
+
+// The point p lies in the closed triangle T (coplanar, then inside in the
+// projection that drops the largest normal component), both within the same
+// relative 1e-12 as above.
+bool point_in_tri3(const P3* T, const P3& p, double L) {
+  const P3 n = cross3(sub3(T[1], T[0]), sub3(T[2], T[0]));
+  const double nn = std::sqrt(dot3(n, n));
+  if (std::fabs(dot3(n, sub3(p, T[0]))) > 1e-12 * nn * L) return false;
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (std::fabs(n[k]) > std::fabs(n[ax])) ax = k;
+  const int u = (ax + 1) % 3, v = (ax + 2) % 3;
+  auto o2 = [&](const P3& a, const P3& b, const P3& c) {
+    return (b[u] - a[u]) * (c[v] - a[v]) - (b[v] - a[v]) * (c[u] - a[u]);
+  };
+  const double tol = 1e-12 * nn * L;
+  const double s0 = o2(T[0], T[1], p), s1 = o2(T[1], T[2], p), s2 = o2(T[2], T[0], p);
+  return (s0 >= -tol && s1 >= -tol && s2 >= -tol) || (s0 <= tol && s1 <= tol && s2 <= tol);
+}
+
+void build_aux_mixed3(Oracle& o) {
+  const int J = o.J;
+  o.lv.assign(J + 1, Level());
+  std::vector<std::array<uint64_t, 4>> tJ;
+  level_tets(o, J, tJ);
+  std::map<std::array<uint64_t, 4>, int64_t> idx;
+  for (size_t t = 0; t < tJ.size(); ++t) idx[tJ[t]] = (int64_t)t;
+  // covered volume and integral of a over tau n Omega (exact intersection)
+  std::vector<double> cov(tJ.size(), 0.0), num(tJ.size(), 0.0);
+  std::vector<std::array<uint64_t, 4>> leaves, kt;
+  for (int64_t e = 0; e < o.ne; ++e) {
+    P3 T[4];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < 4; ++v)
+      for (int k = 0; k < 3; ++k) {
+        T[v][k] = o.X[(int64_t)o.E[4 * e + v] * 3 + k];
+        lo[k] = std::min(lo[k], T[v][k]);
+        hi[k] = std::max(hi[k], T[v][k]);
+      }
+    leaves.clear();
+    leaves_overlapping3(o, lo, hi, leaves);
+    const double a = o.coeff.empty() ? 1.0 : o.coeff[e];
+    for (auto& b : leaves) {
+      kt.clear();
+      uint64_t q[3] = {b[1], b[2], b[3]};
+      box_tets(o, (int)b[0], q, J, kt);
+      for (auto& k4 : kt) {
+        P3 K[4];
+        tet_points(o, k4, K);
+        std::vector<SignedTet> P = intersect_tets(T, K);
+        if (P.empty()) continue;
+        const double vol = pieces_integral(P, [](const P3&) { return 1.0; }, [](const P3&) { return 1.0; });
+        cov[idx.at(k4)] += vol;
+        num[idx.at(k4)] += a * vol;
+      }
+    }
+  }
+  // Gamma_D: faces of one element whose three vertices are Dirichlet
+  std::map<std::array<int32_t, 3>, int> fcount;
+  for (int64_t e = 0; e < o.ne; ++e)
+    for (int k = 0; k < 4; ++k) {
+      std::array<int32_t, 3> f = {o.E[4 * e + (k + 1) % 4], o.E[4 * e + (k + 2) % 4], o.E[4 * e + (k + 3) % 4]};
+      std::sort(f.begin(), f.end());
+      fcount[f] += 1;
+    }
+  std::vector<std::array<P3, 3>> gamma_d;
+  for (auto& kv : fcount) {
+    if (kv.second != 1) continue;
+    bool dir = true;
+    for (int k = 0; k < 3; ++k) dir = dir && o.bflag[kv.first[k]] == 1;
+    if (!dir) continue;
+    std::array<P3, 3> tr;
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) tr[k][d] = o.X[(int64_t)kv.first[k] * 3 + d];
+    gamma_d.push_back(tr);
+  }
+  auto vol_of = [&](const std::array<uint64_t, 4>& t) {
+    P3 K[4];
+    tet_points(o, t, K);
+    return std::fabs(tet_volume(K[0], K[1], K[2], K[3]));
+  };
+  std::vector<std::vector<double>> coef(J + 1);
+  for (int l = 0; l <= J; ++l) {
+    std::vector<std::array<uint64_t, 4>> tl;
+    level_tets(o, l, tl);
+    std::map<std::array<uint64_t, 4>, double> cl, nl;
+    for (size_t t = 0; t < tJ.size(); ++t) {
+      std::array<uint64_t, 4> anc = tJ[t];
+      if (l < J) {
+        uint64_t X4[3] = {0, 0, 0};
+        for (int v = 0; v < 4; ++v) {
+          uint64_t q[3];
+          xyz3(tJ[t][v], q);
+          for (int d = 0; d < 3; ++d) X4[d] += q[d];
+        }
+        if (!locate_level_tet(o, l, X4, anc)) {
+          o.err = "oracle: nested tetrahedron not located";
+          return;
+        }
+      }
+      cl[anc] += cov[t];
+      nl[anc] += num[t];
+    }
+    Level& L = o.lv[l];
+    std::set<uint64_t> dirn;
+    for (auto& t : tl) {
+      P3 K[4];
+      tet_points(o, t, K);
+      double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int v = 0; v < 4; ++v)
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::min(lo[d], K[v][d]);
+          hi[d] = std::max(hi[d], K[v][d]);
+        }
+      bool hit = false;
+      for (auto& g : gamma_d) {
+        bool apart = false;
+        for (int d = 0; d < 3; ++d)
+          apart = apart || std::max({g[0][d], g[1][d], g[2][d]}) < lo[d] || std::min({g[0][d], g[1][d], g[2][d]}) > hi[d];
+        if (!apart && tri_meets_open_tet(g.data(), K, o.L)) {
+          hit = true;
+          break;
+        }
+      }
+      if (hit) {
+        for (int v = 0; v < 4; ++v) dirn.insert(t[v]);
+        continue;
+      }
+      if (!(cl[t] > 1e-12 * vol_of(t))) continue;  // outside Omega
+      L.tet.push_back(t);
+      coef[l].push_back(nl[t] / cl[t]);
+    }
+    for (auto& t : L.tet)
+      for (int k = 0; k < 4; ++k) L.allkey.push_back(t[k]);
+    std::sort(L.allkey.begin(), L.allkey.end());
+    L.allkey.erase(std::unique(L.allkey.begin(), L.allkey.end()), L.allkey.end());
+    for (auto k : L.allkey) {
+      if (dirn.count(k)) continue;
+      double pp[3];
+      physical3(o, k, pp);
+      const P3 p = {pp[0], pp[1], pp[2]};
+      bool ond = false;
+      for (auto& g : gamma_d) ond = ond || point_in_tri3(g.data(), p, o.L);
+      if (!ond) L.key.push_back(k);
+    }
+  }
+  o.c = 0;
+  for (int l = 0; l <= J; ++l)
+    if ((int64_t)o.lv[l].key.size() <= o.prm.coarse_max) o.c = l;
+  o.finest_coef = coef[J];
+  for (int l = o.c; l <= J; ++l) {
+    Level& L = o.lv[l];
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(L.key.size());
+    for (size_t t = 0; t < L.tet.size(); ++t) {
+      P3 K[4];
+      tet_points(o, L.tet[t], K);
+      int32_t id[4];
+      for (int k = 0; k < 4; ++k) id[k] = find_index(L.key, L.tet[t][k]);
+      double Ke[4][4];
+      tet_stiffness(K, Ke);
+      for (int i = 0; i < 4; ++i)
+        if (id[i] >= 0)
+          for (int j = 0; j < 4; ++j)
+            if (id[j] >= 0) rows[id[i]].push_back({id[j], coef[l][t] * Ke[i][j]});
+    }
+    L.A = csr_from_rows(L.key.size(), L.key.size(), rows);
+  }
+  // nodal interpolation from level l-1: the coarse function on its kept
+  // tetrahedra (every box shown at level l-1 whose closed cube holds the
+  // point is searched), zero outside them and at its Dirichlet nodes
+  for (int l = std::max(1, o.c + 1); l <= J; ++l) {
+    Level& Lf = o.lv[l];
+    Level& Lc = o.lv[l - 1];
+    std::set<std::array<uint64_t, 4>> kept(Lc.tet.begin(), Lc.tet.end());
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(Lf.key.size());
+    for (size_t k = 0; k < Lf.key.size(); ++k) {
+      const int32_t j = find_index(Lc.key, Lf.key[k]);
+      if (j >= 0) {
+        rows[k].push_back({j, 1.0});
+        continue;
+      }
+      uint64_t x[3];
+      xyz3(Lf.key[k], x);
+      std::vector<std::array<uint64_t, 4>> hold, stack;  // (depth, qx, qy, qz)
+      stack.push_back({0, 0, 0, 0});
+      while (!stack.empty()) {
+        const auto b = stack.back();
+        stack.pop_back();
+        const int depth = (int)b[0];
+        const uint64_t sz = 1ULL << (o.LB - depth);
+        bool in = true;
+        for (int d = 0; d < 3; ++d) in = in && x[d] >= b[1 + d] * sz && x[d] <= (b[1 + d] + 1) * sz;
+        if (!in) continue;
+        uint64_t q[3] = {b[1], b[2], b[3]};
+        uint8_t sp = 0;
+        if (!box_exists(o, depth, q, &sp)) continue;
+        if (depth == l - 1 || !sp) {
+          hold.push_back(b);
+          continue;
+        }
+        for (uint64_t ch = 0; ch < 8; ++ch)
+          stack.push_back({(uint64_t)depth + 1, 2 * b[1] + (ch & 1), 2 * b[2] + ((ch >> 1) & 1), 2 * b[3] + (ch >> 2)});
+      }
+      bool found = false;
+      for (const auto& b : hold) {
+        if (found) break;
+        std::vector<std::array<uint64_t, 4>> ct;
+        uint64_t q[3] = {b[1], b[2], b[3]};
+        box_tets(o, (int)b[0], q, l - 1, ct);
+        for (auto& t : ct) {
+          if (!kept.count(t)) continue;
+          i128 P[4][3];
+          for (int v = 0; v < 4; ++v) {
+            uint64_t qq[3];
+            xyz3(t[v], qq);
+            for (int d = 0; d < 3; ++d) P[v][d] = (i128)qq[d];
+          }
+          i128 e1[3], e2[3], e3[3], r[3];
+          for (int d = 0; d < 3; ++d) {
+            e1[d] = P[1][d] - P[0][d];
+            e2[d] = P[2][d] - P[0][d];
+            e3[d] = P[3][d] - P[0][d];
+            r[d] = (i128)x[d] - P[0][d];
+          }
+          const i128 det = det3(e1, e2, e3);
+          const i128 n1 = det3(r, e2, e3), n2 = det3(e1, r, e3), n3 = det3(e1, e2, r);
+          const i128 n0 = det - n1 - n2 - n3;
+          const i128 nn[4] = {n0, n1, n2, n3};
+          bool inside = true;
+          for (int v = 0; v < 4; ++v) inside = inside && (det > 0 ? nn[v] >= 0 : nn[v] <= 0);
+          if (!inside) continue;
+          for (int v = 0; v < 4; ++v) {
+            if (nn[v] == 0) continue;
+            const int32_t jj = find_index(Lc.key, t[v]);
+            if (jj >= 0) rows[k].push_back({jj, (double)((long double)nn[v] / (long double)det)});
+          }
+          found = true;
+          break;
+        }
+      }
+    }
+    Lf.I = csr_from_rows(Lf.key.size(), Lc.key.size(), rows);
+  }
+  // every level smoothed as a whole; near-boundary sets of Algorithm 3
+  for (int l = o.c + 1; l <= J; ++l) {
+    Level& L = o.lv[l];
+    L.smooth.resize(L.key.size());
+    for (size_t k = 0; k < L.key.size(); ++k) L.smooth[k] = (int32_t)k;
+    if (o.prm.nb_layers < 0) continue;
+    // Gamma_l: vertices of faces of one kept tetrahedron only; layer 0 = kept
+    // tetrahedra with a vertex on Gamma_l, layer i = those with a vertex in layer i-1
+    std::map<std::array<uint64_t, 3>, int> faces;
+    for (auto& t : L.tet)
+      for (int k = 0; k < 4; ++k) {
+        std::array<uint64_t, 3> f = {t[(k + 1) % 4], t[(k + 2) % 4], t[(k + 3) % 4]};
+        std::sort(f.begin(), f.end());
+        faces[f] += 1;
+      }
+    std::set<uint64_t> verts;
+    for (auto& kv : faces)
+      if (kv.second == 1)
+        for (int k = 0; k < 3; ++k) verts.insert(kv.first[k]);
+    std::set<uint64_t> layer;
+    for (int i = 0; i <= o.prm.nb_layers; ++i) {
+      layer.clear();
+      for (auto& t : L.tet)
+        if (verts.count(t[0]) || verts.count(t[1]) || verts.count(t[2]) || verts.count(t[3]))
+          for (int k = 0; k < 4; ++k) layer.insert(t[k]);
+      if (layer == verts) break;
+      verts = layer;
+    }
+    for (auto k : verts) {
+      const int32_t id = find_index(L.key, k);
+      if (id >= 0) L.nbset.push_back(id);
+    }
+    std::sort(L.nbset.begin(), L.nbset.end());
+    const int64_t m = (int64_t)L.nbset.size();
+    L.nbchol.assign(m * m, 0.0);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = 0; b < m; ++b) L.nbchol[a * m + b] = L.A.get(L.nbset[a], L.nbset[b]);
+    if (m && !cholesky(L.nbchol, m)) {
+      o.err = "oracle: near-boundary block not positive definite";
+      return;
+    }
+  }
+}
+
 void build_aux3(Oracle& o) {
   const int J = o.J;
   o.LB = J + 1;
@@ -1871,6 +2206,11 @@ void build_aux3(Oracle& o) {
       vol += tet_volume(T[0], T[1], T[2], T[3]);
     }
     o.boxdomain = std::fabs(vol - o.L * o.L * o.L) <= 1e-12 * o.L * o.L * o.L;
+  }
+  for (int64_t v = 0; v < o.nv; ++v) o.neumann = o.neumann || o.bflag[v] == 2;
+  if (o.neumann) {
+    build_aux_mixed3(o);
+    return;
   }
   std::vector<std::vector<std::array<uint64_t, 4>>> inside;
   if (!o.boxdomain) {
@@ -2103,7 +2443,7 @@ void build_transfer3(Oracle& o) {
       uint64_t q[3] = {b[1], b[2], b[3]};
       box_tets(o, (int)b[0], q, o.J, kt);
       for (auto& k4 : kt) {
-        if (!o.boxdomain && !tet_in.count(k4)) continue;  // aux hat functions vanish outside Omega^D_J
+        if ((!o.boxdomain || o.neumann) && !tet_in.count(k4)) continue;  // hats only on the kept tetrahedra
         P3 K[4];
         tet_points(o, k4, K);
         std::vector<SignedTet> P = intersect_tets(T, K);
@@ -2505,8 +2845,6 @@ void* orc_create(int dim, int64_t nv, const double* X, int64_t ne, const int32_t
     if (dim == 2) {
       build_aux(*o);
       if (o->err.empty()) build_transfer(*o);
-    } else if (std::find(o->bflag.begin(), o->bflag.end(), (uint8_t)2) != o->bflag.end()) {
-      o->err = "oracle: mixed Dirichlet/Neumann boundaries are built in 2D only";
     } else {
       build_aux3(*o);
       if (o->err.empty()) build_transfer3(*o);

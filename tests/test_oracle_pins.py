@@ -1366,3 +1366,266 @@ def test_mixed_hierarchy_keeps_the_in_place_properties(gen, shape, where):
             ever |= Fc | Ff
     # a Neumann cut through the lattice thins the coverage level by level
     assert left > 0 if where == "inner" else left == 0
+
+
+# ------------------------------------------------ mixed boundaries in 3D (R18)
+
+def _xyz3_keys(keys):
+    k = keys.astype(np.uint64)
+    out = []
+    for a in range(3):
+        v = np.zeros_like(k)
+        for j in range(21):
+            v |= ((k >> np.uint64(3 * j + a)) & np.uint64(1)) << np.uint64(j)
+        out.append(v)
+    return out
+
+
+def _pts3(o, keys):
+    a = o.root()
+    lb = o.info("LB")
+    return np.stack([a[k] + np.ldexp(v.astype(np.float64), -lb) * a[3] for k, v in enumerate(_xyz3_keys(keys))], -1)
+
+
+def _fr3(p):
+    return tuple(Fraction(float(v)) for v in p)
+
+
+def _gamma_d3(m):
+    f = np.sort(np.concatenate([m.elems[:, [1, 2, 3]], m.elems[:, [0, 2, 3]], m.elems[:, [0, 1, 3]],
+                                m.elems[:, [0, 1, 2]]]), axis=1)
+    uniq, cnt = np.unique(f, axis=0, return_counts=True)
+    bd = uniq[cnt == 1]
+    bd = bd[(m.bflag[bd] == 1).all(axis=1)]
+    return [[_fr3(m.verts[v]) for v in t] for t in bd]
+
+
+def _sub(a, b):
+    return tuple(x - y for x, y in zip(a, b))
+
+
+def _cross(a, b):
+    return (a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0])
+
+
+def _dot(a, b):
+    return sum(x * y for x, y in zip(a, b))
+
+
+def _tri_cuts_open_tet(T, K):
+    # exact: clip the triangle by the four closed half-spaces of K; the interior
+    # of K is met when a piece of positive area remains and the triangle does
+    # not lie in the plane of a face of K
+    faces = [(1, 2, 3, 0), (0, 2, 3, 1), (0, 1, 3, 2), (0, 1, 2, 3)]
+    poly = list(T)
+    for a, b, c, opp in faces:
+        n = _cross(_sub(K[b], K[a]), _sub(K[c], K[a]))
+        if _dot(n, _sub(K[opp], K[a])) < 0:
+            n = tuple(-x for x in n)
+        if all(_dot(n, _sub(p, K[a])) == 0 for p in T):
+            return False
+        side = [_dot(n, _sub(p, K[a])) for p in poly]
+        out = []
+        for i in range(len(poly)):
+            p, q, sp_, sq = poly[i], poly[(i + 1) % len(poly)], side[i], side[(i + 1) % len(poly)]
+            if sp_ >= 0:
+                out.append(p)
+            if (sp_ > 0 and sq < 0) or (sp_ < 0 and sq > 0):
+                t = sp_ / (sp_ - sq)
+                out.append(tuple(p[k] + t * (q[k] - p[k]) for k in range(3)))
+        poly = out
+        if len(poly) < 3:
+            return False
+    area = (0, 0, 0)
+    for i in range(1, len(poly) - 1):
+        area = tuple(x + y for x, y in zip(area, _cross(_sub(poly[i], poly[0]), _sub(poly[i + 1], poly[0]))))
+    return area != (0, 0, 0)
+
+
+def _on_tri3(T, p):
+    n = _cross(_sub(T[1], T[0]), _sub(T[2], T[0]))
+    if _dot(n, _sub(p, T[0])) != 0:
+        return False
+    s = [_dot(n, _cross(_sub(T[(k + 1) % 3], T[k]), _sub(p, T[k]))) for k in range(3)]
+    return all(v >= 0 for v in s) or all(v <= 0 for v in s)
+
+
+def test_mixed3_cube_levels_are_the_natural_boundary_7_point(gen):
+    # Unjittered cube, Neumann on x = 1: every tetrahedron is kept.  On levels no
+    # finer than the mesh the free nodes are the lattice nodes off the five
+    # Dirichlet faces and A_l = h (K (x) M (x) M + M (x) K (x) M + M (x) M (x) K)
+    # with the natural condition on x = 1 (1D stiffness with last diagonal 1,
+    # lumped 1D mass with last entry 1/2).  On finer levels, lattice nodes inside
+    # the face triangles whose three vertices are on the face's rim (Gamma_D)
+    # are Dirichlet as well.
+    m = gen.grid3d(9, 1, jitter=0.0)
+    x = m.verts
+    m.bflag = m.bflag.copy()
+    m.bflag[(x[:, 0] == 1.0) & (x[:, 1] > 0) & (x[:, 1] < 1) & (x[:, 2] > 0) & (x[:, 2] < 1)] = NEUMANN
+    o = oracle.Oracle(m, coarse_max=1)
+    top = 1 << o.info("LB")
+    gd = _gamma_d3(m)
+    for l in range(1, o.J + 1):
+        assert {tuple(t) for t in o.level_tet(l).tolist()} == {tuple(t) for t in o.level_alltet(l).tolist()}, l
+        ak = o.level_keys(l, all_nodes=True)
+        X, Y, Z = _xyz3_keys(ak)
+        off = (X > 0) & (Y > 0) & (Y < top) & (Z > 0) & (Z < top)
+        P = _pts3(o, ak)
+        # exact on-Gamma_D test, for the nodes off the Dirichlet faces (the others are out anyway)
+        on_gd = np.zeros(ak.size, bool)
+        for i in np.where(off)[0]:
+            q = _fr3(P[i])
+            on_gd[i] = any(_on_tri3(T, q) for T in gd
+                           if all(min(v[k] for v in T) <= q[k] <= max(v[k] for v in T) for k in range(3)))
+        assert np.array_equal(o.level_keys(l), np.sort(ak[off & ~on_gd])), l
+        if 2 ** l > 8:
+            assert on_gd[off].any()                 # finer than the mesh: rim triangles bite
+            continue
+        keys = o.level_keys(l)
+        X, Y, Z = _xyz3_keys(keys)
+        step = top >> l
+        nx, ny = 2 ** l, 2 ** l - 1
+        rm = ((Z // step - 1) * ny * nx + (Y // step - 1) * nx + (X // step - 1)).astype(np.int64)
+        Pm = np.zeros((keys.size, keys.size))
+        Pm[rm, np.arange(keys.size)] = 1
+        Ky = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(ny, ny)).toarray()
+        Kx = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(nx, nx)).toarray()
+        Kx[-1, -1] = 1
+        Mx = np.eye(nx)
+        Mx[-1, -1] = 0.5
+        My = np.eye(ny)
+        W = (np.kron(np.kron(Ky, My), Mx) + np.kron(np.kron(My, Ky), Mx) + np.kron(np.kron(My, My), Kx)) / 2 ** l
+        assert np.abs(Pm @ o.A(l).toarray() @ Pm.T - W).max() <= 1e-14 * np.abs(W).max(), l
+
+
+def _mixed3_lprism(gen):
+    # jittered L prism: Dirichlet on the jagged cut, Neumann on the face x = 0
+    m = gen.grid3d_domain(5, 2, "L")
+    x = m.verts
+    m.bflag = m.bflag.copy()
+    inner = (x[:, 1] > 0) & (x[:, 1] < 1) & (x[:, 2] > 0) & (x[:, 2] < 1)
+    m.bflag[(m.bflag == 1) & (x[:, 0] == 0) & inner] = NEUMANN
+    return m
+
+
+def test_mixed3_kept_tets_and_free_nodes_exact(gen):
+    m = _mixed3_lprism(gen)
+    o = oracle.Oracle(m, coarse_max=8)
+    gd = _gamma_d3(m)
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    rng = np.random.default_rng(5)
+    cut_any = False
+    for l in range(o.J + 1):
+        allt, kept = o.level_alltet(l), {tuple(t) for t in o.level_tet(l).tolist()}
+        P = _pts3(o, allt.reshape(-1)).reshape(-1, 4, 3)
+        dirn = set()
+        for t in range(allt.shape[0]):
+            K = [_fr3(p) for p in P[t]]
+            tlo, thi = P[t].min(axis=0), P[t].max(axis=0)
+            cut = any(_tri_cuts_open_tet(T, K) for T in gd
+                      if all(min(v[k] for v in T) <= thi[k] and max(v[k] for v in T) >= tlo[k] for k in range(3)))
+            key = tuple(allt[t].tolist())
+            if cut:
+                cut_any = True
+                dirn.update(key)
+                assert key not in kept, (l, t)
+            elif key not in kept:
+                # left out without a cut: no fine element covers any of 20 random interior points
+                w = rng.dirichlet(np.ones(4), size=20)
+                pts = w @ P[t]
+                sel = np.where(np.all(lo <= thi, axis=1) & np.all(hi >= tlo, axis=1))[0]
+                for e in sel:
+                    Te = E[e]
+                    B = np.linalg.solve((Te[1:] - Te[0]).T, (pts - Te[0]).T).T
+                    lam = np.concatenate([1 - B.sum(1, keepdims=True), B], 1)
+                    assert not np.any(lam.min(1) > 1e-12), (l, t)
+        nodes = sorted({k for t in kept for k in t})
+        Pn = _pts3(o, np.array(nodes, dtype=np.uint64))
+        def on_gd(p):
+            q = _fr3(p)
+            return any(_on_tri3(T, q) for T in gd if all(min(v[k] for v in T) <= q[k] <= max(v[k] for v in T)
+                                                       for k in range(3)))
+        free = [k for k, p in zip(nodes, Pn) if k not in dirn and not on_gd(p)]
+        assert o.level_keys(l).tolist() == free, l
+    assert cut_any
+
+
+def _solid_angles(o, tets):
+    # solid angle at each vertex of each tetrahedron (Van Oosterom-Strackee)
+    P = _pts3(o, tets.reshape(-1)).reshape(-1, 4, 3)
+    ang = {}
+    for t in range(tets.shape[0]):
+        for v in range(4):
+            a, b, c = (P[t][(v + k) % 4] - P[t][v] for k in (1, 2, 3))
+            la, lb, lc = np.linalg.norm(a), np.linalg.norm(b), np.linalg.norm(c)
+            num = abs(np.dot(a, np.cross(b, c)))
+            den = la * lb * lc + np.dot(a, b) * lc + np.dot(a, c) * lb + np.dot(b, c) * la
+            ang[int(tets[t, v])] = ang.get(int(tets[t, v]), 0.0) + 2 * np.arctan2(num, den)
+    return ang
+
+
+@pytest.mark.parametrize("layers", [0, 1])
+def test_mixed3_near_boundary_sets_are_graph_balls(gen, layers):
+    from scipy.sparse.csgraph import shortest_path
+    m = _mixed3_lprism(gen)
+    o = oracle.Oracle(m, coarse_max=8, nb_layers=layers)
+    for l in range(o.c + 1, o.J + 1):
+        tets = o.level_tet(l)
+        nodes = np.unique(tets.reshape(-1))
+        pos = {int(k): i for i, k in enumerate(nodes)}
+        r, c = [], []
+        for t in tets.tolist():
+            for a in range(4):
+                for b in range(4):
+                    if a != b:
+                        r.append(pos[t[a]])
+                        c.append(pos[t[b]])
+        G = sp.coo_matrix((np.ones(len(r)), (r, c)), shape=(nodes.size, nodes.size)).tocsr()
+        bnd = [pos[k] for k, a in _solid_angles(o, tets).items() if abs(a - 4 * np.pi) > 1e-9]
+        dist = shortest_path(G, directed=False, unweighted=True, indices=bnd).min(axis=0)
+        ball = set(int(k) for k in nodes[dist <= layers + 1])
+        keys = o.level_keys(l)
+        assert o.near_boundary_set(l).tolist() == [i for i, k in enumerate(keys.tolist()) if k in ball], l
+
+
+def test_mixed3_interpolation_cycle_and_solve(gen):
+    m = _mixed3_lprism(gen)
+    o0 = oracle.Oracle(m)
+    J = o0.J
+    rng = np.random.default_rng(9)
+    # nodal interpolation by point location over all kept coarse tetrahedra
+    o = oracle.Oracle(m, coarse_max=8)
+    for l in range(o.c + 1, o.J + 1):
+        ct, ck = o.level_tet(l - 1), o.level_keys(l - 1)
+        ec = rng.standard_normal(ck.size)
+        val = dict(zip(ck.tolist(), ec))
+        CP = _pts3(o, ct.reshape(-1)).reshape(-1, 4, 3)
+        FP = _pts3(o, o.level_keys(l))
+        Minv = np.linalg.inv(np.transpose(CP[:, 1:] - CP[:, :1], (0, 2, 1)))   # per tet: point -> (l1, l2, l3)
+        cval = np.array([[val.get(int(k), 0.0) for k in t] for t in ct])
+        want = np.zeros(len(FP))
+        for i, p in enumerate(FP):
+            B = np.einsum("tij,tj->ti", Minv, p - CP[:, 0])
+            lam = np.concatenate([1 - B.sum(1, keepdims=True), B], 1)
+            hit = np.where(lam.min(1) >= -1e-12)[0]
+            if hit.size:
+                want[i] = lam[hit[0]] @ cval[hit[0]]
+        assert np.abs(o.I(l) @ ec - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), l
+    # two levels without smoothing: coarse solve, then the J_{l,j} solve
+    o2 = oracle.Oracle(m, coarse_max=o0.info("nlevel", J - 1), nu_pre=0, nu_post=0, nb_layers=1)
+    assert o2.c == J - 1
+    AJ, Ac, I = o2.A(J).toarray(), o2.A(J - 1).toarray(), o2.I(J).toarray()
+    f = rng.standard_normal(AJ.shape[0])
+    u = I @ np.linalg.solve(Ac, I.T @ f)
+    nb = o2.near_boundary_set(J)
+    assert nb.size > 0
+    u[nb] += np.linalg.solve(AJ[np.ix_(nb, nb)], (f - AJ @ u)[nb])
+    assert np.abs(o2.vcycle(f) - u).max() <= 1e-11 * np.abs(u).max()
+    # PCG reaches the dense solution with and without the correction
+    for layers in (-1, 1):
+        o3 = oracle.Oracle(m, coarse_max=8, nb_layers=layers)
+        b = o3.mass_apply(gen.nodal_uniform(m, 2))
+        ref = np.linalg.solve(o3.A().toarray(), b)
+        u3, st, it, _ = o3.solve(b, rtol=1e-13)
+        assert st == 0 and np.linalg.norm(u3 - ref) <= 1e-11 * np.linalg.norm(ref)
