@@ -377,7 +377,92 @@ void lattice_point3(const TreeResult& t, int LB, uint64_t key, double* p) {
   for (int k = 0; k < 3; ++k) p[k] = t.amin[k] + std::ldexp((double)q[k], -LB) * t.L;
 }
 
+// A fine boundary triangle of Gamma_D (mixed boundaries).
+struct GTri {
+  double p[3][3];
+};
+
+inline void vsub(const double* a, const double* b, double* r) {
+  for (int k = 0; k < 3; ++k) r[k] = a[k] - b[k];
+}
+inline void vcross(const double* a, const double* b, double* r) {
+  r[0] = a[1] * b[2] - a[2] * b[1];
+  r[1] = a[2] * b[0] - a[0] * b[2];
+  r[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double vdot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// The closed triangle g meets the interior of the tetrahedron K exactly when
+// no direction separates them, touching allowed.  The directions to try are
+// the facet normals of the Minkowski difference K - g: K's face normals, g's
+// normal, and the cross products of an edge of K with an edge of g.  With FP64
+// projections, an overlap below 1e-12 |a| L along a counts as touching.
+inline bool tri_cuts_open_tet(const double K[4][3], const GTri& g, double L) {
+  double ax[23][3];
+  int na = 0;
+  static const int fv[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  static const int ke[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+  double e1[3], e2[3];
+  for (auto& f : fv) {
+    vsub(K[f[1]], K[f[0]], e1);
+    vsub(K[f[2]], K[f[0]], e2);
+    vcross(e1, e2, ax[na++]);
+  }
+  vsub(g.p[1], g.p[0], e1);
+  vsub(g.p[2], g.p[0], e2);
+  vcross(e1, e2, ax[na++]);
+  for (auto& e : ke)
+    for (int t = 0; t < 3; ++t) {
+      vsub(K[e[1]], K[e[0]], e1);
+      vsub(g.p[(t + 1) % 3], g.p[t], e2);
+      vcross(e1, e2, ax[na++]);
+    }
+  for (int i = 0; i < na; ++i) {
+    const double* a = ax[i];
+    const double n2 = vdot(a, a);
+    if (n2 == 0) continue;
+    const double tol = 1e-12 * std::sqrt(n2) * L;
+    double k0 = INFINITY, k1 = -INFINITY, t0 = INFINITY, t1 = -INFINITY;
+    for (int v = 0; v < 4; ++v) {
+      const double d = vdot(a, K[v]);
+      k0 = std::min(k0, d);
+      k1 = std::max(k1, d);
+    }
+    for (int v = 0; v < 3; ++v) {
+      const double d = vdot(a, g.p[v]);
+      t0 = std::min(t0, d);
+      t1 = std::max(t1, d);
+    }
+    if (t1 <= k0 + tol || t0 >= k1 - tol) return false;
+  }
+  return true;
+}
+
+// The point x lies on the closed triangle g (within the same relative 1e-12).
+inline bool on_tri(const GTri& g, const double* x, double L) {
+  double e1[3], e2[3], n[3], r[3];
+  vsub(g.p[1], g.p[0], e1);
+  vsub(g.p[2], g.p[0], e2);
+  vcross(e1, e2, n);
+  const double nn = std::sqrt(vdot(n, n));
+  vsub(x, g.p[0], r);
+  const double tol = 1e-12 * nn * L;
+  if (std::fabs(vdot(n, r)) > tol) return false;
+  double s[3];
+  for (int k = 0; k < 3; ++k) {
+    double a[3], b[3], c[3];
+    vsub(g.p[(k + 1) % 3], g.p[k], a);
+    vsub(x, g.p[k], b);
+    vcross(a, b, c);
+    s[k] = vdot(n, c) / nn;
+  }
+  return (s[0] >= -tol && s[1] >= -tol && s[2] >= -tol) || (s[0] <= tol && s[1] <= tol && s[2] <= tol);
+}
+
 void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out) {
+  // R18: a Neumann vertex selects the mixed grids (tetrahedra whose interior
+  // meets Omega and no Gamma_D triangle)
+  const bool mixed = mesh.mixed;
   Tree3 T;
   T.S = tree.split;
   // closure, finest depth first: the parents of all face and edge neighbours
@@ -436,7 +521,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         box_tets(T, leaves[q].first, leaves[q].second, J, tt);
         for (auto& x : tt)
           for (int k = 0; k < 4; ++k)
-            if (!bnd3(T, x[k])) part[t].push_back(x[k]);
+            if (mixed || !bnd3(T, x[k])) part[t].push_back(x[k]);
       }
     });
     out.aux_key = uniq_parts(part);
@@ -587,7 +672,8 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   // R17: a domain that does not fill the root cube uses the Dirichlet grids
   // T^D_l (tetrahedra inside Omega); the clipping pass then also measures how
   // much of each tetrahedron the fine elements cover (kcov, fancov)
-  const bool dgrid = !mesh.boxdomain;
+  const bool dgrid = !mesh.boxdomain && !mixed;
+  const bool cover = dgrid || mixed;  // the clipping pass also measures covered volumes
   std::vector<std::vector<std::array<double, 6>>> kint(J + 1), kcov(J + 1);
   std::unordered_map<uint64_t, double> fanint, fancov;  // keyed by the sorted tet's hash below
   auto tet_hash = [](Tet t) {
@@ -596,9 +682,9 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     for (auto v : t) hsh = (hsh ^ v) * 1099511628211ULL;
     return hsh;
   };
-  if (varcoef || dgrid) {
+  if (varcoef || cover) {
     // the constant-leaf shortcut below needs elements that tile every leaf
-    const bool skip_const = varcoef && !dgrid;
+    const bool skip_const = varcoef && !cover;
     // elements in Morton order of their lowest corner, in chunks of 4096;
     // each chunk sums its overlaps per leaf tetrahedron, and the chunk sums
     // are added in chunk order (deterministic for any thread count)
@@ -747,7 +833,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
               clip::clip_tets(tet4(S), tet4(K), [&](const clip::Tet4& pc) { vol += clip::volume(pc); });
               if (!(vol > 0)) continue;
               if (varcoef) acc.push_back({f0 + q, vol * (mesh.coeff[e] - a0)});
-              if (dgrid) cac.push_back({f0 + q, vol});
+              if (cover) cac.push_back({f0 + q, vol});
             }
           }
         }
@@ -799,7 +885,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     // (kcov, fancov)
     for (int pass = 0; pass < 2; ++pass) {
     if (pass == 0 && !varcoef) continue;
-    if (pass == 1 && !dgrid) continue;
+    if (pass == 1 && !cover) continue;
     const std::vector<double>& IA = pass == 0 ? I : C;
     auto& KI = pass == 0 ? kint : kcov;
     auto& FI = pass == 0 ? fanint : fancov;
@@ -856,23 +942,117 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
        dd = {P[3][0], P[3][1], P[3][2]};
     return std::fabs(vol6(a, b, cc, dd)) / 6.0;
   };
-  auto tet_inside = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> bool {
-    if (!dgrid) return true;
-    double cov;
-    if (kuhn) {
-      const size_t i = box_at(d, p);
-      cov = kcov[d][i][q];
-    } else {
-      auto it = fancov.find(tet_hash(t));
-      cov = it == fancov.end() ? 0.0 : it->second;
+  auto tet_cov = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> double {
+    if (kuhn) return kcov[d][box_at(d, p)][q];
+    auto it = fancov.find(tet_hash(t));
+    return it == fancov.end() ? 0.0 : it->second;
+  };
+  // Gamma_D (mixed): the fine boundary faces (faces of one element) with three
+  // Dirichlet vertices, binned by bounding box on gn^3 cells over the root cube
+  std::vector<GTri> gd;
+  int gn = 1;
+  std::vector<int64_t> gstart(2, 0);
+  std::vector<int32_t> gitem;
+  auto gcell = [&](double v, int a, double slack) {
+    const double cc = (v - tree.amin[a]) / tree.L * gn + slack;
+    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(cc)));
+  };
+  if (mixed) {
+    std::vector<std::array<int32_t, 3>> fs;
+    fs.reserve(4 * mesh.ne);
+    for (int64_t e = 0; e < mesh.ne; ++e)
+      for (int k = 0; k < 4; ++k) {
+        std::array<int32_t, 3> f = {mesh.E[4 * e + (k + 1) % 4], mesh.E[4 * e + (k + 2) % 4], mesh.E[4 * e + (k + 3) % 4]};
+        std::sort(f.begin(), f.end());
+        fs.push_back(f);
+      }
+    std::sort(fs.begin(), fs.end());
+    for (size_t i = 0; i < fs.size();) {
+      size_t j = i;
+      while (j < fs.size() && fs[j] == fs[i]) ++j;
+      if (j - i == 1 && mesh.bflag[fs[i][0]] == 1 && mesh.bflag[fs[i][1]] == 1 && mesh.bflag[fs[i][2]] == 1) {
+        GTri g;
+        for (int v = 0; v < 3; ++v)
+          for (int k = 0; k < 3; ++k) g.p[v][k] = mesh.X[3 * (int64_t)fs[i][v] + k];
+        gd.push_back(g);
+      }
+      i = j;
     }
-    return cov >= (1.0 - 1e-9) * tet_vol(t);
+    gn = std::max(1, std::min(128, (int)std::cbrt((double)gd.size())));
+    gstart.assign((size_t)gn * gn * gn + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int64_t> fill(gstart.begin(), gstart.end() - 1);
+      for (size_t q = 0; q < gd.size(); ++q) {
+        int c0[3], c1[3];
+        for (int a = 0; a < 3; ++a) {
+          const double lo = std::min({gd[q].p[0][a], gd[q].p[1][a], gd[q].p[2][a]});
+          const double hi = std::max({gd[q].p[0][a], gd[q].p[1][a], gd[q].p[2][a]});
+          c0[a] = gcell(lo, a, -1e-9);
+          c1[a] = gcell(hi, a, 1e-9);
+        }
+        for (int z = c0[2]; z <= c1[2]; ++z)
+          for (int y = c0[1]; y <= c1[1]; ++y)
+            for (int x = c0[0]; x <= c1[0]; ++x) {
+              const int64_t ci = ((int64_t)z * gn + y) * gn + x;
+              if (pass == 0) gstart[ci + 1] += 1;
+              else gitem[fill[ci]++] = (int32_t)q;
+            }
+      }
+      if (pass == 0) {
+        for (size_t ci = 0; ci + 1 < gstart.size(); ++ci) gstart[ci + 1] += gstart[ci];
+        gitem.assign(gstart.back(), 0);
+      }
+    }
+  }
+  // f(triangle) for the Gamma_D triangles binned in the cells the box
+  // [lo, hi] meets; stops when f returns true
+  auto gd_any = [&](const double* lo, const double* hi, auto&& f) -> bool {
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; ++a) {
+      c0[a] = gcell(lo[a], a, -1e-9);
+      c1[a] = gcell(hi[a], a, 1e-9);
+    }
+    for (int z = c0[2]; z <= c1[2]; ++z)
+      for (int y = c0[1]; y <= c1[1]; ++y)
+        for (int x = c0[0]; x <= c1[0]; ++x) {
+          const int64_t ci = ((int64_t)z * gn + y) * gn + x;
+          for (int64_t q = gstart[ci]; q < gstart[ci + 1]; ++q)
+            if (f(gd[gitem[q]])) return true;
+        }
+    return false;
+  };
+  // the interior of lattice tetrahedron t meets Gamma_D
+  auto gd_cuts = [&](const Tet& t) -> bool {
+    if (gd.empty()) return false;
+    double K[4][3], lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < 4; ++v) {
+      lattice_point3(tree, T.LB, t[v], K[v]);
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], K[v][a]);
+        hi[a] = std::max(hi[a], K[v][a]);
+      }
+    }
+    return gd_any(lo, hi, [&](const GTri& g) { return tri_cuts_open_tet(K, g, tree.L); });
+  };
+  // lattice node x lies on Gamma_D
+  auto on_gd = [&](uint64_t x) -> bool {
+    if (gd.empty()) return false;
+    double P[3];
+    lattice_point3(tree, T.LB, x, P);
+    return gd_any(P, P, [&](const GTri& g) { return on_tri(g, P, tree.L); });
+  };
+  auto tet_inside = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> bool {
+    if (mixed) return tet_cov(d, p, kuhn, q, t) > 1e-12 * tet_vol(t) && !gd_cuts(t);
+    if (!dgrid) return true;
+    return tet_cov(d, p, kuhn, q, t) >= (1.0 - 1e-9) * tet_vol(t);
   };
   // node x is free at level l (a vertex of sigma^(l) off the boundary of
   // Omega^D_l): every level-l tetrahedron around it is inside.  The box
   // shown at level l around x in each octant holds those tetrahedra.
+  // Mixed: x is free when it is a node of a kept tetrahedron, lies on no
+  // tetrahedron cut by Gamma_D and not on Gamma_D itself.
   auto free_at = [&](uint64_t x, int l, std::vector<Tet>& kt) -> bool {
-    if (bnd3(T, x)) return false;
+    if (!mixed && bnd3(T, x)) return false;
     uint64_t X[3];
     um3(x, X);
     bool node = false;
@@ -897,13 +1077,53 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       box_tets(T, d, p, l, kt, &kuhn);
       for (size_t q = 0; q < kt.size(); ++q) {
         if (kt[q][0] != x && kt[q][1] != x && kt[q][2] != x && kt[q][3] != x) continue;
+        if (mixed) {
+          if (gd_cuts(kt[q])) return false;
+          if (tet_cov(d, p, kuhn, (int)q, kt[q]) > 1e-12 * tet_vol(kt[q])) node = true;
+          continue;
+        }
         node = true;
         if (!tet_inside(d, p, kuhn, (int)q, kt[q])) return false;
       }
     }
-    return node;
+    return node && !(mixed && on_gd(x));
   };
-  std::vector<int32_t> phi;  // first level at which each aux node is free (Dirichlet grids)
+  std::vector<int32_t> phi;  // first level at which each aux node is free (Dirichlet and mixed grids)
+  std::vector<int32_t> psi;  // mixed: first level after phi at which it is no longer free
+  if (mixed) {
+    std::vector<std::pair<uint64_t, int32_t>> born;
+    for (int l = 1; l <= J; ++l)
+      for (auto& v : newnodes[l]) born.push_back({v[0], l});
+    std::sort(born.begin(), born.end());
+    const std::vector<uint64_t> cand = out.aux_key;
+    std::vector<int32_t> cphi(cand.size(), J + 1), cpsi(cand.size(), J + 1);
+    pfor((int64_t)cand.size(), [&](unsigned, int64_t b0, int64_t b1) {
+      std::vector<Tet> kt;
+      for (int64_t q = b0; q < b1; ++q) {
+        auto it = std::lower_bound(born.begin(), born.end(), std::pair<uint64_t, int32_t>(cand[q], 0));
+        int l = (it != born.end() && it->first == cand[q]) ? it->second : 0;
+        while (l <= J && !free_at(cand[q], l, kt)) ++l;
+        cphi[q] = l;
+        if (l > J) continue;
+        ++l;
+        while (l <= J && free_at(cand[q], l, kt)) ++l;
+        cpsi[q] = l;
+      }
+    });
+    std::vector<uint64_t> ak;
+    for (size_t q = 0; q < cand.size(); ++q)
+      if (cphi[q] <= J) {
+        ak.push_back(cand[q]);
+        phi.push_back(cphi[q]);
+        psi.push_back(cpsi[q]);
+      }
+    out.aux_key.swap(ak);
+    out.nlevel.assign(J + 1, 0);
+    for (int32_t f : phi) out.nlevel[f] += 1;
+    for (int l = 1; l <= J; ++l) out.nlevel[l] += out.nlevel[l - 1];
+    out.phi = phi;
+    out.psi = psi;
+  }
   if (dgrid) {
     std::vector<int32_t> keep(out.aux_key.size(), 0);
     pfor((int64_t)out.aux_key.size(), [&](unsigned, int64_t b0, int64_t b1) {
@@ -938,6 +1158,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   AKI.build(AK, 20);
   // aux ID of node x at level l, or -1 where it is not a free node there
   auto level_id = [&](uint64_t x, int l) -> int32_t {
+    if (mixed) {
+      const int32_t id = AKI.find(x);
+      return (id >= 0 && phi[id] <= l && l < psi[id]) ? id : -1;
+    }
     if (bnd3(T, x)) return -1;
     const int32_t id = AKI.find(x);
     if (dgrid && (id < 0 || phi[id] > l)) return -1;
@@ -945,13 +1169,31 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   };
   // coarsest level used: finest level with at most coarse_max_dofs free nodes
   out.c = 0;
-  for (int l = 0; l <= J; ++l)
-    if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  if (mixed) {
+    // by the free nodes of each level (the nodes that left the grid excluded)
+    std::vector<int64_t> nreal(J + 2, 0);
+    for (size_t q = 0; q < phi.size(); ++q) {
+      nreal[phi[q]] += 1;
+      nreal[psi[q]] -= 1;
+    }
+    for (int l = 1; l <= J; ++l) nreal[l] += nreal[l - 1];
+    for (int l = 0; l <= J; ++l)
+      if (nreal[l] <= prm.coarse_max_dofs) out.c = l;
+  } else {
+    for (int l = 0; l <= J; ++l)
+      if (out.nlevel[l] <= prm.coarse_max_dofs) out.c = l;
+  }
   const int c = out.c;
 
   // mean of a over the tetrahedron (a = 0 outside Omega, a = 1 inside when no
   // coefficient is given)
   auto tet_coef = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> double {
+    if (mixed) {
+      // the mean of a over tau n Omega (R18)
+      if (!varcoef) return 1.0;
+      const double in = kuhn ? kint[d][box_at(d, p)][q] : fanint.at(tet_hash(t));
+      return in / tet_cov(d, p, kuhn, q, t);
+    }
     if (!varcoef && !dgrid) return 1.0;
     const auto& KI = varcoef ? kint : kcov;
     const auto& FI = varcoef ? fanint : fancov;
@@ -1001,7 +1243,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   // local smoothing: smoothing nodes (by aux ID) and relevant boxes (by index
   // within their depth) of one level are marked in flag arrays and gathered
   // in ascending order; the flags are cleared for the next level
-  const bool local = prm.smoothing != 1;
+  const bool local = prm.smoothing != 1 && !mixed;  // the mixed grids are not nested: whole levels
   std::unique_ptr<std::atomic<uint8_t>[]> sflag;
   std::vector<std::unique_ptr<std::atomic<uint8_t>[]>> rflag(J + 1);
   if (local) {
@@ -1018,7 +1260,7 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     const int d = l - 1;
     std::vector<std::pair<int, uint64_t>> rel;
     std::vector<uint64_t> sm;
-    if (prm.smoothing == 1) {
+    if (!local) {
       for (int dd = 0; dd <= l; ++dd)
         for (uint64_t p : BX[dd])
           if (!(dd < l && T.split(dd, p))) rel.push_back({dd, p});
@@ -1143,7 +1385,72 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       }
       for (auto& x : th) x.join();
     }
-    if (!dgrid) {
+    if (mixed && mesh.nb_layers >= 0) {
+      // Algorithm 3: J_{l,j} = the free nodes within j + 1 edges of a vertex
+      // of a face of one kept tetrahedron only (breadth-first over the edges)
+      std::vector<uint64_t> nodes(L.tri_key.begin(), L.tri_key.end());
+      uniq(nodes);
+      auto loc = [&](uint64_t k) { return (int64_t)(std::lower_bound(nodes.begin(), nodes.end(), k) - nodes.begin()); };
+      const size_t ntet = L.tri_coef.size();
+      std::vector<std::array<int64_t, 3>> fs;
+      std::vector<std::array<int64_t, 2>> es;
+      for (size_t t = 0; t < ntet; ++t) {
+        int64_t v[4];
+        for (int k = 0; k < 4; ++k) v[k] = loc(L.tri_key[4 * t + k]);
+        for (int k = 0; k < 4; ++k) {
+          std::array<int64_t, 3> f = {v[(k + 1) % 4], v[(k + 2) % 4], v[(k + 3) % 4]};
+          std::sort(f.begin(), f.end());
+          fs.push_back(f);
+          for (int k2 = k + 1; k2 < 4; ++k2) es.push_back({std::min(v[k], v[k2]), std::max(v[k], v[k2])});
+        }
+      }
+      std::sort(fs.begin(), fs.end());
+      std::sort(es.begin(), es.end());
+      es.erase(std::unique(es.begin(), es.end()), es.end());
+      std::vector<int32_t> dist(nodes.size(), -1);
+      std::vector<int64_t> frontier;
+      for (size_t i = 0; i < fs.size();) {
+        size_t j = i;
+        while (j < fs.size() && fs[j] == fs[i]) ++j;
+        if (j - i == 1)
+          for (int k = 0; k < 3; ++k)
+            if (dist[fs[i][k]] < 0) {
+              dist[fs[i][k]] = 0;
+              frontier.push_back(fs[i][k]);
+            }
+        i = j;
+      }
+      std::vector<int64_t> adjs(nodes.size() + 1, 0), adj(2 * es.size());
+      for (auto& e : es) {
+        adjs[e[0] + 1] += 1;
+        adjs[e[1] + 1] += 1;
+      }
+      for (size_t i = 0; i < nodes.size(); ++i) adjs[i + 1] += adjs[i];
+      {
+        std::vector<int64_t> fill(adjs.begin(), adjs.end() - 1);
+        for (auto& e : es) {
+          adj[fill[e[0]]++] = e[1];
+          adj[fill[e[1]]++] = e[0];
+        }
+      }
+      for (int r = 1; r <= mesh.nb_layers + 1 && !frontier.empty(); ++r) {
+        std::vector<int64_t> next;
+        for (int64_t v : frontier)
+          for (int64_t q = adjs[v]; q < adjs[v + 1]; ++q)
+            if (dist[adj[q]] < 0) {
+              dist[adj[q]] = r;
+              next.push_back(adj[q]);
+            }
+        frontier.swap(next);
+      }
+      for (size_t i = 0; i < nodes.size(); ++i) {
+        if (dist[i] < 0) continue;
+        const int32_t id = level_id(nodes[i], l);
+        if (id >= 0) L.nb_id.push_back(id);
+      }
+      std::sort(L.nb_id.begin(), L.nb_id.end());
+    }
+    if (!dgrid && !mixed) {
       for (auto& v : newnodes[l]) {
         if (bnd3(T, v[0])) continue;
         L.new_id.push_back(AKI.find(v[0]));

@@ -292,6 +292,22 @@ def _mixed_cases(gen):
     m.bflag = m.bflag.copy()
     m.bflag[((x == 1.0) | (y == 1.0)) & (x > 0) & (y > 0)] = 2
     out["graded33_two_sides_nb3"] = (m, {"coarse_max": 16, "nb_layers": 3})
+    m = gen.grid3d(9, 1)
+    x = m.verts
+    m.bflag = m.bflag.copy()
+    m.bflag[(x[:, 0] == 1.0) & (x[:, 1] > 0) & (x[:, 1] < 1) & (x[:, 2] > 0) & (x[:, 2] < 1)] = 2
+    out["cube9_face"] = (m, {"coarse_max": 8})
+    m = gen.grid3d_domain(5, 2, "L")
+    x = m.verts
+    m.bflag = m.bflag.copy()
+    m.bflag[(m.bflag == 1) & (x[:, 0] == 0) & (x[:, 1] > 0) & (x[:, 1] < 1) & (x[:, 2] > 0) & (x[:, 2] < 1)] = 2
+    m.coeff = np.exp(np.random.default_rng(6).normal(size=m.ne))
+    out["Lprism5_cut_lognormal"] = (m, {"coarse_max": 8, "nb_layers": 1})
+    m = gen.grid3d_domain(7, 3, "L")
+    x = m.verts
+    m.bflag = m.bflag.copy()
+    m.bflag[(m.bflag == 1) & (x[:, 0] > 0) & (x[:, 0] < 1) & (x[:, 1] > 0) & (x[:, 1] < 1)] = 2
+    out["Lprism7_neumann_cut"] = (m, {"coarse_max": 8})
     return out
 
 
@@ -302,17 +318,20 @@ def _compare_mixed(lib, m, o, params):
         splits.pop()
     cnt = np.array([len(s_) for s_ in splits], np.int64)
     flat = np.concatenate(splits) if splits else np.zeros(0, np.uint64)
+    dim = m.dim
     r = o.root()
-    amin = np.ascontiguousarray(r[:2], dtype=np.float64)
+    amin = np.ascontiguousarray(r[:dim], dtype=np.float64)
     L = float(r[3])
     X = np.ascontiguousarray(m.verts, dtype=np.float64)
     E = np.ascontiguousarray(m.elems, dtype=np.int32)
     B = np.ascontiguousarray(m.bflag, dtype=np.uint8)
     C = None if m.coeff is None else np.ascontiguousarray(m.coeff, dtype=np.float64)
-    h = lib.shim_build(2, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
+    h = lib.shim_build(dim, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
                        None if C is None else C.ctypes.data, len(cnt), cnt.ctypes.data, flat.ctypes.data,
                        amin.ctypes.data, L, params.get("n_min", 3), params.get("coarse_max", 512), 1,
                        params.get("nb_layers", 2))
+    nv_s = dim + 1
+    lb = 31 if dim == 2 else o.info("LB")
     try:
         assert lib.shim_error(h) == b"", lib.shim_error(h)
         J, c = lib.shim_get(h, b"J", 0, None), lib.shim_get(h, b"c", 0, None)
@@ -332,16 +351,16 @@ def _compare_mixed(lib, m, o, params):
             assert np.array_equal(np.sort(ak[sm]), lk), ("smooth", l)
             # the level operator rediscretised from the shim's kept triangles
             tk = _get(lib, h, "tri_key", l, np.uint64)
-            tid = _get(lib, h, "tri_id", l, np.int32).reshape(-1, 3)
+            tid = _get(lib, h, "tri_id", l, np.int32).reshape(-1, nv_s)
             tc = _get(lib, h, "tri_coef", l, np.float64)
-            P = np.stack([amin[a] + np.ldexp(v.astype(np.float64), -31) * L
-                          for a, v in enumerate(_deinterleave(tk, 2, 32))], -1)
-            K = _stiffness(P.reshape(-1, 3, 2), tc)
+            P = np.stack([amin[a] + np.ldexp(v.astype(np.float64), -lb) * L
+                          for a, v in enumerate(_deinterleave(tk, dim, 32 if dim == 2 else 21))], -1)
+            K = _stiffness(P.reshape(-1, nv_s, dim), tc)
             n = lk.size
             Ah = np.zeros((n, n))
             for t in range(len(tc)):
-                for i in range(3):
-                    for j in range(3):
+                for i in range(nv_s):
+                    for j in range(nv_s):
                         if tid[t, i] >= 0 and tid[t, j] >= 0:
                             Ah[pos[int(ak[tid[t, i]])], pos[int(ak[tid[t, j]])]] += K[t, i, j]
             Ao = o.A(l).toarray()
@@ -381,7 +400,8 @@ def _compare_mixed(lib, m, o, params):
 
 
 @pytest.mark.parametrize("name", ["square17_right", "L17_cut_c8", "hole17_left_lognormal", "L33_cut_nb0",
-                                  "graded33_two_sides_nb3"])
+                                  "graded33_two_sides_nb3", "cube9_face", "Lprism5_cut_lognormal",
+                                  "Lprism7_neumann_cut"])
 def test_host_setup_mixed_grids_match_oracle(shim, gen, name):
     m, params = _mixed_cases(gen)[name]
     o = oracle.Oracle(m, **params)
