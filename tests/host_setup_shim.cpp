@@ -12,6 +12,7 @@
 
 #include "../paper_1410_2153_gb300/csrc/internal.h"
 #include "../paper_1410_2153_gb300/csrc/keyindex.h"
+#include "../paper_1410_2153_gb300/csrc/nbsolve.h"
 #include "../paper_1410_2153_gb300/csrc/sz_row.h"
 
 using namespace asmg;
@@ -180,6 +181,17 @@ int64_t shim_get(void* hp, const char* what, int l, void* out) {
   if (w == "tri_coef") return put(L.tri_coef.data(), (int64_t)L.tri_coef.size(), 8);
   if (w == "nb_id") return put(L.nb_id.data(), (int64_t)L.nb_id.size(), 4);
   return -1;
+}
+
+// x = A^{-1} b through the near-boundary block cyclic reduction (A: CSR, m
+// rows); returns the number of level-set blocks, or -1 if the factorisation
+// failed
+int64_t shim_nbsolve(int64_t m, const int64_t* ptr, const int32_t* col, const double* val, const double* b,
+                     double* x) {
+  nb::Factor F;
+  if (!nb::factor(m, ptr, col, val, F)) return -1;
+  nb::solve(F, b, x);
+  return m ? (int64_t)F.bstart.size() - 1 : 0;
 }
 
 // positions of the queries in the sorted keys through the host setup's

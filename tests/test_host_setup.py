@@ -53,6 +53,8 @@ def shim(tmp_path_factory):
     lib.shim_get.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_void_p]
     lib.shim_keyindex.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_void_p]
+    lib.shim_nbsolve.restype = ctypes.c_int64
+    lib.shim_nbsolve.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5
     return lib
 
 
@@ -406,3 +408,77 @@ def test_host_setup_mixed_grids_match_oracle(shim, gen, name):
     m, params = _mixed_cases(gen)[name]
     o = oracle.Oracle(m, **params)
     _compare_mixed(shim, m, o, params)
+
+
+# --------------------------------------------------------------------------
+# Near-boundary solve (Algorithm 3): the library's block cyclic reduction over
+# breadth-first level sets, against dense solves
+# --------------------------------------------------------------------------
+
+def _nbsolve(lib, A, b):
+    A = sp.csr_matrix(A)
+    ptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    nbk = lib.shim_nbsolve(A.shape[0], ptr.ctypes.data, col.ctypes.data, val.ctypes.data, b.ctypes.data,
+                           x.ctypes.data)
+    return nbk, x
+
+
+@pytest.mark.parametrize("kind", ["empty", "one", "path", "grid", "two_components", "random_graph"])
+def test_nbsolve_random_spd(shim, kind):
+    rng = np.random.default_rng(11)
+    if kind == "empty":
+        A = sp.csr_matrix((0, 0))
+    elif kind == "one":
+        A = sp.csr_matrix(np.array([[3.0]]))
+    elif kind == "path":
+        A = sp.diags([-1.0, 2.5, -1.0], [-1, 0, 1], shape=(37, 37))
+    elif kind == "grid":               # a 5 x 40 strip: level sets are its cross-sections
+        T = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(40, 40))
+        S = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(5, 5))
+        A = sp.kron(sp.eye(5), T) + sp.kron(S, sp.eye(40)) + 0.01 * sp.eye(200)
+    elif kind == "two_components":
+        B1 = sp.diags([-1.0, 2.2, -1.0], [-1, 0, 1], shape=(15, 15))
+        A = sp.block_diag([B1, B1 + sp.eye(15)])
+    else:                              # SPD by diagonal dominance on a random sparse graph
+        R = sp.random(120, 120, density=0.03, random_state=3)
+        R = R + R.T
+        A = -R + sp.diags(np.asarray(abs(R).sum(axis=1)).ravel() + 0.5)
+    n = A.shape[0]
+    b = rng.standard_normal(n)
+    nbk, x = _nbsolve(shim, A, b)
+    assert nbk >= 0
+    if n:
+        ref = np.linalg.solve(A.toarray(), b)
+        assert np.abs(x - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_nbsolve_near_boundary_blocks_of_the_oracle(shim, gen, dim):
+    if dim == 2:
+        m = gen.grid2d_domain(65, 2, "hole")
+        x, y = m.verts[:, 0], m.verts[:, 1]
+        m.bflag = m.bflag.copy()
+        m.bflag[(m.bflag == 1) & (x > 0) & (x < 1) & (y > 0) & (y < 1)] = 2
+    else:
+        m = gen.grid3d_domain(7, 3, "L")
+        x = m.verts
+        m.bflag = m.bflag.copy()
+        m.bflag[(m.bflag == 1) & (x[:, 0] > 0) & (x[:, 0] < 1) & (x[:, 1] > 0) & (x[:, 1] < 1)] = 2
+    o = oracle.Oracle(m, coarse_max=8, nb_layers=2)
+    rng = np.random.default_rng(dim)
+    tried = 0
+    for l in range(o.c + 1, o.J + 1):
+        nb = o.near_boundary_set(l)
+        if nb.size == 0:
+            continue
+        A = o.A(l).tocsr()[nb][:, nb]
+        b = rng.standard_normal(nb.size)
+        nbk, xs = _nbsolve(shim, A, b)
+        ref = np.linalg.solve(A.toarray(), b)
+        assert nbk > 0 and np.abs(xs - ref).max() <= 1e-10 * np.abs(ref).max(), (l, nbk)
+        tried += 1
+    assert tried >= 2
