@@ -1449,6 +1449,14 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         if (id >= 0) L.nb_id.push_back(id);
       }
       std::sort(L.nb_id.begin(), L.nb_id.end());
+      // A_l[J,J] from the level's kept simplices, factored for the exact
+      // near-boundary solve
+      std::vector<double> pts(L.tri_key.size() * 3);
+      for (size_t k = 0; k < L.tri_key.size(); ++k) lattice_point3(tree, T.LB, L.tri_key[k], &pts[3 * k]);
+      nb::assemble_block(3, L.tri_coef.size(), pts.data(), L.tri_coef.data(), L.tri_id.data(), L.nb_id, L.nb_ptr,
+                         L.nb_col, L.nb_val);
+      if (!nb::factor((int64_t)L.nb_id.size(), L.nb_ptr.data(), L.nb_col.data(), L.nb_val.data(), L.nb_fac))
+        ASMG_FAIL(ASMG_ERR_BAD_MESH, "near-boundary block not positive definite");
     }
     if (!dgrid && !mixed) {
       for (auto& v : newnodes[l]) {

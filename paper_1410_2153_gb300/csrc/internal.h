@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/asmg.h"
+#include "nbsolve.h"
 
 namespace asmg {
 
@@ -133,6 +134,12 @@ struct AuxLevelHost {
   // mixed boundaries: the near-boundary set J_{l,j} of Algorithm 3 (aux IDs,
   // ascending); empty otherwise
   std::vector<int32_t> nb_id;
+  // mixed boundaries: A_l restricted to J_{l,j} (CSR over the positions in
+  // nb_id) and its block cyclic reduction factor
+  std::vector<int64_t> nb_ptr;
+  std::vector<int32_t> nb_col;
+  std::vector<double> nb_val;
+  nb::Factor nb_fac;
 };
 
 // What the device Scott-Zhang kernel needs of the closed tree and the finest

@@ -249,5 +249,89 @@ inline void solve(const Factor& Fz, const double* b, double* x) {
     for (int64_t q = Fz.bstart[k]; q < Fz.bstart[k + 1]; ++q) x[Fz.order[q]] = sol[k].at((int)(q - Fz.bstart[k]), 0);
 }
 
+// The block A_l[J,J] of a level operator from the level's simplices: pts
+// holds the (dim + 1) vertices of each simplex (dim coordinates each), ids
+// their aux IDs (-1: Dirichlet), coef the simplex coefficients; J = nb_id
+// (ascending aux IDs).  Entry (p, q) of the block is the sum over the
+// simplices holding nb_id[p] and nb_id[q] of coef |tau| grad lambda_p .
+// grad lambda_q (P1 stiffness); CSR with ascending columns.
+inline void assemble_block(int dim, size_t nsimp, const double* pts, const double* coef, const int32_t* ids,
+                           const std::vector<int32_t>& nb_id, std::vector<int64_t>& ptr, std::vector<int32_t>& col,
+                           std::vector<double>& val) {
+  const int nv = dim + 1;
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(nb_id.size());
+  for (size_t t = 0; t < nsimp; ++t) {
+    int32_t loc[4];
+    int nin = 0;
+    for (int v = 0; v < nv; ++v) {
+      const int32_t id = ids[nv * t + v];
+      auto it = std::lower_bound(nb_id.begin(), nb_id.end(), id);
+      loc[v] = (id >= 0 && it != nb_id.end() && *it == id) ? (int32_t)(it - nb_id.begin()) : -1;
+      nin += loc[v] >= 0;
+    }
+    if (!nin) continue;
+    const double* P = pts + (size_t)nv * dim * t;
+    double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, inv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int k = 1; k <= dim; ++k)
+      for (int r = 0; r < dim; ++r) M[r][k - 1] = P[k * dim + r] - P[r];
+    double det;
+    if (dim == 2) {
+      det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+      inv[0][0] = M[1][1] / det;
+      inv[0][1] = -M[0][1] / det;
+      inv[1][0] = -M[1][0] / det;
+      inv[1][1] = M[0][0] / det;
+    } else {
+      det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+            M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+      inv[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / det;
+      inv[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+      inv[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+      inv[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / det;
+      inv[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+      inv[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+      inv[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / det;
+      inv[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+      inv[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+    }
+    // row k-1 of M^{-1} is grad lambda_k (k >= 1); grad lambda_0 = -sum
+    double G[4][3];
+    for (int r = 0; r < dim; ++r) {
+      G[0][r] = 0;
+      for (int k = 1; k <= dim; ++k) {
+        G[k][r] = inv[k - 1][r];
+        G[0][r] -= inv[k - 1][r];
+      }
+    }
+    const double vol = std::fabs(det) / (dim == 2 ? 2.0 : 6.0);
+    for (int i = 0; i < nv; ++i) {
+      if (loc[i] < 0) continue;
+      for (int j = 0; j < nv; ++j) {
+        if (loc[j] < 0) continue;
+        double g = 0;
+        for (int r = 0; r < dim; ++r) g += G[i][r] * G[j][r];
+        rows[loc[i]].push_back({loc[j], coef[t] * vol * g});
+      }
+    }
+  }
+  ptr.assign(nb_id.size() + 1, 0);
+  col.clear();
+  val.clear();
+  for (size_t i = 0; i < rows.size(); ++i) {
+    auto& r = rows[i];
+    std::stable_sort(r.begin(), r.end(),
+                     [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) { return a.first < b.first; });
+    for (size_t k = 0; k < r.size();) {
+      size_t j = k;
+      double sum = 0;
+      while (j < r.size() && r[j].first == r[k].first) sum += r[j++].second;
+      col.push_back(r[k].first);
+      val.push_back(sum);
+      k = j;
+    }
+    ptr[i + 1] = (int64_t)col.size();
+  }
+}
+
 }  // namespace nb
 }  // namespace asmg

@@ -180,7 +180,21 @@ int64_t shim_get(void* hp, const char* what, int l, void* out) {
   if (w == "tri_id") return put(L.tri_id.data(), (int64_t)L.tri_id.size(), 4);
   if (w == "tri_coef") return put(L.tri_coef.data(), (int64_t)L.tri_coef.size(), 8);
   if (w == "nb_id") return put(L.nb_id.data(), (int64_t)L.nb_id.size(), 4);
+  if (w == "nb_ptr") return put(L.nb_ptr.data(), (int64_t)L.nb_ptr.size(), 8);
+  if (w == "nb_col") return put(L.nb_col.data(), (int64_t)L.nb_col.size(), 4);
+  if (w == "nb_val") return put(L.nb_val.data(), (int64_t)L.nb_val.size(), 8);
   return -1;
+}
+
+// x = A_l[J,J]^{-1} b with the factor the host setup stored for level l
+// (b, x over the positions in nb_id); -1 if the level has none
+int64_t shim_level_nbsolve(void* hp, int l, const double* b, double* x) {
+  AuxHost& a = ((Shim*)hp)->aux;
+  const int k = l - (a.c + 1);
+  if (k < 0 || k >= (int)a.levels.size()) return -1;
+  const AuxLevelHost& L = a.levels[k];
+  nb::solve(L.nb_fac, b, x);
+  return (int64_t)L.nb_id.size();
 }
 
 // x = A^{-1} b through the near-boundary block cyclic reduction (A: CSR, m

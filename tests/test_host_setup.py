@@ -55,6 +55,8 @@ def shim(tmp_path_factory):
                                   ctypes.c_void_p]
     lib.shim_nbsolve.restype = ctypes.c_int64
     lib.shim_nbsolve.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5
+    lib.shim_level_nbsolve.restype = ctypes.c_int64
+    lib.shim_level_nbsolve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -386,10 +388,22 @@ def _compare_mixed(lib, m, o, params):
             for k in set(int(k) for k in lk) & set(cpos):
                 row = I[pos[k]]
                 assert {int(lkc[j]): v for j, v in zip(row.indices, row.data) if v != 0} == {k: 1.0}
-            # the near-boundary set J_{l,j}
+            # the near-boundary set J_{l,j}, the block A_l[J,J] the setup assembles from its
+            # kept simplices, and the solve with the factor it stores
             nb = _get(lib, h, "nb_id", l, np.int32)
             want = o.near_boundary_set(l)
             assert sorted(pos[int(ak[q])] for q in nb) == want.tolist(), ("J_lj", l)
+            if nb.size:
+                Bh = sp.csr_matrix((_get(lib, h, "nb_val", l, np.float64), _get(lib, h, "nb_col", l, np.int32),
+                                    _get(lib, h, "nb_ptr", l, np.int64)), shape=(nb.size, nb.size)).toarray()
+                perm = np.array([pos[int(ak[q])] for q in nb])
+                Bo = Ao[np.ix_(perm, perm)]
+                assert np.abs(Bh - Bo).max() <= 1e-12 * np.abs(Bo).max(), ("A_JJ", l)
+                rhs = np.random.default_rng(l).standard_normal(nb.size)
+                xs = np.zeros(nb.size)
+                assert lib.shim_level_nbsolve(h, l, rhs.ctypes.data, xs.ctypes.data) == nb.size
+                ref = np.linalg.solve(Bo, rhs)
+                assert np.abs(xs - ref).max() <= 1e-10 * np.abs(ref).max(), ("J solve", l)
         # Scott-Zhang rows, columns mapped to the oracle's free nodes of level J
         lkJ = {int(k): i for i, k in enumerate(o.level_keys(J))}
         Pr = _get(lib, h, "P_r", 0, np.int32)
