@@ -193,6 +193,90 @@ inline bool on_seg(const GSeg& s, double x, double y) {
          std::min(s.ay, s.by) <= y && y <= std::max(s.ay, s.by);
 }
 
+// Gamma_D of a mixed problem: the fine boundary edges (edges of one element)
+// with two Dirichlet endpoints, binned by bounding box on a uniform grid of
+// gn x gn cells over the root box.
+struct GammaD2 {
+  std::vector<GSeg> seg;
+  int gn = 1;
+  double amin[2] = {0, 0}, L = 1;
+  std::vector<int64_t> start = std::vector<int64_t>(2, 0);
+  std::vector<int32_t> item;
+
+  int cell(double v, int a, double slack) const {
+    const double c = (v - amin[a]) / L * gn + slack;
+    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(c)));
+  }
+  void build(const MeshHost& mesh, const TreeResult& tree) {
+    amin[0] = tree.amin[0];
+    amin[1] = tree.amin[1];
+    L = tree.L;
+    std::vector<std::array<int32_t, 2>> ed;
+    ed.reserve(3 * mesh.ne);
+    for (int64_t e = 0; e < mesh.ne; ++e)
+      for (int k = 0; k < 3; ++k) {
+        const int32_t a = mesh.E[3 * e + k], b = mesh.E[3 * e + (k + 1) % 3];
+        ed.push_back({std::min(a, b), std::max(a, b)});
+      }
+    std::sort(ed.begin(), ed.end());
+    for (size_t i = 0; i < ed.size();) {
+      size_t j = i;
+      while (j < ed.size() && ed[j] == ed[i]) ++j;
+      const int32_t a = ed[i][0], b = ed[i][1];
+      if (j - i == 1 && mesh.bflag[a] == 1 && mesh.bflag[b] == 1)
+        seg.push_back(GSeg{mesh.X[2 * (int64_t)a], mesh.X[2 * (int64_t)a + 1], mesh.X[2 * (int64_t)b],
+                           mesh.X[2 * (int64_t)b + 1]});
+      i = j;
+    }
+    gn = std::max(1, std::min(1024, (int)std::sqrt((double)seg.size())));
+    start.assign((size_t)gn * gn + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int64_t> fill(start.begin(), start.end() - 1);
+      for (size_t q = 0; q < seg.size(); ++q) {
+        const GSeg& g = seg[q];
+        const int x0 = cell(std::min(g.ax, g.bx), 0, -1e-9), x1 = cell(std::max(g.ax, g.bx), 0, 1e-9);
+        const int y0 = cell(std::min(g.ay, g.by), 1, -1e-9), y1 = cell(std::max(g.ay, g.by), 1, 1e-9);
+        for (int y = y0; y <= y1; ++y)
+          for (int x = x0; x <= x1; ++x) {
+            const int64_t ci = (int64_t)y * gn + x;
+            if (pass == 0) start[ci + 1] += 1;
+            else item[fill[ci]++] = (int32_t)q;
+          }
+      }
+      if (pass == 0) {
+        for (size_t ci = 0; ci + 1 < start.size(); ++ci) start[ci + 1] += start[ci];
+        item.assign(start.back(), 0);
+      }
+    }
+  }
+  // f(segment) for the segments binned in the cells that the box [lo, hi]
+  // meets; stops when f returns true
+  template <class F>
+  bool any(double lox, double loy, double hix, double hiy, F&& f) const {
+    const int x0 = cell(lox, 0, -1e-9), x1 = cell(hix, 0, 1e-9);
+    const int y0 = cell(loy, 1, -1e-9), y1 = cell(hiy, 1, 1e-9);
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) {
+        const int64_t ci = (int64_t)y * gn + x;
+        for (int64_t q = start[ci]; q < start[ci + 1]; ++q)
+          if (f(seg[item[q]])) return true;
+      }
+    return false;
+  }
+  // the interior of the CCW triangle K meets Gamma_D
+  bool cuts(const double K[3][2]) const {
+    if (seg.empty()) return false;
+    const double lox = std::min({K[0][0], K[1][0], K[2][0]}), hix = std::max({K[0][0], K[1][0], K[2][0]});
+    const double loy = std::min({K[0][1], K[1][1], K[2][1]}), hiy = std::max({K[0][1], K[1][1], K[2][1]});
+    return any(lox, loy, hix, hiy, [&](const GSeg& g) { return seg_cuts_open_tri(K, g); });
+  }
+  // the point P lies on Gamma_D
+  bool on(const double* P) const {
+    if (seg.empty()) return false;
+    return any(P[0], P[1], P[0], P[1], [&](const GSeg& g) { return on_seg(g, P[0], P[1]); });
+  }
+};
+
 // f(thread, nthreads, begin, end) over contiguous ranges of [0, n), in order
 template <class F>
 void parallel_for(int64_t n, F f) {
@@ -573,84 +657,19 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     auto it = std::lower_bound(FI.begin(), FI.end(), std::pair<std::array<uint64_t, 3>, double>(tri_sorted(t), -HUGE_VAL));
     return it->second;
   };
-  // Gamma_D (mixed): the fine boundary edges (edges of one element) with two
-  // Dirichlet endpoints, binned by bounding box on a uniform grid of gn x gn
-  // cells over the root box
-  std::vector<GSeg> gd;
-  int gn = 1;
-  std::vector<int64_t> gstart(2, 0);
-  std::vector<int32_t> gitem;
-  auto gcell = [&](double v, int a, double slack) {
-    const double c = (v - tree.amin[a]) / tree.L * gn + slack;
-    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(c)));
-  };
-  if (mixed) {
-    std::vector<std::array<int32_t, 2>> ed;
-    ed.reserve(3 * mesh.ne);
-    for (int64_t e = 0; e < mesh.ne; ++e)
-      for (int k = 0; k < 3; ++k) {
-        const int32_t a = mesh.E[3 * e + k], b = mesh.E[3 * e + (k + 1) % 3];
-        ed.push_back({std::min(a, b), std::max(a, b)});
-      }
-    std::sort(ed.begin(), ed.end());
-    for (size_t i = 0; i < ed.size();) {
-      size_t j = i;
-      while (j < ed.size() && ed[j] == ed[i]) ++j;
-      const int32_t a = ed[i][0], b = ed[i][1];
-      if (j - i == 1 && mesh.bflag[a] == 1 && mesh.bflag[b] == 1)
-        gd.push_back(GSeg{mesh.X[2 * (int64_t)a], mesh.X[2 * (int64_t)a + 1], mesh.X[2 * (int64_t)b],
-                          mesh.X[2 * (int64_t)b + 1]});
-      i = j;
-    }
-    gn = std::max(1, std::min(1024, (int)std::sqrt((double)gd.size())));
-    gstart.assign((size_t)gn * gn + 1, 0);
-    for (int pass = 0; pass < 2; ++pass) {
-      std::vector<int64_t> fill(gstart.begin(), gstart.end() - 1);
-      for (size_t q = 0; q < gd.size(); ++q) {
-        const GSeg& g = gd[q];
-        const int x0 = gcell(std::min(g.ax, g.bx), 0, -1e-9), x1 = gcell(std::max(g.ax, g.bx), 0, 1e-9);
-        const int y0 = gcell(std::min(g.ay, g.by), 1, -1e-9), y1 = gcell(std::max(g.ay, g.by), 1, 1e-9);
-        for (int y = y0; y <= y1; ++y)
-          for (int x = x0; x <= x1; ++x) {
-            const int64_t cidx = (int64_t)y * gn + x;
-            if (pass == 0) gstart[cidx + 1] += 1;
-            else gitem[fill[cidx]++] = (int32_t)q;
-          }
-      }
-      if (pass == 0) {
-        for (size_t cidx = 0; cidx + 1 < gstart.size(); ++cidx) gstart[cidx + 1] += gstart[cidx];
-        gitem.assign(gstart.back(), 0);
-      }
-    }
-  }
-  // f(segment) for the Gamma_D segments binned in the cells that the box
-  // [lo, hi] meets; stops when f returns true
-  auto gd_any = [&](double lox, double loy, double hix, double hiy, auto&& f) -> bool {
-    const int x0 = gcell(lox, 0, -1e-9), x1 = gcell(hix, 0, 1e-9);
-    const int y0 = gcell(loy, 1, -1e-9), y1 = gcell(hiy, 1, 1e-9);
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        const int64_t cidx = (int64_t)y * gn + x;
-        for (int64_t q = gstart[cidx]; q < gstart[cidx + 1]; ++q)
-          if (f(gd[gitem[q]])) return true;
-      }
-    return false;
-  };
-  // the interior of lattice triangle t meets Gamma_D
+  // Gamma_D (mixed): the interior of lattice triangle t meets it; lattice
+  // node x lies on it
+  GammaD2 gdl;
+  if (mixed) gdl.build(mesh, tree);
   auto gd_cuts = [&](const std::array<uint64_t, 3>& t) -> bool {
-    if (gd.empty()) return false;
     double K[3][2];
     for (int v = 0; v < 3; ++v) lattice_point(tree, t[v], K[v]);
-    const double lox = std::min({K[0][0], K[1][0], K[2][0]}), hix = std::max({K[0][0], K[1][0], K[2][0]});
-    const double loy = std::min({K[0][1], K[1][1], K[2][1]}), hiy = std::max({K[0][1], K[1][1], K[2][1]});
-    return gd_any(lox, loy, hix, hiy, [&](const GSeg& g) { return seg_cuts_open_tri(K, g); });
+    return gdl.cuts(K);
   };
-  // lattice node x lies on Gamma_D
   auto on_gd = [&](uint64_t x) -> bool {
-    if (gd.empty()) return false;
     double P[2];
     lattice_point(tree, x, P);
-    return gd_any(P[0], P[1], P[0], P[1], [&](const GSeg& g) { return on_seg(g, P[0], P[1]); });
+    return gdl.on(P);
   };
   // mixed: a triangle belongs to T^M_l when its interior meets Omega
   // (positive covered area) and not Gamma_D

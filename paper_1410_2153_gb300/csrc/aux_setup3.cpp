@@ -459,6 +459,103 @@ inline bool on_tri(const GTri& g, const double* x, double L) {
   return (s[0] >= -tol && s[1] >= -tol && s[2] >= -tol) || (s[0] <= tol && s[1] <= tol && s[2] <= tol);
 }
 
+// Gamma_D of a mixed problem: the fine boundary faces (faces of one element)
+// with three Dirichlet vertices, binned by bounding box on gn^3 cells over
+// the root cube.
+struct GammaD3 {
+  std::vector<GTri> tri;
+  int gn = 1;
+  double amin[3] = {0, 0, 0}, L = 1;
+  std::vector<int64_t> start = std::vector<int64_t>(2, 0);
+  std::vector<int32_t> item;
+
+  int cell(double v, int a, double slack) const {
+    const double cc = (v - amin[a]) / L * gn + slack;
+    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(cc)));
+  }
+  void build(const MeshHost& mesh, const TreeResult& tree) {
+    for (int a = 0; a < 3; ++a) amin[a] = tree.amin[a];
+    L = tree.L;
+    std::vector<std::array<int32_t, 3>> fs;
+    fs.reserve(4 * mesh.ne);
+    for (int64_t e = 0; e < mesh.ne; ++e)
+      for (int k = 0; k < 4; ++k) {
+        std::array<int32_t, 3> f = {mesh.E[4 * e + (k + 1) % 4], mesh.E[4 * e + (k + 2) % 4], mesh.E[4 * e + (k + 3) % 4]};
+        std::sort(f.begin(), f.end());
+        fs.push_back(f);
+      }
+    std::sort(fs.begin(), fs.end());
+    for (size_t i = 0; i < fs.size();) {
+      size_t j = i;
+      while (j < fs.size() && fs[j] == fs[i]) ++j;
+      if (j - i == 1 && mesh.bflag[fs[i][0]] == 1 && mesh.bflag[fs[i][1]] == 1 && mesh.bflag[fs[i][2]] == 1) {
+        GTri g;
+        for (int v = 0; v < 3; ++v)
+          for (int k = 0; k < 3; ++k) g.p[v][k] = mesh.X[3 * (int64_t)fs[i][v] + k];
+        tri.push_back(g);
+      }
+      i = j;
+    }
+    gn = std::max(1, std::min(128, (int)std::cbrt((double)tri.size())));
+    start.assign((size_t)gn * gn * gn + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int64_t> fill(start.begin(), start.end() - 1);
+      for (size_t q = 0; q < tri.size(); ++q) {
+        int c0[3], c1[3];
+        for (int a = 0; a < 3; ++a) {
+          c0[a] = cell(std::min({tri[q].p[0][a], tri[q].p[1][a], tri[q].p[2][a]}), a, -1e-9);
+          c1[a] = cell(std::max({tri[q].p[0][a], tri[q].p[1][a], tri[q].p[2][a]}), a, 1e-9);
+        }
+        for (int z = c0[2]; z <= c1[2]; ++z)
+          for (int y = c0[1]; y <= c1[1]; ++y)
+            for (int x = c0[0]; x <= c1[0]; ++x) {
+              const int64_t ci = ((int64_t)z * gn + y) * gn + x;
+              if (pass == 0) start[ci + 1] += 1;
+              else item[fill[ci]++] = (int32_t)q;
+            }
+      }
+      if (pass == 0) {
+        for (size_t ci = 0; ci + 1 < start.size(); ++ci) start[ci + 1] += start[ci];
+        item.assign(start.back(), 0);
+      }
+    }
+  }
+  // f(triangle) for the triangles binned in the cells the box [lo, hi]
+  // meets; stops when f returns true
+  template <class F>
+  bool any(const double* lo, const double* hi, F&& f) const {
+    int c0[3], c1[3];
+    for (int a = 0; a < 3; ++a) {
+      c0[a] = cell(lo[a], a, -1e-9);
+      c1[a] = cell(hi[a], a, 1e-9);
+    }
+    for (int z = c0[2]; z <= c1[2]; ++z)
+      for (int y = c0[1]; y <= c1[1]; ++y)
+        for (int x = c0[0]; x <= c1[0]; ++x) {
+          const int64_t ci = ((int64_t)z * gn + y) * gn + x;
+          for (int64_t q = start[ci]; q < start[ci + 1]; ++q)
+            if (f(tri[item[q]])) return true;
+        }
+    return false;
+  }
+  // the interior of the tetrahedron K meets Gamma_D
+  bool cuts(const double K[4][3]) const {
+    if (tri.empty()) return false;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int v = 0; v < 4; ++v)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], K[v][a]);
+        hi[a] = std::max(hi[a], K[v][a]);
+      }
+    return any(lo, hi, [&](const GTri& g) { return tri_cuts_open_tet(K, g, L); });
+  }
+  // the point P lies on Gamma_D
+  bool on(const double* P) const {
+    if (tri.empty()) return false;
+    return any(P, P, [&](const GTri& g) { return on_tri(g, P, L); });
+  }
+};
+
 void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_params& prm, AuxHost& out) {
   // R18: a Neumann vertex selects the mixed grids (tetrahedra whose interior
   // meets Omega and no Gamma_D triangle)
@@ -947,99 +1044,19 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     auto it = fancov.find(tet_hash(t));
     return it == fancov.end() ? 0.0 : it->second;
   };
-  // Gamma_D (mixed): the fine boundary faces (faces of one element) with three
-  // Dirichlet vertices, binned by bounding box on gn^3 cells over the root cube
-  std::vector<GTri> gd;
-  int gn = 1;
-  std::vector<int64_t> gstart(2, 0);
-  std::vector<int32_t> gitem;
-  auto gcell = [&](double v, int a, double slack) {
-    const double cc = (v - tree.amin[a]) / tree.L * gn + slack;
-    return (int)std::min<double>(gn - 1, std::max(0.0, std::floor(cc)));
-  };
-  if (mixed) {
-    std::vector<std::array<int32_t, 3>> fs;
-    fs.reserve(4 * mesh.ne);
-    for (int64_t e = 0; e < mesh.ne; ++e)
-      for (int k = 0; k < 4; ++k) {
-        std::array<int32_t, 3> f = {mesh.E[4 * e + (k + 1) % 4], mesh.E[4 * e + (k + 2) % 4], mesh.E[4 * e + (k + 3) % 4]};
-        std::sort(f.begin(), f.end());
-        fs.push_back(f);
-      }
-    std::sort(fs.begin(), fs.end());
-    for (size_t i = 0; i < fs.size();) {
-      size_t j = i;
-      while (j < fs.size() && fs[j] == fs[i]) ++j;
-      if (j - i == 1 && mesh.bflag[fs[i][0]] == 1 && mesh.bflag[fs[i][1]] == 1 && mesh.bflag[fs[i][2]] == 1) {
-        GTri g;
-        for (int v = 0; v < 3; ++v)
-          for (int k = 0; k < 3; ++k) g.p[v][k] = mesh.X[3 * (int64_t)fs[i][v] + k];
-        gd.push_back(g);
-      }
-      i = j;
-    }
-    gn = std::max(1, std::min(128, (int)std::cbrt((double)gd.size())));
-    gstart.assign((size_t)gn * gn * gn + 1, 0);
-    for (int pass = 0; pass < 2; ++pass) {
-      std::vector<int64_t> fill(gstart.begin(), gstart.end() - 1);
-      for (size_t q = 0; q < gd.size(); ++q) {
-        int c0[3], c1[3];
-        for (int a = 0; a < 3; ++a) {
-          const double lo = std::min({gd[q].p[0][a], gd[q].p[1][a], gd[q].p[2][a]});
-          const double hi = std::max({gd[q].p[0][a], gd[q].p[1][a], gd[q].p[2][a]});
-          c0[a] = gcell(lo, a, -1e-9);
-          c1[a] = gcell(hi, a, 1e-9);
-        }
-        for (int z = c0[2]; z <= c1[2]; ++z)
-          for (int y = c0[1]; y <= c1[1]; ++y)
-            for (int x = c0[0]; x <= c1[0]; ++x) {
-              const int64_t ci = ((int64_t)z * gn + y) * gn + x;
-              if (pass == 0) gstart[ci + 1] += 1;
-              else gitem[fill[ci]++] = (int32_t)q;
-            }
-      }
-      if (pass == 0) {
-        for (size_t ci = 0; ci + 1 < gstart.size(); ++ci) gstart[ci + 1] += gstart[ci];
-        gitem.assign(gstart.back(), 0);
-      }
-    }
-  }
-  // f(triangle) for the Gamma_D triangles binned in the cells the box
-  // [lo, hi] meets; stops when f returns true
-  auto gd_any = [&](const double* lo, const double* hi, auto&& f) -> bool {
-    int c0[3], c1[3];
-    for (int a = 0; a < 3; ++a) {
-      c0[a] = gcell(lo[a], a, -1e-9);
-      c1[a] = gcell(hi[a], a, 1e-9);
-    }
-    for (int z = c0[2]; z <= c1[2]; ++z)
-      for (int y = c0[1]; y <= c1[1]; ++y)
-        for (int x = c0[0]; x <= c1[0]; ++x) {
-          const int64_t ci = ((int64_t)z * gn + y) * gn + x;
-          for (int64_t q = gstart[ci]; q < gstart[ci + 1]; ++q)
-            if (f(gd[gitem[q]])) return true;
-        }
-    return false;
-  };
-  // the interior of lattice tetrahedron t meets Gamma_D
+  // Gamma_D (mixed): the interior of lattice tetrahedron t meets it; lattice
+  // node x lies on it
+  GammaD3 gdl;
+  if (mixed) gdl.build(mesh, tree);
   auto gd_cuts = [&](const Tet& t) -> bool {
-    if (gd.empty()) return false;
-    double K[4][3], lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int v = 0; v < 4; ++v) {
-      lattice_point3(tree, T.LB, t[v], K[v]);
-      for (int a = 0; a < 3; ++a) {
-        lo[a] = std::min(lo[a], K[v][a]);
-        hi[a] = std::max(hi[a], K[v][a]);
-      }
-    }
-    return gd_any(lo, hi, [&](const GTri& g) { return tri_cuts_open_tet(K, g, tree.L); });
+    double K[4][3];
+    for (int v = 0; v < 4; ++v) lattice_point3(tree, T.LB, t[v], K[v]);
+    return gdl.cuts(K);
   };
-  // lattice node x lies on Gamma_D
   auto on_gd = [&](uint64_t x) -> bool {
-    if (gd.empty()) return false;
     double P[3];
     lattice_point3(tree, T.LB, x, P);
-    return gd_any(P, P, [&](const GTri& g) { return on_tri(g, P, tree.L); });
+    return gdl.on(P);
   };
   auto tet_inside = [&](int d, uint64_t p, bool kuhn, int q, const Tet& t) -> bool {
     if (mixed) return tet_cov(d, p, kuhn, q, t) > 1e-12 * tet_vol(t) && !gd_cuts(t);
