@@ -1093,63 +1093,9 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     }
     if (mixed && mesh.nb_layers >= 0) {
       // Algorithm 3: J_{l,j} = the free nodes of the j-th layer of triangles
-      // around Gamma_l, i.e. the nodes within j + 1 edges of a vertex of an
-      // edge of one kept triangle only (breadth-first over the level's edges)
-      std::vector<uint64_t> nodes(L.tri_key.begin(), L.tri_key.end());
-      sort_unique(nodes);
-      auto loc = [&](uint64_t k) { return (int64_t)(std::lower_bound(nodes.begin(), nodes.end(), k) - nodes.begin()); };
-      std::vector<std::array<int64_t, 2>> ed;
-      const size_t nt = L.tri_coef.size();
-      ed.reserve(3 * nt);
-      for (size_t t = 0; t < nt; ++t)
-        for (int e = 0; e < 3; ++e) {
-          const int64_t a = loc(L.tri_key[3 * t + e]), b = loc(L.tri_key[3 * t + (e + 1) % 3]);
-          ed.push_back({std::min(a, b), std::max(a, b)});
-        }
-      std::sort(ed.begin(), ed.end());
-      std::vector<int32_t> dist(nodes.size(), -1);
-      std::vector<int64_t> frontier;
-      std::vector<int64_t> adjs(nodes.size() + 1, 0);
-      std::vector<int64_t> adj;
-      std::vector<std::array<int64_t, 2>> ue;
-      for (size_t i = 0; i < ed.size();) {
-        size_t j = i;
-        while (j < ed.size() && ed[j] == ed[i]) ++j;
-        if (j - i == 1)
-          for (int v = 0; v < 2; ++v)
-            if (dist[ed[i][v]] < 0) {
-              dist[ed[i][v]] = 0;
-              frontier.push_back(ed[i][v]);
-            }
-        ue.push_back(ed[i]);
-        i = j;
-      }
-      for (auto& e : ue) {
-        adjs[e[0] + 1] += 1;
-        adjs[e[1] + 1] += 1;
-      }
-      for (size_t i = 0; i < nodes.size(); ++i) adjs[i + 1] += adjs[i];
-      adj.assign(adjs.back(), 0);
-      {
-        std::vector<int64_t> fill(adjs.begin(), adjs.end() - 1);
-        for (auto& e : ue) {
-          adj[fill[e[0]]++] = e[1];
-          adj[fill[e[1]]++] = e[0];
-        }
-      }
-      for (int r = 1; r <= mesh.nb_layers + 1 && !frontier.empty(); ++r) {
-        std::vector<int64_t> next;
-        for (int64_t v : frontier)
-          for (int64_t q = adjs[v]; q < adjs[v + 1]; ++q)
-            if (dist[adj[q]] < 0) {
-              dist[adj[q]] = r;
-              next.push_back(adj[q]);
-            }
-        frontier.swap(next);
-      }
-      for (size_t i = 0; i < nodes.size(); ++i) {
-        if (dist[i] < 0) continue;
-        const int32_t id = level_id(nodes[i], l);
+      // around Gamma_l
+      for (uint64_t k : nb::near_boundary_nodes(3, L.tri_key, mesh.nb_layers)) {
+        const int32_t id = level_id(k, l);
         if (id >= 0) L.nb_id.push_back(id);
       }
       std::sort(L.nb_id.begin(), L.nb_id.end());

@@ -1403,66 +1403,10 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
       for (auto& x : th) x.join();
     }
     if (mixed && mesh.nb_layers >= 0) {
-      // Algorithm 3: J_{l,j} = the free nodes within j + 1 edges of a vertex
-      // of a face of one kept tetrahedron only (breadth-first over the edges)
-      std::vector<uint64_t> nodes(L.tri_key.begin(), L.tri_key.end());
-      uniq(nodes);
-      auto loc = [&](uint64_t k) { return (int64_t)(std::lower_bound(nodes.begin(), nodes.end(), k) - nodes.begin()); };
-      const size_t ntet = L.tri_coef.size();
-      std::vector<std::array<int64_t, 3>> fs;
-      std::vector<std::array<int64_t, 2>> es;
-      for (size_t t = 0; t < ntet; ++t) {
-        int64_t v[4];
-        for (int k = 0; k < 4; ++k) v[k] = loc(L.tri_key[4 * t + k]);
-        for (int k = 0; k < 4; ++k) {
-          std::array<int64_t, 3> f = {v[(k + 1) % 4], v[(k + 2) % 4], v[(k + 3) % 4]};
-          std::sort(f.begin(), f.end());
-          fs.push_back(f);
-          for (int k2 = k + 1; k2 < 4; ++k2) es.push_back({std::min(v[k], v[k2]), std::max(v[k], v[k2])});
-        }
-      }
-      std::sort(fs.begin(), fs.end());
-      std::sort(es.begin(), es.end());
-      es.erase(std::unique(es.begin(), es.end()), es.end());
-      std::vector<int32_t> dist(nodes.size(), -1);
-      std::vector<int64_t> frontier;
-      for (size_t i = 0; i < fs.size();) {
-        size_t j = i;
-        while (j < fs.size() && fs[j] == fs[i]) ++j;
-        if (j - i == 1)
-          for (int k = 0; k < 3; ++k)
-            if (dist[fs[i][k]] < 0) {
-              dist[fs[i][k]] = 0;
-              frontier.push_back(fs[i][k]);
-            }
-        i = j;
-      }
-      std::vector<int64_t> adjs(nodes.size() + 1, 0), adj(2 * es.size());
-      for (auto& e : es) {
-        adjs[e[0] + 1] += 1;
-        adjs[e[1] + 1] += 1;
-      }
-      for (size_t i = 0; i < nodes.size(); ++i) adjs[i + 1] += adjs[i];
-      {
-        std::vector<int64_t> fill(adjs.begin(), adjs.end() - 1);
-        for (auto& e : es) {
-          adj[fill[e[0]]++] = e[1];
-          adj[fill[e[1]]++] = e[0];
-        }
-      }
-      for (int r = 1; r <= mesh.nb_layers + 1 && !frontier.empty(); ++r) {
-        std::vector<int64_t> next;
-        for (int64_t v : frontier)
-          for (int64_t q = adjs[v]; q < adjs[v + 1]; ++q)
-            if (dist[adj[q]] < 0) {
-              dist[adj[q]] = r;
-              next.push_back(adj[q]);
-            }
-        frontier.swap(next);
-      }
-      for (size_t i = 0; i < nodes.size(); ++i) {
-        if (dist[i] < 0) continue;
-        const int32_t id = level_id(nodes[i], l);
+      // Algorithm 3: J_{l,j} = the free nodes of the j-th layer of tetrahedra
+      // around Gamma_l
+      for (uint64_t k : nb::near_boundary_nodes(4, L.tri_key, mesh.nb_layers)) {
+        const int32_t id = level_id(k, l);
         if (id >= 0) L.nb_id.push_back(id);
       }
       std::sort(L.nb_id.begin(), L.nb_id.end());

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -247,6 +248,79 @@ inline void solve(const Factor& Fz, const double* b, double* x) {
   }
   for (int k = 0; k < nb; ++k)
     for (int64_t q = Fz.bstart[k]; q < Fz.bstart[k + 1]; ++q) x[Fz.order[q]] = sol[k].at((int)(q - Fz.bstart[k]), 0);
+}
+
+// The nodes of the near-boundary region T_(l,j) of Algorithm 3 for the kept
+// simplices of a level (nv = dim + 1 lattice keys each, in `keys`): layer 0
+// is the simplices touching the boundary of their union (the vertices of the
+// facets that belong to one simplex only), layer i those touching layer
+// i - 1.  On a conforming grid these are the nodes within j + 1 edges of a
+// boundary vertex: a breadth-first search over the simplices' edges.
+// Returns the node keys, ascending.
+inline std::vector<uint64_t> near_boundary_nodes(int nv, const std::vector<uint64_t>& keys, int layers) {
+  std::vector<uint64_t> nodes(keys);
+  std::sort(nodes.begin(), nodes.end());
+  nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+  auto loc = [&](uint64_t k) { return (int64_t)(std::lower_bound(nodes.begin(), nodes.end(), k) - nodes.begin()); };
+  const size_t ns = keys.size() / nv;
+  std::vector<std::array<int64_t, 3>> facets;  // sorted vertex positions (third -1 in 2D)
+  std::vector<std::array<int64_t, 2>> edges;
+  for (size_t t = 0; t < ns; ++t) {
+    int64_t v[4];
+    for (int k = 0; k < nv; ++k) v[k] = loc(keys[nv * t + k]);
+    for (int k = 0; k < nv; ++k) {
+      std::array<int64_t, 3> f = {-1, -1, -1};
+      int q = 0;
+      for (int w = 0; w < nv; ++w)
+        if (w != k) f[q++] = v[w];
+      std::sort(f.begin(), f.begin() + q);
+      facets.push_back(f);
+      for (int k2 = k + 1; k2 < nv; ++k2) edges.push_back({std::min(v[k], v[k2]), std::max(v[k], v[k2])});
+    }
+  }
+  std::sort(facets.begin(), facets.end());
+  std::sort(edges.begin(), edges.end());
+  edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+  std::vector<int32_t> dist(nodes.size(), -1);
+  std::vector<int64_t> frontier;
+  for (size_t i = 0; i < facets.size();) {
+    size_t j = i;
+    while (j < facets.size() && facets[j] == facets[i]) ++j;
+    if (j - i == 1)
+      for (int k = 0; k < nv - 1; ++k)
+        if (dist[facets[i][k]] < 0) {
+          dist[facets[i][k]] = 0;
+          frontier.push_back(facets[i][k]);
+        }
+    i = j;
+  }
+  std::vector<int64_t> adjs(nodes.size() + 1, 0), adj(2 * edges.size());
+  for (auto& e : edges) {
+    adjs[e[0] + 1] += 1;
+    adjs[e[1] + 1] += 1;
+  }
+  for (size_t i = 0; i < nodes.size(); ++i) adjs[i + 1] += adjs[i];
+  {
+    std::vector<int64_t> fill(adjs.begin(), adjs.end() - 1);
+    for (auto& e : edges) {
+      adj[fill[e[0]]++] = e[1];
+      adj[fill[e[1]]++] = e[0];
+    }
+  }
+  for (int r = 1; r <= layers + 1 && !frontier.empty(); ++r) {
+    std::vector<int64_t> next;
+    for (int64_t v : frontier)
+      for (int64_t q = adjs[v]; q < adjs[v + 1]; ++q)
+        if (dist[adj[q]] < 0) {
+          dist[adj[q]] = r;
+          next.push_back(adj[q]);
+        }
+    frontier.swap(next);
+  }
+  std::vector<uint64_t> out;
+  for (size_t i = 0; i < nodes.size(); ++i)
+    if (dist[i] >= 0) out.push_back(nodes[i]);
+  return out;
 }
 
 // The block A_l[J,J] of a level operator from the level's simplices: pts
