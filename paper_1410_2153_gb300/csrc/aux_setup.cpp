@@ -727,17 +727,37 @@ void build_aux_host(const MeshHost& mesh, const TreeResult& tree, const asmg_par
     for (int d = 0; d <= J; ++d)
       for (uint64_t p : BX[d])
         if (!T.split(d, p)) leaves.push_back({d, p});
+    // Every node of the closed (conforming, 2:1 balanced) grid lies in the
+    // half-open square [x0, x0 + s) x [y0, y0 + s) of exactly one leaf, as its
+    // SW corner, a hanging midpoint of its S or W edge, or the centre of its
+    // fan; the nodes on the top and right sides of the root box belong to the
+    // leaves along them.  Each leaf emits those nodes, so no key repeats.
     std::vector<std::vector<uint64_t>> part(MAX_THREADS);
+    const uint64_t top = 1ULL << T.D;
     parallel_for((int64_t)leaves.size(), [&](unsigned t, unsigned, int64_t b0, int64_t b1) {
-      std::vector<std::array<uint64_t, 3>> tri;
+      auto put = [&](uint64_t x, uint64_t y) {
+        const uint64_t k = mort(x, y);
+        if (mixed || !boundary_key(T, k)) part[t].push_back(k);
+      };
       for (int64_t q = b0; q < b1; ++q) {
+        const int d = leaves[q].first;
+        const uint64_t p = leaves[q].second;
         bool h[4];
-        T.hanging(leaves[q].first, leaves[q].second, h);
-        tri.clear();
-        box_tris(T, leaves[q].first, leaves[q].second, h, tri);
-        for (auto& x : tri)
-          for (int k = 0; k < 3; ++k)
-            if (mixed || !boundary_key(T, x[k])) part[t].push_back(x[k]);
+        T.hanging(d, p, h);
+        const uint64_t s = 1ULL << (T.D - d), m = s >> 1, x0 = compact(p) * s, y0 = compact(p >> 1) * s;
+        put(x0, y0);
+        if (h[0]) put(x0 + m, y0);
+        if (h[3]) put(x0, y0 + m);
+        if (h[0] || h[1] || h[2] || h[3]) put(x0 + m, y0 + m);
+        if (y0 + s == top) {
+          put(x0, top);
+          if (h[2]) put(x0 + m, top);
+        }
+        if (x0 + s == top) {
+          put(top, y0);
+          if (h[1]) put(top, y0 + m);
+        }
+        if (x0 + s == top && y0 + s == top) put(top, top);
       }
     });
     out.aux_key = merge_unique(part);
