@@ -28,7 +28,10 @@
 //       free colour, on the non-vanishing couplings, then three rounds of
 //       iterated greedy recolouring; the same definition is implemented
 //       independently on the device, so no colouring is ever passed from one
-//       side to the other
+//       side to the other.  Option colouring = 2 colours an auxiliary level
+//       by lattice parity when that parity 2-colours its couplings (uniform
+//       levels are bipartite: couplings across hypotenuses vanish) and by
+//       the default otherwise
 //   R18 mixed Dirichlet/Neumann boundaries (2D and 3D): contact of a simplex with
 //       Omega or Gamma_D means contact of its interior; Dirichlet auxiliary
 //       nodes lie on Gamma_D or on a triangle removed for Gamma_D
@@ -2559,6 +2562,34 @@ void order_by_colour(const std::vector<int32_t>& set, const std::vector<int32_t>
   cstart.push_back((int32_t)smooth.size());
 }
 
+// Colouring mode 2 on an auxiliary level: the lattice parity of each node of
+// the smoothing set, (X + Y [+ Z]) / h_l mod 2 with h_l the lattice spacing of
+// level l, when no two coupled nodes of the set share it (the level's
+// coupling graph is bipartite: two colour classes).  Returns false, leaving
+// `colour` untouched, when some coupled pair shares a parity.
+bool parity_colour(const Oracle& o, int l, const CSR& A, const std::vector<int32_t>& set,
+                   const std::vector<uint64_t>& key, std::vector<int32_t>& colour) {
+  const int bits = o.dim == 2 ? o.D : o.LB;
+  const uint64_t h = 1ULL << (bits - l);
+  std::vector<int32_t> par(A.nr, -1);
+  for (int32_t v : set) {
+    uint64_t q[3] = {0, 0, 0};
+    if (o.dim == 2) node_xy(key[v], q[0], q[1]);
+    else xyz3(key[v], q);
+    par[v] = (int32_t)(((q[0] + q[1] + q[2]) / h) & 1);
+  }
+  std::vector<double> diag(A.nr, 0.0);
+  for (int64_t i = 0; i < A.nr; ++i) diag[i] = A.get(i, (int32_t)i);
+  for (int32_t v : set)
+    for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+      const int32_t w = A.col[p];
+      if (par[w] >= 0 && par[w] == par[v] && coupled(A, p, v, diag)) return false;
+    }
+  colour.assign(A.nr, -1);
+  for (int32_t v : set) colour[v] = par[v];
+  return true;
+}
+
 void build_colourings(Oracle& o) {
   std::vector<int32_t> all(o.A.nr);
   std::vector<uint64_t> pk(o.A.nr);
@@ -2566,11 +2597,13 @@ void build_colourings(Oracle& o) {
     all[i] = (int32_t)i;
     pk[i] = (uint64_t)o.vertex_of_free[i];
   }
-  jp_colour(o.A, all, pk, o.fine_colour, o.prm.colouring, 3);
+  const int mode = o.prm.colouring == 2 ? 0 : o.prm.colouring;  // mode 2: JP on the fine grid
+  jp_colour(o.A, all, pk, o.fine_colour, mode, 3);
   order_by_colour(all, o.fine_colour, o.fine_smooth, o.fine_cstart);
   for (int l = o.c + 1; l <= o.J; ++l) {
     Level& L = o.lv[l];
-    jp_colour(L.A, L.smooth, L.key, L.colour, o.prm.colouring, 3);
+    if (!(o.prm.colouring == 2 && parity_colour(o, l, L.A, L.smooth, L.key, L.colour)))
+      jp_colour(L.A, L.smooth, L.key, L.colour, mode, 3);
     std::vector<int32_t> set = L.smooth;
     order_by_colour(set, L.colour, L.smooth, L.cstart);
   }

@@ -1629,3 +1629,52 @@ def test_mixed3_interpolation_cycle_and_solve(gen):
         ref = np.linalg.solve(o3.A().toarray(), b)
         u3, st, it, _ = o3.solve(b, rtol=1e-13)
         assert st == 0 and np.linalg.norm(u3 - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+# --------------------------------------------------------------------------
+# Colouring option 2: lattice parity on bipartite auxiliary levels (R10)
+# --------------------------------------------------------------------------
+
+def _check_valid_classes(A, smooth, cstart):
+    A = A.tocsr()
+    d = A.diagonal()
+    cls = np.full(A.shape[0], -1)
+    for c in range(len(cstart) - 1):
+        cls[smooth[cstart[c]:cstart[c + 1]]] = c
+    C = A.tocoo()
+    off = (C.row != C.col) & (np.abs(C.data) > 1e-12 * np.sqrt(np.abs(d[C.row] * d[C.col])))
+    r, c = C.row[off], C.col[off]
+    both = (cls[r] >= 0) & (cls[c] >= 0)
+    assert not np.any(cls[r][both] == cls[c][both])
+
+
+@pytest.mark.parametrize("case", ["graded2d", "kuhn3d"])
+def test_parity_colouring_uses_two_classes_where_bipartite(gen, case):
+    m = gen.grid2d(129, 1, graded=True) if case == "graded2d" else gen.grid3d(9, 1)
+    o = oracle.Oracle(m, colouring=2)
+    classes = []
+    for l in range(o.c + 1, o.J + 1):
+        sm, cs, _ = o.smoothing_set(l)
+        _check_valid_classes(o.A(l), sm, cs)
+        classes.append(cs.size - 1)
+    # the uniform levels are bipartite (right-isosceles triangles / Kuhn
+    # tetrahedra: no coupling across a hypotenuse), the first one at least
+    assert classes[0] == 2
+    if case == "graded2d":
+        assert max(classes) > 2              # closure transitions: odd cycles, default colouring
+    else:
+        assert all(c == 2 for c in classes)
+
+
+def test_parity_colouring_keeps_the_preconditioner_spd_and_exact(gen):
+    m = gen.grid3d(7, 2)
+    o = oracle.Oracle(m, colouring=2, coarse_max=8)
+    assert o.c < o.J
+    n = o.nfree
+    B = np.stack([o.precond(np.eye(n)[k]) for k in range(n)], 1)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    b = o.mass_apply(gen.nodal_uniform(m, 3))
+    u, st, it, _ = o.solve(b, rtol=1e-13)
+    ref = np.linalg.solve(o.A().toarray(), b)
+    assert st == 0 and np.linalg.norm(u - ref) <= 1e-11 * np.linalg.norm(ref)
