@@ -496,3 +496,125 @@ def test_nbsolve_near_boundary_blocks_of_the_oracle(shim, gen, dim):
         assert nbk > 0 and np.abs(xs - ref).max() <= 1e-10 * np.abs(ref).max(), (l, nbk)
         tried += 1
     assert tried >= 2
+
+
+# --------------------------------------------------------------------------
+# Mixed grids end to end: one V-cycle (Algorithm 3) run in numpy on the
+# library's host structures only -- level intervals phi <= l < psi, carried and
+# new nodes with their parents, the rediscretised levels from the emitted
+# simplices, the near-boundary factor -- with the oracle's colour classes,
+# against the oracle's V-cycle.  This is the composition the device V-cycle
+# will follow: a node that leaves the grid receives only its midpoint weights
+# in the restriction and is read only as a parent.
+# --------------------------------------------------------------------------
+
+def _level_matrix(lib, h, o, l, ak, dim):
+    lb = 31 if dim == 2 else o.info("LB")
+    r = o.root()
+    amin, L = np.asarray(r[:dim]), float(r[3])
+    tk = _get(lib, h, "tri_key", l, np.uint64)
+    tid = _get(lib, h, "tri_id", l, np.int32).reshape(-1, dim + 1)
+    tc = _get(lib, h, "tri_coef", l, np.float64)
+    P = np.stack([amin[a] + np.ldexp(v.astype(np.float64), -lb) * L
+                  for a, v in enumerate(_deinterleave(tk, dim, 32 if dim == 2 else 21))], -1)
+    K = _stiffness(P.reshape(-1, dim + 1, dim), tc)
+    rows, cols, vals = [], [], []
+    for t in range(len(tc)):
+        for i in range(dim + 1):
+            for j in range(dim + 1):
+                if tid[t, i] >= 0 and tid[t, j] >= 0:
+                    rows.append(tid[t, i])
+                    cols.append(tid[t, j])
+                    vals.append(K[t, i, j])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(ak.size, ak.size))
+
+
+@pytest.mark.parametrize("name", ["L17_cut_c8", "Lprism7_neumann_cut"])
+def test_mixed_vcycle_from_library_structures_matches_oracle(shim, gen, name):
+    m, params = _mixed_cases(gen)[name]
+    o = oracle.Oracle(m, **params)
+    dim = m.dim
+    segs = o.tree_levels()
+    splits = [s_[s_[:, 3] == 1, 0].astype(np.uint64) for s_ in segs]
+    while splits and len(splits[-1]) == 0:
+        splits.pop()
+    cnt = np.array([len(s_) for s_ in splits], np.int64)
+    flat = np.concatenate(splits)
+    r = o.root()
+    amin = np.ascontiguousarray(r[:dim], dtype=np.float64)
+    X = np.ascontiguousarray(m.verts, dtype=np.float64)
+    E = np.ascontiguousarray(m.elems, dtype=np.int32)
+    B = np.ascontiguousarray(m.bflag, dtype=np.uint8)
+    C = None if m.coeff is None else np.ascontiguousarray(m.coeff, dtype=np.float64)
+    h = shim.shim_build(dim, m.nv, X.ctypes.data, m.ne, E.ctypes.data, B.ctypes.data,
+                        None if C is None else C.ctypes.data, len(cnt), cnt.ctypes.data, flat.ctypes.data,
+                        amin.ctypes.data, float(r[3]), params.get("n_min", 3), params.get("coarse_max", 512), 1,
+                        params.get("nb_layers", 2))
+    try:
+        assert shim.shim_error(h) == b""
+        J, c = o.J, o.c
+        ak = _get(shim, h, "aux_key", 0, np.uint64)
+        phi, psi = _get(shim, h, "phi", 0, np.int32), _get(shim, h, "psi", 0, np.int32)
+        idx = {int(k): i for i, k in enumerate(ak)}
+        free = {l: np.where((phi <= l) & (l < psi))[0] for l in range(J + 1)}
+        A = {l: _level_matrix(shim, h, o, l, ak, dim) for l in range(c + 1, J + 1)}
+        # coarsest level: the oracle's operator on the library's IDs (checked equal elsewhere)
+        cid = _get(shim, h, "coarse_id", 0, np.int32)
+        assert np.array_equal(ak[cid], o.level_keys(c))
+        Ac = o.A(c).toarray()
+        classes = {}
+        for l in range(c + 1, J + 1):
+            sm, cs, _ = o.smoothing_set(l)
+            ids = np.array([idx[int(k)] for k in o.level_keys(l)])
+            classes[l] = [ids[sm[cs[q]:cs[q + 1]]] for q in range(cs.size - 1)]
+        newn = {l: (_get(shim, h, "new_id", l, np.int32), _get(shim, h, "new_p0", l, np.int32),
+                    _get(shim, h, "new_p1", l, np.int32)) for l in range(c + 1, J + 1)}
+        nbid = {l: _get(shim, h, "nb_id", l, np.int32) for l in range(c + 1, J + 1)}
+
+        def gs(Al, d, cls, f, u, forward):
+            for q in (cls if forward else cls[::-1]):
+                u[q] += (f[q] - Al[q] @ u) / d[q]
+
+        def vcycle(l, f):
+            u = np.zeros(ak.size)
+            if l == c:
+                u[cid] = np.linalg.solve(Ac, f[cid])
+                return u
+            Al, d = A[l], A[l].diagonal()
+            for _ in range(2):
+                gs(Al, d, classes[l], f, u, True)
+            res = f - Al @ u
+            Fl, Fc = free[l], free[l - 1]
+            fc = np.zeros(ak.size)
+            carried = np.intersect1d(Fl, Fc)
+            fc[carried] = res[carried]
+            w, p0, p1 = newn[l]
+            for a_, b_, c_ in zip(w, p0, p1):
+                if b_ >= 0:
+                    fc[b_] += 0.5 * res[a_]
+                if c_ >= 0:
+                    fc[c_] += 0.5 * res[a_]
+            e = vcycle(l - 1, fc)
+            u[carried] += e[carried]
+            for a_, b_, c_ in zip(w, p0, p1):
+                u[a_] += 0.5 * ((e[b_] if b_ >= 0 else 0.0) + (e[c_] if c_ >= 0 else 0.0))
+            J_ = nbid[l]
+            if J_.size:
+                rj = np.ascontiguousarray((f - Al @ u)[J_])
+                dj = np.zeros(J_.size)
+                assert shim.shim_level_nbsolve(h, l, rj.ctypes.data, dj.ctypes.data) == J_.size
+                u[J_] += dj
+            for _ in range(2):
+                gs(Al, d, classes[l], f, u, False)
+            u[np.setdiff1d(np.arange(ak.size), Fl)] = 0.0
+            return u
+
+        assert np.any(psi <= J)          # some node leaves the grid before the finest level
+        fJ = np.random.default_rng(4).standard_normal(o.info("nlevel", J))
+        f = np.zeros(ak.size)
+        f[[idx[int(k)] for k in o.level_keys(J)]] = fJ
+        got = vcycle(J, f)[[idx[int(k)] for k in o.level_keys(J)]]
+        want = o.vcycle(fJ)
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    finally:
+        shim.shim_free(h)
