@@ -839,6 +839,12 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     if (skip_const) pfor(mesh.ne, [&](unsigned t, int64_t b0, int64_t b1) {
       std::vector<std::pair<int, uint64_t>> lv;
       tb0[t] = b0;
+      // the last leaves looked up (elements in Morton order share most of theirs)
+      struct Hit {
+        int d = -1;
+        uint64_t p = 0;
+        int32_t leaf = -1;
+      } cache[16];
       for (int64_t k = b0; k < b1; ++k) {
         const int64_t e = order[k].second;
         TetP S;
@@ -851,13 +857,21 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
         std::memcpy(&bits, &mesh.coeff[e], 8);
         ecnt[k] = (uint32_t)lv.size();
         for (auto& lf : lv) {
-          int64_t f0;
-          int nq;
-          int32_t leaf;
-          leaf_range(lf, f0, nq, &leaf);
+          Hit& hc = cache[(lf.second ^ (uint64_t)lf.first * 0x9E3779B97F4A7C15ULL) & 15];
+          if (hc.d != lf.first || hc.p != lf.second) {
+            int64_t f0;
+            int nq;
+            leaf_range(lf, f0, nq, &hc.leaf);
+            hc.d = lf.first;
+            hc.p = lf.second;
+          }
+          const int32_t leaf = hc.leaf;
           tl[t].push_back(leaf);
-          uint64_t expect = 0;
-          if (!lval[leaf].compare_exchange_strong(expect, bits, std::memory_order_relaxed) && expect != bits)
+          // first value seen, else a second one makes the leaf mixed (an atomic
+          // write only while the leaf is still empty or not yet mixed)
+          uint64_t expect = lval[leaf].load(std::memory_order_relaxed);
+          if (expect == 0 && lval[leaf].compare_exchange_strong(expect, bits, std::memory_order_relaxed)) expect = bits;
+          if (expect != bits && !lmixed[leaf].load(std::memory_order_relaxed))
             lmixed[leaf].store(1, std::memory_order_relaxed);
           uint64_t cur = lmin[leaf].load(std::memory_order_relaxed);
           while (bits < cur && !lmin[leaf].compare_exchange_weak(cur, bits, std::memory_order_relaxed)) {
