@@ -1241,8 +1241,8 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   };
 
   auto emit_box = [&](int d, uint64_t p, int l, std::vector<int32_t>& ids, std::vector<uint64_t>& keys,
-                      std::vector<double>& coef) {
-    std::vector<Tet> kt;
+                      std::vector<double>& coef, std::vector<Tet>& kt) {  // kt: the caller's scratch
+    kt.clear();
     bool kuhn = false;
     box_tets(T, d, p, l, kt, &kuhn);
     for (size_t q = 0; q < kt.size(); ++q) {
@@ -1256,10 +1256,11 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
   };
 
   // coarsest level
+  std::vector<Tet> ckt;  // scratch
   for (int d = 0; d <= c; ++d)
     for (uint64_t p : BX[d]) {
       if (d < c && T.split(d, p)) continue;
-      emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef);
+      emit_box(d, p, c, out.coarse_tri_id, out.coarse_tri_key, out.coarse_tri_coef, ckt);
     }
   for (auto id : out.coarse_tri_id)
     if (id >= 0) out.coarse_id.push_back(id);
@@ -1393,7 +1394,8 @@ void build_aux_host3(const MeshHost& mesh, const TreeResult& tree, const asmg_pa
     std::vector<std::vector<uint64_t>> keys(nthr);
     std::vector<std::vector<double>> coefs(nthr);
     pfor((int64_t)rel.size(), [&](unsigned t, int64_t b0, int64_t b1) {
-      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t]);
+      std::vector<Tet> kt;  // scratch of this thread
+      for (int64_t q = b0; q < b1; ++q) emit_box(rel[q].first, rel[q].second, l, ids[t], keys[t], coefs[t], kt);
     });
     // concatenate in thread order: sizes first, then one copy per part in parallel
     {
