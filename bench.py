@@ -164,14 +164,53 @@ def _oracle_sample(workload: str):
     return "graded257", {}
 
 
-def cpu_baseline(workload: str = "graded2049"):
+def _baseline_sample(workload: str):
+    """The cpu_baseline sample (larger than the reference arm's per-step
+    sample): 2D the graded mesh at 513^2 (261,121 dofs, one solve is about
+    10 s of single-core work), 3D the Kuhn cube grid at 49^3."""
+    if workload.startswith("kuhn"):
+        return "kuhn49", {"n_min": 6}
+    return "graded513", {}
+
+
+def host_cpu():
+    """Host core count and CPU model (for the CPU baseline record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                k = ln.split(":")[0].strip().lower()
+                if model is None and k in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return os.cpu_count(), model
+
+
+def cpu_baseline(workload: str = "graded2049", sample: str = None, min_s: float = 8.0):
     """The oracle as it stands (single thread) on a bounded sample of the same
-    workload family (2D: the graded mesh at 257^2; 3D: the Kuhn cube grid at
-    33^3), solves repeated for at least 2 s, setup excluded."""
+    workload family, solves repeated for at least `min_s` seconds, setup
+    timed separately."""
     import oracle
-    name, opts = _oracle_sample(workload)
+    name, opts = _baseline_sample(workload)
+    if sample:
+        name = sample
     m, f = _workload(name, 1)
+    ts = time.perf_counter()
     o = oracle.Oracle(m, **opts)
+    t_setup = time.perf_counter() - ts
     b = o.mass_apply(f)
     t = time.perf_counter()
     k = 0
@@ -179,11 +218,13 @@ def cpu_baseline(workload: str = "graded2049"):
         u, st, it, _ = o.solve(b, rtol=RTOL)
         k += 1
         dt = time.perf_counter() - t
-        if dt >= 2.0:
+        if dt >= min_s:
             break
+    nproc, model = host_cpu()
     return {"value": k * o.nfree / dt, "unit": "dofs/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle PCG solve of {name} ({o.nfree} dofs, {it} iterations, {k} solves in {dt:.2f} s; "
-                      f"setup excluded)"}
+            "host_nproc": nproc, "host_cpu": model,
+            "sample": f"oracle PCG solve of {name} ({o.nfree} dofs, {it} iterations, {k} solve(s) in {dt:.2f} s, "
+                      f"single thread; oracle setup {t_setup:.1f} s, not counted)"}
 
 
 def run_reference(args):
@@ -211,7 +252,8 @@ def run_reference(args):
             "config": {"workload": name, "nfree": o.nfree, "iterations": its,
                        "note": f"CPU oracle, bounded sample of the {args.workload} workload family"},
             "cpu_baseline": {"value": val, "unit": "dofs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{name}, {o.nfree} dofs"},
+                             "host_nproc": host_cpu()[0], "host_cpu": host_cpu()[1],
+                             "sample": f"{name}, {o.nfree} dofs, {its} iterations per solve, single thread"},
             "e2e": {"value": val, "unit": "dofs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -350,6 +392,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of the CUDA graph (ncu runs)")
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--batch-count", type=int, default=256, help="problems of the batch workload")
+    ap.add_argument("--cpu-sample", default=None, help="workload of the CPU baseline (default: graded513 / kuhn49)")
     args = ap.parse_args()
     if args.workload == "batch256":
         run_batch(args)
@@ -488,7 +531,7 @@ def main():
                         "iterations": int(np.median(r64["its"]))}
         line["mixed_vs_fp64_speedup"] = ms64 / ms_step
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
     for sol in solvers.values():

@@ -21,6 +21,10 @@
  *   - Indices are 0-based.  Vertex arrays are indexed by vertex number.
  *   - The handle owns all device memory it allocates; amg_destroy frees it.
  *     A handle may be used from one host thread at a time.
+ *   - Every reduction on the device (dot products, norms, the mass product)
+ *     runs in a fixed order: with the same inputs and parameters every
+ *     result is the same bit for bit from run to run, so no separate
+ *     "deterministic" mode exists.
  */
 #ifndef ASMG_H
 #define ASMG_H
@@ -121,7 +125,11 @@ int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* itera
 /*
  * b = M f_h: the consistent P1 mass matrix applied to nodal values f [nv]
  * (float64), result b [nv] with 0 at Dirichlet vertices.  This is the load
- * vector <f, phi_i> of eq. bilinearform for the interpolant f_h.
+ * vector <f, phi_i> of eq. bilinearform for the interpolant f_h.  Each entry
+ * is gathered over the elements around its vertex in ascending element order
+ * (no atomics), so the result is the same bit for bit on every run.  The
+ * first call builds that vertex-to-element list (device memory owned by the
+ * handle).
  */
 int amg_mass_apply(asmg_handle h, const double* f_nodal, double* b, void* stream);
 
@@ -145,6 +153,21 @@ int amg_spmv(asmg_handle h, const double* x, double* y, void* stream);
  * K_e^(1) the element stiffness for a_e = 1 (not in the paper).
  */
 int amg_element_grad(asmg_handle h, const double* u, const double* lambda, double* dL_dcoeff, void* stream);
+
+/*
+ * The same sensitivity with respect to log-coefficients: for a = exp(g) (see
+ * amg_set_log_coefficients), dL_dg[e] = a_e dL/da_e = -a_e lambda_e^T K_e^(1) u_e,
+ * with a_e the handle's current coefficient (1 when none was given).  The
+ * chain-rule factor is applied in the same kernel (not in the paper).
+ */
+int amg_element_grad_log(asmg_handle h, const double* u, const double* lambda, double* dL_dg, void* stream);
+
+/*
+ * Set the element coefficients to a_e = exp(g_e), g float64 [ne] finite, and
+ * rebuild as amg_update_coefficients does (the log-parametrisation of a
+ * coefficient field; not in the paper).
+ */
+int amg_set_log_coefficients(asmg_handle h, const double* g, void* stream);
 
 /*
  * Replace the element coefficients (float64 [ne], > 0) and rebuild every
@@ -264,14 +287,17 @@ void amg_batch_destroy(asmg_batch batch);
  *          rejected (ASMG_ERR_INVALID_ARG): staging them would need memory.
  *          Entries at Dirichlet vertices are ignored.
  *   out    float64 [2], host or device: ||b - A u||_2 and ||b||_2.
- * Scratch: one fixed 64 KB array inside the library (a static device array),
- * which every GPU that loads the library keeps until the process exits.  All
- * calls on a device share it and it keeps the last call's contents; calls
- * that overlap on the GPU (e.g. from two streams) race on it.  The first call
- * on a device looks up the array's device address; make that first call
- * before any stream capture.  Meshes with more than 8,388,608 padded fine
- * rows are rejected with ASMG_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or
- * other allocating routine is called.
+ * Scratch: one fixed 64 KB array inside the library (a static device array).
+ * It is created on a device when amg_setup first runs there: amg_setup loads
+ * the library module that holds it and looks up its device address, so under
+ * lazy module loading too the memory appears at setup, never during a call
+ * of this function.  It then stays until the process exits.  All calls on a
+ * device share it and it keeps the last call's contents; calls that overlap
+ * on the GPU (e.g. from two streams) race on it.  A call made while a device
+ * other than the handle's is current would look the address up itself; make
+ * every call with the handle's device current.  Meshes with more than
+ * 8,388,608 padded fine rows are rejected with ASMG_ERR_INVALID_ARG.  No
+ * cudaMalloc, cudaFree or other allocating routine is called.
  */
 int amg_residual_norm_noalloc(asmg_handle h, const double* b, const double* u, double* out, void* stream);
 

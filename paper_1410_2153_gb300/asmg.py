@@ -70,6 +70,8 @@ def lib():
         L.amg_spmv.argtypes = [vp, vp, vp, vp]
         L.amg_element_grad.argtypes = [vp, vp, vp, vp, vp]
         L.amg_update_coefficients.argtypes = [vp, vp, vp]
+        L.amg_element_grad_log.argtypes = [vp, vp, vp, vp, vp]
+        L.amg_set_log_coefficients.argtypes = [vp, vp, vp]
         L.amg_info.argtypes = [vp, i32, i32, ctypes.POINTER(i64)]
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
         L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
@@ -83,7 +85,8 @@ def lib():
         L.amg_destroy.restype = None
         L.amg_last_error.restype = ctypes.c_char_p
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
-                     "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_info", "amg_export",
+                     "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_element_grad_log",
+                     "amg_set_log_coefficients", "amg_info", "amg_export",
                      "amg_profile", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -111,6 +114,19 @@ def _ptr(a):
     return ctypes.c_void_p(a.data_ptr())
 
 
+def _stream(stream, *arrays):
+    """The stream to enqueue on: the caller's, else torch's current stream of
+    the first CUDA tensor among `arrays` (so that work queued there on the
+    inputs comes first), else NULL (the legacy default stream)."""
+    if stream is not None:
+        return stream
+    for a in arrays:
+        if a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False):
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
 def asmg_default_params() -> asmg_params:
     p = asmg_params()
     _check(lib().asmg_default_params(ctypes.byref(p)))
@@ -128,29 +144,38 @@ def amg_setup(dim, nv, vertices, ne, elements, boundary, coeff, params: Optional
 
 def amg_solve(h, b, u, rtol: float, res_history: Optional[np.ndarray] = None, stream=None):
     it = ctypes.c_int(0)
-    rc = _check(lib().amg_solve(h, _ptr(b), _ptr(u), float(rtol), ctypes.byref(it), _ptr(res_history), stream),
+    rc = _check(lib().amg_solve(h, _ptr(b), _ptr(u), float(rtol), ctypes.byref(it), _ptr(res_history),
+                            _stream(stream, b, u)),
                 allow=(ASMG_OK, ASMG_NOT_CONVERGED))
     return rc, it.value
 
 
 def amg_mass_apply(h, f, b, stream=None):
-    _check(lib().amg_mass_apply(h, _ptr(f), _ptr(b), stream))
+    _check(lib().amg_mass_apply(h, _ptr(f), _ptr(b), _stream(stream, f, b)))
 
 
 def amg_precond_apply(h, r, z, stream=None):
-    _check(lib().amg_precond_apply(h, _ptr(r), _ptr(z), stream))
+    _check(lib().amg_precond_apply(h, _ptr(r), _ptr(z), _stream(stream, r, z)))
 
 
 def amg_spmv(h, x, y, stream=None):
-    _check(lib().amg_spmv(h, _ptr(x), _ptr(y), stream))
+    _check(lib().amg_spmv(h, _ptr(x), _ptr(y), _stream(stream, x, y)))
 
 
 def amg_element_grad(h, u, lam, g, stream=None):
-    _check(lib().amg_element_grad(h, _ptr(u), _ptr(lam), _ptr(g), stream))
+    _check(lib().amg_element_grad(h, _ptr(u), _ptr(lam), _ptr(g), _stream(stream, u, lam, g)))
+
+
+def amg_element_grad_log(h, u, lam, g, stream=None):
+    _check(lib().amg_element_grad_log(h, _ptr(u), _ptr(lam), _ptr(g), _stream(stream, u, lam, g)))
+
+
+def amg_set_log_coefficients(h, g, stream=None):
+    _check(lib().amg_set_log_coefficients(h, _ptr(g), _stream(stream, g)))
 
 
 def amg_update_coefficients(h, coeff, stream=None):
-    _check(lib().amg_update_coefficients(h, _ptr(coeff), stream))
+    _check(lib().amg_update_coefficients(h, _ptr(coeff), _stream(stream, coeff)))
 
 
 def amg_info(h, what, level: int = 0) -> int:
@@ -186,16 +211,19 @@ def amg_profile(h, b, rtol: float, stream=None):
     """Per kernel class: dict(launches, ms, bytes) of one event-timed solve, and the iterations."""
     out = np.zeros(3 * len(PROF_CLASSES))
     it = ctypes.c_int(0)
-    _check(lib().amg_profile(h, _ptr(b), float(rtol), _ptr(out), ctypes.byref(it), stream))
+    _check(lib().amg_profile(h, _ptr(b), float(rtol), _ptr(out), ctypes.byref(it), _stream(stream, b)))
     res = {c: dict(launches=int(out[3 * k]), ms=float(out[3 * k + 1]), bytes=float(out[3 * k + 2]))
            for k, c in enumerate(PROF_CLASSES)}
     return res, it.value
 
 
 def amg_residual_norm_noalloc(h, b, u, stream=None):
-    """(||b - A u||, ||b||) over free dofs; b and u must be CUDA tensors.  Allocates nothing."""
+    """(||b - A u||, ||b||) over free dofs; b and u must be CUDA tensors.  Allocates nothing.
+
+    Runs on `stream`, by default torch's current stream of b, after the work
+    already queued there."""
     out = np.zeros(2)
-    _check(lib().amg_residual_norm_noalloc(h, _ptr(b), _ptr(u), _ptr(out), stream))
+    _check(lib().amg_residual_norm_noalloc(h, _ptr(b), _ptr(u), _ptr(out), _stream(stream, b, u)))
     return float(out[0]), float(out[1])
 
 
@@ -296,4 +324,9 @@ class Solver:
     def element_grad(self, u, lam):
         g = np.empty(self.ne) if isinstance(u, np.ndarray) else u.new_empty(self.ne)
         amg_element_grad(self.h, u, lam, g)
+        return g
+
+    def element_grad_log(self, u, lam):
+        g = np.empty(self.ne) if isinstance(u, np.ndarray) else u.new_empty(self.ne)
+        amg_element_grad_log(self.h, u, lam, g)
         return g

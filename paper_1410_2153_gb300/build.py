@@ -42,8 +42,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
             continue
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", *EXTRA.get(src, []), "-Xcompiler", "-fPIC,-O2", "-c",
                path, "-o", obj]
-        if src.endswith(".cpp"):
-            cmd[1:1] = ["-x", "cu"] if False else []
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -190,44 +190,61 @@ HostCSR coo_to_csr(int64_t m, DBuf<uint64_t>& key, DBuf<double>& val, int64_t nr
   return A;
 }
 
-// consistent P1 mass matrix applied to nodal values: b_i += |T|/12 (f_i + sum_j f_j)
-__global__ void k_mass(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
-                       const double* __restrict__ f, double* __restrict__ b) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne) return;
-  int32_t v0 = E[3 * t], v1 = E[3 * t + 1], v2 = E[3 * t + 2];
-  double area = 0.5 * ((X[2 * v1] - X[2 * v0]) * (X[2 * v2 + 1] - X[2 * v0 + 1]) -
-                       (X[2 * v2] - X[2 * v0]) * (X[2 * v1 + 1] - X[2 * v0 + 1]));
-  double sum = f[v0] + f[v1] + f[v2];
-  double w = area / 12.0;
-  atomicAdd(&b[v0], w * (sum + f[v0]));
-  atomicAdd(&b[v1], w * (sum + f[v1]));
-  atomicAdd(&b[v2], w * (sum + f[v2]));
-}
-
-// consistent P1 mass on tetrahedra: b_i += |T|/20 (f_i + sum_j f_j)
-__global__ void k_mass3(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
-                        const double* __restrict__ f, double* __restrict__ b) {
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= ne) return;
-  int32_t v[4];
-  double P[4][3];
-  for (int k = 0; k < 4; ++k) {
-    v[k] = E[4 * t + k];
-    for (int r = 0; r < 3; ++r) P[k][r] = X[3 * (int64_t)v[k] + r];
+// consistent P1 mass matrix applied to nodal values, gathered per vertex:
+// b_v = sum over the elements T around v (ascending element index) of
+// |T|/12 (f_v + sum_j f_j) in 2D, |T|/20 (f_v + sum_j f_j) in 3D.  Each sum
+// runs in a fixed order, so the result is the same bit for bit on every run
+// (no atomics).  v2e: element indices around each vertex (CSR by vertex).
+__global__ void k_mass_gather(int64_t nv, const int64_t* __restrict__ v2e_ptr, const int32_t* __restrict__ v2e,
+                              const double* __restrict__ X, const int32_t* __restrict__ E,
+                              const double* __restrict__ f, double* __restrict__ b) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  double acc = 0;
+  const double fv = f[v];
+  for (int64_t p = v2e_ptr[v]; p < v2e_ptr[v + 1]; ++p) {
+    const int64_t t = v2e[p];
+    const int32_t v0 = E[3 * t], v1 = E[3 * t + 1], v2 = E[3 * t + 2];
+    const double area = 0.5 * ((X[2 * v1] - X[2 * v0]) * (X[2 * v2 + 1] - X[2 * v0 + 1]) -
+                               (X[2 * v2] - X[2 * v0]) * (X[2 * v1 + 1] - X[2 * v0 + 1]));
+    const double sum = f[v0] + f[v1] + f[v2];
+    acc += area / 12.0 * (sum + fv);
   }
-  double e[3][3];
-  for (int k = 0; k < 3; ++k)
-    for (int r = 0; r < 3; ++r) e[k][r] = P[k + 1][r] - P[0][r];
-  const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) + e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
-                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
-  const double w = det / 120.0;  // |T| / 20
-  const double sum = f[v[0]] + f[v[1]] + f[v[2]] + f[v[3]];
-  for (int k = 0; k < 4; ++k) atomicAdd(&b[v[k]], w * (sum + f[v[k]]));
+  b[v] = acc;
 }
 
+__global__ void k_mass_gather3(int64_t nv, const int64_t* __restrict__ v2e_ptr, const int32_t* __restrict__ v2e,
+                               const double* __restrict__ X, const int32_t* __restrict__ E,
+                               const double* __restrict__ f, double* __restrict__ b) {
+  const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  double acc = 0;
+  const double fv = f[v];
+  for (int64_t p = v2e_ptr[v]; p < v2e_ptr[v + 1]; ++p) {
+    const int64_t t = v2e[p];
+    int32_t w[4];
+    double P[4][3];
+    for (int k = 0; k < 4; ++k) {
+      w[k] = E[4 * t + k];
+      for (int r = 0; r < 3; ++r) P[k][r] = X[3 * (int64_t)w[k] + r];
+    }
+    double e[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) e[k][r] = P[k + 1][r] - P[0][r];
+    const double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) +
+                       e[0][1] * (e[1][2] * e[2][0] - e[1][0] * e[2][2]) +
+                       e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    const double sum = f[w[0]] + f[w[1]] + f[w[2]] + f[w[3]];
+    acc += det / 120.0 * (sum + fv);  // |T| / 20
+  }
+  b[v] = acc;
+}
+
+// dL/da_e = -lambda_e^T K_e^(1) u_e, times scale[e] when scale is given
+// (scale = a: the derivative with respect to g_e for a = exp(g))
 __global__ void k_elem_grad3(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
-                             const double* __restrict__ u, const double* __restrict__ lam, double* __restrict__ g) {
+                             const double* __restrict__ u, const double* __restrict__ lam,
+                             const double* __restrict__ scale, double* __restrict__ g) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= ne) return;
   double P[4][3], ue[4], le[4];
@@ -242,12 +259,13 @@ __global__ void k_elem_grad3(int64_t ne, const double* __restrict__ X, const int
   double s = 0;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) s += le[i] * K[i][j] * ue[j];
-  g[t] = -s;
+  g[t] = scale ? -(scale[t] * s) : -s;
 }
 
-// dL/da_e = -lambda_e^T K_e^(1) u_e
+// dL/da_e = -lambda_e^T K_e^(1) u_e (times scale[e] when given), triangles
 __global__ void k_elem_grad(int64_t ne, const double* __restrict__ X, const int32_t* __restrict__ E,
-                            const double* __restrict__ u, const double* __restrict__ lam, double* __restrict__ g) {
+                            const double* __restrict__ u, const double* __restrict__ lam,
+                            const double* __restrict__ scale, double* __restrict__ g) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= ne) return;
   double x[3], y[3], ue[3], le[3];
@@ -263,7 +281,7 @@ __global__ void k_elem_grad(int64_t ne, const double* __restrict__ X, const int3
   double s = 0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) s += le[i] * K[i][j] * ue[j];
-  g[t] = -s;
+  g[t] = scale ? -(scale[t] * s) : -s;
 }
 
 // splitmix64 (published constants of Steele, Lea and Flood / Vigna).
@@ -376,22 +394,21 @@ HostCSR assemble_mesh(int dim, int64_t ne, const double* dX, const int32_t* dE, 
   return coo_to_csr(m, key, val, nfree, s);
 }
 
-void mass_apply_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
-                    cudaStream_t s) {
-  ASMG_CUDA(cudaMemsetAsync(db, 0, 8 * nv, s));
+void mass_apply_gpu(int dim, int64_t nv, const int64_t* v2e_ptr, const int32_t* v2e, const double* dX,
+                    const int32_t* dE, const double* df, double* db, cudaStream_t s) {
   if (dim == 2)
-    k_mass<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, df, db);
+    k_mass_gather<<<nblk(nv), 256, 0, s>>>(nv, v2e_ptr, v2e, dX, dE, df, db);
   else
-    k_mass3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, df, db);
+    k_mass_gather3<<<nblk(nv), 256, 0, s>>>(nv, v2e_ptr, v2e, dX, dE, df, db);
   ASMG_CUDA(cudaGetLastError());
 }
 
 void element_grad_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl,
-                      double* dg, cudaStream_t s) {
+                      const double* dscale, double* dg, cudaStream_t s) {
   if (dim == 2)
-    k_elem_grad<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dg);
+    k_elem_grad<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dscale, dg);
   else
-    k_elem_grad3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dg);
+    k_elem_grad3<<<nblk(ne), 256, 0, s>>>(ne, dX, dE, du, dl, dscale, dg);
   ASMG_CUDA(cudaGetLastError());
 }
 

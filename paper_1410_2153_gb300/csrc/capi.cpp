@@ -717,6 +717,9 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   }
   build_all(*h, s);
   h->bytes_iter = prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
+  // load the allocation-free entry point's module (and so its fixed scratch
+  // array) on this device now, so that its calls never create memory
+  noalloc_scratch_for_current_device();
   h->stats.t_total = now() - t0;
   *out = h.release();
   return ASMG_OK;
@@ -902,8 +905,22 @@ int amg_mass_apply(asmg_handle h, const double* f, double* bout, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv;
+  if (!h->d_v2e_ptr.p) {
+    // elements around each vertex, ascending element index (counting sort)
+    const MeshHost& m = h->mesh;
+    const int nvert = m.dim + 1;
+    std::vector<int64_t> ptr(nv + 1, 0);
+    for (int64_t k = 0; k < m.ne * nvert; ++k) ++ptr[m.E[k] + 1];
+    for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
+    std::vector<int32_t> el(m.ne * nvert);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < m.ne; ++e)
+      for (int k = 0; k < nvert; ++k) el[fill[m.E[e * nvert + k]]++] = (int32_t)e;
+    h->d_v2e_ptr.upload(ptr, s);
+    h->d_v2e.upload(el, s);
+  }
   copy_in(S0.vb.p, f, nv, s);
-  mass_apply_gpu(h->mesh.dim, h->mesh.ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, nv, s);
+  mass_apply_gpu(h->mesh.dim, nv, h->d_v2e_ptr.p, h->d_v2e.p, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, s);
   gather_rows(*h, S0.vu.p, S0.q.p, s);
   scatter_rows(*h, S0.q.p, false, S0.vu.p, s);  // zero at Dirichlet vertices
   copy_out(bout, S0.vu.p, nv, s);
@@ -947,10 +964,12 @@ int amg_spmv(asmg_handle h, const double* x, double* y, void* stream) {
   API_END
 }
 
-int amg_element_grad(asmg_handle h, const double* u, const double* lambda, double* g, void* stream) {
-  API_BEGIN
-  if (!h || !u || !lambda || !g) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+// dL/da (scale = NULL) or dL/dg = a dL/da for a = exp(g) (scale = the coefficients)
+void element_grad_common(asmg_handle h, const double* u, const double* lambda, double* g, bool log_coeff,
+                         cudaStream_t s) {
   Slot& S0 = h->slot0();
   const int64_t nv = h->mesh.nv, ne = h->mesh.ne;
   // Dirichlet entries are treated as 0: gather/scatter through the free rows
@@ -967,9 +986,50 @@ int amg_element_grad(asmg_handle h, const double* u, const double* lambda, doubl
     dg.alloc(ne);
     out = dg.p;
   }
-  element_grad_gpu(h->mesh.dim, ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, out, s);
+  element_grad_gpu(h->mesh.dim, ne, h->dX.p, h->dE.p, S0.vb.p, S0.vu.p, log_coeff ? h->dCoeff.p : nullptr, out, s);
   if (!dev) ASMG_CUDA(cudaMemcpyAsync(g, dg.p, 8 * ne, cudaMemcpyDeviceToHost, s));
   ASMG_CUDA(cudaStreamSynchronize(s));
+}
+
+void set_coefficients(asmg_handle h, std::vector<double> c, cudaStream_t s) {
+  for (int64_t e = 0; e < h->mesh.ne; ++e)
+    if (!(c[e] > 0) || !std::isfinite(c[e]))
+      ASMG_FAIL(ASMG_ERR_BAD_MESH, "coefficient of element %lld is not positive and finite", (long long)e);
+  h->mesh.coeff = std::move(c);
+  h->dCoeff.upload(h->mesh.coeff, s);
+  build_all(*h, s);
+  h->bytes_iter = h->prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
+}
+}  // namespace
+
+extern "C" {
+
+int amg_element_grad(asmg_handle h, const double* u, const double* lambda, double* g, void* stream) {
+  API_BEGIN
+  if (!h || !u || !lambda || !g) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  element_grad_common(h, u, lambda, g, false, (cudaStream_t)stream);
+  return ASMG_OK;
+  API_END
+}
+
+int amg_element_grad_log(asmg_handle h, const double* u, const double* lambda, double* g, void* stream) {
+  API_BEGIN
+  if (!h || !u || !lambda || !g) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  element_grad_common(h, u, lambda, g, !h->mesh.coeff.empty(), (cudaStream_t)stream);
+  return ASMG_OK;
+  API_END
+}
+
+int amg_set_log_coefficients(asmg_handle h, const double* gl, void* stream) {
+  API_BEGIN
+  if (!h || !gl) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<double> c = to_host(gl, h->mesh.ne, s);
+  for (auto& x : c) {
+    if (!std::isfinite(x)) ASMG_FAIL(ASMG_ERR_BAD_MESH, "log-coefficient is not finite");
+    x = std::exp(x);
+  }
+  set_coefficients(h, std::move(c), s);
   return ASMG_OK;
   API_END
 }
@@ -978,14 +1038,7 @@ int amg_update_coefficients(asmg_handle h, const double* coeff, void* stream) {
   API_BEGIN
   if (!h || !coeff) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<double> c = to_host(coeff, h->mesh.ne, s);
-  for (int64_t e = 0; e < h->mesh.ne; ++e)
-    if (!(c[e] > 0) || !std::isfinite(c[e]))
-      ASMG_FAIL(ASMG_ERR_BAD_MESH, "coefficient of element %lld is not positive and finite", (long long)e);
-  h->mesh.coeff = c;
-  h->dCoeff.upload(c, s);
-  build_all(*h, s);
-  h->bytes_iter = h->prm.precision == ASMG_MIXED ? iteration_bytes(*h, h->p32) : iteration_bytes(*h, h->p64);
+  set_coefficients(h, to_host(coeff, h->mesh.ne, s), s);
   return ASMG_OK;
   API_END
 }

@@ -68,6 +68,8 @@ struct asmg_s {
   asmg::MeshHost mesh;
   asmg::DBuf<double> dX, dCoeff;
   asmg::DBuf<int32_t> dE;
+  asmg::DBuf<int64_t> d_v2e_ptr;  // elements around each vertex (CSR, ascending element), for the mass product
+  asmg::DBuf<int32_t> d_v2e;
   asmg::TreeResult tree;
   asmg::AuxHost aux;
 
@@ -105,6 +107,7 @@ namespace asmg {
 void setup_solve(asmg_s& h, cudaStream_t s);
 int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out);
 // noalloc.cu
+double* noalloc_scratch_for_current_device();
 void residual_norm_noalloc(asmg_s& h, const double* b, const double* u, double* out, cudaStream_t s);
 int run_solve(asmg_s& h, Slot& S, double rtol, cudaStream_t s);
 Slot& add_slot(asmg_s& h, cudaStream_t s);
@@ -117,8 +120,8 @@ void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cuda
 // assemble.cu
 HostCSR assemble_mesh(int dim, int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree,
                       const double* dCoef, int64_t nfree, cudaStream_t s);
-void mass_apply_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* df, double* db, int64_t nv,
-                    cudaStream_t s);
+void mass_apply_gpu(int dim, int64_t nv, const int64_t* v2e_ptr, const int32_t* v2e, const double* dX,
+                    const int32_t* dE, const double* df, double* db, cudaStream_t s);
 void element_grad_gpu(int dim, int64_t ne, const double* dX, const int32_t* dE, const double* du, const double* dl,
-                      double* dg, cudaStream_t s);
+                      const double* dscale, double* dg, cudaStream_t s);
 }  // namespace asmg

@@ -10,6 +10,8 @@
 // output, and this entry point touches no allocator at all.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "handle.h"
 
 namespace asmg {
@@ -25,14 +27,17 @@ constexpr int NA_RESULT = NA_PARTIALS;        // two doubles: ||b - A u||, ||b||
 constexpr int NA_TICKET = NA_PARTIALS + 2;    // one 64-bit counter
 constexpr int NA_SCRATCH_DOUBLES = NA_PARTIALS + 4;
 
-// The scratch: 8,196 doubles (about 64 KB).  Every GPU that loads the library
-// holds it until the process exits.  All calls share it.
+// The scratch: 8,196 doubles (about 64 KB).  It comes into existence on a
+// device when this module is loaded there, which amg_setup forces (see
+// noalloc_scratch_for_current_device), and stays until the process exits.
+// All calls share it.
 static __device__ __align__(256) double g_noalloc_scratch[NA_SCRATCH_DOUBLES];
 
 // Device addresses of g_noalloc_scratch, one per device (host code may not use
-// the symbol itself as a device pointer).
+// the symbol itself as a device pointer).  Atomic: two host threads may make
+// their first call on a device at the same time.
 constexpr int NA_MAX_DEVICES = 64;
-double* g_scratch_ptr[NA_MAX_DEVICES] = {};
+std::atomic<double*> g_scratch_ptr[NA_MAX_DEVICES] = {};
 
 __device__ __forceinline__ double na_block_sum(double v, double* sh) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -113,17 +118,23 @@ bool device_pointer(const void* p) {
 }  // namespace
 
 // Set-up once per device, with that device current: the device address of
-// the scratch array.
+// the scratch array.  Under lazy module loading the first address lookup (or
+// launch) is what loads this module on the device and so creates the array;
+// amg_setup calls this function, so the array exists before any handle is
+// returned and a later amg_residual_norm_noalloc call creates nothing.
 double* noalloc_scratch_for_current_device() {
   int dev = 0;
   ASMG_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NA_MAX_DEVICES) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
-  if (!g_scratch_ptr[dev]) {
-    double* p = nullptr;
+  double* p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
     ASMG_CUDA(cudaGetSymbolAddress((void**)&p, g_noalloc_scratch));
-    g_scratch_ptr[dev] = p;
+    // the kernel too is loaded now, not at the first call
+    cudaFuncAttributes fa;
+    ASMG_CUDA(cudaFuncGetAttributes(&fa, k_residual_norm_noalloc));
+    g_scratch_ptr[dev].store(p, std::memory_order_release);
   }
-  return g_scratch_ptr[dev];
+  return p;
 }
 
 void residual_norm_noalloc(asmg_s& h, const double* b, const double* u, double* out, cudaStream_t s) {

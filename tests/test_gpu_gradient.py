@@ -44,6 +44,11 @@ def test_element_gradient_kernel_matches_oracle(inv):
     got = s.element_grad(torch.from_numpy(_vertex(m, o, u)).cuda(), torch.from_numpy(_vertex(m, o, lam)).cuda())
     want = o.elem_grad(u, lam)
     assert np.abs(got.cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+    # log-parametrisation: a = exp(g) set in the library, dL/dg = a dL/da in the kernel
+    asmg.amg_set_log_coefficients(s.h, torch.from_numpy(g).cuda())
+    got_g = s.element_grad_log(torch.from_numpy(_vertex(m, o, u)).cuda(), torch.from_numpy(_vertex(m, o, lam)).cuda())
+    want_g = np.exp(g) * want
+    assert np.abs(got_g.cpu().numpy() - want_g).max() <= 1e-12 * np.abs(want_g).max()
     s.close()
 
 

@@ -147,6 +147,9 @@ def test_spmv_and_mass(cases, name):
     b = s.mass_apply(torch.from_numpy(f).cuda()).cpu().numpy()
     br = o.mass_apply(f)
     assert np.abs(b[vf] - br).max() <= 1e-13 * np.abs(br).max()
+    # fixed-order gather: the same bits on a second call
+    b2 = s.mass_apply(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert np.array_equal(b, b2)
 
 
 @pytest.mark.parametrize("name", ["poisson65", "graded129", "jitter97"])

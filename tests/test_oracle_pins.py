@@ -1267,6 +1267,48 @@ def test_mixed_level_coefficient_is_the_mean_over_the_covered_part(gen):
             assert np.abs(o.finest_coef() - np.array(coef)).max() <= 1e-12 * max(coef)
 
 
+@pytest.mark.parametrize("kind", ["lognormal", "subcube", "graded_lognormal", "L_lognormal", "hole_subcube"])
+def test_2d_finest_coefficient_is_the_area_average(gen, kind):
+    # Sec. 4.1 (the auxiliary operator from the bilinear form, R6 / R17): on
+    # box and Dirichlet grids the finest auxiliary coefficient of a kept
+    # triangle K is (1/|K|) sum_e a_e |e n K|, with a = 0 outside Omega.  Both
+    # the intersections (the polygon clipper of this file) and |K| (from the
+    # lattice corners) are computed here, independently of the oracle.
+    rng = np.random.default_rng(7)
+    if kind == "lognormal":
+        m = gen.grid2d(17, 5)
+    elif kind == "subcube":
+        m = gen.grid2d(17, 6)
+    elif kind == "graded_lognormal":
+        m = gen.grid2d(17, 2, graded=True)
+    elif kind == "L_lognormal":
+        m = gen.grid2d_domain(17, 3, "L")
+    else:
+        m = gen.grid2d_domain(17, 4, "hole")
+    if kind.endswith("lognormal"):
+        m.coeff = np.exp(rng.normal(size=m.ne))
+    else:
+        m.coeff = gen.subcube_coefficient(m, 5, ncube=4)
+    o = oracle.Oracle(m)
+    E = m.verts[m.elems]
+    lo, hi = E.min(axis=1), E.max(axis=1)
+    tri = o.level_tri(o.J)
+    X, Y = _lattice_pts(o, tri.reshape(-1))
+    X, Y = X.reshape(-1, 3), Y.reshape(-1, 3)
+    want = np.empty(tri.shape[0])
+    for t in range(tri.shape[0]):
+        T = [(X[t, k], Y[t, k]) for k in range(3)]
+        area = 0.5 * ((X[t, 1] - X[t, 0]) * (Y[t, 2] - Y[t, 0]) - (X[t, 2] - X[t, 0]) * (Y[t, 1] - Y[t, 0]))
+        sel = np.where(np.all(lo <= (X[t].max(), Y[t].max()), axis=1) & np.all(hi >= (X[t].min(), Y[t].min()), axis=1))[0]
+        ar = np.array([_area(_clip_poly([tuple(p) for p in E[e]], T)) for e in sel])
+        want[t] = (ar * m.coeff[sel]).sum() / area
+    got = o.finest_coef()
+    assert got.shape == want.shape
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # the averages lie within the fine values' range (a = 0 outside Omega only lowers them)
+    assert got.max() <= m.coeff.max() * (1 + 1e-13)
+
+
 def test_mixed_pcg_and_iteration_reach_the_dense_solution(gen):
     m = _mixed_domain(gen, 17, "hole", "outer")
     b = None

@@ -32,6 +32,16 @@ def test_noalloc_residual_norm_matches_spmv_path(gen):
         ref_b = np.linalg.norm(b[free])
         assert abs(rn - ref_r) <= 1e-12 * ref_r, (trial, rn, ref_r)
         assert abs(bn - ref_b) <= 1e-12 * ref_b, (trial, bn, ref_b)
+    # a warm call creates no device memory: the driver's free-memory count
+    # is the same before and after several more calls
+    db, du = torch.from_numpy(b).cuda(), torch.from_numpy(u).cuda()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        asmg.amg_residual_norm_noalloc(s.h, db, du)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
     # host arrays are refused rather than staged through new memory
     with pytest.raises(asmg.AsmgError) as e:
         asmg.amg_residual_norm_noalloc(s.h, np.zeros(m.nv), np.zeros(m.nv))
