@@ -47,7 +47,9 @@ enum asmg_status {
   ASMG_ERR_BREAKDOWN = -4,    /* <p, A p> <= 0 or NaN, or <r, z> <= 0 in PCG */
   ASMG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
   ASMG_ERR_OOM = -6,          /* device allocation failed */
-  ASMG_ERR_TIMEOUT = -7       /* a bounded device wait expired */
+  ASMG_ERR_TIMEOUT = -7       /* a bounded device wait expired: a tiled sweep's shared-memory copy did
+                                 not complete within about a second; the solve stops, u holds the last
+                                 iterate, and the context stays usable */
 };
 
 enum asmg_precision { ASMG_FP64 = 0, ASMG_MIXED = 1 };
@@ -73,6 +75,10 @@ typedef struct {
   int32_t fine_sweeps;     /* smoothing steps per application of S and of S^t, 1..8; 1 */
   int32_t iteration;       /* 0: PCG (Sec. 5.2); 1: the ASMG iteration u <- u + B (b - A u) (Sec. 5.1
                               rates), meaningful with the multiplicative B; 0 */
+  int32_t tile_rows;       /* schedule of the auxiliary-level sweeps (results are the same bit for
+                              bit): 0 = default, > 0 = own rows per tile (32..65536) of the temporally
+                              blocked sweeps (every sweep of a level in one launch, one thread block
+                              per tile), -1 = one launch per colour class and sweep; 0 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */
@@ -202,7 +208,10 @@ enum asmg_info_what {
   ASMG_INFO_NNZ_P = 10,       /* non-zeros of the transfer P */
   ASMG_INFO_NROWS_E = 11,     /* residual rows of level `level` */
   ASMG_INFO_BYTES_ITER = 12,  /* algorithmic bytes of one PCG iteration (current precision) */
-  ASMG_INFO_NNZ_LEVEL = 13    /* stored non-zeros of level `level` (smoothing + residual rows) */
+  ASMG_INFO_NNZ_LEVEL = 13,   /* stored non-zeros of level `level` (smoothing + residual rows) */
+  ASMG_INFO_NTILES = 14,      /* tiles of the temporally blocked sweeps of level `level` (0: one launch
+                                 per colour class and sweep) */
+  ASMG_INFO_HALO_ROWS = 15    /* halo rows of those tiles (pre-sweeps), summed over the tiles */
 };
 int amg_info(asmg_handle h, int what, int level, int64_t* value);
 
@@ -251,6 +260,18 @@ enum asmg_prof_class {
   ASMG_PROF_NCLASS = 11
 };
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
+
+/*
+ * amg_profile plus a split by auxiliary level (tracing; not part of the
+ * paper).  out as for amg_profile; out_levels: host float64
+ * [nlev * 2 * 3 * 3], for each level index k = l - (coarsest + 1) below nlev,
+ * each direction (0 down, 1 up), each part (0 sweeps, 1 residual, 2 transfer
+ * and bookkeeping): launches, milliseconds, algorithmic bytes.  Levels that
+ * run inside the fused small-level kernels are counted under
+ * ASMG_PROF_AUX_SMALL only.
+ */
+int amg_profile_levels(asmg_handle h, const double* b, double rtol, double* out, double* out_levels, int nlev,
+                       int* iterations, void* stream);
 
 /*
  * Batched solves (not in the paper): many independent problems, each with

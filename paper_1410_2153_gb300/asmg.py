@@ -30,7 +30,7 @@ ASMG_FP64 = 0
 ASMG_MIXED = 1
 
 INFO = dict(nfree=0, J=1, coarse=2, naux=3, nsmooth=4, ncolours=5, ntree_levels=6, nseg=7, nsplit=8, nnz_A=9,
-            nnz_P=10, nrows_E=11, bytes_iter=12, nnz_level=13, launches_per_iter=100, t_setup_us=101,
+            nnz_P=10, nrows_E=11, bytes_iter=12, nnz_level=13, ntiles=14, halo_rows=15, launches_per_iter=100, t_setup_us=101,
             t_tree_us=102, t_aux_us=103, t_fine_us=104, t_levels_us=105,
             t_lv_assemble_us=108, t_lv_colour_us=109, t_lv_pack_us=110, t_lv_export_us=111, t_coarse_us=112,
             t_transfer_us=113, t_slots_us=114, t_sz_us=115)
@@ -42,7 +42,7 @@ class asmg_params(ctypes.Structure):
                 ("coarse_max_dofs", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("smoothing", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("use_pdl", ctypes.c_int32),
                 ("smoother", ctypes.c_int32), ("additive", ctypes.c_int32), ("fine_sweeps", ctypes.c_int32),
-                ("iteration", ctypes.c_int32)]
+                ("iteration", ctypes.c_int32), ("tile_rows", ctypes.c_int32)]
 
 
 class AsmgError(RuntimeError):
@@ -76,6 +76,7 @@ def lib():
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
         L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_residual_norm_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        L.amg_profile_levels.argtypes = [vp, vp, ctypes.c_double, vp, vp, i32, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_batch_create.argtypes = [i32, vp, i32, ctypes.c_double, vp, ctypes.POINTER(vp)]
         L.amg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
         L.amg_batch_destroy.argtypes = [vp]
@@ -87,7 +88,7 @@ def lib():
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
                      "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_element_grad_log",
                      "amg_set_log_coefficients", "amg_info", "amg_export",
-                     "amg_profile", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
+                     "amg_profile", "amg_profile_levels", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -215,6 +216,24 @@ def amg_profile(h, b, rtol: float, stream=None):
     res = {c: dict(launches=int(out[3 * k]), ms=float(out[3 * k + 1]), bytes=float(out[3 * k + 2]))
            for k, c in enumerate(PROF_CLASSES)}
     return res, it.value
+
+
+def amg_profile_levels(h, b, rtol: float, stream=None):
+    """amg_profile plus, per auxiliary level (index l - coarsest - 1), direction and part
+    (sweeps, residual, transfer): dict(launches, ms, bytes)."""
+    nlev = amg_info(h, "J") - amg_info(h, "coarse")
+    out = np.zeros(3 * len(PROF_CLASSES))
+    lv = np.zeros(nlev * 2 * 3 * 3)
+    it = ctypes.c_int(0)
+    _check(lib().amg_profile_levels(h, _ptr(b), float(rtol), _ptr(out), _ptr(lv), nlev, ctypes.byref(it),
+                                    _stream(stream, b)))
+    res = {c: dict(launches=int(out[3 * k]), ms=float(out[3 * k + 1]), bytes=float(out[3 * k + 2]))
+           for k, c in enumerate(PROF_CLASSES)}
+    lv = lv.reshape(nlev, 2, 3, 3)
+    levels = [{d: {part: dict(launches=int(lv[k, di, pi, 0]), ms=float(lv[k, di, pi, 1]), bytes=float(lv[k, di, pi, 2]))
+                   for pi, part in enumerate(("sweeps", "residual", "transfer"))}
+               for di, d in enumerate(("down", "up"))} for k in range(nlev)]
+    return res, levels, it.value
 
 
 def amg_residual_norm_noalloc(h, b, u, stream=None):

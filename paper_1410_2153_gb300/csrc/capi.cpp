@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstring>
 #include <numeric>
 #include <thread>
@@ -52,6 +53,14 @@ void copy_out(double* dst, const double* src, int64_t n, cudaStream_t s) {
 }
 
 int64_t pad32(int64_t n) { return (n + 31) / 32 * 32; }
+
+// Temporally blocked sweeps (asmg_params::tile_rows = 0): tile sizes tried in
+// order (own rows per tile), the shared memory a tile may use (two thread
+// blocks per SM), and the largest halo accepted, as a multiple of the own rows.
+constexpr int TILE_SIZES[] = {256};
+constexpr size_t TILE_SMEM = 110 * 1024;
+constexpr size_t TILE_SMEM_MAX = 200 * 1024;  // one thread block per SM
+constexpr double TILE_MAX_HALO = 1.5;
 
 // f(begin, end) over contiguous ranges of [0, n) on host threads
 template <class F>
@@ -206,9 +215,266 @@ void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<
   S.ok = true;
 }
 
+// Tiles of one sweep direction of a level (TileSweeps).  The own rows of a
+// tile are tile_rows consecutive smoothing rows in aux-ID order.  Its rows
+// are the closure of the pairs (row, sweep) that the own rows' final values
+// depend on: a row's value after sweep s reads its own value after sweep
+// s - 1 and each coupled row j of N~_l either after sweep s (j's class is
+// swept before the row's in this direction) or after sweep s - 1 (j's class
+// comes later).  Before the first sweep the values are the start values:
+// zero on the way down (such reads need no row), read from us on the way up
+// (the row is kept, with its start value).  Every entry of a kept row that
+// points to a row of N~_l outside the tile is left out: no pair of the
+// closure reads it.  Entries of the post-sweeps' rows whose column lies
+// outside N~_l become the tile's outside values.  SMd: SM-order rows with
+// their N~_l columns as SM rows; SM: the same rows with all columns as aux
+// IDs; pos: aux ID -> SM row.  Returns false (and builds nothing) when a tile
+// needs more than smem_max bytes of shared memory or more than 65,535 local
+// values, or when the halo exceeds max_halo times the own rows.
+template <class T>
+bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel, const std::vector<int64_t>& cstart,
+                 const std::vector<T>& dinv, const HostCSR& SMd, const HostCSR& SM, const std::vector<int32_t>& pos,
+                 size_t smem_max, double max_halo, TileSweeps<T>& TS, cudaStream_t s) {
+  const int64_t nsm = (int64_t)sel.size();
+  const int ncol = (int)cstart.size() - 1;
+  std::vector<int32_t> colr(nsm);
+  for (int c = 0; c < ncol; ++c)
+    for (int64_t k = cstart[c]; k < cstart[c + 1]; ++k) colr[k] = c;
+  std::vector<int32_t> own;
+  for (int64_t k = 0; k < nsm; ++k)
+    if (sel[k] >= 0) own.push_back((int32_t)k);
+  std::sort(own.begin(), own.end(), [&](int32_t a, int32_t b) { return sel[a] < sel[b]; });
+  const int64_t ntiles = ((int64_t)own.size() + tile_rows - 1) / tile_rows;
+  struct Out {
+    std::vector<int32_t> lrow, phase, ext;
+    std::vector<unsigned char> blob;
+    int64_t interior = 0, halo = 0, nnz = 0, nnz_real = 0;
+    bool ok = true;
+  };
+  std::vector<Out> out(ntiles);
+  const unsigned nt = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>({8, (int64_t)std::max(1u, std::thread::hardware_concurrency()), ntiles}));
+  std::vector<std::thread> th;
+  for (unsigned w = 0; w < nt; ++w)
+    th.emplace_back([&, w] {
+      // stamps: mark[sw * nsm + k] == tile: pair (k, sw) needed; inx[k] == tile: k kept
+      std::vector<int32_t> mark((size_t)nu * nsm, -1), inx(nsm, -1), loc(nsm, 0), ownm(nsm, -1);
+      std::vector<std::pair<int32_t, int32_t>> stack;
+      std::vector<int32_t> X;
+      std::unordered_map<int32_t, int32_t> extpos;
+      std::vector<int64_t> rptr;
+      std::vector<int32_t> rcol;
+      std::vector<double> rval;
+      std::vector<std::pair<int64_t, int32_t>> rlen;
+      for (int64_t t = ntiles * w / nt; t < ntiles * (w + 1) / nt; ++t) {
+        const int32_t tag = (int32_t)t;
+        stack.clear();
+        X.clear();
+        auto keep = [&](int32_t k) {
+          if (inx[k] != tag) {
+            inx[k] = tag;
+            X.push_back(k);
+          }
+        };
+        auto need = [&](int32_t k, int sw) {
+          int32_t& m = mark[(size_t)sw * nsm + k];
+          if (m != tag) {
+            m = tag;
+            stack.push_back({k, sw});
+          }
+        };
+        const int64_t o0 = t * tile_rows, o1 = std::min<int64_t>((int64_t)own.size(), o0 + tile_rows);
+        for (int64_t q = o0; q < o1; ++q) {
+          ownm[own[q]] = tag;
+          need(own[q], nu - 1);
+        }
+        while (!stack.empty()) {
+          const auto [k, sw] = stack.back();
+          stack.pop_back();
+          keep(k);
+          if (sw >= 1) need(k, sw - 1);
+          for (int64_t p = SMd.ptr[k]; p < SMd.ptr[k + 1]; ++p) {
+            const int32_t j = SMd.col[p];
+            if (j == k) continue;
+            const int cj = colr[j], ck = colr[k];
+            const bool before = up ? cj > ck : cj < ck;
+            if (before || cj == ck) need(j, sw);
+            if (!before) {
+              if (sw >= 1) need(j, sw - 1);
+              else if (up) keep(j);
+            }
+          }
+        }
+        // local rows: grouped by colour class (SM order); within a class,
+        // where order does not matter, longest rows first so that the slices
+        // carry little padding
+        auto row_len = [&](int32_t k) {
+          int64_t n = 0;
+          if (!up) {
+            for (int64_t p = SMd.ptr[k]; p < SMd.ptr[k + 1]; ++p) n += inx[SMd.col[p]] == tag;
+          } else {
+            for (int64_t p = SM.ptr[k]; p < SM.ptr[k + 1]; ++p) {
+              const int32_t j = pos[SM.col[p]];
+              n += j < 0 || inx[j] == tag;
+            }
+          }
+          return n;
+        };
+        std::sort(X.begin(), X.end());
+        rlen.resize(X.size());
+        for (size_t q = 0; q < X.size(); ++q) rlen[q] = {-row_len(X[q]), X[q]};
+        Out& O = out[t];
+        O.phase.assign(ncol + 1, 0);
+        size_t x = 0;
+        for (int c = 0; c < ncol; ++c) {
+          O.phase[c] = (int32_t)O.lrow.size();
+          const size_t x0 = x;
+          while (x < X.size() && X[x] < cstart[c + 1]) ++x;
+          std::sort(rlen.begin() + x0, rlen.begin() + x);
+          for (size_t q = x0; q < x; ++q) {
+            const int32_t k = rlen[q].second;
+            loc[k] = (int32_t)O.lrow.size();
+            const bool mine = ownm[k] == tag;
+            O.lrow.push_back(mine ? k : -2 - k);
+            if (mine) ++O.interior;
+            else ++O.halo;
+          }
+          while (O.lrow.size() % 32) O.lrow.push_back(-1);
+        }
+        O.phase[ncol] = (int32_t)O.lrow.size();
+        const int nl = (int)O.lrow.size();
+        // rows with local columns (outside values numbered after the rows)
+        extpos.clear();
+        rptr.assign(1, 0);
+        rcol.clear();
+        rval.clear();
+        for (int32_t g : O.lrow) {
+          if (g != -1) {
+            const int32_t k = g >= 0 ? g : -2 - g;
+            if (!up) {
+              for (int64_t p = SMd.ptr[k]; p < SMd.ptr[k + 1]; ++p) {
+                const int32_t j = SMd.col[p];
+                if (inx[j] != tag) continue;
+                rcol.push_back(loc[j]);
+                rval.push_back(SMd.val[p]);
+              }
+            } else {
+              for (int64_t p = SM.ptr[k]; p < SM.ptr[k + 1]; ++p) {
+                const int32_t a = SM.col[p];
+                const int32_t j = pos[a];
+                if (j >= 0) {
+                  if (inx[j] != tag) continue;
+                  rcol.push_back(loc[j]);
+                } else {
+                  auto it = extpos.find(a);
+                  int32_t e;
+                  if (it == extpos.end()) {
+                    e = (int32_t)O.ext.size();
+                    extpos.emplace(a, e);
+                    O.ext.push_back(a);
+                  } else {
+                    e = it->second;
+                  }
+                  rcol.push_back(nl + e);
+                }
+                rval.push_back(SM.val[p]);
+              }
+            }
+          }
+          rptr.push_back((int64_t)rcol.size());
+        }
+        if (nl + (int64_t)O.ext.size() > 65535) {
+          O.ok = false;
+          continue;
+        }
+        // the tile's block: SELL-32 slice offsets, uint16 columns, values, then
+        // per local row the diagonal inverse, the SM row (own: k, halo:
+        // -2 - k, padding: -1) and the aux ID, then the outside values' aux
+        // IDs; each part padded to 16 bytes
+        const int nsl = nl / 32;
+        std::vector<int32_t> soff(nsl + 1, 0);
+        for (int sl = 0; sl < nsl; ++sl) {
+          int64_t wmax = 0;
+          for (int r = sl * 32; r < sl * 32 + 32; ++r) wmax = std::max(wmax, rptr[r + 1] - rptr[r]);
+          soff[sl + 1] = soff[sl] + (int32_t)(wmax * 32);
+        }
+        const int64_t ne_ = soff[nsl], nx = (int64_t)O.ext.size();
+        O.nnz = ne_;
+        O.nnz_real = rptr[nl];
+        const TileLayout lay = tile_layout((int64_t)nl, ne_, nx, (int64_t)sizeof(T));
+        O.blob.assign(lay.end, 0);
+        std::memcpy(O.blob.data(), soff.data(), 4 * (size_t)(nsl + 1));
+        uint16_t* cc = reinterpret_cast<uint16_t*>(O.blob.data() + lay.col);
+        T* vv = reinterpret_cast<T*>(O.blob.data() + lay.val);
+        for (int r = 0; r < nl; ++r) {
+          const int sl = r / 32, lane = r % 32;
+          int64_t e = 0;
+          for (int64_t p = rptr[r]; p < rptr[r + 1]; ++p, ++e) {
+            cc[soff[sl] + e * 32 + lane] = (uint16_t)rcol[p];
+            vv[soff[sl] + e * 32 + lane] = (T)rval[p];
+          }
+        }
+        T* dd = reinterpret_cast<T*>(O.blob.data() + lay.dinv);
+        int32_t* ls = reinterpret_cast<int32_t*>(O.blob.data() + lay.lsm);
+        int32_t* la = reinterpret_cast<int32_t*>(O.blob.data() + lay.laux);
+        for (int r = 0; r < nl; ++r) {
+          const int32_t g = O.lrow[r];
+          ls[r] = g;
+          if (g == -1) {
+            dd[r] = (T)0;
+            la[r] = -1;
+          } else {
+            const int32_t k = g >= 0 ? g : -2 - g;
+            dd[r] = dinv[k];
+            la[r] = (int32_t)sel[k];
+          }
+        }
+        if (nx) std::memcpy(O.blob.data() + lay.ext, O.ext.data(), 4 * (size_t)nx);
+      }
+    });
+  for (auto& x : th) x.join();
+  int64_t maxloc = 0, maxext = 0, maxblob = 0, interior = 0, halo = 0;
+  for (auto& O : out) {
+    if (!O.ok) return false;
+    maxloc = std::max<int64_t>(maxloc, (int64_t)O.lrow.size());
+    maxext = std::max<int64_t>(maxext, (int64_t)O.ext.size());
+    maxblob = std::max<int64_t>(maxblob, (int64_t)O.blob.size());
+    interior += O.interior;
+    halo += O.halo;
+  }
+  const size_t smem = (size_t)maxblob + (size_t)(maxloc + maxext) * sizeof(T) + (size_t)maxloc * sizeof(T);
+  if (smem > smem_max || (double)halo > max_halo * (double)interior) return false;
+  std::vector<int64_t> loc_off(1, 0), blob_off(1, 0), ext_off(1, 0);
+  std::vector<int32_t> phase;
+  std::vector<unsigned char> blob;
+  for (auto& O : out) {
+    loc_off.push_back(loc_off.back() + (int64_t)O.lrow.size());
+    blob_off.push_back(blob_off.back() + (int64_t)O.blob.size());
+    ext_off.push_back(ext_off.back() + (int64_t)O.ext.size());
+    phase.insert(phase.end(), O.phase.begin(), O.phase.end());
+    blob.insert(blob.end(), O.blob.begin(), O.blob.end());
+    TS.nnz += O.nnz;
+    TS.nnz_real += O.nnz_real;
+  }
+  TS.ntiles = ntiles;
+  TS.nloc = loc_off.back();
+  TS.maxloc = (int)maxloc;
+  TS.maxext = (int)maxext;
+  TS.maxblob = maxblob;
+  TS.interior = interior;
+  TS.halo = halo;
+  TS.loc_off.upload(loc_off, s);
+  TS.blob_off.upload(blob_off, s);
+  TS.ext_off.upload(ext_off, s);
+  TS.phase.upload(phase, s);
+  TS.blob.upload(blob, s);
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  return true;
+}
+
 template <class T>
 void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
-                     const std::vector<uint8_t>& inset, AuxLevelDev<T>& D, cudaStream_t s) {
+                     const std::vector<uint8_t>& inset, const asmg_params& prm, AuxLevelDev<T>& D, cudaStream_t s) {
   D.level = L.level;
   // smoothing rows ordered by (colour, id), colour blocks padded to 32
   int ncol = 0;
@@ -258,6 +524,42 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
   sell_build<T>(D.SMd, SMd, 0, s);
   D.sm_rows.upload(rows, s);
   D.sm_dinv.upload(dinv, s);
+  // temporal blocking of the level's sweeps (TileSweeps): the largest tile of
+  // TILE_SIZES (or the requested size) whose tiles fit the shared-memory
+  // budget with a halo of at most TILE_MAX_HALO times the own rows; the level
+  // needs at least two tiles and every new node must be a smoothing row
+  // (k_up_init prolongs through the smoothing rows)
+  D.tiled = false;
+  if (prm.tile_rows >= 0 && prm.nu_post >= 1) {
+    bool ok = true;
+    for (int32_t id : L.new_id)
+      if (pos[id] < 0) ok = false;
+    std::vector<int> sizes;
+    if (prm.tile_rows > 0) sizes.push_back(prm.tile_rows);
+    else sizes.assign(std::begin(TILE_SIZES), std::end(TILE_SIZES));
+    // a requested size takes any halo and up to TILE_SMEM_MAX of shared memory
+    const double max_halo = prm.tile_rows > 0 ? 1e30 : TILE_MAX_HALO;
+    const size_t smem_max = prm.tile_rows > 0 ? TILE_SMEM_MAX : TILE_SMEM;
+    for (int trows : sizes) {
+      if (!ok || D.nsm_real < 2 * (int64_t)trows) continue;
+      TileSweeps<T> td, tu;
+      if (!build_tiles<T>(false, prm.nu_pre, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, td, s) ||
+          !build_tiles<T>(true, prm.nu_post, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, tu, s))
+        continue;
+      std::vector<int32_t> p0(sel.size(), -3), p1(sel.size(), -3);
+      for (size_t t = 0; t < L.new_id.size(); ++t) {
+        p0[pos[L.new_id[t]]] = L.new_p0[t];
+        p1[pos[L.new_id[t]]] = L.new_p1[t];
+      }
+      D.sm_par0.upload(p0, s);
+      D.sm_par1.upload(p1, s);
+      D.tdown = std::move(td);
+      D.tup = std::move(tu);
+      D.tiled = true;
+      D.tile_rows = trows;
+      break;
+    }
+  }
   // residual rows: every row with an entry in a smoothing column
   std::vector<uint8_t> touched(Arows.nr, 0);
   host_for(Arows.nr, [&](int64_t i0, int64_t i1) {
@@ -498,10 +800,10 @@ void build_all(asmg_s& h, cudaStream_t s) {
     h.stats.t_lv_export += td - tc;
     if (h.prm.precision == ASMG_MIXED) {
       h.p32.lev.emplace_back();
-      build_level_dev<float>(L, Arows, colour, inset, h.p32.lev.back(), s);
+      build_level_dev<float>(L, Arows, colour, inset, h.prm, h.p32.lev.back(), s);
     } else {
       h.p64.lev.emplace_back();
-      build_level_dev<double>(L, Arows, colour, inset, h.p64.lev.back(), s);
+      build_level_dev<double>(L, Arows, colour, inset, h.prm, h.p64.lev.back(), s);
     }
     h.stats.t_lv_pack += now() - td;
   }
@@ -644,6 +946,7 @@ int asmg_default_params(asmg_params* p) {
   p->additive = 0;
   p->fine_sweeps = 1;
   p->iteration = 0;
+  p->tile_rows = 0;
   return ASMG_OK;
 }
 
@@ -664,7 +967,8 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       (prm.precision != ASMG_FP64 && prm.precision != ASMG_MIXED) || (prm.smoothing != 0 && prm.smoothing != 1) ||
       prm.coarse_max_dofs > 8192 || (prm.use_pdl != 0 && prm.use_pdl != 1) || (prm.use_graph != 0 && prm.use_graph != 1) ||
       (prm.smoother != 0 && prm.smoother != 1) || (prm.additive != 0 && prm.additive != 1) || prm.fine_sweeps < 1 ||
-      prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1))
+      prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1) ||
+      (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)))
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();
@@ -835,11 +1139,15 @@ int amg_batch_solve(asmg_batch B, const double* const* bs, double* const* us, in
   int worst = ASMG_OK;
   for (size_t k = 0; k < sc.size(); ++k) {
     iterations[k] = sc[k].k;
-    const int st = sc[k].status == 0 ? ASMG_OK : sc[k].status == ASMG_ERR_BREAKDOWN ? ASMG_ERR_BREAKDOWN : ASMG_NOT_CONVERGED;
+    const int st = sc[k].status == 0                    ? ASMG_OK
+                   : sc[k].status == ASMG_ERR_BREAKDOWN ? ASMG_ERR_BREAKDOWN
+                   : sc[k].status == ASMG_ERR_TIMEOUT   ? ASMG_ERR_TIMEOUT
+                                                        : ASMG_NOT_CONVERGED;
     if (status) status[k] = st;
     if (st < 0 || (worst == ASMG_OK && st != ASMG_OK)) worst = st;
   }
   if (worst == ASMG_ERR_BREAKDOWN) g_err = "PCG breakdown in a batched solve";
+  if (worst == ASMG_ERR_TIMEOUT) g_err = "a bounded device wait expired in a batched solve";
   return worst;
   API_END
 }
@@ -864,6 +1172,22 @@ int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* i
   gather_rows(*h, S0.vb.p, S0.b.p, s);
   S0.x.zero(s);
   *iterations = profile_solve(*h, rtol, s, out);
+  return ASMG_OK;
+  API_END
+}
+
+int amg_profile_levels(asmg_handle h, const double* b, double rtol, double* out, double* out_levels, int nlev,
+                       int* iterations, void* stream) {
+  API_BEGIN
+  if (!h || !b || !out || !out_levels || !iterations || nlev < 0)
+    ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  Slot& S0 = h->slot0();
+  const int64_t nv = h->mesh.nv;
+  copy_in(S0.vb.p, b, nv, s);
+  gather_rows(*h, S0.vb.p, S0.b.p, s);
+  S0.x.zero(s);
+  *iterations = profile_solve(*h, rtol, s, out, out_levels, nlev);
   return ASMG_OK;
   API_END
 }
@@ -894,6 +1218,10 @@ int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* itera
   if (sc.status == ASMG_ERR_BREAKDOWN) {
     g_err = "PCG breakdown: <p, A p> or <r, z> not positive";
     return ASMG_ERR_BREAKDOWN;
+  }
+  if (sc.status == ASMG_ERR_TIMEOUT) {
+    g_err = "a bounded device wait expired (a tile's shared-memory copy did not complete); u holds the last iterate";
+    return ASMG_ERR_TIMEOUT;
   }
   return sc.status == 0 ? ASMG_OK : ASMG_NOT_CONVERGED;
   API_END
@@ -937,13 +1265,18 @@ int amg_precond_apply(asmg_handle h, const double* r, double* z, void* stream) {
   const int64_t nv = h->mesh.nv;
   copy_in(S0.vb.p, r, nv, s);
   gather_rows(*h, S0.vb.p, S0.r.p, s);
+  int* tflag = reinterpret_cast<int*>(reinterpret_cast<char*>(S0.scal.p) + offsetof(PcgScalars, timeout));
+  ASMG_CUDA(cudaMemsetAsync(tflag, 0, sizeof(int), s));
   precond_apply(*h, S0.r.p, s);
   if (h->prm.precision == ASMG_MIXED)
     scatter_rows(*h, S0.s32.uf.p, true, S0.vu.p, s);
   else
     scatter_rows(*h, S0.s64.uf.p, false, S0.vu.p, s);
   copy_out(z, S0.vu.p, nv, s);
+  int tout = 0;
+  ASMG_CUDA(cudaMemcpyAsync(&tout, tflag, sizeof(int), cudaMemcpyDeviceToHost, s));
   ASMG_CUDA(cudaStreamSynchronize(s));
+  if (tout) ASMG_FAIL(ASMG_ERR_TIMEOUT, "a bounded device wait expired (a tile's shared-memory copy did not complete)");
   return ASMG_OK;
   API_END
 }
@@ -1092,6 +1425,17 @@ int amg_info(asmg_handle h, int what, int level, int64_t* value) {
       int k = lev_index(level);
       *value = h->prm.precision == ASMG_MIXED ? h->p32.lev[k].SM.nnz_real + h->p32.lev[k].RS.nnz_real
                                               : h->p64.lev[k].SM.nnz_real + h->p64.lev[k].RS.nnz_real;
+      break;
+    }
+    case ASMG_INFO_NTILES: {
+      int k = lev_index(level);
+      *value = h->prm.precision == ASMG_MIXED ? (h->p32.lev[k].tiled ? h->p32.lev[k].tdown.ntiles : 0)
+                                              : (h->p64.lev[k].tiled ? h->p64.lev[k].tdown.ntiles : 0);
+      break;
+    }
+    case ASMG_INFO_HALO_ROWS: {
+      int k = lev_index(level);
+      *value = h->prm.precision == ASMG_MIXED ? h->p32.lev[k].tdown.halo : h->p64.lev[k].tdown.halo;
       break;
     }
     case 100: *value = h->gpu_launches_per_iter; break;

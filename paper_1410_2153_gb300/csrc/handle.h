@@ -22,6 +22,7 @@ struct PcgScalars {
   double rz;      // <r_k, z_k>
   double alpha, beta, pq, rr, bnorm, tol;
   int k, maxit, status, cond;
+  int timeout;    // set by a kernel whose bounded wait expired (the solve then stops)
 };
 
 // Preconditioner data in the precision T of the smoother and V-cycle.
@@ -105,7 +106,8 @@ struct asmg_s {
 namespace asmg {
 // solve.cu
 void setup_solve(asmg_s& h, cudaStream_t s);
-int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out);
+int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out, double* out_levels = nullptr,
+                  int nlev_out = 0);
 // noalloc.cu
 double* noalloc_scratch_for_current_device();
 void residual_norm_noalloc(asmg_s& h, const double* b, const double* u, double* out, cudaStream_t s);

@@ -265,6 +265,60 @@ struct SmallLevelDev {
   DBuf<T> sm_val, dinv, rs_val;
 };
 
+// Temporal blocking of the sweeps of one auxiliary level (Algorithm 2's
+// nu pre- or post-smoothing steps over all colour classes in one launch):
+// the smoothing rows N~_l are cut into tiles of consecutive aux IDs (lattice
+// Morton order, so a tile is a compact patch); each tile carries the halo
+// rows whose values its sweeps read, found by a closure over (row, sweep)
+// dependencies, so one thread block can run every sweep of its tile in
+// shared memory and write back only the tile's own rows.  The results equal
+// the class-by-class launches bit for bit (see build_tiles).
+//
+// A tile's rows are stored as one block of bytes (16-byte aligned, a multiple
+// of 16 bytes long; layout in TileLayout) that the kernel copies into shared
+// memory with one bulk copy: SELL-32 slice offsets (int32, relative to the
+// tile), the column of every entry (uint16: a local row, or nl + e for the
+// tile's e-th outside value), the values (T), then per local row its
+// diagonal inverse (T), SM row (int32: own row k, halo row -2 - k, padding
+// -1) and aux ID (int32), then the outside values' aux IDs.  Outside values
+// are the columns outside N~_l of the post-sweeps' rows: the sweeps do not
+// change them, so the tile reads them from U once.
+struct TileLayout {
+  int64_t col, val, dinv, lsm, laux, ext, end;  // byte offsets of the parts, and the total
+};
+
+// nl local rows (a multiple of 32), ne stored entries, nx outside values, s bytes per value
+inline __host__ __device__ TileLayout tile_layout(int64_t nl, int64_t ne, int64_t nx, int64_t s) {
+  auto pad16 = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
+  TileLayout t;
+  t.col = pad16(4 * (nl / 32 + 1));
+  t.val = t.col + pad16(2 * ne);
+  t.dinv = t.val + pad16(s * ne);
+  t.lsm = t.dinv + pad16(s * nl);
+  t.laux = t.lsm + pad16(4 * nl);
+  t.ext = t.laux + pad16(4 * nl);
+  t.end = t.ext + pad16(4 * nx);
+  return t;
+}
+
+template <class T>
+struct TileSweeps {
+  int64_t ntiles = 0, nloc = 0;  // tiles, local rows (each colour group padded to 32)
+  int maxloc = 0, maxext = 0;    // largest local row count and outside-value count of a tile
+  int tpb = 256;                 // threads per block
+  int64_t maxblob = 0;           // largest tile block (bytes)
+  int64_t interior = 0, halo = 0;  // real rows: the tiles' own, and halo copies
+  int64_t nnz = 0, nnz_real = 0;   // stored / real entries over all tiles
+  DBuf<int64_t> loc_off;         // [ntiles + 1] first local row of each tile (multiples of 32)
+  DBuf<int64_t> blob_off;        // [ntiles + 1] byte offset of each tile's block
+  DBuf<int64_t> ext_off;         // [ntiles + 1] first outside value of each tile
+  DBuf<int32_t> phase;           // [ntiles * (ncol + 1)] colour-class starts within each tile
+  DBuf<unsigned char> blob;      // the tiles' blocks
+  // shared memory of a launch: the largest block, then U (rows and outside
+  // values) and F of the largest tile
+  size_t smem() const { return (size_t)maxblob + (size_t)(maxloc + maxext) * sizeof(T) + (size_t)maxloc * sizeof(T); }
+};
+
 // ------------------------------------------------------------ solve data
 template <class T>
 struct AuxLevelDev {
@@ -287,6 +341,12 @@ struct AuxLevelDev {
   DBuf<int32_t> rp_id;           // parents receiving restricted residuals
   DBuf<int32_t> rp_ptr, rp_child;
   SmallLevelDev<T> small;        // shared-memory form, when the level is small
+  // temporal blocking (tiled = 1): pre-sweeps in one launch (k_tile_down), and
+  // after k_up_init, post-sweeps in one launch (k_tile_up)
+  bool tiled = false;
+  int tile_rows = 0;                 // own rows per tile
+  TileSweeps<T> tdown, tup;
+  DBuf<int32_t> sm_par0, sm_par1;    // per SM row: parents of a new node (-1 Dirichlet), -3 not new
 };
 
 struct Stats {

@@ -20,7 +20,9 @@
 // New nodes are midpoints of coarse edges (Sec. 3.3), hence the 1/2 weights.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <vector>
 
 #include "handle.h"
@@ -389,6 +391,259 @@ __global__ void k_coarse(int64_t nc, const int32_t* __restrict__ cid, const doub
   pdl_trigger();
 }
 
+// ------------------------------------------- tiled sweeps (one launch each)
+// One thread block per tile (see TileSweeps): the tile's rows -- its own rows
+// of N~_l plus the halo its sweeps read -- are copied into shared memory with
+// one bulk copy (cp.async.bulk, completion on an mbarrier), and the rows'
+// rhs, diagonal inverse and current value live there too; the colour phases
+// of all nu sweeps are separated by __syncthreads.  Each row is updated with
+// the same arithmetic, over the same stored entries in the same order, as
+// k_gs_aux_down / k_gs_aux do; the entries a tile leaves out are exactly
+// those whose value cannot reach the tile's own rows' results, so those
+// results equal the class-by-class launches bit for bit.  Halo results are
+// discarded.
+constexpr int TILE_TPB = 256;
+// bound on the wait for the bulk copy (SM clock cycles, about 1 s): when it
+// expires the block records the timeout, waits once more (bounded) for its
+// copy to land, and skips its work
+constexpr long long TILE_WAIT_CYCLES = 2000000000LL;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for phase 0 of the mbarrier
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, 0))
+    if (clock64() - t0 > TILE_WAIT_CYCLES) return false;
+  return true;
+}
+
+// Stage the tile's block of `bytes` bytes (16-byte aligned, multiple of 16)
+// into shared memory: thread 0 arms the barrier and issues the copy.  The
+// mbarrier lives in static shared memory.
+__device__ __forceinline__ void tile_stage(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    const uint32_t b = smem_addr(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(b)
+                 : "memory");
+  }
+}
+
+// Every thread waits for the copy (bounded); false in every thread when any
+// thread's wait expired, after the timeout is recorded and the copy given a
+// second bounded wait.
+__device__ __forceinline__ bool tile_staged(uint64_t* bar, int* timeout) {
+  const uint32_t b = smem_addr(bar);
+  __syncthreads();  // the barrier was initialised by thread 0 before this point
+  const bool ok = __syncthreads_and(mbar_wait_bounded(b));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(timeout, 1);
+    mbar_wait_bounded(b);
+    __syncthreads();
+  }
+  return ok;
+}
+
+// the row's entries in stored order, four loaded ahead of their use (the sum
+// is formed in the same order as a plain loop)
+template <class T>
+__device__ __forceinline__ T tile_row_dot(int r, const int32_t* soff, const uint16_t* col, const T* val, const T* Ul) {
+  const int sl = r >> 5, lane = r & 31;
+  const int b = soff[sl], w = (soff[sl + 1] - b) >> 5;
+  T acc = 0;
+  int e = 0;
+  for (; e + 4 <= w; e += 4) {
+    const int q = b + (e << 5) + lane;
+    const int c0 = col[q], c1 = col[q + 32], c2 = col[q + 64], c3 = col[q + 96];
+    const T v0 = val[q], v1 = val[q + 32], v2 = val[q + 64], v3 = val[q + 96];
+    const T x0 = Ul[c0], x1 = Ul[c1], x2 = Ul[c2], x3 = Ul[c3];
+    acc += v0 * x0;
+    acc += v1 * x1;
+    acc += v2 * x2;
+    acc += v3 * x3;
+  }
+  for (; e < w; ++e) {
+    const int q = b + (e << 5) + lane;
+    acc += val[q] * Ul[col[q]];
+  }
+  return acc;
+}
+
+// the staged block of a tile (TileLayout) and, after it, U (local rows and
+// outside values) and F
+template <class T>
+struct TileSmem {
+  const int32_t* soff;
+  const uint16_t* col;
+  const T* val;
+  const T* dinv;
+  const int32_t* lsm;
+  const int32_t* laux;
+  const int32_t* ext;
+  T *Ul, *Fl;
+};
+
+template <class T>
+__device__ __forceinline__ TileSmem<T> tile_smem(unsigned char* raw, int64_t maxblob, int maxloc, int maxext, int nl,
+                                                 int nx) {
+  TileSmem<T> t;
+  t.soff = reinterpret_cast<const int32_t*>(raw);
+  const TileLayout lay = tile_layout(nl, t.soff[nl >> 5], nx, (int64_t)sizeof(T));
+  t.col = reinterpret_cast<const uint16_t*>(raw + lay.col);
+  t.val = reinterpret_cast<const T*>(raw + lay.val);
+  t.dinv = reinterpret_cast<const T*>(raw + lay.dinv);
+  t.lsm = reinterpret_cast<const int32_t*>(raw + lay.lsm);
+  t.laux = reinterpret_cast<const int32_t*>(raw + lay.laux);
+  t.ext = reinterpret_cast<const int32_t*>(raw + lay.ext);
+  t.Ul = reinterpret_cast<T*>(raw + maxblob);
+  t.Fl = t.Ul + maxloc + maxext;
+  return t;
+}
+
+// pre-sweeps: us (the level's own correction, SM order) starts at 0; the
+// first sweep saves F on the tile's own rows in fs.  The block is copied in
+// while the previous kernel finishes.
+template <class T>
+__global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restrict__ loc_off,
+                                                        const int64_t* __restrict__ blob_off,
+                                                        const unsigned char* __restrict__ blob,
+                                                        const int32_t* __restrict__ phase, int ncol, int64_t maxblob,
+                                                        int maxloc, const T* __restrict__ F, T* __restrict__ fs,
+                                                        T* __restrict__ us, int nu, int* timeout) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t base = loc_off[blockIdx.x];
+  const int nl = (int)(loc_off[blockIdx.x + 1] - base);
+  const int64_t b0 = blob_off[blockIdx.x];
+  const uint32_t bytes = (uint32_t)(blob_off[blockIdx.x + 1] - b0);
+  const int32_t* ph = phase + (int64_t)blockIdx.x * (ncol + 1);
+  tile_stage(smraw, blob + b0, bytes, &bar);
+  pdl_wait();
+  if (tile_staged(&bar, timeout)) {
+    TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, 0, nl, 0);
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+      const int32_t g = t.lsm[k];
+      T f = 0;
+      if (g != -1) {
+        f = F[t.laux[k]];
+        if (g >= 0) fs[g] = f;
+      }
+      t.Fl[k] = f;
+      t.Ul[k] = 0;
+    }
+    __syncthreads();
+    for (int sw = 0; sw < nu; ++sw)
+      for (int c = 0; c < ncol; ++c) {
+        for (int k = ph[c] + threadIdx.x; k < ph[c + 1]; k += blockDim.x) {
+          const T acc = tile_row_dot<T>(k, t.soff, t.col, t.val, t.Ul);
+          t.Ul[k] += (t.Fl[k] - acc) * t.dinv[k];
+        }
+        __syncthreads();
+      }
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+      const int32_t g = t.lsm[k];
+      if (g >= 0) us[g] = t.Ul[k];
+    }
+  }
+  pdl_trigger();
+}
+
+// start of the up path of a tiled level, in place on us (SM order): the
+// prolongation of the coarse correction (I_l: new nodes take the mean of
+// their parents) plus the level's saved correction.  U itself is not
+// written, so the tiles of k_tile_up read every row's start value from us
+// while other tiles write their results to U.
+template <class T>
+__global__ void k_up_init(int64_t nsm, const int32_t* __restrict__ rows, const int32_t* __restrict__ par0,
+                          const int32_t* __restrict__ par1, const T* __restrict__ U, T* __restrict__ us) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int32_t i = -1, a = -3, b = -3;
+  if (k < nsm) {
+    i = rows[k];
+    a = par0[k];
+    b = par1[k];
+  }
+  pdl_wait();
+  if (i >= 0) {
+    T v;
+    if (a == -3) {
+      v = U[i];
+    } else {
+      T p = 0;
+      if (a >= 0) p += U[a];
+      if (b >= 0) p += U[b];
+      v = (T)0.5 * p;
+    }
+    us[k] = v + us[k];
+  }
+  pdl_trigger();
+}
+
+// post-sweeps (backward colour order) from the start values in us; the
+// columns outside N~_l (the tile's outside values) are read from U once; the
+// tile's own rows are written to U
+template <class T>
+__global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict__ loc_off,
+                                                      const int64_t* __restrict__ blob_off,
+                                                      const unsigned char* __restrict__ blob,
+                                                      const int64_t* __restrict__ ext_off,
+                                                      const int32_t* __restrict__ phase, int ncol, int64_t maxblob,
+                                                      int maxloc, int maxext, const T* __restrict__ fs,
+                                                      const T* __restrict__ us, T* U, int nu, int* timeout) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t base = loc_off[blockIdx.x];
+  const int nl = (int)(loc_off[blockIdx.x + 1] - base);
+  const int64_t b0 = blob_off[blockIdx.x];
+  const uint32_t bytes = (uint32_t)(blob_off[blockIdx.x + 1] - b0);
+  const int nx = (int)(ext_off[blockIdx.x + 1] - ext_off[blockIdx.x]);
+  const int32_t* ph = phase + (int64_t)blockIdx.x * (ncol + 1);
+  tile_stage(smraw, blob + b0, bytes, &bar);
+  pdl_wait();
+  if (tile_staged(&bar, timeout)) {
+    TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, maxext, nl, nx);
+    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+      const int32_t g = t.lsm[k];
+      T f = 0, u = 0;
+      if (g != -1) {
+        const int32_t sm = g >= 0 ? g : -2 - g;
+        f = fs[sm];
+        u = us[sm];
+      }
+      t.Fl[k] = f;
+      t.Ul[k] = u;
+    }
+    for (int e = threadIdx.x; e < nx; e += blockDim.x) t.Ul[nl + e] = U[t.ext[e]];
+    __syncthreads();
+    for (int sw = 0; sw < nu; ++sw)
+      for (int c = ncol - 1; c >= 0; --c) {
+        for (int k = ph[c] + threadIdx.x; k < ph[c + 1]; k += blockDim.x) {
+          const T acc = tile_row_dot<T>(k, t.soff, t.col, t.val, t.Ul);
+          t.Ul[k] += (t.Fl[k] - acc) * t.dinv[k];
+        }
+        __syncthreads();
+      }
+    for (int k = threadIdx.x; k < nl; k += blockDim.x)
+      if (t.lsm[k] >= 0) U[t.laux[k]] = t.Ul[k];
+  }
+  pdl_trigger();
+}
+
 // ---------------------------------------------------- small levels, fused
 // A run of small levels in one thread block.  Per level the rhs F and the
 // correction U of the rows E_l, and the row pointers of its smoothing and
@@ -579,6 +834,7 @@ __global__ void k_pcg_init(int64_t n, SellView<double> A, const double* __restri
     sc->rz = 0;
     sc->alpha = 0;
     sc->beta = 0;
+    sc->timeout = 0;
     hist[0] = sqrt(v[1]);
     const bool conv = sqrt(v[1]) <= sc->tol;
     if (conv) sc->status = 0;
@@ -657,6 +913,11 @@ __global__ void k_axpy_norm(int64_t n, const double* __restrict__ p, const doubl
       set_cond(sc, 0, hnd, use_hnd);
       return;
     }
+    if (sc->timeout) {
+      sc->status = ASMG_ERR_TIMEOUT;
+      set_cond(sc, 0, hnd, use_hnd);
+      return;
+    }
     sc->k += 1;
     sc->rr = v[0];
     const double nr = sqrt(v[0]);
@@ -690,6 +951,11 @@ __global__ void k_iter_resid(int64_t n, SellView<double> A, const double* __rest
     v[0] += ri * ri;
   }
   if (grid_reduce<1>(v, partial, ticket) && threadIdx.x == 0) {
+    if (sc->timeout) {
+      sc->status = ASMG_ERR_TIMEOUT;
+      set_cond(sc, 0, hnd, use_hnd);
+      return;
+    }
     sc->k += 1;
     sc->rr = v[0];
     const double nr = sqrt(v[0]);
@@ -728,6 +994,7 @@ struct Profiler {
     int cls;
     int64_t bytes;
     int e0;
+    int level;  // index into Prec::lev of an auxiliary-level launch (down: level, up: -2 - level), else -1
   };
   std::vector<Rec> recs;
   int mark() {
@@ -742,6 +1009,7 @@ struct Profiler {
   }
 };
 thread_local Profiler* g_prof = nullptr;
+thread_local int g_prof_level = -1;
 
 #define LAUNCH(cls, bytes, ...)                                                  \
   do {                                                                          \
@@ -749,7 +1017,7 @@ thread_local Profiler* g_prof = nullptr;
     __VA_ARGS__;                                                                \
     if (g_prof) {                                                               \
       g_prof->mark();                                                           \
-      g_prof->recs.push_back(Profiler::Rec{(int)(cls), (int64_t)(bytes), e0_}); \
+      g_prof->recs.push_back(Profiler::Rec{(int)(cls), (int64_t)(bytes), e0_, g_prof_level}); \
     }                                                                           \
   } while (0)
 
@@ -797,6 +1065,11 @@ int64_t small_bytes(const Prec<T>& P, int first, int count, int nu, bool down) {
   return by;
 }
 
+// the slot's timeout flag (PcgScalars::timeout, device memory)
+int* timeout_flag(Slot& S) {
+  return reinterpret_cast<int*>(reinterpret_cast<char*>(S.scal.p) + offsetof(PcgScalars, timeout));
+}
+
 template <class T>
 int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
@@ -815,9 +1088,21 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SMd = view(L.SMd);
+    g_prof_level = li;
+    if (L.tiled) {
+      // all pre-sweeps of the level in one launch (compulsory bytes: the
+      // tiles' blocks once, F gathered and saved, us written)
+      const TileSweeps<T>& Tl = L.tdown;
+      const int64_t by = Tl.nnz_real * (sz + 2) + (Tl.interior + Tl.halo) * (8 + 2 * sz) + Tl.interior * (4 + sz);
+      LAUNCH(ASMG_PROF_AUX_GS, by,
+             launch_smem(h.prm.use_pdl, k_tile_down<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p,
+                         Tl.blob_off.p, (const unsigned char*)Tl.blob.p, Tl.phase.p, L.ncolours, Tl.maxblob,
+                         Tl.maxloc, (const T*)SP.F.p, SP.fs[li].p, SP.us[li].p, npre, timeout_flag(S)));
+      ++launches;
+    }
     // pre-sweeps on us (SM order); the first also saves F on N~_l for the
     // post-sweeps (nu_pre >= 1)
-    for (int sweep = 0; sweep < npre; ++sweep) {
+    for (int sweep = 0; sweep < (L.tiled ? 0 : npre); ++sweep) {
       for (int c = 0; c < L.ncolours; ++c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
@@ -838,6 +1123,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
                   L.rp_ptr.p, L.rp_child.p, SP.F.p));
     launches += 2;
   }
+  g_prof_level = -1;
   if (nbot) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npre, true),
            launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.F.p, npre));
@@ -856,6 +1142,21 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   for (int li = nbot; li <= nlev - 1 - ndeep; ++li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
+    g_prof_level = -2 - li;
+    if (L.tiled) {
+      LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (12 + 2 * sz) + L.nnew * 2 * sz + (L.nsm_real - L.nnew) * sz,
+             launch(h.prm.use_pdl, k_up_init<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p,
+                    L.sm_par0.p, L.sm_par1.p, (const T*)SP.U.p, SP.us[li].p));
+      const TileSweeps<T>& Tl = L.tup;
+      const int64_t by = Tl.nnz_real * (sz + 2) + (Tl.interior + Tl.halo) * (8 + 3 * sz) + Tl.interior * (4 + sz);
+      LAUNCH(ASMG_PROF_AUX_GS, by,
+             launch_smem(h.prm.use_pdl, k_tile_up<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p, Tl.blob_off.p,
+                         (const unsigned char*)Tl.blob.p, Tl.ext_off.p, Tl.phase.p, L.ncolours, Tl.maxblob,
+                         Tl.maxloc, Tl.maxext, (const T*)SP.fs[li].p, (const T*)SP.us[li].p, SP.U.p, npost,
+                         timeout_flag(S)));
+      launches += 2;
+      continue;
+    }
     if (L.nnew) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nnew * (12 + 3 * sz),
              launch(h.prm.use_pdl, k_prolong_aux<T>, nblk(L.nnew, rows_tpb(L.nnew)), rows_tpb(L.nnew), s, L.nnew, L.nn_id.p, L.nn_p0.p, L.nn_p1.p,
@@ -875,6 +1176,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
         ++launches;
       }
   }
+  g_prof_level = -1;
   if (ndeep) {
     LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npost, false),
            launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.U.p, npost));
@@ -1106,7 +1408,7 @@ int run_solve(asmg_s& h, Slot& S, double rtol, cudaStream_t s) {
 
 // One solve without the graph, every launch timed: per class launches,
 // milliseconds and algorithmic bytes; returns the iteration count.
-int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
+int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out, double* out_levels, int nlev_out) {
   Slot& S = *h.slots[0];
   Profiler prof;
   prof.s = s;
@@ -1129,12 +1431,25 @@ int profile_solve(asmg_s& h, double rtol, cudaStream_t s, double* out) {
   }
   g_prof = nullptr;
   for (int k = 0; k < 3 * ASMG_PROF_NCLASS; ++k) out[k] = 0;
+  if (out_levels)
+    for (int k = 0; k < nlev_out * 2 * 3 * 3; ++k) out_levels[k] = 0;
   for (auto& r : prof.recs) {
     float ms = 0;
     ASMG_CUDA(cudaEventElapsedTime(&ms, prof.ev[r.e0], prof.ev[r.e0 + 1]));
     out[3 * r.cls] += 1;
     out[3 * r.cls + 1] += ms;
     out[3 * r.cls + 2] += (double)r.bytes;
+    if (out_levels && r.level != -1) {
+      // [level][down, up][sweeps, residual, transfer][launches, ms, bytes]
+      const int li = r.level >= 0 ? r.level : -2 - r.level, dir = r.level >= 0 ? 0 : 1;
+      const int kind = r.cls == ASMG_PROF_AUX_GS ? 0 : r.cls == ASMG_PROF_AUX_RESID ? 1 : 2;
+      if (li < nlev_out) {
+        double* o = out_levels + ((li * 2 + dir) * 3 + kind) * 3;
+        o[0] += 1;
+        o[1] += ms;
+        o[2] += (double)r.bytes;
+      }
+    }
   }
   return its;
 }
@@ -1155,6 +1470,13 @@ void setup_small(Prec<T>& P) {
   const int smem = (int)small_smem<T>();
   ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int tsm = 0;
+  for (auto& L : P.lev)
+    if (L.tiled) tsm = std::max<int>(tsm, (int)std::max(L.tdown.smem(), L.tup.smem()));
+  if (tsm > 0) {
+    ASMG_CUDA(cudaFuncSetAttribute(k_tile_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+    ASMG_CUDA(cudaFuncSetAttribute(k_tile_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
+  }
 }
 
 // Work state of one solve in precision T: vectors, per-level saved values,
@@ -1216,6 +1538,76 @@ void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
   SP.bot_desc.upload(bot, s);
 }
 
+// Schedule of the auxiliary levels (the autotuner, tile_rows = 0): each level
+// that has tiles runs either its temporally blocked sweeps or its launches
+// per colour class and sweep, with the same results.  The choice is made on
+// the device: one preconditioner application is captured as a CUDA graph
+// and timed (median of 3 runs of 5 launches) with every level tiled, then
+// each level in turn is switched to class launches and kept so when that is
+// faster by more than 0.5% (and 2 us).  Tiles of levels left untiled are
+// freed.
+template <class T>
+void autotune_levels(asmg_s& h, cudaStream_t s) {
+  Prec<T>& P = prec<T>(h);
+  Slot& S = *h.slots[0];
+  const int nlev = (int)P.lev.size();
+  std::vector<int> cand;
+  for (int li = P.n_bottom; li <= nlev - 1 - P.n_deep; ++li)
+    if (P.lev[li].tiled) cand.push_back(li);
+  if (cand.empty()) return;
+  cudaStream_t cs;
+  ASMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  ASMG_CUDA(cudaEventCreate(&e0));
+  ASMG_CUDA(cudaEventCreate(&e1));
+  auto time_once = [&]() -> float {
+    cudaGraph_t g;
+    cudaGraphExec_t ge;
+    ASMG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    enqueue_precond<T>(h, S, S.r.p, cs);
+    ASMG_CUDA(cudaStreamEndCapture(cs, &g));
+    ASMG_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    float best[3];
+    for (int rep = 0; rep < 3; ++rep) {
+      ASMG_CUDA(cudaGraphLaunch(ge, cs));
+      ASMG_CUDA(cudaEventRecord(e0, cs));
+      for (int k = 0; k < 5; ++k) ASMG_CUDA(cudaGraphLaunch(ge, cs));
+      ASMG_CUDA(cudaEventRecord(e1, cs));
+      ASMG_CUDA(cudaEventSynchronize(e1));
+      ASMG_CUDA(cudaEventElapsedTime(&best[rep], e0, e1));
+    }
+    ASMG_CUDA(cudaGraphExecDestroy(ge));
+    ASMG_CUDA(cudaGraphDestroy(g));
+    std::sort(best, best + 3);
+    return best[1] / 5;
+  };
+  try {
+    float cur = time_once();
+    for (int li : cand) {
+      P.lev[li].tiled = false;
+      const float t = time_once();
+      if (t < cur * 0.995f && cur - t > 0.002f) {
+        cur = t;
+      } else {
+        P.lev[li].tiled = true;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(cs);
+    throw;
+  }
+  ASMG_CUDA(cudaEventDestroy(e0));
+  ASMG_CUDA(cudaEventDestroy(e1));
+  ASMG_CUDA(cudaStreamDestroy(cs));
+  for (int li : cand)
+    if (!P.lev[li].tiled) {
+      P.lev[li].tdown = TileSweeps<T>();
+      P.lev[li].tup = TileSweeps<T>();
+    }
+}
+
 Slot& add_slot(asmg_s& h, cudaStream_t s) {
   h.slots.emplace_back(new Slot());
   Slot& S = *h.slots.back();
@@ -1245,13 +1637,34 @@ Slot& add_slot(asmg_s& h, cudaStream_t s) {
   return S;
 }
 
+// Levels inside the fused small-level runs never use their tiles: drop them.
+template <class T>
+void drop_unused_tiles(Prec<T>& P) {
+  const int nlev = (int)P.lev.size();
+  for (int li = 0; li < nlev; ++li)
+    if (li < P.n_bottom || li > nlev - 1 - P.n_deep) {
+      P.lev[li].tiled = false;
+      P.lev[li].tdown = TileSweeps<T>();
+      P.lev[li].tup = TileSweeps<T>();
+    }
+}
+
 void setup_solve(asmg_s& h, cudaStream_t s) {
-  if (h.prm.precision == ASMG_MIXED)
+  if (h.prm.precision == ASMG_MIXED) {
     setup_small(h.p32);
-  else
+    drop_unused_tiles(h.p32);
+  } else {
     setup_small(h.p64);
+    drop_unused_tiles(h.p64);
+  }
   h.slots.clear();
   add_slot(h, s);
+  if (h.prm.tile_rows == 0) {
+    if (h.prm.precision == ASMG_MIXED)
+      autotune_levels<float>(h, s);
+    else
+      autotune_levels<double>(h, s);
+  }
 }
 
 }  // namespace asmg
