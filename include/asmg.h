@@ -79,6 +79,10 @@ typedef struct {
                               bit): 0 = default, > 0 = own rows per tile (32..65536) of the temporally
                               blocked sweeps (every sweep of a level in one launch, one thread block
                               per tile), -1 = one launch per colour class and sweep; 0 */
+  int32_t inject_timeout;  /* failure injection (testing): 1 = every tiled sweep takes the path of an
+                              expired bounded wait (it still waits for its shared-memory copy, skips
+                              its work and records the timeout), so solves and amg_precond_apply
+                              return ASMG_ERR_TIMEOUT; 0 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */

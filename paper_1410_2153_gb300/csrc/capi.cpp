@@ -59,7 +59,7 @@ int64_t pad32(int64_t n) { return (n + 31) / 32 * 32; }
 // blocks per SM), and the largest halo accepted, as a multiple of the own rows.
 constexpr int TILE_SIZES[] = {256};
 constexpr size_t TILE_SMEM = 110 * 1024;
-constexpr size_t TILE_SMEM_MAX = 200 * 1024;  // one thread block per SM
+constexpr size_t TILE_SMEM_MAX = TILE_SMEM_LIMIT;  // one thread block per SM
 constexpr double TILE_MAX_HALO = 1.5;
 
 // f(begin, end) over contiguous ranges of [0, n) on host threads
@@ -947,6 +947,7 @@ int asmg_default_params(asmg_params* p) {
   p->fine_sweeps = 1;
   p->iteration = 0;
   p->tile_rows = 0;
+  p->inject_timeout = 0;
   return ASMG_OK;
 }
 
@@ -968,7 +969,8 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       prm.coarse_max_dofs > 8192 || (prm.use_pdl != 0 && prm.use_pdl != 1) || (prm.use_graph != 0 && prm.use_graph != 1) ||
       (prm.smoother != 0 && prm.smoother != 1) || (prm.additive != 0 && prm.additive != 1) || prm.fine_sweeps < 1 ||
       prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1) ||
-      (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)))
+      (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)) ||
+      (prm.inject_timeout != 0 && prm.inject_timeout != 1))
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();

@@ -283,6 +283,9 @@ struct SmallLevelDev {
 // -1) and aux ID (int32), then the outside values' aux IDs.  Outside values
 // are the columns outside N~_l of the post-sweeps' rows: the sweeps do not
 // change them, so the tile reads them from U once.
+// dynamic shared memory a tile launch may use (bytes)
+constexpr size_t TILE_SMEM_LIMIT = 200 * 1024;
+
 struct TileLayout {
   int64_t col, val, dinv, lsm, laux, ext, end;  // byte offsets of the parts, and the total
 };

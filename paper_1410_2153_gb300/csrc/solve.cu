@@ -446,11 +446,13 @@ __device__ __forceinline__ void tile_stage(void* dst, const void* src, uint32_t 
 
 // Every thread waits for the copy (bounded); false in every thread when any
 // thread's wait expired, after the timeout is recorded and the copy given a
-// second bounded wait.
-__device__ __forceinline__ bool tile_staged(uint64_t* bar, int* timeout) {
+// second bounded wait.  inject != 0 (failure injection, asmg_params::
+// inject_timeout) takes the expired path without polling; the copy is still
+// waited for before the block exits.
+__device__ __forceinline__ bool tile_staged(uint64_t* bar, int* timeout, int inject) {
   const uint32_t b = smem_addr(bar);
   __syncthreads();  // the barrier was initialised by thread 0 before this point
-  const bool ok = __syncthreads_and(mbar_wait_bounded(b));
+  const bool ok = __syncthreads_and(!inject && mbar_wait_bounded(b));
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(timeout, 1);
     mbar_wait_bounded(b);
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restric
                                                         const unsigned char* __restrict__ blob,
                                                         const int32_t* __restrict__ phase, int ncol, int64_t maxblob,
                                                         int maxloc, const T* __restrict__ F, T* __restrict__ fs,
-                                                        T* __restrict__ us, int nu, int* timeout) {
+                                                        T* __restrict__ us, int nu, int* timeout, int inject) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   const int64_t base = loc_off[blockIdx.x];
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restric
   const int32_t* ph = phase + (int64_t)blockIdx.x * (ncol + 1);
   tile_stage(smraw, blob + b0, bytes, &bar);
   pdl_wait();
-  if (tile_staged(&bar, timeout)) {
+  if (tile_staged(&bar, timeout, inject)) {
     TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, 0, nl, 0);
     for (int k = threadIdx.x; k < nl; k += blockDim.x) {
       const int32_t g = t.lsm[k];
@@ -604,7 +606,8 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict_
                                                       const int64_t* __restrict__ ext_off,
                                                       const int32_t* __restrict__ phase, int ncol, int64_t maxblob,
                                                       int maxloc, int maxext, const T* __restrict__ fs,
-                                                      const T* __restrict__ us, T* U, int nu, int* timeout) {
+                                                      const T* __restrict__ us, T* U, int nu, int* timeout,
+                                                      int inject) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   const int64_t base = loc_off[blockIdx.x];
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict_
   const int32_t* ph = phase + (int64_t)blockIdx.x * (ncol + 1);
   tile_stage(smraw, blob + b0, bytes, &bar);
   pdl_wait();
-  if (tile_staged(&bar, timeout)) {
+  if (tile_staged(&bar, timeout, inject)) {
     TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, maxext, nl, nx);
     for (int k = threadIdx.x; k < nl; k += blockDim.x) {
       const int32_t g = t.lsm[k];
@@ -799,8 +802,20 @@ __device__ bool grid_reduce(double (&v)[NV], double* partial, unsigned int* tick
   if (!last) return false;
   __threadfence();
   for (int j = 0; j < NV; ++j) {
+    // the partials of this thread (blocks t, t + blockDim, ...) summed in
+    // ascending order, eight loads in flight
+    const double* pj = partial + (int64_t)j * gridDim.x;
     double s = 0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) s += __ldcg(partial + j * gridDim.x + b);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 8 * blockDim.x) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const unsigned bb = b + u * blockDim.x;
+        x[u] = bb < gridDim.x ? __ldcg(pj + bb) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += x[u];
+    }
     v[j] = block_sum(s, sh);
   }
   if (threadIdx.x == 0) *ticket = 0;
@@ -1097,7 +1112,8 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
       LAUNCH(ASMG_PROF_AUX_GS, by,
              launch_smem(h.prm.use_pdl, k_tile_down<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p,
                          Tl.blob_off.p, (const unsigned char*)Tl.blob.p, Tl.phase.p, L.ncolours, Tl.maxblob,
-                         Tl.maxloc, (const T*)SP.F.p, SP.fs[li].p, SP.us[li].p, npre, timeout_flag(S)));
+                         Tl.maxloc, (const T*)SP.F.p, SP.fs[li].p, SP.us[li].p, npre, timeout_flag(S),
+                         h.prm.inject_timeout));
       ++launches;
     }
     // pre-sweeps on us (SM order); the first also saves F on N~_l for the
@@ -1153,7 +1169,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
              launch_smem(h.prm.use_pdl, k_tile_up<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p, Tl.blob_off.p,
                          (const unsigned char*)Tl.blob.p, Tl.ext_off.p, Tl.phase.p, L.ncolours, Tl.maxblob,
                          Tl.maxloc, Tl.maxext, (const T*)SP.fs[li].p, (const T*)SP.us[li].p, SP.U.p, npost,
-                         timeout_flag(S)));
+                         timeout_flag(S), h.prm.inject_timeout));
       launches += 2;
       continue;
     }
@@ -1470,13 +1486,10 @@ void setup_small(Prec<T>& P) {
   const int smem = (int)small_smem<T>();
   ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int tsm = 0;
-  for (auto& L : P.lev)
-    if (L.tiled) tsm = std::max<int>(tsm, (int)std::max(L.tdown.smem(), L.tup.smem()));
-  if (tsm > 0) {
-    ASMG_CUDA(cudaFuncSetAttribute(k_tile_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-    ASMG_CUDA(cudaFuncSetAttribute(k_tile_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsm));
-  }
+  // the attribute belongs to the kernel, not to this handle: every handle sets
+  // the same bound, the largest a tile may use
+  ASMG_CUDA(cudaFuncSetAttribute(k_tile_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
+  ASMG_CUDA(cudaFuncSetAttribute(k_tile_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
 }
 
 // Work state of one solve in precision T: vectors, per-level saved values,
@@ -1659,7 +1672,7 @@ void setup_solve(asmg_s& h, cudaStream_t s) {
   }
   h.slots.clear();
   add_slot(h, s);
-  if (h.prm.tile_rows == 0) {
+  if (h.prm.tile_rows == 0 && !h.prm.inject_timeout) {
     if (h.prm.precision == ASMG_MIXED)
       autotune_levels<float>(h, s);
     else
