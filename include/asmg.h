@@ -43,7 +43,7 @@ enum asmg_status {
   ASMG_NOT_CONVERGED = 1,     /* max_iter reached; u holds the last iterate */
   ASMG_ERR_INVALID_ARG = -1,  /* null pointer, bad size or bad parameter */
   ASMG_ERR_BAD_MESH = -2,     /* index out of range, non-positive measure, bad flag or coefficient */
-  ASMG_ERR_UNSUPPORTED = -3,  /* Neumann flags, dim not supported */
+  ASMG_ERR_UNSUPPORTED = -3,  /* dim not supported, or a colouring beyond 128 colours */
   ASMG_ERR_BREAKDOWN = -4,    /* <p, A p> <= 0 or NaN, or <r, z> <= 0 in PCG */
   ASMG_ERR_CUDA = -5,         /* a CUDA runtime call failed */
   ASMG_ERR_OOM = -6,          /* device allocation failed */
@@ -83,6 +83,9 @@ typedef struct {
                               expired bounded wait (it still waits for its shared-memory copy, skips
                               its work and records the timeout), so solves and amg_precond_apply
                               return ASMG_ERR_TIMEOUT; 0 */
+  int32_t nb_layers;       /* mixed boundaries: layers j of the near-boundary sets J_{l,j} of Algorithm 3
+                              (Sec. 3.5), whose exact solve follows each coarse-grid correction;
+                              -1 = no near-boundary correction, 0..16; 2 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */
@@ -98,8 +101,15 @@ int asmg_default_params(asmg_params* p);
  *   ne, elements   int32 [ne * (dim + 1)], vertex indices of each simplex,
  *                  positively oriented (counter-clockwise triangles;
  *                  tetrahedra with (p1-p0).((p2-p0)x(p3-p0)) > 0).
- *   boundary   uint8 [nv]: 0 free vertex, 1 Dirichlet vertex (u = 0).  The
- *              value 2 (Neumann) returns ASMG_ERR_UNSUPPORTED.
+ *   boundary   uint8 [nv]: 0 free vertex, 1 Dirichlet vertex (u = 0), 2
+ *              Neumann vertex (a boundary vertex that is an unknown: the
+ *              natural condition).  With any Neumann vertex the auxiliary
+ *              grids are the mixed grids of the remark in Sec. 3.4 (the
+ *              simplices that meet the domain and not the Dirichlet boundary
+ *              Gamma_D, Gamma_D being the boundary facets whose vertices are
+ *              all Dirichlet), every level is smoothed as a whole, and the
+ *              V-cycle adds the near-boundary correction of Algorithm 3 (an
+ *              exact solve on J_{l,j}, see nb_layers).
  *   coeff      float64 [ne] per-element coefficient a_e > 0, or NULL for a = 1.
  *   params     NULL for the defaults.
  *   out        receives the handle (NULL on error).
@@ -261,7 +271,8 @@ enum asmg_prof_class {
   ASMG_PROF_CG_SPMV = 8,      /* PCG q = A p with <p, q> (FP64) */
   ASMG_PROF_CG_VECTOR = 9,    /* PCG vector updates and reductions */
   ASMG_PROF_AUX_SMALL = 10,   /* runs of small auxiliary levels fused into one thread block */
-  ASMG_PROF_NCLASS = 11
+  ASMG_PROF_AUX_NB = 11,      /* near-boundary residual and exact solve (Algorithm 3, mixed boundaries) */
+  ASMG_PROF_NCLASS = 12
 };
 int amg_profile(asmg_handle h, const double* b, double rtol, double* out, int* iterations, void* stream);
 

@@ -43,7 +43,7 @@ class asmg_params(ctypes.Structure):
                 ("smoothing", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("use_pdl", ctypes.c_int32),
                 ("smoother", ctypes.c_int32), ("additive", ctypes.c_int32), ("fine_sweeps", ctypes.c_int32),
                 ("iteration", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-                ("inject_timeout", ctypes.c_int32)]
+                ("inject_timeout", ctypes.c_int32), ("nb_layers", ctypes.c_int32)]
 
 
 class AsmgError(RuntimeError):
@@ -206,7 +206,7 @@ def amg_export(h, what, level: int = 0) -> np.ndarray:
 
 
 PROF_CLASSES = ["fine_gs", "fine_resid", "restrict", "prolong", "aux_gs", "aux_resid", "aux_transfer", "coarse",
-                "cg_spmv", "cg_vector", "aux_small"]
+                "cg_spmv", "cg_vector", "aux_small", "aux_nb"]
 
 
 def amg_profile(h, b, rtol: float, stream=None):

@@ -472,6 +472,75 @@ bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel
   return true;
 }
 
+// The near-boundary solve of a level (mixed boundaries, Algorithm 3) for the
+// device: the rows of A_l on J_{l,j} in the factor's order (all columns) and
+// the block cyclic reduction flattened into NbDev.
+template <class T>
+void build_nb_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& pos, AuxLevelDev<T>& D,
+                  cudaStream_t s) {
+  const nb::Factor& Fz = L.nb_fac;
+  NbDev& N = D.nb;
+  N.m = (int64_t)L.nb_id.size();
+  if (N.m == 0) return;
+  if (!Fz.ok || Fz.m != N.m) ASMG_FAIL(ASMG_ERR_BAD_MESH, "auxiliary level %d: no near-boundary factor", L.level);
+  std::vector<int32_t> aux(N.m), sm(N.m);
+  std::vector<int64_t> sel(N.m);
+  for (int64_t q = 0; q < N.m; ++q) {
+    const int32_t a = L.nb_id[Fz.order[q]];
+    aux[q] = a;
+    sm[q] = pos[a];
+    sel[q] = a;
+    if (sm[q] < 0) ASMG_FAIL(ASMG_ERR_BAD_MESH, "auxiliary level %d: near-boundary node outside the level", L.level);
+  }
+  HostCSR rows = select_rows(Arows, sel, nullptr, nullptr);
+  sell_build<T>(D.NB, rows, 0, s);
+  // block sizes of round 0, then the even blocks of each round form the next
+  std::vector<int> sz0;
+  for (size_t b = 0; b + 1 < Fz.bstart.size(); ++b) sz0.push_back((int)(Fz.bstart[b + 1] - Fz.bstart[b]));
+  N.R = (int)Fz.rounds.size();
+  std::vector<int32_t> nblk, boff;
+  std::vector<int64_t> btab, voff(1, 0);
+  std::vector<double> mats;
+  auto put = [&](const nb::Blk& B) -> int64_t {
+    if (B.empty()) return -1;
+    const int64_t o = (int64_t)mats.size();
+    mats.insert(mats.end(), B.a.begin(), B.a.end());
+    return o;
+  };
+  std::vector<int> sz = sz0;
+  for (int r = 0; r < N.R; ++r) {
+    const nb::Round& Rd = Fz.rounds[r];
+    if (Rd.n != (int)sz.size()) ASMG_FAIL(ASMG_ERR_CUDA, "near-boundary factor: inconsistent rounds");
+    nblk.push_back(Rd.n);
+    boff.push_back((int32_t)(btab.size() / 5));
+    int64_t off = 0;
+    for (int k = 0; k < Rd.n; ++k) {
+      btab.push_back(sz[k]);
+      btab.push_back(off);
+      btab.push_back((k & 1) ? put(Rd.F[k]) : -1);
+      btab.push_back(k > 0 ? put(Rd.Lo[k]) : -1);
+      btab.push_back(k + 1 < Rd.n ? put(Rd.Up[k]) : -1);
+      off += sz[k];
+    }
+    voff.push_back(voff.back() + off);
+    std::vector<int> nx;
+    for (int k = 0; k < Rd.n; k += 2) nx.push_back(sz[k]);
+    sz.swap(nx);
+  }
+  if (sz.size() != 1 || Fz.last.r != sz[0]) ASMG_FAIL(ASMG_ERR_CUDA, "near-boundary factor: inconsistent last block");
+  N.last_size = sz[0];
+  N.last_off = put(Fz.last);
+  voff.push_back(voff.back() + sz[0]);  // the last block's vector, then the pool size
+  N.nblk_h = nblk;
+  N.nblk.upload(nblk, s);
+  N.boff.upload(boff, s);
+  N.btab.upload(btab, s);
+  N.voff.upload(voff, s);
+  N.mats.upload(mats, s);
+  N.aux.upload(aux, s);
+  N.sm.upload(sm, s);
+}
+
 template <class T>
 void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
                      const std::vector<uint8_t>& inset, const asmg_params& prm, AuxLevelDev<T>& D, cudaStream_t s) {
@@ -605,7 +674,11 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
   D.rp_id.upload(pid, s);
   D.rp_ptr.upload(pptr, s);
   D.rp_child.upload(child, s);
-  build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, D, s);
+  build_nb_dev<T>(L, Arows, pos, D, s);
+  // a level with a near-boundary solve keeps its own launches (the solve sits
+  // between the coarse correction and the post-smoothing)
+  if (D.nb.m == 0) build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, D, s);
+  else D.small.ok = false;
 }
 
 // triangles given by lattice keys -> device coordinates, ids, coefficients
@@ -686,7 +759,7 @@ void build_all(asmg_s& h, cudaStream_t s) {
   h.free_of_vertex.assign(nv, -1);
   h.vertex_of_free.clear();
   for (int64_t v = 0; v < nv; ++v)
-    if (m.bflag[v] == 0) {
+    if (m.bflag[v] != 1) {  // free and Neumann vertices are unknowns
       h.free_of_vertex[v] = (int32_t)h.vertex_of_free.size();
       h.vertex_of_free.push_back((int32_t)v);
     }
@@ -948,6 +1021,7 @@ int asmg_default_params(asmg_params* p) {
   p->iteration = 0;
   p->tile_rows = 0;
   p->inject_timeout = 0;
+  p->nb_layers = 2;
   return ASMG_OK;
 }
 
@@ -970,7 +1044,7 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       (prm.smoother != 0 && prm.smoother != 1) || (prm.additive != 0 && prm.additive != 1) || prm.fine_sweeps < 1 ||
       prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1) ||
       (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)) ||
-      (prm.inject_timeout != 0 && prm.inject_timeout != 1))
+      (prm.inject_timeout != 0 && prm.inject_timeout != 1) || prm.nb_layers < -1 || prm.nb_layers > 16)
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();
@@ -985,8 +1059,15 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
   m.bflag = to_host(boundary, nv, s);
   if (coeff) m.coeff = to_host(coeff, ne, s);
   for (int64_t v = 0; v < nv; ++v) {
-    if (m.bflag[v] == 2) ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "Neumann vertices are not supported");
     if (m.bflag[v] > 2) ASMG_FAIL(ASMG_ERR_BAD_MESH, "boundary flag %d at vertex %lld", (int)m.bflag[v], (long long)v);
+    if (m.bflag[v] == 2) m.mixed = true;
+  }
+  m.nb_layers = prm.nb_layers;
+  if (m.mixed) {
+    // the mixed grids are not nested and every level is smoothed as a whole;
+    // the near-boundary solve runs between the coarse correction and the
+    // post-smoothing, so those levels take the per-class launches
+    h->prm.tile_rows = -1;
   }
   for (int64_t e = 0; e < (int64_t)m.coeff.size(); ++e)
     if (!(m.coeff[e] > 0) || !std::isfinite(m.coeff[e]))
@@ -1395,7 +1476,14 @@ int amg_info(asmg_handle h, int what, int level, int64_t* value) {
     case ASMG_INFO_COARSE: *value = h->aux.c; break;
     case ASMG_INFO_NAUX:
       if (level < 0 || level > h->aux.J) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "bad level");
-      *value = h->aux.nlevel[level];
+      if (!h->aux.phi.empty()) {
+        // mixed grids: the nodes free on this level (phi <= l < psi)
+        int64_t c = 0;
+        for (size_t q = 0; q < h->aux.phi.size(); ++q) c += h->aux.phi[q] <= level && level < h->aux.psi[q];
+        *value = c;
+      } else {
+        *value = h->aux.nlevel[level];
+      }
       break;
     case ASMG_INFO_NSMOOTH: *value = level < 0 ? h->n : nsm(lev_index(level)); break;
     case ASMG_INFO_NCOLOURS:

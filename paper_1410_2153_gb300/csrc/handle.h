@@ -40,6 +40,7 @@ template <class T>
 struct SlotPrec {
   DBuf<T> uf, rho, F, U;            // fine work vector, fine residual, aux rhs / correction
   std::vector<DBuf<T>> fs, us;      // per level: saved rhs / pre-smoothed values on N~_l
+  std::vector<DBuf<double>> nbr, nbs;  // per level: near-boundary rhs / solution pools (mixed boundaries)
   DBuf<SmallDesc<T>> deep_desc, bot_desc;
 };
 

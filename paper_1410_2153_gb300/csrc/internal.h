@@ -322,6 +322,28 @@ struct TileSweeps {
   size_t smem() const { return (size_t)maxblob + (size_t)(maxloc + maxext) * sizeof(T) + (size_t)maxloc * sizeof(T); }
 };
 
+// The exact near-boundary solve of Algorithm 3 on the device: the block
+// cyclic reduction of nb::Factor flattened into arrays.  Ordered positions q
+// (0..m-1) follow the factor's breadth-first order.  Round r has nblk[r]
+// blocks; block k of round r is described by 5 int64 at btab[(boff[r] + k) * 5]:
+// size, offset within the round's vector, and the offsets in `mats` of its
+// Cholesky factor F (odd blocks), Lo and Up (-1 when absent); all matrices
+// dense row-major FP64.  The round-r vectors live at voff[r] in the rhs and
+// solution pools (voff[R] = pool size).  `last` is the factor of the one
+// block left after the rounds.
+struct NbDev {
+  int64_t m = 0;
+  int R = 0;
+  int last_size = 0;
+  int64_t last_off = 0;
+  std::vector<int32_t> nblk_h;     // host copy of the per-round block counts
+  DBuf<int32_t> nblk, boff;        // [R]
+  DBuf<int64_t> btab, voff;        // [sum nblk * 5], [R + 1]
+  DBuf<double> mats;
+  DBuf<int32_t> aux;               // [m] aux ID of ordered position q
+  DBuf<int32_t> sm;                // [m] SM row of ordered position q (the saved rhs fs is in SM order)
+};
+
 // ------------------------------------------------------------ solve data
 template <class T>
 struct AuxLevelDev {
@@ -350,6 +372,11 @@ struct AuxLevelDev {
   int tile_rows = 0;                 // own rows per tile
   TileSweeps<T> tdown, tup;
   DBuf<int32_t> sm_par0, sm_par1;    // per SM row: parents of a new node (-1 Dirichlet), -3 not new
+  // mixed boundaries: the near-boundary correction of Algorithm 3 (nb.m > 0):
+  // rows of A_l on J_{l,j} in ordered positions (all columns, aux IDs) and the
+  // flattened factor
+  NbDev nb;
+  Sell<T> NB;
 };
 
 struct Stats {

@@ -647,6 +647,137 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict_
   pdl_trigger();
 }
 
+// ------------------------------------------- near-boundary solve (Alg. 3)
+// After the coarse-grid correction of a level with mixed boundaries:
+// r_J = f_J - (A_l U)_J on the near-boundary set J = J_{l,j}, then the exact
+// solve A_JJ d = r_J by block cyclic reduction (NbDev), then U_J += d.
+
+// r_J in the factor's order (the saved rhs of a whole-level smoothing set)
+template <class T>
+__global__ void k_nb_resid(int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                           const T* __restrict__ val, const int32_t* __restrict__ sm, const T* __restrict__ fs,
+                           const T* U, double* __restrict__ rhs) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool act = q < m;
+  Row<T> row;
+  int32_t k = 0;
+  if (act) {
+    row_load(row, q, off, col, val);
+    k = sm[q];
+  }
+  pdl_wait();
+  if (act) rhs[q] = (double)(fs[k] - row_dot(row, col, val, U));
+  pdl_trigger();
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x := F^{-T} F^{-1} x for the lower Cholesky factor F (s x s, row-major) of
+// a block, one warp; x in global memory (lane 0 writes, __syncwarp orders)
+__device__ void nb_chol_solve(const double* __restrict__ F, int s, double* x) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < s; ++i) {
+    double t = 0;
+    for (int k = lane; k < i; k += 32) t += F[(int64_t)i * s + k] * x[k];
+    t = warp_sum(t);
+    if (lane == 0) x[i] = (x[i] - t) / F[(int64_t)i * s + i];
+    __syncwarp();
+  }
+  for (int i = s - 1; i >= 0; --i) {
+    double t = 0;
+    for (int k = i + 1 + lane; k < s; k += 32) t += F[(int64_t)k * s + i] * x[k];
+    t = warp_sum(t);
+    if (lane == 0) x[i] = (x[i] - t) / F[(int64_t)i * s + i];
+    __syncwarp();
+  }
+}
+
+// y -= M z for M (r x c, row-major), one warp, lanes over the rows
+__device__ void nb_gemv_sub(const double* __restrict__ M, int r, int c, const double* z, double* y) {
+  for (int i = threadIdx.x & 31; i < r; i += 32) {
+    double t = y[i];
+    for (int j = 0; j < c; ++j) t -= M[(int64_t)i * c + j] * z[j];
+    y[i] = t;
+  }
+  __syncwarp();
+}
+
+__device__ void nb_copy(const double* src, double* dst, int n) {
+  for (int i = threadIdx.x & 31; i < n; i += 32) dst[i] = src[i];
+  __syncwarp();
+}
+
+constexpr int NB_TPB = 1024;
+
+// One thread block: the rounds of the reduction (odd blocks solved, even
+// blocks' right-hand sides updated), the last block, then the rounds
+// backwards (odd blocks from their even neighbours), then U_J += d.  The
+// blocks of a step are independent: one warp each.
+template <class T>
+__global__ void __launch_bounds__(NB_TPB) k_nb_solve(int R, const int32_t* __restrict__ nblk,
+                                                     const int32_t* __restrict__ boff, const int64_t* __restrict__ btab,
+                                                     const int64_t* __restrict__ voff, const double* __restrict__ mats,
+                                                     int last_size, int64_t last_off, int64_t m,
+                                                     const int32_t* __restrict__ aux, double* rhs, double* sol, T* U) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  pdl_wait();
+  for (int r = 0; r < R; ++r) {
+    const int n = nblk[r];
+    const int64_t* bt = btab + (int64_t)boff[r] * 5;
+    double* V = rhs + voff[r];
+    double* Y = sol + voff[r];
+    double* Vn = rhs + voff[r + 1];
+    const int64_t* btn = r + 1 < R ? btab + (int64_t)boff[r + 1] * 5 : nullptr;
+    for (int k = 1 + 2 * warp; k < n; k += 2 * nw) {
+      const int sk = (int)bt[5 * k];
+      const int64_t o = bt[5 * k + 1];
+      nb_copy(V + o, Y + o, sk);
+      nb_chol_solve(mats + bt[5 * k + 2], sk, Y + o);
+    }
+    __syncthreads();
+    for (int e = 2 * warp; e < n; e += 2 * nw) {
+      const int se = (int)bt[5 * e];
+      const int64_t o = bt[5 * e + 1], on = btn ? btn[5 * (e / 2) + 1] : 0;
+      nb_copy(V + o, Vn + on, se);
+      if (e > 0) nb_gemv_sub(mats + bt[5 * e + 3], se, (int)bt[5 * (e - 1)], Y + bt[5 * (e - 1) + 1], Vn + on);
+      if (e + 1 < n) nb_gemv_sub(mats + bt[5 * e + 4], se, (int)bt[5 * (e + 1)], Y + bt[5 * (e + 1) + 1], Vn + on);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    nb_copy(rhs + voff[R], sol + voff[R], last_size);
+    nb_chol_solve(mats + last_off, last_size, sol + voff[R]);
+  }
+  __syncthreads();
+  for (int r = R - 1; r >= 0; --r) {
+    const int n = nblk[r];
+    const int64_t* bt = btab + (int64_t)boff[r] * 5;
+    const double* V = rhs + voff[r];
+    double* S = sol + voff[r];
+    const double* Sn = sol + voff[r + 1];
+    const int64_t* btn = r + 1 < R ? btab + (int64_t)boff[r + 1] * 5 : nullptr;
+    for (int e = 2 * warp; e < n; e += 2 * nw) {
+      const int64_t on = btn ? btn[5 * (e / 2) + 1] : 0;
+      nb_copy(Sn + on, S + bt[5 * e + 1], (int)bt[5 * e]);
+    }
+    __syncthreads();
+    for (int k = 1 + 2 * warp; k < n; k += 2 * nw) {
+      const int sk = (int)bt[5 * k];
+      const int64_t o = bt[5 * k + 1];
+      nb_copy(V + o, S + o, sk);
+      nb_gemv_sub(mats + bt[5 * k + 3], sk, (int)bt[5 * (k - 1)], S + bt[5 * (k - 1) + 1], S + o);
+      if (k + 1 < n) nb_gemv_sub(mats + bt[5 * k + 4], sk, (int)bt[5 * (k + 1)], S + bt[5 * (k + 1) + 1], S + o);
+      nb_chol_solve(mats + bt[5 * k + 2], sk, S + o);
+    }
+    __syncthreads();
+  }
+  for (int64_t q = threadIdx.x; q < m; q += blockDim.x) U[aux[q]] += (T)sol[q];
+  pdl_trigger();
+}
+
 // ---------------------------------------------------- small levels, fused
 // A run of small levels in one thread block.  Per level the rhs F and the
 // correction U of the rows E_l, and the row pointers of its smoothing and
@@ -1182,6 +1313,18 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (4 + 3 * sz),
            launch(h.prm.use_pdl, k_addsaved_aux<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p, SP.us[li].p, SP.U.p));
     ++launches;
+    if (L.nb.m > 0) {
+      // Algorithm 3: exact solve on the near-boundary set after the coarse correction
+      const NbDev& N = L.nb;
+      LAUNCH(ASMG_PROF_AUX_NB, L.NB.nnz_real * (sz + 4) + N.m * (16 + 2 * sz),
+             launch(h.prm.use_pdl, k_nb_resid<T>, nblk(N.m), TPB, s, N.m, L.NB.off.p, L.NB.col.p, L.NB.val.p, N.sm.p,
+                    (const T*)SP.fs[li].p, (const T*)SP.U.p, SP.nbr[li].p));
+      LAUNCH(ASMG_PROF_AUX_NB, (int64_t)N.mats.n * 8 + N.m * (8 + 2 * sz),
+             launch(h.prm.use_pdl, k_nb_solve<T>, 1, NB_TPB, s, N.R, N.nblk.p, N.boff.p, N.btab.p, N.voff.p,
+                    (const double*)N.mats.p, N.last_size, N.last_off, N.m, N.aux.p, SP.nbr[li].p, SP.nbs[li].p,
+                    SP.U.p));
+      launches += 2;
+    }
     for (int sweep = 0; sweep < npost; ++sweep)
       for (int c = L.ncolours - 1; c >= 0; --c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
@@ -1510,11 +1653,28 @@ void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
   SP.us.clear();
   SP.fs.resize(nlev);
   SP.us.resize(nlev);
+  SP.nbr.clear();
+  SP.nbs.clear();
+  SP.nbr.resize(nlev);
+  SP.nbs.resize(nlev);
   for (int li = 0; li < nlev; ++li) {
     SP.fs[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
     SP.us[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
     SP.fs[li].zero(s);
     SP.us[li].zero(s);
+    const NbDev& N = P.lev[li].nb;
+    if (N.m > 0) {
+      // the pools: every round's vector and the last block's (voff[R + 1] doubles)
+      int64_t pool = 0;
+      {
+        std::vector<int64_t> vo = N.voff.download(s);
+        pool = vo.back();
+      }
+      SP.nbr[li].alloc(pool);
+      SP.nbs[li].alloc(pool);
+      SP.nbr[li].zero(s);
+      SP.nbs[li].zero(s);
+    }
   }
   auto desc = [&](int li) {
     AuxLevelDev<T>& L = P.lev[li];

@@ -65,16 +65,18 @@ def test_rejections_before_any_gpu_work(lib, gen):
     assert _setup_code(lib, m, dim=1) == lib.ASMG_ERR_UNSUPPORTED
     t = gen.grid3d(3, 1)                                         # tetrahedra take the same checks
     t.bflag = t.bflag.copy()
-    t.bflag[0] = 2
-    assert _setup_code(lib, t, dim=3) == lib.ASMG_ERR_UNSUPPORTED
+    t.bflag[0] = 3
+    assert _setup_code(lib, t, dim=3) == lib.ASMG_ERR_BAD_MESH
     t = gen.grid3d(3, 1)
     t.coeff = np.ones(t.ne)
     t.coeff[5] = 0.0
     assert _setup_code(lib, t, dim=3) == lib.ASMG_ERR_BAD_MESH
-    m2 = _mesh(gen)
-    m2.bflag = m2.bflag.copy()
-    m2.bflag[0] = 2
-    assert _setup_code(lib, m2) == lib.ASMG_ERR_UNSUPPORTED      # Neumann
+    # Neumann vertices (flag 2) are accepted: only the parameters of the
+    # near-boundary correction and of the schedule are checked here
+    assert _setup_code(lib, _mesh(gen), nb_layers=-2) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, _mesh(gen), nb_layers=17) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, _mesh(gen), tile_rows=5) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, _mesh(gen), inject_timeout=2) == lib.ASMG_ERR_INVALID_ARG
     m3 = _mesh(gen)
     m3.bflag = m3.bflag.copy()
     m3.bflag[0] = 7
