@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from conftest import oracle_iterate  # noqa: E402
+from conftest import mixed_iterations_ok, oracle_iterate  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -165,9 +165,9 @@ def test_domain_solves_match_oracle(cases, gen, A, name):
 # the coverage of the tetrahedra at the jagged domain boundary comes from two
 # different exact clippers (positive pieces here, signed pieces in the
 # oracle) whose rounding differs by up to ~1e-11 of a tetrahedron's volume,
-# and the rediscretised level operators carry it: one B application is
-# compared at 1e-9, FP64 solutions at 1e-8 (the same load vector on both
-# sides).
+# and the rediscretised level operators carry it.  One B application and the
+# FP64 solutions are held to the box-domain 1e-10 (measured: 8e-11 with the
+# cut 1e3 jump, 4e-16 otherwise; the same load vector on both sides).
 def _meshes3(gen):
     lj = gen.grid3d_domain(11, 3, "L")
     lj.coeff = gen.subcube_coefficient(lj, 5, ncube=4)
@@ -241,7 +241,7 @@ def test_domain3d_operators_transfer_preconditioner(cases3, name):
     r[vf] = rng.uniform(-1, 1, o.nfree)
     z_ref = o.precond(r[vf])
     z = s.precond(torch.from_numpy(r).cuda()).cpu().numpy()
-    assert np.linalg.norm(z[vf] - z_ref) <= 1e-9 * np.linalg.norm(z_ref)
+    assert np.linalg.norm(z[vf] - z_ref) <= 1e-10 * np.linalg.norm(z_ref)
     assert np.all(z[m.bflag == 1] == 0)
 
 
@@ -259,12 +259,16 @@ def test_domain3d_solves_match_oracle(cases3, gen, A, name):
     u = u.cpu().numpy()
     assert rc == A.ASMG_OK and abs(it - it_ref) <= 2, (it, it_ref)
     u_same = u_ref if it == it_ref else oracle_iterate(m, b_ref, it, **po)
-    assert np.linalg.norm(u[vf] - u_same) <= 1e-8 * np.linalg.norm(u_same)
+    assert np.linalg.norm(u[vf] - u_same) <= 1e-10 * np.linalg.norm(u_same)
     assert np.linalg.norm(b_ref - o.spmv(u[vf])) <= 2e-8 * np.linalg.norm(b_ref)
     sm = A.Solver(m, precision=A.ASMG_MIXED, **p)
     u2, rc2, it2, _ = sm.solve(torch.from_numpy(bv).cuda(), rtol=1e-8)
+    u2 = u2.cpu().numpy()
     # the FP32 V-cycle perturbs B; with the 1e3 coefficient jump cut by the
-    # domain the flexible CG then takes up to a fifth more steps (37 -> 44)
-    assert rc2 == A.ASMG_OK and abs(it2 - it_ref) <= max(2, 0.25 * it_ref), (it2, it_ref)
-    assert np.linalg.norm(u2.cpu().numpy()[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+    # domain the flexible CG takes more steps (37 -> 44): accepted only with
+    # the rtol-1e-13 check of mixed_iterations_ok
+    assert rc2 == A.ASMG_OK
+    ok, msg = mixed_iterations_ok(m, b_ref, it2, it_ref, u2[vf], **po)
+    assert ok, msg
+    assert np.linalg.norm(u2[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
     sm.close()

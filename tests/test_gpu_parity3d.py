@@ -9,9 +9,10 @@ fine A and level operators 1e-12 of the largest entry (rediscretisation with
 volume-averaged coefficients vs the oracle's Galerkin products), P 1e-11
 absolute, one B_co application 1e-11 relative, FP64 solutions 1e-10 relative
 with iterations within 2, mixed solutions 1e-6 relative with iterations
-within max(2, 10%): the FP32 V-cycle is a perturbed preconditioner, and with
-a 1e3 coefficient jump the flexible CG needs ~110 steps, where the
-perturbation shifts the count by a few.
+within 2 -- or, where the FP32 V-cycle (a perturbed preconditioner) costs the
+flexible CG more steps, as with a 1e3 coefficient jump (112 -> 119 steps),
+with the check of conftest.mixed_iterations_ok: the mixed solution is as
+close to the oracle's rtol-1e-13 solve as the oracle's own rtol-1e-8 solution.
 """
 import numpy as np
 import pytest
@@ -20,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from conftest import oracle_iterate  # noqa: E402
+from conftest import mixed_iterations_ok, oracle_iterate  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -158,7 +159,9 @@ def test_3d_solves_match_oracle(cases, gen, A, name):
     sm = A.Solver(m, precision=A.ASMG_MIXED, **p)
     u2, rc2, it2, _ = sm.solve(sm.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
     u2 = u2.cpu().numpy()
-    assert rc2 == A.ASMG_OK and abs(it2 - it_ref) <= max(2, 0.1 * it_ref), (it2, it_ref)
+    assert rc2 == A.ASMG_OK
+    ok, msg = mixed_iterations_ok(m, b_ref, it2, it_ref, u2[vf], **p)
+    assert ok, msg
     assert np.linalg.norm(u2[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
     sm.close()
 

@@ -4,13 +4,16 @@ B = S + Pi Btilde Pi^t (eq. fasp), several fine smoothing steps per
 application, and the ASMG iteration u <- u + B (b - A u) (Sec. 5.1).
 
 Tolerances as in the parity tests: one B application 1e-11 relative (FP64),
-FP64 solutions 1e-10 relative, mixed solutions 1e-6.  Iterations within
-max(2, 10%): with the undamped Jacobi smoother on the graded mesh B is far
-from the ideal preconditioner and the flexible CG's step count is sensitive
-to rounding (58 vs 63 steps at 65^2) while single applications agree to
-1e-11.  Residual histories of the ASMG iteration agree to 1e-9 relative, or
-to 1e-13 of the first residual where they reach the rounding floor of
-b - A x.
+FP64 solutions 1e-10 relative (1e-9 for the Jacobi forms, whose ~60 flexible
+CG steps on the graded mesh carry the ~1e-14 differences of the clipped
+transfer entries), mixed solutions 1e-6.  Iterations within 2; with the
+undamped Jacobi smoother on the graded mesh B is far from the ideal
+preconditioner and the flexible CG's step count is sensitive to rounding, so
+a larger difference is accepted only with the check of
+conftest.mixed_iterations_ok (the solution as close to the oracle's
+rtol-1e-13 solve as the oracle's own).  Residual histories of the ASMG
+iteration agree to 1e-9 relative, or to 1e-13 of the first residual where
+they reach the rounding floor of b - A x.
 """
 import numpy as np
 import pytest
@@ -19,7 +22,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
-from conftest import oracle_iterate  # noqa: E402
+from conftest import mixed_iterations_ok, oracle_iterate  # noqa: E402
 
 VARIANTS = {  # (smoother, additive, fine_sweeps)
     "jacobi": (1, 0, 1),
@@ -56,23 +59,27 @@ def test_variant_preconditioner_and_solve(gen, mesh, variant):
     b_ref = o.mass_apply(f)
     u_ref, st, it_ref, _ = o.solve(b_ref, rtol=1e-8)
     assert st == 0
-    # the oracle's load vector on both sides: the device mass product adds
-    # with atomics, and the Jacobi forms amplify its rounding differences
+    # the oracle's load vector on both sides (the Jacobi forms amplify any
+    # rounding difference of the right-hand side)
     bv = np.zeros(m.nv)
     bv[vf] = b_ref
     u, rc, it, _ = s.solve(torch.from_numpy(bv).cuda(), rtol=1e-8)
     u = u.cpu().numpy()
-    assert rc == asmg.ASMG_OK and abs(it - it_ref) <= max(2, 0.1 * it_ref), (it, it_ref)
-    u_same = u_ref if it == it_ref else oracle_iterate(m, b_ref, it, smoother=sm, additive=add, fine_sweeps=fs)
-    # Jacobi forms take ~60 flexible CG steps on the graded mesh, which carry
-    # the ~1e-14 differences of the clipped transfer entries to a few 1e-10
+    pr = dict(smoother=sm, additive=add, fine_sweeps=fs)
+    assert rc == asmg.ASMG_OK
+    ok, msg = mixed_iterations_ok(m, b_ref, it, it_ref, u[vf], **pr)
+    assert ok, msg
+    u_same = u_ref if it == it_ref else oracle_iterate(m, b_ref, it, **pr)
     tol = 1e-9 if sm == 1 else 1e-10
     assert np.linalg.norm(u[vf] - u_same) <= tol * np.linalg.norm(u_same)
     s.close()
     sm32 = asmg.Solver(m, precision=asmg.ASMG_MIXED, smoother=sm, additive=add, fine_sweeps=fs)
     u2, rc2, it2, _ = sm32.solve(sm32.mass_apply(torch.from_numpy(f).cuda()), rtol=1e-8)
-    assert rc2 == asmg.ASMG_OK and abs(it2 - it_ref) <= max(2, 0.1 * it_ref), (it2, it_ref)
-    assert np.linalg.norm(u2.cpu().numpy()[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
+    u2 = u2.cpu().numpy()
+    assert rc2 == asmg.ASMG_OK
+    ok, msg = mixed_iterations_ok(m, b_ref, it2, it_ref, u2[vf], **pr)
+    assert ok, msg
+    assert np.linalg.norm(u2[vf] - u_ref) <= 1e-6 * np.linalg.norm(u_ref)
     sm32.close()
 
 
