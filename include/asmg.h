@@ -143,6 +143,27 @@ int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* itera
               void* stream);
 
 /*
+ * k (1..4) right-hand sides of one handle solved together (not in the paper):
+ * the PCG of amg_solve on k columns at once.  Vectors are kept with their
+ * columns interleaved, so every matrix entry the solve reads (fine operator,
+ * transfer, level operators) serves all k columns (the SpMM form).  Each
+ * column has its own scalars and its own stopping test; a column that has
+ * stopped takes no further steps.  Per column the arithmetic is that of
+ * amg_solve, except on small auxiliary levels whose fused kernels hold fewer
+ * rows here.
+ *   b            float64 [k * nv]: right-hand side c at b + c * nv.
+ *   u            float64 [k * nv]: initial guesses in, solutions out.
+ *   iterations   host int [k]; status host int [k] or NULL (ASMG_OK,
+ *                ASMG_NOT_CONVERGED, ASMG_ERR_BREAKDOWN per column).
+ *   res_history  host float64 [k * (max_iter + 1)] or NULL: column c's
+ *                residual norms at res_history + c * (max_iter + 1).
+ * Returns the worst column status.  ASMG_ERR_UNSUPPORTED for handles with
+ * Neumann vertices or with the Jacobi, additive or iteration variants.
+ */
+int amg_solve_multi(asmg_handle h, int k, const double* b, double* u, double rtol, int* iterations, int* status,
+                    double* res_history, void* stream);
+
+/*
  * b = M f_h: the consistent P1 mass matrix applied to nodal values f [nv]
  * (float64), result b [nv] with 0 at Dirichlet vertices.  This is the load
  * vector <f, phi_i> of eq. bilinearform for the interpolant f_h.  Each entry
@@ -293,12 +314,16 @@ int amg_profile_levels(asmg_handle h, const double* b, double rtol, double* out,
  * several right-hand sides, solved by one CUDA graph launch.
  *   amg_batch_create  nprob handles (distinct meshes, any precisions), nrhs
  *                     right-hand sides per handle, the relative tolerance.
- *                     The batch adds nrhs work slots to every handle and
- *                     captures one graph in which every (problem, rhs) solve
- *                     -- gather, PCG start, WHILE loop, scatter -- is an
- *                     independent branch, so the device runs the solves of
- *                     all problems concurrently.  Handles must outlive the
- *                     batch and may not be destroyed before it.
+ *                     With nrhs > 1 (and handles amg_solve_multi accepts)
+ *                     the right-hand sides of a problem are solved in groups
+ *                     of 4 columns as by amg_solve_multi, so each matrix read
+ *                     serves 4 right-hand sides; the batch captures one graph
+ *                     in which every (problem, group) solve -- gather, PCG
+ *                     start, WHILE loop, scatter -- is an independent branch,
+ *                     so the device runs the solves of all problems
+ *                     concurrently.  Otherwise every (problem, rhs) solve is
+ *                     a branch of its own.  Handles must outlive the batch
+ *                     and may not be destroyed before it.
  *   amg_batch_solve   bs[p * nrhs + j]: float64 [nv_p] right-hand side j of
  *                     problem p; us[...]: initial guess in, solution out (host
  *                     or device arrays).  iterations, status: host int

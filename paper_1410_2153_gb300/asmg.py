@@ -77,6 +77,7 @@ def lib():
         L.amg_export.argtypes = [vp, i32, i32, vp, ctypes.POINTER(i64)]
         L.amg_profile.argtypes = [vp, vp, ctypes.c_double, vp, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_residual_norm_noalloc.argtypes = [vp, vp, vp, vp, vp]
+        L.amg_solve_multi.argtypes = [vp, i32, vp, vp, ctypes.c_double, vp, vp, vp, vp]
         L.amg_profile_levels.argtypes = [vp, vp, ctypes.c_double, vp, vp, i32, ctypes.POINTER(ctypes.c_int), vp]
         L.amg_batch_create.argtypes = [i32, vp, i32, ctypes.c_double, vp, ctypes.POINTER(vp)]
         L.amg_batch_solve.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -89,7 +90,7 @@ def lib():
         for name in ("asmg_default_params", "amg_setup", "amg_solve", "amg_mass_apply", "amg_precond_apply",
                      "amg_spmv", "amg_element_grad", "amg_update_coefficients", "amg_element_grad_log",
                      "amg_set_log_coefficients", "amg_info", "amg_export",
-                     "amg_profile", "amg_profile_levels", "amg_residual_norm_noalloc", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
+                     "amg_profile", "amg_profile_levels", "amg_residual_norm_noalloc", "amg_solve_multi", "amg_batch_create", "amg_batch_solve", "amg_cluster_tree"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -150,6 +151,16 @@ def amg_solve(h, b, u, rtol: float, res_history: Optional[np.ndarray] = None, st
                             _stream(stream, b, u)),
                 allow=(ASMG_OK, ASMG_NOT_CONVERGED))
     return rc, it.value
+
+
+def amg_solve_multi(h, k: int, b, u, rtol: float, res_history: Optional[np.ndarray] = None, stream=None):
+    """k right-hand sides at once: b, u float64 [k * nv] (column c at c * nv);
+    returns (worst status, iterations [k], statuses [k])."""
+    its = np.zeros(k, dtype=np.int32)
+    st = np.zeros(k, dtype=np.int32)
+    rc = _check(lib().amg_solve_multi(h, k, _ptr(b), _ptr(u), float(rtol), _ptr(its), _ptr(st), _ptr(res_history),
+                                      _stream(stream, b, u)), allow=(ASMG_OK, ASMG_NOT_CONVERGED))
+    return rc, its, st
 
 
 def amg_mass_apply(h, f, b, stream=None):

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libasmg.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cu", "assemble.cu", "transfer.cu", "solve.cu", "noalloc.cu", "aux_setup.cpp", "aux_setup3.cpp", "capi.cpp"]
+SOURCES = ["tree.cu", "assemble.cu", "transfer.cu", "solve.cu", "solve_multi.cu", "noalloc.cu", "aux_setup.cpp", "aux_setup3.cpp", "capi.cpp"]
 # the transfer kernel rounds like the host code (separate multiply and add),
 # so the clipped integrals carry no extra rounding differences into parity
 EXTRA = {"transfer.cu": ["-fmad=false"]}

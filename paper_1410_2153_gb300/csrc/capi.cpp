@@ -1141,6 +1141,7 @@ struct asmg_batch_s {
   std::vector<asmg_handle> H;
   int nrhs = 0;
   double rtol = 0;
+  bool multi = false;  // right-hand sides in groups of KRHS columns (SpMM form), one graph branch per group
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ~asmg_batch_s() {
@@ -1148,6 +1149,7 @@ struct asmg_batch_s {
     if (graph) cudaGraphDestroy(graph);
   }
   Slot& slot(int p, int j) { return *H[p]->slots.at(1 + j); }
+  MultiSlot& mslot(int p, int g) { return *H[p]->mslots.at(1 + g); }
 };
 
 extern "C" {
@@ -1162,14 +1164,47 @@ int amg_batch_create(int nprob, const asmg_handle* handles, int nrhs, double rto
   B->H.assign(handles, handles + nprob);
   B->nrhs = nrhs;
   B->rtol = rtol;
+  B->multi = nrhs > 1;
   for (auto h : B->H) {
     if (!h) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null handle in batch");
-    while ((int)h->slots.size() < 1 + nrhs) add_slot(*h, s);
+    if (!multi_supported(*h)) B->multi = false;
+  }
+  const int ngroups = (nrhs + KRHS - 1) / KRHS;
+  for (auto h : B->H) {
+    if (B->multi) {
+      if (h->mslots.empty()) add_multi_slot(*h, s);
+      while ((int)h->mslots.size() < 1 + ngroups) add_multi_slot(*h, s);
+    } else {
+      while ((int)h->slots.size() < 1 + nrhs) add_slot(*h, s);
+    }
   }
   ASMG_CUDA(cudaGraphCreate(&B->graph, 0));
   cudaStream_t cs;
   ASMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  for (int p = 0; p < nprob; ++p)
+  if (B->multi) {
+    // one branch per (problem, group of KRHS right-hand sides): gather, the
+    // multiple solve's graph, scatter
+    for (int p = 0; p < nprob; ++p)
+      for (int g = 0; g < ngroups; ++g) {
+        asmg_s& h = *B->H[p];
+        MultiSlot& S = B->mslot(p, g);
+        ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, B->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        gather_multi(h, S.vb.p, S.b.p, cs);
+        gather_multi(h, S.vu.p, S.x.p, cs);
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* leaf = nullptr;
+        size_t nleaf = 0;
+        ASMG_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &leaf, nullptr, &nleaf));
+        std::vector<cudaGraphNode_t> leaves(leaf, leaf + nleaf);
+        cudaGraph_t gg;
+        ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
+        cudaGraphNode_t wnode = capture_solve_multi(h, S, rtol, B->graph, leaves.data(), leaves.size());
+        ASMG_CUDA(cudaStreamBeginCaptureToGraph(cs, B->graph, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+        scatter_multi(h, S.x.p, S.vu.p, cs);
+        ASMG_CUDA(cudaStreamEndCapture(cs, &gg));
+      }
+  }
+  for (int p = 0; p < (B->multi ? 0 : nprob); ++p)
     for (int j = 0; j < nrhs; ++j) {
       asmg_s& h = *B->H[p];
       Slot& S = B->slot(p, j);
@@ -1202,11 +1237,56 @@ int amg_batch_solve(asmg_batch B, const double* const* bs, double* const* us, in
   if (!B || !bs || !us || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int np = (int)B->H.size(), nr = B->nrhs;
+  for (int k = 0; k < np * nr; ++k)
+    if (!bs[k] || !us[k]) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null array in batch");
+  if (B->multi) {
+    const int ngroups = (nr + KRHS - 1) / KRHS;
+    for (int p = 0; p < np; ++p)
+      for (int g = 0; g < ngroups; ++g) {
+        MultiSlot& S = B->mslot(p, g);
+        const int64_t nv = B->H[p]->mesh.nv;
+        for (int c = 0; c < KRHS; ++c) {
+          const int j = g * KRHS + c;
+          if (j < nr) {
+            copy_in(S.vb.p + c * nv, bs[p * nr + j], nv, s);
+            copy_in(S.vu.p + c * nv, us[p * nr + j], nv, s);
+          } else {
+            // unused column: zero right-hand side, converged from the start
+            ASMG_CUDA(cudaMemsetAsync(S.vb.p + c * nv, 0, 8 * nv, s));
+            ASMG_CUDA(cudaMemsetAsync(S.vu.p + c * nv, 0, 8 * nv, s));
+          }
+        }
+      }
+    ASMG_CUDA(cudaGraphLaunch(B->exec, s));
+    std::vector<MultiScalars> sc((size_t)np * ngroups);
+    for (int p = 0; p < np; ++p)
+      for (int g = 0; g < ngroups; ++g) {
+        MultiSlot& S = B->mslot(p, g);
+        const int64_t nv = B->H[p]->mesh.nv;
+        for (int c = 0; c < KRHS && g * KRHS + c < nr; ++c) copy_out(us[p * nr + g * KRHS + c], S.vu.p + c * nv, nv, s);
+        ASMG_CUDA(cudaMemcpyAsync(&sc[p * ngroups + g], S.scal.p, sizeof(MultiScalars), cudaMemcpyDeviceToHost, s));
+      }
+    ASMG_CUDA(cudaStreamSynchronize(s));
+    int worst = ASMG_OK;
+    for (int p = 0; p < np; ++p)
+      for (int j = 0; j < nr; ++j) {
+        const MultiScalars& m = sc[p * ngroups + j / KRHS];
+        const int c = j % KRHS;
+        iterations[p * nr + j] = m.k[c];
+        const int st = m.status[c] == 0                    ? ASMG_OK
+                       : m.status[c] == ASMG_ERR_BREAKDOWN ? ASMG_ERR_BREAKDOWN
+                       : m.status[c] == ASMG_ERR_TIMEOUT   ? ASMG_ERR_TIMEOUT
+                                                           : ASMG_NOT_CONVERGED;
+        if (status) status[p * nr + j] = st;
+        if (st < 0 || (worst == ASMG_OK && st != ASMG_OK)) worst = st;
+      }
+    if (worst == ASMG_ERR_BREAKDOWN) g_err = "PCG breakdown in a batched solve";
+    return worst;
+  }
   for (int p = 0; p < np; ++p)
     for (int j = 0; j < nr; ++j) {
       Slot& S = B->slot(p, j);
       const int64_t nv = B->H[p]->mesh.nv;
-      if (!bs[p * nr + j] || !us[p * nr + j]) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null array in batch");
       copy_in(S.vb.p, bs[p * nr + j], nv, s);
       copy_in(S.vu.p, us[p * nr + j], nv, s);
     }
@@ -1307,6 +1387,56 @@ int amg_solve(asmg_handle h, const double* b, double* u, double rtol, int* itera
     return ASMG_ERR_TIMEOUT;
   }
   return sc.status == 0 ? ASMG_OK : ASMG_NOT_CONVERGED;
+  API_END
+}
+
+int amg_solve_multi(asmg_handle h, int k, const double* b, double* u, double rtol, int* iterations, int* status,
+                    double* res_history, void* stream) {
+  API_BEGIN
+  if (!h || !b || !u || !iterations) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "null argument");
+  if (k < 1 || k > KRHS) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "k = %d right-hand sides (1..%d)", k, KRHS);
+  if (!(rtol >= 0) || !std::isfinite(rtol)) ASMG_FAIL(ASMG_ERR_INVALID_ARG, "rtol must be finite and >= 0");
+  if (!multi_supported(*h))
+    ASMG_FAIL(ASMG_ERR_UNSUPPORTED, "multiple right-hand sides need the multiplicative Gauss-Seidel PCG without "
+                                    "Neumann vertices");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->mslots.empty()) add_multi_slot(*h, s);
+  MultiSlot& S = *h->mslots[0];
+  const int64_t nv = h->mesh.nv;
+  for (int c = 0; c < KRHS; ++c) {
+    if (c < k) {
+      copy_in(S.vb.p + c * nv, b + c * nv, nv, s);
+      copy_in(S.vu.p + c * nv, u + c * nv, nv, s);
+    } else {
+      ASMG_CUDA(cudaMemsetAsync(S.vb.p + c * nv, 0, 8 * nv, s));
+      ASMG_CUDA(cudaMemsetAsync(S.vu.p + c * nv, 0, 8 * nv, s));
+    }
+  }
+  gather_multi(*h, S.vb.p, S.b.p, s);
+  gather_multi(*h, S.vu.p, S.x.p, s);
+  run_solve_multi(*h, S, rtol, s);
+  scatter_multi(*h, S.x.p, S.vu.p, s);
+  for (int c = 0; c < k; ++c) copy_out(u + c * nv, S.vu.p + c * nv, nv, s);
+  MultiScalars sc;
+  ASMG_CUDA(cudaMemcpyAsync(&sc, S.scal.p, sizeof sc, cudaMemcpyDeviceToHost, s));
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  const int64_t hl = h->prm.max_iter + 1;
+  int worst = ASMG_OK;
+  for (int c = 0; c < k; ++c) {
+    iterations[c] = sc.k[c];
+    const int st = sc.status[c] == 0                    ? ASMG_OK
+                   : sc.status[c] == ASMG_ERR_BREAKDOWN ? ASMG_ERR_BREAKDOWN
+                   : sc.status[c] == ASMG_ERR_TIMEOUT   ? ASMG_ERR_TIMEOUT
+                                                        : ASMG_NOT_CONVERGED;
+    if (status) status[c] = st;
+    if (st < 0 || (worst == ASMG_OK && st != ASMG_OK)) worst = st;
+    if (res_history)
+      ASMG_CUDA(cudaMemcpyAsync(res_history + c * hl, S.hist.p + c * hl, 8 * (size_t)(sc.k[c] + 1),
+                                cudaMemcpyDeviceToHost, s));
+  }
+  ASMG_CUDA(cudaStreamSynchronize(s));
+  if (worst == ASMG_ERR_BREAKDOWN) g_err = "PCG breakdown in a column of a multiple solve";
+  return worst;
   API_END
 }
 

@@ -63,6 +63,43 @@ struct Slot {
   }
 };
 
+// Several right-hand sides of one handle in one solve (the SpMM form): every
+// vector holds KRHS columns interleaved, element (i, j) at i * KRHS + j, so
+// each matrix entry read serves all columns.  Columns converge on their own:
+// a column that has stopped keeps alpha = 0 and takes no further steps.
+constexpr int KRHS = 4;
+
+struct MultiScalars {
+  double rz[KRHS], alpha[KRHS], beta[KRHS], pq[KRHS], rr[KRHS], bnorm[KRHS], tol[KRHS];
+  int k[KRHS], status[KRHS], active[KRHS];
+  int maxit, cond, timeout;
+};
+
+template <class T>
+struct MultiPrec {
+  DBuf<T> uf, rho, F, U;                  // [rows][KRHS]
+  std::vector<DBuf<T>> fs, us;            // per level [nsm][KRHS]
+  DBuf<SmallDesc<T>> deep_desc, bot_desc;
+  int n_deep = 0, n_bottom = 0;           // fused small-level runs for KRHS columns
+};
+
+struct MultiSlot {
+  DBuf<double> b, x, r, p, q;             // [npad][KRHS]
+  DBuf<double> vb, vu;                    // [KRHS][nv] vertex order (staging)
+  DBuf<double> partial, hist;             // hist [KRHS][max_iter + 1]
+  DBuf<unsigned int> ticket;
+  DBuf<MultiScalars> scal;
+  MultiPrec<double> m64;
+  MultiPrec<float> m32;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double graph_rtol = -1;
+  ~MultiSlot() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
 }  // namespace asmg
 
 struct asmg_s {
@@ -97,6 +134,8 @@ struct asmg_s {
 
   // per-solve state (slot 0 serves amg_solve)
   std::vector<std::unique_ptr<asmg::Slot>> slots;
+  // multiple-right-hand-side solves (slot 0 serves amg_solve_multi)
+  std::vector<std::unique_ptr<asmg::MultiSlot>> mslots;
   int64_t bytes_iter = 0;
   asmg::Stats stats;
   int gpu_launches_per_iter = 0;
@@ -120,6 +159,14 @@ void precond_apply(asmg_s& h, const double* r_perm, cudaStream_t s);  // result 
 void spmv64(asmg_s& h, const double* x_perm, double* y_perm, cudaStream_t s);
 void gather_rows(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s);
 void scatter_rows(asmg_s& h, const void* src, bool src_float, double* vdst, cudaStream_t s);
+// solve_multi.cu
+bool multi_supported(const asmg_s& h);
+MultiSlot& add_multi_slot(asmg_s& h, cudaStream_t s);
+void gather_multi(asmg_s& h, const double* vsrc, double* dst, cudaStream_t s);
+void scatter_multi(asmg_s& h, const double* src, double* vdst, cudaStream_t s);
+void run_solve_multi(asmg_s& h, MultiSlot& S, double rtol, cudaStream_t s);
+cudaGraphNode_t capture_solve_multi(asmg_s& h, MultiSlot& S, double rtol, cudaGraph_t g, const cudaGraphNode_t* deps,
+                                    size_t ndeps);
 // assemble.cu
 HostCSR assemble_mesh(int dim, int64_t ne, const double* dX, const int32_t* dE, const int32_t* dFree,
                       const double* dCoef, int64_t nfree, cudaStream_t s);

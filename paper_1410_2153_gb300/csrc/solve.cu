@@ -26,119 +26,13 @@
 #include <vector>
 
 #include "handle.h"
+#include "kernels.h"
 
 namespace asmg {
 
 namespace {
 
-constexpr int TPB = 256;
-constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
-
-int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
-
-// Block size of a row-parallel launch: 256 threads when that fills every SM
-// twice, else 64 so that small colour classes still spread over all SMs.
-constexpr int NSM = 152;
-inline int rows_tpb(int64_t rows) { return rows >= (int64_t)NSM * 2 * 256 ? 256 : 64; }
-
-// Kernel launch with dynamic shared memory, optionally with programmatic dependent launch.
-template <typename... KArgs, typename... Args>
-void launch_smem(bool pdl, void (*kern)(KArgs...), int64_t grid, int block, size_t smem, cudaStream_t s,
-                 Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  ASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
-}
-
-// Kernel launch, optionally with programmatic dependent launch (the kernel may
-// start while its predecessor on the stream finishes; see pdl_wait below).
-template <typename... KArgs, typename... Args>
-void launch(bool pdl, void (*kern)(KArgs...), int64_t grid, int block, cudaStream_t s, Args... args) {
-  if (!pdl) {
-    kern<<<(unsigned)grid, (unsigned)block, 0, s>>>(static_cast<KArgs>(args)...);
-    return;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  ASMG_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
-}
-
-template <class T, class X>
-__device__ __forceinline__ T sell_dot(int64_t row, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                      const T* __restrict__ val, const X* x) {
-  const int64_t sl = row >> 5, lane = row & 31;
-  const int64_t b = __ldg(off + sl), w = (__ldg(off + sl + 1) - b) >> 5;
-  T s = 0;
-  for (int64_t k = 0; k < w; ++k) {
-    const int64_t e = b + (k << 5) + lane;
-    s += __ldg(val + e) * (T)x[__ldg(col + e)];
-  }
-  return s;
-}
-
-// Programmatic dependent launch: every solve kernel first loads what was
-// written at setup (matrix rows, index lists), then waits for the preceding
-// kernel (griddepcontrol.wait), and lets the next kernel launch once its own
-// work is done (griddepcontrol.launch_dependents).  Launched without the
-// attribute, both instructions are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// A SELL-32 row held in registers (up to MAXW entries; longer rows read the rest later).
-constexpr int MAXW = 10;
-template <class T>
-struct Row {
-  int64_t b = 0, lane = 0;
-  int w = 0;
-  int32_t c[MAXW];
-  T v[MAXW];
-};
-
-template <class T>
-__device__ __forceinline__ void row_load(Row<T>& R, int64_t row, const int64_t* __restrict__ off,
-                                         const int32_t* __restrict__ col, const T* __restrict__ val) {
-  const int64_t sl = row >> 5;
-  R.lane = row & 31;
-  R.b = __ldg(off + sl);
-  R.w = (int)((__ldg(off + sl + 1) - R.b) >> 5);
-#pragma unroll
-  for (int k = 0; k < MAXW; ++k)
-    if (k < R.w) {
-      const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
-      R.c[k] = __ldcs(col + e);
-      R.v[k] = __ldcs(val + e);
-    }
-}
-
-template <class T, class X>
-__device__ __forceinline__ T row_dot(const Row<T>& R, const int32_t* __restrict__ col, const T* __restrict__ val,
-                                     const X* x) {
-  T s = 0;
-#pragma unroll
-  for (int k = 0; k < MAXW; ++k)
-    if (k < R.w) s += R.v[k] * (T)x[R.c[k]];
-  for (int k = MAXW; k < R.w; ++k) {
-    const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
-    s += __ldg(val + e) * (T)x[__ldg(col + e)];
-  }
-  return s;
-}
+using namespace kern;
 
 // ------------------------------------------------------------- fine grid
 // one colour of a Gauss-Seidel sweep: u_i += (rhs_i - (A u)_i) / a_ii
@@ -904,55 +798,6 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
 }
 
 // ------------------------------------------------------------------ PCG
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-  if (w == 0)
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;  // valid in thread 0
-}
-
-// Deterministic grid reduction of NV values: partials per block, the last
-// block to finish sums them in block order.  Returns true in that block.
-template <int NV>
-__device__ bool grid_reduce(double (&v)[NV], double* partial, unsigned int* ticket) {
-  __shared__ double sh[32];
-  __shared__ bool last;
-  for (int j = 0; j < NV; ++j) {
-    double t = block_sum(v[j], sh);
-    if (threadIdx.x == 0) partial[j * gridDim.x + blockIdx.x] = t;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  for (int j = 0; j < NV; ++j) {
-    // the partials of this thread (blocks t, t + blockDim, ...) summed in
-    // ascending order, eight loads in flight
-    const double* pj = partial + (int64_t)j * gridDim.x;
-    double s = 0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += 8 * blockDim.x) {
-      double x[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const unsigned bb = b + u * blockDim.x;
-        x[u] = bb < gridDim.x ? __ldcg(pj + bb) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s += x[u];
-    }
-    v[j] = block_sum(s, sh);
-  }
-  if (threadIdx.x == 0) *ticket = 0;
-  return true;
-}
-
 __device__ __forceinline__ void set_cond(PcgScalars* sc, int cond, cudaGraphConditionalHandle hnd, int use_hnd) {
   sc->cond = cond;
   if (use_hnd) cudaGraphSetConditional(hnd, cond ? 1u : 0u);

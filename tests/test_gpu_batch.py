@@ -1,7 +1,10 @@
 """Batched solves: independent meshes of uneven size, several right-hand
-sides each, one graph launch.  Every batched solution must equal the single
-solve of the same handle (same kernels, deterministic reductions) and match
-the oracle (1e-10 relative in FP64, 1e-6 in mixed precision)."""
+sides each, one graph launch.  A problem's right-hand sides are solved in
+groups of 4 columns (amg_solve_multi's SpMM form, one graph branch per
+group): every batched solution must equal the multiple solve of the same
+handle bit for bit (same kernels, deterministic reductions), agree with the
+single-column solve to 1e-9, and match the oracle (1e-10 relative in FP64,
+1e-6 in mixed precision)."""
 import numpy as np
 import pytest
 
@@ -44,13 +47,21 @@ def test_batched_solves_match_single_solves_and_oracle(gen):
         assert rc == asmg.ASMG_OK and (st == 0).all()
         k = 0
         for p, (m, s) in enumerate(zip(meshes, solvers)):
+            bm = np.concatenate([bs[p * nrhs + j].cpu().numpy() if hasattr(bs[p * nrhs + j], "cpu")
+                                 else bs[p * nrhs + j] for j in range(nrhs)])
+            um = np.zeros(nrhs * m.nv)
+            rcm, itm, _ = asmg.amg_solve_multi(s.h, nrhs, bm, um, 1e-8)
+            assert rcm == asmg.ASMG_OK
             for j in range(nrhs):
                 o, b = refs[k]
                 u = us[k].cpu().numpy() if hasattr(us[k], "cpu") else us[k]
                 bv = bs[k].cpu().numpy() if hasattr(bs[k], "cpu") else bs[k]
+                assert itm[j] == its[k]
+                assert np.array_equal(um[j * m.nv:(j + 1) * m.nv], u)
                 single, rc1, it1, _ = s.solve(bv, rtol=1e-8)
-                assert rc1 == asmg.ASMG_OK and it1 == its[k]
-                assert np.array_equal(single, u)
+                assert rc1 == asmg.ASMG_OK and abs(it1 - its[k]) <= 2
+                if it1 == its[k]:
+                    assert np.linalg.norm(single - u) <= 1e-9 * np.linalg.norm(single)
                 u_ref, st_o, it_o, _ = o.solve(b, rtol=1e-8)
                 tol = 1e-10 if precisions[p] == 0 else 1e-6
                 vf = o.vertex_of_free()
