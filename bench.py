@@ -507,7 +507,10 @@ def main():
                    "nfree": n, "elements": mesh.ne, "dim": mesh.dim, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
                    "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
-                   "tiled_levels": [l for l in range(s.info("coarse") + 1, s.info("J") + 1) if s.info("ntiles", l) > 0],
+                   "tiled_levels": {"down": [l for l in range(s.info("coarse") + 1, s.info("J") + 1)
+                                             if s.info("ntiles", l) > 0],
+                                    "up": [l for l in range(s.info("coarse") + 1, s.info("J") + 1)
+                                           if s.info("ntiles_up", l) > 0]},
                    "setup_breakdown_s": {k: s.info(f"t_{k}_us") / 1e6 for k in
                                          ("tree", "aux", "sz", "fine", "levels", "lv_assemble", "lv_colour", "lv_pack",
                                           "lv_export", "coarse", "transfer", "slots")},

@@ -244,9 +244,10 @@ enum asmg_info_what {
   ASMG_INFO_NROWS_E = 11,     /* residual rows of level `level` */
   ASMG_INFO_BYTES_ITER = 12,  /* algorithmic bytes of one PCG iteration (current precision) */
   ASMG_INFO_NNZ_LEVEL = 13,   /* stored non-zeros of level `level` (smoothing + residual rows) */
-  ASMG_INFO_NTILES = 14,      /* tiles of the temporally blocked sweeps of level `level` (0: one launch
-                                 per colour class and sweep) */
-  ASMG_INFO_HALO_ROWS = 15    /* halo rows of those tiles (pre-sweeps), summed over the tiles */
+  ASMG_INFO_NTILES = 14,      /* tiles of the temporally blocked pre-sweeps of level `level` (0: one
+                                 launch per colour class and sweep) */
+  ASMG_INFO_HALO_ROWS = 15,   /* halo rows of those tiles (pre-sweeps), summed over the tiles */
+  ASMG_INFO_NTILES_UP = 16    /* tiles of the temporally blocked post-sweeps of level `level` (0: per class) */
 };
 int amg_info(asmg_handle h, int what, int level, int64_t* value);
 

@@ -30,7 +30,7 @@ ASMG_FP64 = 0
 ASMG_MIXED = 1
 
 INFO = dict(nfree=0, J=1, coarse=2, naux=3, nsmooth=4, ncolours=5, ntree_levels=6, nseg=7, nsplit=8, nnz_A=9,
-            nnz_P=10, nrows_E=11, bytes_iter=12, nnz_level=13, ntiles=14, halo_rows=15, launches_per_iter=100, t_setup_us=101,
+            nnz_P=10, nrows_E=11, bytes_iter=12, nnz_level=13, ntiles=14, halo_rows=15, ntiles_up=16, launches_per_iter=100, t_setup_us=101,
             t_tree_us=102, t_aux_us=103, t_fine_us=104, t_levels_us=105,
             t_lv_assemble_us=108, t_lv_colour_us=109, t_lv_pack_us=110, t_lv_export_us=111, t_coarse_us=112,
             t_transfer_us=113, t_slots_us=114, t_sz_us=115)

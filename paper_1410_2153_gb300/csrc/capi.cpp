@@ -624,7 +624,7 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
       D.sm_par1.upload(p1, s);
       D.tdown = std::move(td);
       D.tup = std::move(tu);
-      D.tiled = true;
+      D.tiled = D.tiled_down = D.tiled_up = true;
       D.tile_rows = trows;
       break;
     }
@@ -1649,8 +1649,14 @@ int amg_info(asmg_handle h, int what, int level, int64_t* value) {
     }
     case ASMG_INFO_NTILES: {
       int k = lev_index(level);
-      *value = h->prm.precision == ASMG_MIXED ? (h->p32.lev[k].tiled ? h->p32.lev[k].tdown.ntiles : 0)
-                                              : (h->p64.lev[k].tiled ? h->p64.lev[k].tdown.ntiles : 0);
+      *value = h->prm.precision == ASMG_MIXED ? (h->p32.lev[k].tiled_down ? h->p32.lev[k].tdown.ntiles : 0)
+                                              : (h->p64.lev[k].tiled_down ? h->p64.lev[k].tdown.ntiles : 0);
+      break;
+    }
+    case ASMG_INFO_NTILES_UP: {
+      int k = lev_index(level);
+      *value = h->prm.precision == ASMG_MIXED ? (h->p32.lev[k].tiled_up ? h->p32.lev[k].tup.ntiles : 0)
+                                              : (h->p64.lev[k].tiled_up ? h->p64.lev[k].tup.ntiles : 0);
       break;
     }
     case ASMG_INFO_HALO_ROWS: {

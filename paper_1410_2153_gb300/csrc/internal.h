@@ -368,7 +368,8 @@ struct AuxLevelDev {
   SmallLevelDev<T> small;        // shared-memory form, when the level is small
   // temporal blocking (tiled = 1): pre-sweeps in one launch (k_tile_down), and
   // after k_up_init, post-sweeps in one launch (k_tile_up)
-  bool tiled = false;
+  bool tiled = false;                // tiles built for both directions
+  bool tiled_down = false, tiled_up = false;  // the directions that run on them (the autotuner's choice)
   int tile_rows = 0;                 // own rows per tile
   TileSweeps<T> tdown, tup;
   DBuf<int32_t> sm_par0, sm_par1;    // per SM row: parents of a new node (-1 Dirichlet), -3 not new

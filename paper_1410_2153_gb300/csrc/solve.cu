@@ -1080,7 +1080,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SMd = view(L.SMd);
     g_prof_level = li;
-    if (L.tiled) {
+    if (L.tiled_down) {
       // all pre-sweeps of the level in one launch (compulsory bytes: the
       // tiles' blocks once, F gathered and saved, us written)
       const TileSweeps<T>& Tl = L.tdown;
@@ -1094,7 +1094,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     }
     // pre-sweeps on us (SM order); the first also saves F on N~_l for the
     // post-sweeps (nu_pre >= 1)
-    for (int sweep = 0; sweep < (L.tiled ? 0 : npre); ++sweep) {
+    for (int sweep = 0; sweep < (L.tiled_down ? 0 : npre); ++sweep) {
       for (int c = 0; c < L.ncolours; ++c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
@@ -1135,7 +1135,7 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
     g_prof_level = -2 - li;
-    if (L.tiled) {
+    if (L.tiled_up) {
       LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (12 + 2 * sz) + L.nnew * 2 * sz + (L.nsm_real - L.nnew) * sz,
              launch(h.prm.use_pdl, k_up_init<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p,
                     L.sm_par0.p, L.sm_par1.p, (const T*)SP.U.p, SP.us[li].p));
@@ -1556,14 +1556,15 @@ void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
   SP.bot_desc.upload(bot, s);
 }
 
-// Schedule of the auxiliary levels (the autotuner, tile_rows = 0): each level
-// that has tiles runs either its temporally blocked sweeps or its launches
-// per colour class and sweep, with the same results.  The choice is made on
-// the device: one preconditioner application is captured as a CUDA graph
-// and timed (median of 3 runs of 5 launches) with every level tiled, then
-// each level in turn is switched to class launches and kept so when that is
-// faster by more than 0.5% (and 2 us).  Tiles of levels left untiled are
-// freed.
+// Schedule of the auxiliary levels (the autotuner, tile_rows = 0): each
+// direction of a level that has tiles runs either its temporally blocked
+// sweeps or its launches per colour class and sweep, with the same results.
+// The choice is made on the device: one preconditioner application is
+// captured as a CUDA graph and timed (median of 3 runs of 5 launches) with
+// every level tiled both ways, then for each level in turn the post-sweeps
+// and then the pre-sweeps are switched to class launches, each switch kept
+// when it is faster by more than 0.5% (and 2 us).  Tiles of a direction left
+// untiled are freed.
 template <class T>
 void autotune_levels(asmg_s& h, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
@@ -1601,15 +1602,16 @@ void autotune_levels(asmg_s& h, cudaStream_t s) {
   };
   try {
     float cur = time_once();
-    for (int li : cand) {
-      P.lev[li].tiled = false;
-      const float t = time_once();
-      if (t < cur * 0.995f && cur - t > 0.002f) {
-        cur = t;
-      } else {
-        P.lev[li].tiled = true;
+    for (int li : cand)
+      for (bool* flag : {&P.lev[li].tiled_up, &P.lev[li].tiled_down}) {
+        *flag = false;
+        const float t = time_once();
+        if (t < cur * 0.995f && cur - t > 0.002f) {
+          cur = t;
+        } else {
+          *flag = true;
+        }
       }
-    }
   } catch (...) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1619,11 +1621,12 @@ void autotune_levels(asmg_s& h, cudaStream_t s) {
   ASMG_CUDA(cudaEventDestroy(e0));
   ASMG_CUDA(cudaEventDestroy(e1));
   ASMG_CUDA(cudaStreamDestroy(cs));
-  for (int li : cand)
-    if (!P.lev[li].tiled) {
-      P.lev[li].tdown = TileSweeps<T>();
-      P.lev[li].tup = TileSweeps<T>();
-    }
+  for (int li : cand) {
+    AuxLevelDev<T>& L = P.lev[li];
+    if (!L.tiled_down) L.tdown = TileSweeps<T>();
+    if (!L.tiled_up) L.tup = TileSweeps<T>();
+    L.tiled = L.tiled_down || L.tiled_up;
+  }
 }
 
 Slot& add_slot(asmg_s& h, cudaStream_t s) {
@@ -1661,7 +1664,7 @@ void drop_unused_tiles(Prec<T>& P) {
   const int nlev = (int)P.lev.size();
   for (int li = 0; li < nlev; ++li)
     if (li < P.n_bottom || li > nlev - 1 - P.n_deep) {
-      P.lev[li].tiled = false;
+      P.lev[li].tiled = P.lev[li].tiled_down = P.lev[li].tiled_up = false;
       P.lev[li].tdown = TileSweeps<T>();
       P.lev[li].tup = TileSweeps<T>();
     }
