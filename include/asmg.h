@@ -86,6 +86,10 @@ typedef struct {
   int32_t nb_layers;       /* mixed boundaries: layers j of the near-boundary sets J_{l,j} of Algorithm 3
                               (Sec. 3.5), whose exact solve follows each coarse-grid correction;
                               -1 = no near-boundary correction, 0..16; 2 */
+  int32_t colouring;       /* colour classes of the Gauss-Seidel sweeps: 0 = Jones-Plassmann with
+                              splitmix64 priorities on every grid; 2 = on an auxiliary level whose
+                              couplings the lattice parity (X + Y [+ Z]) / h_l mod 2 separates (uniform
+                              levels), that parity (two classes), else Jones-Plassmann; 2 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */

@@ -19,8 +19,10 @@ _SRC = os.path.join(_HERE, "asmg_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
+# colouring = 2 (lattice parity on the auxiliary levels it 2-colours, Jones-
+# Plassmann elsewhere) is the library's default too
 PARAM_DEFAULTS = dict(n_min=3, nu_pre=2, nu_post=2, coarse_max=512, smoothing=0, max_iter=500,
-                      colouring=0, stage=2, smoother=0, additive=0, fine_sweeps=1, iteration=0, nb_layers=2)
+                      colouring=2, stage=2, smoother=0, additive=0, fine_sweeps=1, iteration=0, nb_layers=2)
 PARAM_ORDER = ("n_min", "nu_pre", "nu_post", "coarse_max", "smoothing", "max_iter", "colouring", "stage",
                "smoother", "additive", "fine_sweeps", "iteration", "nb_layers")
 

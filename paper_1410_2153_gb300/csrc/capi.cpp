@@ -1,5 +1,6 @@
 // C ABI entry points (include/asmg.h) and the setup pipeline.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -751,6 +752,53 @@ void build_prec(asmg_s& h, Prec<T>& P, const HostCSR& Aperm, const std::vector<d
   sell_build<T>(P.PT, Ptc, 0, s);
 }
 
+// Colouring option 2 on an auxiliary level: the lattice parity of each node
+// of the smoothing set, (X + Y [+ Z]) / h_l mod 2 with h_l the lattice
+// spacing of level l (2^(bits - l) on the lattice of the node keys), used when
+// no two coupled nodes of the set share it (couplings as for the Jones-
+// Plassmann colouring: |a_vw| > 1e-12 sqrt(a_vv a_ww), w != v).  Uniform
+// levels are bipartite this way (couplings across hypotenuses vanish), so
+// they take two colour classes.  Returns false, leaving `colour` as it is,
+// when some coupled pair shares a parity.
+bool parity_colour(const asmg_s& h, int l, const HostCSR& A, const std::vector<int32_t>& smooth,
+                   const std::vector<uint8_t>& inset, std::vector<int32_t>& colour) {
+  const int dim = h.mesh.dim;
+  const int bits = dim == 2 ? h.tree.D : h.aux.LB;
+  const uint64_t step = 1ULL << (bits - l);
+  std::vector<int8_t> par(A.nr, -1);
+  for (int32_t v : smooth) {
+    const uint64_t k = h.aux.aux_key[v];
+    uint64_t q[3] = {0, 0, 0};
+    for (int j = 0; j < 64 / dim; ++j)
+      for (int c = 0; c < dim; ++c)
+        if ((k >> (dim * j + c)) & 1ULL) q[c] |= 1ULL << j;
+    par[v] = (int8_t)(((q[0] + q[1] + q[2]) / step) & 1);
+  }
+  std::vector<double> diag(A.nr, 0.0);
+  host_for(A.nr, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+        if (A.col[p] == i) diag[i] = A.val[p];
+  });
+  std::atomic<bool> ok(true);
+  host_for((int64_t)smooth.size(), [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1 && ok.load(std::memory_order_relaxed); ++k) {
+      const int32_t v = smooth[k];
+      for (int64_t p = A.ptr[v]; p < A.ptr[v + 1]; ++p) {
+        const int32_t w = A.col[p];
+        if (w == v || !inset[w] || par[w] != par[v]) continue;
+        if (std::fabs(A.val[p]) > 1e-12 * std::sqrt(diag[v] * diag[w])) {
+          ok.store(false, std::memory_order_relaxed);
+          break;
+        }
+      }
+    }
+  });
+  if (!ok.load()) return false;
+  for (int32_t v : smooth) colour[v] = par[v];
+  return true;
+}
+
 void build_all(asmg_s& h, cudaStream_t s) {
   double t0 = now();
   MeshHost& m = h.mesh;
@@ -848,6 +896,7 @@ void build_all(asmg_s& h, cudaStream_t s) {
     double tb = now();
     h.stats.t_lv_assemble += tb - ta;
     std::vector<int32_t> colour = jp_colour_gpu(Arows, inset, h.aux.aux_key, s);
+    if (h.prm.colouring == 2) parity_colour(h, L.level, Arows, L.smooth, inset, colour);
     double tc = now();
     h.stats.t_lv_colour += tc - tb;
     // export copies
@@ -1022,6 +1071,7 @@ int asmg_default_params(asmg_params* p) {
   p->tile_rows = 0;
   p->inject_timeout = 0;
   p->nb_layers = 2;
+  p->colouring = 2;
   return ASMG_OK;
 }
 
@@ -1044,7 +1094,8 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       (prm.smoother != 0 && prm.smoother != 1) || (prm.additive != 0 && prm.additive != 1) || prm.fine_sweeps < 1 ||
       prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1) ||
       (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)) ||
-      (prm.inject_timeout != 0 && prm.inject_timeout != 1) || prm.nb_layers < -1 || prm.nb_layers > 16)
+      (prm.inject_timeout != 0 && prm.inject_timeout != 1) || prm.nb_layers < -1 || prm.nb_layers > 16 ||
+      (prm.colouring != 0 && prm.colouring != 2))
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();
