@@ -14,6 +14,7 @@ namespace kern {
 
 constexpr int TPB = 256;
 constexpr int RED_BLOCKS = 152 * 4;  // persistent reduction grid: 4 CTAs per SM
+constexpr int VEC_BLOCKS = 152 * 8;  // grid of the vector-only PCG kernels: 8 CTAs (full occupancy) per SM
 
 inline int nblk(int64_t n, int t = TPB) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 1 << 24)); }
 

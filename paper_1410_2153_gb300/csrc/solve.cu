@@ -839,6 +839,7 @@ __global__ void k_dots(int64_t n, const T* __restrict__ z, const double* __restr
                        double* partial, unsigned int* ticket, PcgScalars* sc) {
   pdl_wait();
   double v[2] = {0, 0};
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double zi = (double)z[i];
     v[0] += zi * r[i];
@@ -860,6 +861,7 @@ template <class T>
 __global__ void k_pupd(int64_t n, const T* __restrict__ z, double* __restrict__ p, const PcgScalars* __restrict__ sc) {
   pdl_wait();
   const double beta = sc->beta;
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (double)z[i] + beta * p[i];
   pdl_trigger();
@@ -893,6 +895,7 @@ __global__ void k_axpy_norm(int64_t n, const double* __restrict__ p, const doubl
   pdl_wait();
   const double a = sc->alpha;
   double v[1] = {0};
+#pragma unroll 4
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += a * p[i];
     double ri = r[i] - a * q[i];
@@ -1261,15 +1264,15 @@ template <class T>
 int enqueue_body(asmg_s& h, Slot& S, cudaStream_t s, cudaGraphConditionalHandle hnd, int use_hnd) {
   int launches = enqueue_precond<T>(h, S, S.r.p, s);
   const T* z = slotprec<T>(S).uf.p;
-  const int G = RED_BLOCKS;
+  const int G = RED_BLOCKS, GV = VEC_BLOCKS;
   const int64_t n = h.n, sz = sizeof(T);
   LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16),
-         launch(h.prm.use_pdl, k_dots<T>, G, TPB, s, h.npad, z, S.r.p, S.q.p, S.partial.p, S.ticket.p, S.scal.p));
-  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_pupd<T>, G, TPB, s, h.npad, z, S.p.p, S.scal.p));
+         launch(h.prm.use_pdl, k_dots<T>, GV, TPB, s, h.npad, z, S.r.p, S.q.p, S.partial.p, S.ticket.p, S.scal.p));
+  LAUNCH(ASMG_PROF_CG_VECTOR, n * (sz + 16), launch(h.prm.use_pdl, k_pupd<T>, GV, TPB, s, h.npad, z, S.p.p, S.scal.p));
   LAUNCH(ASMG_PROF_CG_SPMV, h.A64.nnz_real * 12 + n * 16,
          launch(h.prm.use_pdl, k_spmv_dot, G, TPB, s, h.npad, view(h.A64), S.p.p, S.q.p, S.partial.p, S.ticket.p, S.scal.p));
   LAUNCH(ASMG_PROF_CG_VECTOR, n * 48,
-         launch(h.prm.use_pdl, k_axpy_norm, G, TPB, s, h.npad, S.p.p, S.q.p, S.x.p, S.r.p, S.partial.p, S.ticket.p, S.scal.p,
+         launch(h.prm.use_pdl, k_axpy_norm, GV, TPB, s, h.npad, S.p.p, S.q.p, S.x.p, S.r.p, S.partial.p, S.ticket.p, S.scal.p,
                                        S.hist.p, hnd, use_hnd));
   ASMG_CUDA(cudaGetLastError());
   return launches + 4;
@@ -1644,7 +1647,7 @@ Slot& add_slot(asmg_s& h, cudaStream_t s) {
   S.q.zero(s);
   S.vb.alloc(h.mesh.nv);
   S.vu.alloc(h.mesh.nv);
-  S.partial.alloc(4 * RED_BLOCKS);
+  S.partial.alloc(std::max(4 * RED_BLOCKS, 2 * VEC_BLOCKS));
   S.ticket.alloc(1);
   S.ticket.zero(s);
   S.scal.alloc(1);
