@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstring>
+#include <exception>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -235,7 +236,7 @@ void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<
 template <class T>
 bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel, const std::vector<int64_t>& cstart,
                  const std::vector<T>& dinv, const HostCSR& SMd, const HostCSR& SM, const std::vector<int32_t>& pos,
-                 size_t smem_max, double max_halo, TileSweeps<T>& TS, cudaStream_t s) {
+                 size_t smem_max, double max_halo, unsigned max_threads, TileSweeps<T>& TS, cudaStream_t s) {
   const int64_t nsm = (int64_t)sel.size();
   const int ncol = (int)cstart.size() - 1;
   std::vector<int32_t> colr(nsm);
@@ -253,8 +254,7 @@ bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel
     bool ok = true;
   };
   std::vector<Out> out(ntiles);
-  const unsigned nt = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>({8, (int64_t)std::max(1u, std::thread::hardware_concurrency()), ntiles}));
+  const unsigned nt = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)max_threads, ntiles));
   std::vector<std::thread> th;
   for (unsigned w = 0; w < nt; ++w)
     th.emplace_back([&, w] {
@@ -612,10 +612,29 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
     const size_t smem_max = prm.tile_rows > 0 ? TILE_SMEM_MAX : TILE_SMEM;
     for (int trows : sizes) {
       if (!ok || D.nsm_real < 2 * (int64_t)trows) continue;
+      // the two directions are built at the same time, each on half the host threads
       TileSweeps<T> td, tu;
-      if (!build_tiles<T>(false, prm.nu_pre, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, td, s) ||
-          !build_tiles<T>(true, prm.nu_post, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, tu, s))
-        continue;
+      const unsigned half = std::max(1u, std::thread::hardware_concurrency() / 2);
+      bool okd = false, oku = false;
+      std::exception_ptr eu, ed;
+      std::thread up_th([&] {
+        try {
+          oku = build_tiles<T>(true, prm.nu_post, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, half,
+                               tu, s);
+        } catch (...) {
+          eu = std::current_exception();
+        }
+      });
+      try {
+        okd = build_tiles<T>(false, prm.nu_pre, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, half,
+                             td, s);
+      } catch (...) {
+        ed = std::current_exception();
+      }
+      up_th.join();
+      if (ed) std::rethrow_exception(ed);
+      if (eu) std::rethrow_exception(eu);
+      if (!okd || !oku) continue;
       std::vector<int32_t> p0(sel.size(), -3), p1(sel.size(), -3);
       for (size_t t = 0; t < L.new_id.size(); ++t) {
         p0[pos[L.new_id[t]]] = L.new_p0[t];
