@@ -443,7 +443,7 @@ bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel
     interior += O.interior;
     halo += O.halo;
   }
-  const size_t smem = (size_t)maxblob + (size_t)(maxloc + maxext) * sizeof(T) + (size_t)maxloc * sizeof(T);
+  const size_t smem = (size_t)maxblob + (size_t)(maxloc + (maxext + 3) / 4 * 4) * sizeof(T) + (size_t)maxloc * sizeof(T);
   if (smem > smem_max || (double)halo > max_halo * (double)interior) return false;
   std::vector<int64_t> loc_off(1, 0), blob_off(1, 0), ext_off(1, 0);
   std::vector<int32_t> phase;
@@ -457,10 +457,27 @@ bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel
     TS.nnz += O.nnz;
     TS.nnz_real += O.nnz_real;
   }
+  if (up) {
+    // where each SM row sits in tile order (own and halo copies)
+    std::vector<int64_t> pptr(nsm + 1, 0);
+    for (auto& O : out)
+      for (int32_t g : O.lrow)
+        if (g != -1) ++pptr[(g >= 0 ? g : -2 - g) + 1];
+    for (int64_t k = 0; k < nsm; ++k) pptr[k + 1] += pptr[k];
+    std::vector<int32_t> pos(pptr[nsm]);
+    std::vector<int64_t> fill(pptr.begin(), pptr.end() - 1);
+    for (int64_t t = 0; t < ntiles; ++t)
+      for (size_t k = 0; k < out[t].lrow.size(); ++k) {
+        const int32_t g = out[t].lrow[k];
+        if (g != -1) pos[fill[g >= 0 ? g : -2 - g]++] = (int32_t)(loc_off[t] + (int64_t)k);
+      }
+    TS.pos_ptr.upload(pptr, s);
+    TS.pos.upload(pos, s);
+  }
   TS.ntiles = ntiles;
   TS.nloc = loc_off.back();
   TS.maxloc = (int)maxloc;
-  TS.maxext = (int)maxext;
+  TS.maxext = (int)((maxext + 3) / 4 * 4);  // F follows U in shared memory, 16-byte aligned
   TS.maxblob = maxblob;
   TS.interior = interior;
   TS.halo = halo;

@@ -41,6 +41,7 @@ struct SlotPrec {
   DBuf<T> uf, rho, F, U;            // fine work vector, fine residual, aux rhs / correction
   std::vector<DBuf<T>> fs, us;      // per level: saved rhs / pre-smoothed values on N~_l
   std::vector<DBuf<double>> nbr, nbs;  // per level: near-boundary rhs / solution pools (mixed boundaries)
+  std::vector<DBuf<T>> ust, fsl;    // per level with tiled post-sweeps: start values and saved rhs in tile order
   DBuf<SmallDesc<T>> deep_desc, bot_desc;
 };
 

@@ -317,6 +317,11 @@ struct TileSweeps {
   DBuf<int64_t> ext_off;         // [ntiles + 1] first outside value of each tile
   DBuf<int32_t> phase;           // [ntiles * (ncol + 1)] colour-class starts within each tile
   DBuf<unsigned char> blob;      // the tiles' blocks
+  // post-sweeps: every place (local row of some tile) where each SM row sits,
+  // own or halo (CSR by SM row), so that k_up_init can write the start values
+  // and saved rhs straight into tile order for the tiles to copy in
+  DBuf<int64_t> pos_ptr;         // [nsm + 1]
+  DBuf<int32_t> pos;             // positions in [0, nloc)
   // shared memory of a launch: the largest block, then U (rows and outside
   // values) and F of the largest tile
   size_t smem() const { return (size_t)maxblob + (size_t)(maxloc + maxext) * sizeof(T) + (size_t)maxloc * sizeof(T); }

@@ -459,20 +459,26 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restric
   pdl_trigger();
 }
 
-// start of the up path of a tiled level, in place on us (SM order): the
-// prolongation of the coarse correction (I_l: new nodes take the mean of
-// their parents) plus the level's saved correction.  U itself is not
-// written, so the tiles of k_tile_up read every row's start value from us
+// start of the up path of a tiled level: the prolongation of the coarse
+// correction (I_l: new nodes take the mean of their parents) plus the level's
+// saved correction, and the saved rhs, written for every SM row to each place
+// the row holds in the post-sweep tiles (own and halo copies; TileSweeps::
+// pos).  U itself is not written, so the tiles can copy their start values in
 // while other tiles write their results to U.
 template <class T>
 __global__ void k_up_init(int64_t nsm, const int32_t* __restrict__ rows, const int32_t* __restrict__ par0,
-                          const int32_t* __restrict__ par1, const T* __restrict__ U, T* __restrict__ us) {
+                          const int32_t* __restrict__ par1, const int64_t* __restrict__ pos_ptr,
+                          const int32_t* __restrict__ pos, const T* __restrict__ U, const T* __restrict__ us,
+                          const T* __restrict__ fs, T* __restrict__ ust, T* __restrict__ fsl) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1, a = -3, b = -3;
+  int64_t p0 = 0, p1 = 0;
   if (k < nsm) {
     i = rows[k];
     a = par0[k];
     b = par1[k];
+    p0 = pos_ptr[k];
+    p1 = pos_ptr[k + 1];
   }
   pdl_wait();
   if (i >= 0) {
@@ -485,48 +491,66 @@ __global__ void k_up_init(int64_t nsm, const int32_t* __restrict__ rows, const i
       if (b >= 0) p += U[b];
       v = (T)0.5 * p;
     }
-    us[k] = v + us[k];
+    v = v + us[k];
+    const T f = fs[k];
+    for (int64_t q = p0; q < p1; ++q) {
+      const int32_t o = pos[q];
+      ust[o] = v;
+      fsl[o] = f;
+    }
   }
   pdl_trigger();
 }
 
-// post-sweeps (backward colour order) from the start values in us; the
-// columns outside N~_l (the tile's outside values) are read from U once; the
-// tile's own rows are written to U
+// post-sweeps (backward colour order) from the start values and saved rhs
+// that k_up_init wrote in tile order: both arrive by bulk copy after the
+// wait on the previous kernel, the tile's block before it; the columns
+// outside N~_l (the tile's outside values) are read from U once; the tile's
+// own rows are written to U
 template <class T>
 __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict__ loc_off,
                                                       const int64_t* __restrict__ blob_off,
                                                       const unsigned char* __restrict__ blob,
                                                       const int64_t* __restrict__ ext_off,
                                                       const int32_t* __restrict__ phase, int ncol, int64_t maxblob,
-                                                      int maxloc, int maxext, const T* __restrict__ fs,
-                                                      const T* __restrict__ us, T* U, int nu, int* timeout,
+                                                      int maxloc, int maxext, const T* __restrict__ ust,
+                                                      const T* __restrict__ fsl, T* U, int nu, int* timeout,
                                                       int inject) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar2;
   const int64_t base = loc_off[blockIdx.x];
   const int nl = (int)(loc_off[blockIdx.x + 1] - base);
   const int64_t b0 = blob_off[blockIdx.x];
   const uint32_t bytes = (uint32_t)(blob_off[blockIdx.x + 1] - b0);
   const int nx = (int)(ext_off[blockIdx.x + 1] - ext_off[blockIdx.x]);
   const int32_t* ph = phase + (int64_t)blockIdx.x * (ncol + 1);
+  T* Ul = reinterpret_cast<T*>(smraw + maxblob);
+  T* Fl = Ul + maxloc + maxext;
+  if (threadIdx.x == 0) {
+    // initialised before tile_stage's fence.mbarrier_init, which covers it
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar2)) : "memory");
+  }
   tile_stage(smraw, blob + b0, bytes, &bar);
   pdl_wait();
-  if (tile_staged(&bar, timeout, inject)) {
-    TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, maxext, nl, nx);
-    for (int k = threadIdx.x; k < nl; k += blockDim.x) {
-      const int32_t g = t.lsm[k];
-      T f = 0, u = 0;
-      if (g != -1) {
-        const int32_t sm = g >= 0 ? g : -2 - g;
-        f = fs[sm];
-        u = us[sm];
-      }
-      t.Fl[k] = f;
-      t.Ul[k] = u;
-    }
+  if (threadIdx.x == 0) {
+    const uint32_t b2 = smem_addr(&bar2), vb = (uint32_t)((int64_t)nl * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b2), "r"(2 * vb) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(Ul)),
+                 "l"(ust + base), "r"(vb), "r"(b2)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(Fl)),
+                 "l"(fsl + base), "r"(vb), "r"(b2)
+                 : "memory");
+  }
+  const bool ok1 = tile_staged(&bar, timeout, inject);
+  // the outside values, once the block (which holds their IDs) is in place
+  TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, maxext, nl, nx);
+  if (ok1)
     for (int e = threadIdx.x; e < nx; e += blockDim.x) t.Ul[nl + e] = U[t.ext[e]];
-    __syncthreads();
+  const bool ok2 = tile_staged(&bar2, timeout, inject || !ok1);
+  if (ok1 && ok2) {
     for (int sw = 0; sw < nu; ++sw)
       for (int c = ncol - 1; c >= 0; --c) {
         for (int k = ph[c] + threadIdx.x; k < ph[c + 1]; k += blockDim.x) {
@@ -1139,15 +1163,18 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     auto SM = view(L.SM);
     g_prof_level = -2 - li;
     if (L.tiled_up) {
-      LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nsm_real * (12 + 2 * sz) + L.nnew * 2 * sz + (L.nsm_real - L.nnew) * sz,
-             launch(h.prm.use_pdl, k_up_init<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p,
-                    L.sm_par0.p, L.sm_par1.p, (const T*)SP.U.p, SP.us[li].p));
       const TileSweeps<T>& Tl = L.tup;
+      LAUNCH(ASMG_PROF_AUX_TRANSFER,
+             L.nsm_real * (28 + 3 * sz) + L.nnew * 2 * sz + (L.nsm_real - L.nnew) * sz +
+                 (Tl.interior + Tl.halo) * (4 + 2 * sz),
+             launch(h.prm.use_pdl, k_up_init<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p,
+                    L.sm_par0.p, L.sm_par1.p, Tl.pos_ptr.p, Tl.pos.p, (const T*)SP.U.p, (const T*)SP.us[li].p,
+                    (const T*)SP.fs[li].p, SP.ust[li].p, SP.fsl[li].p));
       const int64_t by = Tl.nnz_real * (sz + 2) + (Tl.interior + Tl.halo) * (8 + 3 * sz) + Tl.interior * (4 + sz);
       LAUNCH(ASMG_PROF_AUX_GS, by,
              launch_smem(h.prm.use_pdl, k_tile_up<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p, Tl.blob_off.p,
                          (const unsigned char*)Tl.blob.p, Tl.ext_off.p, Tl.phase.p, L.ncolours, Tl.maxblob,
-                         Tl.maxloc, Tl.maxext, (const T*)SP.fs[li].p, (const T*)SP.us[li].p, SP.U.p, npost,
+                         Tl.maxloc, Tl.maxext, (const T*)SP.ust[li].p, (const T*)SP.fsl[li].p, SP.U.p, npost,
                          timeout_flag(S), h.prm.inject_timeout));
       launches += 2;
       continue;
@@ -1505,11 +1532,22 @@ void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
   SP.nbs.clear();
   SP.nbr.resize(nlev);
   SP.nbs.resize(nlev);
+  SP.ust.clear();
+  SP.fsl.clear();
+  SP.ust.resize(nlev);
+  SP.fsl.resize(nlev);
   for (int li = 0; li < nlev; ++li) {
     SP.fs[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
     SP.us[li].alloc(std::max<int64_t>(P.lev[li].nsm, 1));
     SP.fs[li].zero(s);
     SP.us[li].zero(s);
+    if (P.lev[li].tiled_up) {
+      // post-sweep start values and saved rhs in tile order (padding rows stay 0)
+      SP.ust[li].alloc(std::max<int64_t>(P.lev[li].tup.nloc, 1));
+      SP.fsl[li].alloc(std::max<int64_t>(P.lev[li].tup.nloc, 1));
+      SP.ust[li].zero(s);
+      SP.fsl[li].zero(s);
+    }
     const NbDev& N = P.lev[li].nb;
     if (N.m > 0) {
       // the pools: every round's vector and the last block's (voff[R + 1] doubles)
@@ -1627,7 +1665,11 @@ void autotune_levels(asmg_s& h, cudaStream_t s) {
   for (int li : cand) {
     AuxLevelDev<T>& L = P.lev[li];
     if (!L.tiled_down) L.tdown = TileSweeps<T>();
-    if (!L.tiled_up) L.tup = TileSweeps<T>();
+    if (!L.tiled_up) {
+      L.tup = TileSweeps<T>();
+      slotprec<T>(S).ust[li] = DBuf<T>();
+      slotprec<T>(S).fsl[li] = DBuf<T>();
+    }
     L.tiled = L.tiled_down || L.tiled_up;
   }
 }
