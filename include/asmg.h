@@ -90,6 +90,11 @@ typedef struct {
                               splitmix64 priorities on every grid; 2 = on an auxiliary level whose
                               couplings the lattice parity (X + Y [+ Z]) / h_l mod 2 separates (uniform
                               levels), that parity (two classes), else Jones-Plassmann; 2 */
+  int32_t level_bf16;      /* ASMG_MIXED only: 1 = the V-cycle reads the auxiliary-level matrices A_l
+                              (sweeps and residuals) in BF16, each value the FP32 value rounded to
+                              nearest even (arithmetic, diagonal inverses and vectors stay FP32);
+                              0 = FP32.  A precision choice, not the paper's: the preconditioner
+                              changes, the solve still stops at rtol on the FP64 residual; 0 */
 } asmg_params;
 
 /* Fill *p with the defaults listed above.  Returns ASMG_ERR_INVALID_ARG if p is NULL. */

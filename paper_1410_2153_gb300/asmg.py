@@ -44,7 +44,7 @@ class asmg_params(ctypes.Structure):
                 ("smoother", ctypes.c_int32), ("additive", ctypes.c_int32), ("fine_sweeps", ctypes.c_int32),
                 ("iteration", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
                 ("inject_timeout", ctypes.c_int32), ("nb_layers", ctypes.c_int32),
-                ("colouring", ctypes.c_int32)]
+                ("colouring", ctypes.c_int32), ("level_bf16", ctypes.c_int32)]
 
 
 class AsmgError(RuntimeError):

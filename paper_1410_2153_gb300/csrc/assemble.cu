@@ -517,4 +517,18 @@ void sell_build(Sell<T>& S, const HostCSR& rows, int32_t pad_col, cudaStream_t s
 template void sell_build<float>(Sell<float>&, const HostCSR&, int32_t, cudaStream_t);
 template void sell_build<double>(Sell<double>&, const HostCSR&, int32_t, cudaStream_t);
 
+__global__ void k_to_bf16(int64_t n, const float* __restrict__ x, bf16v* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i].bits = bf16_bits(x[i]);
+}
+
+void sell_bf16(Sell<float>& S, cudaStream_t s) {
+  S.v16.alloc(std::max<int64_t>(S.nnz, 1));
+  if (S.nnz > 0) {
+    k_to_bf16<<<(unsigned)((S.nnz + 255) / 256), 256, 0, s>>>(S.nnz, S.val.p, S.v16.p);
+    ASMG_CUDA(cudaGetLastError());
+  }
+  ASMG_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace asmg

@@ -124,7 +124,7 @@ template <class T>
 void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<uint8_t>& inset,
                  const std::vector<int64_t>& sel, const std::vector<int64_t>& rsel, const std::vector<T>& dinv_pad,
                  const std::vector<int32_t>& pid, const std::vector<int32_t>& pptr, const std::vector<int32_t>& child,
-                 AuxLevelDev<T>& D, cudaStream_t s) {
+                 bool bf16, AuxLevelDev<T>& D, cudaStream_t s) {
   SmallLevelDev<T>& S = D.small;
   S.ok = false;
   std::vector<int32_t> gid;
@@ -213,6 +213,13 @@ void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<
   S.rs_ptr.upload(rs_ptr, s);
   S.rs_col.upload(rs_col, s);
   S.rs_val.upload(rs_val, s);
+  if (bf16) {
+    std::vector<bf16v> a(sm_val.size()), b(rs_val.size());
+    for (size_t k = 0; k < a.size(); ++k) a[k].bits = bf16_bits((float)sm_val[k]);
+    for (size_t k = 0; k < b.size(); ++k) b[k].bits = bf16_bits((float)rs_val[k]);
+    S.sm_v16.upload(a, s);
+    S.rs_v16.upload(b, s);
+  }
   S.nn_id.upload(nn_id, s);
   S.nn_p0.upload(nn_p0, s);
   S.nn_p1.upload(nn_p1, s);
@@ -241,7 +248,8 @@ void build_small(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<
 template <class T>
 bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel, const std::vector<int64_t>& cstart,
                  const std::vector<T>& dinv, const HostCSR& SMd, const HostCSR& SM, const std::vector<int32_t>& pos,
-                 size_t smem_max, double max_halo, unsigned max_threads, TileSweeps<T>& TS, cudaStream_t s) {
+                 size_t smem_max, double max_halo, unsigned max_threads, bool bf16, TileSweeps<T>& TS,
+                 cudaStream_t s) {
   const int64_t nsm = (int64_t)sel.size();
   const int ncol = (int)cstart.size() - 1;
   std::vector<int32_t> colr(nsm);
@@ -407,17 +415,22 @@ bool build_tiles(bool up, int nu, int tile_rows, const std::vector<int64_t>& sel
         const int64_t ne_ = soff[nsl], nx = (int64_t)O.ext.size();
         O.nnz = ne_;
         O.nnz_real = rptr[nl];
-        const TileLayout lay = tile_layout((int64_t)nl, ne_, nx, (int64_t)sizeof(T));
+        const TileLayout lay =
+            tile_layout((int64_t)nl, ne_, nx, (int64_t)sizeof(T), bf16 ? (int64_t)sizeof(bf16v) : (int64_t)sizeof(T));
         O.blob.assign(lay.end, 0);
         std::memcpy(O.blob.data(), soff.data(), 4 * (size_t)(nsl + 1));
         uint16_t* cc = reinterpret_cast<uint16_t*>(O.blob.data() + lay.col);
         T* vv = reinterpret_cast<T*>(O.blob.data() + lay.val);
+        bf16v* vb = reinterpret_cast<bf16v*>(O.blob.data() + lay.val);
         for (int r = 0; r < nl; ++r) {
           const int sl = r / 32, lane = r % 32;
           int64_t e = 0;
           for (int64_t p = rptr[r]; p < rptr[r + 1]; ++p, ++e) {
             cc[soff[sl] + e * 32 + lane] = (uint16_t)rcol[p];
-            vv[soff[sl] + e * 32 + lane] = (T)rval[p];
+            if (bf16)
+              vb[soff[sl] + e * 32 + lane].bits = bf16_bits((float)rval[p]);
+            else
+              vv[soff[sl] + e * 32 + lane] = (T)rval[p];
           }
         }
         T* dd = reinterpret_cast<T*>(O.blob.data() + lay.dinv);
@@ -568,6 +581,8 @@ template <class T>
 void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vector<int32_t>& colour,
                      const std::vector<uint8_t>& inset, const asmg_params& prm, AuxLevelDev<T>& D, cudaStream_t s) {
   D.level = L.level;
+  // the mixed form may read the level matrices in BF16 (asmg_params::level_bf16)
+  const bool bf16 = std::is_same<T, float>::value && prm.level_bf16 == 1;
   // smoothing rows ordered by (colour, id), colour blocks padded to 32
   int ncol = 0;
   for (int32_t id : L.smooth) ncol = std::max(ncol, colour[id] + 1);
@@ -614,6 +629,11 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
       }
   sell_build<T>(D.SM, SM, 0, s);
   sell_build<T>(D.SMd, SMd, 0, s);
+  if constexpr (std::is_same<T, float>::value)
+    if (bf16) {
+      sell_bf16(D.SM, s);
+      sell_bf16(D.SMd, s);
+    }
   D.sm_rows.upload(rows, s);
   D.sm_dinv.upload(dinv, s);
   // temporal blocking of the level's sweeps (TileSweeps): the first tile size
@@ -643,14 +663,14 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
       std::thread up_th([&] {
         try {
           oku = build_tiles<T>(true, prm.nu_post, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, half,
-                               tu, s);
+                               bf16, tu, s);
         } catch (...) {
           eu = std::current_exception();
         }
       });
       try {
         okd = build_tiles<T>(false, prm.nu_pre, trows, sel, D.cstart, dinv, SMd, SM, pos, smem_max, max_halo, half,
-                             td, s);
+                             bf16, td, s);
       } catch (...) {
         ed = std::current_exception();
       }
@@ -690,6 +710,8 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
   D.nrs = (int64_t)rsel.size();
   HostCSR RS = select_rows(Arows, rsel, &pos, &inset);
   sell_build<T>(D.RS, RS, 0, s);
+  if constexpr (std::is_same<T, float>::value)
+    if (bf16) sell_bf16(D.RS, s);
   std::vector<int32_t> rsrows(rsel.begin(), rsel.end());
   D.rs_rows.upload(rsrows, s);
   // prolongation and restriction of the new nodes
@@ -720,7 +742,7 @@ void build_level_dev(const AuxLevelHost& L, const HostCSR& Arows, const std::vec
   build_nb_dev<T>(L, Arows, pos, D, s);
   // a level with a near-boundary solve keeps its own launches (the solve sits
   // between the coarse correction and the post-smoothing)
-  if (D.nb.m == 0) build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, D, s);
+  if (D.nb.m == 0) build_small<T>(L, Arows, inset, sel, rsel, dinv, pid, pptr, child, bf16, D, s);
   else D.small.ok = false;
 }
 
@@ -1114,6 +1136,7 @@ int asmg_default_params(asmg_params* p) {
   p->inject_timeout = 0;
   p->nb_layers = 2;
   p->colouring = 2;
+  p->level_bf16 = 0;
   return ASMG_OK;
 }
 
@@ -1137,7 +1160,8 @@ int amg_setup(int dim, int64_t nv, const double* vertices, int64_t ne, const int
       prm.fine_sweeps > 8 || (prm.iteration != 0 && prm.iteration != 1) ||
       (prm.tile_rows != -1 && prm.tile_rows != 0 && (prm.tile_rows < 32 || prm.tile_rows > 65536)) ||
       (prm.inject_timeout != 0 && prm.inject_timeout != 1) || prm.nb_layers < -1 || prm.nb_layers > 16 ||
-      (prm.colouring != 0 && prm.colouring != 2))
+      (prm.colouring != 0 && prm.colouring != 2) || (prm.level_bf16 != 0 && prm.level_bf16 != 1) ||
+      (prm.level_bf16 == 1 && prm.precision != ASMG_MIXED))
     ASMG_FAIL(ASMG_ERR_INVALID_ARG, "invalid parameter");
   cudaStream_t s = (cudaStream_t)stream;
   double t0 = now();

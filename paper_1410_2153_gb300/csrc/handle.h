@@ -17,6 +17,16 @@ SellView<T> view(const Sell<T>& S) {
   return SellView<T>{S.off.p, S.col.p, S.val.p};
 }
 
+// a Sell's stored values, in the arithmetic type or in BF16 (level_bf16)
+template <class T>
+const T* sell_vals(const Sell<T>& S, const T*) {
+  return S.val.p;
+}
+template <class T>
+const bf16v* sell_vals(const Sell<T>& S, const bf16v*) {
+  return S.v16.p;
+}
+
 // Scalars of the PCG recurrences, device resident.
 struct PcgScalars {
   double rz;      // <r_k, z_k>

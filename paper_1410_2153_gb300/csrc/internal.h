@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <memory>
 #include <string>
 #include <vector>
@@ -93,6 +94,27 @@ struct HostCSR {
 // off[s] + 32 k + t.  Padding entries have col = pad_col, val = 0.
 constexpr int SELL_C = 32;
 
+// An auxiliary-level matrix value stored in BF16 (asmg_params::level_bf16):
+// the upper 16 bits of its FP32 value rounded to nearest even, which widen
+// back to FP32 exactly.
+struct bf16v {
+  uint16_t bits;
+};
+
+// FP32 -> BF16 bits, round to nearest even (finite values): adding 0x7FFF plus
+// the lowest kept bit carries into the kept half exactly when the dropped half
+// is above one half ulp, or equal to it with an odd kept half.
+inline __host__ __device__ uint16_t bf16_bits(float f) {
+  uint32_t u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(f);
+#else
+  std::memcpy(&u, &f, 4);
+#endif
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
 template <class T>
 struct Sell {
   int64_t nrows = 0;   // multiple of 32
@@ -102,12 +124,16 @@ struct Sell {
   DBuf<int64_t> off;   // [nslices + 1]
   DBuf<int32_t> col;   // [nnz]
   DBuf<T> val;         // [nnz]
+  DBuf<bf16v> v16;     // [nnz] the values in BF16 (auxiliary levels with level_bf16), else empty
 };
 
 // Build SELL-32 from host rows given as CSR in the SELL row order
 // (row k of `rows` is SELL row k; rows.nr need not be a multiple of 32).
 template <class T>
 void sell_build(Sell<T>& S, const HostCSR& rows, int32_t pad_col, cudaStream_t s);
+
+// Fill S.v16 with the BF16 form (bf16_bits) of S.val, on the device.
+void sell_bf16(Sell<float>& S, cudaStream_t s);
 
 // --------------------------------------------------------------- tree
 struct TreeResult {
@@ -235,15 +261,18 @@ constexpr int SMALL_MAXC = 24;
 template <class T>
 struct SmallDesc {
   int mS, mE, ncol, nnew, npar;
+  int nnz_sm, nnz_rs, nchild;  // entries of the smoothing / residual rows, children of the restriction
   int cs[SMALL_MAXC + 1];
   const int32_t* gid;
   const int32_t* sm_ptr;
   const uint16_t* sm_col;
   const T* sm_val;
+  const bf16v* sm_v16;  // the same values in BF16 (level_bf16), else null
   const T* dinv;
   const int32_t* rs_ptr;
   const uint16_t* rs_col;
   const T* rs_val;
+  const bf16v* rs_v16;
   const uint16_t* nn_id;
   const int32_t* nn_p0;
   const int32_t* nn_p1;
@@ -263,6 +292,7 @@ struct SmallLevelDev {
   DBuf<int32_t> gid, sm_ptr, rs_ptr, nn_p0, nn_p1, rp_ptr;
   DBuf<uint16_t> sm_col, rs_col, nn_id, rp_id, rp_child;
   DBuf<T> sm_val, dinv, rs_val;
+  DBuf<bf16v> sm_v16, rs_v16;  // level_bf16: sm_val / rs_val in BF16
 };
 
 // Temporal blocking of the sweeps of one auxiliary level (Algorithm 2's
@@ -291,12 +321,13 @@ struct TileLayout {
 };
 
 // nl local rows (a multiple of 32), ne stored entries, nx outside values, s bytes per value
-inline __host__ __device__ TileLayout tile_layout(int64_t nl, int64_t ne, int64_t nx, int64_t s) {
+// (diagonal inverses), sv bytes per stored matrix value
+inline __host__ __device__ TileLayout tile_layout(int64_t nl, int64_t ne, int64_t nx, int64_t s, int64_t sv) {
   auto pad16 = [](int64_t b) { return (b + 15) & ~(int64_t)15; };
   TileLayout t;
   t.col = pad16(4 * (nl / 32 + 1));
   t.val = t.col + pad16(2 * ne);
-  t.dinv = t.val + pad16(s * ne);
+  t.dinv = t.val + pad16(sv * ne);
   t.lsm = t.dinv + pad16(s * nl);
   t.laux = t.lsm + pad16(4 * nl);
   t.ext = t.laux + pad16(4 * nl);

@@ -92,9 +92,26 @@ struct Row {
   T v[MAXW];
 };
 
-template <class T>
+// Matrix values as stored (FP64, FP32 or BF16), widened to the arithmetic
+// type exactly; the ldg forms read through the read-only path, the ldcs forms
+// stream (evict first).
+__device__ __forceinline__ double ldg_val(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_val(const bf16v* p) {
+  return __uint_as_float((uint32_t)__ldg(&p->bits) << 16);
+}
+__device__ __forceinline__ double ldcs_val(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldcs_val(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ldcs_val(const bf16v* p) {
+  return __uint_as_float((uint32_t)__ldcs(&p->bits) << 16);
+}
+__device__ __forceinline__ double val_of(double v) { return v; }
+__device__ __forceinline__ float val_of(float v) { return v; }
+__device__ __forceinline__ float val_of(bf16v v) { return __uint_as_float((uint32_t)v.bits << 16); }
+
+template <class T, class V>
 __device__ __forceinline__ void row_load(Row<T>& R, int64_t row, const int64_t* __restrict__ off,
-                                         const int32_t* __restrict__ col, const T* __restrict__ val) {
+                                         const int32_t* __restrict__ col, const V* __restrict__ val) {
   const int64_t sl = row >> 5;
   R.lane = row & 31;
   R.b = __ldg(off + sl);
@@ -104,12 +121,12 @@ __device__ __forceinline__ void row_load(Row<T>& R, int64_t row, const int64_t* 
     if (k < R.w) {
       const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
       R.c[k] = __ldcs(col + e);
-      R.v[k] = __ldcs(val + e);
+      R.v[k] = (T)ldcs_val(val + e);
     }
 }
 
-template <class T, class X>
-__device__ __forceinline__ T row_dot(const Row<T>& R, const int32_t* __restrict__ col, const T* __restrict__ val,
+template <class T, class V, class X>
+__device__ __forceinline__ T row_dot(const Row<T>& R, const int32_t* __restrict__ col, const V* __restrict__ val,
                                      const X* x) {
   T s = 0;
 #pragma unroll
@@ -117,7 +134,7 @@ __device__ __forceinline__ T row_dot(const Row<T>& R, const int32_t* __restrict_
     if (k < R.w) s += R.v[k] * (T)x[R.c[k]];
   for (int k = MAXW; k < R.w; ++k) {
     const int64_t e = R.b + ((int64_t)k << 5) + R.lane;
-    s += __ldg(val + e) * (T)x[__ldg(col + e)];
+    s += (T)ldg_val(val + e) * (T)x[__ldg(col + e)];
   }
   return s;
 }
@@ -170,6 +187,51 @@ __device__ bool grid_reduce(double (&v)[NV], double* partial, unsigned int* tick
   if (threadIdx.x == 0) *ticket = 0;
   return true;
 }
+
+// Ask L1 for the [p, p + bytes) lines (a hint: no data moves into registers,
+// nothing is waited for); the block's threads share the lines.
+__device__ __forceinline__ void l1_prefetch(const void* p, int64_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (int64_t o = (int64_t)threadIdx.x * 128; o < bytes; o += (int64_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(c + o));
+}
+
+// The setup data one level of a fused run reads (never written by a solve, so
+// it may be requested before the wait on the previous kernel): the level's
+// own descriptor, row pointers, entries and diagonal, and the tables of the
+// restriction (down) or of the new nodes' parents (up).  Its phases then read
+// these from L1 rather than waiting on L2 at every colour phase.
+template <class T>
+__device__ __forceinline__ void small_prefetch(const SmallDesc<T>* Dd, bool down) {
+  const SmallDesc<T>& L = *Dd;
+  l1_prefetch(L.gid, (int64_t)L.mE * 4);
+  l1_prefetch(L.sm_ptr, (int64_t)(L.mS + 1) * 4);
+  l1_prefetch(L.sm_col, (int64_t)L.nnz_sm * 2);
+  l1_prefetch(L.sm_val, (int64_t)L.nnz_sm * sizeof(T));
+  l1_prefetch(L.dinv, (int64_t)L.mS * sizeof(T));
+  if (down) {
+    l1_prefetch(L.rs_ptr, (int64_t)(L.mE + 1) * 4);
+    l1_prefetch(L.rs_col, (int64_t)L.nnz_rs * 2);
+    l1_prefetch(L.rs_val, (int64_t)L.nnz_rs * sizeof(T));
+    l1_prefetch(L.rp_id, (int64_t)L.npar * 2);
+    l1_prefetch(L.rp_ptr, (int64_t)(L.npar + 1) * 4);
+    l1_prefetch(L.rp_child, (int64_t)L.nchild * 2);
+  } else {
+    l1_prefetch(L.nn_id, (int64_t)L.nnew * 2);
+    l1_prefetch(L.nn_p0, (int64_t)L.nnew * 4);
+    l1_prefetch(L.nn_p1, (int64_t)L.nnew * 4);
+  }
+}
+
+// the level's stored values: FP32/FP64, or their BF16 copy
+template <class T>
+__device__ __forceinline__ const T* sm_vals(const SmallDesc<T>& L, const T*) { return L.sm_val; }
+template <class T>
+__device__ __forceinline__ const bf16v* sm_vals(const SmallDesc<T>& L, const bf16v*) { return L.sm_v16; }
+template <class T>
+__device__ __forceinline__ const T* rs_vals(const SmallDesc<T>& L, const T*) { return L.rs_val; }
+template <class T>
+__device__ __forceinline__ const bf16v* rs_vals(const SmallDesc<T>& L, const bf16v*) { return L.rs_v16; }
 
 }  // namespace kern
 }  // namespace asmg

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <type_traits>
 #include <vector>
 
 #include "handle.h"
@@ -133,9 +134,9 @@ __global__ void k_cast_fine(int64_t n, const double* __restrict__ r, T* __restri
 // ------------------------------------------------------ auxiliary levels
 // one colour of an up (post-smoothing) sweep on the smoothing rows of a
 // level: U[i] += (fs_k - (A_l U)_i) / a_ii with the F saved on the way down
-template <class T>
+template <class T, class V>
 __global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                         const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
+                         const V* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
                          const T* __restrict__ fs, T* U) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
@@ -163,9 +164,9 @@ __global__ void k_gs_aux(int64_t k0, int64_t nk, const int64_t* __restrict__ off
 // later ones: only columns of earlier classes (below k0) are read, and the
 // class's rows are set rather than updated.  The first sweep takes F and
 // saves it in fs.
-template <class T>
+template <class T, class V>
 __global__ void k_gs_aux_down(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                              const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
+                              const V* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
                               const T* __restrict__ F, int first, T* __restrict__ fs, T* us) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
@@ -190,7 +191,7 @@ __global__ void k_gs_aux_down(int64_t k0, int64_t nk, const int64_t* __restrict_
       for (int q = MAXW; q < row.w; ++q) {
         const int64_t e = row.b + ((int64_t)q << 5) + row.lane;
         const int32_t c = __ldg(col + e);
-        if (c < k0) acc += __ldg(val + e) * us[c];
+        if (c < k0) acc += (T)ldg_val(val + e) * us[c];
       }
       us[k] = (f - acc) * di;
     } else {
@@ -203,9 +204,9 @@ __global__ void k_gs_aux_down(int64_t k0, int64_t nk, const int64_t* __restrict_
 }
 
 // F_i -= sum_{j in N~_l} a_ij U_j on the rows E_l
-template <class T>
+template <class T, class V>
 __global__ void k_resid_aux(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                            const T* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
+                            const V* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
                             T* __restrict__ F) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
@@ -357,8 +358,8 @@ __device__ __forceinline__ bool tile_staged(uint64_t* bar, int* timeout, int inj
 
 // the row's entries in stored order, four loaded ahead of their use (the sum
 // is formed in the same order as a plain loop)
-template <class T>
-__device__ __forceinline__ T tile_row_dot(int r, const int32_t* soff, const uint16_t* col, const T* val, const T* Ul) {
+template <class T, class V>
+__device__ __forceinline__ T tile_row_dot(int r, const int32_t* soff, const uint16_t* col, const V* val, const T* Ul) {
   const int sl = r >> 5, lane = r & 31;
   const int b = soff[sl], w = (soff[sl + 1] - b) >> 5;
   T acc = 0;
@@ -366,7 +367,8 @@ __device__ __forceinline__ T tile_row_dot(int r, const int32_t* soff, const uint
   for (; e + 4 <= w; e += 4) {
     const int q = b + (e << 5) + lane;
     const int c0 = col[q], c1 = col[q + 32], c2 = col[q + 64], c3 = col[q + 96];
-    const T v0 = val[q], v1 = val[q + 32], v2 = val[q + 64], v3 = val[q + 96];
+    const T v0 = (T)val_of(val[q]), v1 = (T)val_of(val[q + 32]), v2 = (T)val_of(val[q + 64]),
+            v3 = (T)val_of(val[q + 96]);
     const T x0 = Ul[c0], x1 = Ul[c1], x2 = Ul[c2], x3 = Ul[c3];
     acc += v0 * x0;
     acc += v1 * x1;
@@ -375,18 +377,18 @@ __device__ __forceinline__ T tile_row_dot(int r, const int32_t* soff, const uint
   }
   for (; e < w; ++e) {
     const int q = b + (e << 5) + lane;
-    acc += val[q] * Ul[col[q]];
+    acc += (T)val_of(val[q]) * Ul[col[q]];
   }
   return acc;
 }
 
 // the staged block of a tile (TileLayout) and, after it, U (local rows and
 // outside values) and F
-template <class T>
+template <class T, class V>
 struct TileSmem {
   const int32_t* soff;
   const uint16_t* col;
-  const T* val;
+  const V* val;
   const T* dinv;
   const int32_t* lsm;
   const int32_t* laux;
@@ -394,14 +396,14 @@ struct TileSmem {
   T *Ul, *Fl;
 };
 
-template <class T>
-__device__ __forceinline__ TileSmem<T> tile_smem(unsigned char* raw, int64_t maxblob, int maxloc, int maxext, int nl,
-                                                 int nx) {
-  TileSmem<T> t;
+template <class T, class V>
+__device__ __forceinline__ TileSmem<T, V> tile_smem(unsigned char* raw, int64_t maxblob, int maxloc, int maxext,
+                                                    int nl, int nx) {
+  TileSmem<T, V> t;
   t.soff = reinterpret_cast<const int32_t*>(raw);
-  const TileLayout lay = tile_layout(nl, t.soff[nl >> 5], nx, (int64_t)sizeof(T));
+  const TileLayout lay = tile_layout(nl, t.soff[nl >> 5], nx, (int64_t)sizeof(T), (int64_t)sizeof(V));
   t.col = reinterpret_cast<const uint16_t*>(raw + lay.col);
-  t.val = reinterpret_cast<const T*>(raw + lay.val);
+  t.val = reinterpret_cast<const V*>(raw + lay.val);
   t.dinv = reinterpret_cast<const T*>(raw + lay.dinv);
   t.lsm = reinterpret_cast<const int32_t*>(raw + lay.lsm);
   t.laux = reinterpret_cast<const int32_t*>(raw + lay.laux);
@@ -414,7 +416,7 @@ __device__ __forceinline__ TileSmem<T> tile_smem(unsigned char* raw, int64_t max
 // pre-sweeps: us (the level's own correction, SM order) starts at 0; the
 // first sweep saves F on the tile's own rows in fs.  The block is copied in
 // while the previous kernel finishes.
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restrict__ loc_off,
                                                         const int64_t* __restrict__ blob_off,
                                                         const unsigned char* __restrict__ blob,
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restric
   tile_stage(smraw, blob + b0, bytes, &bar);
   pdl_wait();
   if (tile_staged(&bar, timeout, inject)) {
-    TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, 0, nl, 0);
+    TileSmem<T, V> t = tile_smem<T, V>(smraw, maxblob, maxloc, 0, nl, 0);
     for (int k = threadIdx.x; k < nl; k += blockDim.x) {
       const int32_t g = t.lsm[k];
       T f = 0;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_down(const int64_t* __restric
     for (int sw = 0; sw < nu; ++sw)
       for (int c = 0; c < ncol; ++c) {
         for (int k = ph[c] + threadIdx.x; k < ph[c + 1]; k += blockDim.x) {
-          const T acc = tile_row_dot<T>(k, t.soff, t.col, t.val, t.Ul);
+          const T acc = tile_row_dot<T, V>(k, t.soff, t.col, t.val, t.Ul);
           t.Ul[k] += (t.Fl[k] - acc) * t.dinv[k];
         }
         __syncthreads();
@@ -507,7 +509,7 @@ __global__ void k_up_init(int64_t nsm, const int32_t* __restrict__ rows, const i
 // wait on the previous kernel, the tile's block before it; the columns
 // outside N~_l (the tile's outside values) are read from U once; the tile's
 // own rows are written to U
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict__ loc_off,
                                                       const int64_t* __restrict__ blob_off,
                                                       const unsigned char* __restrict__ blob,
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict_
   }
   const bool ok1 = tile_staged(&bar, timeout, inject);
   // the outside values, once the block (which holds their IDs) is in place
-  TileSmem<T> t = tile_smem<T>(smraw, maxblob, maxloc, maxext, nl, nx);
+  TileSmem<T, V> t = tile_smem<T, V>(smraw, maxblob, maxloc, maxext, nl, nx);
   if (ok1)
     for (int e = threadIdx.x; e < nx; e += blockDim.x) t.Ul[nl + e] = U[t.ext[e]];
   const bool ok2 = tile_staged(&bar2, timeout, inject || !ok1);
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(TILE_TPB) k_tile_up(const int64_t* __restrict_
     for (int sw = 0; sw < nu; ++sw)
       for (int c = ncol - 1; c >= 0; --c) {
         for (int k = ph[c] + threadIdx.x; k < ph[c + 1]; k += blockDim.x) {
-          const T acc = tile_row_dot<T>(k, t.soff, t.col, t.val, t.Ul);
+          const T acc = tile_row_dot<T, V>(k, t.soff, t.col, t.val, t.Ul);
           t.Ul[k] += (t.Fl[k] - acc) * t.dinv[k];
         }
         __syncthreads();
@@ -713,25 +715,25 @@ constexpr size_t small_smem() {
 
 // acc - sum_p val[p] * x[col[p]] over p0 <= p < p1, the first SMALL_B
 // entries loaded together (ascending p, as a plain loop would add them)
-template <class T>
-__device__ __forceinline__ T small_row(T acc, int p0, int p1, const T* __restrict__ val,
+template <class T, class V>
+__device__ __forceinline__ T small_row(T acc, int p0, int p1, const V* __restrict__ val,
                                        const uint16_t* __restrict__ col, const T* x) {
   T v[SMALL_B];
   uint16_t c[SMALL_B];
 #pragma unroll
   for (int q = 0; q < SMALL_B; ++q)
     if (p0 + q < p1) {
-      v[q] = val[p0 + q];
+      v[q] = (T)val_of(val[p0 + q]);
       c[q] = col[p0 + q];
     }
 #pragma unroll
   for (int q = 0; q < SMALL_B; ++q)
     if (p0 + q < p1) acc -= v[q] * x[c[q]];
-  for (int p = p0 + SMALL_B; p < p1; ++p) acc -= val[p] * x[col[p]];
+  for (int p = p0 + SMALL_B; p < p1; ++p) acc -= (T)val_of(val[p]) * x[col[p]];
   return acc;
 }
 
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(SMALL_TPB, 1)
     k_small_down(const SmallDesc<T>* __restrict__ D, int nlev, T* F, int nu) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -739,10 +741,12 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   T* Fl = Ul + SMALL_LMAX;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
   int32_t* Prs = Psm + SMALL_LMAX + 1;
+  if (nlev > 0) small_prefetch(D, true);
   pdl_wait();
   for (int d = 0; d < nlev; ++d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
+    if (d + 1 < nlev) small_prefetch(D + d + 1, true);
     for (int k = threadIdx.x; k <= mE; k += blockDim.x) {
       if (k < mE) {
         const T f = F[L.gid[k]];
@@ -757,12 +761,12 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
     for (int sw = 0; sw < nu; ++sw)
       for (int c = 0; c < L.ncol; ++c) {
         for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
-          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
+          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], sm_vals(L, (const V*)nullptr), L.sm_col, Ul);
           Ul[k] += acc * L.dinv[k];
         }
         __syncthreads();
       }
-    for (int k = threadIdx.x; k < mE; k += blockDim.x) Fl[k] = small_row(Fl[k], Prs[k], Prs[k + 1], L.rs_val, L.rs_col, Ul);
+    for (int k = threadIdx.x; k < mE; k += blockDim.x) Fl[k] = small_row(Fl[k], Prs[k], Prs[k + 1], rs_vals(L, (const V*)nullptr), L.rs_col, Ul);
     __syncthreads();
     for (int t = threadIdx.x; t < L.npar; t += blockDim.x) {
       T acc = 0;
@@ -779,17 +783,19 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   pdl_trigger();
 }
 
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(SMALL_TPB, 1)
     k_small_up(const SmallDesc<T>* __restrict__ D, int nlev, T* U, int nu) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + SMALL_LMAX;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
+  if (nlev > 0) small_prefetch(D + nlev - 1, false);
   pdl_wait();
   for (int d = nlev - 1; d >= 0; --d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
+    if (d > 0) small_prefetch(D + d - 1, false);
     for (int k = threadIdx.x; k < mE; k += blockDim.x) {
       Ul[k] = U[L.gid[k]];
       if (k < mS) Fl[k] = L.fs[k];
@@ -810,7 +816,7 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
     for (int sw = 0; sw < nu; ++sw)
       for (int c = L.ncol - 1; c >= 0; --c) {
         for (int k = L.cs[c] + threadIdx.x; k < L.cs[c + 1]; k += blockDim.x) {
-          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
+          const T acc = small_row(Fl[k], Psm[k], Psm[k + 1], sm_vals(L, (const V*)nullptr), L.sm_col, Ul);
           Ul[k] += acc * L.dinv[k];
         }
         __syncthreads();
@@ -1067,15 +1073,15 @@ SlotPrec<double>& slotprec<double>(Slot& S) { return S.s64; }
 template <>
 SlotPrec<float>& slotprec<float>(Slot& S) { return S.s32; }
 
-template <class T>
+template <class T, class V>
 int64_t small_bytes(const Prec<T>& P, int first, int count, int nu, bool down) {
-  const int64_t sz = sizeof(T);
+  const int64_t sz = sizeof(T), sv = sizeof(V);
   int64_t by = 0;
   for (int k = 0; k < count; ++k) {
     const SmallLevelDev<T>& S = P.lev[first + k].small;
-    by += nu * (S.nnz_sm * (2 + sz) + (int64_t)S.mS * (4 + sz));
+    by += nu * (S.nnz_sm * (2 + sv) + (int64_t)S.mS * (4 + sz));
     if (down)
-      by += (int64_t)S.mE * (4 + 2 * sz) + (int64_t)S.mS * 2 * sz + S.nnz_rs * (2 + sz) + (int64_t)S.mE * 4 +
+      by += (int64_t)S.mE * (4 + 2 * sz) + (int64_t)S.mS * 2 * sz + S.nnz_rs * (2 + sv) + (int64_t)S.mE * 4 +
             (int64_t)S.npar * 10 + S.nchild * 2;
     else
       by += (int64_t)S.mE * (4 + sz) + (int64_t)S.mS * 3 * sz + (int64_t)S.nnew * 10;
@@ -1088,19 +1094,20 @@ int* timeout_flag(Slot& S) {
   return reinterpret_cast<int*>(reinterpret_cast<char*>(S.scal.p) + offsetof(PcgScalars, timeout));
 }
 
-template <class T>
+// V: how the auxiliary-level matrices are read (T, or bf16v with level_bf16)
+template <class T, class V>
 int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   Prec<T>& P = prec<T>(h);
   SlotPrec<T>& SP = slotprec<T>(S);
   int launches = 0;
-  const int64_t sz = sizeof(T);
+  const int64_t sz = sizeof(T), sv = sizeof(V);
   const int npre = h.prm.nu_pre, npost = h.prm.nu_post;
   const int nlev = (int)P.lev.size();
   const int ndeep = P.n_deep, nbot = P.n_bottom;  // fused runs at the top and at the bottom
   const size_t smem = small_smem<T>();
   if (ndeep) {
-    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npre, true),
-           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.F.p, npre));
+    LAUNCH(ASMG_PROF_AUX_SMALL, (small_bytes<T, V>(P, nlev - ndeep, ndeep, npre, true)),
+           launch_smem(h.prm.use_pdl, k_small_down<T, V>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.F.p, npre));
     ++launches;
   }
   for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
@@ -1111,9 +1118,9 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
       // all pre-sweeps of the level in one launch (compulsory bytes: the
       // tiles' blocks once, F gathered and saved, us written)
       const TileSweeps<T>& Tl = L.tdown;
-      const int64_t by = Tl.nnz_real * (sz + 2) + (Tl.interior + Tl.halo) * (8 + 2 * sz) + Tl.interior * (4 + sz);
+      const int64_t by = Tl.nnz_real * (sv + 2) + (Tl.interior + Tl.halo) * (8 + 2 * sz) + Tl.interior * (4 + sz);
       LAUNCH(ASMG_PROF_AUX_GS, by,
-             launch_smem(h.prm.use_pdl, k_tile_down<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p,
+             launch_smem(h.prm.use_pdl, k_tile_down<T, V>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p,
                          Tl.blob_off.p, (const unsigned char*)Tl.blob.p, Tl.phase.p, L.ncolours, Tl.maxblob,
                          Tl.maxloc, (const T*)SP.F.p, SP.fs[li].p, SP.us[li].p, npre, timeout_flag(S),
                          h.prm.inject_timeout));
@@ -1125,17 +1132,17 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
       for (int c = 0; c < L.ncolours; ++c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        const int64_t by = L.cnnz_d[c] * (sz + 4) + L.crows[c] * (4 + (sweep == 0 ? 4 + 4 * sz : 4 * sz));
+        const int64_t by = L.cnnz_d[c] * (sv + 4) + L.crows[c] * (4 + (sweep == 0 ? 4 + 4 * sz : 4 * sz));
         LAUNCH(ASMG_PROF_AUX_GS, by,
-               launch(h.prm.use_pdl, k_gs_aux_down<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SMd.off,
-                      SMd.col, SMd.val, L.sm_dinv.p, L.sm_rows.p, (const T*)SP.F.p, sweep == 0 ? 1 : 0, SP.fs[li].p,
+               launch(h.prm.use_pdl, k_gs_aux_down<T, V>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SMd.off,
+                      SMd.col, sell_vals(L.SMd, (const V*)nullptr), L.sm_dinv.p, L.sm_rows.p, (const T*)SP.F.p, sweep == 0 ? 1 : 0, SP.fs[li].p,
                       SP.us[li].p));
         ++launches;
       }
     }
     auto RS = view(L.RS);
-    LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sz + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
-           launch(h.prm.use_pdl, k_resid_aux<T>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, RS.val, L.rs_rows.p,
+    LAUNCH(ASMG_PROF_AUX_RESID, L.RS.nnz_real * (sv + 4) + L.nrs_real * (4 + 2 * sz) + L.nsm_real * sz,
+           launch(h.prm.use_pdl, k_resid_aux<T, V>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, sell_vals(L.RS, (const V*)nullptr), L.rs_rows.p,
                   (const T*)SP.us[li].p, SP.F.p));
     LAUNCH(ASMG_PROF_AUX_TRANSFER, L.nchild * (4 + sz) + L.npar * (8 + 2 * sz),
            launch(h.prm.use_pdl, k_restrict_aux<T>, nblk(L.npar, rows_tpb(L.npar)), rows_tpb(L.npar), s, L.npar, L.rp_id.p,
@@ -1144,8 +1151,8 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
   }
   g_prof_level = -1;
   if (nbot) {
-    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npre, true),
-           launch_smem(h.prm.use_pdl, k_small_down<T>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.F.p, npre));
+    LAUNCH(ASMG_PROF_AUX_SMALL, (small_bytes<T, V>(P, 0, nbot, npre, true)),
+           launch_smem(h.prm.use_pdl, k_small_down<T, V>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.F.p, npre));
     ++launches;
   }
   if (h.nc > 0) {
@@ -1154,8 +1161,8 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
     ++launches;
   }
   if (nbot) {
-    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, 0, nbot, npost, false),
-           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.U.p, npost));
+    LAUNCH(ASMG_PROF_AUX_SMALL, (small_bytes<T, V>(P, 0, nbot, npost, false)),
+           launch_smem(h.prm.use_pdl, k_small_up<T, V>, 1, SMALL_TPB, smem, s, SP.bot_desc.p, nbot, SP.U.p, npost));
     ++launches;
   }
   for (int li = nbot; li <= nlev - 1 - ndeep; ++li) {
@@ -1170,9 +1177,9 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
              launch(h.prm.use_pdl, k_up_init<T>, nblk(L.nsm, rows_tpb(L.nsm)), rows_tpb(L.nsm), s, L.nsm, L.sm_rows.p,
                     L.sm_par0.p, L.sm_par1.p, Tl.pos_ptr.p, Tl.pos.p, (const T*)SP.U.p, (const T*)SP.us[li].p,
                     (const T*)SP.fs[li].p, SP.ust[li].p, SP.fsl[li].p));
-      const int64_t by = Tl.nnz_real * (sz + 2) + (Tl.interior + Tl.halo) * (8 + 3 * sz) + Tl.interior * (4 + sz);
+      const int64_t by = Tl.nnz_real * (sv + 2) + (Tl.interior + Tl.halo) * (8 + 3 * sz) + Tl.interior * (4 + sz);
       LAUNCH(ASMG_PROF_AUX_GS, by,
-             launch_smem(h.prm.use_pdl, k_tile_up<T>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p, Tl.blob_off.p,
+             launch_smem(h.prm.use_pdl, k_tile_up<T, V>, Tl.ntiles, Tl.tpb, Tl.smem(), s, Tl.loc_off.p, Tl.blob_off.p,
                          (const unsigned char*)Tl.blob.p, Tl.ext_off.p, Tl.phase.p, L.ncolours, Tl.maxblob,
                          Tl.maxloc, Tl.maxext, (const T*)SP.ust[li].p, (const T*)SP.fsl[li].p, SP.U.p, npost,
                          timeout_flag(S), h.prm.inject_timeout));
@@ -1204,19 +1211,28 @@ int enqueue_vcycle(asmg_s& h, Slot& S, cudaStream_t s) {
       for (int c = L.ncolours - 1; c >= 0; --c) {
         int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sz + 4) + L.crows[c] * (4 + 5 * sz),
-               launch(h.prm.use_pdl, k_gs_aux<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val, L.sm_dinv.p,
+        LAUNCH(ASMG_PROF_AUX_GS, L.cnnz[c] * (sv + 4) + L.crows[c] * (4 + 5 * sz),
+               launch(h.prm.use_pdl, k_gs_aux<T, V>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, sell_vals(L.SM, (const V*)nullptr), L.sm_dinv.p,
                       L.sm_rows.p, (const T*)SP.fs[li].p, SP.U.p));
         ++launches;
       }
   }
   g_prof_level = -1;
   if (ndeep) {
-    LAUNCH(ASMG_PROF_AUX_SMALL, small_bytes(P, nlev - ndeep, ndeep, npost, false),
-           launch_smem(h.prm.use_pdl, k_small_up<T>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.U.p, npost));
+    LAUNCH(ASMG_PROF_AUX_SMALL, (small_bytes<T, V>(P, nlev - ndeep, ndeep, npost, false)),
+           launch_smem(h.prm.use_pdl, k_small_up<T, V>, 1, SMALL_TPB, smem, s, SP.deep_desc.p, ndeep, SP.U.p, npost));
     ++launches;
   }
   return launches;
+}
+
+// the V-cycle with the level matrices read in BF16 (mixed form with
+// level_bf16) or in the arithmetic type
+template <class T>
+int enqueue_vcycle_vals(asmg_s& h, Slot& S, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value)
+    if (h.prm.level_bf16) return enqueue_vcycle<float, bf16v>(h, S, s);
+  return enqueue_vcycle<T, T>(h, S, s);
 }
 
 template <class T>
@@ -1275,7 +1291,7 @@ int enqueue_precond(asmg_s& h, Slot& S, const double* r, cudaStream_t s) {
     LAUNCH(ASMG_PROF_RESTRICT, P.PT.nnz_real * (sz + 4) + n * sz + 2 * nJ * sz,
            launch(h.prm.use_pdl, k_restrict_fine<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, SP.rho.p, SP.F.p, SP.U.p));
     launches += 2;
-    launches += enqueue_vcycle<T>(h, S, s);
+    launches += enqueue_vcycle_vals<T>(h, S, s);
     auto PP = view(P.P);
     LAUNCH(ASMG_PROF_PROLONG, P.P.nnz_real * (sz + 4) + nJ * sz + 2 * n * sz,
            launch(h.prm.use_pdl, k_prolong_fine<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, SP.U.p, SP.uf.p));
@@ -1502,12 +1518,19 @@ void setup_small(Prec<T>& P) {
   P.n_deep = nd;
   P.n_bottom = nb;
   const int smem = (int)small_smem<T>();
-  ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   // the attribute belongs to the kernel, not to this handle: every handle sets
-  // the same bound, the largest a tile may use
-  ASMG_CUDA(cudaFuncSetAttribute(k_tile_down<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
-  ASMG_CUDA(cudaFuncSetAttribute(k_tile_up<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
+  // the same bound, for tiles the largest a tile may use
+  auto attrs = [&](auto vtag) {
+    using V = decltype(vtag);
+    ASMG_CUDA(cudaFuncSetAttribute(k_small_down<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ASMG_CUDA(cudaFuncSetAttribute(k_small_up<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ASMG_CUDA(
+        cudaFuncSetAttribute(k_tile_down<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
+    ASMG_CUDA(
+        cudaFuncSetAttribute(k_tile_up<T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM_LIMIT));
+  };
+  attrs(T{});
+  if constexpr (std::is_same<T, float>::value) attrs(bf16v{});
 }
 
 // Work state of one solve in precision T: vectors, per-level saved values,
@@ -1571,15 +1594,20 @@ void alloc_slot_prec(asmg_s& h, Prec<T>& P, SlotPrec<T>& SP, cudaStream_t s) {
     d.ncol = M.ncol;
     d.nnew = M.nnew;
     d.npar = M.npar;
+    d.nnz_sm = (int)M.nnz_sm;
+    d.nnz_rs = (int)M.nnz_rs;
+    d.nchild = (int)M.nchild;
     for (int c = 0; c <= SMALL_MAXC; ++c) d.cs[c] = c <= M.ncol ? M.cs[c] : M.mS;
     d.gid = M.gid.p;
     d.sm_ptr = M.sm_ptr.p;
     d.sm_col = M.sm_col.p;
     d.sm_val = M.sm_val.p;
+    d.sm_v16 = M.sm_v16.p;
     d.dinv = M.dinv.p;
     d.rs_ptr = M.rs_ptr.p;
     d.rs_col = M.rs_col.p;
     d.rs_val = M.rs_val.p;
+    d.rs_v16 = M.rs_v16.p;
     d.nn_id = M.nn_id.p;
     d.nn_p0 = M.nn_p0.p;
     d.nn_p1 = M.nn_p1.p;

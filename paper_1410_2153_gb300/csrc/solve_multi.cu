@@ -18,6 +18,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <type_traits>
 #include <vector>
 
 #include "handle.h"
@@ -72,8 +73,8 @@ __device__ __forceinline__ void stk(T* p, const VK<T>& r) {
 }
 
 // acc[j] += sum_e a_e x[c_e][j] over a SELL row held in registers (the order of row_dot)
-template <class T, class X>
-__device__ __forceinline__ void row_dot_k(const Row<T>& R, const int32_t* __restrict__ col, const T* __restrict__ val,
+template <class T, class X, class V>
+__device__ __forceinline__ void row_dot_k(const Row<T>& R, const int32_t* __restrict__ col, const V* __restrict__ val,
                                           const X* x, T (&acc)[K]) {
 #pragma unroll
   for (int j = 0; j < K; ++j) acc[j] = 0;
@@ -86,7 +87,7 @@ __device__ __forceinline__ void row_dot_k(const Row<T>& R, const int32_t* __rest
     }
   for (int q = MAXW; q < R.w; ++q) {
     const int64_t e = R.b + ((int64_t)q << 5) + R.lane;
-    const T a = __ldg(val + e);
+    const T a = (T)ldg_val(val + e);
     const VK<X> xv = ldk<X>(x + (int64_t)__ldg(col + e) * K);
 #pragma unroll
     for (int j = 0; j < K; ++j) acc[j] += a * (T)xv.v[j];
@@ -187,9 +188,9 @@ __global__ void k_prolong_fine_k(int64_t n, const int64_t* __restrict__ off, con
 }
 
 // ------------------------------------------------------ auxiliary levels
-template <class T>
+template <class T, class V>
 __global__ void k_gs_aux_k(int64_t k0, int64_t nk, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                           const T* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
+                           const V* __restrict__ val, const T* __restrict__ dinv, const int32_t* __restrict__ rows,
                            const T* __restrict__ fs, T* U) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
@@ -218,9 +219,9 @@ __global__ void k_gs_aux_k(int64_t k0, int64_t nk, const int64_t* __restrict__ o
   pdl_trigger();
 }
 
-template <class T>
+template <class T, class V>
 __global__ void k_gs_aux_down_k(int64_t k0, int64_t nk, const int64_t* __restrict__ off,
-                                const int32_t* __restrict__ col, const T* __restrict__ val,
+                                const int32_t* __restrict__ col, const V* __restrict__ val,
                                 const T* __restrict__ dinv, const int32_t* __restrict__ rows, const T* __restrict__ F,
                                 int first, T* __restrict__ fs, T* us) {
   const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -253,7 +254,7 @@ __global__ void k_gs_aux_down_k(int64_t k0, int64_t nk, const int64_t* __restric
         const int64_t e = row.b + ((int64_t)q << 5) + row.lane;
         const int32_t c = __ldg(col + e);
         if (c < k0) {
-          const T a = __ldg(val + e);
+          const T a = (T)ldg_val(val + e);
           const VK<T> xv = ldk<T>(us + (int64_t)c * K);
 #pragma unroll
           for (int j = 0; j < K; ++j) acc[j] += a * xv.v[j];
@@ -275,9 +276,9 @@ __global__ void k_gs_aux_down_k(int64_t k0, int64_t nk, const int64_t* __restric
   pdl_trigger();
 }
 
-template <class T>
+template <class T, class V>
 __global__ void k_resid_aux_k(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                              const T* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
+                              const V* __restrict__ val, const int32_t* __restrict__ rows, const T* __restrict__ U,
                               T* __restrict__ F) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int32_t i = -1;
@@ -421,15 +422,15 @@ constexpr size_t small_smem_k() {
 }
 
 // acc[j] - sum_p val[p] x[col[p]][j] over p0 <= p < p1 (the order of small_row)
-template <class T>
-__device__ __forceinline__ void small_row_k(T (&acc)[K], int p0, int p1, const T* __restrict__ val,
+template <class T, class V>
+__device__ __forceinline__ void small_row_k(T (&acc)[K], int p0, int p1, const V* __restrict__ val,
                                             const uint16_t* __restrict__ col, const T* x) {
   T v[SMALL_B_K];
   uint16_t c[SMALL_B_K];
 #pragma unroll
   for (int q = 0; q < SMALL_B_K; ++q)
     if (p0 + q < p1) {
-      v[q] = val[p0 + q];
+      v[q] = (T)val_of(val[p0 + q]);
       c[q] = col[p0 + q];
     }
 #pragma unroll
@@ -439,14 +440,14 @@ __device__ __forceinline__ void small_row_k(T (&acc)[K], int p0, int p1, const T
       for (int j = 0; j < K; ++j) acc[j] -= v[q] * x[(int)c[q] * K + j];
     }
   for (int p = p0 + SMALL_B_K; p < p1; ++p) {
-    const T a = val[p];
+    const T a = (T)val_of(val[p]);
     const int cc = col[p];
 #pragma unroll
     for (int j = 0; j < K; ++j) acc[j] -= a * x[cc * K + j];
   }
 }
 
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(SMALL_TPB_K, 1)
     k_small_down_k(const SmallDesc<T>* __restrict__ D, int nlev, T* F, int nu) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -455,10 +456,12 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
   T* Fl = Ul + LM * K;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + LM * K);
   int32_t* Prs = Psm + LM + 1;
+  if (nlev > 0) small_prefetch(D, true);
   pdl_wait();
   for (int d = 0; d < nlev; ++d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
+    if (d + 1 < nlev) small_prefetch(D + d + 1, true);
     for (int k = threadIdx.x; k <= mE; k += blockDim.x) {
       if (k < mE) {
         const VK<T> f = ldk<T>(F + (int64_t)L.gid[k] * K);
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
           T acc[K];
 #pragma unroll
           for (int j = 0; j < K; ++j) acc[j] = Fl[k * K + j];
-          small_row_k(acc, Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
+          small_row_k(acc, Psm[k], Psm[k + 1], sm_vals(L, (const V*)nullptr), L.sm_col, Ul);
           const T di = L.dinv[k];
 #pragma unroll
           for (int j = 0; j < K; ++j) Ul[k * K + j] += acc[j] * di;
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
       T acc[K];
 #pragma unroll
       for (int j = 0; j < K; ++j) acc[j] = Fl[k * K + j];
-      small_row_k(acc, Prs[k], Prs[k + 1], L.rs_val, L.rs_col, Ul);
+      small_row_k(acc, Prs[k], Prs[k + 1], rs_vals(L, (const V*)nullptr), L.rs_col, Ul);
 #pragma unroll
       for (int j = 0; j < K; ++j) Fl[k * K + j] = acc[j];
     }
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
   pdl_trigger();
 }
 
-template <class T>
+template <class T, class V>
 __global__ void __launch_bounds__(SMALL_TPB_K, 1)
     k_small_up_k(const SmallDesc<T>* __restrict__ D, int nlev, T* U, int nu) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -530,10 +533,12 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + LM * K;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + LM * K);
+  if (nlev > 0) small_prefetch(D + nlev - 1, false);
   pdl_wait();
   for (int d = nlev - 1; d >= 0; --d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
+    if (d > 0) small_prefetch(D + d - 1, false);
     for (int k = threadIdx.x; k < mE; k += blockDim.x) {
       const VK<T> u = ldk<T>(U + (int64_t)L.gid[k] * K);
 #pragma unroll
@@ -571,7 +576,7 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
           T acc[K];
 #pragma unroll
           for (int j = 0; j < K; ++j) acc[j] = Fl[k * K + j];
-          small_row_k(acc, Psm[k], Psm[k + 1], L.sm_val, L.sm_col, Ul);
+          small_row_k(acc, Psm[k], Psm[k + 1], sm_vals(L, (const V*)nullptr), L.sm_col, Ul);
           const T di = L.dinv[k];
 #pragma unroll
           for (int j = 0; j < K; ++j) Ul[k * K + j] += acc[j] * di;
@@ -851,7 +856,8 @@ const double* fine_dinv_of<double>(asmg_s& h) { return h.dinv64.p; }
 template <>
 const float* fine_dinv_of<float>(asmg_s& h) { return h.p32.dinv_f.p; }
 
-template <class T>
+// V: how the auxiliary-level matrices are read (T, or bf16v with level_bf16)
+template <class T, class V>
 void enqueue_vcycle_k(asmg_s& h, MultiSlot& S, cudaStream_t s) {
   Prec<T>& P = prec_of<T>(h);
   MultiPrec<T>& M = mprec_of<T>(S);
@@ -860,7 +866,7 @@ void enqueue_vcycle_k(asmg_s& h, MultiSlot& S, cudaStream_t s) {
   const int nlev = (int)P.lev.size();
   const int ndeep = M.n_deep, nbot = M.n_bottom;
   const size_t smem = small_smem_k<T>();
-  if (ndeep) launch_smem(pdl, k_small_down_k<T>, 1, SMALL_TPB_K, smem, s, M.deep_desc.p, ndeep, M.F.p, npre);
+  if (ndeep) launch_smem(pdl, k_small_down_k<T, V>, 1, SMALL_TPB_K, smem, s, M.deep_desc.p, ndeep, M.F.p, npre);
   for (int li = nlev - 1 - ndeep; li >= nbot; --li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SMd = view(L.SMd);
@@ -868,19 +874,19 @@ void enqueue_vcycle_k(asmg_s& h, MultiSlot& S, cudaStream_t s) {
       for (int c = 0; c < L.ncolours; ++c) {
         const int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        launch(pdl, k_gs_aux_down_k<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SMd.off, SMd.col, SMd.val,
+        launch(pdl, k_gs_aux_down_k<T, V>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SMd.off, SMd.col, sell_vals(L.SMd, (const V*)nullptr),
                L.sm_dinv.p, L.sm_rows.p, (const T*)M.F.p, sweep == 0 ? 1 : 0, M.fs[li].p, M.us[li].p);
       }
     auto RS = view(L.RS);
-    launch(pdl, k_resid_aux_k<T>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, RS.val,
+    launch(pdl, k_resid_aux_k<T, V>, nblk(L.nrs, rows_tpb(L.nrs)), rows_tpb(L.nrs), s, L.nrs, RS.off, RS.col, sell_vals(L.RS, (const V*)nullptr),
            L.rs_rows.p, (const T*)M.us[li].p, M.F.p);
     launch(pdl, k_restrict_aux_k<T>, nblk(L.npar, rows_tpb(L.npar)), rows_tpb(L.npar), s, L.npar, L.rp_id.p,
            L.rp_ptr.p, L.rp_child.p, M.F.p);
   }
-  if (nbot) launch_smem(pdl, k_small_down_k<T>, 1, SMALL_TPB_K, smem, s, M.bot_desc.p, nbot, M.F.p, npre);
+  if (nbot) launch_smem(pdl, k_small_down_k<T, V>, 1, SMALL_TPB_K, smem, s, M.bot_desc.p, nbot, M.F.p, npre);
   if (h.nc > 0)
     launch(pdl, k_coarse_k<T>, nblk(h.nc * 32), TPB, s, h.nc, h.d_cid.p, h.d_cinv.p, (const T*)M.F.p, M.U.p);
-  if (nbot) launch_smem(pdl, k_small_up_k<T>, 1, SMALL_TPB_K, smem, s, M.bot_desc.p, nbot, M.U.p, npost);
+  if (nbot) launch_smem(pdl, k_small_up_k<T, V>, 1, SMALL_TPB_K, smem, s, M.bot_desc.p, nbot, M.U.p, npost);
   for (int li = nbot; li <= nlev - 1 - ndeep; ++li) {
     AuxLevelDev<T>& L = P.lev[li];
     auto SM = view(L.SM);
@@ -893,14 +899,21 @@ void enqueue_vcycle_k(asmg_s& h, MultiSlot& S, cudaStream_t s) {
       for (int c = L.ncolours - 1; c >= 0; --c) {
         const int64_t k0 = L.cstart[c], nk = L.cstart[c + 1] - L.cstart[c];
         if (!nk) continue;
-        launch(pdl, k_gs_aux_k<T>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, SM.val,
+        launch(pdl, k_gs_aux_k<T, V>, nblk(nk, rows_tpb(nk)), rows_tpb(nk), s, k0, nk, SM.off, SM.col, sell_vals(L.SM, (const V*)nullptr),
                L.sm_dinv.p, L.sm_rows.p, (const T*)M.fs[li].p, M.U.p);
       }
   }
-  if (ndeep) launch_smem(pdl, k_small_up_k<T>, 1, SMALL_TPB_K, smem, s, M.deep_desc.p, ndeep, M.U.p, npost);
+  if (ndeep) launch_smem(pdl, k_small_up_k<T, V>, 1, SMALL_TPB_K, smem, s, M.deep_desc.p, ndeep, M.U.p, npost);
 }
 
 // z = B_co r for KRHS columns (Algorithm 1, multiplicative, Gauss-Seidel)
+template <class T>
+void enqueue_vcycle_vals_k(asmg_s& h, MultiSlot& S, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value)
+    if (h.prm.level_bf16) return enqueue_vcycle_k<float, bf16v>(h, S, s);
+  enqueue_vcycle_k<T, T>(h, S, s);
+}
+
 template <class T>
 void enqueue_precond_k(asmg_s& h, MultiSlot& S, const double* r, cudaStream_t s) {
   Prec<T>& P = prec_of<T>(h);
@@ -926,7 +939,7 @@ void enqueue_precond_k(asmg_s& h, MultiSlot& S, const double* r, cudaStream_t s)
     auto PT = view(P.PT);
     launch(pdl, k_restrict_fine_k<T>, nblk(h.nJpad), TPB, s, h.nJpad, PT.off, PT.col, PT.val, (const T*)M.rho.p,
            M.F.p, M.U.p);
-    enqueue_vcycle_k<T>(h, S, s);
+    enqueue_vcycle_vals_k<T>(h, S, s);
     auto PP = view(P.P);
     launch(pdl, k_prolong_fine_k<T>, nblk(h.npad), TPB, s, h.npad, PP.off, PP.col, PP.val, (const T*)M.U.p, M.uf.p);
   }
@@ -1007,15 +1020,20 @@ void alloc_multi_prec(asmg_s& h, MultiPrec<T>& M, cudaStream_t s) {
     d.ncol = S.ncol;
     d.nnew = S.nnew;
     d.npar = S.npar;
+    d.nnz_sm = (int)S.nnz_sm;
+    d.nnz_rs = (int)S.nnz_rs;
+    d.nchild = (int)S.nchild;
     for (int c = 0; c <= SMALL_MAXC; ++c) d.cs[c] = c <= S.ncol ? S.cs[c] : S.mS;
     d.gid = S.gid.p;
     d.sm_ptr = S.sm_ptr.p;
     d.sm_col = S.sm_col.p;
     d.sm_val = S.sm_val.p;
+    d.sm_v16 = S.sm_v16.p;
     d.dinv = S.dinv.p;
     d.rs_ptr = S.rs_ptr.p;
     d.rs_col = S.rs_col.p;
     d.rs_val = S.rs_val.p;
+    d.rs_v16 = S.rs_v16.p;
     d.nn_id = S.nn_id.p;
     d.nn_p0 = S.nn_p0.p;
     d.nn_p1 = S.nn_p1.p;
@@ -1032,8 +1050,12 @@ void alloc_multi_prec(asmg_s& h, MultiPrec<T>& M, cudaStream_t s) {
   M.deep_desc.upload(deep, s);
   M.bot_desc.upload(bot, s);
   const int smem = (int)small_smem_k<T>();
-  ASMG_CUDA(cudaFuncSetAttribute(k_small_down_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  ASMG_CUDA(cudaFuncSetAttribute(k_small_up_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  ASMG_CUDA(cudaFuncSetAttribute(k_small_down_k<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  ASMG_CUDA(cudaFuncSetAttribute(k_small_up_k<T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if constexpr (std::is_same<T, float>::value) {
+    ASMG_CUDA(cudaFuncSetAttribute(k_small_down_k<T, bf16v>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ASMG_CUDA(cudaFuncSetAttribute(k_small_up_k<T, bf16v>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
 }
 
 void build_graph_k(asmg_s& h, MultiSlot& S, double rtol) {

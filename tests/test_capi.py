@@ -111,5 +111,9 @@ def test_variant_parameters_validated(lib, gen):
     assert _setup_code(lib, m, fine_sweeps=0) == lib.ASMG_ERR_INVALID_ARG
     assert _setup_code(lib, m, fine_sweeps=9) == lib.ASMG_ERR_INVALID_ARG
     assert _setup_code(lib, m, iteration=2) == lib.ASMG_ERR_INVALID_ARG
+    # BF16 level matrices: a switch of the mixed form only
+    assert lib.asmg_default_params().level_bf16 == 0
+    assert _setup_code(lib, m, level_bf16=2, precision=1) == lib.ASMG_ERR_INVALID_ARG
+    assert _setup_code(lib, m, level_bf16=1, precision=0) == lib.ASMG_ERR_INVALID_ARG
     p = lib.asmg_default_params()
     assert (p.smoother, p.additive, p.fine_sweeps, p.iteration) == (0, 0, 1, 0)
