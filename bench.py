@@ -393,6 +393,9 @@ def main():
     ap.add_argument("--no-pdl", action="store_true", help="launch without programmatic dependent launch")
     ap.add_argument("--batch-count", type=int, default=256, help="problems of the batch workload")
     ap.add_argument("--cpu-sample", default=None, help="workload of the CPU baseline (default: graded513 / kuhn49)")
+    ap.add_argument("--level-values", default="auto", choices=("auto", "fp32", "bf16"),
+                    help="storage of the auxiliary-level matrices in the mixed form; auto: BF16 when its iteration "
+                         "count is not above FP32's")
     args = ap.parse_args()
     if args.workload == "batch256":
         run_batch(args)
@@ -420,14 +423,23 @@ def main():
     sp = ctypes_stream = stream.cuda_stream
 
     mesh, f = _workload(args.workload, 1 + rank)
-    t0 = time.perf_counter()
-    solvers = {}
-    for prec in ([asmg.ASMG_MIXED] if args.no_fp64 else [asmg.ASMG_MIXED, asmg.ASMG_FP64]):
-        s = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1,
-                        use_pdl=0 if args.no_pdl else 1, **_solver_options(args.workload))
-        solvers[prec] = s
-    t_setup = time.perf_counter() - t0
-    s = solvers[asmg.ASMG_MIXED]
+    # the mixed form with the level matrices in FP32 and in BF16 (a storage
+    # choice the precision plan allows where the iteration count holds), and
+    # the plain FP64 form
+    variants = []
+    if args.level_values in ("auto", "fp32"):
+        variants.append(("mixed", asmg.ASMG_MIXED, {}))
+    if args.level_values in ("auto", "bf16"):
+        variants.append(("mixed_bf16", asmg.ASMG_MIXED, {"level_bf16": 1}))
+    if not args.no_fp64:
+        variants.append(("fp64", asmg.ASMG_FP64, {}))
+    solvers, t_setup = {}, {}
+    for key, prec, extra in variants:
+        t0 = time.perf_counter()
+        solvers[key] = asmg.Solver(mesh, precision=prec, stream=ctypes_stream, use_graph=0 if args.no_graph else 1,
+                                   use_pdl=0 if args.no_pdl else 1, **_solver_options(args.workload), **extra)
+        t_setup[key] = time.perf_counter() - t0
+    s = next(iter(solvers.values()))
     n = s.info("nfree")
     fd = torch.from_numpy(f).to(dev)
     b = s.mass_apply(fd)
@@ -440,13 +452,13 @@ def main():
         return rc, it
 
     results = {}
-    for prec, sol in solvers.items():
+    for key, sol in solvers.items():
         for _ in range(args.warmup):
             solve_dev(sol)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        clk = ClockSampler(local) if prec == asmg.ASMG_MIXED else None
+        clk = ClockSampler(local) if key != "fp64" else None
         if clk:
             clk.start()
             time.sleep(0.3)
@@ -463,7 +475,14 @@ def main():
         torch.cuda.synchronize()
         clocks = clk.stop() if clk else None
         ms, rate = replica_throughput(dist, dev, n * args.steps, e0.elapsed_time(e1))
-        results[prec] = dict(ms=ms, rate=rate, its=its, clocks=clocks)
+        results[key] = dict(ms=ms, rate=rate, its=its, clocks=clocks)
+
+    # the headline mixed form: BF16 level values unless they cost iterations
+    mkey = "mixed" if "mixed" in results else "mixed_bf16"
+    if "mixed" in results and "mixed_bf16" in results:
+        if np.median(results["mixed_bf16"]["its"]) <= np.median(results["mixed"]["its"]):
+            mkey = "mixed_bf16"
+    s = solvers[mkey]
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     bh = b.cpu().numpy()
@@ -481,7 +500,7 @@ def main():
     e2e_ms, e2e_rate = replica_throughput(dist, dev, n, e2e_s * 1e3)
     e2e_s = e2e_ms / 1e3
 
-    mix = results[asmg.ASMG_MIXED]
+    mix = results[mkey]
     ms_step = mix["ms"] / args.steps
     value = mix["rate"]
     it_mix = int(np.median(mix["its"]))
@@ -505,8 +524,9 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": _describe(args.workload),
                    "nfree": n, "elements": mesh.ne, "dim": mesh.dim, "rtol": RTOL, "precision": "mixed (FP32 V-cycle, FP64 CG)",
+                   "level_values": "bf16" if mkey == "mixed_bf16" else "fp32",
                    "iterations": it_mix, "aux_levels": s.info("J") - s.info("coarse"),
-                   "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup / len(solvers),
+                   "aux_dofs": s.info("naux", s.info("J")), "setup_s": t_setup[mkey],
                    "tiled_levels": {"down": [l for l in range(s.info("coarse") + 1, s.info("J") + 1)
                                              if s.info("ntiles", l) > 0],
                                     "up": [l for l in range(s.info("coarse") + 1, s.info("J") + 1)
@@ -528,8 +548,12 @@ def main():
         "kernels": kernels,
         "clocks": mix["clocks"],
     }
-    if asmg.ASMG_FP64 in results:
-        r64 = results[asmg.ASMG_FP64]
+    line["level_values"] = {
+        k: {"ms_per_step": results[k]["ms"] / args.steps, "iterations": int(np.median(results[k]["its"]))}
+        for k in ("mixed", "mixed_bf16") if k in results}
+    line["level_values"]["rule"] = "headline: BF16 level matrices when their iteration count is not above FP32's"
+    if "fp64" in results:
+        r64 = results["fp64"]
         ms64 = r64["ms"] / args.steps
         line["fp64"] = {"value": r64["rate"], "ms_per_step": ms64,
                         "iterations": int(np.median(r64["its"]))}
