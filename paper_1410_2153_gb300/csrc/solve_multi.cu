@@ -600,33 +600,21 @@ __device__ __forceinline__ void set_cond_k(MultiScalars* sc, int cond, cudaGraph
   if (use_hnd) cudaGraphSetConditional(hnd, cond ? 1u : 0u);
 }
 
-// y[j] = sum_e a_e x[c_e][j] for the row (the order of sell_dot)
-__device__ __forceinline__ void sell_dot_k(int64_t row, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                                           const double* __restrict__ val, const double* x, double (&y)[K]) {
-  const int64_t sl = row >> 5, lane = row & 31;
-  const int64_t b = __ldg(off + sl), w = (__ldg(off + sl + 1) - b) >> 5;
-#pragma unroll
-  for (int j = 0; j < K; ++j) y[j] = 0;
-  for (int64_t q = 0; q < w; ++q) {
-    const int64_t e = b + (q << 5) + lane;
-    const double a = __ldg(val + e);
-    const VK<double> xv = ldk<double>(x + (int64_t)__ldg(col + e) * K);
-#pragma unroll
-    for (int j = 0; j < K; ++j) y[j] += a * xv.v[j];
-  }
-}
-
 // r = b - A x; ||b||, ||r|| per column; scalars initialised, columns activated
 __global__ void k_pcg_init_k(int64_t n, SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
                              double* __restrict__ r, double* partial, unsigned int* ticket, MultiScalars* sc,
                              double rtol, int maxit, double* hist, cudaGraphConditionalHandle hnd, int use_hnd) {
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  Row<double> row;
+  if (i0 < n) row_load(row, i0, A.off, A.col, A.val);
   pdl_wait();
   double v[2 * K];
 #pragma unroll
   for (int j = 0; j < 2 * K; ++j) v[j] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = i0; i < n; i += st) {
+    if (i != i0) row_load(row, i, A.off, A.col, A.val);
     double ax[K];
-    sell_dot_k(i, A.off, A.col, A.val, x, ax);
+    row_dot_k<double, double>(row, A.col, A.val, x, ax);
     const VK<double> bi = ldk<double>(b + i * K);
     VK<double> ri;
 #pragma unroll
@@ -715,13 +703,18 @@ __global__ void k_pupd_k(int64_t n, const T* __restrict__ z, double* __restrict_
 // q = A p, <p, q>  ->  alpha per active column
 __global__ void k_spmv_dot_k(int64_t n, SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
                              double* partial, unsigned int* ticket, MultiScalars* sc) {
+  // the row's entries in registers at once, the first row before the wait
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  Row<double> row;
+  if (i0 < n) row_load(row, i0, A.off, A.col, A.val);
   pdl_wait();
   double v[K];
 #pragma unroll
   for (int j = 0; j < K; ++j) v[j] = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = i0; i < n; i += st) {
+    if (i != i0) row_load(row, i, A.off, A.col, A.val);
     double qi[K];
-    sell_dot_k(i, A.off, A.col, A.val, p, qi);
+    row_dot_k<double, double>(row, A.col, A.val, p, qi);
     const VK<double> pi = ldk<double>(p + i * K);
     VK<double> qo;
 #pragma unroll
