@@ -77,6 +77,13 @@ void transfer_rows(const MeshHost& m, const std::vector<int32_t>& vof, const SZT
 
 extern "C" {
 
+// BF16 bits of FP32 values as the library stores auxiliary-level values
+// (asmg_params::level_bf16)
+void shim_bf16(const float* x, uint16_t* y, int64_t n) {
+  for (int64_t k = 0; k < n; ++k) y[k] = asmg::bf16_bits(x[k]);
+}
+
+
 // dim 2 or 3; the tree as split prefixes per depth (cnt[d] of them in flat);
 // root box: amin[dim], side L; returns a handle (errors: see shim_error)
 void* shim_build(int dim, int64_t nv, const double* X, int64_t ne, const int32_t* E, const uint8_t* bflag,

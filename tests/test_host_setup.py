@@ -57,6 +57,7 @@ def shim(tmp_path_factory):
     lib.shim_nbsolve.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5
     lib.shim_level_nbsolve.restype = ctypes.c_int64
     lib.shim_level_nbsolve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.shim_bf16.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     return lib
 
 
@@ -618,3 +619,25 @@ def test_mixed_vcycle_from_library_structures_matches_oracle(shim, gen, name):
         assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
     finally:
         shim.shim_free(h)
+
+
+def test_bf16_rounding_is_round_to_nearest_even(shim):
+    # the library's FP32 -> BF16 rounding of level values against torch's
+    # conversion (round to nearest, ties to even) and against the definition
+    # on hand-made ties: x = (kept half) + exactly half an ulp of BF16
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+                        [0.0, -0.0, 1.0, -2.5, 4.0, -0.5, 1e-38, 3.0e38]]).astype(np.float32)
+    # finite kept halves (exponent below all ones), either sign
+    kept = rng.integers(0, 0x7F00, 64, dtype=np.uint32) | (rng.integers(0, 2, 64, dtype=np.uint32) << 15)
+    ties = ((kept << 16) | np.uint32(0x8000)).astype(np.uint32)
+    x = np.concatenate([x, ties.view(np.float32)])
+    y = np.zeros(x.size, dtype=np.uint16)
+    shim.shim_bf16(x.ctypes.data, y.ctypes.data, x.size)
+    ref = torch.from_numpy(x.copy()).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16)
+    assert np.array_equal(y, ref)
+    # the ties: the kept half rounds up exactly when it is odd
+    kept = (ties >> 16).astype(np.uint32)
+    want = np.where(kept & 1, kept + 1, kept).astype(np.uint16)
+    assert np.array_equal(y[-64:], want)
