@@ -196,33 +196,6 @@ __device__ __forceinline__ void l1_prefetch(const void* p, int64_t bytes) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(c + o));
 }
 
-// The setup data one level of a fused run reads (never written by a solve, so
-// it may be requested before the wait on the previous kernel): the level's
-// own descriptor, row pointers, entries and diagonal, and the tables of the
-// restriction (down) or of the new nodes' parents (up).  Its phases then read
-// these from L1 rather than waiting on L2 at every colour phase.
-template <class T>
-__device__ __forceinline__ void small_prefetch(const SmallDesc<T>* Dd, bool down) {
-  const SmallDesc<T>& L = *Dd;
-  l1_prefetch(L.gid, (int64_t)L.mE * 4);
-  l1_prefetch(L.sm_ptr, (int64_t)(L.mS + 1) * 4);
-  l1_prefetch(L.sm_col, (int64_t)L.nnz_sm * 2);
-  l1_prefetch(L.sm_val, (int64_t)L.nnz_sm * sizeof(T));
-  l1_prefetch(L.dinv, (int64_t)L.mS * sizeof(T));
-  if (down) {
-    l1_prefetch(L.rs_ptr, (int64_t)(L.mE + 1) * 4);
-    l1_prefetch(L.rs_col, (int64_t)L.nnz_rs * 2);
-    l1_prefetch(L.rs_val, (int64_t)L.nnz_rs * sizeof(T));
-    l1_prefetch(L.rp_id, (int64_t)L.npar * 2);
-    l1_prefetch(L.rp_ptr, (int64_t)(L.npar + 1) * 4);
-    l1_prefetch(L.rp_child, (int64_t)L.nchild * 2);
-  } else {
-    l1_prefetch(L.nn_id, (int64_t)L.nnew * 2);
-    l1_prefetch(L.nn_p0, (int64_t)L.nnew * 4);
-    l1_prefetch(L.nn_p1, (int64_t)L.nnew * 4);
-  }
-}
-
 // the level's stored values: FP32/FP64, or their BF16 copy
 template <class T>
 __device__ __forceinline__ const T* sm_vals(const SmallDesc<T>& L, const T*) { return L.sm_val; }
@@ -232,6 +205,34 @@ template <class T>
 __device__ __forceinline__ const T* rs_vals(const SmallDesc<T>& L, const T*) { return L.rs_val; }
 template <class T>
 __device__ __forceinline__ const bf16v* rs_vals(const SmallDesc<T>& L, const bf16v*) { return L.rs_v16; }
+
+// The setup data one level of a fused run reads (never written by a solve, so
+// it may be requested before the wait on the previous kernel): the level's
+// own descriptor, row pointers, entries as the kernel reads them (V) and
+// diagonal, and the tables of the restriction (down) or of the new nodes'
+// parents (up).  Its phases then read
+// these from L1 rather than waiting on L2 at every colour phase.
+template <class T, class V>
+__device__ __forceinline__ void small_prefetch(const SmallDesc<T>* Dd, bool down) {
+  const SmallDesc<T>& L = *Dd;
+  l1_prefetch(L.gid, (int64_t)L.mE * 4);
+  l1_prefetch(L.sm_ptr, (int64_t)(L.mS + 1) * 4);
+  l1_prefetch(L.sm_col, (int64_t)L.nnz_sm * 2);
+  l1_prefetch(sm_vals(L, (const V*)nullptr), (int64_t)L.nnz_sm * sizeof(V));
+  l1_prefetch(L.dinv, (int64_t)L.mS * sizeof(T));
+  if (down) {
+    l1_prefetch(L.rs_ptr, (int64_t)(L.mE + 1) * 4);
+    l1_prefetch(L.rs_col, (int64_t)L.nnz_rs * 2);
+    l1_prefetch(rs_vals(L, (const V*)nullptr), (int64_t)L.nnz_rs * sizeof(V));
+    l1_prefetch(L.rp_id, (int64_t)L.npar * 2);
+    l1_prefetch(L.rp_ptr, (int64_t)(L.npar + 1) * 4);
+    l1_prefetch(L.rp_child, (int64_t)L.nchild * 2);
+  } else {
+    l1_prefetch(L.nn_id, (int64_t)L.nnew * 2);
+    l1_prefetch(L.nn_p0, (int64_t)L.nnew * 4);
+    l1_prefetch(L.nn_p1, (int64_t)L.nnew * 4);
+  }
+}
 
 }  // namespace kern
 }  // namespace asmg

@@ -741,12 +741,12 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   T* Fl = Ul + SMALL_LMAX;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
   int32_t* Prs = Psm + SMALL_LMAX + 1;
-  if (nlev > 0) small_prefetch(D, true);
+  if (nlev > 0) small_prefetch<T, V>(D, true);
   pdl_wait();
   for (int d = 0; d < nlev; ++d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
-    if (d + 1 < nlev) small_prefetch(D + d + 1, true);
+    if (d + 1 < nlev) small_prefetch<T, V>(D + d + 1, true);
     for (int k = threadIdx.x; k <= mE; k += blockDim.x) {
       if (k < mE) {
         const T f = F[L.gid[k]];
@@ -790,12 +790,12 @@ __global__ void __launch_bounds__(SMALL_TPB, 1)
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + SMALL_LMAX;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + SMALL_LMAX);
-  if (nlev > 0) small_prefetch(D + nlev - 1, false);
+  if (nlev > 0) small_prefetch<T, V>(D + nlev - 1, false);
   pdl_wait();
   for (int d = nlev - 1; d >= 0; --d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
-    if (d > 0) small_prefetch(D + d - 1, false);
+    if (d > 0) small_prefetch<T, V>(D + d - 1, false);
     for (int k = threadIdx.x; k < mE; k += blockDim.x) {
       Ul[k] = U[L.gid[k]];
       if (k < mS) Fl[k] = L.fs[k];

@@ -456,12 +456,12 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
   T* Fl = Ul + LM * K;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + LM * K);
   int32_t* Prs = Psm + LM + 1;
-  if (nlev > 0) small_prefetch(D, true);
+  if (nlev > 0) small_prefetch<T, V>(D, true);
   pdl_wait();
   for (int d = 0; d < nlev; ++d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
-    if (d + 1 < nlev) small_prefetch(D + d + 1, true);
+    if (d + 1 < nlev) small_prefetch<T, V>(D + d + 1, true);
     for (int k = threadIdx.x; k <= mE; k += blockDim.x) {
       if (k < mE) {
         const VK<T> f = ldk<T>(F + (int64_t)L.gid[k] * K);
@@ -533,12 +533,12 @@ __global__ void __launch_bounds__(SMALL_TPB_K, 1)
   T* Ul = reinterpret_cast<T*>(smraw);
   T* Fl = Ul + LM * K;
   int32_t* Psm = reinterpret_cast<int32_t*>(Fl + LM * K);
-  if (nlev > 0) small_prefetch(D + nlev - 1, false);
+  if (nlev > 0) small_prefetch<T, V>(D + nlev - 1, false);
   pdl_wait();
   for (int d = nlev - 1; d >= 0; --d) {
     const SmallDesc<T>& L = D[d];
     const int mS = L.mS, mE = L.mE;
-    if (d > 0) small_prefetch(D + d - 1, false);
+    if (d > 0) small_prefetch<T, V>(D + d - 1, false);
     for (int k = threadIdx.x; k < mE; k += blockDim.x) {
       const VK<T> u = ldk<T>(U + (int64_t)L.gid[k] * K);
 #pragma unroll
