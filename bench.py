@@ -135,8 +135,8 @@ class ClockSampler:
 
 def _measured_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when it was taken on another workload or the kernel source has changed
-    since (git blob hash of the source file)."""
+    when it was taken on another workload or a recorded source (the kernels,
+    the tile schedule) has changed since (git blob hashes of the files)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
@@ -144,9 +144,13 @@ def _measured_traffic(kernel: str, workload: str):
     d = json.load(open(p))
     if d.get("kernel") != kernel or d.get("workload") != workload:
         return None
-    src = open(os.path.join(ROOT, d["source"]), "rb").read()
-    blob = hashlib.sha1(b"blob %d\0" % len(src) + src).hexdigest()
-    return float(d["traffic_bytes_per_launch"]) if blob == d.get("source_blob") else None
+    # the kernels' source and the schedule's (tile sizes) must be the ones measured
+    sources = d.get("sources", {d.get("source"): d.get("source_blob")})
+    for path, want in sources.items():
+        src = open(os.path.join(ROOT, path), "rb").read()
+        if hashlib.sha1(b"blob %d\0" % len(src) + src).hexdigest() != want:
+            return None
+    return float(d["traffic_bytes_per_launch"])
 
 
 def _peaks():
