@@ -19,3 +19,23 @@ def test_reference_arm_json_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["config"]["iterations"] > 0
+
+
+def test_measured_traffic_follows_its_sources(tmp_path, monkeypatch):
+    # the bench reports the committed ncu traffic only while every source it
+    # names (the sweep kernels, the tile schedule) is the one measured
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "a.cu").write_bytes(b"kernel\n")
+    (tmp_path / "b.cpp").write_bytes(b"schedule\n")
+    blob = lambda b: __import__("hashlib").sha1(b"blob %d\0" % len(b) + b).hexdigest()
+    rec = {"kernel": "aux_gs", "workload": "graded2049", "traffic_bytes_per_launch": 123.0,
+           "sources": {"a.cu": blob(b"kernel\n"), "b.cpp": blob(b"schedule\n")}}
+    (tmp_path / "profiles" / "roofline_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._measured_traffic("aux_gs", "graded2049") == 123.0
+    assert bench._measured_traffic("aux_gs", "kuhn129") is None
+    assert bench._measured_traffic("fine_gs", "graded2049") is None
+    (tmp_path / "b.cpp").write_bytes(b"schedule changed\n")
+    assert bench._measured_traffic("aux_gs", "graded2049") is None
